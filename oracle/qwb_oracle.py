@@ -1,0 +1,399 @@
+"""Plain FP64 CPU oracle for the quantization-based W_p bounds.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import or call
+this module.  It shares no code, header, table or helper with the CUDA library
+(``paper_2506_00976_gb300``) and never imports it.
+
+Every function follows the paper (Bobrutsky & Moscovich, "Quantization-based
+Bounds on the Wasserstein Metric") step by step in numpy float64, in the
+paper's order and notation; the citation in each docstring names the section,
+equation or algorithm.  Library primitives (reshape, sum, min, matmul, sqrt)
+serve as steps; there is no blocking or fusion beyond what the definitions
+state, apart from chunking loops over output indices to bound memory.
+
+Conventions (readings where the paper is silent; each is listed in the design doc):
+  * grid points are 0-based pixel coordinates (row, col) with unit spacing;
+    flat index i = row * N + col (row-major);
+  * rho is the Euclidean distance and C_ij = rho(x_i, y_j)^p (Sec. 5);
+  * coarse index k = k1 * n + k2 for the block of rows k1*kappa.. and columns
+    k2*kappa..; block centres are the AvgPool of coordinates (Sec. 2.2);
+  * a coarse block of zero mass gets C-bar equal to the unweighted mean of the
+    cost over the block pair, and IPF sets a_i = 0 where (pi-hat b)_i = 0;
+  * the coarse potential is shifted so that <f~, mu~> = 0 before upscaling
+    (the lower bound does not change under such shifts);
+  * the upscaling interpolation R is bilinear in block-centre coordinates with
+    linear extrapolation outside the hull of the centres.
+
+Parity status: every function here is pinned by ``tests/test_oracle_*.py``
+against closed forms, a library LP solver, brute force or invariants.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import build as _build
+
+_SSP = None
+
+
+def _ssp_lib():
+    global _SSP
+    if _SSP is None:
+        lib = ctypes.CDLL(_build.build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        lib.oracle_ssp.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp, dp, dp,
+                                   ctypes.POINTER(ctypes.c_int)]
+        lib.oracle_ssp.restype = ctypes.c_int
+        _SSP = lib
+    return _SSP
+
+
+# --------------------------------------------------------------------------
+# Grid model: Sec. 2.1 (Kantorovich problem, W_p = L_C^(1/p)), Sec. 2.2
+# (regular grid [N]^d), Sec. 5 (rho = Euclidean).
+# --------------------------------------------------------------------------
+def grid_points(N: int) -> np.ndarray:
+    """All points of the N x N grid as an (N*N, 2) float64 array, row-major."""
+    r, c = np.meshgrid(np.arange(N, dtype=np.float64), np.arange(N, dtype=np.float64),
+                       indexing="ij")
+    return np.stack([r.ravel(), c.ravel()], axis=1)
+
+
+def ground_cost(X: np.ndarray, Y: np.ndarray, p: float) -> np.ndarray:
+    """C_ij = rho(x_i, y_j)^p with rho the Euclidean distance (Sec. 2.1, Sec. 5)."""
+    d2 = ((X[:, None, :] - Y[None, :, :]) ** 2).sum(axis=-1)
+    if p == 2:
+        return d2
+    if p == 1:
+        return np.sqrt(d2)
+    return d2 ** (p / 2.0)
+
+
+# --------------------------------------------------------------------------
+# Coarsening: Sec. 2.2 (SumPool of the measure, AvgPool of the coordinates).
+# --------------------------------------------------------------------------
+def sumpool(mu: np.ndarray, N: int, kappa: int) -> np.ndarray:
+    """mu~_k = mu(X_k): the mass of each kappa x kappa block (Sec. 2.2)."""
+    n = N // kappa
+    return mu.reshape(n, kappa, n, kappa).sum(axis=(1, 3)).ravel()
+
+
+def block_centres(N: int, kappa: int) -> np.ndarray:
+    """x~_k = mean(X_k), the AvgPool of the grid coordinates (Sec. 2.2)."""
+    n = N // kappa
+    return grid_points(N).reshape(n, kappa, n, kappa, 2).mean(axis=(1, 3)).reshape(-1, 2)
+
+
+def _block_row_pixels(N: int, kappa: int, k1: int) -> np.ndarray:
+    rows = np.arange(k1 * kappa, (k1 + 1) * kappa)
+    return (rows[:, None] * N + np.arange(N)[None, :]).ravel()
+
+
+# --------------------------------------------------------------------------
+# Coarse costs.
+# --------------------------------------------------------------------------
+def weighted_cost_numerators(mu, nu, N, kappa, p):
+    """num_kl = sum over x in X_k, y in Y_l of rho(x,y)^p mu(x) nu(y).
+
+    The numerator of the marginally weighted coarse cost (Sec. 3.2, the
+    equation defining C-bar; Alg. 3), summed over every fine pixel pair inside
+    each block pair.  Processed one block row of sources at a time.
+    """
+    n = N // kappa
+    M = n * n
+    X = grid_points(N)
+    num = np.empty((M, M))
+    for k1 in range(n):
+        I = _block_row_pixels(N, kappa, k1)
+        T = ground_cost(X[I], X, p) * nu[None, :]                       # rho^p nu(y)
+        T = T.reshape(len(I), n, kappa, n, kappa).sum(axis=(2, 4))       # sum y in Y_l
+        T = T.reshape(len(I), M) * mu[I][:, None]                        # times mu(x)
+        T = T.reshape(kappa, n, kappa, M).sum(axis=(0, 2))               # sum x in X_k
+        num[k1 * n:(k1 + 1) * n] = T
+    return num
+
+
+def coarse_cost_weighted(mu, nu, N, kappa, p):
+    """C-bar_kl = num_kl / (mu(X_k) nu(Y_l))  (Sec. 3.2, eq. for C-bar; Alg. 3).
+
+    Where mu(X_k) nu(Y_l) = 0 the paper's quotient is undefined; this oracle
+    then uses the unweighted mean of rho^p over the block pair (any finite
+    value is valid there because the coarse plan puts no mass on that entry).
+    """
+    num = weighted_cost_numerators(mu, nu, N, kappa, p)
+    mt, nt = sumpool(mu, N, kappa), sumpool(nu, N, kappa)
+    den = np.outer(mt, nt)
+    Cbar = np.empty_like(num)
+    pos = den > 0
+    Cbar[pos] = num[pos] / den[pos]
+    if not pos.all():
+        ones = np.ones(N * N)
+        mean = weighted_cost_numerators(ones, ones, N, kappa, p) / float(kappa) ** 4
+        Cbar[~pos] = mean[~pos]
+    return Cbar
+
+
+def coarse_cost_centre(N, kappa, p):
+    """C~_kl = rho(x~_k, x~_l)^p between block centres (Alg. 4 and Alg. 5)."""
+    Xc = block_centres(N, kappa)
+    return ground_cost(Xc, Xc, p)
+
+
+def coarse_cost_min(N, kappa, p):
+    """C^min_kl = min over x in X_k, y in Y_l of rho(x,y)^p (Sec. 3.3)."""
+    n = N // kappa
+    M = n * n
+    X = grid_points(N)
+    out = np.empty((M, M))
+    for k1 in range(n):
+        I = _block_row_pixels(N, kappa, k1)
+        T = ground_cost(X[I], X, p)
+        T = T.reshape(len(I), n, kappa, n, kappa).min(axis=(2, 4)).reshape(len(I), M)
+        out[k1 * n:(k1 + 1) * n] = T.reshape(kappa, n, kappa, M).min(axis=(0, 2))
+    return out
+
+
+# --------------------------------------------------------------------------
+# Exact Kantorovich problem (Sec. 2.1) by successive shortest paths (ssp.c).
+# --------------------------------------------------------------------------
+def exact_ot(C, a, b):
+    """Solve min <pi, C> over pi in Pi(a, b) and its dual exactly (Sec. 2.1).
+
+    Returns (plan, f, g, objective): an optimal coupling (dense) and optimal
+    Kantorovich potentials with f_i + g_j <= C_ij (Sec. 2.1, the set R(C)).
+    """
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    n, m = C.shape
+    plan = np.empty((n, m))
+    f = np.empty(n)
+    g = np.empty(m)
+    obj = ctypes.c_double()
+    rounds = ctypes.c_int()
+    dp = ctypes.POINTER(ctypes.c_double)
+    st = _ssp_lib().oracle_ssp(n, m, C.ctypes.data_as(dp), a.ctypes.data_as(dp),
+                               b.ctypes.data_as(dp), plan.ctypes.data_as(dp),
+                               f.ctypes.data_as(dp), g.ctypes.data_as(dp),
+                               ctypes.byref(obj), ctypes.byref(rounds))
+    if st != 0:
+        raise RuntimeError(f"oracle_ssp failed with status {st}")
+    return plan, f, g, obj.value
+
+
+def wasserstein_exact(mu, nu, N, p):
+    """W_p(mu, nu) = L_C(mu, nu)^(1/p) on the full grid (Sec. 2.1).  Small N only."""
+    X = grid_points(N)
+    _, _, _, obj = exact_ot(ground_cost(X, X, p), mu, nu)
+    return max(obj, 0.0) ** (1.0 / p)
+
+
+# --------------------------------------------------------------------------
+# Weighted-cost upper bound: Sec. 3.2, Theorem (weighted cost UB), Alg. 3.
+# --------------------------------------------------------------------------
+def ub_weighted(mu, nu, N, kappa, p):
+    mt, nt = sumpool(mu, N, kappa), sumpool(nu, N, kappa)
+    Cbar = coarse_cost_weighted(mu, nu, N, kappa, p)
+    plan, _, _, L = exact_ot(Cbar, mt, nt)
+    return {"ub_weighted": max(L, 0.0) ** (1.0 / p), "L_cbar": L, "plan": plan,
+            "cbar": Cbar}
+
+
+# --------------------------------------------------------------------------
+# Min-cost lower bound: Sec. 3.3, Theorem (locally minimal cost LB).
+# --------------------------------------------------------------------------
+def lb_mincost(mu, nu, N, kappa, p):
+    mt, nt = sumpool(mu, N, kappa), sumpool(nu, N, kappa)
+    _, _, _, L = exact_ot(coarse_cost_min(N, kappa, p), mt, nt)
+    return max(L, 0.0) ** (1.0 / p)
+
+
+# --------------------------------------------------------------------------
+# Primal upscaling upper bound: Sec. 3.4, Alg. 4.
+# --------------------------------------------------------------------------
+def upscaled_plan_apply(plan_c, v, N, kappa):
+    """(pi-hat v)_i where pi-hat = reshape^-1(P~* (x) K), K = kappa^(-2d) (Alg. 4).
+
+    With the uniform kernel, pi-hat_ij = kappa^-4 pi~*_{k(i) l(j)}, so
+    (pi-hat v)_i = kappa^-4 sum_l pi~*_{k(i) l} sum_{j in Y_l} v_j.
+    """
+    n = N // kappa
+    V = v.reshape(n, kappa, n, kappa).sum(axis=(1, 3)).ravel()
+    r = (plan_c @ V) * float(kappa) ** -4
+    return np.repeat(np.repeat(r.reshape(n, n), kappa, axis=0), kappa, axis=1).ravel()
+
+
+def upscaled_plan_apply_T(plan_c, u, N, kappa):
+    """(pi-hat^T u)_j, the transpose of ``upscaled_plan_apply`` (Alg. 4)."""
+    return upscaled_plan_apply(plan_c.T, u, N, kappa)
+
+
+def _safe_div(num, den):
+    out = np.zeros_like(num)
+    pos = den > 0
+    out[pos] = num[pos] / den[pos]
+    return out
+
+
+def ipf(mu, nu, plan_c, N, kappa, xi=1e-13, max_sweeps=1000):
+    """Iterative proportional fitting of pi-hat to (mu, nu) (Sec. 3.4 step 2, Alg. 4).
+
+    b <- 1; repeat a <- mu / (pi-hat b); b <- nu / (pi-hat^T a);
+    mu-hat <- a * (pi-hat b); nu-hat <- b * (pi-hat^T a)
+    until ||mu-hat - mu||_1 + ||nu - nu-hat||_1 < xi (or max_sweeps sweeps).
+    """
+    b = np.ones(N * N)
+    sweeps = 0
+    resid = np.inf
+    while sweeps < max_sweeps:
+        a = _safe_div(mu, upscaled_plan_apply(plan_c, b, N, kappa))
+        b = _safe_div(nu, upscaled_plan_apply_T(plan_c, a, N, kappa))
+        sweeps += 1
+        mu_hat = a * upscaled_plan_apply(plan_c, b, N, kappa)
+        nu_hat = b * upscaled_plan_apply_T(plan_c, a, N, kappa)
+        resid = np.abs(mu_hat - mu).sum() + np.abs(nu - nu_hat).sum()
+        if resid < xi:
+            break
+    return {"a": a, "b": b, "mu_hat": mu_hat, "nu_hat": nu_hat, "sweeps": sweeps,
+            "residual": resid}
+
+
+def upscaled_cost(a, b, plan_c, N, kappa, p):
+    """<pi-hat_xi, C> = sum over supp(pi-hat) of a_i pi-hat_ij b_j rho(x_i,y_j)^p.
+
+    Sec. 4 (the sum over the support of the upscaled coupling); Alg. 4 step 3.
+    supp(pi-hat) is the union of the fine block pairs X_k x Y_l with pi~*_kl > 0.
+    """
+    n = N // kappa
+    X = grid_points(N)
+    blk = np.arange(N * N).reshape(n, kappa, n, kappa).transpose(0, 2, 1, 3).reshape(n * n, -1)
+    total = 0.0
+    for k, l in zip(*np.nonzero(plan_c)):
+        I, J = blk[k], blk[l]
+        pij = plan_c[k, l] * float(kappa) ** -4
+        total += (a[I][:, None] * pij * b[J][None, :] * ground_cost(X[I], X[J], p)).sum()
+    return total
+
+
+def tv_weights(N, p):
+    """w_i = rho(x-bar, x_i)^p with x-bar = mean of the grid (Alg. 2 and Alg. 4)."""
+    X = grid_points(N)
+    xbar = X.mean(axis=0, keepdims=True)
+    return ground_cost(xbar, X, p)[0]
+
+
+def tv_correction(mu_hat, mu, N, p):
+    """Delta = TV_p^w(mu-hat, mu) = 2^(1-1/p) <w, |mu-hat - mu|>^(1/p) (eq. weighted TV)."""
+    s = float(np.dot(tv_weights(N, p), np.abs(mu_hat - mu)))
+    return 2.0 ** (1.0 - 1.0 / p) * s ** (1.0 / p)
+
+
+def ub_primal(mu, nu, N, kappa, p, xi=1e-13, max_sweeps=1000, plan_c=None):
+    """Upscaling upper bound W-hat_p + Delta_mu-hat + Delta_nu-hat (Sec. 3.4, Alg. 4)."""
+    if plan_c is None:
+        mt, nt = sumpool(mu, N, kappa), sumpool(nu, N, kappa)
+        plan_c, _, _, _ = exact_ot(coarse_cost_centre(N, kappa, p), mt, nt)
+    fit = ipf(mu, nu, plan_c, N, kappa, xi, max_sweeps)
+    w_hat_p = upscaled_cost(fit["a"], fit["b"], plan_c, N, kappa, p)
+    d_mu = tv_correction(fit["mu_hat"], mu, N, p)
+    d_nu = tv_correction(nu, fit["nu_hat"], N, p)
+    w_hat = max(w_hat_p, 0.0) ** (1.0 / p)
+    return {"ub_primal": w_hat + d_mu + d_nu, "w_hat": w_hat, "w_hat_p": w_hat_p,
+            "delta_mu": d_mu, "delta_nu": d_nu, "plan": plan_c, **fit}
+
+
+# --------------------------------------------------------------------------
+# Dual upscaling lower bound: Sec. 3.5, eq. (lazy c-transform), Alg. 5.
+# --------------------------------------------------------------------------
+def upsample_potential(f_c, N, kappa):
+    """f-hat = {R_{f~, X~}(x_i)}: bilinear interpolation of f~ at the block centres.
+
+    Sec. 3.5 allows any interpolation R; this one is bilinear in block-centre
+    coordinates, extrapolated linearly from the edge cells outside the hull of
+    the centres.  Coordinate t = (x - (kappa-1)/2) / kappa per axis.
+    """
+    n = N // kappa
+    F = np.asarray(f_c, dtype=np.float64).reshape(n, n)
+    if n == 1:
+        return np.full(N * N, F[0, 0])
+    t = (np.arange(N) - (kappa - 1) / 2.0) / kappa
+    k0 = np.clip(np.floor(t).astype(np.int64), 0, n - 2)
+    w = t - k0
+    r0, r1 = k0[:, None], (k0 + 1)[:, None]
+    c0, c1 = k0[None, :], (k0 + 1)[None, :]
+    wr, wc = w[:, None], w[None, :]
+    top = (1.0 - wc) * F[r0, c0] + wc * F[r0, c1]
+    bot = (1.0 - wc) * F[r1, c0] + wc * F[r1, c1]
+    return ((1.0 - wr) * top + wr * bot).ravel()
+
+
+def c_transform(h, N, p, chunk=1024):
+    """h^c_j = min_i rho(x_i, y_j)^p - h_i over the whole grid (Sec. 3.5; eq. lazy c-transform)."""
+    X = grid_points(N)
+    m = N * N
+    out = np.empty(m)
+    for j0 in range(0, m, chunk):
+        J = slice(j0, min(m, j0 + chunk))
+        out[J] = (ground_cost(X, X[J], p) - h[:, None]).min(axis=0)
+    return out
+
+
+def centre_potential(f_c, mu_c):
+    """Shift f~ so that <f~, mu~> = 0; the dual objective is unchanged (masses are 1)."""
+    return f_c - float(np.dot(f_c, mu_c))
+
+
+def lb_from_potential(mu, nu, N, kappa, p, f_c):
+    """Alg. 5 from the coarse potential on: f-hat, g = f-hat^c, f = g^c, LB."""
+    f_hat = upsample_potential(f_c, N, kappa)
+    g = c_transform(f_hat, N, p)
+    f = c_transform(g, N, p)            # the cost is symmetric, so g^c uses the same map
+    s = float(np.dot(f, mu) + np.dot(g, nu))
+    return {"lb": max(s, 0.0) ** (1.0 / p), "lb_p": s, "f_hat": f_hat, "f": f, "g": g}
+
+
+def lb_dual(mu, nu, N, kappa, p, f_c=None):
+    """Upscaling lower bound (<f, mu> + <g, nu>)^(1/p) (Sec. 3.5, eq. upscaling LB, Alg. 5)."""
+    mt = sumpool(mu, N, kappa)
+    if f_c is None:
+        nt = sumpool(nu, N, kappa)
+        _, f_c, _, _ = exact_ot(coarse_cost_centre(N, kappa, p), mt, nt)
+    f_c = centre_potential(np.asarray(f_c, dtype=np.float64), mt)
+    out = lb_from_potential(mu, nu, N, kappa, p, f_c)
+    out["f_coarse"] = f_c
+    return out
+
+
+def lb_grad_mu(mu, f, lb_p, p):
+    """Derivative of the lower bound along the simplex, d LB / d mu_i.
+
+    For fixed potentials the dual objective S = <f, mu> + <g, nu> is linear in
+    mu (Sec. 3.5, the proposition that a c-transformed pair is admissible);
+    along the mass-preserving direction e_i - mu its derivative is
+    f_i - <f, mu>, and LB = S^(1/p) gives (1/p) S^(1/p - 1) (f_i - <f, mu>).
+    """
+    if lb_p <= 0.0:
+        return np.zeros_like(f)
+    return (1.0 / p) * lb_p ** (1.0 / p - 1.0) * (f - float(np.dot(f, mu)))
+
+
+# --------------------------------------------------------------------------
+# Whole method for one pair.
+# --------------------------------------------------------------------------
+def bounds(mu, nu, N, kappa, p, xi=1e-13, max_sweeps=1000):
+    """All quantization bounds of Sec. 3 for one pair of N x N measures."""
+    mt, nt = sumpool(mu, N, kappa), sumpool(nu, N, kappa)
+    Ct = coarse_cost_centre(N, kappa, p)
+    plan_c, f_c, g_c, Lt = exact_ot(Ct, mt, nt)
+    ubw = ub_weighted(mu, nu, N, kappa, p)
+    ubp = ub_primal(mu, nu, N, kappa, p, xi, max_sweeps, plan_c=plan_c)
+    lbd = lb_dual(mu, nu, N, kappa, p, f_c=f_c)
+    return {"ub_weighted": ubw["ub_weighted"], "ub_primal": ubp["ub_primal"],
+            "lb": lbd["lb"], "lb_p": lbd["lb_p"], "w_hat_p": ubp["w_hat_p"],
+            "delta_mu": ubp["delta_mu"], "delta_nu": ubp["delta_nu"],
+            "ipf_sweeps": ubp["sweeps"], "ipf_residual": ubp["residual"],
+            "plan_coarse": plan_c, "f_coarse": lbd["f_coarse"], "L_ctilde": Lt,
+            "cbar": ubw["cbar"], "f": lbd["f"], "g": lbd["g"], "f_hat": lbd["f_hat"]}

@@ -1,0 +1,105 @@
+"""Seeded synthetic grid measures that stand in for the DOTmark images.
+
+This module generates inputs only: it holds none of the bound computation, and
+both the CUDA library's tests and the oracle's tests draw their inputs from it.
+Every measure is float64, non-negative, row-major N x N, normalised to mass 1.
+
+Value classes (the paper evaluates 10 images per class, all 45 pairs, Sec. 5):
+  white  -- i.i.d. uniform (0, 1] per pixel;
+  gauss  -- K ~ U{1..10} isotropic Gaussian blobs, centres uniform on the
+            grid, sigma ~ U[2, 6] * N/32 px, amplitudes U[0.5, 1], plus a
+            1e-3 floor per pixel;
+  cauchy -- the same with the profile 1 / (1 + r^2 / gamma^2),
+            gamma ~ U[2, 6] * N/32 px, plus the 1e-3 floor;
+  field  -- exp(z) for z a Gaussian-filtered (sigma = 4 px, reflect) standard
+            normal field rescaled to unit variance.
+The small blob case (``blobs3``) is three Gaussian blobs of amplitude 1 with
+sigma ~ U[2, 6] px plus the 1e-3 floor.
+
+Seeds: numpy PCG64 over SeedSequence([250600976, workload, class, image]).
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+CLASSES = ("white", "gauss", "cauchy", "field")
+_CLASS_ID = {"white": 0, "gauss": 1, "cauchy": 2, "field": 3, "blobs3": 4}
+_ROOT_SEED = 250600976
+
+
+def _rng(workload: int, cls: str, image: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(
+        np.random.SeedSequence([_ROOT_SEED, int(workload), _CLASS_ID[cls], int(image)])))
+
+
+def _blobs(rng, N, count, profile, amp_lo, amp_hi, scale_lo, scale_hi):
+    r, c = np.meshgrid(np.arange(N, dtype=np.float64), np.arange(N, dtype=np.float64),
+                       indexing="ij")
+    img = np.full((N, N), 1e-3)
+    for _ in range(count):
+        cr, cc = rng.uniform(0.0, N, size=2)
+        s = rng.uniform(scale_lo, scale_hi)
+        amp = 1.0 if amp_lo == amp_hi else rng.uniform(amp_lo, amp_hi)
+        d2 = (r - cr) ** 2 + (c - cc) ** 2
+        if profile == "gauss":
+            img += amp * np.exp(-0.5 * d2 / (s * s))
+        else:
+            img += amp / (1.0 + d2 / (s * s))
+    return img
+
+
+def make_measure(N: int, cls: str, workload: int = 0, image: int = 0) -> np.ndarray:
+    """One seeded N x N measure of class ``cls`` as a flat float64 array of mass 1."""
+    rng = _rng(workload, cls, image)
+    scale = N / 32.0
+    if cls == "white":
+        img = 1.0 - rng.random((N, N))                 # uniform on (0, 1]
+    elif cls == "gauss":
+        img = _blobs(rng, N, int(rng.integers(1, 11)), "gauss", 0.5, 1.0,
+                     2.0 * scale, 6.0 * scale)
+    elif cls == "cauchy":
+        img = _blobs(rng, N, int(rng.integers(1, 11)), "cauchy", 0.5, 1.0,
+                     2.0 * scale, 6.0 * scale)
+    elif cls == "blobs3":
+        img = _blobs(rng, N, 3, "gauss", 1.0, 1.0, 2.0, 6.0)
+    elif cls == "field":
+        from scipy.ndimage import gaussian_filter
+        z = gaussian_filter(rng.standard_normal((N, N)), sigma=4.0, mode="reflect")
+        z = (z - z.mean()) / z.std()
+        img = np.exp(z)
+    else:
+        raise ValueError(f"unknown class {cls!r}")
+    img = img.ravel()
+    return img / img.sum()
+
+
+def class_images(N: int, cls: str, workload: int, count: int = 10):
+    return [make_measure(N, cls, workload, i) for i in range(count)]
+
+
+def all_pairs(count: int = 10):
+    """The 45 unordered pairs (i, j), i < j, of ``count`` images."""
+    return list(itertools.combinations(range(count), 2))
+
+
+def class_pairs(N: int, cls: str, workload: int, count: int = 10):
+    """All 45 pairs (mu, nu) of one class, in a fixed order."""
+    imgs = class_images(N, cls, workload, count)
+    return [(imgs[i], imgs[j]) for i, j in all_pairs(count)]
+
+
+def uneven_workload(n_pairs: int = 200, workload: int = 3):
+    """Pairs with N ~ U{32,64,128,256}, kappa ~ U{4,8}, p ~ U{1,2}, class ~ U(4 classes)."""
+    rng = _rng(workload, "white", 10**6)
+    out = []
+    for t in range(n_pairs):
+        N = int(rng.choice([32, 64, 128, 256]))
+        kappa = int(rng.choice([4, 8]))
+        p = float(rng.choice([1, 2]))
+        cls = CLASSES[int(rng.integers(0, 4))]
+        mu = make_measure(N, cls, workload, 2 * t)
+        nu = make_measure(N, cls, workload, 2 * t + 1)
+        out.append({"N": N, "kappa": kappa, "p": p, "cls": cls, "mu": mu, "nu": nu})
+    return out
