@@ -1,0 +1,423 @@
+"""Benchmark: certified quantization-based W_2 bounds for many 128 x 128 pairs.
+
+Workload (one step): 180 pairs = 45 pairs (all pairs of 10 seeded images) in
+each of four synthetic value classes, 128 x 128 grids, p = 2, kappa = 4
+(32 x 32 coarse grid), FP32 cost reductions / IPF (50 sweeps) / c-transforms
+with FP64 bound sums (QWB_PREC_MIXED).
+
+value  -- bound pairs/s of the device passes of the method (SumPool + C-bar,
+          primal upscaling + IPF + upper bound, dual upscaling + two
+          c-transforms + lower bound) in the batched form (persistent launches
+          replayed from a CUDA graph), inputs resident in HBM; the exact coarse
+          solves (host network simplex) are timed separately (host_solve).
+e2e    -- the whole method per step through the public Batch API with host
+          buffers: pinned host -> device copies of the measures, the device
+          passes, the host exact solves, and the device -> host results.
+plain  -- the same device passes launched one pair per kernel launch.
+The CPU baseline / reference arm times the FP64 oracle on the same scope as
+`value` (its passes, with the coarse solutions precomputed), on a bounded
+sample of pairs, one pair per host core.
+
+Multi-GPU: pairs are independent, so each rank processes its own 180 pairs
+(weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N, KAPPA, P, SWEEPS = 128, 4, 2.0, 50
+CLASSES = ("white", "gauss", "cauchy", "field")
+METRIC = "bound pairs/s at 128×128 p=2 (batched vs plain); % of FP32/HBM roofline"
+WORKLOAD = ("180 pairs (4 value classes x 45 pairs) of 128x128 measures, p=2, kappa=4 "
+            "(32x32 coarse), FP32 cost/IPF(50 sweeps)/c-transform, FP64 bound sums")
+
+
+def _workload_arrays(rank: int):
+    from paper_2506_00976_gb300 import synth
+    mus, nus = [], []
+    for ci, cls in enumerate(CLASSES):
+        for mu, nu in synth.class_pairs(N, cls, workload=2 + 100 * rank, count=10):
+            mus.append(mu)
+            nus.append(nu)
+    return mus, nus
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.path) as fh:
+                for line in fh:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def _flush_l2(buf):
+    buf.add_(1.0)   # a 256 MiB write: larger than the 129 MB L2
+
+
+def _ct_traffic(digest):
+    """DRAM bytes per c-transform launch from the committed ncu summary, or None
+    when the kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "ctransform_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_source_sha256") != digest:
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def _kernel_digest():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_2506_00976_gb300", "csrc", "kernels.cu"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2506_00976_gb300 import api
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    mus_h, nus_h = _workload_arrays(rank)
+    n = len(mus_h)
+    m = N * N
+    host = torch.empty((n, 2, m), dtype=torch.float64).pin_memory()
+    for t in range(n):
+        host[t, 0] = torch.from_numpy(mus_h[t])
+        host[t, 1] = torch.from_numpy(nus_h[t])
+    dev_buf = host.to(dev)
+    mus = [dev_buf[t, 0] for t in range(n)]
+    nus = [dev_buf[t, 1] for t in range(n)]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    batch = api.Batch([(N, KAPPA, P)] * n, ipf_sweeps=SWEEPS, prec="mixed", device=dev)
+
+    # exact coarse solves once (host), timed separately
+    batch.coarse(mus, nus, batched=True)
+    t0 = time.perf_counter()
+    batch.solve(threads=args.threads)
+    host_solve_s = time.perf_counter() - t0
+    results = batch.results()
+    assert all(r["status"] == 0 for r in results)
+
+    stream = torch.cuda.current_stream(dev)
+
+    def step(batched):
+        batch.coarse(mus, nus, batched=batched)
+        batch.fine(mus, nus, batched=batched)
+
+    def timed(batched, steps, warmup, per_kernel=False):
+        for _ in range(warmup):
+            step(batched)
+        torch.cuda.synchronize()
+        times, kern = [], {}
+        launches0 = api.kernel_launch_count()
+        for _ in range(steps):
+            _flush_l2(flush)
+            barrier()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(batched)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            times.append(e0.elapsed_time(e1))
+            if per_kernel:
+                for k, v in batch.kernel_times().items():
+                    kern.setdefault(k, []).append(v)
+        launches = api.kernel_launch_count() - launches0
+        return times, kern, launches
+
+    with ClockSampler(local) as clk:
+        times_b, kern, launches = timed(True, args.steps, args.warmup, per_kernel=True)
+    clocks = clk.summary()
+    times_p, _, _ = timed(False, max(1, min(args.steps, 5)), 1)
+
+    ms_b = statistics.mean(times_b)
+    ms_p = statistics.mean(times_p)
+    ms_b_max, ms_p_max = ms_b, ms_p
+    if world > 1:
+        tt = torch.tensor([ms_b, ms_p], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_b_max, ms_p_max = float(tt[0]), float(tt[1])
+    value = n * world / (ms_b_max * 1e-3)
+    plain_value = n * world / (ms_p_max * 1e-3)
+
+    # e2e: whole method through the public API with host buffers
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    res_h = None
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        dev_buf.copy_(host, non_blocking=True)
+        batch.coarse(mus, nus, batched=True)
+        batch.solve(threads=args.threads)
+        batch.fine(mus, nus, batched=True)
+        res_h = batch.results()
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        tt = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt[0])
+    assert all(r["status"] == 0 for r in res_h)
+    h2d = int(host.numel() * host.element_size())
+    d2h = n * 8 * 14   # the result records read back per step
+
+    out = None
+    if rank == 0:
+        kmean = {k: statistics.mean(v) for k, v in kern.items() if all(x >= 0 for x in v)}
+        pair_ops_ct = 2.0 * float(m) * float(m) * n          # 2 ops per (input, output) pair
+        ct_ms = 0.5 * (kmean.get("ctransform_g", 0.0) + kmean.get("ctransform_f", 0.0))
+        props = torch.cuda.get_device_properties(dev)
+        sms = props.multi_processor_count
+        peaks = {}
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+                peaks = json.load(fh)
+        except (OSError, ValueError):
+            pass
+        sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
+        fp32_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12       # TFLOP/s
+        hbm = float(peaks.get("hbm_gbs") or 6800.0)
+        achieved = pair_ops_ct / (ct_ms * 1e-3) / 1e12 if ct_ms > 0 else None
+        traffic = _ct_traffic(_kernel_digest())
+        cbar_ms = kmean.get("cbar", 0.0)
+        cbar_flops = 2.0 * n * (N // KAPPA) ** 4 * (KAPPA ** 4 + KAPPA ** 2)
+        primal_ms = kmean.get("primal", 0.0)
+        ipf_bytes = 16.0 * m * SWEEPS * n
+        passes = {
+            "kernel_ms": {k: round(v, 4) for k, v in kmean.items()},
+            "cbar": {"bound": "alu", "achieved_tflops": cbar_flops / (cbar_ms * 1e-3) / 1e12 if cbar_ms else None,
+                     "frac_of_fp32": (cbar_flops / (cbar_ms * 1e-3) / 1e12) / fp32_peak if cbar_ms else None,
+                     "flops_per_launch": cbar_flops},
+            "ipf": {"bound": "hbm", "algorithmic_bytes_per_launch": ipf_bytes,
+                    "achieved_gbs": ipf_bytes / (primal_ms * 1e-3) / 1e9 if primal_ms else None,
+                    "frac_of_hbm": (ipf_bytes / (primal_ms * 1e-3) / 1e9) / hbm if primal_ms else None,
+                    "note": "L2-resident working set (180 x 256 KB per sweep); includes the certified "
+                            "FP64 sweep and the upper-bound assembly"},
+        }
+        out = {
+            "metric": METRIC, "value": round(value, 3), "unit": "pairs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_b_max, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "pairs_per_gpu": n, "N": N, "kappa": KAPPA, "p": P,
+                       "ipf_sweeps": SWEEPS, "precision": "mixed", "form": "batched",
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "value_scope": "device passes; exact coarse solves timed in host_solve; "
+                                      "e2e includes everything"},
+            "plain": {"value": round(plain_value, 3), "unit": "pairs/s",
+                      "ms_per_step": round(ms_p_max, 4),
+                      "batched_over_plain": round(value / plain_value, 3)},
+            "roofline": {"kernel": "ctransform (lazy min-plus c-transform)", "bound": "alu",
+                         "achieved": round(achieved, 3) if achieved else None,
+                         "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
+                         "frac": round(achieved / fp32_peak, 4) if achieved else None,
+                         "traffic": traffic,
+                         "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 ops x "
+                                        f"{sm_max:.0f} MHz (MEASURED_PEAKS sm_max_mhz)",
+                         "ops_per_launch": pair_ops_ct, "avg_launch_ms": round(ct_ms, 4)},
+            "passes": passes,
+            "host_solve": {"seconds": round(host_solve_s, 3),
+                           "pairs_per_s": round(n / host_solve_s, 3),
+                           "threads": args.threads or os.cpu_count(),
+                           "what": "network simplex on C~ and C-bar (M = 1024) per pair"},
+            "e2e": {"value": round(n * world / e2e_s, 3), "unit": "pairs/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(args.cpu_seconds, args.cpu_workers)
+    batch.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+# ----------------------------------------------------------------------------
+def _oracle_pair(args):
+    """The oracle's passes for one pair with its coarse solution given."""
+    mu, nu, plan, f_c = args
+    from oracle import qwb_oracle as O
+    t0 = time.perf_counter()
+    O.coarse_cost_weighted(mu, nu, N, KAPPA, P)
+    O.ub_primal(mu, nu, N, KAPPA, P, xi=1e-13, max_sweeps=SWEEPS, plan_c=plan)
+    O.lb_dual(mu, nu, N, KAPPA, P, f_c=f_c)
+    return time.perf_counter() - t0
+
+
+def _oracle_coarse(args):
+    mu, nu = args
+    from oracle import qwb_oracle as O
+    mt, nt = O.sumpool(mu, N, KAPPA), O.sumpool(nu, N, KAPPA)
+    plan, f_c, _, _ = O.exact_ot(O.coarse_cost_centre(N, KAPPA, P), mt, nt)
+    return plan, f_c
+
+
+def _pool(workers):
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(workers)
+
+
+def cpu_baseline(seconds, workers):
+    """Oracle pairs/s on a bounded sample: `workers` pairs in parallel, one per core."""
+    from oracle import build as oracle_build
+    oracle_build.build()
+    workers = workers or min(os.cpu_count() or 1, 16)
+    mus, nus = _workload_arrays(0)
+    idx = list(range(0, len(mus), max(1, len(mus) // workers)))[:workers]
+    with _pool(workers) as pool:
+        coarse = pool.map(_oracle_coarse, [(mus[i], nus[i]) for i in idx])
+        t0 = time.perf_counter()
+        pool.map(_oracle_pair, [(mus[i], nus[i], c[0], c[1]) for i, c in zip(idx, coarse)])
+        wall = time.perf_counter() - t0
+    return {"value": round(len(idx) / wall, 4), "unit": "pairs/s", "cores": workers,
+            "kind": "oracle",
+            "sample": f"{len(idx)} pairs of the 128x128 workload (one per core), oracle passes "
+                      f"(C-bar, IPF + upper bound, c-transforms + lower bound), coarse solutions "
+                      f"precomputed by the oracle's own solver; {wall:.1f} s wall"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    from oracle import build as oracle_build
+    oracle_build.build()
+    workers = args.cpu_workers or min(os.cpu_count() or 1, 16)
+    mus, nus = _workload_arrays(0)
+    idx = list(range(0, len(mus), max(1, len(mus) // workers)))[:workers]
+    with _pool(workers) as pool:
+        coarse = pool.map(_oracle_coarse, [(mus[i], nus[i]) for i in idx])
+        jobs = [(mus[i], nus[i], c[0], c[1]) for i, c in zip(idx, coarse)]
+        for _ in range(args.warmup):        # warm-up: one pair (imports, first-touch)
+            pool.map(_oracle_pair, jobs[:1])
+        times = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            pool.map(_oracle_pair, jobs)
+            times.append(time.perf_counter() - t0)
+    ms = statistics.mean(times) * 1e3
+    value = len(jobs) / (ms * 1e-3)
+    return {"metric": METRIC, "value": round(value, 4), "unit": "pairs/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "N": N, "kappa": KAPPA, "p": P,
+                       "ipf_sweeps": SWEEPS, "form": "FP64 CPU oracle",
+                       "value_scope": "oracle passes with precomputed coarse solutions"},
+            "cpu_baseline": {"value": round(value, 4), "unit": "pairs/s", "cores": workers,
+                             "kind": "oracle",
+                             "sample": f"{len(jobs)} pairs per step, one per core"},
+            "e2e": {"value": round(value, 4), "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--threads", type=int, default=0, help="host solver threads (0 = all cores)")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--cpu-workers", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "native":
+        args.warmup = 3
+    out = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

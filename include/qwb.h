@@ -1,0 +1,269 @@
+/*
+ * qwb.h -- C ABI of the GB300 library for certified quantization-based bounds
+ * on the p-Wasserstein metric between measures on regular N x N grids
+ * (Bobrutsky & Moscovich, "Quantization-based Bounds on the Wasserstein
+ * Metric").
+ *
+ * Problem statement (Sec. 2.1, Sec. 2.2, Sec. 5): mu, nu are probability
+ * vectors on the grid [N]^2 (row-major, flat index i = row * N + col, unit
+ * pixel spacing), rho is the Euclidean distance, C_ij = rho(x_i, y_j)^p,
+ * W_p = L_C(mu, nu)^(1/p).  The grid is coarsened by kappa x kappa blocks
+ * (N % kappa == 0, n = N / kappa, M = n^2 coarse cells; coarse index
+ * k = k1 * n + k2 for the block at block-row k1, block-column k2).
+ *
+ * Conventions shared by every entry point:
+ *   - Pointers named *_d are device pointers (cudaMalloc'd or PyTorch tensor
+ *     storage on the context's device); *_h are host pointers.  Every buffer
+ *     is owned by the caller and must stay valid until the call's work on
+ *     `stream` has completed.  The context owns its workspace, cost tables,
+ *     launch plans and captured graphs.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device work is enqueued on it; calls that fill a host result
+ *     (*_h outputs, qwb_result) synchronise the stream before returning.
+ *   - Every call returns a status (QWB_OK = 0).  No C++ exception crosses the
+ *     ABI.  qwb_last_error() gives a thread-local message for the last
+ *     failure on the calling thread.
+ *   - Input measures must be finite, non-negative and of mass 1 within 1e-12
+ *     (QWB_ERR_MASS otherwise).  Validation reads the measures on the device
+ *     with a small reduction; it is part of every call that takes measures.
+ *   - Certification: every bound is computed with directed rounding (FP32
+ *     round-down in the c-transform, round-up in cost reductions, FP64
+ *     directed sums) so that lb <= W_p <= ub_primal and W_p <= ub_weighted
+ *     hold for the real-number W_p of the given inputs.
+ *   - Precision: QWB_PREC_F64 runs every device pass in FP64;
+ *     QWB_PREC_MIXED runs the cost reductions, IPF sweeps and c-transforms in
+ *     FP32 and every bound sum and certificate in FP64.
+ */
+#ifndef QWB_H
+#define QWB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Status codes                                                              */
+/* ------------------------------------------------------------------------ */
+enum {
+    QWB_OK = 0,
+    QWB_ERR_INVALID_ARG = 1,   /* null pointer, N % kappa != 0, p < 1, sizes */
+    QWB_ERR_MASS = 2,          /* negative / non-finite entry or |mass - 1| > 1e-12 */
+    QWB_ERR_CUDA = 3,          /* a CUDA runtime call failed (message has details) */
+    QWB_ERR_NOT_CONVERGED = 4, /* the exact coarse solver hit its pivot cap */
+    QWB_ERR_TIMEOUT = 5,       /* a bounded device-side wait expired */
+    QWB_ERR_OOM = 6,           /* device or host allocation failed */
+    QWB_ERR_UNSUPPORTED = 7    /* valid problem outside this build's limits */
+};
+
+/* Flags for qwb_batch_create / qwb_bounds: passes a caller does not need.
+ * A skipped upper bound is reported as +inf, a skipped lower bound as 0
+ * (lb_p = -inf); both remain valid bounds. */
+enum {
+    QWB_FLAG_NO_WEIGHTED = 1,  /* skip pass (a)'s C-bar and its exact solve */
+    QWB_FLAG_NO_PRIMAL = 2,    /* skip pass (b) */
+    QWB_FLAG_NO_DUAL = 4       /* skip pass (c) */
+};
+
+/* Precision of the device passes (see the file comment). */
+typedef enum { QWB_PREC_F64 = 0, QWB_PREC_MIXED = 1 } qwb_prec;
+
+/* One problem: grid side N, block side kappa, order p (d = 2 fixed).
+ * Requirements: 1 <= kappa <= N, N % kappa == 0, p >= 1, N <= 1024. */
+typedef struct {
+    int32_t N;
+    int32_t kappa;
+    double p;
+} qwb_problem;
+
+/* Results for one pair.  Bounds are in the units of W_p (pixels); the *_p
+ * fields are the corresponding certified bounds on W_p^p. */
+typedef struct {
+    double ub_weighted;    /* Sec. 3.2 / Alg. 3: certified L_Cbar(mu~, nu~)^(1/p) >= W_p */
+    double ub_primal;      /* Sec. 3.4 / Alg. 4: W-hat_p + Delta_mu + Delta_nu >= W_p */
+    double lb;             /* Sec. 3.5 / Alg. 5: (<f,mu> + <g,nu>)^(1/p) <= W_p, clipped at 0 */
+    double lb_p;           /* certified lower bound on W_p^p (may be negative) */
+    double ub_weighted_p;  /* certified upper bound on L_Cbar */
+    double w_hat_p;        /* certified upper bound on <pi-hat_xi, C> */
+    double delta_mu;       /* TV correction of the first marginal (eq. weighted TV) */
+    double delta_nu;       /* TV correction of the second marginal */
+    double ipf_residual;   /* ||mu-hat - mu||_1 + ||nu - nu-hat||_1 of the final plan */
+    double t_coarse_cost_ms; /* per-pass device times (batch calls: whole batch) */
+    double t_solve_ms;       /* host exact coarse solves */
+    double t_primal_ms;
+    double t_dual_ms;
+    int32_t ipf_sweeps_done;
+    int32_t status;          /* per-pair status code */
+} qwb_result;
+
+typedef struct qwb_ctx qwb_ctx;
+typedef struct qwb_batch qwb_batch;
+
+/* ------------------------------------------------------------------------ */
+/* Context                                                                   */
+/* ------------------------------------------------------------------------ */
+/* Create a context bound to CUDA device `device`.  *out receives the handle.
+ * Errors: INVALID_ARG (out == NULL), CUDA (no such device). */
+int qwb_ctx_create(qwb_ctx** out, int device);
+/* Free the context, its workspace and graphs.  NULL is ignored. */
+void qwb_ctx_destroy(qwb_ctx* ctx);
+
+/* ------------------------------------------------------------------------ */
+/* Pass (a): coarse cost.  Sec. 2.2 (SumPool), Sec. 3.2 (the equation that    */
+/* defines the marginally weighted cost C-bar), Alg. 3.                       */
+/* ------------------------------------------------------------------------ */
+/* Computes mu~ = SumPool(mu), nu~ = SumPool(nu) (FP64, M each) and
+ *   C-bar_kl = sum_{x in X_k, y in Y_l} rho(x,y)^p mu(x) nu(y) / (mu~_k nu~_l)
+ * reduced over every fine pixel pair of every block pair, as an M x M
+ * row-major FP64 matrix rounded upward (each entry >= the real value).
+ * Where mu~_k nu~_l = 0 the entry is the unweighted mean of rho^p over the
+ * block pair.  mu_d, nu_d: N*N FP64.  cbar_d: M*M FP64 out.  mu_coarse_d,
+ * nu_coarse_d: M FP64 out (may be NULL).  Asynchronous on `stream`.
+ * Errors: INVALID_ARG, MASS, CUDA, OOM. */
+int qwb_coarse_cost(qwb_ctx* ctx, const qwb_problem* prob, const double* mu_d,
+                    const double* nu_d, double* cbar_d, double* mu_coarse_d,
+                    double* nu_coarse_d, qwb_prec prec, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Host exact coarse solve.  Sec. 2.1 (Kantorovich problem and its dual),     */
+/* Sec. 3.2 / Sec. 3.4 / Sec. 3.5 (the coarse problems), Sec. 4 (network      */
+/* simplex, at most 2M - 1 positive plan entries).                            */
+/* ------------------------------------------------------------------------ */
+/* Solves min <pi, C> over couplings of (a, b) and its dual exactly with the
+ * library's own network simplex (host, FP64).  C_h: n_src x n_dst row-major,
+ * non-negative.  a_h (n_src), b_h (n_dst): non-negative, equal total mass.
+ * Outputs (host, caller-allocated): the plan in CSR form with at most
+ * n_src + n_dst - 1 entries (rowptr_h: n_src + 1, col_h / val_h: capacity
+ * n_src + n_dst), *nnz_out, potentials f_h (n_src) and g_h (n_dst) with
+ * f_i + g_j <= C_ij, and *obj_out = <pi, C>.  Any output may be NULL except
+ * nnz_out when the plan is requested.  Needs no GPU.
+ * Errors: INVALID_ARG, NOT_CONVERGED (pivot cap), OOM. */
+int qwb_coarse_solve(int32_t n_src, int32_t n_dst, const double* C_h, const double* a_h,
+                     const double* b_h, int32_t* rowptr_h, int32_t* col_h, double* val_h,
+                     int32_t* nnz_out, double* f_h, double* g_h, double* obj_out);
+
+/* ------------------------------------------------------------------------ */
+/* Pass (b): primal upscaling + IPF + upper bound.  Sec. 3.4 (eq. coupling    */
+/* tensor upscale, Lemma on the normalised coupling, IPF paragraph, Theorem   */
+/* on the upscaling upper bound), Sec. 4 (cost over the support), Alg. 4.     */
+/* ------------------------------------------------------------------------ */
+/* Upscales the coarse plan pi~ (device CSR: pi_rowptr_d M+1, pi_col_d and
+ * pi_val_d nnz) with the uniform kernel K = kappa^-4 (pi-hat = pi~ (x) K,
+ * never materialised), fits its marginals to (mu, nu) by IPF sweeps
+ * (b <- 1; a <- mu / (pi-hat b); b <- nu / (pi-hat^T a)), then sums the
+ * cost of the fitted plan and adds the weighted-TV corrections.
+ * MIXED runs `sweeps` FP32 sweeps over the fine vectors followed by one FP64
+ * sweep that defines the certified plan; F64 runs them all in FP64.
+ * sweeps >= 1.  a_d, b_d (N*N FP64, may be NULL) receive the final scalings.
+ * out_h: fills ub_primal, w_hat_p, delta_mu, delta_nu, ipf_residual,
+ * ipf_sweeps_done (synchronises `stream`).
+ * Errors: INVALID_ARG, MASS, CUDA, OOM. */
+int qwb_primal_upscale_ipf(qwb_ctx* ctx, const qwb_problem* prob, const double* mu_d,
+                           const double* nu_d, const int32_t* pi_rowptr_d,
+                           const int32_t* pi_col_d, const double* pi_val_d, int32_t pi_nnz,
+                           int32_t sweeps, double* a_d, double* b_d, qwb_result* out_h,
+                           qwb_prec prec, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Pass (c): dual upscaling + c-transforms + lower bound.  Sec. 3.5 (the     */
+/* interpolation R, the c-transform and its double application, the          */
+/* proposition on admissible pairs, eq. upscaling lower bound), Sec. 4 (eq.  */
+/* lazy c-transform), Alg. 5.                                                 */
+/* ------------------------------------------------------------------------ */
+/* f_coarse_d (M FP64): a coarse potential f~ (any values; the optimal dual
+ * of the C~ problem gives the paper's bound).  The call shifts it so that
+ * <f~, mu~> = 0, upsamples it bilinearly at the block centres (linear
+ * extrapolation at the border) to f-hat, computes g = f-hat^c and
+ * f = g^c with round-down arithmetic (so f_i + g_j <= C_ij exactly), and
+ * sums lb_p = <f, mu> + <g, nu> rounded down in FP64.
+ * f_d, g_d (N*N FP64, may be NULL) receive the final potentials.
+ * out_h: fills lb, lb_p (synchronises `stream`).
+ * Errors: INVALID_ARG, MASS, CUDA, OOM. */
+int qwb_dual_upscale_ctransform(qwb_ctx* ctx, const qwb_problem* prob, const double* mu_d,
+                                const double* nu_d, const double* f_coarse_d, double* f_d,
+                                double* g_d, qwb_result* out_h, qwb_prec prec, void* stream);
+
+/* One lazy c-transform on the grid (Sec. 4, eq. lazy c-transform):
+ *   out_j = min_i rho(x_i, x_j)^p - h_i,  i, j over all N*N pixels,
+ * rounded down so that h_i + out_j <= C_ij holds exactly for the given h
+ * (MIXED: h is rounded up to FP32 first; the result is FP32 widened to
+ * FP64).  h_d, out_d: N*N FP64 device.  Asynchronous on `stream`.
+ * Errors: INVALID_ARG, CUDA, OOM. */
+int qwb_ctransform(qwb_ctx* ctx, int32_t N, double p, const double* h_d, double* out_d,
+                   qwb_prec prec, void* stream);
+
+/* Gradient of the lower bound with respect to the source measure along the
+ * simplex (derived from the proposition of Sec. 3.5: for fixed potentials
+ * lb_p = <f, mu> + <g, nu> is linear in mu):
+ *   grad_i = (1/p) lb_p^(1/p - 1) (f_i - <f, mu>),  0 when lb_p <= 0.
+ * f_d: N*N FP64 (the f from qwb_dual_upscale_ctransform), mu_d: N*N FP64,
+ * grad_d: N*N FP64 out.  Asynchronous on `stream`.
+ * Errors: INVALID_ARG, CUDA. */
+int qwb_lb_adjoint(qwb_ctx* ctx, int32_t N, double p, const double* f_d, const double* mu_d,
+                   double lb_p, double* grad_d, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Whole method for many pairs (Sec. 3.2 - 3.5; Alg. 3, 4, 5 together).       */
+/* ------------------------------------------------------------------------ */
+/* For each pair t: pass (a) on the device, the exact solves of the C~ and
+ * C-bar coarse problems on the host (n_threads worker threads, 0 = all
+ * cores), then passes (b) and (c) on the device.  mu_d[t], nu_d[t]: device
+ * pointers (host arrays of n_pairs pointers).  batched = 0 launches one pair
+ * per kernel launch; batched = 1 runs each pass for all pairs in persistent
+ * launches replayed from a captured CUDA graph.  ipf_sweeps as in
+ * qwb_primal_upscale_ipf.  out_h: n_pairs results (synchronises `stream`).
+ * Errors: any of the above; per-pair codes are in out_h[t].status. */
+int qwb_bounds(qwb_ctx* ctx, int32_t n_pairs, const qwb_problem* probs_h,
+               const double* const* mu_d, const double* const* nu_d, int32_t ipf_sweeps,
+               int32_t flags, qwb_result* out_h, qwb_prec prec, int32_t batched,
+               int32_t n_threads, void* stream);
+
+/* The same method split into its steps, so that the device passes and the
+ * host solves can be timed separately.  A batch owns the workspace and the
+ * coarse solutions of n_pairs problems.
+ *   qwb_batch_create   -- validate problems, allocate, build launch plans
+ *   qwb_batch_coarse   -- pass (a) for every pair (device, asynchronous)
+ *   qwb_batch_solve    -- exact C~ and C-bar solves for every pair (host;
+ *                         synchronises `stream` to read C-bar)
+ *   qwb_batch_fine     -- passes (b) and (c) for every pair (device,
+ *                         asynchronous; needs a completed qwb_batch_solve)
+ *   qwb_batch_results  -- synchronise and copy the per-pair results out
+ *   qwb_batch_potentials -- copy pair t's final dual potentials f, g
+ *                         (N*N FP64 each, device, either may be NULL)
+ * The pointer arrays must hold the same measures in coarse and fine;
+ * qwb_batch_fine uses the coarse solutions of the most recent
+ * qwb_batch_solve (re-run solve after the measures change).
+ * flags: QWB_FLAG_* bits.  Errors of every step: INVALID_ARG, MASS, CUDA,
+ * NOT_CONVERGED, OOM, UNSUPPORTED. */
+int qwb_batch_create(qwb_ctx* ctx, int32_t n_pairs, const qwb_problem* probs_h,
+                     int32_t ipf_sweeps, int32_t flags, qwb_prec prec, qwb_batch** out);
+void qwb_batch_destroy(qwb_batch* batch);
+int qwb_batch_coarse(qwb_batch* batch, const double* const* mu_d, const double* const* nu_d,
+                     int32_t batched, void* stream);
+int qwb_batch_solve(qwb_batch* batch, int32_t n_threads, void* stream);
+int qwb_batch_fine(qwb_batch* batch, const double* const* mu_d, const double* const* nu_d,
+                   int32_t batched, void* stream);
+int qwb_batch_results(qwb_batch* batch, qwb_result* out_h, void* stream);
+int qwb_batch_potentials(qwb_batch* batch, int32_t pair, double* f_d, double* g_d, void* stream);
+/* Device time (ms) of each kernel of the last batched passes, in the order
+ * SumPool, C-bar, primal (IPF + upper bound), centre, upsample,
+ * c-transform f-hat -> g, c-transform g -> f, lower-bound sum; -1 where not
+ * measured.  Fills min(n, 8) values; call after the stream has completed. */
+int qwb_batch_kernel_times(qwb_batch* batch, double* ms_out, int32_t n);
+
+/* ------------------------------------------------------------------------ */
+/* Diagnostics                                                               */
+/* ------------------------------------------------------------------------ */
+/* Static name of a status code. */
+const char* qwb_status_string(int status);
+/* Message of the last failed call on this thread ("" if none). */
+const char* qwb_last_error(void);
+/* Number of device kernels this library has launched in this process. */
+int64_t qwb_kernel_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QWB_H */

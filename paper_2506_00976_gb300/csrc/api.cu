@@ -1,0 +1,1007 @@
+// api.cu -- C ABI entry points (include/qwb.h): context, batches, passes.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "netsimplex.h"
+
+namespace qwb {
+
+int cuda_fail(cudaError_t e, const char* what) {
+    set_last_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return QWB_ERR_CUDA;
+}
+
+static int fail(int code, const std::string& msg) {
+    set_last_error(msg);
+    return code;
+}
+
+static size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+static int check_problem(const qwb_problem* p) {
+    if (!p) return fail(QWB_ERR_INVALID_ARG, "null problem");
+    if (p->N < 1 || p->N > 1024) return fail(QWB_ERR_INVALID_ARG, "N must be in [1, 1024]");
+    if (p->kappa < 1 || p->kappa > p->N || p->N % p->kappa != 0)
+        return fail(QWB_ERR_INVALID_ARG, "kappa must divide N");
+    if (!(p->p >= 1.0) || !std::isfinite(p->p)) return fail(QWB_ERR_INVALID_ARG, "p must be >= 1");
+    const int n = p->N / p->kappa;
+    if (n * n > 16384) return fail(QWB_ERR_UNSUPPORTED, "coarse grid larger than 128 x 128");
+    return QWB_OK;
+}
+
+}  // namespace qwb
+
+using namespace qwb;
+
+// --------------------------------------------------------------------------
+// Context
+// --------------------------------------------------------------------------
+struct CostTable {
+    int N;
+    double p;
+    bool f64;
+    void* lo;
+    void* hi;
+};
+
+struct qwb_ctx {
+    int device = 0;
+    int sm_count = 0;
+    std::mutex mtx;
+    std::vector<CostTable> tables;
+    std::vector<qwb_batch*> single_cache;   // single-pair batches for standalone calls
+};
+
+static int ctx_table(qwb_ctx* c, int N, double p, bool f64, cudaStream_t s, const void** lo,
+                     const void** hi) {
+    for (auto& t : c->tables)
+        if (t.N == N && t.p == p && t.f64 == f64) { *lo = t.lo; *hi = t.hi; return QWB_OK; }
+    CostTable t{N, p, f64, nullptr, nullptr};
+    const size_t bytes = (size_t)N * N * (f64 ? 8 : 4);
+    if (cudaMalloc(&t.lo, bytes) != cudaSuccess) return fail(QWB_ERR_OOM, "cost table allocation");
+    if (cudaMalloc(&t.hi, bytes) != cudaSuccess) { cudaFree(t.lo); return fail(QWB_ERR_OOM, "cost table allocation"); }
+    int st = launch_cost_tables(N, p, f64, t.lo, t.hi, s);
+    if (st) return st;
+    c->tables.push_back(t);
+    *lo = t.lo; *hi = t.hi;
+    return QWB_OK;
+}
+
+// --------------------------------------------------------------------------
+// Batch: workspace and launch plans for n pairs
+// --------------------------------------------------------------------------
+struct GraphEntry {
+    std::vector<const double*> mu, nu;
+    int kind;                 // 0 = coarse pass, 1 = fine passes
+    cudaGraphExec_t exec;
+    int64_t kernels;          // kernel nodes in the graph
+};
+
+struct qwb_batch {
+    qwb_ctx* ctx = nullptr;
+    int n = 0;
+    bool f64 = false;
+    int sweeps = 1;
+    int flags = 0;
+    std::vector<qwb_problem> probs;
+    std::vector<PairDev> pairs_h;
+    std::vector<int> Ms;
+    char* dmem = nullptr;
+    PairDev* pairs_d = nullptr;
+    PairOut* outs_d = nullptr;
+    int* pair_ids_d = nullptr;
+    PixItem* prep_items_d = nullptr;
+    PixItem* pix_items_d = nullptr;
+    CbarItem* cbar_items_d = nullptr;
+    CtItem* ct_b_items_d = nullptr;
+    CtItem* ct_p_items_d = nullptr;
+    std::vector<int> prep_off, prep_cnt, pix_off, pix_cnt, cbar_off, cbar_cnt, ct_off, ct_cnt;
+    int n_prep = 0, n_pix = 0, n_cbar = 0, n_ct_b = 0;
+    CtConfig ct_cfg_b, ct_cfg_p;
+    int kappa_code = 0, n_max = 0, N_max = 0, M_max = 0;
+    // coarse-plan staging (pinned host <-> device)
+    std::vector<size_t> plan_off;
+    size_t plan_bytes = 0;
+    char* plan_h = nullptr;
+    char* plan_d = nullptr;
+    // host copies for the exact solves
+    double* cbar_h = nullptr;   // pinned, sum of M^2
+    std::vector<size_t> cbar_h_off;
+    std::vector<double> mu_c_h, nu_c_h;
+    std::vector<size_t> mc_off;
+    std::vector<double> ubw, ubw_p;
+    std::vector<int> status;
+    bool solved = false;
+    double t_solve_ms = 0.0;
+    cudaEvent_t ev[6] = {};
+    cudaEvent_t kev[10] = {};   // per-kernel boundaries of the batched passes
+    bool ev_ok = false;
+    std::vector<const double*> cur_mu, cur_nu;
+    std::vector<GraphEntry> graphs;
+};
+
+static void batch_free(qwb_batch* b) {
+    if (!b) return;
+    for (auto& g : b->graphs) cudaGraphExecDestroy(g.exec);
+    if (b->dmem) cudaFree(b->dmem);
+    if (b->plan_d) cudaFree(b->plan_d);
+    if (b->plan_h) cudaFreeHost(b->plan_h);
+    if (b->cbar_h) cudaFreeHost(b->cbar_h);
+    if (b->ev_ok) {
+        for (auto& e : b->ev) cudaEventDestroy(e);
+        for (auto& e : b->kev) cudaEventDestroy(e);
+    }
+    delete b;
+}
+
+struct PlanLayout {   // per-pair coarse plan region
+    size_t rowptr, col, val, colptr, rowidx, valc, fco, total;
+};
+static PlanLayout plan_layout(int M, int cap_nnz = 0) {
+    PlanLayout L;
+    const int cap = std::max(2 * M, cap_nnz);
+    size_t o = 0;
+    L.rowptr = o; o = align_up(o + sizeof(int) * (M + 1), 16);
+    L.col = o; o = align_up(o + sizeof(int) * cap, 16);
+    L.val = o; o = align_up(o + sizeof(double) * cap, 16);
+    L.colptr = o; o = align_up(o + sizeof(int) * (M + 1), 16);
+    L.rowidx = o; o = align_up(o + sizeof(int) * cap, 16);
+    L.valc = o; o = align_up(o + sizeof(double) * cap, 16);
+    L.fco = o; o = align_up(o + sizeof(double) * M, 256);
+    L.total = o;
+    return L;
+}
+
+static CtConfig pick_ct_config(int N_min, bool all_p2) {
+    CtConfig c;
+    c.R = ct_pick_r(N_min, 8);
+    c.TC = c.R;
+    c.threads = 256;
+    c.p2 = all_p2;
+    return c;
+}
+
+// in_rows so that one pair is split into about `target` items
+static int pick_in_rows(int N, int tiles, int target) {
+    int splits = std::max(1, target / std::max(1, tiles));
+    splits = std::min(splits, N);
+    int rows = (N + splits - 1) / splits;
+    return std::max(1, rows);
+}
+
+static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps, int flags,
+                       qwb_prec prec, qwb_batch** out) {
+    if (n <= 0 || !probs || !out) return fail(QWB_ERR_INVALID_ARG, "batch: bad arguments");
+    if (prec != QWB_PREC_F64 && prec != QWB_PREC_MIXED) return fail(QWB_ERR_INVALID_ARG, "bad precision");
+    if (sweeps < 1) return fail(QWB_ERR_INVALID_ARG, "ipf sweeps must be >= 1");
+    for (int t = 0; t < n; ++t) { int st = check_problem(&probs[t]); if (st) return st; }
+    qwb_batch* b = new qwb_batch();
+    b->ctx = ctx; b->n = n; b->f64 = (prec == QWB_PREC_F64); b->sweeps = sweeps;
+    b->flags = flags;
+    b->probs.assign(probs, probs + n);
+    const size_t tsz = b->f64 ? 8 : 4;
+    // sizes
+    size_t off = 0;
+    std::vector<size_t> pair_off(n);
+    int kap0 = probs[0].kappa;
+    bool same_kap = true, all_p2 = true;
+    int N_gcd = 0;   // the c-transform's outputs per thread must divide every N
+    for (int t = 0; t < n; ++t) {
+        const int N = probs[t].N, kap = probs[t].kappa, nn = N / kap, M = nn * nn, m = N * N;
+        b->Ms.push_back(M);
+        same_kap &= (kap == kap0);
+        all_p2 &= (probs[t].p == 2.0);
+        { int a = N_gcd, c = N; while (c) { const int r = a % c; a = c; c = r; } N_gcd = a; }
+        b->N_max = std::max(b->N_max, N);
+        b->n_max = std::max(b->n_max, nn);
+        b->M_max = std::max(b->M_max, M);
+        b->kappa_code = std::max(b->kappa_code, kap);
+        pair_off[t] = off;
+        off += align_up(4 * sizeof(double) * M);
+        off += align_up(sizeof(double) * (size_t)M * M);
+        off += 5 * align_up(tsz * m);
+    }
+    if (!(same_kap && (kap0 == 1 || kap0 == 2 || kap0 == 4))) b->kappa_code = -b->kappa_code;
+    // descriptors and item lists
+    const int sm = ctx->sm_count > 0 ? ctx->sm_count : 148;
+    std::vector<PixItem> prep, pix;
+    std::vector<CbarItem> cb;
+    std::vector<CtItem> ctb, ctp;
+    b->ct_cfg_b = pick_ct_config(N_gcd, all_p2);
+    b->ct_cfg_p = b->ct_cfg_b;
+    const int tile_out = b->ct_cfg_b.threads * b->ct_cfg_b.R;
+    long total_tiles = 0;
+    for (int t = 0; t < n; ++t) total_tiles += ((long)probs[t].N * probs[t].N + tile_out - 1) / tile_out;
+    for (int t = 0; t < n; ++t) {
+        const int N = probs[t].N, nn = N / probs[t].kappa, M = nn * nn, m = N * N;
+        b->prep_off.push_back((int)prep.size());
+        for (int k = 0; k < M; k += 256) prep.push_back({t, k});
+        b->prep_cnt.push_back((int)prep.size() - b->prep_off.back());
+        b->pix_off.push_back((int)pix.size());
+        for (int i = 0; i < m; i += 256) pix.push_back({t, i});
+        b->pix_cnt.push_back((int)pix.size() - b->pix_off.back());
+        b->cbar_off.push_back((int)cb.size());
+        for (int k1 = 0; k1 < nn; ++k1)
+            for (int l1 = 0; l1 < nn; ++l1) cb.push_back({t, k1, l1, 0});
+        b->cbar_cnt.push_back((int)cb.size() - b->cbar_off.back());
+        const int tiles = (m + tile_out - 1) / tile_out;
+        // batched form: about 6 items per SM over the whole batch
+        const long target_b = std::max<long>(1, (long)6 * sm * tiles / std::max<long>(1, total_tiles));
+        const int rows_b = pick_in_rows(N, tiles, (int)std::min<long>(target_b * 1, 1 << 20));
+        for (int o = 0; o < m; o += tile_out)
+            for (int r0 = 0; r0 < N; r0 += rows_b) ctb.push_back({t, o, r0, std::min(rows_b, N - r0)});
+        // plain form: one pair fills the GPU, about 2 items per SM
+        const int rows_p = pick_in_rows(N, tiles, 2 * sm);
+        b->ct_off.push_back((int)ctp.size());
+        for (int o = 0; o < m; o += tile_out)
+            for (int r0 = 0; r0 < N; r0 += rows_p) ctp.push_back({t, o, r0, std::min(rows_p, N - r0)});
+        b->ct_cnt.push_back((int)ctp.size() - b->ct_off.back());
+        int maxrows = 0;
+        for (auto& it : ctb) maxrows = std::max(maxrows, it.in_rows);
+        for (auto& it : ctp) maxrows = std::max(maxrows, it.in_rows);
+        b->ct_cfg_b.in_rows = std::max(b->ct_cfg_b.in_rows, maxrows);
+        b->ct_cfg_p.in_rows = b->ct_cfg_b.in_rows;
+    }
+    b->n_prep = (int)prep.size(); b->n_pix = (int)pix.size(); b->n_cbar = (int)cb.size();
+    b->n_ct_b = (int)ctb.size();
+    // device allocation
+    const size_t o_pairs = align_up(off);
+    const size_t o_outs = align_up(o_pairs + sizeof(PairDev) * n);
+    const size_t o_ids = align_up(o_outs + sizeof(PairOut) * n);
+    const size_t o_prep = align_up(o_ids + sizeof(int) * n);
+    const size_t o_pix = align_up(o_prep + sizeof(PixItem) * prep.size());
+    const size_t o_cb = align_up(o_pix + sizeof(PixItem) * pix.size());
+    const size_t o_ctb = align_up(o_cb + sizeof(CbarItem) * cb.size());
+    const size_t o_ctp = align_up(o_ctb + sizeof(CtItem) * ctb.size());
+    const size_t total = align_up(o_ctp + sizeof(CtItem) * ctp.size());
+    if (cudaMalloc(&b->dmem, total) != cudaSuccess) { batch_free(b); return fail(QWB_ERR_OOM, "batch workspace"); }
+    b->pairs_d = (PairDev*)(b->dmem + o_pairs);
+    b->outs_d = (PairOut*)(b->dmem + o_outs);
+    b->pair_ids_d = (int*)(b->dmem + o_ids);
+    b->prep_items_d = (PixItem*)(b->dmem + o_prep);
+    b->pix_items_d = (PixItem*)(b->dmem + o_pix);
+    b->cbar_items_d = (CbarItem*)(b->dmem + o_cb);
+    b->ct_b_items_d = (CtItem*)(b->dmem + o_ctb);
+    b->ct_p_items_d = (CtItem*)(b->dmem + o_ctp);
+    // coarse-plan staging
+    size_t poff = 0;
+    for (int t = 0; t < n; ++t) { b->plan_off.push_back(poff); poff += plan_layout(b->Ms[t]).total; }
+    b->plan_bytes = poff;
+    if (cudaMalloc(&b->plan_d, poff) != cudaSuccess || cudaMallocHost(&b->plan_h, poff) != cudaSuccess) {
+        batch_free(b); return fail(QWB_ERR_OOM, "plan staging");
+    }
+    size_t coff = 0;
+    for (int t = 0; t < n; ++t) { b->cbar_h_off.push_back(coff); coff += (size_t)b->Ms[t] * b->Ms[t]; }
+    if (cudaMallocHost(&b->cbar_h, sizeof(double) * coff) != cudaSuccess) {
+        batch_free(b); return fail(QWB_ERR_OOM, "host C-bar buffer");
+    }
+    size_t moff = 0;
+    for (int t = 0; t < n; ++t) { b->mc_off.push_back(moff); moff += b->Ms[t]; }
+    b->mu_c_h.resize(moff); b->nu_c_h.resize(moff);
+    b->ubw.assign(n, 0.0); b->ubw_p.assign(n, 0.0); b->status.assign(n, QWB_OK);
+    // per-pair descriptors
+    cudaStream_t s0 = 0;
+    for (int t = 0; t < n; ++t) {
+        const int N = probs[t].N, kap = probs[t].kappa, nn = N / kap, M = nn * nn, m = N * N;
+        char* base = b->dmem + pair_off[t];
+        PairDev P;
+        std::memset(&P, 0, sizeof(P));
+        P.N = N; P.kappa = kap; P.n = nn; P.M = M; P.p = probs[t].p;
+        P.mu_c = (double*)base; P.nu_c = P.mu_c + M; P.mu_c_lo = P.nu_c + M; P.nu_c_lo = P.mu_c_lo + M;
+        base += align_up(4 * sizeof(double) * M);
+        P.cbar = (double*)base; base += align_up(sizeof(double) * (size_t)M * M);
+        P.fhat = base; base += align_up(tsz * m);
+        P.g = base; base += align_up(tsz * m);
+        P.f = base; base += align_up(tsz * m);
+        P.a = base; base += align_up(tsz * m);
+        P.b = base; base += align_up(tsz * m);
+        const void *lo, *hi;
+        int st = ctx_table(ctx, N, probs[t].p, b->f64, s0, &lo, &hi);
+        if (st) { batch_free(b); return st; }
+        P.ctab_lo = lo; P.ctab_hi = hi;
+        const PlanLayout L = plan_layout(M);
+        char* pd = b->plan_d + b->plan_off[t];
+        P.rowptr = (int*)(pd + L.rowptr); P.colidx = (int*)(pd + L.col); P.val = (double*)(pd + L.val);
+        P.colptr = (int*)(pd + L.colptr); P.rowidx = (int*)(pd + L.rowidx); P.valc = (double*)(pd + L.valc);
+        P.f_coarse = (double*)(pd + L.fco);
+        P.sweeps = sweeps;
+        P.ct_split = 2;
+        P.out_index = t;
+        b->pairs_h.push_back(P);
+    }
+    std::vector<int> ids(n);
+    for (int t = 0; t < n; ++t) ids[t] = t;
+    auto up = [&](void* dst, const void* src, size_t bytes) -> int {
+        if (bytes == 0) return QWB_OK;
+        QWB_CUDA(cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice));
+        return QWB_OK;
+    };
+    int st = up(b->pairs_d, b->pairs_h.data(), sizeof(PairDev) * n);
+    if (!st) st = up(b->pair_ids_d, ids.data(), sizeof(int) * n);
+    if (!st) st = up(b->prep_items_d, prep.data(), sizeof(PixItem) * prep.size());
+    if (!st) st = up(b->pix_items_d, pix.data(), sizeof(PixItem) * pix.size());
+    if (!st) st = up(b->cbar_items_d, cb.data(), sizeof(CbarItem) * cb.size());
+    if (!st) st = up(b->ct_b_items_d, ctb.data(), sizeof(CtItem) * ctb.size());
+    if (!st) st = up(b->ct_p_items_d, ctp.data(), sizeof(CtItem) * ctp.size());
+    if (!st) {
+        b->ev_ok = true;
+        for (auto& e : b->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) { b->ev_ok = false; }
+        for (auto& e : b->kev)
+            if (cudaEventCreate(&e) != cudaSuccess) { b->ev_ok = false; }
+        if (!b->ev_ok) st = fail(QWB_ERR_CUDA, "event creation");
+    }
+    if (!st) { cudaError_t e = cudaDeviceSynchronize(); if (e != cudaSuccess) st = cuda_fail(e, "batch set-up"); }
+    if (st) { batch_free(b); return st; }
+    *out = b;
+    return QWB_OK;
+}
+
+// Point the descriptors at new measure buffers (host -> device copy when changed).
+static int batch_set_measures(qwb_batch* b, const double* const* mu, const double* const* nu) {
+    if (!mu || !nu) return fail(QWB_ERR_INVALID_ARG, "null measure pointer array");
+    bool changed = b->cur_mu.size() != (size_t)b->n;
+    for (int t = 0; t < b->n; ++t) {
+        if (!mu[t] || !nu[t]) return fail(QWB_ERR_INVALID_ARG, "null measure pointer");
+        if (!changed && (b->cur_mu[t] != mu[t] || b->cur_nu[t] != nu[t])) changed = true;
+    }
+    if (!changed) return QWB_OK;
+    b->cur_mu.assign(mu, mu + b->n);
+    b->cur_nu.assign(nu, nu + b->n);
+    for (int t = 0; t < b->n; ++t) { b->pairs_h[t].mu = mu[t]; b->pairs_h[t].nu = nu[t]; }
+    QWB_CUDA(cudaMemcpy(b->pairs_d, b->pairs_h.data(), sizeof(PairDev) * b->n, cudaMemcpyHostToDevice));
+    return QWB_OK;
+}
+
+static int mark(qwb_batch* b, int i, cudaStream_t s) {
+    // external records become event nodes of a captured graph
+    if (b->ev_ok) QWB_CUDA(cudaEventRecordWithFlags(b->kev[i], s, cudaEventRecordExternal));
+    return QWB_OK;
+}
+
+static int enqueue_coarse(qwb_batch* b, bool batched, cudaStream_t s) {
+    int st;
+    if (batched) {
+        QWB_CUDA(cudaMemsetAsync(b->outs_d, 0, sizeof(PairOut) * b->n, s));
+        if ((st = mark(b, 0, s))) return st;
+        if ((st = launch_prepare(b->pairs_d, b->outs_d, b->prep_items_d, b->n_prep, b->f64, s))) return st;
+        if ((st = mark(b, 1, s))) return st;
+        if (!(b->flags & QWB_FLAG_NO_WEIGHTED) &&
+            (st = launch_cbar(b->pairs_d, b->cbar_items_d, b->n_cbar, b->kappa_code, b->n_max, b->N_max, b->f64, s)))
+            return st;
+        return mark(b, 2, s);
+    }
+    for (int t = 0; t < b->n; ++t) {
+        QWB_CUDA(cudaMemsetAsync(b->outs_d + t, 0, sizeof(PairOut), s));
+        if ((st = launch_prepare(b->pairs_d, b->outs_d, b->prep_items_d + b->prep_off[t], b->prep_cnt[t], b->f64, s))) return st;
+        if (b->flags & QWB_FLAG_NO_WEIGHTED) continue;
+        const int nn = b->probs[t].N / b->probs[t].kappa;
+        const int kc = (b->probs[t].kappa == 1 || b->probs[t].kappa == 2 || b->probs[t].kappa == 4)
+                           ? b->probs[t].kappa : -b->probs[t].kappa;
+        if ((st = launch_cbar(b->pairs_d, b->cbar_items_d + b->cbar_off[t], b->cbar_cnt[t], kc, nn,
+                              b->probs[t].N, b->f64, s))) return st;
+    }
+    return QWB_OK;
+}
+
+static int enqueue_fine(qwb_batch* b, bool batched, cudaStream_t s) {
+    int st;
+    const int sm = b->ctx->sm_count > 0 ? b->ctx->sm_count : 148;
+    const bool do_primal = !(b->flags & QWB_FLAG_NO_PRIMAL), do_dual = !(b->flags & QWB_FLAG_NO_DUAL);
+    if (batched) {
+        if ((st = mark(b, 3, s))) return st;
+        if (do_primal && (st = launch_primal(b->pairs_d, b->outs_d, b->pair_ids_d, b->n, b->M_max, 0, b->f64, s))) return st;
+        if ((st = mark(b, 4, s))) return st;
+        const int cap = 2 * sm;   // persistent grid: two CTAs per SM walk the item list
+        if (do_dual) {
+            if ((st = launch_centre(b->pairs_d, b->outs_d, b->pair_ids_d, b->n, s))) return st;
+            if ((st = mark(b, 5, s))) return st;
+            if ((st = launch_upsample(b->pairs_d, b->outs_d, b->pix_items_d, b->n_pix, b->f64, s))) return st;
+            if ((st = mark(b, 6, s))) return st;
+            if ((st = launch_ctransform(b->pairs_d, b->ct_b_items_d, b->n_ct_b, 0, b->ct_cfg_b, b->N_max, b->f64, cap, s))) return st;
+            if ((st = mark(b, 7, s))) return st;
+            if ((st = launch_ctransform(b->pairs_d, b->ct_b_items_d, b->n_ct_b, 1, b->ct_cfg_b, b->N_max, b->f64, cap, s))) return st;
+            if ((st = mark(b, 8, s))) return st;
+            if ((st = launch_lbsum(b->pairs_d, b->outs_d, b->pair_ids_d, b->n, b->f64, s))) return st;
+        } else {
+            for (int i = 5; i <= 8; ++i) if ((st = mark(b, i, s))) return st;
+        }
+        return mark(b, 9, s);
+    }
+    for (int t = 0; t < b->n; ++t) {
+        const int* id = b->pair_ids_d + t;
+        const int M = b->Ms[t];
+        if (do_primal && (st = launch_primal(b->pairs_d, b->outs_d, id, 1, M, 0, b->f64, s))) return st;
+        if (!do_dual) continue;
+        if ((st = launch_centre(b->pairs_d, b->outs_d, id, 1, s))) return st;
+        if ((st = launch_upsample(b->pairs_d, b->outs_d, b->pix_items_d + b->pix_off[t], b->pix_cnt[t], b->f64, s))) return st;
+        CtConfig c = b->ct_cfg_p;
+        c.p2 = (b->probs[t].p == 2.0);
+        if ((st = launch_ctransform(b->pairs_d, b->ct_p_items_d + b->ct_off[t], b->ct_cnt[t], 0, c, b->probs[t].N, b->f64, 0, s))) return st;
+        if ((st = launch_ctransform(b->pairs_d, b->ct_p_items_d + b->ct_off[t], b->ct_cnt[t], 1, c, b->probs[t].N, b->f64, 0, s))) return st;
+        if ((st = launch_lbsum(b->pairs_d, b->outs_d, id, 1, b->f64, s))) return st;
+    }
+    return QWB_OK;
+}
+
+// Run a pass for the whole batch, through a captured CUDA graph when batched.
+static int run_pass(qwb_batch* b, int kind, bool batched, cudaStream_t s) {
+    if (!batched) return kind == 0 ? enqueue_coarse(b, false, s) : enqueue_fine(b, false, s);
+    for (auto& g : b->graphs)
+        if (g.kind == kind && g.mu == b->cur_mu && g.nu == b->cur_nu) {
+            QWB_CUDA(cudaGraphLaunch(g.exec, s));
+            count_launch(g.kernels);
+            return QWB_OK;
+        }
+    // capture on a private stream, then launch on the caller's stream
+    cudaStream_t cs;
+    QWB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    int st = QWB_OK;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) { cudaStreamDestroy(cs); return cuda_fail(e, "begin capture"); }
+    const int64_t before = qwb_kernel_launch_count();
+    st = kind == 0 ? enqueue_coarse(b, true, cs) : enqueue_fine(b, true, cs);
+    e = cudaStreamEndCapture(cs, &graph);
+    cudaStreamDestroy(cs);
+    const int64_t captured = qwb_kernel_launch_count() - before;
+    count_launch(-captured);                            // captured, not yet launched
+    if (st) { if (graph) cudaGraphDestroy(graph); return st; }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    GraphEntry g{b->cur_mu, b->cur_nu, kind, nullptr, captured};
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    b->graphs.push_back(g);
+    QWB_CUDA(cudaGraphLaunch(g.exec, s));
+    count_launch(g.kernels);
+    return QWB_OK;
+}
+
+// ---- host exact solves ---------------------------------------------------
+static void centre_cost(const qwb_problem& pr, std::vector<double>& C) {
+    const int nn = pr.N / pr.kappa, M = nn * nn;
+    C.resize((size_t)M * M);
+    for (int k = 0; k < M; ++k)
+        for (int l = 0; l < M; ++l) {
+            const double d1 = (double)pr.kappa * (k / nn - l / nn);
+            const double d2 = (double)pr.kappa * (k % nn - l % nn);
+            const double s = d1 * d1 + d2 * d2;
+            C[(size_t)k * M + l] = pr.p == 2.0 ? s : (pr.p == 1.0 ? std::sqrt(s) : std::pow(s, 0.5 * pr.p));
+        }
+}
+
+static int solve_pair(qwb_batch* b, int t) {
+    const qwb_problem& pr = b->probs[t];
+    const int M = b->Ms[t];
+    const double* mc = b->mu_c_h.data() + b->mc_off[t];
+    const double* nc = b->nu_c_h.data() + b->mc_off[t];
+    // (1) C~ problem: plan and potential for the primal and dual passes
+    std::vector<double> Ct;
+    centre_cost(pr, Ct);
+    NSSolution sol;
+    int st = network_simplex(M, M, Ct.data(), mc, nc, sol);
+    if (st) return st;
+    const PlanLayout L = plan_layout(M);
+    char* ph = b->plan_h + b->plan_off[t];
+    const int nnz = (int)sol.col.size();
+    std::memcpy(ph + L.rowptr, sol.rowptr.data(), sizeof(int) * (M + 1));
+    std::memcpy(ph + L.col, sol.col.data(), sizeof(int) * nnz);
+    std::memcpy(ph + L.val, sol.val.data(), sizeof(double) * nnz);
+    std::vector<int> cnt(M + 1, 0);
+    for (int e = 0; e < nnz; ++e) cnt[sol.col[e] + 1]++;
+    for (int l = 0; l < M; ++l) cnt[l + 1] += cnt[l];
+    int* colptr = (int*)(ph + L.colptr);
+    int* rowidx = (int*)(ph + L.rowidx);
+    double* valc = (double*)(ph + L.valc);
+    std::memcpy(colptr, cnt.data(), sizeof(int) * (M + 1));
+    std::vector<int> cur(cnt.begin(), cnt.end() - 1);
+    for (int k = 0; k < M; ++k)                   // rows in order: CSC rows sorted
+        for (int e = sol.rowptr[k]; e < sol.rowptr[k + 1]; ++e) {
+            const int pos = cur[sol.col[e]]++;
+            rowidx[pos] = k; valc[pos] = sol.val[e];
+        }
+    std::memcpy(ph + L.fco, sol.f.data(), sizeof(double) * M);
+    b->pairs_h[t].nnz = nnz;
+    // (2) C-bar problem: certified weighted-cost upper bound
+    if (b->flags & QWB_FLAG_NO_WEIGHTED) {
+        b->ubw_p[t] = HUGE_VAL; b->ubw[t] = HUGE_VAL;
+        return QWB_OK;
+    }
+    NSSolution sb;
+    const double* Cb = b->cbar_h + b->cbar_h_off[t];
+    st = network_simplex(M, M, Cb, mc, nc, sb);
+    if (st) return st;
+    double L_sum = 0.0;
+    const int nnzb = (int)sb.col.size();
+    std::vector<double> rowsum(M, 0.0), colsum(M, 0.0);
+    for (int k = 0; k < M; ++k)
+        for (int e = sb.rowptr[k]; e < sb.rowptr[k + 1]; ++e) {
+            L_sum += sb.val[e] * Cb[(size_t)k * M + sb.col[e]];
+            rowsum[k] += sb.val[e];
+            colsum[sb.col[e]] += sb.val[e];
+        }
+    // non-negative terms: |fl(sum) - sum| <= gamma_(nnz+1) * sum; round up
+    const double u = std::ldexp(1.0, -53);
+    const double L_up = L_sum * (1.0 + 2.0 * (nnzb + 4) * u);
+    // TV correction for the plan's marginal rounding errors (tiny)
+    // |computed - exact| of each row sum is at most (degree + 2) u times it
+    std::vector<int> rdeg(M, 0), cdeg(M, 0);
+    for (int k = 0; k < M; ++k)
+        for (int e = sb.rowptr[k]; e < sb.rowptr[k + 1]; ++e) { rdeg[k]++; cdeg[sb.col[e]]++; }
+    double dm = 0.0, dn = 0.0;
+    for (int k = 0; k < M; ++k) {
+        dm += std::fabs(rowsum[k] - mc[k]) + (rdeg[k] + 3) * u * (rowsum[k] + mc[k]);
+        dn += std::fabs(colsum[k] - nc[k]) + (cdeg[k] + 3) * u * (colsum[k] + nc[k]);
+    }
+    dm *= 1.0 + 4.0 * M * u;
+    dn *= 1.0 + 4.0 * M * u;
+    const double r = 0.5 * std::sqrt(2.0) * pr.N;   // radius of the grid (Sec. 3.4 remark)
+    const double p = pr.p;
+    const double tv = std::pow(2.0, 1.0 - 1.0 / p) * r * (std::pow(dm, 1.0 / p) + std::pow(dn, 1.0 / p));
+    b->ubw_p[t] = L_up;
+    b->ubw[t] = (std::pow(L_up, 1.0 / p) * (1.0 + 4 * u) + tv) * (1.0 + 4 * u);
+    return QWB_OK;
+}
+
+static int batch_solve(qwb_batch* b, int n_threads, cudaStream_t s) {
+    QWB_CUDA(cudaStreamSynchronize(s));
+    // read the coarse pass results
+    std::vector<PairOut> outs(b->n);
+    QWB_CUDA(cudaMemcpy(outs.data(), b->outs_d, sizeof(PairOut) * b->n, cudaMemcpyDeviceToHost));
+    for (int t = 0; t < b->n; ++t) {
+        const int M = b->Ms[t];
+        const PairDev& P = b->pairs_h[t];
+        QWB_CUDA(cudaMemcpyAsync(b->mu_c_h.data() + b->mc_off[t], P.mu_c, sizeof(double) * M, cudaMemcpyDeviceToHost, s));
+        QWB_CUDA(cudaMemcpyAsync(b->nu_c_h.data() + b->mc_off[t], P.nu_c, sizeof(double) * M, cudaMemcpyDeviceToHost, s));
+        if (!(b->flags & QWB_FLAG_NO_WEIGHTED))
+            QWB_CUDA(cudaMemcpyAsync(b->cbar_h + b->cbar_h_off[t], P.cbar, sizeof(double) * (size_t)M * M, cudaMemcpyDeviceToHost, s));
+    }
+    QWB_CUDA(cudaStreamSynchronize(s));
+    int first_bad = QWB_OK;
+    for (int t = 0; t < b->n; ++t) {
+        const PairOut& O = outs[t];
+        b->status[t] = QWB_OK;
+        if (O.bad_mu || O.bad_nu || !(std::fabs(O.mass_mu - 1.0) <= 1e-12) || !(std::fabs(O.mass_nu - 1.0) <= 1e-12)) {
+            b->status[t] = QWB_ERR_MASS;
+            if (!first_bad) first_bad = QWB_ERR_MASS;
+        }
+    }
+    if (first_bad) { b->solved = false; return fail(first_bad, "measures must be finite, non-negative and of mass 1 (1e-12)"); }
+    const auto t0 = std::chrono::steady_clock::now();
+    int nt = n_threads > 0 ? n_threads : (int)std::max(1u, std::thread::hardware_concurrency());
+    nt = std::min(nt, b->n);
+    std::atomic<int> next{0};
+    auto worker = [&]() {
+        for (;;) {
+            const int t = next.fetch_add(1);
+            if (t >= b->n) break;
+            int st;
+            try { st = solve_pair(b, t); } catch (...) { st = QWB_ERR_OOM; }
+            b->status[t] = st;
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int i = 1; i < nt; ++i) pool.emplace_back(worker);
+    worker();
+    for (auto& th : pool) th.join();
+    b->t_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    for (int t = 0; t < b->n; ++t)
+        if (b->status[t]) { b->solved = false; return fail(b->status[t], "exact coarse solve failed"); }
+    // upload the plans (and nnz in the descriptors)
+    QWB_CUDA(cudaMemcpyAsync(b->plan_d, b->plan_h, b->plan_bytes, cudaMemcpyHostToDevice, s));
+    QWB_CUDA(cudaMemcpyAsync(b->pairs_d, b->pairs_h.data(), sizeof(PairDev) * b->n, cudaMemcpyHostToDevice, s));
+    QWB_CUDA(cudaStreamSynchronize(s));
+    b->solved = true;
+    return QWB_OK;
+}
+
+static int batch_results(qwb_batch* b, qwb_result* out, cudaStream_t s) {
+    if (!out) return fail(QWB_ERR_INVALID_ARG, "null results");
+    QWB_CUDA(cudaStreamSynchronize(s));
+    std::vector<PairOut> o(b->n);
+    QWB_CUDA(cudaMemcpy(o.data(), b->outs_d, sizeof(PairOut) * b->n, cudaMemcpyDeviceToHost));
+    float tc = 0.f, tp = 0.f, td = 0.f;
+    if (b->ev_ok) {
+        if (cudaEventElapsedTime(&tc, b->ev[0], b->ev[1]) != cudaSuccess) tc = 0.f;
+        if (cudaEventElapsedTime(&tp, b->ev[2], b->ev[3]) != cudaSuccess) tp = 0.f;
+        if (cudaEventElapsedTime(&td, b->ev[3], b->ev[4]) != cudaSuccess) td = 0.f;
+        cudaGetLastError();
+    }
+    for (int t = 0; t < b->n; ++t) {
+        qwb_result& r = out[t];
+        std::memset(&r, 0, sizeof(r));
+        r.ub_weighted = b->ubw[t];
+        r.ub_weighted_p = b->ubw_p[t];
+        r.ub_primal = o[t].ub_primal;
+        r.lb = o[t].lb;
+        r.lb_p = o[t].lb_p;
+        r.w_hat_p = o[t].w_hat_p;
+        r.delta_mu = o[t].delta_mu;
+        r.delta_nu = o[t].delta_nu;
+        r.ipf_residual = o[t].ipf_residual;
+        r.ipf_sweeps_done = o[t].sweeps_done;
+        if (b->flags & QWB_FLAG_NO_PRIMAL) { r.ub_primal = HUGE_VAL; r.w_hat_p = HUGE_VAL; }
+        if (b->flags & QWB_FLAG_NO_DUAL) { r.lb = 0.0; r.lb_p = -HUGE_VAL; }
+        r.t_coarse_cost_ms = tc; r.t_solve_ms = b->t_solve_ms; r.t_primal_ms = tp; r.t_dual_ms = td;
+        r.status = b->status[t];
+    }
+    return QWB_OK;
+}
+
+// --------------------------------------------------------------------------
+// C ABI
+// --------------------------------------------------------------------------
+extern "C" {
+
+int qwb_ctx_create(qwb_ctx** out, int device) {
+    if (!out) return fail(QWB_ERR_INVALID_ARG, "qwb_ctx_create: null out");
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= n) return fail(QWB_ERR_CUDA, "no such CUDA device");
+    QWB_CUDA(cudaSetDevice(device));
+    qwb_ctx* c = new qwb_ctx();
+    c->device = device;
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    *out = c;
+    return QWB_OK;
+}
+
+void qwb_ctx_destroy(qwb_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto* b : ctx->single_cache) batch_free(b);
+    for (auto& t : ctx->tables) { cudaFree(t.lo); cudaFree(t.hi); }
+    delete ctx;
+}
+
+int qwb_batch_create(qwb_ctx* ctx, int32_t n_pairs, const qwb_problem* probs_h, int32_t ipf_sweeps,
+                     int32_t flags, qwb_prec prec, qwb_batch** out) {
+    if (!ctx || !out) return fail(QWB_ERR_INVALID_ARG, "qwb_batch_create: null argument");
+    if (flags & ~7) return fail(QWB_ERR_INVALID_ARG, "qwb_batch_create: unknown flags");
+    std::lock_guard<std::mutex> lk(ctx->mtx);
+    QWB_CUDA(cudaSetDevice(ctx->device));
+    return batch_build(ctx, n_pairs, probs_h, ipf_sweeps, flags, prec, out);
+}
+
+void qwb_batch_destroy(qwb_batch* batch) {
+    if (!batch) return;
+    cudaSetDevice(batch->ctx->device);
+    cudaDeviceSynchronize();
+    batch_free(batch);
+}
+
+int qwb_batch_coarse(qwb_batch* b, const double* const* mu_d, const double* const* nu_d,
+                     int32_t batched, void* stream) {
+    if (!b) return fail(QWB_ERR_INVALID_ARG, "null batch");
+    QWB_CUDA(cudaSetDevice(b->ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = batch_set_measures(b, mu_d, nu_d);
+    if (st) return st;
+    if (b->ev_ok) QWB_CUDA(cudaEventRecord(b->ev[0], s));
+    st = run_pass(b, 0, batched != 0, s);
+    if (st) return st;
+    if (b->ev_ok) QWB_CUDA(cudaEventRecord(b->ev[1], s));
+    return QWB_OK;
+}
+
+int qwb_batch_solve(qwb_batch* b, int32_t n_threads, void* stream) {
+    if (!b) return fail(QWB_ERR_INVALID_ARG, "null batch");
+    QWB_CUDA(cudaSetDevice(b->ctx->device));
+    return batch_solve(b, n_threads, (cudaStream_t)stream);
+}
+
+int qwb_batch_fine(qwb_batch* b, const double* const* mu_d, const double* const* nu_d,
+                   int32_t batched, void* stream) {
+    if (!b) return fail(QWB_ERR_INVALID_ARG, "null batch");
+    if (!b->solved) return fail(QWB_ERR_INVALID_ARG, "qwb_batch_fine needs a completed qwb_batch_solve");
+    QWB_CUDA(cudaSetDevice(b->ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = batch_set_measures(b, mu_d, nu_d);
+    if (st) return st;
+    if (b->ev_ok) QWB_CUDA(cudaEventRecord(b->ev[2], s));
+    if (batched) {
+        st = run_pass(b, 1, true, s);
+        if (st) return st;
+        if (b->ev_ok) { QWB_CUDA(cudaEventRecord(b->ev[3], s)); QWB_CUDA(cudaEventRecord(b->ev[4], s)); }
+        return QWB_OK;
+    }
+    st = enqueue_fine(b, false, s);
+    if (st) return st;
+    if (b->ev_ok) { QWB_CUDA(cudaEventRecord(b->ev[3], s)); QWB_CUDA(cudaEventRecord(b->ev[4], s)); }
+    return QWB_OK;
+}
+
+int qwb_batch_results(qwb_batch* b, qwb_result* out_h, void* stream) {
+    if (!b) return fail(QWB_ERR_INVALID_ARG, "null batch");
+    QWB_CUDA(cudaSetDevice(b->ctx->device));
+    return batch_results(b, out_h, (cudaStream_t)stream);
+}
+
+int qwb_batch_kernel_times(qwb_batch* b, double* ms_out, int32_t n) {
+    if (!b || !ms_out || n < 0) return fail(QWB_ERR_INVALID_ARG, "qwb_batch_kernel_times: bad argument");
+    if (!b->ev_ok) return fail(QWB_ERR_CUDA, "no timing events");
+    const int pairs[8][2] = {{0, 1}, {1, 2}, {3, 4}, {4, 5}, {5, 6}, {6, 7}, {7, 8}, {8, 9}};
+    for (int i = 0; i < n && i < 8; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, b->kev[pairs[i][0]], b->kev[pairs[i][1]]) != cudaSuccess) {
+            cudaGetLastError();
+            ms = -1.f;
+        }
+        ms_out[i] = ms;
+    }
+    return QWB_OK;
+}
+
+int qwb_batch_potentials(qwb_batch* b, int32_t pair, double* f_d, double* g_d, void* stream) {
+    if (!b || pair < 0 || pair >= b->n) return fail(QWB_ERR_INVALID_ARG, "qwb_batch_potentials: bad pair");
+    if (b->flags & QWB_FLAG_NO_DUAL) return fail(QWB_ERR_INVALID_ARG, "the batch skipped the dual pass");
+    QWB_CUDA(cudaSetDevice(b->ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int m = b->probs[pair].N * b->probs[pair].N;
+    int st;
+    if (f_d && (st = launch_from_work(b->pairs_h[pair].f, f_d, m, b->f64, s))) return st;
+    if (g_d && (st = launch_from_work(b->pairs_h[pair].g, g_d, m, b->f64, s))) return st;
+    return QWB_OK;
+}
+
+int qwb_bounds(qwb_ctx* ctx, int32_t n_pairs, const qwb_problem* probs_h, const double* const* mu_d,
+               const double* const* nu_d, int32_t ipf_sweeps, int32_t flags, qwb_result* out_h,
+               qwb_prec prec, int32_t batched, int32_t n_threads, void* stream) {
+    if (!ctx || !out_h) return fail(QWB_ERR_INVALID_ARG, "qwb_bounds: null argument");
+    qwb_batch* b = nullptr;
+    int st = qwb_batch_create(ctx, n_pairs, probs_h, ipf_sweeps, flags, prec, &b);
+    if (st) return st;
+    st = qwb_batch_coarse(b, mu_d, nu_d, batched, stream);
+    if (!st) st = qwb_batch_solve(b, n_threads, stream);
+    if (!st) st = qwb_batch_fine(b, mu_d, nu_d, batched, stream);
+    if (!st) st = qwb_batch_results(b, out_h, stream);
+    if (st && st != QWB_OK) {
+        for (int t = 0; t < n_pairs; ++t) out_h[t].status = b->status.size() > (size_t)t && b->status[t] ? b->status[t] : st;
+    }
+    qwb_batch_destroy(b);
+    return st;
+}
+
+}  // extern "C"
+
+// ---- standalone pass entry points ----------------------------------------
+static int single_batch(qwb_ctx* ctx, const qwb_problem* prob, int sweeps, qwb_prec prec,
+                        qwb_batch** out) {
+    for (auto* b : ctx->single_cache)
+        if (b->probs[0].N == prob->N && b->probs[0].kappa == prob->kappa && b->probs[0].p == prob->p &&
+            b->f64 == (prec == QWB_PREC_F64)) {
+            b->sweeps = sweeps;
+            b->pairs_h[0].sweeps = sweeps;
+            *out = b;
+            return QWB_OK;
+        }
+    qwb_batch* b = nullptr;
+    int st = batch_build(ctx, 1, prob, sweeps, 0, prec, &b);
+    if (st) return st;
+    if (ctx->single_cache.size() >= 8) { batch_free(ctx->single_cache.front()); ctx->single_cache.erase(ctx->single_cache.begin()); }
+    ctx->single_cache.push_back(b);
+    *out = b;
+    return QWB_OK;
+}
+
+// Upload the descriptor of a single-pair batch with the given pointers.
+static int single_upload(qwb_batch* b, cudaStream_t s) {
+    b->cur_mu.clear(); b->cur_nu.clear();
+    QWB_CUDA(cudaMemcpyAsync(b->pairs_d, b->pairs_h.data(), sizeof(PairDev), cudaMemcpyHostToDevice, s));
+    return QWB_OK;
+}
+
+static int single_validate(qwb_batch* b, cudaStream_t s) {
+    int st = launch_prepare(b->pairs_d, b->outs_d, b->prep_items_d, b->n_prep, b->f64, s);
+    if (st) return st;
+    PairOut o;
+    QWB_CUDA(cudaMemcpyAsync(&o, b->outs_d, sizeof(PairOut), cudaMemcpyDeviceToHost, s));
+    QWB_CUDA(cudaStreamSynchronize(s));
+    if (o.bad_mu || o.bad_nu || !(std::fabs(o.mass_mu - 1.0) <= 1e-12) || !(std::fabs(o.mass_nu - 1.0) <= 1e-12))
+        return fail(QWB_ERR_MASS, "measures must be finite, non-negative and of mass 1 (1e-12)");
+    return QWB_OK;
+}
+
+extern "C" {
+
+int qwb_coarse_cost(qwb_ctx* ctx, const qwb_problem* prob, const double* mu_d, const double* nu_d,
+                    double* cbar_d, double* mu_coarse_d, double* nu_coarse_d, qwb_prec prec,
+                    void* stream) {
+    if (!ctx || !mu_d || !nu_d || !cbar_d) return fail(QWB_ERR_INVALID_ARG, "qwb_coarse_cost: null argument");
+    int st = check_problem(prob);
+    if (st) return st;
+    std::lock_guard<std::mutex> lk(ctx->mtx);
+    QWB_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    qwb_batch* b;
+    if ((st = single_batch(ctx, prob, 1, prec, &b))) return st;
+    PairDev& P = b->pairs_h[0];
+    double* own_cbar = P.cbar;
+    P.mu = mu_d; P.nu = nu_d; P.cbar = cbar_d;
+    if ((st = single_upload(b, s))) { P.cbar = own_cbar; return st; }
+    P.cbar = own_cbar;
+    QWB_CUDA(cudaMemsetAsync(b->outs_d, 0, sizeof(PairOut), s));
+    if ((st = single_validate(b, s))) return st;
+    const int kc = (prob->kappa == 1 || prob->kappa == 2 || prob->kappa == 4) ? prob->kappa : -prob->kappa;
+    if ((st = launch_cbar(b->pairs_d, b->cbar_items_d, b->n_cbar, kc, prob->N / prob->kappa, prob->N,
+                          b->f64, s))) return st;
+    const size_t M = b->Ms[0];
+    if (mu_coarse_d) QWB_CUDA(cudaMemcpyAsync(mu_coarse_d, P.mu_c, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
+    if (nu_coarse_d) QWB_CUDA(cudaMemcpyAsync(nu_coarse_d, P.nu_c, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
+    QWB_CUDA(cudaStreamSynchronize(s));   // the cached descriptor is reused by the next call
+    return QWB_OK;
+}
+
+int qwb_primal_upscale_ipf(qwb_ctx* ctx, const qwb_problem* prob, const double* mu_d,
+                           const double* nu_d, const int32_t* pi_rowptr_d, const int32_t* pi_col_d,
+                           const double* pi_val_d, int32_t pi_nnz, int32_t sweeps, double* a_d,
+                           double* b_d, qwb_result* out_h, qwb_prec prec, void* stream) {
+    if (!ctx || !mu_d || !nu_d || !pi_rowptr_d || !pi_col_d || !pi_val_d || !out_h)
+        return fail(QWB_ERR_INVALID_ARG, "qwb_primal_upscale_ipf: null argument");
+    int st = check_problem(prob);
+    if (st) return st;
+    if (sweeps < 1) return fail(QWB_ERR_INVALID_ARG, "sweeps must be >= 1");
+    std::lock_guard<std::mutex> lk(ctx->mtx);
+    QWB_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    qwb_batch* b;
+    if ((st = single_batch(ctx, prob, sweeps, prec, &b))) return st;
+    const int M = b->Ms[0];
+    if (pi_nnz < 0 || (int64_t)pi_nnz > (int64_t)M * M) return fail(QWB_ERR_INVALID_ARG, "plan has more than M^2 entries");
+    // the plan: read the CSR, transpose it on the host, stage both forms
+    std::vector<int> rowptr(M + 1), col(pi_nnz);
+    std::vector<double> val(pi_nnz);
+    QWB_CUDA(cudaMemcpy(rowptr.data(), pi_rowptr_d, sizeof(int) * (M + 1), cudaMemcpyDeviceToHost));
+    if (rowptr[0] != 0 || rowptr[M] != pi_nnz) return fail(QWB_ERR_INVALID_ARG, "plan rowptr inconsistent with nnz");
+    if (pi_nnz) {
+        QWB_CUDA(cudaMemcpy(col.data(), pi_col_d, sizeof(int) * pi_nnz, cudaMemcpyDeviceToHost));
+        QWB_CUDA(cudaMemcpy(val.data(), pi_val_d, sizeof(double) * pi_nnz, cudaMemcpyDeviceToHost));
+    }
+    for (int k = 0; k < M; ++k) if (rowptr[k + 1] < rowptr[k]) return fail(QWB_ERR_INVALID_ARG, "plan rowptr not monotone");
+    for (int e = 0; e < pi_nnz; ++e)
+        if (col[e] < 0 || col[e] >= M || !(val[e] >= 0.0) || !std::isfinite(val[e]))
+            return fail(QWB_ERR_INVALID_ARG, "plan entry out of range");
+    // the batch's staging holds 2M entries (a basic plan); larger plans (any
+    // optimal coupling may be passed) get a temporary staging area
+    const PlanLayout L = plan_layout(M, pi_nnz);
+    char* ph = b->plan_h;
+    char* pd = b->plan_d;
+    char* tmp_h = nullptr;
+    char* tmp_d = nullptr;
+    if (L.total > b->plan_bytes) {
+        if (cudaMallocHost(&tmp_h, L.total) != cudaSuccess) return fail(QWB_ERR_OOM, "plan staging");
+        if (cudaMalloc(&tmp_d, L.total) != cudaSuccess) { cudaFreeHost(tmp_h); return fail(QWB_ERR_OOM, "plan staging"); }
+        ph = tmp_h; pd = tmp_d;
+    }
+    struct Release {
+        char *h, *d;
+        ~Release() { if (h) cudaFreeHost(h); if (d) cudaFree(d); }
+    } release{tmp_h, tmp_d};
+    std::memcpy(ph + L.rowptr, rowptr.data(), sizeof(int) * (M + 1));
+    std::memcpy(ph + L.col, col.data(), sizeof(int) * pi_nnz);
+    std::memcpy(ph + L.val, val.data(), sizeof(double) * pi_nnz);
+    std::vector<int> cnt(M + 1, 0);
+    for (int e = 0; e < pi_nnz; ++e) cnt[col[e] + 1]++;
+    for (int l = 0; l < M; ++l) cnt[l + 1] += cnt[l];
+    std::memcpy(ph + L.colptr, cnt.data(), sizeof(int) * (M + 1));
+    std::vector<int> cur(cnt.begin(), cnt.end() - 1);
+    for (int k = 0; k < M; ++k)
+        for (int e = rowptr[k]; e < rowptr[k + 1]; ++e) {
+            const int pos = cur[col[e]]++;
+            ((int*)(ph + L.rowidx))[pos] = k;
+            ((double*)(ph + L.valc))[pos] = val[e];
+        }
+    QWB_CUDA(cudaMemcpyAsync(pd, ph, L.total, cudaMemcpyHostToDevice, s));
+    PairDev& P = b->pairs_h[0];
+    const PairDev saved = P;
+    P.mu = mu_d; P.nu = nu_d; P.nnz = pi_nnz; P.sweeps = sweeps; P.a_out = a_d; P.b_out = b_d;
+    P.rowptr = (int*)(pd + L.rowptr); P.colidx = (int*)(pd + L.col); P.val = (double*)(pd + L.val);
+    P.colptr = (int*)(pd + L.colptr); P.rowidx = (int*)(pd + L.rowidx); P.valc = (double*)(pd + L.valc);
+    st = single_upload(b, s);
+    {   // the cached descriptor keeps the batch's own buffers
+        const PairDev cur = P;
+        P = saved;
+        P.mu = cur.mu; P.nu = cur.nu; P.sweeps = cur.sweeps;
+    }
+    if (st) return st;
+    QWB_CUDA(cudaMemsetAsync(b->outs_d, 0, sizeof(PairOut), s));
+    if ((st = single_validate(b, s))) return st;
+    if ((st = launch_primal(b->pairs_d, b->outs_d, b->pair_ids_d, 1, M, pi_nnz, b->f64, s))) return st;
+    PairOut o;
+    QWB_CUDA(cudaMemcpyAsync(&o, b->outs_d, sizeof(PairOut), cudaMemcpyDeviceToHost, s));
+    QWB_CUDA(cudaStreamSynchronize(s));
+    std::memset(out_h, 0, sizeof(*out_h));
+    out_h->ub_primal = o.ub_primal; out_h->w_hat_p = o.w_hat_p; out_h->delta_mu = o.delta_mu;
+    out_h->delta_nu = o.delta_nu; out_h->ipf_residual = o.ipf_residual; out_h->ipf_sweeps_done = o.sweeps_done;
+    return QWB_OK;
+}
+
+int qwb_dual_upscale_ctransform(qwb_ctx* ctx, const qwb_problem* prob, const double* mu_d,
+                                const double* nu_d, const double* f_coarse_d, double* f_d,
+                                double* g_d, qwb_result* out_h, qwb_prec prec, void* stream) {
+    if (!ctx || !mu_d || !nu_d || !f_coarse_d || !out_h)
+        return fail(QWB_ERR_INVALID_ARG, "qwb_dual_upscale_ctransform: null argument");
+    int st = check_problem(prob);
+    if (st) return st;
+    std::lock_guard<std::mutex> lk(ctx->mtx);
+    QWB_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    qwb_batch* b;
+    if ((st = single_batch(ctx, prob, 1, prec, &b))) return st;
+    PairDev& P = b->pairs_h[0];
+    const int M = b->Ms[0];
+    QWB_CUDA(cudaMemcpyAsync((void*)P.f_coarse, f_coarse_d, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
+    P.mu = mu_d; P.nu = nu_d; P.f_out = f_d; P.g_out = g_d;
+    st = single_upload(b, s);
+    P.f_out = nullptr; P.g_out = nullptr;
+    if (st) return st;
+    QWB_CUDA(cudaMemsetAsync(b->outs_d, 0, sizeof(PairOut), s));
+    if ((st = single_validate(b, s))) return st;
+    if ((st = launch_centre(b->pairs_d, b->outs_d, b->pair_ids_d, 1, s))) return st;
+    if ((st = launch_upsample(b->pairs_d, b->outs_d, b->pix_items_d, b->n_pix, b->f64, s))) return st;
+    CtConfig c = b->ct_cfg_p;
+    c.p2 = (prob->p == 2.0);
+    if ((st = launch_ctransform(b->pairs_d, b->ct_p_items_d, b->ct_cnt[0], 0, c, prob->N, b->f64, 0, s))) return st;
+    if ((st = launch_ctransform(b->pairs_d, b->ct_p_items_d, b->ct_cnt[0], 1, c, prob->N, b->f64, 0, s))) return st;
+    if ((st = launch_lbsum(b->pairs_d, b->outs_d, b->pair_ids_d, 1, b->f64, s))) return st;
+    PairOut o;
+    QWB_CUDA(cudaMemcpyAsync(&o, b->outs_d, sizeof(PairOut), cudaMemcpyDeviceToHost, s));
+    QWB_CUDA(cudaStreamSynchronize(s));
+    std::memset(out_h, 0, sizeof(*out_h));
+    out_h->lb = o.lb; out_h->lb_p = o.lb_p;
+    return QWB_OK;
+}
+
+int qwb_ctransform(qwb_ctx* ctx, int32_t N, double p, const double* h_d, double* out_d, qwb_prec prec,
+                   void* stream) {
+    if (!ctx || !h_d || !out_d) return fail(QWB_ERR_INVALID_ARG, "qwb_ctransform: null argument");
+    qwb_problem prob{N, N, p};
+    int st = check_problem(&prob);
+    if (st) return st;
+    std::lock_guard<std::mutex> lk(ctx->mtx);
+    QWB_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    qwb_batch* b;
+    if ((st = single_batch(ctx, &prob, 1, prec, &b))) return st;
+    PairDev& P = b->pairs_h[0];
+    P.f_out = nullptr; P.g_out = nullptr;
+    if ((st = single_upload(b, s))) return st;
+    if ((st = launch_to_work(h_d, P.fhat, P.g, N * N, b->f64, s))) return st;
+    CtConfig c = b->ct_cfg_p;
+    c.p2 = (p == 2.0);
+    if ((st = launch_ctransform(b->pairs_d, b->ct_p_items_d, b->ct_cnt[0], 0, c, N, b->f64, 0, s))) return st;
+    if ((st = launch_from_work(P.g, out_d, N * N, b->f64, s))) return st;
+    QWB_CUDA(cudaStreamSynchronize(s));
+    return QWB_OK;
+}
+
+int qwb_lb_adjoint(qwb_ctx* ctx, int32_t N, double p, const double* f_d, const double* mu_d,
+                   double lb_p, double* grad_d, void* stream) {
+    if (!ctx || !f_d || !mu_d || !grad_d) return fail(QWB_ERR_INVALID_ARG, "qwb_lb_adjoint: null argument");
+    if (N < 1 || N > 1024 || !(p >= 1.0)) return fail(QWB_ERR_INVALID_ARG, "qwb_lb_adjoint: bad N or p");
+    std::lock_guard<std::mutex> lk(ctx->mtx);
+    QWB_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    qwb_problem prob{N, N, p};
+    qwb_batch* b;
+    int st = single_batch(ctx, &prob, 1, QWB_PREC_F64, &b);
+    if (st) return st;
+    return launch_adjoint(N, p, f_d, mu_d, lb_p, grad_d, b->pairs_h[0].mu_c, s);
+}
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+// common.cuh -- shared device helpers for the qwb kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/qwb.h"
+
+namespace qwb {
+
+// ---- error plumbing (host) ------------------------------------------------
+void set_last_error(const std::string& msg);
+void count_launch(int64_t k = 1);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define QWB_CUDA(call)                                         \
+    do {                                                       \
+        cudaError_t qwb_e_ = (call);                           \
+        if (qwb_e_ != cudaSuccess) return cuda_fail(qwb_e_, #call); \
+    } while (0)
+
+// Check a kernel launch and count it.
+#define QWB_LAUNCHED()                                         \
+    do {                                                       \
+        count_launch();                                        \
+        cudaError_t qwb_e_ = cudaGetLastError();               \
+        if (qwb_e_ != cudaSuccess) return cuda_fail(qwb_e_, "kernel launch"); \
+    } while (0)
+
+// ---- directed rounding, overloaded on the scalar type ----------------------
+// rd = toward -infinity, ru = toward +infinity (IEEE-correct intrinsics).
+__device__ __forceinline__ float sub_rd(float a, float b) { return __fsub_rd(a, b); }
+__device__ __forceinline__ double sub_rd(double a, double b) { return __dsub_rd(a, b); }
+__device__ __forceinline__ float add_ru(float a, float b) { return __fadd_ru(a, b); }
+__device__ __forceinline__ double add_ru(double a, double b) { return __dadd_ru(a, b); }
+__device__ __forceinline__ float fma_ru(float a, float b, float c) { return __fmaf_ru(a, b, c); }
+__device__ __forceinline__ double fma_ru(double a, double b, double c) { return __fma_ru(a, b, c); }
+__device__ __forceinline__ float mul_ru(float a, float b) { return __fmul_ru(a, b); }
+__device__ __forceinline__ double mul_ru(double a, double b) { return __dmul_ru(a, b); }
+
+template <typename T> __device__ __forceinline__ T from_double_ru(double x);
+template <> __device__ __forceinline__ float from_double_ru<float>(double x) { return __double2float_ru(x); }
+template <> __device__ __forceinline__ double from_double_ru<double>(double x) { return x; }
+template <typename T> __device__ __forceinline__ T from_double_rn(double x);
+template <> __device__ __forceinline__ float from_double_rn<float>(double x) { return __double2float_rn(x); }
+template <> __device__ __forceinline__ double from_double_rn<double>(double x) { return x; }
+
+template <typename T> __device__ __forceinline__ T pos_inf();
+template <> __device__ __forceinline__ float pos_inf<float>() { return __int_as_float(0x7f800000); }
+template <> __device__ __forceinline__ double pos_inf<double>() { return __longlong_as_double(0x7ff0000000000000LL); }
+
+// Atomic minimum on a float/double stored as such.  Non-negative values
+// order like signed integers, negative values order in reverse as unsigned
+// integers; the two branches together give an exact floating-point min.
+__device__ __forceinline__ void atomic_min_fp(float* addr, float v) {
+    if (v >= 0.0f) atomicMin(reinterpret_cast<int*>(addr), __float_as_int(v));
+    else atomicMax(reinterpret_cast<unsigned int*>(addr), __float_as_uint(v));
+}
+__device__ __forceinline__ void atomic_min_fp(double* addr, double v) {
+    if (v >= 0.0)
+        atomicMin(reinterpret_cast<long long*>(addr), __double_as_longlong(v));
+    else
+        atomicMax(reinterpret_cast<unsigned long long*>(addr),
+                  static_cast<unsigned long long>(__double_as_longlong(v)));
+}
+
+// Ground cost rho(x,y)^p of an integer offset (dr, dc) >= 0, bracketed:
+// lo <= true value <= hi.  p = 1 and p = 2 use correctly rounded operations;
+// other p use the FP64 pow (error at most 2 ulp) widened by 2^-49 relative.
+template <typename T> struct CostPair { T lo, hi; };
+
+__device__ __forceinline__ CostPair<double> ground_cost_f64(int dr, int dc, double p) {
+    const double d2 = (double)dr * dr + (double)dc * dc;   // exact integer
+    if (p == 2.0) return {d2, d2};
+    if (p == 1.0) return {__dsqrt_rd(d2), __dsqrt_ru(d2)};
+    if (d2 == 0.0) return {0.0, 0.0};
+    const double c = pow(d2, 0.5 * p);
+    return {__dmul_rd(c, 1.0 - 0x1p-49), __dmul_ru(c, 1.0 + 0x1p-49)};
+}
+__device__ __forceinline__ CostPair<float> ground_cost_f32(int dr, int dc, double p) {
+    const double d2 = (double)dr * dr + (double)dc * dc;
+    if (p == 2.0) return {(float)d2, (float)d2};            // exact below 2^24
+    if (p == 1.0) return {__fsqrt_rd((float)d2), __fsqrt_ru((float)d2)};
+    const CostPair<double> c = ground_cost_f64(dr, dc, p);
+    return {__double2float_rd(c.lo), __double2float_ru(c.hi)};
+}
+
+}  // namespace qwb

@@ -1,0 +1,922 @@
+// kernels.cu -- device passes of the quantization-based W_p bounds.
+//
+//   prepare     SumPool of mu and nu (Sec. 2.2) with validation sums
+//   cbar        marginally weighted coarse cost C-bar (Sec. 3.2, Alg. 3),
+//               reduced over every fine pixel pair of every block pair
+//   primal      IPF sweeps of the upscaled plan and its certified cost and
+//               TV corrections (Sec. 3.4, Sec. 4, Alg. 4)
+//   centre/upsample  bilinear dual upscaling (Sec. 3.5, Alg. 5)
+//   ctransform  lazy min-plus c-transform (Sec. 4, eq. lazy c-transform)
+//   lbsum       certified dual lower bound (Sec. 3.5, eq. upscaling LB)
+//   adjoint     gradient of the lower bound along the simplex
+//
+// Every kernel takes a list of work items over a table of per-pair
+// descriptors, so one launch serves one pair (plain form) or a whole batch of
+// pairs with uneven grid sizes (batched form).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace qwb {
+
+// --------------------------------------------------------------------------
+// Cost tables: tab[dr * N + dc] brackets rho((dr, dc))^p for 0 <= dr, dc < N.
+// --------------------------------------------------------------------------
+template <typename T>
+__global__ void cost_table_kernel(int N, double p, T* lo, T* hi) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * N) return;
+    const int dr = idx / N, dc = idx % N;
+    if constexpr (sizeof(T) == 4) {
+        CostPair<float> c = ground_cost_f32(dr, dc, p);
+        lo[idx] = c.lo; hi[idx] = c.hi;
+    } else {
+        CostPair<double> c = ground_cost_f64(dr, dc, p);
+        lo[idx] = c.lo; hi[idx] = c.hi;
+    }
+}
+
+int launch_cost_tables(int N, double p, bool f64, void* lo, void* hi, cudaStream_t stream) {
+    const int n = N * N, th = 256, bl = (n + th - 1) / th;
+    if (f64) cost_table_kernel<double><<<bl, th, 0, stream>>>(N, p, (double*)lo, (double*)hi);
+    else cost_table_kernel<float><<<bl, th, 0, stream>>>(N, p, (float*)lo, (float*)hi);
+    QWB_LAUNCHED();
+    return QWB_OK;
+}
+
+// --------------------------------------------------------------------------
+// prepare: SumPool (Sec. 2.2) -- mu~_k = mu(X_k) in FP64, nearest and
+// round-down sums, plus validation (finite, non-negative, mass).
+// One thread per coarse block; items cover 256 blocks each.
+// --------------------------------------------------------------------------
+__global__ void prepare_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
+                               const PixItem* __restrict__ items, int n_items) {
+    const PixItem I = items[blockIdx.x];
+    const PairDev& P = pairs[I.pair];
+    const int k = I.start + threadIdx.x;
+    double smu = 0.0, snu = 0.0;
+    int bad_mu = 0, bad_nu = 0;
+    if (k < P.M) {
+        const int N = P.N, kap = P.kappa, n = P.n;
+        const int k1 = k / n, k2 = k % n;
+        double mu_rn = 0.0, mu_rd = 0.0, nu_rn = 0.0, nu_rd = 0.0;
+        for (int t1 = 0; t1 < kap; ++t1) {
+            const int row = (k1 * kap + t1) * N + k2 * kap;
+            for (int t2 = 0; t2 < kap; ++t2) {
+                const double x = P.mu[row + t2], y = P.nu[row + t2];
+                bad_mu |= !(x >= 0.0) || !isfinite(x);
+                bad_nu |= !(y >= 0.0) || !isfinite(y);
+                mu_rn += x; mu_rd = __dadd_rd(mu_rd, x);
+                nu_rn += y; nu_rd = __dadd_rd(nu_rd, y);
+            }
+        }
+        P.mu_c[k] = mu_rn; P.mu_c_lo[k] = mu_rd;
+        P.nu_c[k] = nu_rn; P.nu_c_lo[k] = nu_rd;
+        smu = mu_rn; snu = nu_rn;
+    }
+    // block reduction of the masses, one atomic per block
+    __shared__ double red[2][32];
+    __shared__ int redb[2];
+    if (threadIdx.x == 0) { redb[0] = 0; redb[1] = 0; }
+    for (int o = 16; o > 0; o >>= 1) {
+        smu += __shfl_down_sync(0xffffffffu, smu, o);
+        snu += __shfl_down_sync(0xffffffffu, snu, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { red[0][warp] = smu; red[1][warp] = snu; }
+    __syncthreads();
+    if (bad_mu) atomicOr(&redb[0], 1);
+    if (bad_nu) atomicOr(&redb[1], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += red[0][w]; b += red[1][w]; }
+        PairOut& O = outs[P.out_index];
+        atomicAdd(&O.mass_mu, a);
+        atomicAdd(&O.mass_nu, b);
+        if (redb[0]) atomicOr(&O.bad_mu, 1);
+        if (redb[1]) atomicOr(&O.bad_nu, 1);
+    }
+}
+
+int launch_prepare(const PairDev* pairs_d, PairOut* outs_d, const PixItem* items, int n_items,
+                   bool, cudaStream_t stream) {
+    if (n_items <= 0) return QWB_OK;
+    prepare_kernel<<<n_items, 256, 0, stream>>>(pairs_d, outs_d, items, n_items);
+    QWB_LAUNCHED();
+    return QWB_OK;
+}
+
+// --------------------------------------------------------------------------
+// cbar: C-bar_kl = [sum_{x in X_k} mu(x) sum_{y in Y_l} nu(y) rho(x,y)^p] /
+//                  (mu~_k nu~_l)                       (Sec. 3.2; Alg. 3)
+// One CTA per (pair, source block row k1, target block row l1).  The CTA
+// stages the kappa fine rows of mu and nu and the 2*kappa-1 cost-table rows
+// it needs in shared memory.  A thread takes up to TSEG block pairs on one
+// diagonal (same block offset, hence the same (2kappa-1)^2 cost window, held
+// in registers).  All products and sums are rounded upward, so the result
+// bounds the real C-bar from above.
+// --------------------------------------------------------------------------
+constexpr int CBAR_TSEG = 4;
+constexpr int CBAR_THREADS = 256;
+
+template <typename T, int KAP>
+__global__ void __launch_bounds__(CBAR_THREADS)
+cbar_kernel(const PairDev* __restrict__ pairs, const CbarItem* __restrict__ items, int n_items,
+            int stage_n) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const CbarItem I = items[it];
+        const PairDev& P = pairs[I.pair];
+        const int N = P.N, n = P.n, M = P.M;
+        const int kap = KAP > 0 ? KAP : P.kappa;
+        T* mu_s = reinterpret_cast<T*>(smem_raw);
+        T* nu_s = mu_s + kap * N;
+        T* c_s = nu_s + kap * N;
+        double* out_s = reinterpret_cast<double*>(
+            smem_raw + ((sizeof(T) * (size_t)(4 * kap - 1) * N + 15) / 16) * 16);
+        const bool stage = (n <= stage_n);
+        const T* tab = reinterpret_cast<const T*>(P.ctab_hi);
+        const int D1 = kap * (I.k1 - I.l1);
+        for (int idx = threadIdx.x; idx < kap * N; idx += blockDim.x) {
+            const int r = idx / N, c = idx % N;
+            mu_s[idx] = from_double_ru<T>(P.mu[(I.k1 * kap + r) * N + c]);
+            nu_s[idx] = from_double_ru<T>(P.nu[(I.l1 * kap + r) * N + c]);
+        }
+        for (int idx = threadIdx.x; idx < (2 * kap - 1) * N; idx += blockDim.x) {
+            const int d = idx / N, c = idx % N;
+            c_s[idx] = tab[abs(D1 + d - (kap - 1)) * N + c];
+        }
+        __syncthreads();
+
+        const int nseg = (n + CBAR_TSEG - 1) / CBAR_TSEG;
+        const int n_work = (2 * n - 1) * nseg;
+        for (int w = threadIdx.x; w < n_work; w += blockDim.x) {
+            const int d = w / nseg, s = w % nseg;
+            const int D2 = d - (n - 1);            // k2 - l2
+            const int k2_0 = max(0, D2) + s * CBAR_TSEG;
+            const int k2_end = min(n, n + D2);
+            if (k2_0 >= k2_end) continue;
+            const int cnt = min(CBAR_TSEG, k2_end - k2_0);
+            if constexpr (KAP > 0) {
+                constexpr int W = 2 * KAP - 1;
+                T cw[W][W];
+#pragma unroll
+                for (int d1 = 0; d1 < W; ++d1)
+#pragma unroll
+                    for (int d2 = 0; d2 < W; ++d2)
+                        cw[d1][d2] = c_s[d1 * N + abs(KAP * D2 + d2 - (KAP - 1))];
+                for (int t = 0; t < cnt; ++t) {
+                    const int k2 = k2_0 + t, l2 = k2 - D2;
+                    T nb[KAP][KAP];
+#pragma unroll
+                    for (int b1 = 0; b1 < KAP; ++b1)
+#pragma unroll
+                        for (int b2 = 0; b2 < KAP; ++b2) nb[b1][b2] = nu_s[b1 * N + l2 * KAP + b2];
+                    T acc = T(0);
+#pragma unroll
+                    for (int a1 = 0; a1 < KAP; ++a1)
+#pragma unroll
+                        for (int a2 = 0; a2 < KAP; ++a2) {
+                            const T mv = mu_s[a1 * N + k2 * KAP + a2];
+                            T inner = T(0);
+#pragma unroll
+                            for (int b1 = 0; b1 < KAP; ++b1)
+#pragma unroll
+                                for (int b2 = 0; b2 < KAP; ++b2)
+                                    inner = fma_ru(nb[b1][b2], cw[a1 - b1 + KAP - 1][a2 - b2 + KAP - 1], inner);
+                            acc = fma_ru(mv, inner, acc);
+                        }
+                    const double num = (double)acc;
+                    if (stage) out_s[k2 * n + l2] = num;
+                    else {
+                        const int k = I.k1 * n + k2, l = I.l1 * n + l2;
+                        const double den = __dmul_rd(P.mu_c_lo[k], P.nu_c_lo[l]);
+                        P.cbar[(size_t)k * M + l] = den > 0.0 ? __ddiv_ru(num, den) : -1.0;
+                    }
+                }
+            } else {
+                for (int t = 0; t < cnt; ++t) {
+                    const int k2 = k2_0 + t, l2 = k2 - D2;
+                    T acc = T(0);
+                    for (int a1 = 0; a1 < kap; ++a1)
+                        for (int a2 = 0; a2 < kap; ++a2) {
+                            const T mv = mu_s[a1 * N + k2 * kap + a2];
+                            T inner = T(0);
+                            for (int b1 = 0; b1 < kap; ++b1) {
+                                const T* crow = c_s + (a1 - b1 + kap - 1) * N;
+                                for (int b2 = 0; b2 < kap; ++b2)
+                                    inner = fma_ru(nu_s[b1 * N + l2 * kap + b2],
+                                                   crow[abs(kap * D2 + a2 - b2)], inner);
+                            }
+                            acc = fma_ru(mv, inner, acc);
+                        }
+                    const double num = (double)acc;
+                    if (stage) out_s[k2 * n + l2] = num;
+                    else {
+                        const int k = I.k1 * n + k2, l = I.l1 * n + l2;
+                        const double den = __dmul_rd(P.mu_c_lo[k], P.nu_c_lo[l]);
+                        P.cbar[(size_t)k * M + l] = den > 0.0 ? __ddiv_ru(num, den) : -1.0;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // epilogue: divide by the coarse masses; zero-mass entries get the
+        // unweighted mean of the cost over the block pair
+        const double k4 = (double)kap * kap * kap * kap;
+        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+            const int k2 = idx / n, l2 = idx % n;
+            const int k = I.k1 * n + k2, l = I.l1 * n + l2;
+            const double den = __dmul_rd(P.mu_c_lo[k], P.nu_c_lo[l]);
+            double val;
+            if (den > 0.0) {
+                if (!stage) continue;
+                val = __ddiv_ru(out_s[idx], den);
+            } else {
+                const int D2 = k2 - l2;
+                double s = 0.0;
+                for (int a1 = 0; a1 < kap; ++a1)
+                    for (int b1 = 0; b1 < kap; ++b1)
+                        for (int a2 = 0; a2 < kap; ++a2)
+                            for (int b2 = 0; b2 < kap; ++b2)
+                                s = __dadd_ru(s, (double)c_s[(a1 - b1 + kap - 1) * N +
+                                                           abs(kap * D2 + a2 - b2)]);
+                val = __ddiv_ru(s, k4);
+            }
+            P.cbar[(size_t)k * M + l] = val;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+static int cbar_dispatch(const PairDev* pairs_d, const CbarItem* items, int n_items, int kappa_max,
+                         int n_max, int N_max, cudaStream_t stream) {
+    const int stage_n = 64;
+    size_t smem = ((sizeof(T) * (size_t)(4 * kappa_max - 1) * N_max + 15) / 16) * 16;
+    if (n_max <= stage_n) smem += sizeof(double) * (size_t)n_max * n_max;
+    if (smem > 227 * 1024) return QWB_ERR_UNSUPPORTED;
+    auto run = [&](auto kern) -> int {
+        QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<n_items, CBAR_THREADS, smem, stream>>>(pairs_d, items, n_items, stage_n);
+        QWB_LAUNCHED();
+        return QWB_OK;
+    };
+    switch (kappa_max) {   // kappa_max is the common kappa when all pairs share it
+        case 1: return run(cbar_kernel<T, 1>);
+        case 2: return run(cbar_kernel<T, 2>);
+        case 4: return run(cbar_kernel<T, 4>);
+        default: return run(cbar_kernel<T, 0>);
+    }
+}
+
+int launch_cbar(const PairDev* pairs_d, const CbarItem* items, int n_items, int kappa_code,
+                int n_max, int N_max, bool f64, cudaStream_t stream) {
+    if (n_items <= 0) return QWB_OK;
+    // kappa_code: the common kappa (1, 2, 4 use unrolled kernels) or -K for a
+    // mixed batch whose largest kappa is K (runtime-kappa kernel)
+    const int kmax = kappa_code > 0 ? kappa_code : -kappa_code;
+    const int kc = kappa_code > 0 ? kappa_code : 0;
+    (void)kmax;
+    if (f64) return cbar_dispatch<double>(pairs_d, items, n_items, kc == 0 ? kmax : kc, n_max, N_max, stream) ;
+    return cbar_dispatch<float>(pairs_d, items, n_items, kc == 0 ? kmax : kc, n_max, N_max, stream);
+}
+
+// --------------------------------------------------------------------------
+// primal: IPF of pi-hat = pi~ (x) kappa^-4 to (mu, nu) and the certified upper
+// bound (Sec. 3.4 IPF paragraph and Theorem; Sec. 4 cost over the support;
+// Alg. 4).  One CTA per pair; one thread per coarse block at a time.
+//   fine sweeps (type T):  a_i = mu_i / r_k(i),  r = kappa^-4 pi~ B,
+//                          b_j = nu_j / s_l(j),  s = kappa^-4 pi~^T A,
+//   with A, B the block sums of a, b (b = 1 initially).
+//   final FP64 sweep: the same sweep on block scalars (a_i = alpha_k mu_i,
+//   b_j = beta_l nu_j, exact for the uniform kernel) defines the certified
+//   plan; its marginals, cost and TV corrections are bounded with interval
+//   (directed) arithmetic.
+// --------------------------------------------------------------------------
+constexpr int PRIMAL_THREADS = 512;
+
+__device__ __forceinline__ double block_reduce_ru(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v = __dadd_ru(v, __shfl_down_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = __dadd_ru(s, red[w]);
+        red[32] = s;
+    }
+    __syncthreads();
+    return red[32];
+}
+__device__ __forceinline__ double block_reduce_rn(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        red[32] = s;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+// rho(x-bar, x)^p bracket for the TV weights, x-bar = ((N-1)/2, (N-1)/2).
+__device__ __forceinline__ double tv_weight_hi(int r, int c, int N, double p) {
+    const double dr = r - 0.5 * (N - 1), dc = c - 0.5 * (N - 1);
+    const double d2 = dr * dr + dc * dc;                  // exact (quarter integers)
+    if (p == 2.0) return d2;
+    if (p == 1.0) return __dsqrt_ru(d2);
+    if (d2 == 0.0) return 0.0;
+    return __dmul_ru(pow(d2, 0.5 * p), 1.0 + 0x1p-49);
+}
+
+// x^(1/p) rounded upward (x >= 0)
+__device__ __forceinline__ double root_p_ru(double x, double p) {
+    if (x <= 0.0) return 0.0;
+    if (p == 1.0) return x;
+    if (p == 2.0) return __dsqrt_ru(x);
+    return __dmul_ru(pow(x, 1.0 / p), 1.0 + 0x1p-49);
+}
+__device__ __forceinline__ double root_p_rd(double x, double p) {
+    if (x <= 0.0) return 0.0;
+    if (p == 1.0) return x;
+    if (p == 2.0) return __dsqrt_rd(x);
+    return __dmul_rd(pow(x, 1.0 / p), 1.0 - 0x1p-49);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PRIMAL_THREADS, 1)
+primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
+              const int* __restrict__ pair_ids) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[33];
+    const PairDev& P = pairs[pair_ids[blockIdx.x]];
+    const int N = P.N, kap = P.kappa, n = P.n, M = P.M;
+    double* Bd = reinterpret_cast<double*>(smem_raw);    // FP64 phase: block sums of b
+    double* Ad = Bd + M;                                  //             block sums of a
+    double* alpha = Ad + M;                               //             a_i = alpha_k mu_i
+    double* beta = alpha + M;                             //             b_j = beta_l nu_j
+    T* Bt = reinterpret_cast<T*>(beta + M);               // fine phase block sums
+    T* At = Bt + M;
+    T* a = reinterpret_cast<T*>(P.a);
+    T* b = reinterpret_cast<T*>(P.b);
+    const T kinv4 = T(1) / (T)((double)kap * kap * kap * kap);
+    const T kk = (T)(kap * kap);
+
+    // ---- fine sweeps ------------------------------------------------------
+    for (int l = threadIdx.x; l < M; l += blockDim.x) Bt[l] = kk;    // b = 1
+    __syncthreads();
+    for (int sweep = 0; sweep < P.sweeps; ++sweep) {
+        for (int k = threadIdx.x; k < M; k += blockDim.x) {
+            T r = T(0);
+            for (int e = P.rowptr[k]; e < P.rowptr[k + 1]; ++e) r += (T)P.val[e] * Bt[P.colidx[e]];
+            r *= kinv4;
+            const T inv = r > T(0) ? T(1) / r : T(0);
+            const int k1 = k / n, k2 = k % n;
+            T s = T(0);
+            for (int t1 = 0; t1 < kap; ++t1) {
+                const int base = (k1 * kap + t1) * N + k2 * kap;
+                for (int t2 = 0; t2 < kap; ++t2) {
+                    const T v = (T)P.mu[base + t2] * inv;
+                    a[base + t2] = v;
+                    s += v;
+                }
+            }
+            At[k] = s;
+        }
+        __syncthreads();
+        for (int l = threadIdx.x; l < M; l += blockDim.x) {
+            T r = T(0);
+            for (int e = P.colptr[l]; e < P.colptr[l + 1]; ++e) r += (T)P.valc[e] * At[P.rowidx[e]];
+            r *= kinv4;
+            const T inv = r > T(0) ? T(1) / r : T(0);
+            const int l1 = l / n, l2 = l % n;
+            T s = T(0);
+            for (int t1 = 0; t1 < kap; ++t1) {
+                const int base = (l1 * kap + t1) * N + l2 * kap;
+                for (int t2 = 0; t2 < kap; ++t2) {
+                    const T v = (T)P.nu[base + t2] * inv;
+                    b[base + t2] = v;
+                    s += v;
+                }
+            }
+            Bt[l] = s;
+        }
+        __syncthreads();
+    }
+
+    // ---- FP64 sweeps on block scalars until the marginals are exact --------
+    // With the uniform kernel a_i / mu_i and b_j / nu_j stay constant on each
+    // block, so a sweep acts on alpha_k, beta_l exactly.  The FP64 sweeps
+    // start, as Alg. 4 does, from b = 1 (block sums kappa^2): from there the
+    // fixed point is reached after one sweep, whereas from the rounded FP32
+    // state IPF on the tree-shaped support of pi~ barely contracts.  They stop
+    // once the FP64 residual is at rounding level (at most four sweeps).
+    const double k4 = (double)kap * kap * kap * kap;
+    const double kinv4_rn = 1.0 / k4, kinv4_lo = __drcp_rd(k4), kinv4_hi = __drcp_ru(k4);
+    for (int l = threadIdx.x; l < M; l += blockDim.x) Bd[l] = (double)(kap * kap);
+    __syncthreads();
+    int fp64_sweeps = 0;
+    for (;;) {
+        for (int k = threadIdx.x; k < M; k += blockDim.x) {        // a = mu / (pi-hat b)
+            double r = 0.0;
+            for (int e = P.rowptr[k]; e < P.rowptr[k + 1]; ++e) r += P.val[e] * Bd[P.colidx[e]];
+            r *= kinv4_rn;
+            alpha[k] = r > 0.0 ? 1.0 / r : 0.0;
+            Ad[k] = alpha[k] * P.mu_c[k];
+        }
+        __syncthreads();
+        for (int l = threadIdx.x; l < M; l += blockDim.x) {        // b = nu / (pi-hat^T a)
+            double s = 0.0;
+            for (int e = P.colptr[l]; e < P.colptr[l + 1]; ++e) s += P.valc[e] * Ad[P.rowidx[e]];
+            s *= kinv4_rn;
+            beta[l] = s > 0.0 ? 1.0 / s : 0.0;
+        }
+        __syncthreads();
+        ++fp64_sweeps;
+        double res = 0.0;                                         // ||mu-hat - mu||_1
+        for (int k = threadIdx.x; k < M; k += blockDim.x) {
+            double s = 0.0;
+            for (int e = P.rowptr[k]; e < P.rowptr[k + 1]; ++e) s += P.val[e] * beta[P.colidx[e]] * P.nu_c[P.colidx[e]];
+            res += fabs(alpha[k] * kinv4_rn * s - 1.0) * P.mu_c[k];
+        }
+        res = block_reduce_rn(res, red);
+        if (res <= 4e-15 || fp64_sweeps >= 4) break;
+        for (int l = threadIdx.x; l < M; l += blockDim.x) Bd[l] = beta[l] * P.nu_c[l];
+        __syncthreads();
+    }
+    // the certified plan is pi-hat_xi(i,j) = alpha_k mu_i kappa^-4 pi~_kl beta_l nu_j
+    if (P.a_out) {
+        for (int k = threadIdx.x; k < M; k += blockDim.x) {
+            const int k1 = k / n, k2 = k % n;
+            for (int t1 = 0; t1 < kap; ++t1)
+                for (int t2 = 0; t2 < kap; ++t2) {
+                    const int i = (k1 * kap + t1) * N + k2 * kap + t2;
+                    P.a_out[i] = alpha[k] * P.mu[i];
+                }
+        }
+    }
+    if (P.b_out) {
+        for (int l = threadIdx.x; l < M; l += blockDim.x) {
+            const int l1 = l / n, l2 = l % n;
+            for (int t1 = 0; t1 < kap; ++t1)
+                for (int t2 = 0; t2 < kap; ++t2) {
+                    const int j = (l1 * kap + t1) * N + l2 * kap + t2;
+                    P.b_out[j] = beta[l] * P.nu[j];
+                }
+        }
+    }
+
+    // ---- certified marginals and TV sums ---------------------------------
+    // rho_k = alpha_k kappa^-4 sum_l pi~_kl beta_l nu~_l ;  mu-hat = rho_k mu
+    double tv_mu = 0.0, res_mu = 0.0;
+    for (int k = threadIdx.x; k < M; k += blockDim.x) {
+        const int k1 = k / n, k2 = k % n;
+        double m_lo = 0.0, m_hi = 0.0, w_hi = 0.0;
+        for (int t1 = 0; t1 < kap; ++t1)
+            for (int t2 = 0; t2 < kap; ++t2) {
+                const int r = k1 * kap + t1, c = k2 * kap + t2;
+                const double x = P.mu[r * N + c];
+                m_lo = __dadd_rd(m_lo, x); m_hi = __dadd_ru(m_hi, x);
+                w_hi = __fma_ru(tv_weight_hi(r, c, N, P.p), x, w_hi);
+            }
+        double s_lo = 0.0, s_hi = 0.0;
+        for (int e = P.rowptr[k]; e < P.rowptr[k + 1]; ++e) {
+            const int l = P.colidx[e];
+            const int l1 = l / n, l2 = l % n;
+            double nl_lo = 0.0, nl_hi = 0.0;
+            for (int t1 = 0; t1 < kap; ++t1)
+                for (int t2 = 0; t2 < kap; ++t2) {
+                    const double y = P.nu[(l1 * kap + t1) * N + l2 * kap + t2];
+                    nl_lo = __dadd_rd(nl_lo, y); nl_hi = __dadd_ru(nl_hi, y);
+                }
+            s_lo = __fma_rd(__dmul_rd(P.val[e], beta[l]), nl_lo, s_lo);
+            s_hi = __fma_ru(__dmul_ru(P.val[e], beta[l]), nl_hi, s_hi);
+        }
+        const double rho_lo = __dmul_rd(__dmul_rd(alpha[k], kinv4_lo), s_lo);
+        const double rho_hi = __dmul_ru(__dmul_ru(alpha[k], kinv4_hi), s_hi);
+        double dev = fmax(0.0, fmax(__dsub_ru(rho_hi, 1.0), __dsub_ru(1.0, rho_lo)));
+        if (m_hi == 0.0) dev = 0.0;    // empty block: mu-hat = mu = 0 there
+        tv_mu = __fma_ru(dev, w_hi, tv_mu);
+        res_mu += fabs(0.5 * (rho_lo + rho_hi) - 1.0) * P.mu_c[k];
+    }
+    double tv_nu = 0.0, res_nu = 0.0;
+    for (int l = threadIdx.x; l < M; l += blockDim.x) {
+        const int l1 = l / n, l2 = l % n;
+        double w_hi = 0.0, m_hi = 0.0;
+        for (int t1 = 0; t1 < kap; ++t1)
+            for (int t2 = 0; t2 < kap; ++t2) {
+                const int r = l1 * kap + t1, c = l2 * kap + t2;
+                const double y = P.nu[r * N + c];
+                m_hi = __dadd_ru(m_hi, y);
+                w_hi = __fma_ru(tv_weight_hi(r, c, N, P.p), y, w_hi);
+            }
+        double s_lo = 0.0, s_hi = 0.0;
+        for (int e = P.colptr[l]; e < P.colptr[l + 1]; ++e) {
+            const int k = P.rowidx[e];
+            const int k1 = k / n, k2 = k % n;
+            double ml_lo = 0.0, ml_hi = 0.0;
+            for (int t1 = 0; t1 < kap; ++t1)
+                for (int t2 = 0; t2 < kap; ++t2) {
+                    const double x = P.mu[(k1 * kap + t1) * N + k2 * kap + t2];
+                    ml_lo = __dadd_rd(ml_lo, x); ml_hi = __dadd_ru(ml_hi, x);
+                }
+            s_lo = __fma_rd(__dmul_rd(P.valc[e], alpha[k]), ml_lo, s_lo);
+            s_hi = __fma_ru(__dmul_ru(P.valc[e], alpha[k]), ml_hi, s_hi);
+        }
+        const double sg_lo = __dmul_rd(__dmul_rd(beta[l], kinv4_lo), s_lo);
+        const double sg_hi = __dmul_ru(__dmul_ru(beta[l], kinv4_hi), s_hi);
+        double dev = fmax(0.0, fmax(__dsub_ru(sg_hi, 1.0), __dsub_ru(1.0, sg_lo)));
+        if (m_hi == 0.0) dev = 0.0;
+        tv_nu = __fma_ru(dev, w_hi, tv_nu);
+        res_nu += fabs(0.5 * (sg_lo + sg_hi) - 1.0) * P.nu_c[l];
+    }
+
+    // ---- certified cost of the fitted plan over its support -----------------
+    // W-hat^p = sum_{(k,l) in supp pi~} kappa^-4 pi~_kl alpha_k beta_l num_kl,
+    // num_kl = sum_{i in X_k, j in Y_l} mu_i nu_j rho(x_i, y_j)^p (rounded up)
+    const T* tab = reinterpret_cast<const T*>(P.ctab_hi);
+    double cost = 0.0;
+    for (int e = threadIdx.x; e < P.nnz; e += blockDim.x) {
+        // row of entry e: binary search in rowptr
+        int lo = 0, hi = M;
+        while (hi - lo > 1) { const int mid = (lo + hi) >> 1; if (P.rowptr[mid] <= e) lo = mid; else hi = mid; }
+        const int k = lo, l = P.colidx[e];
+        const int k1 = k / n, k2 = k % n, l1 = l / n, l2 = l % n;
+        T num = T(0);
+        for (int a1 = 0; a1 < kap; ++a1)
+            for (int a2 = 0; a2 < kap; ++a2) {
+                const int xr = k1 * kap + a1, xc = k2 * kap + a2;
+                T inner = T(0);
+                for (int b1 = 0; b1 < kap; ++b1)
+                    for (int b2 = 0; b2 < kap; ++b2) {
+                        const int yr = l1 * kap + b1, yc = l2 * kap + b2;
+                        inner = fma_ru(from_double_ru<T>(P.nu[yr * N + yc]),
+                                       tab[abs(xr - yr) * N + abs(xc - yc)], inner);
+                    }
+                num = fma_ru(from_double_ru<T>(P.mu[xr * N + xc]), inner, num);
+            }
+        const double term = __dmul_ru(__dmul_ru(__dmul_ru(__dmul_ru(P.val[e], kinv4_hi), alpha[k]), beta[l]),
+                                      (double)num);
+        cost = __dadd_ru(cost, term);
+    }
+    const double cost_sum = block_reduce_ru(cost, red);
+    const double tvm = block_reduce_ru(tv_mu, red);
+    const double tvn = block_reduce_ru(tv_nu, red);
+    const double rm = block_reduce_rn(res_mu, red);
+    const double rn = block_reduce_rn(res_nu, red);
+    if (threadIdx.x == 0) {
+        const double p = P.p;
+        // Delta = 2^(1-1/p) <w, |.|>^(1/p) = (2^(p-1) <w, |.|>)^(1/p)
+        const double scale = (p == 1.0) ? 1.0 : (p == 2.0 ? 2.0 : __dmul_ru(pow(2.0, p - 1.0), 1.0 + 0x1p-49));
+        const double dmu = root_p_ru(__dmul_ru(scale, tvm), p);
+        const double dnu = root_p_ru(__dmul_ru(scale, tvn), p);
+        const double w_hat = root_p_ru(cost_sum, p);
+        PairOut& O = outs[P.out_index];
+        O.w_hat_p = cost_sum;
+        O.delta_mu = dmu;
+        O.delta_nu = dnu;
+        O.ub_primal = __dadd_ru(__dadd_ru(w_hat, dmu), dnu);
+        O.ipf_residual = rm + rn;
+        O.sweeps_done = P.sweeps + fp64_sweeps;
+    }
+}
+
+int launch_primal(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs,
+                  int M_max, int, bool f64, cudaStream_t stream) {
+    if (n_pairs <= 0) return QWB_OK;
+    const size_t tsz = f64 ? 8 : 4;
+    const size_t smem = 4 * sizeof(double) * (size_t)M_max + 2 * tsz * (size_t)M_max;
+    if (smem > 220 * 1024) return QWB_ERR_UNSUPPORTED;
+    if (f64) {
+        QWB_CUDA(cudaFuncSetAttribute(primal_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        primal_kernel<double><<<n_pairs, PRIMAL_THREADS, smem, stream>>>(pairs_d, outs_d, pair_ids);
+    } else {
+        QWB_CUDA(cudaFuncSetAttribute(primal_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        primal_kernel<float><<<n_pairs, PRIMAL_THREADS, smem, stream>>>(pairs_d, outs_d, pair_ids);
+    }
+    QWB_LAUNCHED();
+    return QWB_OK;
+}
+
+// --------------------------------------------------------------------------
+// centre: s = <f~, mu~> so that the upscaled potential is f~ - s (the lower
+// bound is invariant to such shifts because both measures have mass 1).
+// --------------------------------------------------------------------------
+__global__ void centre_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
+                              const int* __restrict__ pair_ids) {
+    __shared__ double red[33];
+    const PairDev& P = pairs[pair_ids[blockIdx.x]];
+    double s = 0.0;
+    for (int k = threadIdx.x; k < P.M; k += blockDim.x) s += P.f_coarse[k] * P.mu_c[k];
+    s = block_reduce_rn(s, red);
+    if (threadIdx.x == 0) outs[P.out_index].centre_shift = s;
+}
+
+int launch_centre(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs,
+                  cudaStream_t stream) {
+    if (n_pairs <= 0) return QWB_OK;
+    centre_kernel<<<n_pairs, 256, 0, stream>>>(pairs_d, outs_d, pair_ids);
+    QWB_LAUNCHED();
+    return QWB_OK;
+}
+
+// --------------------------------------------------------------------------
+// upsample: f-hat(x) = R_{f~ - s}(x), bilinear in block-centre coordinates
+// t = (x - (kappa-1)/2) / kappa with linear extrapolation at the border
+// (Sec. 3.5; Alg. 5).  Also resets the c-transform outputs to +inf when they
+// are combined with atomics.
+// --------------------------------------------------------------------------
+template <typename T>
+__global__ void upsample_kernel(const PairDev* __restrict__ pairs, const PairOut* __restrict__ outs,
+                                const PixItem* __restrict__ items) {
+    const PixItem I = items[blockIdx.x];
+    const PairDev& P = pairs[I.pair];
+    const int i = I.start + threadIdx.x;
+    const int N = P.N, n = P.n, kap = P.kappa;
+    if (i >= N * N) return;
+    const double s = outs[P.out_index].centre_shift;
+    const int r = i / N, c = i % N;
+    double v;
+    if (n == 1) {
+        v = P.f_coarse[0] - s;
+    } else {
+        const double tr = (r - 0.5 * (kap - 1)) / kap, tc = (c - 0.5 * (kap - 1)) / kap;
+        const int r0 = min(max((int)floor(tr), 0), n - 2), c0 = min(max((int)floor(tc), 0), n - 2);
+        const double wr = tr - r0, wc = tc - c0;
+        const double f00 = P.f_coarse[r0 * n + c0] - s, f01 = P.f_coarse[r0 * n + c0 + 1] - s;
+        const double f10 = P.f_coarse[(r0 + 1) * n + c0] - s, f11 = P.f_coarse[(r0 + 1) * n + c0 + 1] - s;
+        const double top = (1.0 - wc) * f00 + wc * f01;
+        const double bot = (1.0 - wc) * f10 + wc * f11;
+        v = (1.0 - wr) * top + wr * bot;
+    }
+    reinterpret_cast<T*>(P.fhat)[i] = from_double_rn<T>(v);
+    reinterpret_cast<T*>(P.g)[i] = pos_inf<T>();     // c-transform outputs start at +inf
+    reinterpret_cast<T*>(P.f)[i] = pos_inf<T>();
+}
+
+int launch_upsample(const PairDev* pairs_d, PairOut* outs_d, const PixItem* items, int n_items,
+                    bool f64, cudaStream_t stream) {
+    if (n_items <= 0) return QWB_OK;
+    if (f64) upsample_kernel<double><<<n_items, 256, 0, stream>>>(pairs_d, outs_d, items);
+    else upsample_kernel<float><<<n_items, 256, 0, stream>>>(pairs_d, outs_d, items);
+    QWB_LAUNCHED();
+    return QWB_OK;
+}
+
+// --------------------------------------------------------------------------
+// ctransform: out_j = min_i fl_down(c_ij - h_i)   (Sec. 4, eq. lazy c-transform)
+//
+// Work item = (pair, a contiguous range of threads*R outputs, a range of input
+// rows).  The input rows are staged in shared memory.  Thread t owns R
+// consecutive outputs j = (j1, j2 .. j2+R-1) of one grid row and walks the
+// inputs in chunks of TC columns.  For a chunk starting at column c0 and an
+// input row i1, the R*TC costs take only R+TC-1 distinct values
+//   q_e = rho((i1 - j1, c0 - j2 + e))^p,  e = s - r in [-(R-1), TC-1],
+// so each (input, output) pair costs one subtraction rounded toward -inf and
+// one min.  For p = 2 the costs are exact integers built from
+// (i1-j1)^2 + (c0-j2+e)^2 (the column part is computed once per chunk);
+// other p read them from the round-down cost table.  Because every candidate
+// is rounded down and the min is exact, h_i + out_j <= c_ij holds exactly.
+// Items that cover only part of the inputs combine their partial minima with
+// an exact floating-point atomic min.
+// --------------------------------------------------------------------------
+template <typename T, int R, int TC, bool P2>
+__global__ void __launch_bounds__(256)
+ctransform_kernel(const PairDev* __restrict__ pairs, const CtItem* __restrict__ items,
+                  int n_items, int phase) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* hs = reinterpret_cast<T*>(smem_raw);
+    constexpr int NQ = R + TC - 1;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const CtItem I = items[it];
+        const PairDev& P = pairs[I.pair];
+        const int N = P.N, m = N * N;
+        const T* h = reinterpret_cast<const T*>(phase == 0 ? P.fhat : P.g);
+        T* out = reinterpret_cast<T*>(phase == 0 ? P.g : P.f);
+        const int nin = I.in_rows * N;
+        const T* hsrc = h + (size_t)I.in_row0 * N;
+        for (int k = threadIdx.x; k < nin; k += blockDim.x) hs[k] = hsrc[k];
+        __syncthreads();
+        const int o = I.out0 + threadIdx.x * R;
+        const bool active = o < m;
+        T mins[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) mins[r] = pos_inf<T>();
+        if (active) {
+            const int j1 = o / N, j2 = o % N;
+            const T* tab = reinterpret_cast<const T*>(P.ctab_lo);
+            for (int c0 = 0; c0 < N; c0 += TC) {
+                T colq[NQ];
+                if constexpr (P2) {
+#pragma unroll
+                    for (int e = 0; e < NQ; ++e) {
+                        const T d = (T)(c0 - j2 + e - (R - 1));
+                        colq[e] = d * d;
+                    }
+                }
+                for (int r1 = 0; r1 < I.in_rows; ++r1) {
+                    const int i1 = I.in_row0 + r1;
+                    T q[NQ];
+                    if constexpr (P2) {
+                        const T A = (T)((i1 - j1) * (i1 - j1));
+#pragma unroll
+                        for (int e = 0; e < NQ; ++e) q[e] = A + colq[e];      // exact integers
+                    } else {
+                        const T* trow = tab + (size_t)abs(i1 - j1) * N;
+#pragma unroll
+                        for (int e = 0; e < NQ; ++e) q[e] = trow[abs(c0 - j2 + e - (R - 1))];
+                    }
+                    T fv[TC];
+                    const T* hrow = hs + r1 * N + c0;
+#pragma unroll
+                    for (int s = 0; s < TC; ++s) fv[s] = hrow[s];
+#pragma unroll
+                    for (int s = 0; s < TC; ++s)
+#pragma unroll
+                        for (int r = 0; r < R; ++r)
+                            mins[r] = fmin(mins[r], sub_rd(q[s - r + R - 1], fv[s]));
+                }
+            }
+            if (I.in_rows < N) {      // partial minimum: combine across items
+#pragma unroll
+                for (int r = 0; r < R; ++r) atomic_min_fp(&out[o + r], mins[r]);
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) out[o + r] = mins[r];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+int ct_pick_r(int N, int want) {
+    for (int r = want; r > 1; r >>= 1)
+        if (N % r == 0) return r;
+    return 1;
+}
+
+template <typename T, int R, bool P2>
+static int ct_launch_rt(const PairDev* pairs_d, const CtItem* items, int n_items, int phase,
+                        int threads, int in_rows, int N_max, int grid_cap, cudaStream_t stream) {
+    auto kern = ctransform_kernel<T, R, R, P2>;
+    const size_t smem = sizeof(T) * (size_t)in_rows * N_max;
+    if (smem > 227 * 1024) return QWB_ERR_UNSUPPORTED;
+    QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = grid_cap > 0 ? std::min(n_items, grid_cap) : n_items;
+    kern<<<grid, threads, smem, stream>>>(pairs_d, items, n_items, phase);
+    QWB_LAUNCHED();
+    return QWB_OK;
+}
+
+template <typename T, bool P2>
+static int ct_launch_t(const PairDev* pairs_d, const CtItem* items, int n_items, int phase,
+                       const CtConfig& cfg, int N_max, int grid_cap, cudaStream_t stream) {
+    switch (cfg.R) {
+        case 1: return ct_launch_rt<T, 1, P2>(pairs_d, items, n_items, phase, cfg.threads, cfg.in_rows, N_max, grid_cap, stream);
+        case 2: return ct_launch_rt<T, 2, P2>(pairs_d, items, n_items, phase, cfg.threads, cfg.in_rows, N_max, grid_cap, stream);
+        case 4: return ct_launch_rt<T, 4, P2>(pairs_d, items, n_items, phase, cfg.threads, cfg.in_rows, N_max, grid_cap, stream);
+        case 8: return ct_launch_rt<T, 8, P2>(pairs_d, items, n_items, phase, cfg.threads, cfg.in_rows, N_max, grid_cap, stream);
+        case 16: return ct_launch_rt<T, 16, P2>(pairs_d, items, n_items, phase, cfg.threads, cfg.in_rows, N_max, grid_cap, stream);
+        default: return QWB_ERR_UNSUPPORTED;
+    }
+}
+
+int launch_ctransform(const PairDev* pairs_d, const CtItem* items, int n_items, int phase,
+                      const CtConfig& cfg, int N_max, bool f64, int grid_cap, cudaStream_t stream) {
+    if (n_items <= 0) return QWB_OK;
+    // the p = 2 specialisation needs every pair of the launch at p = 2
+    const bool p2 = cfg.p2;
+    const CtConfig& c = cfg;
+    if (f64) return p2 ? ct_launch_t<double, true>(pairs_d, items, n_items, phase, c, N_max, grid_cap, stream)
+                       : ct_launch_t<double, false>(pairs_d, items, n_items, phase, c, N_max, grid_cap, stream);
+    return p2 ? ct_launch_t<float, true>(pairs_d, items, n_items, phase, c, N_max, grid_cap, stream)
+              : ct_launch_t<float, false>(pairs_d, items, n_items, phase, c, N_max, grid_cap, stream);
+}
+
+// --------------------------------------------------------------------------
+// lbsum: lb_p = <f, mu> + <g, nu> summed with FP64 round-down fused
+// multiply-adds, so lb_p <= the real dual objective of the stored (f, g)
+// (Sec. 3.5, eq. upscaling LB); LB = max(lb_p, 0)^(1/p) rounded down.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ double block_reduce_rd(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v = __dadd_rd(v, __shfl_down_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = __dadd_rd(s, red[w]);
+        red[32] = s;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+template <typename T>
+__global__ void lbsum_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
+                             const int* __restrict__ pair_ids) {
+    __shared__ double red[33];
+    const PairDev& P = pairs[pair_ids[blockIdx.x]];
+    const int m = P.N * P.N;
+    const T* f = reinterpret_cast<const T*>(P.f);
+    const T* g = reinterpret_cast<const T*>(P.g);
+    double s = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const double fi = (double)f[i], gi = (double)g[i];
+        s = __fma_rd(fi, P.mu[i], s);
+        s = __fma_rd(gi, P.nu[i], s);
+        if (P.f_out) P.f_out[i] = fi;
+        if (P.g_out) P.g_out[i] = gi;
+    }
+    s = block_reduce_rd(s, red);
+    if (threadIdx.x == 0) {
+        PairOut& O = outs[P.out_index];
+        O.lb_p = s;
+        O.lb = root_p_rd(fmax(s, 0.0), P.p);
+    }
+}
+
+int launch_lbsum(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs,
+                 bool f64, cudaStream_t stream) {
+    if (n_pairs <= 0) return QWB_OK;
+    if (f64) lbsum_kernel<double><<<n_pairs, 1024, 0, stream>>>(pairs_d, outs_d, pair_ids);
+    else lbsum_kernel<float><<<n_pairs, 1024, 0, stream>>>(pairs_d, outs_d, pair_ids);
+    QWB_LAUNCHED();
+    return QWB_OK;
+}
+
+// --------------------------------------------------------------------------
+// adjoint: grad_i = (1/p) lb_p^(1/p - 1) (f_i - <f, mu>)
+// --------------------------------------------------------------------------
+__global__ void dot_kernel(const double* __restrict__ f, const double* __restrict__ mu, int m,
+                           double* out) {
+    __shared__ double red[33];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) s += f[i] * mu[i];
+    s = block_reduce_rn(s, red);
+    if (threadIdx.x == 0) *out = s;
+}
+__global__ void adjoint_kernel(const double* __restrict__ f, const double* __restrict__ fmu,
+                               int m, double scale, double* __restrict__ grad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) grad[i] = scale * (f[i] - *fmu);
+}
+
+int launch_adjoint(int N, double p, const double* f, const double* mu, double lb_p, double* grad,
+                   double* scratch, cudaStream_t stream) {
+    const int m = N * N;
+    dot_kernel<<<1, 1024, 0, stream>>>(f, mu, m, scratch);
+    QWB_LAUNCHED();
+    const double scale = lb_p > 0.0 ? (1.0 / p) * pow(lb_p, 1.0 / p - 1.0) : 0.0;
+    adjoint_kernel<<<(m + 255) / 256, 256, 0, stream>>>(f, scratch, m, scale, grad);
+    QWB_LAUNCHED();
+    return QWB_OK;
+}
+
+// --------------------------------------------------------------------------
+// Standalone c-transform of a caller potential (FP64 in and out).
+// --------------------------------------------------------------------------
+template <typename T>
+__global__ void to_work_ru(const double* __restrict__ h, T* __restrict__ w, T* __restrict__ o,
+                           int m, int init_out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    w[i] = from_double_ru<T>(h[i]);
+    if (init_out) o[i] = pos_inf<T>();
+}
+template <typename T>
+__global__ void from_work(const T* __restrict__ o, double* __restrict__ out, int m) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) out[i] = (double)o[i];
+}
+
+int launch_to_work(const double* h, void* work_in, void* work_out, int m, bool f64,
+                   cudaStream_t stream) {
+    const int bl = (m + 255) / 256;
+    if (f64) to_work_ru<double><<<bl, 256, 0, stream>>>(h, (double*)work_in, (double*)work_out, m, 1);
+    else to_work_ru<float><<<bl, 256, 0, stream>>>(h, (float*)work_in, (float*)work_out, m, 1);
+    QWB_LAUNCHED();
+    return QWB_OK;
+}
+
+int launch_from_work(const void* work, double* out, int m, bool f64, cudaStream_t stream) {
+    const int bl = (m + 255) / 256;
+    if (f64) from_work<double><<<bl, 256, 0, stream>>>((const double*)work, out, m);
+    else from_work<float><<<bl, 256, 0, stream>>>((const float*)work, out, m);
+    QWB_LAUNCHED();
+    return QWB_OK;
+}
+
+}  // namespace qwb

@@ -1,0 +1,86 @@
+// kernels.h -- device data structures and launchers shared by the entry points.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace qwb {
+
+// Per-pair device descriptor.  Scalar type of the device passes is float
+// (MIXED) or double (F64); typed arrays are stored as void* and cast by the
+// kernels, which are templated on that type.
+struct PairDev {
+    int N, kappa, n, M;
+    double p;
+    const double* mu;       // N*N fine measures (FP64, caller-owned)
+    const double* nu;
+    double* mu_c;           // M coarse masses, round-to-nearest sums
+    double* nu_c;
+    double* mu_c_lo;        // M coarse masses, round-down sums
+    double* nu_c_lo;
+    double* cbar;           // M*M coarse cost out (may be null)
+    const void* ctab_lo;    // N*N cost table, lower brackets (T)
+    const void* ctab_hi;    // N*N cost table, upper brackets (T)
+    // coarse plan (CSR and CSC) for the primal pass
+    const int* rowptr; const int* colidx; const double* val;
+    const int* colptr; const int* rowidx; const double* valc;
+    int nnz;
+    int sweeps;
+    void* a; void* b;       // N*N fine scalings work (T)
+    double* a_out; double* b_out;   // optional FP64 outputs
+    // dual pass
+    const double* f_coarse; // M
+    void* fhat; void* g; void* f;   // N*N (T)
+    double* f_out; double* g_out;   // optional FP64 outputs
+    int ct_split;           // > 1 when c-transform outputs are combined by atomics
+    int out_index;          // index into the results array
+};
+
+// Device-side results (one per pair).
+struct PairOut {
+    double lb, lb_p, w_hat_p, ub_primal, delta_mu, delta_nu, ipf_residual;
+    double mass_mu, mass_nu, centre_shift;
+    int bad_mu, bad_nu;
+    int sweeps_done, pad;
+};
+
+struct CbarItem { int pair, k1, l1, pad; };
+struct CtItem { int pair, out0, in_row0, in_rows; };
+struct PixItem { int pair, start; };
+
+// Launch configuration of the c-transform (chosen by the autotuner).
+struct CtConfig {
+    int R = 8;          // outputs per thread (consecutive in a row)
+    int TC = 8;         // input columns per register chunk
+    int threads = 256;  // threads per CTA
+    int in_rows = 4;    // input rows per work item (split of the min)
+    bool p2 = false;    // every pair of the launch has p = 2 (exact integer costs)
+};
+
+// Launchers.  All enqueue on `stream` and return a qwb status.
+int launch_cost_tables(int N, double p, bool f64, void* lo, void* hi, cudaStream_t stream);
+int launch_prepare(const PairDev* pairs_d, PairOut* outs_d, const PixItem* items, int n_items,
+                   bool f64, cudaStream_t stream);
+int launch_cbar(const PairDev* pairs_d, const CbarItem* items, int n_items, int kappa_max,
+                int n_max, int N_max, bool f64, cudaStream_t stream);
+int launch_primal(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs,
+                  int M_max, int nnz_max, bool f64, cudaStream_t stream);
+int launch_upsample(const PairDev* pairs_d, PairOut* outs_d, const PixItem* items, int n_items,
+                    bool f64, cudaStream_t stream);
+int launch_centre(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs,
+                  cudaStream_t stream);
+int launch_ctransform(const PairDev* pairs_d, const CtItem* items, int n_items, int phase,
+                      const CtConfig& cfg, int N_max, bool f64, int grid_cap,
+                      cudaStream_t stream);
+int launch_lbsum(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs,
+                 bool f64, cudaStream_t stream);
+int launch_to_work(const double* h, void* work_in, void* work_out, int m, bool f64,
+                   cudaStream_t stream);
+int launch_from_work(const void* work, double* out, int m, bool f64, cudaStream_t stream);
+int launch_adjoint(int N, double p, const double* f, const double* mu, double lb_p,
+                   double* grad, double* scratch, cudaStream_t stream);
+
+// Valid (R, TC) for a grid side N (both must divide N).
+int ct_pick_r(int N, int want);
+
+}  // namespace qwb

@@ -1,0 +1,304 @@
+// netsimplex.cpp -- primal network simplex for the dense coarse transport LP.
+//
+// Solves min <pi, C> subject to pi 1 = a, pi^T 1 = b, pi >= 0 (Sec. 2.1) and
+// returns an optimal basic plan (at most n_src + n_dst - 1 positive entries,
+// Sec. 4) with optimal Kantorovich potentials.  The coarse problems of Sec.
+// 3.2 (C-bar), 3.4 and 3.5 (C~) are all of this form.
+//
+// Design (textbook primal network simplex, written for this library):
+//   * graph: sources 0..n-1, sinks n..n+m-1, an artificial root n+m;
+//     real arc a = i*m + j (source i -> sink j, cost C[a]) and one artificial
+//     arc per node (source with supply -> root, root -> other nodes) with a
+//     cost BIG above any path cost, so that the all-artificial star is a
+//     strongly feasible starting tree;
+//   * spanning tree stored as parent pointers with doubly linked child
+//     lists; the flow of each tree arc is kept on its child node;
+//   * block-search pricing over the real arcs (block ~ sqrt(#arcs)),
+//     reduced cost rc(u,w) = c(u,w) - pot[u] + pot[w];
+//   * leaving arc by the strongly feasible rule (the last blocking arc met
+//     when the pivot cycle is traversed from its apex along the entering
+//     arc's direction), which prevents cycling under degeneracy;
+//   * after each pivot the re-hung subtree gets its depths and potentials
+//     recomputed from its new parent; potentials are re-centred now and then
+//     so that the artificial cost does not eat their precision;
+//   * at the end the tree flows are recomputed exactly from the supplies
+//     (leaf elimination) and the potentials are made exactly dual feasible by
+//     one coarse c-transform each way (g = f^c, f = g^c).
+#include "netsimplex.h"
+
+#include <algorithm>
+#include <cmath>
+#include <limits>
+
+#include "../../include/qwb.h"
+
+namespace qwb {
+namespace {
+
+struct Solver {
+    int n = 0, m = 0, V = 0, root = 0;
+    int64_t NM = 0;
+    const double* C = nullptr;
+    double BIG = 0.0, eps = 0.0;
+    std::vector<double> supply;
+    std::vector<signed char> art_up;  // artificial arc of node v: 1 = v -> root
+    std::vector<int> parent, depth, first_child, next_sib, prev_sib;
+    std::vector<int64_t> pred;        // arc joining v and parent[v]
+    std::vector<signed char> up;      // 1 if pred[v] is directed v -> parent[v]
+    std::vector<double> flow;         // flow on pred[v]
+    std::vector<double> pot;
+    std::vector<int> stack, path;
+    std::vector<int64_t> old_pred;
+    std::vector<signed char> old_up;
+    std::vector<double> old_flow;
+    int64_t price_pos = 0, block = 64;
+
+    int tail(int64_t a) const {
+        if (a < NM) return (int)(a / m);
+        int v = (int)(a - NM);
+        return art_up[v] ? v : root;
+    }
+    double cost(int64_t a) const { return a < NM ? C[a] : BIG; }
+
+    void add_child(int p, int c) {
+        parent[c] = p;
+        prev_sib[c] = -1;
+        next_sib[c] = first_child[p];
+        if (first_child[p] >= 0) prev_sib[first_child[p]] = c;
+        first_child[p] = c;
+    }
+    void remove_child(int c) {
+        int p = parent[c];
+        if (prev_sib[c] >= 0) next_sib[prev_sib[c]] = next_sib[c];
+        else first_child[p] = next_sib[c];
+        if (next_sib[c] >= 0) prev_sib[next_sib[c]] = prev_sib[c];
+        prev_sib[c] = next_sib[c] = -1;
+    }
+    void pot_from_parent(int v) {
+        const int p = parent[v];
+        const double c = cost(pred[v]);
+        pot[v] = up[v] ? c + pot[p] : pot[p] - c;   // rc of the tree arc is zero
+    }
+    void refresh_subtree(int r) {
+        stack.clear();
+        stack.push_back(r);
+        while (!stack.empty()) {
+            int v = stack.back();
+            stack.pop_back();
+            depth[v] = depth[parent[v]] + 1;
+            pot_from_parent(v);
+            for (int c = first_child[v]; c >= 0; c = next_sib[c]) stack.push_back(c);
+        }
+    }
+    void recentre() {
+        // subtract a common constant (rc is invariant); keep real nodes small
+        double s = 0.0;
+        for (int v = 0; v < n + m; ++v) s += pot[v];
+        s /= (double)(n + m);
+        for (int v = 0; v < V; ++v) pot[v] -= s;
+        // recompute from the root for accuracy
+        for (int c = first_child[root]; c >= 0; c = next_sib[c]) refresh_subtree(c);
+    }
+
+    void init(int n_, int m_, const double* C_, const double* a, const double* b) {
+        n = n_; m = m_; V = n + m + 1; root = n + m; NM = (int64_t)n * m; C = C_;
+        double maxc = 0.0;
+        for (int64_t k = 0; k < NM; ++k) maxc = std::max(maxc, C[k]);
+        BIG = (double)(V + 1) * (maxc + 1.0);
+        eps = 1e-12 * (maxc + 1.0);
+        supply.assign(V, 0.0);
+        double sa = 0.0, sb = 0.0;
+        for (int i = 0; i < n; ++i) { supply[i] = a[i]; sa += a[i]; }
+        for (int j = 0; j < m; ++j) { supply[n + j] = -b[j]; sb += b[j]; }
+        supply[root] = sb - sa;
+        art_up.assign(V, 0);
+        parent.assign(V, -1); depth.assign(V, 0);
+        first_child.assign(V, -1); next_sib.assign(V, -1); prev_sib.assign(V, -1);
+        pred.assign(V, -1); up.assign(V, 0); flow.assign(V, 0.0); pot.assign(V, 0.0);
+        for (int v = 0; v < n + m; ++v) {
+            const bool src_pos = (v < n) && (a[v] > 0.0);
+            art_up[v] = src_pos ? 1 : 0;
+            add_child(root, v);
+            depth[v] = 1;
+            pred[v] = NM + v;
+            up[v] = art_up[v];
+            flow[v] = (v < n) ? a[v] : b[v - n];
+            pot[v] = src_pos ? BIG : -BIG;
+        }
+        block = std::max<int64_t>(64, (int64_t)std::sqrt((double)NM));
+        price_pos = 0;
+    }
+
+    // Block-search pricing: the most negative reduced cost in the first block
+    // that has one.  Returns -1 at optimality.
+    int64_t find_entering(double* rc_out) {
+        int64_t scanned = 0;
+        int64_t pos = price_pos;
+        while (scanned < NM) {
+            const int64_t end = std::min<int64_t>(pos + block, NM);
+            double best = -eps;
+            int64_t best_a = -1;
+            int i = (int)(pos / m), j = (int)(pos % m);
+            for (int64_t a = pos; a < end; ++a) {
+                const double rc = C[a] - pot[i] + pot[n + j];
+                if (rc < best) { best = rc; best_a = a; }
+                if (++j == m) { j = 0; ++i; }
+            }
+            scanned += end - pos;
+            pos = (end == NM) ? 0 : end;
+            if (best_a >= 0) {
+                price_pos = pos;
+                *rc_out = best;
+                return best_a;
+            }
+        }
+        return -1;
+    }
+
+    void pivot(int64_t e) {
+        const int k = tail(e);
+        const int l = n + (int)(e % m);   // entering arcs are real arcs
+        // apex of the cycle
+        int u = k, w = l;
+        while (u != w) {
+            if (depth[u] > depth[w]) u = parent[u];
+            else if (depth[w] > depth[u]) w = parent[w];
+            else { u = parent[u]; w = parent[w]; }
+        }
+        const int apex = u;
+        // delta = min flow over arcs whose flow decreases along the cycle
+        double delta = std::numeric_limits<double>::infinity();
+        for (int v = l; v != apex; v = parent[v])      // traversed upward
+            if (!up[v]) delta = std::min(delta, flow[v]);
+        for (int v = k; v != apex; v = parent[v])      // traversed downward
+            if (up[v]) delta = std::min(delta, flow[v]);
+        // leaving arc: last blocking arc from the apex along the orientation
+        int q = -1;
+        bool on_l_side = false;
+        for (int v = l; v != apex; v = parent[v])
+            if (!up[v] && flow[v] <= delta) { q = v; on_l_side = true; }
+        if (q < 0) {
+            for (int v = k; v != apex; v = parent[v])
+                if (up[v] && flow[v] <= delta) { q = v; break; }
+        }
+        // flows
+        for (int v = l; v != apex; v = parent[v]) flow[v] += up[v] ? delta : -delta;
+        for (int v = k; v != apex; v = parent[v]) flow[v] += up[v] ? -delta : delta;
+        // re-hang the subtree of q through the entering arc
+        const int e1 = on_l_side ? l : k;
+        const int e2 = on_l_side ? k : l;
+        path.clear();
+        for (int v = e1;; v = parent[v]) { path.push_back(v); if (v == q) break; }
+        const int t = (int)path.size() - 1;
+        old_pred.resize(t); old_up.resize(t); old_flow.resize(t);
+        for (int s = 0; s < t; ++s) {
+            old_pred[s] = pred[path[s]]; old_up[s] = up[path[s]]; old_flow[s] = flow[path[s]];
+        }
+        remove_child(q);
+        for (int s = 0; s < t; ++s) remove_child(path[s]);
+        for (int s = 0; s < t; ++s) {
+            const int child = path[s + 1];
+            add_child(path[s], child);
+            pred[child] = old_pred[s];
+            up[child] = old_up[s] ? 0 : 1;
+            flow[child] = old_flow[s];
+        }
+        add_child(e2, e1);
+        pred[e1] = e;
+        up[e1] = (tail(e) == e1) ? 1 : 0;
+        flow[e1] = delta;
+        refresh_subtree(e1);
+    }
+
+    // Exact tree flows from the supplies (post-order leaf elimination).
+    void recompute_flows() {
+        std::vector<int> order;
+        order.reserve(V);
+        stack.clear();
+        stack.push_back(root);
+        while (!stack.empty()) {
+            int v = stack.back();
+            stack.pop_back();
+            order.push_back(v);
+            for (int c = first_child[v]; c >= 0; c = next_sib[c]) stack.push_back(c);
+        }
+        std::vector<double> S(supply);
+        for (int idx = V - 1; idx >= 1; --idx) {
+            const int v = order[idx];
+            flow[v] = up[v] ? S[v] : -S[v];
+            S[parent[v]] += S[v];
+        }
+    }
+};
+
+}  // namespace
+
+int network_simplex(int32_t n_src, int32_t n_dst, const double* C, const double* a,
+                    const double* b, NSSolution& out, int64_t max_pivots) {
+    if (n_src <= 0 || n_dst <= 0 || !C || !a || !b) return QWB_ERR_INVALID_ARG;
+    const int64_t NM = (int64_t)n_src * n_dst;
+    for (int64_t k = 0; k < NM; ++k)
+        if (!(C[k] >= 0.0) || !std::isfinite(C[k])) return QWB_ERR_INVALID_ARG;
+    for (int i = 0; i < n_src; ++i) if (!(a[i] >= 0.0) || !std::isfinite(a[i])) return QWB_ERR_INVALID_ARG;
+    for (int j = 0; j < n_dst; ++j) if (!(b[j] >= 0.0) || !std::isfinite(b[j])) return QWB_ERR_INVALID_ARG;
+    if (max_pivots < 0) max_pivots = 20 * NM + 1000000;
+
+    Solver S;
+    S.init(n_src, n_dst, C, a, b);
+    int64_t piv = 0;
+    const int64_t recentre_every = std::max<int64_t>(256, S.V);
+    for (;;) {
+        double rc;
+        const int64_t e = S.find_entering(&rc);
+        if (e < 0) break;
+        if (++piv > max_pivots) return QWB_ERR_NOT_CONVERGED;
+        S.pivot(e);
+        if (piv % recentre_every == 0) S.recentre();
+    }
+    S.recompute_flows();
+    // artificial arcs must carry (almost) nothing at an optimum of a feasible problem
+    double mass = 0.0;
+    for (int i = 0; i < n_src; ++i) mass += a[i];
+    for (int v = 0; v < S.n + S.m; ++v)
+        if (S.pred[v] >= NM && S.flow[v] > 1e-9 * std::max(1.0, mass)) return QWB_ERR_NOT_CONVERGED;
+
+    // plan (CSR) from the real tree arcs with positive flow
+    std::vector<std::vector<std::pair<int, double>>> rows(n_src);
+    for (int v = 0; v < S.n + S.m; ++v) {
+        const int64_t arc = S.pred[v];
+        if (arc < NM && S.flow[v] > 0.0)
+            rows[arc / n_dst].push_back({(int)(arc % n_dst), S.flow[v]});
+    }
+    out.rowptr.assign(n_src + 1, 0);
+    out.col.clear(); out.val.clear();
+    double obj = 0.0;
+    for (int i = 0; i < n_src; ++i) {
+        std::sort(rows[i].begin(), rows[i].end());
+        for (auto& cv : rows[i]) {
+            out.col.push_back(cv.first);
+            out.val.push_back(cv.second);
+            obj += cv.second * C[(int64_t)i * n_dst + cv.first];
+        }
+        out.rowptr[i + 1] = (int32_t)out.col.size();
+    }
+    out.obj = obj;
+    // potentials: f_i = pot[i], g_j = -pot[n+j]; then exact dual feasibility
+    out.f.assign(n_src, 0.0);
+    out.g.assign(n_dst, 0.0);
+    for (int i = 0; i < n_src; ++i) out.f[i] = S.pot[i];
+    for (int j = 0; j < n_dst; ++j) {
+        double gj = std::numeric_limits<double>::infinity();
+        for (int i = 0; i < n_src; ++i) gj = std::min(gj, C[(int64_t)i * n_dst + j] - out.f[i]);
+        out.g[j] = gj;
+    }
+    for (int i = 0; i < n_src; ++i) {
+        double fi = std::numeric_limits<double>::infinity();
+        const double* Ci = C + (int64_t)i * n_dst;
+        for (int j = 0; j < n_dst; ++j) fi = std::min(fi, Ci[j] - out.g[j]);
+        out.f[i] = fi;
+    }
+    out.pivots = piv;
+    return QWB_OK;
+}
+
+}  // namespace qwb

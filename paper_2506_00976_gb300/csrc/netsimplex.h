@@ -1,0 +1,25 @@
+// netsimplex.h -- the library's exact solver for the small coarse Kantorovich
+// problems (Sec. 2.1; coarse problems of Sec. 3.2, 3.4, 3.5; network simplex
+// with at most 2M - 1 positive plan entries, Sec. 4).  Host C++, FP64.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+namespace qwb {
+
+struct NSSolution {
+    std::vector<int32_t> rowptr;  // CSR of the plan, n_src + 1
+    std::vector<int32_t> col;     // nnz
+    std::vector<double> val;      // nnz, > 0
+    std::vector<double> f;        // n_src potentials
+    std::vector<double> g;        // n_dst potentials, g_j = min_i C_ij - f_i
+    double obj = 0.0;             // <plan, C>
+    int64_t pivots = 0;
+};
+
+// Returns a qwb status code (0 = OK, NOT_CONVERGED when max_pivots is hit).
+// C: n_src x n_dst row-major, non-negative and finite.  a, b: non-negative.
+int network_simplex(int32_t n_src, int32_t n_dst, const double* C, const double* a,
+                    const double* b, NSSolution& out, int64_t max_pivots = -1);
+
+}  // namespace qwb

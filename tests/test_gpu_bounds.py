@@ -1,0 +1,144 @@
+"""End-to-end GPU tests of the whole method (qwb_bounds / batches) and the
+differentiable lower bound, against the FP64 oracle and exact LP values."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import qwb_oracle as O
+from paper_2506_00976_gb300 import api, synth
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def T(x):
+    return torch.tensor(np.asarray(x, dtype=np.float64), device="cuda")
+
+
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+def test_blob_pair_32_certified(prec):
+    """32 x 32 three-blob pair, kappa 4, p 2: LB <= W (exact 1024 x 1024 LP)
+    <= UB_weighted <= UB_primal; the weighted-cost bound (a unique LP value)
+    matches the oracle."""
+    with open(os.path.join(GOLDEN, "blobs3_32_k4_p2.json")) as fh:
+        gold = json.load(fh)
+    N, kappa, p = 32, 4, 2.0
+    mu, nu = synth.make_measure(N, "blobs3", 0, 0), synth.make_measure(N, "blobs3", 0, 1)
+    r = api.bounds([T(mu)], [T(nu)], [(N, kappa, p)], ipf_sweeps=50, prec=prec)[0]
+    W = gold["w_exact"]
+    assert r["status"] == 0
+    assert r["lb"] <= W <= r["ub_weighted"] <= r["ub_primal"] * (1 + 1e-9)
+    tol = 1e-6 if prec == "f64" else 1e-4
+    assert abs(r["ub_weighted"] - gold["ub_weighted"]) <= tol * gold["ub_weighted"]
+    # LB and UB_primal depend on which optimal coarse solution (the C~ LP is
+    # degenerate on a grid) the solver returns; pass-level tests pin them on
+    # identical inputs, here they are valid and close to the oracle's
+    assert abs(r["lb"] - gold["lb"]) <= 5e-3 * gold["lb"]
+    assert abs(r["ub_primal"] - gold["ub_primal"]) <= 5e-3 * gold["ub_primal"]
+
+
+@pytest.mark.parametrize("p", [1.0, 2.0])
+def test_batched_equals_plain(p):
+    """The batched (graph-captured, persistent) form gives bit-identical results
+    to one pair per launch."""
+    N, kappa = 32, 4
+    pairs = synth.class_pairs(N, "gauss", 30, count=4)
+    mus = [T(a) for a, _ in pairs]
+    nus = [T(b) for _, b in pairs]
+    probs = [(N, kappa, p)] * len(pairs)
+    rb = api.bounds(mus, nus, probs, ipf_sweeps=10, prec="mixed", batched=True)
+    rp = api.bounds(mus, nus, probs, ipf_sweeps=10, prec="mixed", batched=False)
+    for a, b in zip(rb, rp):
+        for k in ("lb", "lb_p", "ub_weighted", "ub_primal", "w_hat_p"):
+            assert a[k] == b[k], k
+
+
+def test_uneven_batch_matches_single_pairs():
+    """Pairs of different N, kappa and p in one batch: each result equals the
+    single-pair result, and every bound is valid against the exact LP."""
+    cases = [(16, 4, 2.0, "gauss"), (32, 8, 1.0, "cauchy"), (24, 4, 2.0, "field"),
+             (16, 2, 1.0, "white"), (32, 4, 2.0, "blobs3")]
+    mus, nus, probs, raw = [], [], [], []
+    for t, (N, kappa, p, cls) in enumerate(cases):
+        mu, nu = synth.make_measure(N, cls, 31, 2 * t), synth.make_measure(N, cls, 31, 2 * t + 1)
+        raw.append((mu, nu))
+        mus.append(T(mu)); nus.append(T(nu)); probs.append((N, kappa, p))
+    rb = api.bounds(mus, nus, probs, ipf_sweeps=5, prec="mixed", batched=True)
+    for t, (N, kappa, p, cls) in enumerate(cases):
+        rs = api.bounds([mus[t]], [nus[t]], [probs[t]], ipf_sweeps=5, prec="mixed", batched=False)[0]
+        for k in ("lb", "ub_weighted", "ub_primal"):
+            assert rb[t][k] == rs[k], (t, k)
+        if N <= 16:
+            W = O.wasserstein_exact(raw[t][0], raw[t][1], N, p)
+            assert rb[t]["lb"] <= W <= min(rb[t]["ub_weighted"], rb[t]["ub_primal"])
+
+
+@pytest.mark.parametrize("cls", ["gauss", "field", "white"])
+def test_small_grid_certified_all_classes(cls):
+    N, kappa = 16, 4
+    mu, nu = synth.make_measure(N, cls, 32, 0), synth.make_measure(N, cls, 32, 1)
+    for p in (1.0, 2.0):
+        W = O.wasserstein_exact(mu, nu, N, p)
+        for prec in ("mixed", "f64"):
+            r = api.bounds([T(mu)], [T(nu)], [(N, kappa, p)], ipf_sweeps=3, prec=prec)[0]
+            assert r["lb"] <= W <= r["ub_weighted"] and W <= r["ub_primal"], (p, prec, r, W)
+
+
+def test_kappa_one_zero_gap():
+    N = 8
+    mu, nu = synth.make_measure(N, "gauss", 33, 0), synth.make_measure(N, "gauss", 33, 1)
+    W = O.wasserstein_exact(mu, nu, N, 2.0)
+    r = api.bounds([T(mu)], [T(nu)], [(N, 1, 2.0)], ipf_sweeps=2, prec="f64")[0]
+    assert r["lb"] <= W <= r["ub_weighted"]
+    assert abs(r["lb"] - W) <= 1e-9 * W
+    assert abs(r["ub_weighted"] - W) <= 1e-6 * W
+    assert abs(r["ub_primal"] - W) <= 1e-6 * W
+
+
+@pytest.mark.parametrize("p", [1.0, 2.0])
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+def test_adjoint_kernel_fd(p, prec):
+    """The adjoint kernel's gradient vs central finite differences of the
+    oracle LB (h = 1e-6, FP64) along e_i - mu, for the same fixed coarse
+    potential (the oracle's)."""
+    N, kappa = 16, 4
+    mu, nu = synth.make_measure(N, "field", 34, 0), synth.make_measure(N, "field", 34, 1)
+    mt, nt = O.sumpool(mu, N, kappa), O.sumpool(nu, N, kappa)
+    _, f_c, _, _ = O.exact_ot(O.coarse_cost_centre(N, kappa, p), mt, nt)
+    r = api.dual_upscale_ctransform(T(mu), T(nu), N, kappa, p, f_c, prec=prec)
+    grad = api.lb_adjoint(r["f"], T(mu), N, p, r["lb_p"]).cpu().numpy()
+    ref = O.lb_dual(mu, nu, N, kappa, p, f_c=f_c)
+    h = 1e-6
+    for i in np.random.default_rng(5).choice(N * N, 20, replace=False):
+        e = np.zeros(N * N); e[i] = 1.0
+        lp = O.lb_from_potential((mu + h * e) / (1 + h), nu, N, kappa, p, ref["f_coarse"])["lb"]
+        lm = O.lb_from_potential((mu - h * e) / (1 - h), nu, N, kappa, p, ref["f_coarse"])["lb"]
+        fd = (lp - lm) / (2 * h)
+        assert grad[i] == pytest.approx(fd, rel=1e-3 if prec == "mixed" else 1e-5, abs=1e-6)
+
+
+def test_lower_bound_autograd():
+    """LowerBound.apply: forward equals the batch LB; backward is the adjoint of
+    its own potential; finite differences through the whole method (coarse
+    re-solve included) agree wherever the coarse basis does not change."""
+    N, kappa, p = 16, 4, 2.0
+    mu, nu = synth.make_measure(N, "field", 35, 0), synth.make_measure(N, "field", 35, 1)
+    mu_t = T(mu).requires_grad_(True)
+    lb = api.LowerBound.apply(mu_t, T(nu), N, kappa, p, "f64")
+    r = api.bounds([T(mu)], [T(nu)], [(N, kappa, p)], ipf_sweeps=1, prec="f64")[0]
+    assert float(lb) == r["lb"]
+    lb.backward()
+    grad = mu_t.grad.cpu().numpy()
+    assert np.isfinite(grad).all() and abs(float(grad @ mu)) <= 1e-9 * np.abs(grad).max()
+    h = 1e-6
+    agree = 0
+    picks = np.random.default_rng(6).choice(N * N, 10, replace=False)
+    for i in picks:
+        e = np.zeros(N * N); e[i] = 1.0
+        lp = float(api.LowerBound.apply(T((mu + h * e) / (1 + h)), T(nu), N, kappa, p, "f64"))
+        lm = float(api.LowerBound.apply(T((mu - h * e) / (1 - h)), T(nu), N, kappa, p, "f64"))
+        agree += abs((lp - lm) / (2 * h) - grad[i]) <= 1e-4 * (1 + abs(grad[i]))
+    assert agree >= 8, agree
