@@ -44,11 +44,11 @@ WORKLOAD = ("180 pairs (4 value classes x 45 pairs) of 128x128 measures, p=2, ka
             "(32x32 coarse), FP32 cost/IPF(50 sweeps)/c-transform, FP64 bound sums")
 
 
-def _workload_arrays(rank: int):
+def _workload_arrays(rank: int, per_class: int = 45):
     from paper_2506_00976_gb300 import synth
     mus, nus = [], []
     for ci, cls in enumerate(CLASSES):
-        for mu, nu in synth.class_pairs(N, cls, workload=2 + 100 * rank, count=10):
+        for mu, nu in synth.class_pairs(N, cls, workload=2 + 100 * rank, count=10)[:per_class]:
             mus.append(mu)
             nus.append(nu)
     return mus, nus
@@ -156,7 +156,7 @@ def run_gpu(args):
         if world > 1:
             dist.barrier()
 
-    mus_h, nus_h = _workload_arrays(rank)
+    mus_h, nus_h = _workload_arrays(rank, args.pairs_per_class)
     n = len(mus_h)
     m = N * N
     host = torch.empty((n, 2, m), dtype=torch.float64).pin_memory()
@@ -210,7 +210,7 @@ def run_gpu(args):
     with ClockSampler(local) as clk:
         times_b, kern, launches = timed(True, args.steps, args.warmup, per_kernel=True)
     clocks = clk.summary()
-    times_p, _, _ = timed(False, max(1, min(args.steps, 5)), 1)
+    times_p = timed(False, max(1, min(args.steps, 5)), 1)[0] if not args.skip_plain else [float("nan")]
 
     ms_b = statistics.mean(times_b)
     ms_p = statistics.mean(times_p)
@@ -223,8 +223,8 @@ def run_gpu(args):
     plain_value = n * world / (ms_p_max * 1e-3)
 
     # e2e: whole method through the public API with host buffers
-    e2e_steps = max(1, min(args.steps, args.e2e_steps))
-    res_h = None
+    e2e_steps = max(1, min(args.steps, args.e2e_steps)) if not args.skip_e2e else 0
+    res_h = results
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
@@ -236,7 +236,7 @@ def run_gpu(args):
         res_h = batch.results()
     torch.cuda.synchronize()
     barrier()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = (time.perf_counter() - t0) / max(1, e2e_steps) if e2e_steps else float("nan")
     if world > 1:
         tt = torch.tensor([e2e_s], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -411,6 +411,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--cpu-workers", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--pairs-per-class", type=int, default=45,
+                    help="pairs per value class (45 = the full workload; smaller for profiling)")
+    ap.add_argument("--skip-plain", action="store_true", help="time only the batched form")
+    ap.add_argument("--skip-e2e", action="store_true", help="skip the end-to-end timing")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "native":
         args.warmup = 3

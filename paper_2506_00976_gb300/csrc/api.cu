@@ -163,9 +163,9 @@ static PlanLayout plan_layout(int M, int cap_nnz = 0) {
     return L;
 }
 
-static CtConfig pick_ct_config(int N_min, bool all_p2) {
+static CtConfig pick_ct_config(int N_gcd, bool all_p2) {
     CtConfig c;
-    c.R = ct_pick_r(N_min, 8);
+    c.R = ct_pick_r(N_gcd, 16);
     c.TC = c.R;
     c.threads = 256;
     c.p2 = all_p2;
@@ -208,9 +208,9 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         b->M_max = std::max(b->M_max, M);
         b->kappa_code = std::max(b->kappa_code, kap);
         pair_off[t] = off;
-        off += align_up(4 * sizeof(double) * M);
+        off += align_up(10 * sizeof(double) * M);
         off += align_up(sizeof(double) * (size_t)M * M);
-        off += 5 * align_up(tsz * m);
+        off += 7 * align_up(tsz * m);
     }
     if (!(same_kap && (kap0 == 1 || kap0 == 2 || kap0 == 4))) b->kappa_code = -b->kappa_code;
     // descriptors and item lists
@@ -232,13 +232,14 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         for (int i = 0; i < m; i += 256) pix.push_back({t, i});
         b->pix_cnt.push_back((int)pix.size() - b->pix_off.back());
         b->cbar_off.push_back((int)cb.size());
-        for (int k1 = 0; k1 < nn; ++k1)
-            for (int l1 = 0; l1 < nn; ++l1) cb.push_back({t, k1, l1, 0});
+        for (int w1 = 0; w1 < nn; ++w1)
+            for (int seg = 0; seg * CBAR_S < nn; ++seg) cb.push_back({t, w1, seg, 0});
         b->cbar_cnt.push_back((int)cb.size() - b->cbar_off.back());
         const int tiles = (m + tile_out - 1) / tile_out;
-        // batched form: about 6 items per SM over the whole batch
-        const long target_b = std::max<long>(1, (long)6 * sm * tiles / std::max<long>(1, total_tiles));
-        const int rows_b = pick_in_rows(N, tiles, (int)std::min<long>(target_b * 1, 1 << 20));
+        // batched form: about 12 items per SM over the whole batch (six waves
+        // of the persistent grid), each pair split evenly
+        const long splits_b = std::max<long>(1, (12L * sm + total_tiles - 1) / std::max<long>(1, total_tiles));
+        const int rows_b = pick_in_rows(N, 1, (int)std::min<long>(splits_b, N));
         for (int o = 0; o < m; o += tile_out)
             for (int r0 = 0; r0 < N; r0 += rows_b) ctb.push_back({t, o, r0, std::min(rows_b, N - r0)});
         // plain form: one pair fills the GPU, about 2 items per SM
@@ -299,13 +300,18 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         std::memset(&P, 0, sizeof(P));
         P.N = N; P.kappa = kap; P.n = nn; P.M = M; P.p = probs[t].p;
         P.mu_c = (double*)base; P.nu_c = P.mu_c + M; P.mu_c_lo = P.nu_c + M; P.nu_c_lo = P.mu_c_lo + M;
-        base += align_up(4 * sizeof(double) * M);
+        P.mu_rinv = P.nu_c_lo + M; P.nu_rinv = P.mu_rinv + M;
+        P.mu_rinv32 = (float*)(P.nu_rinv + M); P.nu_rinv32 = P.mu_rinv32 + M;
+        P.mu_c_hi = (double*)(P.nu_rinv32 + M); P.nu_c_hi = P.mu_c_hi + M;
+        base += align_up(10 * sizeof(double) * M);
         P.cbar = (double*)base; base += align_up(sizeof(double) * (size_t)M * M);
         P.fhat = base; base += align_up(tsz * m);
         P.g = base; base += align_up(tsz * m);
         P.f = base; base += align_up(tsz * m);
         P.a = base; base += align_up(tsz * m);
         P.b = base; base += align_up(tsz * m);
+        P.mu_t = base; base += align_up(tsz * m);
+        P.nu_t = base; base += align_up(tsz * m);
         const void *lo, *hi;
         int st = ctx_table(ctx, N, probs[t].p, b->f64, s0, &lo, &hi);
         if (st) { batch_free(b); return st; }

@@ -63,19 +63,24 @@ __global__ void prepare_kernel(const PairDev* __restrict__ pairs, PairOut* __res
     if (k < P.M) {
         const int N = P.N, kap = P.kappa, n = P.n;
         const int k1 = k / n, k2 = k % n;
-        double mu_rn = 0.0, mu_rd = 0.0, nu_rn = 0.0, nu_rd = 0.0;
+        double mu_rn = 0.0, mu_rd = 0.0, nu_rn = 0.0, nu_rd = 0.0, mu_ru = 0.0, nu_ru = 0.0;
         for (int t1 = 0; t1 < kap; ++t1) {
             const int row = (k1 * kap + t1) * N + k2 * kap;
             for (int t2 = 0; t2 < kap; ++t2) {
                 const double x = P.mu[row + t2], y = P.nu[row + t2];
                 bad_mu |= !(x >= 0.0) || !isfinite(x);
                 bad_nu |= !(y >= 0.0) || !isfinite(y);
-                mu_rn += x; mu_rd = __dadd_rd(mu_rd, x);
-                nu_rn += y; nu_rd = __dadd_rd(nu_rd, y);
+                mu_rn += x; mu_rd = __dadd_rd(mu_rd, x); mu_ru = __dadd_ru(mu_ru, x);
+                nu_rn += y; nu_rd = __dadd_rd(nu_rd, y); nu_ru = __dadd_ru(nu_ru, y);
             }
         }
-        P.mu_c[k] = mu_rn; P.mu_c_lo[k] = mu_rd;
-        P.nu_c[k] = nu_rn; P.nu_c_lo[k] = nu_rd;
+        P.mu_c[k] = mu_rn; P.mu_c_lo[k] = mu_rd; P.mu_c_hi[k] = mu_ru;
+        P.nu_c[k] = nu_rn; P.nu_c_lo[k] = nu_rd; P.nu_c_hi[k] = nu_ru;
+        // upper bounds of 1 / mu~_k for C-bar (0: zero mass, or too small for FP32)
+        P.mu_rinv[k] = mu_rd > 0.0 ? __drcp_ru(mu_rd) : 0.0;
+        P.nu_rinv[k] = nu_rd > 0.0 ? __drcp_ru(nu_rd) : 0.0;
+        P.mu_rinv32[k] = mu_rd >= 1e-30 ? __frcp_ru(__double2float_rd(mu_rd)) : 0.0f;
+        P.nu_rinv32[k] = nu_rd >= 1e-30 ? __frcp_ru(__double2float_rd(nu_rd)) : 0.0f;
         smu = mu_rn; snu = nu_rn;
     }
     // block reduction of the masses, one atomic per block
@@ -114,75 +119,91 @@ int launch_prepare(const PairDev* pairs_d, PairOut* outs_d, const PixItem* items
 // --------------------------------------------------------------------------
 // cbar: C-bar_kl = [sum_{x in X_k} mu(x) sum_{y in Y_l} nu(y) rho(x,y)^p] /
 //                  (mu~_k nu~_l)                       (Sec. 3.2; Alg. 3)
-// One CTA per (pair, source block row k1, target block row l1).  The CTA
-// stages the kappa fine rows of mu and nu and the 2*kappa-1 cost-table rows
-// it needs in shared memory.  A thread takes up to TSEG block pairs on one
-// diagonal (same block offset, hence the same (2kappa-1)^2 cost window, held
-// in registers).  All products and sums are rounded upward, so the result
-// bounds the real C-bar from above.
+//
+// Every fine pixel pair of every block pair contributes one fused multiply-
+// add.  Work item = (pair, wrapped block-row diagonal w1, segment): the
+// CBAR_S block-row pairs (k1, l1 = (k1 - w1) mod n), k1 = seg*S + s.  Inside a
+// block-row pair the n*n block pairs (k2, l2) are walked by wrapped column
+// diagonal (slot b: w2 = b / n, k2 = b % n, l2 = (k2 - w2) mod n), so every
+// warp gets full, equal work and a thread's block offset (k - l) takes at most
+// two values; its (2kappa-1)^2 cost window is held in registers across the S
+// block rows.  The staged mu, nu rows and cost-table rows live in shared
+// memory; results are staged too and stored as contiguous row segments.
+// All products and sums round upward and the division by mu~_k nu~_l is a
+// multiplication by upward-rounded reciprocals, so C-bar is bounded from
+// above.  A zero-mass block pair gets the unweighted mean of the cost.
 // --------------------------------------------------------------------------
-constexpr int CBAR_TSEG = 4;
 constexpr int CBAR_THREADS = 256;
+
+template <typename T>
+__device__ __forceinline__ double cbar_special(const PairDev& P, int k, int l, double num,
+                                               double mean_up) {
+    if (P.mu_c_lo[k] > 0.0 && P.nu_c_lo[l] > 0.0)
+        return __dmul_ru(__dmul_ru(num, P.mu_rinv[k]), P.nu_rinv[l]);
+    return mean_up;
+}
 
 template <typename T, int KAP>
 __global__ void __launch_bounds__(CBAR_THREADS)
-cbar_kernel(const PairDev* __restrict__ pairs, const CbarItem* __restrict__ items, int n_items,
-            int stage_n) {
+cbar_kernel(const PairDev* __restrict__ pairs, const CbarItem* __restrict__ items, int n_items) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const CbarItem I = items[it];
         const PairDev& P = pairs[I.pair];
         const int N = P.N, n = P.n, M = P.M;
         const int kap = KAP > 0 ? KAP : P.kappa;
-        T* mu_s = reinterpret_cast<T*>(smem_raw);
-        T* nu_s = mu_s + kap * N;
-        T* c_s = nu_s + kap * N;
-        double* out_s = reinterpret_cast<double*>(
-            smem_raw + ((sizeof(T) * (size_t)(4 * kap - 1) * N + 15) / 16) * 16);
-        const bool stage = (n <= stage_n);
+        const int W = 2 * kap - 1;
+        const int k1_0 = I.seg * CBAR_S;
+        const int S = min(CBAR_S, n - k1_0);
+        T* mu_s = reinterpret_cast<T*>(smem_raw);         // [S][kap][N]
+        T* nu_s = mu_s + CBAR_S * kap * N;                 // [S][kap][N]
+        T* c_s = nu_s + CBAR_S * kap * N;                  // [2][W][N]: block-row offsets w1, w1 - n
+        T* out_s = c_s + 2 * W * N;                        // [S][n][n]
         const T* tab = reinterpret_cast<const T*>(P.ctab_hi);
-        const int D1 = kap * (I.k1 - I.l1);
-        for (int idx = threadIdx.x; idx < kap * N; idx += blockDim.x) {
-            const int r = idx / N, c = idx % N;
-            mu_s[idx] = from_double_ru<T>(P.mu[(I.k1 * kap + r) * N + c]);
-            nu_s[idx] = from_double_ru<T>(P.nu[(I.l1 * kap + r) * N + c]);
+        for (int idx = threadIdx.x; idx < S * kap * N; idx += blockDim.x) {
+            const int s = idx / (kap * N), r = (idx / N) % kap, c = idx % N;
+            const int k1 = k1_0 + s, l1 = (k1 - I.w1 + n) % n;
+            mu_s[idx] = from_double_ru<T>(P.mu[(k1 * kap + r) * N + c]);
+            nu_s[idx] = from_double_ru<T>(P.nu[(l1 * kap + r) * N + c]);
         }
-        for (int idx = threadIdx.x; idx < (2 * kap - 1) * N; idx += blockDim.x) {
-            const int d = idx / N, c = idx % N;
-            c_s[idx] = tab[abs(D1 + d - (kap - 1)) * N + c];
+        for (int idx = threadIdx.x; idx < 2 * W * N; idx += blockDim.x) {
+            const int v = idx / (W * N), d = (idx / N) % W, c = idx % N;
+            const int row = abs(kap * (v == 0 ? I.w1 : I.w1 - n) + d - (kap - 1));
+            c_s[idx] = row < N ? tab[row * N + c] : T(0);   // rows >= N belong to unused offsets
         }
         __syncthreads();
 
-        const int nseg = (n + CBAR_TSEG - 1) / CBAR_TSEG;
-        const int n_work = (2 * n - 1) * nseg;
-        for (int w = threadIdx.x; w < n_work; w += blockDim.x) {
-            const int d = w / nseg, s = w % nseg;
-            const int D2 = d - (n - 1);            // k2 - l2
-            const int k2_0 = max(0, D2) + s * CBAR_TSEG;
-            const int k2_end = min(n, n + D2);
-            if (k2_0 >= k2_end) continue;
-            const int cnt = min(CBAR_TSEG, k2_end - k2_0);
+        for (int b = threadIdx.x; b < n * n; b += blockDim.x) {
+            const int w2 = b / n, k2 = b % n, l2 = (k2 - w2 + n) % n;
+            const int D2 = k2 - l2;
             if constexpr (KAP > 0) {
-                constexpr int W = 2 * KAP - 1;
-                T cw[W][W];
+                constexpr int WK = 2 * KAP - 1;
+                T cw[WK][WK];
+                int cur_v = -1;
+                for (int s = 0; s < S; ++s) {
+                    const int k1 = k1_0 + s;
+                    const int v = k1 >= I.w1 ? 0 : 1;          // block-row offset w1 or w1 - n
+                    if (v != cur_v) {
+                        const T* cv = c_s + v * WK * N;
 #pragma unroll
-                for (int d1 = 0; d1 < W; ++d1)
+                        for (int d1 = 0; d1 < WK; ++d1)
 #pragma unroll
-                    for (int d2 = 0; d2 < W; ++d2)
-                        cw[d1][d2] = c_s[d1 * N + abs(KAP * D2 + d2 - (KAP - 1))];
-                for (int t = 0; t < cnt; ++t) {
-                    const int k2 = k2_0 + t, l2 = k2 - D2;
+                            for (int d2 = 0; d2 < WK; ++d2)
+                                cw[d1][d2] = cv[d1 * N + abs(KAP * D2 + d2 - (KAP - 1))];
+                        cur_v = v;
+                    }
                     T nb[KAP][KAP];
 #pragma unroll
                     for (int b1 = 0; b1 < KAP; ++b1)
 #pragma unroll
-                        for (int b2 = 0; b2 < KAP; ++b2) nb[b1][b2] = nu_s[b1 * N + l2 * KAP + b2];
+                        for (int b2 = 0; b2 < KAP; ++b2)
+                            nb[b1][b2] = nu_s[(s * KAP + b1) * N + l2 * KAP + b2];
                     T acc = T(0);
 #pragma unroll
                     for (int a1 = 0; a1 < KAP; ++a1)
 #pragma unroll
                         for (int a2 = 0; a2 < KAP; ++a2) {
-                            const T mv = mu_s[a1 * N + k2 * KAP + a2];
+                            const T mv = mu_s[(s * KAP + a1) * N + k2 * KAP + a2];
                             T inner = T(0);
 #pragma unroll
                             for (int b1 = 0; b1 < KAP; ++b1)
@@ -191,83 +212,110 @@ cbar_kernel(const PairDev* __restrict__ pairs, const CbarItem* __restrict__ item
                                     inner = fma_ru(nb[b1][b2], cw[a1 - b1 + KAP - 1][a2 - b2 + KAP - 1], inner);
                             acc = fma_ru(mv, inner, acc);
                         }
-                    const double num = (double)acc;
-                    if (stage) out_s[k2 * n + l2] = num;
-                    else {
-                        const int k = I.k1 * n + k2, l = I.l1 * n + l2;
-                        const double den = __dmul_rd(P.mu_c_lo[k], P.nu_c_lo[l]);
-                        P.cbar[(size_t)k * M + l] = den > 0.0 ? __ddiv_ru(num, den) : -1.0;
+                    const int l1 = (k1 - I.w1 + n) % n;
+                    const int k = k1 * n + k2, l = l1 * n + l2;
+                    T outv;
+                    bool ok;
+                    if constexpr (sizeof(T) == 4) {
+                        const float rk = P.mu_rinv32[k], rl = P.nu_rinv32[l];
+                        ok = rk > 0.f && rl > 0.f;
+                        outv = ok ? __fmul_ru(__fmul_ru(acc, rk), rl) : T(0);
+                    } else {
+                        const double rk = P.mu_rinv[k], rl = P.nu_rinv[l];
+                        ok = rk > 0.0 && rl > 0.0;
+                        outv = ok ? __dmul_ru(__dmul_ru(acc, rk), rl) : T(0);
                     }
+                    if (!ok) {
+                        double mean = 0.0;
+#pragma unroll
+                        for (int d1 = 0; d1 < WK; ++d1)
+#pragma unroll
+                            for (int d2 = 0; d2 < WK; ++d2)
+                                mean = __fma_ru((double)((KAP - abs(d1 - (KAP - 1))) * (KAP - abs(d2 - (KAP - 1)))),
+                                                (double)cw[d1][d2], mean);
+                        mean = __ddiv_ru(mean, (double)(KAP * KAP * KAP * KAP));
+                        P.cbar[(size_t)k * M + l] = cbar_special<T>(P, k, l, (double)acc, mean);
+                        outv = __int_as_float(0x7fc00000);        // NaN: already written
+                    }
+                    out_s[(s * n + k2) * n + l2] = outv;
                 }
             } else {
-                for (int t = 0; t < cnt; ++t) {
-                    const int k2 = k2_0 + t, l2 = k2 - D2;
+                for (int s = 0; s < S; ++s) {
+                    const int k1 = k1_0 + s;
+                    const int v = k1 >= I.w1 ? 0 : 1;
+                    const T* cv = c_s + v * W * N;
                     T acc = T(0);
+                    double mean = 0.0;
                     for (int a1 = 0; a1 < kap; ++a1)
                         for (int a2 = 0; a2 < kap; ++a2) {
-                            const T mv = mu_s[a1 * N + k2 * kap + a2];
+                            const T mv = mu_s[(s * kap + a1) * N + k2 * kap + a2];
                             T inner = T(0);
                             for (int b1 = 0; b1 < kap; ++b1) {
-                                const T* crow = c_s + (a1 - b1 + kap - 1) * N;
+                                const T* crow = cv + (a1 - b1 + kap - 1) * N;
                                 for (int b2 = 0; b2 < kap; ++b2)
-                                    inner = fma_ru(nu_s[b1 * N + l2 * kap + b2],
+                                    inner = fma_ru(nu_s[(s * kap + b1) * N + l2 * kap + b2],
                                                    crow[abs(kap * D2 + a2 - b2)], inner);
                             }
                             acc = fma_ru(mv, inner, acc);
                         }
-                    const double num = (double)acc;
-                    if (stage) out_s[k2 * n + l2] = num;
-                    else {
-                        const int k = I.k1 * n + k2, l = I.l1 * n + l2;
-                        const double den = __dmul_rd(P.mu_c_lo[k], P.nu_c_lo[l]);
-                        P.cbar[(size_t)k * M + l] = den > 0.0 ? __ddiv_ru(num, den) : -1.0;
+                    const int l1 = (k1 - I.w1 + n) % n;
+                    const int k = k1 * n + k2, l = l1 * n + l2;
+                    T outv;
+                    bool ok;
+                    if constexpr (sizeof(T) == 4) {
+                        const float rk = P.mu_rinv32[k], rl = P.nu_rinv32[l];
+                        ok = rk > 0.f && rl > 0.f;
+                        outv = ok ? __fmul_ru(__fmul_ru(acc, rk), rl) : T(0);
+                    } else {
+                        const double rk = P.mu_rinv[k], rl = P.nu_rinv[l];
+                        ok = rk > 0.0 && rl > 0.0;
+                        outv = ok ? __dmul_ru(__dmul_ru(acc, rk), rl) : T(0);
                     }
+                    if (!ok) {
+                        for (int a1 = 0; a1 < kap; ++a1)
+                            for (int b1 = 0; b1 < kap; ++b1)
+                                for (int a2 = 0; a2 < kap; ++a2)
+                                    for (int b2 = 0; b2 < kap; ++b2)
+                                        mean = __dadd_ru(mean, (double)cv[(a1 - b1 + kap - 1) * N +
+                                                                          abs(kap * D2 + a2 - b2)]);
+                        mean = __ddiv_ru(mean, (double)kap * kap * kap * kap);
+                        P.cbar[(size_t)k * M + l] = cbar_special<T>(P, k, l, (double)acc, mean);
+                        outv = sizeof(T) == 4 ? (T)__int_as_float(0x7fc00000) : (T)__longlong_as_double(0x7ff8000000000000LL);
+                    }
+                    out_s[(s * n + k2) * n + l2] = outv;
                 }
             }
         }
         __syncthreads();
-        // epilogue: divide by the coarse masses; zero-mass entries get the
-        // unweighted mean of the cost over the block pair
-        const double k4 = (double)kap * kap * kap * kap;
-        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-            const int k2 = idx / n, l2 = idx % n;
-            const int k = I.k1 * n + k2, l = I.l1 * n + l2;
-            const double den = __dmul_rd(P.mu_c_lo[k], P.nu_c_lo[l]);
-            double val;
-            if (den > 0.0) {
-                if (!stage) continue;
-                val = __ddiv_ru(out_s[idx], den);
-            } else {
-                const int D2 = k2 - l2;
-                double s = 0.0;
-                for (int a1 = 0; a1 < kap; ++a1)
-                    for (int b1 = 0; b1 < kap; ++b1)
-                        for (int a2 = 0; a2 < kap; ++a2)
-                            for (int b2 = 0; b2 < kap; ++b2)
-                                s = __dadd_ru(s, (double)c_s[(a1 - b1 + kap - 1) * N +
-                                                           abs(kap * D2 + a2 - b2)]);
-                val = __ddiv_ru(s, k4);
+        for (int idx = threadIdx.x; idx < S * n * n; idx += blockDim.x) {
+            const int s = idx / (n * n), k2 = (idx / n) % n, l2 = idx % n;
+            const T v = out_s[idx];
+            if (v == v) {                                          // NaN marks a direct write
+                const int k1 = k1_0 + s, l1 = (k1 - I.w1 + n) % n;
+                P.cbar[(size_t)(k1 * n + k2) * M + l1 * n + l2] = (double)v;
             }
-            P.cbar[(size_t)k * M + l] = val;
         }
         __syncthreads();
     }
 }
 
+static size_t cbar_smem(size_t tsz, int kap, int n, int N) {
+    return tsz * ((size_t)2 * CBAR_S * kap * N + (size_t)2 * (2 * kap - 1) * N + (size_t)CBAR_S * n * n);
+}
+
 template <typename T>
-static int cbar_dispatch(const PairDev* pairs_d, const CbarItem* items, int n_items, int kappa_max,
+static int cbar_dispatch(const PairDev* pairs_d, const CbarItem* items, int n_items, int kappa_code,
                          int n_max, int N_max, cudaStream_t stream) {
-    const int stage_n = 64;
-    size_t smem = ((sizeof(T) * (size_t)(4 * kappa_max - 1) * N_max + 15) / 16) * 16;
-    if (n_max <= stage_n) smem += sizeof(double) * (size_t)n_max * n_max;
+    const int kmax = kappa_code > 0 ? kappa_code : -kappa_code;
+    const size_t smem = cbar_smem(sizeof(T), kmax, n_max, N_max);
     if (smem > 227 * 1024) return QWB_ERR_UNSUPPORTED;
     auto run = [&](auto kern) -> int {
         QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<n_items, CBAR_THREADS, smem, stream>>>(pairs_d, items, n_items, stage_n);
+        kern<<<n_items, CBAR_THREADS, smem, stream>>>(pairs_d, items, n_items);
         QWB_LAUNCHED();
         return QWB_OK;
     };
-    switch (kappa_max) {   // kappa_max is the common kappa when all pairs share it
+    switch (kappa_code) {   // positive: every pair of the launch has this kappa
         case 1: return run(cbar_kernel<T, 1>);
         case 2: return run(cbar_kernel<T, 2>);
         case 4: return run(cbar_kernel<T, 4>);
@@ -279,12 +327,9 @@ int launch_cbar(const PairDev* pairs_d, const CbarItem* items, int n_items, int 
                 int n_max, int N_max, bool f64, cudaStream_t stream) {
     if (n_items <= 0) return QWB_OK;
     // kappa_code: the common kappa (1, 2, 4 use unrolled kernels) or -K for a
-    // mixed batch whose largest kappa is K (runtime-kappa kernel)
-    const int kmax = kappa_code > 0 ? kappa_code : -kappa_code;
-    const int kc = kappa_code > 0 ? kappa_code : 0;
-    (void)kmax;
-    if (f64) return cbar_dispatch<double>(pairs_d, items, n_items, kc == 0 ? kmax : kc, n_max, N_max, stream) ;
-    return cbar_dispatch<float>(pairs_d, items, n_items, kc == 0 ? kmax : kc, n_max, N_max, stream);
+    // launch whose pairs differ in kappa or use another kappa (largest K)
+    if (f64) return cbar_dispatch<double>(pairs_d, items, n_items, kappa_code, n_max, N_max, stream);
+    return cbar_dispatch<float>(pairs_d, items, n_items, kappa_code, n_max, N_max, stream);
 }
 
 // --------------------------------------------------------------------------
@@ -299,7 +344,7 @@ int launch_cbar(const PairDev* pairs_d, const CbarItem* items, int n_items, int 
 //   plan; its marginals, cost and TV corrections are bounded with interval
 //   (directed) arithmetic.
 // --------------------------------------------------------------------------
-constexpr int PRIMAL_THREADS = 512;
+constexpr int PRIMAL_THREADS = 256;
 
 __device__ __forceinline__ double block_reduce_ru(double v, double* red) {
     for (int o = 16; o > 0; o >>= 1) v = __dadd_ru(v, __shfl_down_sync(0xffffffffu, v, o));
@@ -355,7 +400,7 @@ __device__ __forceinline__ double root_p_rd(double x, double p) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(PRIMAL_THREADS, 1)
+__global__ void __launch_bounds__(PRIMAL_THREADS, 2)
 primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
               const int* __restrict__ pair_ids) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -374,45 +419,55 @@ primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
     const T kk = (T)(kap * kap);
 
     // ---- fine sweeps ------------------------------------------------------
+    T* mu_t = reinterpret_cast<T*>(P.mu_t);
+    T* nu_t = reinterpret_cast<T*>(P.nu_t);
+    for (int i = threadIdx.x; i < N * N; i += blockDim.x) {      // one conversion per call
+        mu_t[i] = (T)P.mu[i];
+        nu_t[i] = (T)P.nu[i];
+    }
     for (int l = threadIdx.x; l < M; l += blockDim.x) Bt[l] = kk;    // b = 1
     __syncthreads();
+    const bool vec4 = (sizeof(T) == 4) && (kap == 4);              // block rows are one float4
     for (int sweep = 0; sweep < P.sweeps; ++sweep) {
-        for (int k = threadIdx.x; k < M; k += blockDim.x) {
-            T r = T(0);
-            for (int e = P.rowptr[k]; e < P.rowptr[k + 1]; ++e) r += (T)P.val[e] * Bt[P.colidx[e]];
-            r *= kinv4;
-            const T inv = r > T(0) ? T(1) / r : T(0);
-            const int k1 = k / n, k2 = k % n;
-            T s = T(0);
-            for (int t1 = 0; t1 < kap; ++t1) {
-                const int base = (k1 * kap + t1) * N + k2 * kap;
-                for (int t2 = 0; t2 < kap; ++t2) {
-                    const T v = (T)P.mu[base + t2] * inv;
-                    a[base + t2] = v;
-                    s += v;
+        for (int half = 0; half < 2; ++half) {
+            // half 0: a = mu / (pi-hat b), A = block sums of a
+            // half 1: b = nu / (pi-hat^T a), B = block sums of b
+            const int* ptr = half == 0 ? P.rowptr : P.colptr;
+            const int* idx = half == 0 ? P.colidx : P.rowidx;
+            const double* val = half == 0 ? P.val : P.valc;
+            const T* src = half == 0 ? mu_t : nu_t;
+            T* dst = half == 0 ? a : b;
+            const T* other = half == 0 ? Bt : At;
+            T* mine = half == 0 ? At : Bt;
+            for (int k = threadIdx.x; k < M; k += blockDim.x) {
+                T r = T(0);
+                for (int e = ptr[k]; e < ptr[k + 1]; ++e) r += (T)val[e] * other[idx[e]];
+                r *= kinv4;
+                const T inv = r > T(0) ? T(1) / r : T(0);
+                const int k1 = k / n, k2 = k % n;
+                T s = T(0);
+                if (vec4) {
+                    for (int t1 = 0; t1 < 4; ++t1) {
+                        const int base = (k1 * 4 + t1) * N + k2 * 4;
+                        float4 v = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(src) + base);
+                        v.x *= (float)inv; v.y *= (float)inv; v.z *= (float)inv; v.w *= (float)inv;
+                        *reinterpret_cast<float4*>(reinterpret_cast<float*>(dst) + base) = v;
+                        s += (T)((v.x + v.y) + (v.z + v.w));
+                    }
+                } else {
+                    for (int t1 = 0; t1 < kap; ++t1) {
+                        const int base = (k1 * kap + t1) * N + k2 * kap;
+                        for (int t2 = 0; t2 < kap; ++t2) {
+                            const T v = src[base + t2] * inv;
+                            dst[base + t2] = v;
+                            s += v;
+                        }
+                    }
                 }
+                mine[k] = s;
             }
-            At[k] = s;
+            __syncthreads();
         }
-        __syncthreads();
-        for (int l = threadIdx.x; l < M; l += blockDim.x) {
-            T r = T(0);
-            for (int e = P.colptr[l]; e < P.colptr[l + 1]; ++e) r += (T)P.valc[e] * At[P.rowidx[e]];
-            r *= kinv4;
-            const T inv = r > T(0) ? T(1) / r : T(0);
-            const int l1 = l / n, l2 = l % n;
-            T s = T(0);
-            for (int t1 = 0; t1 < kap; ++t1) {
-                const int base = (l1 * kap + t1) * N + l2 * kap;
-                for (int t2 = 0; t2 < kap; ++t2) {
-                    const T v = (T)P.nu[base + t2] * inv;
-                    b[base + t2] = v;
-                    s += v;
-                }
-            }
-            Bt[l] = s;
-        }
-        __syncthreads();
     }
 
     // ---- FP64 sweeps on block scalars until the marginals are exact --------
@@ -493,15 +548,8 @@ primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
         double s_lo = 0.0, s_hi = 0.0;
         for (int e = P.rowptr[k]; e < P.rowptr[k + 1]; ++e) {
             const int l = P.colidx[e];
-            const int l1 = l / n, l2 = l % n;
-            double nl_lo = 0.0, nl_hi = 0.0;
-            for (int t1 = 0; t1 < kap; ++t1)
-                for (int t2 = 0; t2 < kap; ++t2) {
-                    const double y = P.nu[(l1 * kap + t1) * N + l2 * kap + t2];
-                    nl_lo = __dadd_rd(nl_lo, y); nl_hi = __dadd_ru(nl_hi, y);
-                }
-            s_lo = __fma_rd(__dmul_rd(P.val[e], beta[l]), nl_lo, s_lo);
-            s_hi = __fma_ru(__dmul_ru(P.val[e], beta[l]), nl_hi, s_hi);
+            s_lo = __fma_rd(__dmul_rd(P.val[e], beta[l]), P.nu_c_lo[l], s_lo);
+            s_hi = __fma_ru(__dmul_ru(P.val[e], beta[l]), P.nu_c_hi[l], s_hi);
         }
         const double rho_lo = __dmul_rd(__dmul_rd(alpha[k], kinv4_lo), s_lo);
         const double rho_hi = __dmul_ru(__dmul_ru(alpha[k], kinv4_hi), s_hi);
@@ -524,15 +572,8 @@ primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
         double s_lo = 0.0, s_hi = 0.0;
         for (int e = P.colptr[l]; e < P.colptr[l + 1]; ++e) {
             const int k = P.rowidx[e];
-            const int k1 = k / n, k2 = k % n;
-            double ml_lo = 0.0, ml_hi = 0.0;
-            for (int t1 = 0; t1 < kap; ++t1)
-                for (int t2 = 0; t2 < kap; ++t2) {
-                    const double x = P.mu[(k1 * kap + t1) * N + k2 * kap + t2];
-                    ml_lo = __dadd_rd(ml_lo, x); ml_hi = __dadd_ru(ml_hi, x);
-                }
-            s_lo = __fma_rd(__dmul_rd(P.valc[e], alpha[k]), ml_lo, s_lo);
-            s_hi = __fma_ru(__dmul_ru(P.valc[e], alpha[k]), ml_hi, s_hi);
+            s_lo = __fma_rd(__dmul_rd(P.valc[e], alpha[k]), P.mu_c_lo[k], s_lo);
+            s_hi = __fma_ru(__dmul_ru(P.valc[e], alpha[k]), P.mu_c_hi[k], s_hi);
         }
         const double sg_lo = __dmul_rd(__dmul_rd(beta[l], kinv4_lo), s_lo);
         const double sg_hi = __dmul_ru(__dmul_ru(beta[l], kinv4_hi), s_hi);
@@ -691,6 +732,15 @@ int launch_upsample(const PairDev* pairs_d, PairOut* outs_d, const PixItem* item
 // Items that cover only part of the inputs combine their partial minima with
 // an exact floating-point atomic min.
 // --------------------------------------------------------------------------
+// 3-input minimum: one instruction for two candidates in FP32 (PTX min with
+// three operands, sm_100 and later); FP64 uses two two-input minima.
+__device__ __forceinline__ float min3(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ double min3(double a, double b, double c) { return fmin(a, fmin(b, c)); }
+
 template <typename T, int R, int TC, bool P2>
 __global__ void __launch_bounds__(256)
 ctransform_kernel(const PairDev* __restrict__ pairs, const CtItem* __restrict__ items,
@@ -741,11 +791,20 @@ ctransform_kernel(const PairDev* __restrict__ pairs, const CtItem* __restrict__ 
                     const T* hrow = hs + r1 * N + c0;
 #pragma unroll
                     for (int s = 0; s < TC; ++s) fv[s] = hrow[s];
+                    if constexpr (TC % 2 == 0) {
 #pragma unroll
-                    for (int s = 0; s < TC; ++s)
+                        for (int s = 0; s < TC; s += 2)
 #pragma unroll
-                        for (int r = 0; r < R; ++r)
-                            mins[r] = fmin(mins[r], sub_rd(q[s - r + R - 1], fv[s]));
+                            for (int r = 0; r < R; ++r)
+                                mins[r] = min3(mins[r], sub_rd(q[s - r + R - 1], fv[s]),
+                                               sub_rd(q[s + 1 - r + R - 1], fv[s + 1]));
+                    } else {
+#pragma unroll
+                        for (int s = 0; s < TC; ++s)
+#pragma unroll
+                            for (int r = 0; r < R; ++r)
+                                mins[r] = fmin(mins[r], sub_rd(q[s - r + R - 1], fv[s]));
+                    }
                 }
             }
             if (I.in_rows < N) {      // partial minimum: combine across items
@@ -766,10 +825,10 @@ int ct_pick_r(int N, int want) {
     return 1;
 }
 
-template <typename T, int R, bool P2>
+template <typename T, int R, int TC, bool P2>
 static int ct_launch_rt(const PairDev* pairs_d, const CtItem* items, int n_items, int phase,
                         int threads, int in_rows, int N_max, int grid_cap, cudaStream_t stream) {
-    auto kern = ctransform_kernel<T, R, R, P2>;
+    auto kern = ctransform_kernel<T, R, TC, P2>;
     const size_t smem = sizeof(T) * (size_t)in_rows * N_max;
     if (smem > 227 * 1024) return QWB_ERR_UNSUPPORTED;
     QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -781,15 +840,14 @@ static int ct_launch_rt(const PairDev* pairs_d, const CtItem* items, int n_items
 
 template <typename T, bool P2>
 static int ct_launch_t(const PairDev* pairs_d, const CtItem* items, int n_items, int phase,
-                       const CtConfig& cfg, int N_max, int grid_cap, cudaStream_t stream) {
-    switch (cfg.R) {
-        case 1: return ct_launch_rt<T, 1, P2>(pairs_d, items, n_items, phase, cfg.threads, cfg.in_rows, N_max, grid_cap, stream);
-        case 2: return ct_launch_rt<T, 2, P2>(pairs_d, items, n_items, phase, cfg.threads, cfg.in_rows, N_max, grid_cap, stream);
-        case 4: return ct_launch_rt<T, 4, P2>(pairs_d, items, n_items, phase, cfg.threads, cfg.in_rows, N_max, grid_cap, stream);
-        case 8: return ct_launch_rt<T, 8, P2>(pairs_d, items, n_items, phase, cfg.threads, cfg.in_rows, N_max, grid_cap, stream);
-        case 16: return ct_launch_rt<T, 16, P2>(pairs_d, items, n_items, phase, cfg.threads, cfg.in_rows, N_max, grid_cap, stream);
-        default: return QWB_ERR_UNSUPPORTED;
-    }
+                       const CtConfig& c, int N_max, int grid_cap, cudaStream_t stream) {
+#define QWB_CT(RR, TT)                                                                     \
+    if (c.R == RR && c.TC == TT)                                                           \
+        return ct_launch_rt<T, RR, TT, P2>(pairs_d, items, n_items, phase, c.threads,      \
+                                           c.in_rows, N_max, grid_cap, stream);
+    QWB_CT(1, 1) QWB_CT(2, 2) QWB_CT(4, 4) QWB_CT(8, 8) QWB_CT(16, 8) QWB_CT(16, 16) QWB_CT(8, 16)
+#undef QWB_CT
+    return QWB_ERR_UNSUPPORTED;
 }
 
 int launch_ctransform(const PairDev* pairs_d, const CtItem* items, int n_items, int phase,

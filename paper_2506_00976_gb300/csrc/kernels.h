@@ -18,6 +18,13 @@ struct PairDev {
     double* nu_c;
     double* mu_c_lo;        // M coarse masses, round-down sums
     double* nu_c_lo;
+    double* mu_rinv;        // M upper bounds of 1 / mu~_k (0 where mu~_k = 0)
+    double* nu_rinv;
+    float* mu_rinv32;       // M FP32 upper bounds of 1 / mu~_k (0: use the FP64 path)
+    float* nu_rinv32;
+    double* mu_c_hi;        // M coarse masses, round-up sums
+    double* nu_c_hi;
+    void* mu_t; void* nu_t; // N*N copies of mu, nu in the pass type T (IPF sweeps)
     double* cbar;           // M*M coarse cost out (may be null)
     const void* ctab_lo;    // N*N cost table, lower brackets (T)
     const void* ctab_hi;    // N*N cost table, upper brackets (T)
@@ -44,7 +51,7 @@ struct PairOut {
     int sweeps_done, pad;
 };
 
-struct CbarItem { int pair, k1, l1, pad; };
+struct CbarItem { int pair, w1, seg, pad; };   // wrapped block-row diagonal w1, rows seg*S..
 struct CtItem { int pair, out0, in_row0, in_rows; };
 struct PixItem { int pair, start; };
 
@@ -61,6 +68,7 @@ struct CtConfig {
 int launch_cost_tables(int N, double p, bool f64, void* lo, void* hi, cudaStream_t stream);
 int launch_prepare(const PairDev* pairs_d, PairOut* outs_d, const PixItem* items, int n_items,
                    bool f64, cudaStream_t stream);
+constexpr int CBAR_S = 4;   // block rows per C-bar work item
 int launch_cbar(const PairDev* pairs_d, const CbarItem* items, int n_items, int kappa_max,
                 int n_max, int N_max, bool f64, cudaStream_t stream);
 int launch_primal(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs,

@@ -1,6 +1,6 @@
 """Summarise an ncu launch list (--metrics gpu__time_duration.sum --csv) per kernel.
 
-Usage: python profiles/summarize_launches.py launches.csv [skip_first_n]
+Usage: python -m paper_2506_00976_gb300.ncu_summary launches.csv [skip_first_n]
 Prints launches, total device time and share per kernel (cold-cache,
 serialised times: compare shares, not absolutes).
 """

@@ -1,0 +1,96 @@
+"""CPU checks of the C ABI: the library builds, loads without a GPU, exports
+every function include/qwb.h declares, and its host exact solver (network
+simplex) agrees with the oracle's successive-shortest-path solver."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import qwb_oracle as O
+from paper_2506_00976_gb300 import _lib, build, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _lib.load()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "qwb.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qwb_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 18
+    for name in names:
+        assert hasattr(lib, name), name
+    bound = {s[0] for s in _lib.SIGNATURES}
+    assert set(names) == bound, set(names) ^ bound
+
+
+def test_status_strings(lib):
+    assert lib.qwb_status_string(0) == b"QWB_OK"
+    assert lib.qwb_status_string(2) == b"QWB_ERR_MASS"
+
+
+def _solve(C, a, b):
+    from paper_2506_00976_gb300 import api
+    return api.coarse_solve(C, a, b)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_network_simplex_random_dense(lib, seed):
+    rng = np.random.default_rng(seed)
+    n, m = rng.integers(1, 60, size=2)
+    C = rng.random((n, m)) * 100
+    a = rng.random(n); a /= a.sum()
+    b = rng.random(m); b /= b.sum()
+    r = _solve(C, a, b)
+    _, _, _, obj = O.exact_ot(C, a, b)
+    assert r["obj"] == pytest.approx(obj, rel=1e-10, abs=1e-12)
+    assert len(r["val"]) <= n + m - 1
+    plan = np.zeros((n, m))
+    for i in range(n):
+        for e in range(r["rowptr"][i], r["rowptr"][i + 1]):
+            plan[i, r["col"][e]] += r["val"][e]
+    assert np.abs(plan.sum(1) - a).max() < 1e-13 and np.abs(plan.sum(0) - b).max() < 1e-13
+    assert (C - r["f"][:, None] - r["g"][None, :]).min() >= -1e-12 * C.max()
+    assert float(r["f"] @ a + r["g"] @ b) == pytest.approx(obj, rel=1e-9, abs=1e-12)
+
+
+@pytest.mark.parametrize("p", [1.0, 2.0])
+@pytest.mark.parametrize("cls", ["white", "gauss", "field"])
+def test_network_simplex_grid_costs(lib, p, cls):
+    """Degenerate grid costs (many ties): objective equals the oracle's."""
+    N, kappa = 32, 2
+    mu, nu = synth.make_measure(N, cls, 40, 0), synth.make_measure(N, cls, 40, 1)
+    C = O.coarse_cost_centre(N, kappa, p)
+    a, b = O.sumpool(mu, N, kappa), O.sumpool(nu, N, kappa)
+    r = _solve(C, a, b)
+    _, _, _, obj = O.exact_ot(C, a, b)
+    assert r["obj"] == pytest.approx(obj, rel=1e-10)
+    assert len(r["val"]) <= 2 * len(a) - 1
+    assert (C - r["f"][:, None] - r["g"][None, :]).min() >= -1e-10
+
+
+def test_network_simplex_zero_masses(lib):
+    rng = np.random.default_rng(9)
+    C = rng.random((20, 15))
+    a = rng.random(20); a[[0, 5, 7]] = 0; a /= a.sum()
+    b = rng.random(15); b[[3]] = 0; b /= b.sum()
+    r = _solve(C, a, b)
+    assert r["obj"] == pytest.approx(O.exact_ot(C, a, b)[3], rel=1e-10)
+
+
+def test_network_simplex_rejects_bad_input(lib):
+    from paper_2506_00976_gb300._lib import QwbError
+    with pytest.raises(QwbError, match="INVALID_ARG"):
+        _solve(-np.ones((2, 2)), np.array([0.5, 0.5]), np.array([0.5, 0.5]))
+    with pytest.raises(QwbError, match="INVALID_ARG"):
+        _solve(np.ones((2, 2)), np.array([np.nan, 1.0]), np.array([0.5, 0.5]))
