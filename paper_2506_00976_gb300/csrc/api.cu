@@ -146,7 +146,7 @@ static void batch_free(qwb_batch* b) {
 }
 
 struct PlanLayout {   // per-pair coarse plan region
-    size_t rowptr, col, val, colptr, rowidx, valc, fco, total;
+    size_t rowptr, col, val, colptr, rowidx, valc, val_t, valc_t, fco, total;
 };
 static PlanLayout plan_layout(int M, int cap_nnz = 0) {
     PlanLayout L;
@@ -158,9 +158,25 @@ static PlanLayout plan_layout(int M, int cap_nnz = 0) {
     L.colptr = o; o = align_up(o + sizeof(int) * (M + 1), 16);
     L.rowidx = o; o = align_up(o + sizeof(int) * cap, 16);
     L.valc = o; o = align_up(o + sizeof(double) * cap, 16);
+    L.val_t = o; o = align_up(o + sizeof(double) * cap, 16);    // room for either type
+    L.valc_t = o; o = align_up(o + sizeof(double) * cap, 16);
     L.fco = o; o = align_up(o + sizeof(double) * M, 256);
     L.total = o;
     return L;
+}
+
+// Plan values in the pass type, for the fine sweeps.
+static void stage_typed_values(char* ph, const PlanLayout& L, int nnz, bool f64) {
+    const double* v = (const double*)(ph + L.val);
+    const double* vc = (const double*)(ph + L.valc);
+    if (f64) {
+        std::memcpy(ph + L.val_t, v, sizeof(double) * nnz);
+        std::memcpy(ph + L.valc_t, vc, sizeof(double) * nnz);
+    } else {
+        float* vt = (float*)(ph + L.val_t);
+        float* vct = (float*)(ph + L.valc_t);
+        for (int e = 0; e < nnz; ++e) { vt[e] = (float)v[e]; vct[e] = (float)vc[e]; }
+    }
 }
 
 static CtConfig pick_ct_config(int N_gcd, bool all_p2) {
@@ -208,9 +224,9 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         b->M_max = std::max(b->M_max, M);
         b->kappa_code = std::max(b->kappa_code, kap);
         pair_off[t] = off;
-        off += align_up(10 * sizeof(double) * M);
+        off += align_up(12 * sizeof(double) * M);
         off += align_up(sizeof(double) * (size_t)M * M);
-        off += 7 * align_up(tsz * m);
+        off += 9 * align_up(tsz * m);
     }
     if (!(same_kap && (kap0 == 1 || kap0 == 2 || kap0 == 4))) b->kappa_code = -b->kappa_code;
     // descriptors and item lists
@@ -303,7 +319,8 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         P.mu_rinv = P.nu_c_lo + M; P.nu_rinv = P.mu_rinv + M;
         P.mu_rinv32 = (float*)(P.nu_rinv + M); P.nu_rinv32 = P.mu_rinv32 + M;
         P.mu_c_hi = (double*)(P.nu_rinv32 + M); P.nu_c_hi = P.mu_c_hi + M;
-        base += align_up(10 * sizeof(double) * M);
+        P.mu_w_hi = P.nu_c_hi + M; P.nu_w_hi = P.mu_w_hi + M;
+        base += align_up(12 * sizeof(double) * M);
         P.cbar = (double*)base; base += align_up(sizeof(double) * (size_t)M * M);
         P.fhat = base; base += align_up(tsz * m);
         P.g = base; base += align_up(tsz * m);
@@ -312,6 +329,8 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         P.b = base; base += align_up(tsz * m);
         P.mu_t = base; base += align_up(tsz * m);
         P.nu_t = base; base += align_up(tsz * m);
+        P.mu_up = base; base += align_up(tsz * m);
+        P.nu_up = base; base += align_up(tsz * m);
         const void *lo, *hi;
         int st = ctx_table(ctx, N, probs[t].p, b->f64, s0, &lo, &hi);
         if (st) { batch_free(b); return st; }
@@ -320,6 +339,7 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         char* pd = b->plan_d + b->plan_off[t];
         P.rowptr = (int*)(pd + L.rowptr); P.colidx = (int*)(pd + L.col); P.val = (double*)(pd + L.val);
         P.colptr = (int*)(pd + L.colptr); P.rowidx = (int*)(pd + L.rowidx); P.valc = (double*)(pd + L.valc);
+        P.val_t = pd + L.val_t; P.valc_t = pd + L.valc_t;
         P.f_coarse = (double*)(pd + L.fco);
         P.sweeps = sweeps;
         P.ct_split = 2;
@@ -409,7 +429,7 @@ static int enqueue_fine(qwb_batch* b, bool batched, cudaStream_t s) {
         if ((st = mark(b, 3, s))) return st;
         if (do_primal && (st = launch_primal(b->pairs_d, b->outs_d, b->pair_ids_d, b->n, b->M_max, 0, b->f64, s))) return st;
         if ((st = mark(b, 4, s))) return st;
-        const int cap = 2 * sm;   // persistent grid: two CTAs per SM walk the item list
+        const int cap = sm;       // persistent grid: all resident CTAs walk the item list
         if (do_dual) {
             if ((st = launch_centre(b->pairs_d, b->outs_d, b->pair_ids_d, b->n, s))) return st;
             if ((st = mark(b, 5, s))) return st;
@@ -519,6 +539,7 @@ static int solve_pair(qwb_batch* b, int t) {
             rowidx[pos] = k; valc[pos] = sol.val[e];
         }
     std::memcpy(ph + L.fco, sol.f.data(), sizeof(double) * M);
+    stage_typed_values(ph, L, nnz, b->f64);
     b->pairs_h[t].nnz = nnz;
     // (2) C-bar problem: certified weighted-cost upper bound
     if (b->flags & QWB_FLAG_NO_WEIGHTED) {
@@ -912,12 +933,14 @@ int qwb_primal_upscale_ipf(qwb_ctx* ctx, const qwb_problem* prob, const double* 
             ((int*)(ph + L.rowidx))[pos] = k;
             ((double*)(ph + L.valc))[pos] = val[e];
         }
+    stage_typed_values(ph, L, pi_nnz, b->f64);
     QWB_CUDA(cudaMemcpyAsync(pd, ph, L.total, cudaMemcpyHostToDevice, s));
     PairDev& P = b->pairs_h[0];
     const PairDev saved = P;
     P.mu = mu_d; P.nu = nu_d; P.nnz = pi_nnz; P.sweeps = sweeps; P.a_out = a_d; P.b_out = b_d;
     P.rowptr = (int*)(pd + L.rowptr); P.colidx = (int*)(pd + L.col); P.val = (double*)(pd + L.val);
     P.colptr = (int*)(pd + L.colptr); P.rowidx = (int*)(pd + L.rowidx); P.valc = (double*)(pd + L.valc);
+    P.val_t = pd + L.val_t; P.valc_t = pd + L.valc_t;
     st = single_upload(b, s);
     {   // the cached descriptor keeps the batch's own buffers
         const PairDev cur = P;

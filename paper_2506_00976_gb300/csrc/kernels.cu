@@ -48,11 +48,22 @@ int launch_cost_tables(int N, double p, bool f64, void* lo, void* hi, cudaStream
     return QWB_OK;
 }
 
+// rho(x-bar, x)^p bracket for the TV weights, x-bar = ((N-1)/2, (N-1)/2).
+__device__ __forceinline__ double tv_weight_hi(int r, int c, int N, double p) {
+    const double dr = r - 0.5 * (N - 1), dc = c - 0.5 * (N - 1);
+    const double d2 = dr * dr + dc * dc;                  // exact (quarter integers)
+    if (p == 2.0) return d2;
+    if (p == 1.0) return __dsqrt_ru(d2);
+    if (d2 == 0.0) return 0.0;
+    return __dmul_ru(pow(d2, 0.5 * p), 1.0 + 0x1p-49);
+}
+
 // --------------------------------------------------------------------------
 // prepare: SumPool (Sec. 2.2) -- mu~_k = mu(X_k) in FP64, nearest and
 // round-down sums, plus validation (finite, non-negative, mass).
 // One thread per coarse block; items cover 256 blocks each.
 // --------------------------------------------------------------------------
+template <typename T>
 __global__ void prepare_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
                                const PixItem* __restrict__ items, int n_items) {
     const PixItem I = items[blockIdx.x];
@@ -64,10 +75,18 @@ __global__ void prepare_kernel(const PairDev* __restrict__ pairs, PairOut* __res
         const int N = P.N, kap = P.kappa, n = P.n;
         const int k1 = k / n, k2 = k % n;
         double mu_rn = 0.0, mu_rd = 0.0, nu_rn = 0.0, nu_rd = 0.0, mu_ru = 0.0, nu_ru = 0.0;
+        double mu_w = 0.0, nu_w = 0.0;
         for (int t1 = 0; t1 < kap; ++t1) {
             const int row = (k1 * kap + t1) * N + k2 * kap;
             for (int t2 = 0; t2 < kap; ++t2) {
                 const double x = P.mu[row + t2], y = P.nu[row + t2];
+                reinterpret_cast<T*>(P.mu_up)[row + t2] = from_double_ru<T>(x);
+                reinterpret_cast<T*>(P.nu_up)[row + t2] = from_double_ru<T>(y);
+                reinterpret_cast<T*>(P.mu_t)[row + t2] = (T)x;
+                reinterpret_cast<T*>(P.nu_t)[row + t2] = (T)y;
+                const double w = tv_weight_hi(k1 * kap + t1, k2 * kap + t2, N, P.p);
+                mu_w = __fma_ru(w, x, mu_w);
+                nu_w = __fma_ru(w, y, nu_w);
                 bad_mu |= !(x >= 0.0) || !isfinite(x);
                 bad_nu |= !(y >= 0.0) || !isfinite(y);
                 mu_rn += x; mu_rd = __dadd_rd(mu_rd, x); mu_ru = __dadd_ru(mu_ru, x);
@@ -76,6 +95,7 @@ __global__ void prepare_kernel(const PairDev* __restrict__ pairs, PairOut* __res
         }
         P.mu_c[k] = mu_rn; P.mu_c_lo[k] = mu_rd; P.mu_c_hi[k] = mu_ru;
         P.nu_c[k] = nu_rn; P.nu_c_lo[k] = nu_rd; P.nu_c_hi[k] = nu_ru;
+        P.mu_w_hi[k] = mu_w; P.nu_w_hi[k] = nu_w;
         // upper bounds of 1 / mu~_k for C-bar (0: zero mass, or too small for FP32)
         P.mu_rinv[k] = mu_rd > 0.0 ? __drcp_ru(mu_rd) : 0.0;
         P.nu_rinv[k] = nu_rd > 0.0 ? __drcp_ru(nu_rd) : 0.0;
@@ -109,9 +129,10 @@ __global__ void prepare_kernel(const PairDev* __restrict__ pairs, PairOut* __res
 }
 
 int launch_prepare(const PairDev* pairs_d, PairOut* outs_d, const PixItem* items, int n_items,
-                   bool, cudaStream_t stream) {
+                   bool f64, cudaStream_t stream) {
     if (n_items <= 0) return QWB_OK;
-    prepare_kernel<<<n_items, 256, 0, stream>>>(pairs_d, outs_d, items, n_items);
+    if (f64) prepare_kernel<double><<<n_items, 256, 0, stream>>>(pairs_d, outs_d, items, n_items);
+    else prepare_kernel<float><<<n_items, 256, 0, stream>>>(pairs_d, outs_d, items, n_items);
     QWB_LAUNCHED();
     return QWB_OK;
 }
@@ -144,7 +165,7 @@ __device__ __forceinline__ double cbar_special(const PairDev& P, int k, int l, d
 }
 
 template <typename T, int KAP>
-__global__ void __launch_bounds__(CBAR_THREADS)
+__global__ void __launch_bounds__(CBAR_THREADS, sizeof(T) == 4 ? 3 : 1)
 cbar_kernel(const PairDev* __restrict__ pairs, const CbarItem* __restrict__ items, int n_items) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
@@ -160,11 +181,13 @@ cbar_kernel(const PairDev* __restrict__ pairs, const CbarItem* __restrict__ item
         T* c_s = nu_s + CBAR_S * kap * N;                  // [2][W][N]: block-row offsets w1, w1 - n
         T* out_s = c_s + 2 * W * N;                        // [S][n][n]
         const T* tab = reinterpret_cast<const T*>(P.ctab_hi);
+        const T* mu_up = reinterpret_cast<const T*>(P.mu_up);   // rounded upward
+        const T* nu_up = reinterpret_cast<const T*>(P.nu_up);
         for (int idx = threadIdx.x; idx < S * kap * N; idx += blockDim.x) {
             const int s = idx / (kap * N), r = (idx / N) % kap, c = idx % N;
             const int k1 = k1_0 + s, l1 = (k1 - I.w1 + n) % n;
-            mu_s[idx] = from_double_ru<T>(P.mu[(k1 * kap + r) * N + c]);
-            nu_s[idx] = from_double_ru<T>(P.nu[(l1 * kap + r) * N + c]);
+            mu_s[idx] = mu_up[(k1 * kap + r) * N + c];
+            nu_s[idx] = nu_up[(l1 * kap + r) * N + c];
         }
         for (int idx = threadIdx.x; idx < 2 * W * N; idx += blockDim.x) {
             const int v = idx / (W * N), d = (idx / N) % W, c = idx % N;
@@ -192,26 +215,49 @@ cbar_kernel(const PairDev* __restrict__ pairs, const CbarItem* __restrict__ item
                                 cw[d1][d2] = cv[d1 * N + abs(KAP * D2 + d2 - (KAP - 1))];
                         cur_v = v;
                     }
-                    T nb[KAP][KAP];
-#pragma unroll
-                    for (int b1 = 0; b1 < KAP; ++b1)
-#pragma unroll
-                        for (int b2 = 0; b2 < KAP; ++b2)
-                            nb[b1][b2] = nu_s[(s * KAP + b1) * N + l2 * KAP + b2];
-                    T acc = T(0);
+                    // inner[a] = sum_b nu[b] c(a - b): every nu value feeds KAP^2
+                    // independent accumulators (summation order per accumulator
+                    // is b1, b2); then acc = sum_a mu[a] inner[a] in order a1, a2
+                    T inner[KAP][KAP];
 #pragma unroll
                     for (int a1 = 0; a1 < KAP; ++a1)
 #pragma unroll
-                        for (int a2 = 0; a2 < KAP; ++a2) {
-                            const T mv = mu_s[(s * KAP + a1) * N + k2 * KAP + a2];
-                            T inner = T(0);
+                        for (int a2 = 0; a2 < KAP; ++a2) inner[a1][a2] = T(0);
 #pragma unroll
-                            for (int b1 = 0; b1 < KAP; ++b1)
+                    for (int b1 = 0; b1 < KAP; ++b1) {
+                        T nrow[KAP];
+                        const T* np_ = nu_s + (s * KAP + b1) * N + l2 * KAP;
+                        if constexpr (KAP == 4 && sizeof(T) == 4) {
+                            const float4 v = *reinterpret_cast<const float4*>(np_);
+                            nrow[0] = v.x; nrow[1] = v.y; nrow[2] = v.z; nrow[3] = v.w;
+                        } else {
 #pragma unroll
-                                for (int b2 = 0; b2 < KAP; ++b2)
-                                    inner = fma_ru(nb[b1][b2], cw[a1 - b1 + KAP - 1][a2 - b2 + KAP - 1], inner);
-                            acc = fma_ru(mv, inner, acc);
+                            for (int b2 = 0; b2 < KAP; ++b2) nrow[b2] = np_[b2];
                         }
+#pragma unroll
+                        for (int b2 = 0; b2 < KAP; ++b2)
+#pragma unroll
+                            for (int a1 = 0; a1 < KAP; ++a1)
+#pragma unroll
+                                for (int a2 = 0; a2 < KAP; ++a2)
+                                    inner[a1][a2] = fma_ru(nrow[b2], cw[a1 - b1 + KAP - 1][a2 - b2 + KAP - 1],
+                                                           inner[a1][a2]);
+                    }
+                    T acc = T(0);
+#pragma unroll
+                    for (int a1 = 0; a1 < KAP; ++a1) {
+                        T mrow[KAP];
+                        const T* mp_ = mu_s + (s * KAP + a1) * N + k2 * KAP;
+                        if constexpr (KAP == 4 && sizeof(T) == 4) {
+                            const float4 v = *reinterpret_cast<const float4*>(mp_);
+                            mrow[0] = v.x; mrow[1] = v.y; mrow[2] = v.z; mrow[3] = v.w;
+                        } else {
+#pragma unroll
+                            for (int a2 = 0; a2 < KAP; ++a2) mrow[a2] = mp_[a2];
+                        }
+#pragma unroll
+                        for (int a2 = 0; a2 < KAP; ++a2) acc = fma_ru(mrow[a2], inner[a1][a2], acc);
+                    }
                     const int l1 = (k1 - I.w1 + n) % n;
                     const int k = k1 * n + k2, l = l1 * n + l2;
                     T outv;
@@ -375,16 +421,6 @@ __device__ __forceinline__ double block_reduce_rn(double v, double* red) {
     return red[32];
 }
 
-// rho(x-bar, x)^p bracket for the TV weights, x-bar = ((N-1)/2, (N-1)/2).
-__device__ __forceinline__ double tv_weight_hi(int r, int c, int N, double p) {
-    const double dr = r - 0.5 * (N - 1), dc = c - 0.5 * (N - 1);
-    const double d2 = dr * dr + dc * dc;                  // exact (quarter integers)
-    if (p == 2.0) return d2;
-    if (p == 1.0) return __dsqrt_ru(d2);
-    if (d2 == 0.0) return 0.0;
-    return __dmul_ru(pow(d2, 0.5 * p), 1.0 + 0x1p-49);
-}
-
 // x^(1/p) rounded upward (x >= 0)
 __device__ __forceinline__ double root_p_ru(double x, double p) {
     if (x <= 0.0) return 0.0;
@@ -397,6 +433,60 @@ __device__ __forceinline__ double root_p_rd(double x, double p) {
     if (p == 1.0) return x;
     if (p == 2.0) return __dsqrt_rd(x);
     return __dmul_rd(pow(x, 1.0 / p), 1.0 - 0x1p-49);
+}
+
+// num_kl = sum_{i in X_k} mu_i sum_{j in Y_l} nu_j rho(x_i, y_j)^p with upward
+// rounding, accumulated in the same order as the C-bar kernel.
+template <typename T, int KAP>
+__device__ T block_pair_num(const PairDev& P, int k, int l) {
+    const int N = P.N, n = P.n, kap = KAP > 0 ? KAP : P.kappa;
+    const int k1 = k / n, k2 = k % n, l1 = l / n, l2 = l % n;
+    const T* tab = reinterpret_cast<const T*>(P.ctab_hi);
+    const T* mu_up = reinterpret_cast<const T*>(P.mu_up);
+    const T* nu_up = reinterpret_cast<const T*>(P.nu_up);
+    const int D1 = kap * (k1 - l1), D2 = kap * (k2 - l2);
+    T acc = T(0);
+    if constexpr (KAP > 0) {
+        constexpr int WK = 2 * KAP - 1;
+        T cw[WK][WK];
+#pragma unroll
+        for (int d1 = 0; d1 < WK; ++d1)
+#pragma unroll
+            for (int d2 = 0; d2 < WK; ++d2)
+                cw[d1][d2] = tab[abs(D1 + d1 - (KAP - 1)) * N + abs(D2 + d2 - (KAP - 1))];
+        T inner[KAP][KAP];
+#pragma unroll
+        for (int a1 = 0; a1 < KAP; ++a1)
+#pragma unroll
+            for (int a2 = 0; a2 < KAP; ++a2) inner[a1][a2] = T(0);
+#pragma unroll
+        for (int b1 = 0; b1 < KAP; ++b1)
+#pragma unroll
+            for (int b2 = 0; b2 < KAP; ++b2) {
+                const T nv = nu_up[(l1 * KAP + b1) * N + l2 * KAP + b2];
+#pragma unroll
+                for (int a1 = 0; a1 < KAP; ++a1)
+#pragma unroll
+                    for (int a2 = 0; a2 < KAP; ++a2)
+                        inner[a1][a2] = fma_ru(nv, cw[a1 - b1 + KAP - 1][a2 - b2 + KAP - 1], inner[a1][a2]);
+            }
+#pragma unroll
+        for (int a1 = 0; a1 < KAP; ++a1)
+#pragma unroll
+            for (int a2 = 0; a2 < KAP; ++a2)
+                acc = fma_ru(mu_up[(k1 * KAP + a1) * N + k2 * KAP + a2], inner[a1][a2], acc);
+    } else {
+        for (int a1 = 0; a1 < kap; ++a1)
+            for (int a2 = 0; a2 < kap; ++a2) {
+                T inner = T(0);
+                for (int b1 = 0; b1 < kap; ++b1)
+                    for (int b2 = 0; b2 < kap; ++b2)
+                        inner = fma_ru(nu_up[(l1 * kap + b1) * N + l2 * kap + b2],
+                                       tab[abs(D1 + a1 - b1) * N + abs(D2 + a2 - b2)], inner);
+                acc = fma_ru(mu_up[(k1 * kap + a1) * N + k2 * kap + a2], inner, acc);
+            }
+    }
+    return acc;
 }
 
 template <typename T>
@@ -419,12 +509,8 @@ primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
     const T kk = (T)(kap * kap);
 
     // ---- fine sweeps ------------------------------------------------------
-    T* mu_t = reinterpret_cast<T*>(P.mu_t);
-    T* nu_t = reinterpret_cast<T*>(P.nu_t);
-    for (int i = threadIdx.x; i < N * N; i += blockDim.x) {      // one conversion per call
-        mu_t[i] = (T)P.mu[i];
-        nu_t[i] = (T)P.nu[i];
-    }
+    const T* mu_t = reinterpret_cast<const T*>(P.mu_t);    // written by the SumPool pass
+    const T* nu_t = reinterpret_cast<const T*>(P.nu_t);
     for (int l = threadIdx.x; l < M; l += blockDim.x) Bt[l] = kk;    // b = 1
     __syncthreads();
     const bool vec4 = (sizeof(T) == 4) && (kap == 4);              // block rows are one float4
@@ -434,14 +520,14 @@ primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
             // half 1: b = nu / (pi-hat^T a), B = block sums of b
             const int* ptr = half == 0 ? P.rowptr : P.colptr;
             const int* idx = half == 0 ? P.colidx : P.rowidx;
-            const double* val = half == 0 ? P.val : P.valc;
+            const T* val = reinterpret_cast<const T*>(half == 0 ? P.val_t : P.valc_t);
             const T* src = half == 0 ? mu_t : nu_t;
             T* dst = half == 0 ? a : b;
             const T* other = half == 0 ? Bt : At;
             T* mine = half == 0 ? At : Bt;
             for (int k = threadIdx.x; k < M; k += blockDim.x) {
                 T r = T(0);
-                for (int e = ptr[k]; e < ptr[k + 1]; ++e) r += (T)val[e] * other[idx[e]];
+                for (int e = ptr[k]; e < ptr[k + 1]; ++e) r += val[e] * other[idx[e]];
                 r *= kinv4;
                 const T inv = r > T(0) ? T(1) / r : T(0);
                 const int k1 = k / n, k2 = k % n;
@@ -536,15 +622,7 @@ primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
     // rho_k = alpha_k kappa^-4 sum_l pi~_kl beta_l nu~_l ;  mu-hat = rho_k mu
     double tv_mu = 0.0, res_mu = 0.0;
     for (int k = threadIdx.x; k < M; k += blockDim.x) {
-        const int k1 = k / n, k2 = k % n;
-        double m_lo = 0.0, m_hi = 0.0, w_hi = 0.0;
-        for (int t1 = 0; t1 < kap; ++t1)
-            for (int t2 = 0; t2 < kap; ++t2) {
-                const int r = k1 * kap + t1, c = k2 * kap + t2;
-                const double x = P.mu[r * N + c];
-                m_lo = __dadd_rd(m_lo, x); m_hi = __dadd_ru(m_hi, x);
-                w_hi = __fma_ru(tv_weight_hi(r, c, N, P.p), x, w_hi);
-            }
+        const double m_hi = P.mu_c_hi[k], w_hi = P.mu_w_hi[k];
         double s_lo = 0.0, s_hi = 0.0;
         for (int e = P.rowptr[k]; e < P.rowptr[k + 1]; ++e) {
             const int l = P.colidx[e];
@@ -560,15 +638,7 @@ primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
     }
     double tv_nu = 0.0, res_nu = 0.0;
     for (int l = threadIdx.x; l < M; l += blockDim.x) {
-        const int l1 = l / n, l2 = l % n;
-        double w_hi = 0.0, m_hi = 0.0;
-        for (int t1 = 0; t1 < kap; ++t1)
-            for (int t2 = 0; t2 < kap; ++t2) {
-                const int r = l1 * kap + t1, c = l2 * kap + t2;
-                const double y = P.nu[r * N + c];
-                m_hi = __dadd_ru(m_hi, y);
-                w_hi = __fma_ru(tv_weight_hi(r, c, N, P.p), y, w_hi);
-            }
+        const double m_hi = P.nu_c_hi[l], w_hi = P.nu_w_hi[l];
         double s_lo = 0.0, s_hi = 0.0;
         for (int e = P.colptr[l]; e < P.colptr[l + 1]; ++e) {
             const int k = P.rowidx[e];
@@ -586,27 +656,13 @@ primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
     // ---- certified cost of the fitted plan over its support -----------------
     // W-hat^p = sum_{(k,l) in supp pi~} kappa^-4 pi~_kl alpha_k beta_l num_kl,
     // num_kl = sum_{i in X_k, j in Y_l} mu_i nu_j rho(x_i, y_j)^p (rounded up)
-    const T* tab = reinterpret_cast<const T*>(P.ctab_hi);
     double cost = 0.0;
     for (int e = threadIdx.x; e < P.nnz; e += blockDim.x) {
         // row of entry e: binary search in rowptr
         int lo = 0, hi = M;
         while (hi - lo > 1) { const int mid = (lo + hi) >> 1; if (P.rowptr[mid] <= e) lo = mid; else hi = mid; }
         const int k = lo, l = P.colidx[e];
-        const int k1 = k / n, k2 = k % n, l1 = l / n, l2 = l % n;
-        T num = T(0);
-        for (int a1 = 0; a1 < kap; ++a1)
-            for (int a2 = 0; a2 < kap; ++a2) {
-                const int xr = k1 * kap + a1, xc = k2 * kap + a2;
-                T inner = T(0);
-                for (int b1 = 0; b1 < kap; ++b1)
-                    for (int b2 = 0; b2 < kap; ++b2) {
-                        const int yr = l1 * kap + b1, yc = l2 * kap + b2;
-                        inner = fma_ru(from_double_ru<T>(P.nu[yr * N + yc]),
-                                       tab[abs(xr - yr) * N + abs(xc - yc)], inner);
-                    }
-                num = fma_ru(from_double_ru<T>(P.mu[xr * N + xc]), inner, num);
-            }
+        const T num = kap == 4 ? block_pair_num<T, 4>(P, k, l) : block_pair_num<T, 0>(P, k, l);
         const double term = __dmul_ru(__dmul_ru(__dmul_ru(__dmul_ru(P.val[e], kinv4_hi), alpha[k]), beta[l]),
                                       (double)num);
         cost = __dadd_ru(cost, term);
@@ -741,6 +797,21 @@ __device__ __forceinline__ float min3(float a, float b, float c) {
 }
 __device__ __forceinline__ double min3(double a, double b, double c) { return fmin(a, fmin(b, c)); }
 
+// Packed pair of FP32 values and a packed subtraction rounded toward -inf
+// (PTX sub.rm.f32x2, sm_100 and later).
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ unsigned long long pack2(double, double) { return 0ull; }
+__device__ __forceinline__ void sub_rd_x2(unsigned long long a, unsigned long long b, float& lo,
+                                          float& hi) {
+    unsigned long long d;
+    asm("sub.rm.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(d));
+}
+
 template <typename T, int R, int TC, bool P2>
 __global__ void __launch_bounds__(256)
 ctransform_kernel(const PairDev* __restrict__ pairs, const CtItem* __restrict__ items,
@@ -791,7 +862,29 @@ ctransform_kernel(const PairDev* __restrict__ pairs, const CtItem* __restrict__ 
                     const T* hrow = hs + r1 * N + c0;
 #pragma unroll
                     for (int s = 0; s < TC; ++s) fv[s] = hrow[s];
-                    if constexpr (TC % 2 == 0) {
+                    if constexpr (TC % 2 == 0 && sizeof(T) == 4) {
+                        // two candidates per packed subtraction: (q_e, q_e+1) - (f_s, f_s+1)
+                        // rounded toward -inf, then one 3-input min
+                        unsigned long long qa[(NQ + 1) / 2], qb[NQ / 2], fp[TC / 2];
+#pragma unroll
+                        for (int j = 0; j < (NQ + 1) / 2; ++j)
+                            qa[j] = pack2(q[2 * j], 2 * j + 1 < NQ ? q[2 * j + 1] : T(0));
+#pragma unroll
+                        for (int j = 0; j < NQ / 2; ++j)
+                            qb[j] = pack2(q[2 * j + 1], 2 * j + 2 < NQ ? q[2 * j + 2] : T(0));
+#pragma unroll
+                        for (int j = 0; j < TC / 2; ++j) fp[j] = pack2(fv[2 * j], fv[2 * j + 1]);
+#pragma unroll
+                        for (int s = 0; s < TC; s += 2)
+#pragma unroll
+                            for (int r = 0; r < R; ++r) {
+                                const int e = s - r + R - 1;
+                                const unsigned long long qq = (e % 2 == 0) ? qa[e / 2] : qb[e / 2];
+                                float t0, t1;
+                                sub_rd_x2(qq, fp[s / 2], t0, t1);
+                                mins[r] = min3(mins[r], t0, t1);
+                            }
+                    } else if constexpr (TC % 2 == 0) {
 #pragma unroll
                         for (int s = 0; s < TC; s += 2)
 #pragma unroll
@@ -832,7 +925,13 @@ static int ct_launch_rt(const PairDev* pairs_d, const CtItem* items, int n_items
     const size_t smem = sizeof(T) * (size_t)in_rows * N_max;
     if (smem > 227 * 1024) return QWB_ERR_UNSUPPORTED;
     QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int grid = grid_cap > 0 ? std::min(n_items, grid_cap) : n_items;
+    // persistent form: grid_cap = SM count; as many CTAs as fit at once
+    int grid = n_items;
+    if (grid_cap > 0) {
+        int occ = 1;
+        QWB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem));
+        grid = std::min(n_items, grid_cap * std::max(1, occ));
+    }
     kern<<<grid, threads, smem, stream>>>(pairs_d, items, n_items, phase);
     QWB_LAUNCHED();
     return QWB_OK;

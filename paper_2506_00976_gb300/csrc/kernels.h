@@ -25,12 +25,16 @@ struct PairDev {
     double* mu_c_hi;        // M coarse masses, round-up sums
     double* nu_c_hi;
     void* mu_t; void* nu_t; // N*N copies of mu, nu in the pass type T (IPF sweeps)
+    void* mu_up; void* nu_up; // N*N copies of mu, nu in type T rounded upward (C-bar)
+    double* mu_w_hi;        // M upper bounds of sum_{x in X_k} rho(x-bar, x)^p mu(x) (TV weights)
+    double* nu_w_hi;
     double* cbar;           // M*M coarse cost out (may be null)
     const void* ctab_lo;    // N*N cost table, lower brackets (T)
     const void* ctab_hi;    // N*N cost table, upper brackets (T)
     // coarse plan (CSR and CSC) for the primal pass
     const int* rowptr; const int* colidx; const double* val;
     const int* colptr; const int* rowidx; const double* valc;
+    const void* val_t; const void* valc_t;   // plan values in the pass type T
     int nnz;
     int sweeps;
     void* a; void* b;       // N*N fine scalings work (T)
