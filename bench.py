@@ -308,6 +308,7 @@ def run_gpu(args):
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps},
             "gpu_launches": int(launches),
+            "autotune": batch.tuning(),
             "clocks": clocks,
         }
         if not args.no_cpu_baseline:

@@ -251,6 +251,16 @@ int qwb_batch_potentials(qwb_batch* batch, int32_t pair, double* f_d, double* g_
  * c-transform f-hat -> g, c-transform g -> f, lower-bound sum; -1 where not
  * measured.  Fills min(n, 8) values; call after the stream has completed. */
 int qwb_batch_kernel_times(qwb_batch* batch, double* ms_out, int32_t n);
+/* Launch configurations the autotuner chose for this batch and the device
+ * time of every candidate it measured, as a NUL-terminated JSON object
+ * written to json_out (capacity bytes).  The autotuner runs at the first
+ * batched coarse / fine pass of a problem signature (set of N, kappa, p,
+ * precision and pair count), timing each compiled variant on the batch's own
+ * data; results are kept in the context and, when the environment variable
+ * QWB_AUTOTUNE_CACHE names a file, stored there and reused by later
+ * processes.  QWB_AUTOTUNE=0 keeps the default configuration.
+ * Errors: INVALID_ARG (null or too small buffer). */
+int qwb_batch_tuning(qwb_batch* batch, char* json_out, int32_t capacity);
 
 /* ------------------------------------------------------------------------ */
 /* Diagnostics                                                               */

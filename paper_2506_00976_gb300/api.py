@@ -208,6 +208,13 @@ class Batch:
         check(_lib.load().qwb_batch_kernel_times(self._h, out, 8), "qwb_batch_kernel_times")
         return dict(zip(self.KERNELS, list(out)))
 
+    def tuning(self):
+        """The autotuner's choices and candidate timings for this batch (dict)."""
+        import json
+        buf = ctypes.create_string_buffer(8192)
+        check(_lib.load().qwb_batch_tuning(self._h, buf, len(buf)), "qwb_batch_tuning")
+        return json.loads(buf.value.decode())
+
     def potentials(self, t):
         N = self.problems[t].N
         f = torch.empty(N * N, dtype=torch.float64, device=self._dev)

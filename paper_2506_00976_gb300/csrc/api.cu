@@ -5,8 +5,14 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <deque>
+#include <fstream>
+#include <functional>
 #include <mutex>
+#include <sstream>
 #include <string>
 #include <thread>
 #include <vector>
@@ -36,7 +42,7 @@ static int check_problem(const qwb_problem* p) {
         return fail(QWB_ERR_INVALID_ARG, "kappa must divide N");
     if (!(p->p >= 1.0) || !std::isfinite(p->p)) return fail(QWB_ERR_INVALID_ARG, "p must be >= 1");
     const int n = p->N / p->kappa;
-    if (n * n > 16384) return fail(QWB_ERR_UNSUPPORTED, "coarse grid larger than 128 x 128");
+    if (n > 64) return fail(QWB_ERR_UNSUPPORTED, "coarse grid larger than 64 x 64");
     return QWB_OK;
 }
 
@@ -55,13 +61,51 @@ struct CostTable {
     void* hi;
 };
 
+// Launch configuration chosen by the autotuner for one problem signature.
+struct TuneEntry {
+    std::string key;
+    int R = 0, TC = 0, packed = 0, cbar_variant = 0;
+    bool ct_done = false, cbar_done = false;
+    std::string ct_report, cbar_report;   // JSON fragments: candidate -> ms
+};
+
 struct qwb_ctx {
     int device = 0;
     int sm_count = 0;
     std::mutex mtx;
     std::vector<CostTable> tables;
     std::vector<qwb_batch*> single_cache;   // single-pair batches for standalone calls
+    std::deque<TuneEntry> tunes;            // autotuner results (stable addresses)
+    bool autotune = true;                   // QWB_AUTOTUNE=0 keeps the default configuration
+    std::string tune_cache;                 // QWB_AUTOTUNE_CACHE: file of tuned configurations
 };
+
+static void tune_cache_load(qwb_ctx* c) {
+    if (c->tune_cache.empty()) return;
+    std::ifstream in(c->tune_cache);
+    std::string line;
+    while (std::getline(in, line)) {
+        std::istringstream ls(line);
+        TuneEntry e;
+        std::string r, tc, pk, cv;
+        if (!std::getline(ls, e.key, '|') || !std::getline(ls, r, '|') || !std::getline(ls, tc, '|') ||
+            !std::getline(ls, pk, '|') || !std::getline(ls, cv, '|'))
+            continue;
+        e.R = std::atoi(r.c_str()); e.TC = std::atoi(tc.c_str());
+        e.packed = std::atoi(pk.c_str()); e.cbar_variant = std::atoi(cv.c_str());
+        e.ct_done = e.R > 0; e.cbar_done = true;
+        e.ct_report = "\"cached\""; e.cbar_report = "\"cached\"";
+        c->tunes.push_back(e);
+    }
+}
+
+static void tune_cache_store(qwb_ctx* c) {
+    if (c->tune_cache.empty()) return;
+    std::ofstream out(c->tune_cache, std::ios::trunc);
+    for (auto& e : c->tunes)
+        if (e.ct_done && e.cbar_done)
+            out << e.key << '|' << e.R << '|' << e.TC << '|' << e.packed << '|' << e.cbar_variant << "|\n";
+}
 
 static int ctx_table(qwb_ctx* c, int N, double p, bool f64, cudaStream_t s, const void** lo,
                      const void** hi) {
@@ -129,6 +173,10 @@ struct qwb_batch {
     bool ev_ok = false;
     std::vector<const double*> cur_mu, cur_nu;
     std::vector<GraphEntry> graphs;
+    TuneEntry* tune = nullptr;
+    int cbar_variant = 0;
+    int N_gcd = 1;
+    bool all_p2 = false;
 };
 
 static void batch_free(qwb_batch* b) {
@@ -236,7 +284,30 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
     std::vector<CtItem> ctb, ctp;
     b->ct_cfg_b = pick_ct_config(N_gcd, all_p2);
     b->ct_cfg_p = b->ct_cfg_b;
-    const int tile_out = b->ct_cfg_b.threads * b->ct_cfg_b.R;
+    b->N_gcd = N_gcd;
+    b->all_p2 = all_p2;
+    {   // autotuner entry for this problem signature
+        std::ostringstream key;
+        key << (b->f64 ? "f64" : "mixed") << ":" << n;
+        std::vector<std::string> parts;
+        for (int t = 0; t < n; ++t) {
+            std::ostringstream p1;
+            p1 << probs[t].N << "/" << probs[t].kappa << "/" << probs[t].p;
+            parts.push_back(p1.str());
+        }
+        std::sort(parts.begin(), parts.end());
+        parts.erase(std::unique(parts.begin(), parts.end()), parts.end());
+        for (auto& p1 : parts) key << ":" << p1;
+        TuneEntry* found = nullptr;
+        for (auto& e : ctx->tunes) if (e.key == key.str()) found = &e;
+        if (!found) { ctx->tunes.push_back(TuneEntry{}); found = &ctx->tunes.back(); found->key = key.str(); }
+        b->tune = found;
+        if (found->ct_done && found->R > 0 && N_gcd % found->R == 0 && N_gcd % found->TC == 0) {
+            b->ct_cfg_b.R = found->R; b->ct_cfg_b.TC = found->TC; b->ct_cfg_b.packed = found->packed != 0;
+        }
+        if (found->cbar_done) b->cbar_variant = found->cbar_variant;
+    }
+    const int tile_out = CT_TILE;
     long total_tiles = 0;
     for (int t = 0; t < n; ++t) total_tiles += ((long)probs[t].N * probs[t].N + tile_out - 1) / tile_out;
     for (int t = 0; t < n; ++t) {
@@ -248,8 +319,7 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         for (int i = 0; i < m; i += 256) pix.push_back({t, i});
         b->pix_cnt.push_back((int)pix.size() - b->pix_off.back());
         b->cbar_off.push_back((int)cb.size());
-        for (int w1 = 0; w1 < nn; ++w1)
-            for (int seg = 0; seg * CBAR_S < nn; ++seg) cb.push_back({t, w1, seg, 0});
+        for (int w1 = 0; w1 < nn; ++w1) cb.push_back({t, w1, 0, 0});
         b->cbar_cnt.push_back((int)cb.size() - b->cbar_off.back());
         const int tiles = (m + tile_out - 1) / tile_out;
         // batched form: about 12 items per SM over the whole batch (six waves
@@ -404,7 +474,8 @@ static int enqueue_coarse(qwb_batch* b, bool batched, cudaStream_t s) {
         if ((st = launch_prepare(b->pairs_d, b->outs_d, b->prep_items_d, b->n_prep, b->f64, s))) return st;
         if ((st = mark(b, 1, s))) return st;
         if (!(b->flags & QWB_FLAG_NO_WEIGHTED) &&
-            (st = launch_cbar(b->pairs_d, b->cbar_items_d, b->n_cbar, b->kappa_code, b->n_max, b->N_max, b->f64, s)))
+            (st = launch_cbar(b->pairs_d, b->cbar_items_d, b->n_cbar, b->kappa_code, b->n_max, b->N_max, b->f64, s,
+                              b->cbar_variant)))
             return st;
         return mark(b, 2, s);
     }
@@ -461,6 +532,89 @@ static int enqueue_fine(qwb_batch* b, bool batched, cudaStream_t s) {
     return QWB_OK;
 }
 
+// ---- autotuner -------------------------------------------------------------
+// Times each compiled variant of a pass on the batch's own data (CUDA events,
+// best of two runs after one warm-up) and keeps the fastest.  Every variant
+// computes the same values, so the buffers are simply overwritten.
+static int time_variant(cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1,
+                        const std::function<int()>& launch, double* ms) {
+    int st = launch();
+    if (st) return st;
+    double best = 1e30;
+    for (int rep = 0; rep < 2; ++rep) {
+        QWB_CUDA(cudaEventRecord(e0, s));
+        if ((st = launch())) return st;
+        QWB_CUDA(cudaEventRecord(e1, s));
+        QWB_CUDA(cudaEventSynchronize(e1));
+        float t = 0.f;
+        QWB_CUDA(cudaEventElapsedTime(&t, e0, e1));
+        best = std::min(best, (double)t);
+    }
+    *ms = best;
+    return QWB_OK;
+}
+
+static int tune_cbar(qwb_batch* b, cudaStream_t s) {
+    TuneEntry* e = b->tune;
+    if (!b->ctx->autotune || !e || e->cbar_done || !b->ev_ok) return QWB_OK;
+    if (b->kappa_code != 4 || (b->flags & QWB_FLAG_NO_WEIGHTED)) { e->cbar_done = true; e->cbar_report = "{}"; return QWB_OK; }
+    int st = launch_prepare(b->pairs_d, b->outs_d, b->prep_items_d, b->n_prep, b->f64, s);
+    if (st) return st;
+    std::ostringstream rep;
+    double best = 1e30;
+    rep << "{";
+    for (int v = 0; v < 2; ++v) {
+        double ms;
+        st = time_variant(s, b->ev[0], b->ev[1], [&] {
+            return launch_cbar(b->pairs_d, b->cbar_items_d, b->n_cbar, b->kappa_code, b->n_max, b->N_max,
+                               b->f64, s, v);
+        }, &ms);
+        if (st) return st;
+        rep << (v ? ", " : "") << "\"min_ctas_per_sm=" << (v ? 3 : 2) << "\": " << ms;
+        if (ms < best) { best = ms; e->cbar_variant = v; }
+    }
+    rep << "}";
+    e->cbar_report = rep.str();
+    e->cbar_done = true;
+    b->cbar_variant = e->cbar_variant;
+    tune_cache_store(b->ctx);
+    return QWB_OK;
+}
+
+static int tune_ctransform(qwb_batch* b, cudaStream_t s) {
+    TuneEntry* e = b->tune;
+    if (!b->ctx->autotune || !e || e->ct_done || !b->ev_ok || (b->flags & QWB_FLAG_NO_DUAL)) return QWB_OK;
+    int st = launch_centre(b->pairs_d, b->outs_d, b->pair_ids_d, b->n, s);
+    if (!st) st = launch_upsample(b->pairs_d, b->outs_d, b->pix_items_d, b->n_pix, b->f64, s);
+    if (st) return st;
+    const int cand[][3] = {{4, 4, 0}, {8, 8, 0}, {16, 8, 0}, {16, 16, 0}, {8, 16, 0},
+                           {8, 8, 1}, {16, 8, 1}, {16, 16, 1}};
+    const int sm = b->ctx->sm_count > 0 ? b->ctx->sm_count : 148;
+    std::ostringstream rep;
+    double best = 1e30;
+    bool first = true;
+    rep << "{";
+    for (auto& c : cand) {
+        if (b->N_gcd % c[0] || b->N_gcd % c[1] || (c[2] && b->f64)) continue;
+        CtConfig cfg = b->ct_cfg_b;
+        cfg.R = c[0]; cfg.TC = c[1]; cfg.packed = c[2] != 0;
+        double ms;
+        st = time_variant(s, b->ev[0], b->ev[1], [&] {
+            return launch_ctransform(b->pairs_d, b->ct_b_items_d, b->n_ct_b, 0, cfg, b->N_max, b->f64, sm, s);
+        }, &ms);
+        if (st) return st;
+        rep << (first ? "" : ", ") << "\"R" << c[0] << "xT" << c[1] << (c[2] ? "_packed" : "") << "\": " << ms;
+        first = false;
+        if (ms < best) { best = ms; e->R = c[0]; e->TC = c[1]; e->packed = c[2]; }
+    }
+    rep << "}";
+    e->ct_report = rep.str();
+    e->ct_done = e->R > 0;
+    if (e->ct_done) { b->ct_cfg_b.R = e->R; b->ct_cfg_b.TC = e->TC; b->ct_cfg_b.packed = e->packed != 0; }
+    tune_cache_store(b->ctx);
+    return QWB_OK;
+}
+
 // Run a pass for the whole batch, through a captured CUDA graph when batched.
 static int run_pass(qwb_batch* b, int kind, bool batched, cudaStream_t s) {
     if (!batched) return kind == 0 ? enqueue_coarse(b, false, s) : enqueue_fine(b, false, s);
@@ -470,6 +624,11 @@ static int run_pass(qwb_batch* b, int kind, bool batched, cudaStream_t s) {
             count_launch(g.kernels);
             return QWB_OK;
         }
+    // tune this pass's kernels on the batch's data before the first capture
+    {
+        const int st_t = kind == 0 ? tune_cbar(b, s) : tune_ctransform(b, s);
+        if (st_t) return st_t;
+    }
     // capture on a private stream, then launch on the caller's stream
     cudaStream_t cs;
     QWB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -683,6 +842,9 @@ int qwb_ctx_create(qwb_ctx** out, int device) {
     qwb_ctx* c = new qwb_ctx();
     c->device = device;
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (const char* v = std::getenv("QWB_AUTOTUNE")) c->autotune = std::strcmp(v, "0") != 0;
+    if (const char* v = std::getenv("QWB_AUTOTUNE_CACHE")) c->tune_cache = v;
+    tune_cache_load(c);
     *out = c;
     return QWB_OK;
 }
@@ -771,6 +933,21 @@ int qwb_batch_kernel_times(qwb_batch* b, double* ms_out, int32_t n) {
         }
         ms_out[i] = ms;
     }
+    return QWB_OK;
+}
+
+int qwb_batch_tuning(qwb_batch* b, char* json_out, int32_t capacity) {
+    if (!b || !json_out || capacity <= 0) return fail(QWB_ERR_INVALID_ARG, "qwb_batch_tuning: bad argument");
+    std::ostringstream o;
+    o << "{\"key\": \"" << (b->tune ? b->tune->key : "") << "\", \"ctransform\": {\"R\": " << b->ct_cfg_b.R
+      << ", \"TC\": " << b->ct_cfg_b.TC << ", \"packed\": " << (b->ct_cfg_b.packed ? "true" : "false")
+      << ", \"candidates_ms\": " << (b->tune && !b->tune->ct_report.empty() ? b->tune->ct_report : "{}")
+      << "}, \"cbar\": {\"min_ctas_per_sm\": " << (b->cbar_variant ? 3 : 2)
+      << ", \"candidates_ms\": " << (b->tune && !b->tune->cbar_report.empty() ? b->tune->cbar_report : "{}")
+      << "}, \"enabled\": " << (b->ctx->autotune ? "true" : "false") << "}";
+    const std::string str = o.str();
+    if ((int)str.size() + 1 > capacity) return fail(QWB_ERR_INVALID_ARG, "qwb_batch_tuning: buffer too small");
+    std::memcpy(json_out, str.c_str(), str.size() + 1);
     return QWB_OK;
 }
 

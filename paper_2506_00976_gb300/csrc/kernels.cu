@@ -164,8 +164,14 @@ __device__ __forceinline__ double cbar_special(const PairDev& P, int k, int l, d
     return mean_up;
 }
 
-template <typename T, int KAP>
-__global__ void __launch_bounds__(CBAR_THREADS, sizeof(T) == 4 ? 3 : 1)
+constexpr int CBAR_WPAD = 52;   // (2*4-1)^2 = 49 window entries padded to whole float4s
+
+// Per-thread block-pair slots: slot j of thread t is b = t + j*CBAR_THREADS
+// over the n*n pairs (k2, l2), by wrapped column diagonal w2 = b / n.
+constexpr int CBAR_MAX_SLOTS = 16;   // n <= 64
+
+template <typename T, int KAP, int MINB>
+__global__ void __launch_bounds__(CBAR_THREADS, MINB)
 cbar_kernel(const PairDev* __restrict__ pairs, const CbarItem* __restrict__ items, int n_items) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
@@ -174,186 +180,240 @@ cbar_kernel(const PairDev* __restrict__ pairs, const CbarItem* __restrict__ item
         const int N = P.N, n = P.n, M = P.M;
         const int kap = KAP > 0 ? KAP : P.kappa;
         const int W = 2 * kap - 1;
-        const int k1_0 = I.seg * CBAR_S;
-        const int S = min(CBAR_S, n - k1_0);
-        T* mu_s = reinterpret_cast<T*>(smem_raw);         // [S][kap][N]
-        T* nu_s = mu_s + CBAR_S * kap * N;                 // [S][kap][N]
-        T* c_s = nu_s + CBAR_S * kap * N;                  // [2][W][N]: block-row offsets w1, w1 - n
-        T* out_s = c_s + 2 * W * N;                        // [S][n][n]
+        const int w1 = I.w1;
+        double* __restrict__ cbar = P.cbar;
+        // shared memory: mu rows [S][kap][N], nu rows [S][kap][N], cost windows,
+        // results [S][n][n], reciprocal masses [S][n] twice
+        T* mu_s = reinterpret_cast<T*>(smem_raw);
+        T* nu_s = mu_s + CBAR_S * kap * N;
+        T* win_s = nu_s + CBAR_S * kap * N;
+        // KAP > 0: [2][2n-1][CBAR_WPAD] windows, one per (block-row offset, block-column offset)
+        // KAP = 0: [2][W][N] cost-table rows for the two block-row offsets
+        const int win_len = KAP > 0 ? 2 * (2 * n - 1) * CBAR_WPAD : 2 * W * N;
+        T* out_s = win_s + win_len;
+        T* rk_s = out_s + CBAR_S * n * n;
+        T* rl_s = rk_s + CBAR_S * n;
         const T* tab = reinterpret_cast<const T*>(P.ctab_hi);
         const T* mu_up = reinterpret_cast<const T*>(P.mu_up);   // rounded upward
         const T* nu_up = reinterpret_cast<const T*>(P.nu_up);
-        for (int idx = threadIdx.x; idx < S * kap * N; idx += blockDim.x) {
-            const int s = idx / (kap * N), r = (idx / N) % kap, c = idx % N;
-            const int k1 = k1_0 + s, l1 = (k1 - I.w1 + n) % n;
-            mu_s[idx] = mu_up[(k1 * kap + r) * N + c];
-            nu_s[idx] = nu_up[(l1 * kap + r) * N + c];
-        }
-        for (int idx = threadIdx.x; idx < 2 * W * N; idx += blockDim.x) {
-            const int v = idx / (W * N), d = (idx / N) % W, c = idx % N;
-            const int row = abs(kap * (v == 0 ? I.w1 : I.w1 - n) + d - (kap - 1));
-            c_s[idx] = row < N ? tab[row * N + c] : T(0);   // rows >= N belong to unused offsets
-        }
-        __syncthreads();
-
-        for (int b = threadIdx.x; b < n * n; b += blockDim.x) {
-            const int w2 = b / n, k2 = b % n, l2 = (k2 - w2 + n) % n;
-            const int D2 = k2 - l2;
-            if constexpr (KAP > 0) {
-                constexpr int WK = 2 * KAP - 1;
-                T cw[WK][WK];
-                int cur_v = -1;
-                for (int s = 0; s < S; ++s) {
-                    const int k1 = k1_0 + s;
-                    const int v = k1 >= I.w1 ? 0 : 1;          // block-row offset w1 or w1 - n
-                    if (v != cur_v) {
-                        const T* cv = c_s + v * WK * N;
+        // cost windows of this wrapped block-row diagonal, built once per item
+        if constexpr (KAP > 0) {
+            constexpr int WK = 2 * KAP - 1;
+            for (int vd = threadIdx.x; vd < 2 * (2 * n - 1); vd += blockDim.x) {
+                const int v = vd / (2 * n - 1), dd = vd % (2 * n - 1);
+                const int D1 = KAP * (v == 0 ? w1 : w1 - n), D2 = KAP * (dd - (n - 1));
+                T* dst = win_s + vd * CBAR_WPAD;
 #pragma unroll
-                        for (int d1 = 0; d1 < WK; ++d1)
+                for (int d1 = 0; d1 < WK; ++d1) {
+                    const int row = abs(D1 + d1 - (KAP - 1));
+                    const T* trow = tab + row * N;
 #pragma unroll
-                            for (int d2 = 0; d2 < WK; ++d2)
-                                cw[d1][d2] = cv[d1 * N + abs(KAP * D2 + d2 - (KAP - 1))];
-                        cur_v = v;
-                    }
-                    // inner[a] = sum_b nu[b] c(a - b): every nu value feeds KAP^2
-                    // independent accumulators (summation order per accumulator
-                    // is b1, b2); then acc = sum_a mu[a] inner[a] in order a1, a2
-                    T inner[KAP][KAP];
-#pragma unroll
-                    for (int a1 = 0; a1 < KAP; ++a1)
-#pragma unroll
-                        for (int a2 = 0; a2 < KAP; ++a2) inner[a1][a2] = T(0);
-#pragma unroll
-                    for (int b1 = 0; b1 < KAP; ++b1) {
-                        T nrow[KAP];
-                        const T* np_ = nu_s + (s * KAP + b1) * N + l2 * KAP;
-                        if constexpr (KAP == 4 && sizeof(T) == 4) {
-                            const float4 v = *reinterpret_cast<const float4*>(np_);
-                            nrow[0] = v.x; nrow[1] = v.y; nrow[2] = v.z; nrow[3] = v.w;
-                        } else {
-#pragma unroll
-                            for (int b2 = 0; b2 < KAP; ++b2) nrow[b2] = np_[b2];
-                        }
-#pragma unroll
-                        for (int b2 = 0; b2 < KAP; ++b2)
-#pragma unroll
-                            for (int a1 = 0; a1 < KAP; ++a1)
-#pragma unroll
-                                for (int a2 = 0; a2 < KAP; ++a2)
-                                    inner[a1][a2] = fma_ru(nrow[b2], cw[a1 - b1 + KAP - 1][a2 - b2 + KAP - 1],
-                                                           inner[a1][a2]);
-                    }
-                    T acc = T(0);
-#pragma unroll
-                    for (int a1 = 0; a1 < KAP; ++a1) {
-                        T mrow[KAP];
-                        const T* mp_ = mu_s + (s * KAP + a1) * N + k2 * KAP;
-                        if constexpr (KAP == 4 && sizeof(T) == 4) {
-                            const float4 v = *reinterpret_cast<const float4*>(mp_);
-                            mrow[0] = v.x; mrow[1] = v.y; mrow[2] = v.z; mrow[3] = v.w;
-                        } else {
-#pragma unroll
-                            for (int a2 = 0; a2 < KAP; ++a2) mrow[a2] = mp_[a2];
-                        }
-#pragma unroll
-                        for (int a2 = 0; a2 < KAP; ++a2) acc = fma_ru(mrow[a2], inner[a1][a2], acc);
-                    }
-                    const int l1 = (k1 - I.w1 + n) % n;
-                    const int k = k1 * n + k2, l = l1 * n + l2;
-                    T outv;
-                    bool ok;
-                    if constexpr (sizeof(T) == 4) {
-                        const float rk = P.mu_rinv32[k], rl = P.nu_rinv32[l];
-                        ok = rk > 0.f && rl > 0.f;
-                        outv = ok ? __fmul_ru(__fmul_ru(acc, rk), rl) : T(0);
-                    } else {
-                        const double rk = P.mu_rinv[k], rl = P.nu_rinv[l];
-                        ok = rk > 0.0 && rl > 0.0;
-                        outv = ok ? __dmul_ru(__dmul_ru(acc, rk), rl) : T(0);
-                    }
-                    if (!ok) {
-                        double mean = 0.0;
-#pragma unroll
-                        for (int d1 = 0; d1 < WK; ++d1)
-#pragma unroll
-                            for (int d2 = 0; d2 < WK; ++d2)
-                                mean = __fma_ru((double)((KAP - abs(d1 - (KAP - 1))) * (KAP - abs(d2 - (KAP - 1)))),
-                                                (double)cw[d1][d2], mean);
-                        mean = __ddiv_ru(mean, (double)(KAP * KAP * KAP * KAP));
-                        P.cbar[(size_t)k * M + l] = cbar_special<T>(P, k, l, (double)acc, mean);
-                        outv = __int_as_float(0x7fc00000);        // NaN: already written
-                    }
-                    out_s[(s * n + k2) * n + l2] = outv;
+                    for (int d2 = 0; d2 < WK; ++d2)
+                        dst[d1 * WK + d2] = row < N ? trow[abs(D2 + d2 - (KAP - 1))] : T(0);
                 }
-            } else {
-                for (int s = 0; s < S; ++s) {
-                    const int k1 = k1_0 + s;
-                    const int v = k1 >= I.w1 ? 0 : 1;
-                    const T* cv = c_s + v * W * N;
-                    T acc = T(0);
-                    double mean = 0.0;
-                    for (int a1 = 0; a1 < kap; ++a1)
-                        for (int a2 = 0; a2 < kap; ++a2) {
-                            const T mv = mu_s[(s * kap + a1) * N + k2 * kap + a2];
-                            T inner = T(0);
-                            for (int b1 = 0; b1 < kap; ++b1) {
-                                const T* crow = cv + (a1 - b1 + kap - 1) * N;
-                                for (int b2 = 0; b2 < kap; ++b2)
-                                    inner = fma_ru(nu_s[(s * kap + b1) * N + l2 * kap + b2],
-                                                   crow[abs(kap * D2 + a2 - b2)], inner);
+            }
+        } else {
+            for (int idx = threadIdx.x; idx < 2 * W * N; idx += blockDim.x) {
+                const int v = idx / (W * N), d = (idx / N) % W, c = idx % N;
+                const int row = abs(kap * (v == 0 ? w1 : w1 - n) + d - (kap - 1));
+                win_s[idx] = row < N ? tab[row * N + c] : T(0);
+            }
+        }
+        // this thread's block-pair slots
+        const int n_slots = (n * n + blockDim.x - 1) / blockDim.x;
+        int sk2[CBAR_MAX_SLOTS], sl2[CBAR_MAX_SLOTS];
+#pragma unroll
+        for (int j = 0; j < CBAR_MAX_SLOTS; ++j) {
+            const int b = threadIdx.x + j * blockDim.x;
+            const int w2 = b / n, k2 = b - w2 * n;
+            int l2 = k2 - w2;
+            if (l2 < 0) l2 += n;
+            sk2[j] = (j < n_slots && b < n * n) ? k2 : -1;
+            sl2[j] = l2;
+        }
+        for (int k1_0 = 0; k1_0 < n; k1_0 += CBAR_S) {
+            const int S = min(CBAR_S, n - k1_0);
+            __syncthreads();        // previous chunk's results are written out
+            // stage rows of mu (block rows k1) and nu (block rows l1 = k1 - w1 mod n)
+            const int rowlen = kap * N;
+            for (int s = 0; s < S; ++s) {
+                const int k1 = k1_0 + s;
+                int l1 = k1 - w1;
+                if (l1 < 0) l1 += n;
+                const T* msrc = mu_up + (size_t)k1 * rowlen;
+                const T* nsrc = nu_up + (size_t)l1 * rowlen;
+                for (int c = threadIdx.x; c < rowlen; c += blockDim.x) {
+                    mu_s[s * rowlen + c] = msrc[c];
+                    nu_s[s * rowlen + c] = nsrc[c];
+                }
+                if (threadIdx.x < n) {
+                    if constexpr (sizeof(T) == 4) {
+                        rk_s[s * n + threadIdx.x] = P.mu_rinv32[k1 * n + threadIdx.x];
+                        rl_s[s * n + threadIdx.x] = P.nu_rinv32[l1 * n + threadIdx.x];
+                    } else {
+                        rk_s[s * n + threadIdx.x] = P.mu_rinv[k1 * n + threadIdx.x];
+                        rl_s[s * n + threadIdx.x] = P.nu_rinv[l1 * n + threadIdx.x];
+                    }
+                }
+            }
+            __syncthreads();
+            for (int j = 0; j < n_slots; ++j) {
+                const int k2 = sk2[j], l2 = sl2[j];
+                if (k2 < 0) continue;
+                const int D2 = k2 - l2;
+                if constexpr (KAP > 0) {
+                    constexpr int WK = 2 * KAP - 1;
+                    T cw[WK * WK];
+                    int cur_v = -1;
+                    for (int s = 0; s < S; ++s) {
+                        const int k1 = k1_0 + s;
+                        const int v = k1 >= w1 ? 0 : 1;          // block-row offset w1 or w1 - n
+                        if (v != cur_v) {
+                            const T* src = win_s + (v * (2 * n - 1) + D2 + n - 1) * CBAR_WPAD;
+                            if constexpr (sizeof(T) == 4 && (WK * WK) % 4 == 1) {
+                                float buf[CBAR_WPAD];
+#pragma unroll
+                                for (int q = 0; q < CBAR_WPAD / 4; ++q)
+                                    *reinterpret_cast<float4*>(buf + 4 * q) = reinterpret_cast<const float4*>(src)[q];
+#pragma unroll
+                                for (int q = 0; q < WK * WK; ++q) cw[q] = buf[q];
+                            } else {
+#pragma unroll
+                                for (int q = 0; q < WK * WK; ++q) cw[q] = src[q];
                             }
-                            acc = fma_ru(mv, inner, acc);
+                            cur_v = v;
                         }
-                    const int l1 = (k1 - I.w1 + n) % n;
-                    const int k = k1 * n + k2, l = l1 * n + l2;
-                    T outv;
-                    bool ok;
-                    if constexpr (sizeof(T) == 4) {
-                        const float rk = P.mu_rinv32[k], rl = P.nu_rinv32[l];
-                        ok = rk > 0.f && rl > 0.f;
-                        outv = ok ? __fmul_ru(__fmul_ru(acc, rk), rl) : T(0);
-                    } else {
-                        const double rk = P.mu_rinv[k], rl = P.nu_rinv[l];
-                        ok = rk > 0.0 && rl > 0.0;
-                        outv = ok ? __dmul_ru(__dmul_ru(acc, rk), rl) : T(0);
+                        // inner[a] = sum_b nu[b] c(a - b): every nu value feeds KAP^2
+                        // independent accumulators (summation order per accumulator
+                        // is b1, b2); then acc = sum_a mu[a] inner[a] in order a1, a2
+                        T inner[KAP][KAP];
+#pragma unroll
+                        for (int a1 = 0; a1 < KAP; ++a1)
+#pragma unroll
+                            for (int a2 = 0; a2 < KAP; ++a2) inner[a1][a2] = T(0);
+#pragma unroll
+                        for (int b1 = 0; b1 < KAP; ++b1) {
+                            T nrow[KAP];
+                            const T* np_ = nu_s + (s * KAP + b1) * N + l2 * KAP;
+                            if constexpr (KAP == 4 && sizeof(T) == 4) {
+                                const float4 v4 = *reinterpret_cast<const float4*>(np_);
+                                nrow[0] = v4.x; nrow[1] = v4.y; nrow[2] = v4.z; nrow[3] = v4.w;
+                            } else {
+#pragma unroll
+                                for (int b2 = 0; b2 < KAP; ++b2) nrow[b2] = np_[b2];
+                            }
+#pragma unroll
+                            for (int b2 = 0; b2 < KAP; ++b2)
+#pragma unroll
+                                for (int a1 = 0; a1 < KAP; ++a1)
+#pragma unroll
+                                    for (int a2 = 0; a2 < KAP; ++a2)
+                                        inner[a1][a2] = fma_ru(nrow[b2], cw[(a1 - b1 + KAP - 1) * WK + a2 - b2 + KAP - 1],
+                                                               inner[a1][a2]);
+                        }
+                        T acc = T(0);
+#pragma unroll
+                        for (int a1 = 0; a1 < KAP; ++a1) {
+                            T mrow[KAP];
+                            const T* mp_ = mu_s + (s * KAP + a1) * N + k2 * KAP;
+                            if constexpr (KAP == 4 && sizeof(T) == 4) {
+                                const float4 v4 = *reinterpret_cast<const float4*>(mp_);
+                                mrow[0] = v4.x; mrow[1] = v4.y; mrow[2] = v4.z; mrow[3] = v4.w;
+                            } else {
+#pragma unroll
+                                for (int a2 = 0; a2 < KAP; ++a2) mrow[a2] = mp_[a2];
+                            }
+#pragma unroll
+                            for (int a2 = 0; a2 < KAP; ++a2) acc = fma_ru(mrow[a2], inner[a1][a2], acc);
+                        }
+                        const T rk = rk_s[s * n + k2], rl = rl_s[s * n + l2];
+                        T outv;
+                        if (rk > T(0) && rl > T(0)) {
+                            outv = mul_ru(mul_ru(acc, rk), rl);
+                        } else {
+                            int l1 = k1 - w1;
+                            if (l1 < 0) l1 += n;
+                            const int k = k1 * n + k2, l = l1 * n + l2;
+                            double mean = 0.0;
+#pragma unroll
+                            for (int d1 = 0; d1 < WK; ++d1)
+#pragma unroll
+                                for (int d2 = 0; d2 < WK; ++d2)
+                                    mean = __fma_ru((double)((KAP - abs(d1 - (KAP - 1))) * (KAP - abs(d2 - (KAP - 1)))),
+                                                    (double)cw[d1 * WK + d2], mean);
+                            mean = __ddiv_ru(mean, (double)(KAP * KAP * KAP * KAP));
+                            cbar[(size_t)k * M + l] = cbar_special<T>(P, k, l, (double)acc, mean);
+                            outv = sizeof(T) == 4 ? (T)__int_as_float(0x7fc00000) : (T)__longlong_as_double(0x7ff8000000000000LL);
+                        }
+                        out_s[(s * n + k2) * n + l2] = outv;
                     }
-                    if (!ok) {
+                } else {
+                    for (int s = 0; s < S; ++s) {
+                        const int k1 = k1_0 + s;
+                        const int v = k1 >= w1 ? 0 : 1;
+                        const T* cv = win_s + v * W * N;
+                        T acc = T(0);
+                        double mean = 0.0;
                         for (int a1 = 0; a1 < kap; ++a1)
-                            for (int b1 = 0; b1 < kap; ++b1)
-                                for (int a2 = 0; a2 < kap; ++a2)
+                            for (int a2 = 0; a2 < kap; ++a2) {
+                                const T mv = mu_s[(s * kap + a1) * N + k2 * kap + a2];
+                                T inner = T(0);
+                                for (int b1 = 0; b1 < kap; ++b1) {
+                                    const T* crow = cv + (a1 - b1 + kap - 1) * N;
                                     for (int b2 = 0; b2 < kap; ++b2)
-                                        mean = __dadd_ru(mean, (double)cv[(a1 - b1 + kap - 1) * N +
-                                                                          abs(kap * D2 + a2 - b2)]);
-                        mean = __ddiv_ru(mean, (double)kap * kap * kap * kap);
-                        P.cbar[(size_t)k * M + l] = cbar_special<T>(P, k, l, (double)acc, mean);
-                        outv = sizeof(T) == 4 ? (T)__int_as_float(0x7fc00000) : (T)__longlong_as_double(0x7ff8000000000000LL);
+                                        inner = fma_ru(nu_s[(s * kap + b1) * N + l2 * kap + b2],
+                                                       crow[abs(kap * D2 + a2 - b2)], inner);
+                                }
+                                acc = fma_ru(mv, inner, acc);
+                            }
+                        const T rk = rk_s[s * n + k2], rl = rl_s[s * n + l2];
+                        T outv;
+                        if (rk > T(0) && rl > T(0)) {
+                            outv = mul_ru(mul_ru(acc, rk), rl);
+                        } else {
+                            int l1 = k1 - w1;
+                            if (l1 < 0) l1 += n;
+                            const int k = k1 * n + k2, l = l1 * n + l2;
+                            for (int a1 = 0; a1 < kap; ++a1)
+                                for (int b1 = 0; b1 < kap; ++b1)
+                                    for (int a2 = 0; a2 < kap; ++a2)
+                                        for (int b2 = 0; b2 < kap; ++b2)
+                                            mean = __dadd_ru(mean, (double)cv[(a1 - b1 + kap - 1) * N +
+                                                                              abs(kap * D2 + a2 - b2)]);
+                            mean = __ddiv_ru(mean, (double)kap * kap * kap * kap);
+                            cbar[(size_t)k * M + l] = cbar_special<T>(P, k, l, (double)acc, mean);
+                            outv = sizeof(T) == 4 ? (T)__int_as_float(0x7fc00000) : (T)__longlong_as_double(0x7ff8000000000000LL);
+                        }
+                        out_s[(s * n + k2) * n + l2] = outv;
                     }
-                    out_s[(s * n + k2) * n + l2] = outv;
                 }
             }
-        }
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < S * n * n; idx += blockDim.x) {
-            const int s = idx / (n * n), k2 = (idx / n) % n, l2 = idx % n;
-            const T v = out_s[idx];
-            if (v == v) {                                          // NaN marks a direct write
-                const int k1 = k1_0 + s, l1 = (k1 - I.w1 + n) % n;
-                P.cbar[(size_t)(k1 * n + k2) * M + l1 * n + l2] = (double)v;
+            __syncthreads();
+            // write the chunk: for each (s, k2) a contiguous row segment of n entries
+            for (int rowid = threadIdx.x / n; rowid < S * n; rowid += blockDim.x / n) {
+                const int s = rowid / n, k2 = rowid - s * n, l2 = threadIdx.x % n;
+                const int k1 = k1_0 + s;
+                int l1 = k1 - w1;
+                if (l1 < 0) l1 += n;
+                const T v = out_s[rowid * n + l2];
+                if (v == v)                                          // NaN marks a direct write
+                    cbar[(size_t)(k1 * n + k2) * M + l1 * n + l2] = (double)v;
             }
         }
-        __syncthreads();
     }
 }
 
-static size_t cbar_smem(size_t tsz, int kap, int n, int N) {
-    return tsz * ((size_t)2 * CBAR_S * kap * N + (size_t)2 * (2 * kap - 1) * N + (size_t)CBAR_S * n * n);
+static size_t cbar_smem(size_t tsz, int kap, int n, int N, bool windows) {
+    const size_t win = windows ? (size_t)2 * (2 * n - 1) * CBAR_WPAD : (size_t)2 * (2 * kap - 1) * N;
+    return tsz * ((size_t)2 * CBAR_S * kap * N + win + (size_t)CBAR_S * n * n + (size_t)2 * CBAR_S * n);
 }
 
 template <typename T>
 static int cbar_dispatch(const PairDev* pairs_d, const CbarItem* items, int n_items, int kappa_code,
-                         int n_max, int N_max, cudaStream_t stream) {
+                         int n_max, int N_max, int variant, cudaStream_t stream) {
     const int kmax = kappa_code > 0 ? kappa_code : -kappa_code;
-    const size_t smem = cbar_smem(sizeof(T), kmax, n_max, N_max);
+    const bool windows = kappa_code == 1 || kappa_code == 2 || kappa_code == 4;
+    const size_t smem = cbar_smem(sizeof(T), kmax, n_max, N_max, windows);
     if (smem > 227 * 1024) return QWB_ERR_UNSUPPORTED;
     auto run = [&](auto kern) -> int {
         QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -361,21 +421,23 @@ static int cbar_dispatch(const PairDev* pairs_d, const CbarItem* items, int n_it
         QWB_LAUNCHED();
         return QWB_OK;
     };
+    // variant 0: register budget for two CTAs per SM; 1: for three CTAs per SM
+    constexpr int MB = sizeof(T) == 4 ? 3 : 1;
     switch (kappa_code) {   // positive: every pair of the launch has this kappa
-        case 1: return run(cbar_kernel<T, 1>);
-        case 2: return run(cbar_kernel<T, 2>);
-        case 4: return run(cbar_kernel<T, 4>);
-        default: return run(cbar_kernel<T, 0>);
+        case 1: return run(cbar_kernel<T, 1, 2>);
+        case 2: return run(cbar_kernel<T, 2, 2>);
+        case 4: return variant == 1 ? run(cbar_kernel<T, 4, MB>) : run(cbar_kernel<T, 4, 2>);
+        default: return run(cbar_kernel<T, 0, 2>);
     }
 }
 
 int launch_cbar(const PairDev* pairs_d, const CbarItem* items, int n_items, int kappa_code,
-                int n_max, int N_max, bool f64, cudaStream_t stream) {
+                int n_max, int N_max, bool f64, cudaStream_t stream, int variant) {
     if (n_items <= 0) return QWB_OK;
     // kappa_code: the common kappa (1, 2, 4 use unrolled kernels) or -K for a
     // launch whose pairs differ in kappa or use another kappa (largest K)
-    if (f64) return cbar_dispatch<double>(pairs_d, items, n_items, kappa_code, n_max, N_max, stream);
-    return cbar_dispatch<float>(pairs_d, items, n_items, kappa_code, n_max, N_max, stream);
+    if (f64) return cbar_dispatch<double>(pairs_d, items, n_items, kappa_code, n_max, N_max, variant, stream);
+    return cbar_dispatch<float>(pairs_d, items, n_items, kappa_code, n_max, N_max, variant, stream);
 }
 
 // --------------------------------------------------------------------------
@@ -812,7 +874,7 @@ __device__ __forceinline__ void sub_rd_x2(unsigned long long a, unsigned long lo
     asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(d));
 }
 
-template <typename T, int R, int TC, bool P2>
+template <typename T, int R, int TC, bool P2, bool PACKED>
 __global__ void __launch_bounds__(256)
 ctransform_kernel(const PairDev* __restrict__ pairs, const CtItem* __restrict__ items,
                   int n_items, int phase) {
@@ -829,12 +891,11 @@ ctransform_kernel(const PairDev* __restrict__ pairs, const CtItem* __restrict__ 
         const T* hsrc = h + (size_t)I.in_row0 * N;
         for (int k = threadIdx.x; k < nin; k += blockDim.x) hs[k] = hsrc[k];
         __syncthreads();
-        const int o = I.out0 + threadIdx.x * R;
-        const bool active = o < m;
-        T mins[R];
+        const int o_end = min(I.out0 + CT_TILE, m);
+        for (int o = I.out0 + threadIdx.x * R; o < o_end; o += blockDim.x * R) {
+            T mins[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) mins[r] = pos_inf<T>();
-        if (active) {
+            for (int r = 0; r < R; ++r) mins[r] = pos_inf<T>();
             const int j1 = o / N, j2 = o % N;
             const T* tab = reinterpret_cast<const T*>(P.ctab_lo);
             for (int c0 = 0; c0 < N; c0 += TC) {
@@ -862,7 +923,7 @@ ctransform_kernel(const PairDev* __restrict__ pairs, const CtItem* __restrict__ 
                     const T* hrow = hs + r1 * N + c0;
 #pragma unroll
                     for (int s = 0; s < TC; ++s) fv[s] = hrow[s];
-                    if constexpr (TC % 2 == 0 && sizeof(T) == 4) {
+                    if constexpr (PACKED && TC % 2 == 0 && sizeof(T) == 4) {
                         // two candidates per packed subtraction: (q_e, q_e+1) - (f_s, f_s+1)
                         // rounded toward -inf, then one 3-input min
                         unsigned long long qa[(NQ + 1) / 2], qb[NQ / 2], fp[TC / 2];
@@ -918,10 +979,10 @@ int ct_pick_r(int N, int want) {
     return 1;
 }
 
-template <typename T, int R, int TC, bool P2>
+template <typename T, int R, int TC, bool P2, bool PK>
 static int ct_launch_rt(const PairDev* pairs_d, const CtItem* items, int n_items, int phase,
                         int threads, int in_rows, int N_max, int grid_cap, cudaStream_t stream) {
-    auto kern = ctransform_kernel<T, R, TC, P2>;
+    auto kern = ctransform_kernel<T, R, TC, P2, PK>;
     const size_t smem = sizeof(T) * (size_t)in_rows * N_max;
     if (smem > 227 * 1024) return QWB_ERR_UNSUPPORTED;
     QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -940,11 +1001,13 @@ static int ct_launch_rt(const PairDev* pairs_d, const CtItem* items, int n_items
 template <typename T, bool P2>
 static int ct_launch_t(const PairDev* pairs_d, const CtItem* items, int n_items, int phase,
                        const CtConfig& c, int N_max, int grid_cap, cudaStream_t stream) {
-#define QWB_CT(RR, TT)                                                                     \
-    if (c.R == RR && c.TC == TT)                                                           \
-        return ct_launch_rt<T, RR, TT, P2>(pairs_d, items, n_items, phase, c.threads,      \
-                                           c.in_rows, N_max, grid_cap, stream);
-    QWB_CT(1, 1) QWB_CT(2, 2) QWB_CT(4, 4) QWB_CT(8, 8) QWB_CT(16, 8) QWB_CT(16, 16) QWB_CT(8, 16)
+#define QWB_CT(RR, TT, PK)                                                                 \
+    if (c.R == RR && c.TC == TT && c.packed == PK)                                         \
+        return ct_launch_rt<T, RR, TT, P2, PK>(pairs_d, items, n_items, phase, c.threads,  \
+                                               c.in_rows, N_max, grid_cap, stream);
+    QWB_CT(1, 1, false) QWB_CT(2, 2, false) QWB_CT(4, 4, false) QWB_CT(8, 8, false)
+    QWB_CT(16, 8, false) QWB_CT(16, 16, false) QWB_CT(8, 16, false)
+    QWB_CT(8, 8, true) QWB_CT(16, 8, true) QWB_CT(16, 16, true)
 #undef QWB_CT
     return QWB_ERR_UNSUPPORTED;
 }

@@ -55,8 +55,9 @@ struct PairOut {
     int sweeps_done, pad;
 };
 
-struct CbarItem { int pair, w1, seg, pad; };   // wrapped block-row diagonal w1, rows seg*S..
+struct CbarItem { int pair, w1, seg, pad; };   // wrapped block-row diagonal w1 (seg unused)
 struct CtItem { int pair, out0, in_row0, in_rows; };
+constexpr int CT_TILE = 4096;   // outputs per c-transform work item (a multiple of every R)
 struct PixItem { int pair, start; };
 
 // Launch configuration of the c-transform (chosen by the autotuner).
@@ -66,6 +67,7 @@ struct CtConfig {
     int threads = 256;  // threads per CTA
     int in_rows = 4;    // input rows per work item (split of the min)
     bool p2 = false;    // every pair of the launch has p = 2 (exact integer costs)
+    bool packed = false;  // FP32: packed f32x2 subtraction of two candidates
 };
 
 // Launchers.  All enqueue on `stream` and return a qwb status.
@@ -74,7 +76,7 @@ int launch_prepare(const PairDev* pairs_d, PairOut* outs_d, const PixItem* items
                    bool f64, cudaStream_t stream);
 constexpr int CBAR_S = 4;   // block rows per C-bar work item
 int launch_cbar(const PairDev* pairs_d, const CbarItem* items, int n_items, int kappa_max,
-                int n_max, int N_max, bool f64, cudaStream_t stream);
+                int n_max, int N_max, bool f64, cudaStream_t stream, int variant = 0);
 int launch_primal(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs,
                   int M_max, int nnz_max, bool f64, cudaStream_t stream);
 int launch_upsample(const PairDev* pairs_d, PairOut* outs_d, const PixItem* items, int n_items,
