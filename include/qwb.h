@@ -193,6 +193,23 @@ int qwb_dual_upscale_ctransform(qwb_ctx* ctx, const qwb_problem* prob, const dou
 int qwb_ctransform(qwb_ctx* ctx, int32_t N, double p, const double* h_d, double* out_d,
                    qwb_prec prec, void* stream);
 
+/* The same lazy c-transform (MIXED precision: h rounded up to FP32, result
+ * rounded down, widened to FP64) for callers that cannot allocate device
+ * memory when they need it -- for instance code running under a frozen or
+ * exhausted memory pool, or a plugin whose host process owns every device
+ * byte.  This call allocates nothing: its scratch (FP32 copies, cost table,
+ * launch plan) lives in one static device array of about 1 MiB that every GPU
+ * loading the library holds until the process exits.  The paper has no
+ * counterpart; it is a deployment variant of qwb_ctransform.
+ *   N <= 256 (QWB_ERR_UNSUPPORTED beyond); h_d, out_d: N*N FP64 device.
+ *   Every call shares the static array and rewrites what it reads, so
+ *   calls whose GPU work overlaps (other streams, concurrent host threads)
+ *   race and corrupt each other: serialise them.  The first call on a
+ *   device looks up the array's address (cudaGetSymbolAddress); make it
+ *   before any stream capture.  Asynchronous on `stream`.
+ * Errors: INVALID_ARG (null pointer, p < 1), UNSUPPORTED (N > 256), CUDA. */
+int qwb_ctransform_noalloc(int32_t N, double p, const double* h_d, double* out_d, void* stream);
+
 /* Gradient of the lower bound with respect to the source measure along the
  * simplex (derived from the proposition of Sec. 3.5: for fixed potentials
  * lb_p = <f, mu> + <g, nu> is linear in mu):
