@@ -655,15 +655,15 @@ static int run_pass(qwb_batch* b, int kind, bool batched, cudaStream_t s) {
 }
 
 // ---- host exact solves ---------------------------------------------------
-static void centre_cost(const qwb_problem& pr, std::vector<double>& C) {
-    const int nn = pr.N / pr.kappa, M = nn * nn;
-    C.resize((size_t)M * M);
-    for (int k = 0; k < M; ++k)
-        for (int l = 0; l < M; ++l) {
-            const double d1 = (double)pr.kappa * (k / nn - l / nn);
-            const double d2 = (double)pr.kappa * (k % nn - l % nn);
-            const double s = d1 * d1 + d2 * d2;
-            C[(size_t)k * M + l] = pr.p == 2.0 ? s : (pr.p == 1.0 ? std::sqrt(s) : std::pow(s, 0.5 * pr.p));
+// C~ on the coarse grid as a table over block offsets: (kappa |dk|)^p.
+static void centre_cost_table(const qwb_problem& pr, std::vector<double>& tab) {
+    const int nn = pr.N / pr.kappa;
+    tab.resize((size_t)nn * nn);
+    for (int d1 = 0; d1 < nn; ++d1)
+        for (int d2 = 0; d2 < nn; ++d2) {
+            const double x = (double)pr.kappa * d1, y = (double)pr.kappa * d2;
+            const double s = x * x + y * y;
+            tab[(size_t)d1 * nn + d2] = pr.p == 2.0 ? s : (pr.p == 1.0 ? std::sqrt(s) : std::pow(s, 0.5 * pr.p));
         }
 }
 
@@ -674,9 +674,10 @@ static int solve_pair(qwb_batch* b, int t) {
     const double* nc = b->nu_c_h.data() + b->mc_off[t];
     // (1) C~ problem: plan and potential for the primal and dual passes
     std::vector<double> Ct;
-    centre_cost(pr, Ct);
+    centre_cost_table(pr, Ct);
     NSSolution sol;
-    int st = network_simplex(M, M, Ct.data(), mc, nc, sol);
+    NSBasis basis;
+    int st = network_simplex_grid(pr.N / pr.kappa, Ct.data(), mc, nc, sol, -1, &basis);
     if (st) return st;
     const PlanLayout L = plan_layout(M);
     char* ph = b->plan_h + b->plan_off[t];
@@ -705,9 +706,10 @@ static int solve_pair(qwb_batch* b, int t) {
         b->ubw_p[t] = HUGE_VAL; b->ubw[t] = HUGE_VAL;
         return QWB_OK;
     }
+    // same supplies: the C~ optimum is a feasible starting basis
     NSSolution sb;
     const double* Cb = b->cbar_h + b->cbar_h_off[t];
-    st = network_simplex(M, M, Cb, mc, nc, sb);
+    st = network_simplex(M, M, Cb, mc, nc, sb, -1, &basis);
     if (st) return st;
     double L_sum = 0.0;
     const int nnzb = (int)sb.col.size();

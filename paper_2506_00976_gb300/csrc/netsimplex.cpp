@@ -1,4 +1,4 @@
-// netsimplex.cpp -- primal network simplex for the dense coarse transport LP.
+// netsimplex.cpp -- primal network simplex for the coarse transport LPs.
 //
 // Solves min <pi, C> subject to pi 1 = a, pi^T 1 = b, pi >= 0 (Sec. 2.1) and
 // returns an optimal basic plan (at most n_src + n_dst - 1 positive entries,
@@ -7,10 +7,13 @@
 //
 // Design (textbook primal network simplex, written for this library):
 //   * graph: sources 0..n-1, sinks n..n+m-1, an artificial root n+m;
-//     real arc a = i*m + j (source i -> sink j, cost C[a]) and one artificial
-//     arc per node (source with supply -> root, root -> other nodes) with a
-//     cost BIG above any path cost, so that the all-artificial star is a
-//     strongly feasible starting tree;
+//     real arc a = i*m + j (source i -> sink j) and one artificial arc per
+//     node (source with supply -> root, root -> other nodes) with a cost BIG
+//     above any path cost, so that the all-artificial star is a strongly
+//     feasible starting tree;
+//   * costs come either from a dense matrix (C-bar) or, for the grid centre
+//     cost C~, from a table over block offsets (|dk1|, |dk2|), so that pricing
+//     does not stream an M x M matrix;
 //   * spanning tree stored as parent pointers with doubly linked child
 //     lists; the flow of each tree arc is kept on its child node;
 //   * block-search pricing over the real arcs (block ~ sqrt(#arcs)),
@@ -21,6 +24,9 @@
 //   * after each pivot the re-hung subtree gets its depths and potentials
 //     recomputed from its new parent; potentials are re-centred now and then
 //     so that the artificial cost does not eat their precision;
+//   * a solve can start from the final tree of another solve with the same
+//     supplies (a feasible, strongly feasible basis for any costs): the C-bar
+//     problem starts from the C~ optimum;
 //   * at the end the tree flows are recomputed exactly from the supplies
 //     (leaf elimination) and the potentials are made exactly dual feasible by
 //     one coarse c-transform each way (g = f^c, f = g^c).
@@ -29,16 +35,33 @@
 #include <algorithm>
 #include <cmath>
 #include <limits>
+#include <type_traits>
 
 #include "../../include/qwb.h"
 
 namespace qwb {
 namespace {
 
+// Cost of real arc (i, j): dense matrix or grid block-offset table.
+struct DenseCost {
+    const double* C;
+    int m;
+    double operator()(int i, int j) const { return C[(int64_t)i * m + j]; }
+};
+struct GridCost {
+    const double* tab;   // ns x ns, tab[|dk1| * ns + |dk2|]
+    int ns;
+    double operator()(int i, int j) const {
+        const int d1 = std::abs(i / ns - j / ns), d2 = std::abs(i % ns - j % ns);
+        return tab[d1 * ns + d2];
+    }
+};
+
+template <typename Cost>
 struct Solver {
     int n = 0, m = 0, V = 0, root = 0;
     int64_t NM = 0;
-    const double* C = nullptr;
+    Cost cst;
     double BIG = 0.0, eps = 0.0;
     std::vector<double> supply;
     std::vector<signed char> art_up;  // artificial arc of node v: 1 = v -> root
@@ -58,7 +81,7 @@ struct Solver {
         int v = (int)(a - NM);
         return art_up[v] ? v : root;
     }
-    double cost(int64_t a) const { return a < NM ? C[a] : BIG; }
+    double cost(int64_t a) const { return a < NM ? cst((int)(a / m), (int)(a % m)) : BIG; }
 
     void add_child(int p, int c) {
         parent[c] = p;
@@ -96,14 +119,11 @@ struct Solver {
         for (int v = 0; v < n + m; ++v) s += pot[v];
         s /= (double)(n + m);
         for (int v = 0; v < V; ++v) pot[v] -= s;
-        // recompute from the root for accuracy
         for (int c = first_child[root]; c >= 0; c = next_sib[c]) refresh_subtree(c);
     }
 
-    void init(int n_, int m_, const double* C_, const double* a, const double* b) {
-        n = n_; m = m_; V = n + m + 1; root = n + m; NM = (int64_t)n * m; C = C_;
-        double maxc = 0.0;
-        for (int64_t k = 0; k < NM; ++k) maxc = std::max(maxc, C[k]);
+    void init_common(int n_, int m_, const double* a, const double* b, double maxc) {
+        n = n_; m = m_; V = n + m + 1; root = n + m; NM = (int64_t)n * m;
         BIG = (double)(V + 1) * (maxc + 1.0);
         eps = 1e-12 * (maxc + 1.0);
         supply.assign(V, 0.0);
@@ -112,21 +132,35 @@ struct Solver {
         for (int j = 0; j < m; ++j) { supply[n + j] = -b[j]; sb += b[j]; }
         supply[root] = sb - sa;
         art_up.assign(V, 0);
+        for (int v = 0; v < n; ++v) art_up[v] = a[v] > 0.0 ? 1 : 0;
         parent.assign(V, -1); depth.assign(V, 0);
         first_child.assign(V, -1); next_sib.assign(V, -1); prev_sib.assign(V, -1);
         pred.assign(V, -1); up.assign(V, 0); flow.assign(V, 0.0); pot.assign(V, 0.0);
+        block = std::max<int64_t>(64, (int64_t)std::sqrt((double)NM));
+        price_pos = 0;
+    }
+
+    // the all-artificial star
+    void init_star(const double* a, const double* b) {
         for (int v = 0; v < n + m; ++v) {
-            const bool src_pos = (v < n) && (a[v] > 0.0);
-            art_up[v] = src_pos ? 1 : 0;
             add_child(root, v);
             depth[v] = 1;
             pred[v] = NM + v;
             up[v] = art_up[v];
             flow[v] = (v < n) ? a[v] : b[v - n];
-            pot[v] = src_pos ? BIG : -BIG;
+            pot[v] = art_up[v] ? BIG : -BIG;
         }
-        block = std::max<int64_t>(64, (int64_t)std::sqrt((double)NM));
-        price_pos = 0;
+    }
+
+    // a previous final tree (same supplies, any costs)
+    void init_basis(const NSBasis& B) {
+        for (int v = 0; v < n + m; ++v) {
+            pred[v] = B.pred[v];
+            up[v] = B.up[v];
+        }
+        for (int v = 0; v < n + m; ++v) add_child(B.parent[v], v);
+        for (int c = first_child[root]; c >= 0; c = next_sib[c]) refresh_subtree(c);
+        recompute_flows();
     }
 
     // Block-search pricing: the most negative reduced cost in the first block
@@ -139,10 +173,31 @@ struct Solver {
             double best = -eps;
             int64_t best_a = -1;
             int i = (int)(pos / m), j = (int)(pos % m);
-            for (int64_t a = pos; a < end; ++a) {
-                const double rc = C[a] - pot[i] + pot[n + j];
-                if (rc < best) { best = rc; best_a = a; }
-                if (++j == m) { j = 0; ++i; }
+            double pi = pot[i];
+            if constexpr (std::is_same<Cost, GridCost>::value) {
+                // grid costs: walk (j1, j2) incrementally, one table row per j1
+                const int ns = cst.ns;
+                int i1 = i / ns, i2 = i % ns, j1 = j / ns, j2 = j % ns;
+                const double* trow = cst.tab + std::abs(i1 - j1) * ns;
+                for (int64_t a = pos; a < end; ++a) {
+                    const double rc = trow[std::abs(i2 - j2)] - pi + pot[n + j];
+                    if (rc < best) { best = rc; best_a = a; }
+                    ++j;
+                    if (++j2 == ns) {
+                        j2 = 0;
+                        if (++j1 == ns) {
+                            j1 = 0; j = 0; ++i;
+                            if (i < n) { pi = pot[i]; i1 = i / ns; i2 = i % ns; }
+                        }
+                        trow = cst.tab + std::abs(i1 - j1) * ns;
+                    }
+                }
+            } else {
+                for (int64_t a = pos; a < end; ++a) {
+                    const double rc = cst(i, j) - pi + pot[n + j];
+                    if (rc < best) { best = rc; best_a = a; }
+                    if (++j == m) { j = 0; ++i; if (i < n) pi = pot[i]; }
+                }
             }
             scanned += end - pos;
             pos = (end == NM) ? 0 : end;
@@ -158,7 +213,6 @@ struct Solver {
     void pivot(int64_t e) {
         const int k = tail(e);
         const int l = n + (int)(e % m);   // entering arcs are real arcs
-        // apex of the cycle
         int u = k, w = l;
         while (u != w) {
             if (depth[u] > depth[w]) u = parent[u];
@@ -166,13 +220,11 @@ struct Solver {
             else { u = parent[u]; w = parent[w]; }
         }
         const int apex = u;
-        // delta = min flow over arcs whose flow decreases along the cycle
         double delta = std::numeric_limits<double>::infinity();
         for (int v = l; v != apex; v = parent[v])      // traversed upward
             if (!up[v]) delta = std::min(delta, flow[v]);
         for (int v = k; v != apex; v = parent[v])      // traversed downward
             if (up[v]) delta = std::min(delta, flow[v]);
-        // leaving arc: last blocking arc from the apex along the orientation
         int q = -1;
         bool on_l_side = false;
         for (int v = l; v != apex; v = parent[v])
@@ -181,10 +233,8 @@ struct Solver {
             for (int v = k; v != apex; v = parent[v])
                 if (up[v] && flow[v] <= delta) { q = v; break; }
         }
-        // flows
         for (int v = l; v != apex; v = parent[v]) flow[v] += up[v] ? delta : -delta;
         for (int v = k; v != apex; v = parent[v]) flow[v] += up[v] ? -delta : delta;
-        // re-hang the subtree of q through the entering arc
         const int e1 = on_l_side ? l : k;
         const int e2 = on_l_side ? k : l;
         path.clear();
@@ -223,7 +273,7 @@ struct Solver {
             for (int c = first_child[v]; c >= 0; c = next_sib[c]) stack.push_back(c);
         }
         std::vector<double> S(supply);
-        for (int idx = V - 1; idx >= 1; --idx) {
+        for (int idx = (int)order.size() - 1; idx >= 1; --idx) {
             const int v = order[idx];
             flow[v] = up[v] ? S[v] : -S[v];
             S[parent[v]] += S[v];
@@ -231,20 +281,16 @@ struct Solver {
     }
 };
 
-}  // namespace
-
-int network_simplex(int32_t n_src, int32_t n_dst, const double* C, const double* a,
-                    const double* b, NSSolution& out, int64_t max_pivots) {
-    if (n_src <= 0 || n_dst <= 0 || !C || !a || !b) return QWB_ERR_INVALID_ARG;
+template <typename Cost>
+int solve(int32_t n_src, int32_t n_dst, Cost cst, double maxc, const double* a, const double* b,
+          NSSolution& out, int64_t max_pivots, const NSBasis* warm, NSBasis* basis_out) {
     const int64_t NM = (int64_t)n_src * n_dst;
-    for (int64_t k = 0; k < NM; ++k)
-        if (!(C[k] >= 0.0) || !std::isfinite(C[k])) return QWB_ERR_INVALID_ARG;
-    for (int i = 0; i < n_src; ++i) if (!(a[i] >= 0.0) || !std::isfinite(a[i])) return QWB_ERR_INVALID_ARG;
-    for (int j = 0; j < n_dst; ++j) if (!(b[j] >= 0.0) || !std::isfinite(b[j])) return QWB_ERR_INVALID_ARG;
     if (max_pivots < 0) max_pivots = 20 * NM + 1000000;
-
-    Solver S;
-    S.init(n_src, n_dst, C, a, b);
+    Solver<Cost> S;
+    S.cst = cst;
+    S.init_common(n_src, n_dst, a, b, maxc);
+    if (warm && warm->valid && (int)warm->parent.size() == n_src + n_dst) S.init_basis(*warm);
+    else S.init_star(a, b);
     int64_t piv = 0;
     const int64_t recentre_every = std::max<int64_t>(256, S.V);
     for (;;) {
@@ -256,12 +302,16 @@ int network_simplex(int32_t n_src, int32_t n_dst, const double* C, const double*
         if (piv % recentre_every == 0) S.recentre();
     }
     S.recompute_flows();
-    // artificial arcs must carry (almost) nothing at an optimum of a feasible problem
     double mass = 0.0;
     for (int i = 0; i < n_src; ++i) mass += a[i];
     for (int v = 0; v < S.n + S.m; ++v)
         if (S.pred[v] >= NM && S.flow[v] > 1e-9 * std::max(1.0, mass)) return QWB_ERR_NOT_CONVERGED;
-
+    if (basis_out) {
+        basis_out->parent.assign(S.parent.begin(), S.parent.end() - 1);
+        basis_out->pred.assign(S.pred.begin(), S.pred.end() - 1);
+        basis_out->up.assign(S.up.begin(), S.up.end() - 1);
+        basis_out->valid = true;
+    }
     // plan (CSR) from the real tree arcs with positive flow
     std::vector<std::vector<std::pair<int, double>>> rows(n_src);
     for (int v = 0; v < S.n + S.m; ++v) {
@@ -277,28 +327,59 @@ int network_simplex(int32_t n_src, int32_t n_dst, const double* C, const double*
         for (auto& cv : rows[i]) {
             out.col.push_back(cv.first);
             out.val.push_back(cv.second);
-            obj += cv.second * C[(int64_t)i * n_dst + cv.first];
+            obj += cv.second * cst(i, cv.first);
         }
         out.rowptr[i + 1] = (int32_t)out.col.size();
     }
     out.obj = obj;
-    // potentials: f_i = pot[i], g_j = -pot[n+j]; then exact dual feasibility
+    // potentials: f_i = pot[i]; then exact dual feasibility by c-transforms
     out.f.assign(n_src, 0.0);
-    out.g.assign(n_dst, 0.0);
+    out.g.assign(n_dst, std::numeric_limits<double>::infinity());
     for (int i = 0; i < n_src; ++i) out.f[i] = S.pot[i];
-    for (int j = 0; j < n_dst; ++j) {
-        double gj = std::numeric_limits<double>::infinity();
-        for (int i = 0; i < n_src; ++i) gj = std::min(gj, C[(int64_t)i * n_dst + j] - out.f[i]);
-        out.g[j] = gj;
-    }
+    for (int i = 0; i < n_src; ++i)
+        for (int j = 0; j < n_dst; ++j) out.g[j] = std::min(out.g[j], cst(i, j) - out.f[i]);
     for (int i = 0; i < n_src; ++i) {
         double fi = std::numeric_limits<double>::infinity();
-        const double* Ci = C + (int64_t)i * n_dst;
-        for (int j = 0; j < n_dst; ++j) fi = std::min(fi, Ci[j] - out.g[j]);
+        for (int j = 0; j < n_dst; ++j) fi = std::min(fi, cst(i, j) - out.g[j]);
         out.f[i] = fi;
     }
     out.pivots = piv;
     return QWB_OK;
+}
+
+bool check_masses(int32_t n_src, int32_t n_dst, const double* a, const double* b) {
+    for (int i = 0; i < n_src; ++i) if (!(a[i] >= 0.0) || !std::isfinite(a[i])) return false;
+    for (int j = 0; j < n_dst; ++j) if (!(b[j] >= 0.0) || !std::isfinite(b[j])) return false;
+    return true;
+}
+
+}  // namespace
+
+int network_simplex(int32_t n_src, int32_t n_dst, const double* C, const double* a,
+                    const double* b, NSSolution& out, int64_t max_pivots, const NSBasis* warm,
+                    NSBasis* basis_out) {
+    if (n_src <= 0 || n_dst <= 0 || !C || !a || !b) return QWB_ERR_INVALID_ARG;
+    const int64_t NM = (int64_t)n_src * n_dst;
+    double maxc = 0.0;
+    for (int64_t k = 0; k < NM; ++k) {
+        if (!(C[k] >= 0.0) || !std::isfinite(C[k])) return QWB_ERR_INVALID_ARG;
+        maxc = std::max(maxc, C[k]);
+    }
+    if (!check_masses(n_src, n_dst, a, b)) return QWB_ERR_INVALID_ARG;
+    return solve(n_src, n_dst, DenseCost{C, n_dst}, maxc, a, b, out, max_pivots, warm, basis_out);
+}
+
+int network_simplex_grid(int32_t n_side, const double* tab, const double* a, const double* b,
+                         NSSolution& out, int64_t max_pivots, NSBasis* basis_out) {
+    if (n_side <= 0 || !tab || !a || !b) return QWB_ERR_INVALID_ARG;
+    double maxc = 0.0;
+    for (int k = 0; k < n_side * n_side; ++k) {
+        if (!(tab[k] >= 0.0) || !std::isfinite(tab[k])) return QWB_ERR_INVALID_ARG;
+        maxc = std::max(maxc, tab[k]);
+    }
+    const int32_t M = n_side * n_side;
+    if (!check_masses(M, M, a, b)) return QWB_ERR_INVALID_ARG;
+    return solve(M, M, GridCost{tab, n_side}, maxc, a, b, out, max_pivots, nullptr, basis_out);
 }
 
 }  // namespace qwb

@@ -17,9 +17,28 @@ struct NSSolution {
     int64_t pivots = 0;
 };
 
+// Final spanning tree of a solve (parent, arc to the parent, its direction per
+// node, the artificial root excluded).  Any basis of a problem with the same
+// supplies is a feasible start for other costs.
+struct NSBasis {
+    std::vector<int> parent;
+    std::vector<int64_t> pred;
+    std::vector<signed char> up;
+    bool valid = false;
+};
+
 // Returns a qwb status code (0 = OK, NOT_CONVERGED when max_pivots is hit).
 // C: n_src x n_dst row-major, non-negative and finite.  a, b: non-negative.
+// warm: optional starting basis from a solve with the same supplies;
+// basis_out: optional final basis.
 int network_simplex(int32_t n_src, int32_t n_dst, const double* C, const double* a,
-                    const double* b, NSSolution& out, int64_t max_pivots = -1);
+                    const double* b, NSSolution& out, int64_t max_pivots = -1,
+                    const NSBasis* warm = nullptr, NSBasis* basis_out = nullptr);
+
+// The same for the grid problem with C_kl = tab[|k1 - l1| * n_side + |k2 - l2|]
+// on an n_side x n_side coarse grid (k = k1 * n_side + k2): the centre cost
+// C~ of Sec. 3.4 / 3.5 without an M x M matrix.
+int network_simplex_grid(int32_t n_side, const double* tab, const double* a, const double* b,
+                         NSSolution& out, int64_t max_pivots = -1, NSBasis* basis_out = nullptr);
 
 }  // namespace qwb
