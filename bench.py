@@ -212,13 +212,11 @@ def run_gpu(args):
     clocks = clk.summary()
     times_p = timed(False, max(1, min(args.steps, 5)), 1)[0] if not args.skip_plain else [float("nan")]
 
+    from paper_2506_00976_gb300 import shard
     ms_b = statistics.mean(times_b)
     ms_p = statistics.mean(times_p)
-    ms_b_max, ms_p_max = ms_b, ms_p
-    if world > 1:
-        tt = torch.tensor([ms_b, ms_p], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_b_max, ms_p_max = float(tt[0]), float(tt[1])
+    ms_b_max = shard.max_over_ranks(ms_b, dev)
+    ms_p_max = shard.max_over_ranks(ms_p, dev)
     value = n * world / (ms_b_max * 1e-3)
     plain_value = n * world / (ms_p_max * 1e-3)
 
@@ -237,10 +235,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     barrier()
     e2e_s = (time.perf_counter() - t0) / max(1, e2e_steps) if e2e_steps else float("nan")
-    if world > 1:
-        tt = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt[0])
+    e2e_s = shard.max_over_ranks(e2e_s, dev)
     assert all(r["status"] == 0 for r in res_h)
     h2d = int(host.numel() * host.element_size())
     d2h = n * 8 * 14   # the result records read back per step

@@ -63,7 +63,8 @@ enum {
 enum {
     QWB_FLAG_NO_WEIGHTED = 1,  /* skip pass (a)'s C-bar and its exact solve */
     QWB_FLAG_NO_PRIMAL = 2,    /* skip pass (b) */
-    QWB_FLAG_NO_DUAL = 4       /* skip pass (c) */
+    QWB_FLAG_NO_DUAL = 4,      /* skip pass (c) */
+    QWB_FLAG_MINCOST = 8       /* also compute the min-cost lower bound (Sec. 3.3) */
 };
 
 /* Precision of the device passes (see the file comment). */
@@ -89,6 +90,7 @@ typedef struct {
     double delta_mu;       /* TV correction of the first marginal (eq. weighted TV) */
     double delta_nu;       /* TV correction of the second marginal */
     double ipf_residual;   /* ||mu-hat - mu||_1 + ||nu - nu-hat||_1 of the final plan */
+    double lb_mincost;     /* Sec. 3.3: certified L_Cmin(mu~, nu~)^(1/p) <= W_p (QWB_FLAG_MINCOST; else 0) */
     double t_coarse_cost_ms; /* per-pass device times (batch calls: whole batch) */
     double t_solve_ms;       /* host exact coarse solves */
     double t_primal_ms;

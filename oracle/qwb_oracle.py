@@ -341,6 +341,15 @@ def c_transform(h, N, p, chunk=1024):
     return out
 
 
+def c_transform_at(h, N, p, J):
+    """h^c_j for the listed outputs j only (the same definition as
+    ``c_transform``, one output at a time): for spot checks on grids whose
+    full transform the oracle cannot afford."""
+    X = grid_points(N)
+    J = np.asarray(J, dtype=np.int64)
+    return np.array([float((ground_cost(X, X[j:j + 1], p)[:, 0] - h).min()) for j in J])
+
+
 def centre_potential(f_c, mu_c):
     """Shift f~ so that <f~, mu~> = 0; the dual objective is unchanged (masses are 1)."""
     return f_c - float(np.dot(f_c, mu_c))

@@ -17,7 +17,7 @@ P_int32 = ctypes.POINTER(ctypes.c_int32)
 QWB_OK = 0
 QWB_PREC_F64 = 0
 QWB_PREC_MIXED = 1
-QWB_FLAG_NO_WEIGHTED, QWB_FLAG_NO_PRIMAL, QWB_FLAG_NO_DUAL = 1, 2, 4
+QWB_FLAG_NO_WEIGHTED, QWB_FLAG_NO_PRIMAL, QWB_FLAG_NO_DUAL, QWB_FLAG_MINCOST = 1, 2, 4, 8
 STATUS_NAMES = {0: "QWB_OK", 1: "QWB_ERR_INVALID_ARG", 2: "QWB_ERR_MASS", 3: "QWB_ERR_CUDA",
                 4: "QWB_ERR_NOT_CONVERGED", 5: "QWB_ERR_TIMEOUT", 6: "QWB_ERR_OOM",
                 7: "QWB_ERR_UNSUPPORTED"}
@@ -31,6 +31,7 @@ class QwbResult(ctypes.Structure):
     _fields_ = [("ub_weighted", c_double), ("ub_primal", c_double), ("lb", c_double),
                 ("lb_p", c_double), ("ub_weighted_p", c_double), ("w_hat_p", c_double),
                 ("delta_mu", c_double), ("delta_nu", c_double), ("ipf_residual", c_double),
+                ("lb_mincost", c_double),
                 ("t_coarse_cost_ms", c_double), ("t_solve_ms", c_double),
                 ("t_primal_ms", c_double), ("t_dual_ms", c_double),
                 ("ipf_sweeps_done", c_int32), ("status", c_int32)]

@@ -164,7 +164,7 @@ struct qwb_batch {
     std::vector<size_t> cbar_h_off;
     std::vector<double> mu_c_h, nu_c_h;
     std::vector<size_t> mc_off;
-    std::vector<double> ubw, ubw_p;
+    std::vector<double> ubw, ubw_p, lbmin;
     std::vector<int> status;
     bool solved = false;
     double t_solve_ms = 0.0;
@@ -376,7 +376,7 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
     size_t moff = 0;
     for (int t = 0; t < n; ++t) { b->mc_off.push_back(moff); moff += b->Ms[t]; }
     b->mu_c_h.resize(moff); b->nu_c_h.resize(moff);
-    b->ubw.assign(n, 0.0); b->ubw_p.assign(n, 0.0); b->status.assign(n, QWB_OK);
+    b->ubw.assign(n, 0.0); b->ubw_p.assign(n, 0.0); b->lbmin.assign(n, 0.0); b->status.assign(n, QWB_OK);
     // per-pair descriptors
     cudaStream_t s0 = 0;
     for (int t = 0; t < n; ++t) {
@@ -655,6 +655,26 @@ static int run_pass(qwb_batch* b, int kind, bool batched, cudaStream_t s) {
 }
 
 // ---- host exact solves ---------------------------------------------------
+// C^min on the coarse grid as a table over block offsets (Sec. 3.3): the
+// per-axis gap between two blocks is max(0, kappa |dk| - (kappa - 1)) pixels,
+// C^min = (gap1^2 + gap2^2)^(p/2), rounded down so that the LP value stays a
+// lower bound.
+static void mincost_table(const qwb_problem& pr, std::vector<double>& tab) {
+    const int nn = pr.N / pr.kappa;
+    tab.resize((size_t)nn * nn);
+    for (int d1 = 0; d1 < nn; ++d1)
+        for (int d2 = 0; d2 < nn; ++d2) {
+            const double g1 = std::max(0, pr.kappa * d1 - (pr.kappa - 1));
+            const double g2 = std::max(0, pr.kappa * d2 - (pr.kappa - 1));
+            const double s = g1 * g1 + g2 * g2;   // exact integer
+            double c;
+            if (pr.p == 2.0) c = s;
+            else if (pr.p == 1.0) { c = std::sqrt(s); if (c * c > s) c = std::nextafter(c, 0.0); }
+            else c = std::pow(s, 0.5 * pr.p) * (1.0 - std::ldexp(1.0, -49));
+            tab[(size_t)d1 * nn + d2] = c;
+        }
+}
+
 // C~ on the coarse grid as a table over block offsets: (kappa |dk|)^p.
 static void centre_cost_table(const qwb_problem& pr, std::vector<double>& tab) {
     const int nn = pr.N / pr.kappa;
@@ -701,6 +721,35 @@ static int solve_pair(qwb_batch* b, int t) {
     std::memcpy(ph + L.fco, sol.f.data(), sizeof(double) * M);
     stage_typed_values(ph, L, nnz, b->f64);
     b->pairs_h[t].nnz = nnz;
+    // (1b) optional min-cost lower bound: a dual-feasible pair of the C^min
+    // problem bounds L_Cmin <= W_p^p from below (weak duality); the dual
+    // objective is summed with an error margin
+    if (b->flags & QWB_FLAG_MINCOST) {
+        std::vector<double> Cm;
+        mincost_table(pr, Cm);
+        NSSolution sm;
+        st = network_simplex_grid(pr.N / pr.kappa, Cm.data(), mc, nc, sm, -1, nullptr, &basis);
+        if (st) return st;
+        const int nn = pr.N / pr.kappa;
+        // g_j = min_i C_ij - f_i rounded down keeps f_i + g_j <= C_ij exactly
+        std::vector<double> g(M, HUGE_VAL);
+        for (int i = 0; i < M; ++i)
+            for (int j = 0; j < M; ++j) {
+                const double c = Cm[(size_t)std::abs(i / nn - j / nn) * nn + std::abs(i % nn - j % nn)];
+                double v = c - sm.f[i];
+                if (v + sm.f[i] > c) v = std::nextafter(v, -HUGE_VAL);
+                g[j] = std::min(g[j], v);
+            }
+        double s = 0.0, mag = 0.0;
+        for (int k = 0; k < M; ++k) {
+            s += sm.f[k] * mc[k] + g[k] * nc[k];
+            mag += std::fabs(sm.f[k]) * mc[k] + std::fabs(g[k]) * nc[k];
+        }
+        const double u = std::ldexp(1.0, -53);
+        const double s_lo = s - (2.0 * M + 4) * u * mag;
+        const double p = pr.p;
+        b->lbmin[t] = s_lo > 0.0 ? std::pow(s_lo, 1.0 / p) * (1.0 - 4 * u) : 0.0;
+    }
     // (2) C-bar problem: certified weighted-cost upper bound
     if (b->flags & QWB_FLAG_NO_WEIGHTED) {
         b->ubw_p[t] = HUGE_VAL; b->ubw[t] = HUGE_VAL;
@@ -820,6 +869,7 @@ static int batch_results(qwb_batch* b, qwb_result* out, cudaStream_t s) {
         r.delta_nu = o[t].delta_nu;
         r.ipf_residual = o[t].ipf_residual;
         r.ipf_sweeps_done = o[t].sweeps_done;
+        r.lb_mincost = b->lbmin[t];
         if (b->flags & QWB_FLAG_NO_PRIMAL) { r.ub_primal = HUGE_VAL; r.w_hat_p = HUGE_VAL; }
         if (b->flags & QWB_FLAG_NO_DUAL) { r.lb = 0.0; r.lb_p = -HUGE_VAL; }
         r.t_coarse_cost_ms = tc; r.t_solve_ms = b->t_solve_ms; r.t_primal_ms = tp; r.t_dual_ms = td;
@@ -863,7 +913,7 @@ void qwb_ctx_destroy(qwb_ctx* ctx) {
 int qwb_batch_create(qwb_ctx* ctx, int32_t n_pairs, const qwb_problem* probs_h, int32_t ipf_sweeps,
                      int32_t flags, qwb_prec prec, qwb_batch** out) {
     if (!ctx || !out) return fail(QWB_ERR_INVALID_ARG, "qwb_batch_create: null argument");
-    if (flags & ~7) return fail(QWB_ERR_INVALID_ARG, "qwb_batch_create: unknown flags");
+    if (flags & ~15) return fail(QWB_ERR_INVALID_ARG, "qwb_batch_create: unknown flags");
     std::lock_guard<std::mutex> lk(ctx->mtx);
     QWB_CUDA(cudaSetDevice(ctx->device));
     return batch_build(ctx, n_pairs, probs_h, ipf_sweeps, flags, prec, out);

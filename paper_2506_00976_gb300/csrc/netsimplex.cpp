@@ -332,10 +332,17 @@ int solve(int32_t n_src, int32_t n_dst, Cost cst, double maxc, const double* a, 
         out.rowptr[i + 1] = (int32_t)out.col.size();
     }
     out.obj = obj;
-    // potentials: f_i = pot[i]; then exact dual feasibility by c-transforms
+    // potentials: f_i = pot[i] shifted to a zero midrange (a warm start can
+    // leave every potential offset by a multiple of the artificial arc cost,
+    // and sums of large offset terms would lose the digits that matter; the
+    // dual objective does not change, the masses being equal); then exact
+    // dual feasibility by c-transforms
     out.f.assign(n_src, 0.0);
     out.g.assign(n_dst, std::numeric_limits<double>::infinity());
-    for (int i = 0; i < n_src; ++i) out.f[i] = S.pot[i];
+    double f_lo = std::numeric_limits<double>::infinity(), f_hi = -f_lo;
+    for (int i = 0; i < n_src; ++i) { f_lo = std::min(f_lo, S.pot[i]); f_hi = std::max(f_hi, S.pot[i]); }
+    const double shift = n_src > 0 ? 0.5 * (f_lo + f_hi) : 0.0;
+    for (int i = 0; i < n_src; ++i) out.f[i] = S.pot[i] - shift;
     for (int i = 0; i < n_src; ++i)
         for (int j = 0; j < n_dst; ++j) out.g[j] = std::min(out.g[j], cst(i, j) - out.f[i]);
     for (int i = 0; i < n_src; ++i) {
@@ -370,7 +377,7 @@ int network_simplex(int32_t n_src, int32_t n_dst, const double* C, const double*
 }
 
 int network_simplex_grid(int32_t n_side, const double* tab, const double* a, const double* b,
-                         NSSolution& out, int64_t max_pivots, NSBasis* basis_out) {
+                         NSSolution& out, int64_t max_pivots, NSBasis* basis_out, const NSBasis* warm) {
     if (n_side <= 0 || !tab || !a || !b) return QWB_ERR_INVALID_ARG;
     double maxc = 0.0;
     for (int k = 0; k < n_side * n_side; ++k) {
@@ -379,7 +386,7 @@ int network_simplex_grid(int32_t n_side, const double* tab, const double* a, con
     }
     const int32_t M = n_side * n_side;
     if (!check_masses(M, M, a, b)) return QWB_ERR_INVALID_ARG;
-    return solve(M, M, GridCost{tab, n_side}, maxc, a, b, out, max_pivots, nullptr, basis_out);
+    return solve(M, M, GridCost{tab, n_side}, maxc, a, b, out, max_pivots, warm, basis_out);
 }
 
 }  // namespace qwb

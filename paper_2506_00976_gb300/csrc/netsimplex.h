@@ -39,6 +39,7 @@ int network_simplex(int32_t n_src, int32_t n_dst, const double* C, const double*
 // on an n_side x n_side coarse grid (k = k1 * n_side + k2): the centre cost
 // C~ of Sec. 3.4 / 3.5 without an M x M matrix.
 int network_simplex_grid(int32_t n_side, const double* tab, const double* a, const double* b,
-                         NSSolution& out, int64_t max_pivots = -1, NSBasis* basis_out = nullptr);
+                         NSSolution& out, int64_t max_pivots = -1, NSBasis* basis_out = nullptr,
+                         const NSBasis* warm = nullptr);
 
 }  // namespace qwb

@@ -142,3 +142,34 @@ def test_lower_bound_autograd():
         lm = float(api.LowerBound.apply(T((mu - h * e) / (1 - h)), T(nu), N, kappa, p, "f64"))
         agree += abs((lp - lm) / (2 * h) - grad[i]) <= 1e-4 * (1 + abs(grad[i]))
     assert agree >= 8, agree
+
+
+@pytest.mark.parametrize("p", [1.0, 2.0])
+def test_mincost_lower_bound(p):
+    """Min-cost lower bound (Sec. 3.3): the LP value is unique, so the library's
+    certified value sits just below the oracle's and below the exact W; it is
+    not above the dual-upscaling LB's coarse counterpart by more than rounding
+    and is reported as 0 when the flag is off."""
+    N, kappa = 16, 4
+    for cls in ("gauss", "blobs3"):
+        mu, nu = synth.make_measure(N, cls, 36, 0), synth.make_measure(N, cls, 36, 1)
+        ref = O.lb_mincost(mu, nu, N, kappa, p)
+        W = O.wasserstein_exact(mu, nu, N, p)
+        r = api.bounds([T(mu)], [T(nu)], [(N, kappa, p)], ipf_sweeps=2, prec="f64",
+                       flags=8)[0]
+        assert r["status"] == 0
+        assert r["lb_mincost"] <= ref * (1 + 1e-12) and r["lb_mincost"] <= W
+        assert abs(r["lb_mincost"] - ref) <= 1e-9 * max(ref, 1e-300), (cls, r["lb_mincost"], ref)
+        r0 = api.bounds([T(mu)], [T(nu)], [(N, kappa, p)], ipf_sweeps=2, prec="f64")[0]
+        assert r0["lb_mincost"] == 0.0
+        assert r0["lb"] == r["lb"]
+
+
+def test_mincost_lower_bound_larger_grid():
+    """32 x 32, kappa 2 (M = 256 coarse pixels per side of the LP): the grid
+    network simplex's value matches the oracle's SSP value."""
+    N, kappa, p = 32, 2, 2.0
+    mu, nu = synth.make_measure(N, "cauchy", 37, 0), synth.make_measure(N, "cauchy", 37, 1)
+    ref = O.lb_mincost(mu, nu, N, kappa, p)
+    r = api.bounds([T(mu)], [T(nu)], [(N, kappa, p)], ipf_sweeps=2, prec="mixed", flags=8)[0]
+    assert abs(r["lb_mincost"] - ref) <= 1e-9 * ref and r["lb_mincost"] <= ref * (1 + 1e-12)

@@ -217,3 +217,23 @@ def test_small_blob_pair_against_full_lp():
     assert b["lb"] <= W <= b["ub_weighted"] <= b["ub_primal"]
     for key in ("lb", "ub_weighted", "ub_primal"):
         assert b[key] == pytest.approx(gold[key], rel=1e-9), key
+
+
+def test_ctransform_at_closed_form_and_brute_force():
+    """The one-output-at-a-time c-transform: the affine closed form (p = 2) on a
+    grid too large for the full transform, and a brute-force double loop."""
+    N = 200
+    t = np.array([3.0, -5.0])
+    X = O.grid_points(N)
+    J = np.random.default_rng(14).choice(N * N, 40, replace=False)
+    inside = ((X[J] + t >= 0) & (X[J] + t <= N - 1)).all(axis=1)
+    got = O.c_transform_at(2.0 * X @ t, N, 2.0, J)
+    np.testing.assert_allclose(got[inside], (-2.0 * X[J] @ t - t @ t)[inside], atol=1e-7)
+    n = 5
+    h = np.random.default_rng(15).standard_normal(n * n) * 4.0
+    for p in (1.0, 1.5, 2.0):
+        for j in range(n * n):
+            xj, yj = divmod(j, n)
+            brute = min(((xi - xj) ** 2 + (yi - yj) ** 2) ** (p / 2) - h[xi * n + yi]
+                        for xi in range(n) for yi in range(n))
+            assert O.c_transform_at(h, n, p, [j])[0] == pytest.approx(brute, abs=1e-12)
