@@ -16,14 +16,18 @@
 //     does not stream an M x M matrix;
 //   * spanning tree stored as parent pointers with doubly linked child
 //     lists; the flow of each tree arc is kept on its child node;
-//   * block-search pricing over the real arcs (block ~ sqrt(#arcs)),
+//   * block-search pricing over the real arcs (block ~ sqrt(#arcs)), each
+//     block walked as contiguous runs of one source row (grid costs through
+//     a reflected table row, so a run is two unit-stride streams),
 //     reduced cost rc(u,w) = c(u,w) - pot[u] + pot[w];
 //   * leaving arc by the strongly feasible rule (the last blocking arc met
 //     when the pivot cycle is traversed from its apex along the entering
 //     arc's direction), which prevents cycling under degeneracy;
-//   * after each pivot the re-hung subtree gets its depths and potentials
-//     recomputed from its new parent; potentials are re-centred now and then
-//     so that the artificial cost does not eat their precision;
+//   * after each pivot the re-hung subtree gets its depths from its new
+//     parent and its potentials shifted by one common amount (its internal
+//     arcs do not change); every V pivots all potentials are recomputed from
+//     the tree and re-centred, so that neither the shifts' rounding nor the
+//     artificial cost eats their precision;
 //   * a solve can start from the final tree of another solve with the same
 //     supplies (a feasible, strongly feasible basis for any costs): the C-bar
 //     problem starts from the C~ optimum;
@@ -34,6 +38,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <limits>
 #include <type_traits>
 
@@ -51,6 +56,7 @@ struct DenseCost {
 struct GridCost {
     const double* tab;   // ns x ns, tab[|dk1| * ns + |dk2|]
     int ns;
+    const double* refl = nullptr;   // ns x (2 ns - 1): refl[d1][ns - 1 + d2] = tab[d1][|d2|]
     double operator()(int i, int j) const {
         const int d1 = std::abs(i / ns - j / ns), d2 = std::abs(i % ns - j % ns);
         return tab[d1 * ns + d2];
@@ -113,6 +119,23 @@ struct Solver {
             for (int c = first_child[v]; c >= 0; c = next_sib[c]) stack.push_back(c);
         }
     }
+    // the re-hung subtree keeps its internal arcs: its potentials move by one
+    // common amount, its depths follow from the new parent
+    void shift_subtree(int r) {
+        const double old = pot[r];
+        pot_from_parent(r);
+        const double d = pot[r] - old;
+        depth[r] = depth[parent[r]] + 1;
+        stack.clear();
+        for (int c = first_child[r]; c >= 0; c = next_sib[c]) stack.push_back(c);
+        while (!stack.empty()) {
+            int v = stack.back();
+            stack.pop_back();
+            depth[v] = depth[parent[v]] + 1;
+            pot[v] += d;
+            for (int c = first_child[v]; c >= 0; c = next_sib[c]) stack.push_back(c);
+        }
+    }
     void recentre() {
         // subtract a common constant (rc is invariant); keep real nodes small
         double s = 0.0;
@@ -163,6 +186,53 @@ struct Solver {
         recompute_flows();
     }
 
+    // minimum of c[t] + pg[t] over a contiguous run: four independent chains
+    static double run_min(const double* c, const double* pg, int len) {
+        double m0 = HUGE_VAL, m1 = HUGE_VAL, m2 = HUGE_VAL, m3 = HUGE_VAL;
+        int t = 0;
+        for (; t + 4 <= len; t += 4) {
+            const double r0 = c[t] + pg[t], r1 = c[t + 1] + pg[t + 1];
+            const double r2 = c[t + 2] + pg[t + 2], r3 = c[t + 3] + pg[t + 3];
+            m0 = r0 < m0 ? r0 : m0; m1 = r1 < m1 ? r1 : m1;
+            m2 = r2 < m2 ? r2 : m2; m3 = r3 < m3 ? r3 : m3;
+        }
+        for (; t < len; ++t) { const double r = c[t] + pg[t]; m0 = r < m0 ? r : m0; }
+        m0 = m1 < m0 ? m1 : m0; m2 = m3 < m2 ? m3 : m2;
+        return m2 < m0 ? m2 : m0;
+    }
+    // scan row i, columns [j0, j1): cost run against sink potentials
+    void scan_run(int i, int j0, int j1, double& best, int64_t& best_a) {
+        const double pi = pot[i];
+        const double* pg = pot.data() + n;
+        if constexpr (std::is_same<Cost, GridCost>::value) {
+            const int ns = cst.ns;
+            const int i1 = i / ns, i2 = i % ns;
+            int j = j0;
+            while (j < j1) {
+                const int jr = j / ns, jc0 = j % ns;
+                const int len = std::min(ns - jc0, j1 - j);
+                // reflected table row: refl[ns - 1 + d] = tab[|i1 - jr|][|d|]
+                const double* refl = cst.refl + (size_t)std::abs(i1 - jr) * (2 * ns - 1) + (ns - 1 - i2);
+                const double mn = run_min(refl + jc0, pg + j, len) - pi;
+                if (mn < best) {
+                    for (int t = 0; t < len; ++t) {
+                        const double rc = refl[jc0 + t] + pg[j + t] - pi;
+                        if (rc < best) { best = rc; best_a = (int64_t)i * m + j + t; }
+                    }
+                }
+                j += len;
+            }
+        } else {
+            const double* c = cst.C + (int64_t)i * m;
+            const double mn = run_min(c + j0, pg + j0, j1 - j0) - pi;
+            if (mn < best)
+                for (int j = j0; j < j1; ++j) {
+                    const double rc = c[j] + pg[j] - pi;
+                    if (rc < best) { best = rc; best_a = (int64_t)i * m + j; }
+                }
+        }
+    }
+
     // Block-search pricing: the most negative reduced cost in the first block
     // that has one.  Returns -1 at optimality.
     int64_t find_entering(double* rc_out) {
@@ -172,32 +242,11 @@ struct Solver {
             const int64_t end = std::min<int64_t>(pos + block, NM);
             double best = -eps;
             int64_t best_a = -1;
-            int i = (int)(pos / m), j = (int)(pos % m);
-            double pi = pot[i];
-            if constexpr (std::is_same<Cost, GridCost>::value) {
-                // grid costs: walk (j1, j2) incrementally, one table row per j1
-                const int ns = cst.ns;
-                int i1 = i / ns, i2 = i % ns, j1 = j / ns, j2 = j % ns;
-                const double* trow = cst.tab + std::abs(i1 - j1) * ns;
-                for (int64_t a = pos; a < end; ++a) {
-                    const double rc = trow[std::abs(i2 - j2)] - pi + pot[n + j];
-                    if (rc < best) { best = rc; best_a = a; }
-                    ++j;
-                    if (++j2 == ns) {
-                        j2 = 0;
-                        if (++j1 == ns) {
-                            j1 = 0; j = 0; ++i;
-                            if (i < n) { pi = pot[i]; i1 = i / ns; i2 = i % ns; }
-                        }
-                        trow = cst.tab + std::abs(i1 - j1) * ns;
-                    }
-                }
-            } else {
-                for (int64_t a = pos; a < end; ++a) {
-                    const double rc = cst(i, j) - pi + pot[n + j];
-                    if (rc < best) { best = rc; best_a = a; }
-                    if (++j == m) { j = 0; ++i; if (i < n) pi = pot[i]; }
-                }
+            for (int64_t a = pos; a < end;) {
+                const int i = (int)(a / m), j0 = (int)(a % m);
+                const int j1 = (int)std::min<int64_t>(m, j0 + (end - a));
+                scan_run(i, j0, j1, best, best_a);
+                a += j1 - j0;
             }
             scanned += end - pos;
             pos = (end == NM) ? 0 : end;
@@ -257,7 +306,7 @@ struct Solver {
         pred[e1] = e;
         up[e1] = (tail(e) == e1) ? 1 : 0;
         flow[e1] = delta;
-        refresh_subtree(e1);
+        shift_subtree(e1);
     }
 
     // Exact tree flows from the supplies (post-order leaf elimination).
@@ -386,7 +435,11 @@ int network_simplex_grid(int32_t n_side, const double* tab, const double* a, con
     }
     const int32_t M = n_side * n_side;
     if (!check_masses(M, M, a, b)) return QWB_ERR_INVALID_ARG;
-    return solve(M, M, GridCost{tab, n_side}, maxc, a, b, out, max_pivots, warm, basis_out);
+    std::vector<double> refl((size_t)n_side * (2 * n_side - 1));
+    for (int d1 = 0; d1 < n_side; ++d1)
+        for (int d2 = -(n_side - 1); d2 < n_side; ++d2)
+            refl[(size_t)d1 * (2 * n_side - 1) + n_side - 1 + d2] = tab[d1 * n_side + std::abs(d2)];
+    return solve(M, M, GridCost{tab, n_side, refl.data()}, maxc, a, b, out, max_pivots, warm, basis_out);
 }
 
 }  // namespace qwb
