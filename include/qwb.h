@@ -64,7 +64,13 @@ enum {
     QWB_FLAG_NO_WEIGHTED = 1,  /* skip pass (a)'s C-bar and its exact solve */
     QWB_FLAG_NO_PRIMAL = 2,    /* skip pass (b) */
     QWB_FLAG_NO_DUAL = 4,      /* skip pass (c) */
-    QWB_FLAG_MINCOST = 8       /* also compute the min-cost lower bound (Sec. 3.3) */
+    QWB_FLAG_MINCOST = 8,      /* also compute the min-cost lower bound (Sec. 3.3) */
+    QWB_FLAG_SEPARABLE = 16,   /* p = 2 pairs: separable c-transform (see
+                                  qwb_ctransform_separable) instead of the
+                                  N^4 lazy transform of Sec. 4 */
+    QWB_FLAG_SYMMETRIC_DUAL = 32 /* also run the dual pass from the coarse
+                                  potential g~ (Sec. 3.5 from nu's side) and
+                                  report the larger of the two lower bounds */
 };
 
 /* Precision of the device passes (see the file comment). */
@@ -211,6 +217,19 @@ int qwb_ctransform(qwb_ctx* ctx, int32_t N, double p, const double* h_d, double*
  *   before any stream capture.  Asynchronous on `stream`.
  * Errors: INVALID_ARG (null pointer, p < 1), UNSUPPORTED (N > 256), CUDA. */
 int qwb_ctransform_noalloc(int32_t N, double p, const double* h_d, double* out_d, void* stream);
+
+/* The same transform for p = 2 by separation of the squared Euclidean cost
+ * over the two grid axes (not a step of the paper; an exact reformulation of
+ * its lazy c-transform of Sec. 4):
+ *   t(i1, j2) = min_i2 (i2 - j2)^2 - h(i1, i2),
+ *   out(j1, j2) = min_i1 (i1 - j1)^2 + t(i1, j2),
+ * 2 N^3 candidate pairs instead of N^4.  Every candidate is rounded toward
+ * -inf, so h_i + out_j <= c_ij holds exactly; out is within two roundings of
+ * the exact minimum (MIXED: FP32, h rounded up first; F64: FP64).
+ * h_d, out_d: N*N FP64 device.  Asynchronous on `stream`.
+ * Errors: INVALID_ARG, CUDA, OOM. */
+int qwb_ctransform_separable(qwb_ctx* ctx, int32_t N, const double* h_d, double* out_d,
+                             qwb_prec prec, void* stream);
 
 /* Gradient of the lower bound with respect to the source measure along the
  * simplex (derived from the proposition of Sec. 3.5: for fixed potentials

@@ -376,6 +376,31 @@ def lb_dual(mu, nu, N, kappa, p, f_c=None):
     return out
 
 
+def lb_dual_from_g(mu, nu, N, kappa, p, g_c):
+    """The same upscaling lower bound started from the other coarse potential
+    (Sec. 3.5 applies to either side): g-hat = R(g~ - <g~, nu~>), f = g-hat^c,
+    g = f^c, LB = (<f, mu> + <g, nu>)^(1/p)."""
+    nt = sumpool(nu, N, kappa)
+    g_c = np.asarray(g_c, dtype=np.float64)
+    g_c = g_c - float(np.dot(g_c, nt))
+    g_hat = upsample_potential(g_c, N, kappa)
+    f = c_transform(g_hat, N, p)        # the cost is symmetric: the same map
+    g = c_transform(f, N, p)
+    s = float(np.dot(f, mu) + np.dot(g, nu))
+    return {"lb": max(s, 0.0) ** (1.0 / p), "lb_p": s, "g_hat": g_hat, "f": f, "g": g}
+
+
+def lb_dual_symmetric(mu, nu, N, kappa, p, f_c=None, g_c=None):
+    """The larger of the two upscaling lower bounds, from f~ and from g~
+    (both coarse potentials of one exact coarse solution, Sec. 3.5)."""
+    if f_c is None or g_c is None:
+        mt, nt = sumpool(mu, N, kappa), sumpool(nu, N, kappa)
+        _, f_c, g_c, _ = exact_ot(coarse_cost_centre(N, kappa, p), mt, nt)
+    a = lb_dual(mu, nu, N, kappa, p, f_c=f_c)
+    b = lb_dual_from_g(mu, nu, N, kappa, p, g_c)
+    return a if a["lb_p"] >= b["lb_p"] else b
+
+
 def lb_grad_mu(mu, f, lb_p, p):
     """Derivative of the lower bound along the simplex, d LB / d mu_i.
 

@@ -14,6 +14,8 @@ import torch
 
 from . import _lib
 from ._lib import QwbProblem, QwbResult, check
+from ._lib import (QWB_FLAG_MINCOST, QWB_FLAG_NO_DUAL, QWB_FLAG_NO_PRIMAL,  # noqa: F401
+                   QWB_FLAG_NO_WEIGHTED, QWB_FLAG_SEPARABLE, QWB_FLAG_SYMMETRIC_DUAL)
 
 _CTX = {}
 _CTX_LOCK = threading.Lock()
@@ -146,6 +148,14 @@ def ctransform(h, N, p, prec="mixed"):
     out = torch.empty(N * N, dtype=torch.float64, device=h.device)
     check(_lib.load().qwb_ctransform(context(h.device), int(N), float(p), _dev64(h, "h"),
                                      _ptr(out), _prec(prec), _stream(h)), "qwb_ctransform")
+    return out
+
+
+def ctransform_separable(h, N, prec="mixed"):
+    """qwb_ctransform_separable: the p = 2 c-transform by separation over the grid axes."""
+    out = torch.empty(N * N, dtype=torch.float64, device=h.device)
+    check(_lib.load().qwb_ctransform_separable(context(h.device), int(N), _dev64(h, "h"), _ptr(out),
+                                               _prec(prec), _stream(h)), "qwb_ctransform_separable")
     return out
 
 

@@ -150,6 +150,9 @@ struct qwb_batch {
     CbarItem* cbar_items_d = nullptr;
     CtItem* ct_b_items_d = nullptr;
     CtItem* ct_p_items_d = nullptr;
+    SepItem* sep_items_d = nullptr;          // separable p = 2 c-transform items
+    std::vector<int> sep_off, sep_cnt;       // per pair (count 0: brute-force transform)
+    int n_sep = 0;
     std::vector<int> prep_off, prep_cnt, pix_off, pix_cnt, cbar_off, cbar_cnt, ct_off, ct_cnt;
     int n_prep = 0, n_pix = 0, n_cbar = 0, n_ct_b = 0;
     CtConfig ct_cfg_b, ct_cfg_p;
@@ -194,7 +197,7 @@ static void batch_free(qwb_batch* b) {
 }
 
 struct PlanLayout {   // per-pair coarse plan region
-    size_t rowptr, col, val, colptr, rowidx, valc, val_t, valc_t, fco, total;
+    size_t rowptr, col, val, colptr, rowidx, valc, val_t, valc_t, fco, gco, total;
 };
 static PlanLayout plan_layout(int M, int cap_nnz = 0) {
     PlanLayout L;
@@ -209,6 +212,7 @@ static PlanLayout plan_layout(int M, int cap_nnz = 0) {
     L.val_t = o; o = align_up(o + sizeof(double) * cap, 16);    // room for either type
     L.valc_t = o; o = align_up(o + sizeof(double) * cap, 16);
     L.fco = o; o = align_up(o + sizeof(double) * M, 256);
+    L.gco = o; o = align_up(o + sizeof(double) * M, 256);
     L.total = o;
     return L;
 }
@@ -261,27 +265,37 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
     int kap0 = probs[0].kappa;
     bool same_kap = true, all_p2 = true;
     int N_gcd = 0;   // the c-transform's outputs per thread must divide every N
+    // p = 2 pairs take the separable c-transform when QWB_FLAG_SEPARABLE is set
+    auto separable = [&](int t) { return (flags & QWB_FLAG_SEPARABLE) && probs[t].p == 2.0; };
+    const bool want_cbar = !(flags & QWB_FLAG_NO_WEIGHTED);
     for (int t = 0; t < n; ++t) {
         const int N = probs[t].N, kap = probs[t].kappa, nn = N / kap, M = nn * nn, m = N * N;
         b->Ms.push_back(M);
         same_kap &= (kap == kap0);
-        all_p2 &= (probs[t].p == 2.0);
-        { int a = N_gcd, c = N; while (c) { const int r = a % c; a = c; c = r; } N_gcd = a; }
+        if (!separable(t)) {
+            all_p2 &= (probs[t].p == 2.0);
+            int a = N_gcd, c = N;
+            while (c) { const int r = a % c; a = c; c = r; }
+            N_gcd = a;
+        }
         b->N_max = std::max(b->N_max, N);
         b->n_max = std::max(b->n_max, nn);
         b->M_max = std::max(b->M_max, M);
         b->kappa_code = std::max(b->kappa_code, kap);
         pair_off[t] = off;
         off += align_up(12 * sizeof(double) * M);
-        off += align_up(sizeof(double) * (size_t)M * M);
-        off += 9 * align_up(tsz * m);
+        if (want_cbar) off += align_up(sizeof(double) * (size_t)M * M);
+        off += (separable(t) ? 10 : 9) * align_up(tsz * m);
+        if (flags & QWB_FLAG_SYMMETRIC_DUAL) off += 2 * align_up(sizeof(double) * m);
     }
+    if (N_gcd == 0) N_gcd = 8;   // every pair is separable: no brute-force items
     if (!(same_kap && (kap0 == 1 || kap0 == 2 || kap0 == 4))) b->kappa_code = -b->kappa_code;
     // descriptors and item lists
     const int sm = ctx->sm_count > 0 ? ctx->sm_count : 148;
     std::vector<PixItem> prep, pix;
     std::vector<CbarItem> cb;
     std::vector<CtItem> ctb, ctp;
+    std::vector<SepItem> sep;
     b->ct_cfg_b = pick_ct_config(N_gcd, all_p2);
     b->ct_cfg_p = b->ct_cfg_b;
     b->N_gcd = N_gcd;
@@ -321,6 +335,16 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         b->cbar_off.push_back((int)cb.size());
         for (int w1 = 0; w1 < nn; ++w1) cb.push_back({t, w1, 0, 0});
         b->cbar_cnt.push_back((int)cb.size() - b->cbar_off.back());
+        b->sep_off.push_back((int)sep.size());
+        if (separable(t)) {
+            const int lines = sep_lines_per_cta(N);
+            for (int r0 = 0; r0 < N; r0 += lines) sep.push_back({t, r0, std::min(lines, N - r0)});
+            b->sep_cnt.push_back((int)sep.size() - b->sep_off.back());
+            b->ct_off.push_back((int)ctp.size());
+            b->ct_cnt.push_back(0);
+            continue;
+        }
+        b->sep_cnt.push_back(0);
         const int tiles = (m + tile_out - 1) / tile_out;
         // batched form: about 12 items per SM over the whole batch (six waves
         // of the persistent grid), each pair split evenly
@@ -342,6 +366,7 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
     }
     b->n_prep = (int)prep.size(); b->n_pix = (int)pix.size(); b->n_cbar = (int)cb.size();
     b->n_ct_b = (int)ctb.size();
+    b->n_sep = (int)sep.size();
     // device allocation
     const size_t o_pairs = align_up(off);
     const size_t o_outs = align_up(o_pairs + sizeof(PairDev) * n);
@@ -351,7 +376,8 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
     const size_t o_cb = align_up(o_pix + sizeof(PixItem) * pix.size());
     const size_t o_ctb = align_up(o_cb + sizeof(CbarItem) * cb.size());
     const size_t o_ctp = align_up(o_ctb + sizeof(CtItem) * ctb.size());
-    const size_t total = align_up(o_ctp + sizeof(CtItem) * ctp.size());
+    const size_t o_sep = align_up(o_ctp + sizeof(CtItem) * ctp.size());
+    const size_t total = align_up(o_sep + sizeof(SepItem) * sep.size());
     if (cudaMalloc(&b->dmem, total) != cudaSuccess) { batch_free(b); return fail(QWB_ERR_OOM, "batch workspace"); }
     b->pairs_d = (PairDev*)(b->dmem + o_pairs);
     b->outs_d = (PairOut*)(b->dmem + o_outs);
@@ -361,6 +387,7 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
     b->cbar_items_d = (CbarItem*)(b->dmem + o_cb);
     b->ct_b_items_d = (CtItem*)(b->dmem + o_ctb);
     b->ct_p_items_d = (CtItem*)(b->dmem + o_ctp);
+    b->sep_items_d = (SepItem*)(b->dmem + o_sep);
     // coarse-plan staging
     size_t poff = 0;
     for (int t = 0; t < n; ++t) { b->plan_off.push_back(poff); poff += plan_layout(b->Ms[t]).total; }
@@ -369,8 +396,8 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         batch_free(b); return fail(QWB_ERR_OOM, "plan staging");
     }
     size_t coff = 0;
-    for (int t = 0; t < n; ++t) { b->cbar_h_off.push_back(coff); coff += (size_t)b->Ms[t] * b->Ms[t]; }
-    if (cudaMallocHost(&b->cbar_h, sizeof(double) * coff) != cudaSuccess) {
+    for (int t = 0; t < n; ++t) { b->cbar_h_off.push_back(coff); if (want_cbar) coff += (size_t)b->Ms[t] * b->Ms[t]; }
+    if (coff > 0 && cudaMallocHost(&b->cbar_h, sizeof(double) * coff) != cudaSuccess) {
         batch_free(b); return fail(QWB_ERR_OOM, "host C-bar buffer");
     }
     size_t moff = 0;
@@ -391,7 +418,7 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         P.mu_c_hi = (double*)(P.nu_rinv32 + M); P.nu_c_hi = P.mu_c_hi + M;
         P.mu_w_hi = P.nu_c_hi + M; P.nu_w_hi = P.mu_w_hi + M;
         base += align_up(12 * sizeof(double) * M);
-        P.cbar = (double*)base; base += align_up(sizeof(double) * (size_t)M * M);
+        if (want_cbar) { P.cbar = (double*)base; base += align_up(sizeof(double) * (size_t)M * M); }
         P.fhat = base; base += align_up(tsz * m);
         P.g = base; base += align_up(tsz * m);
         P.f = base; base += align_up(tsz * m);
@@ -401,6 +428,11 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         P.nu_t = base; base += align_up(tsz * m);
         P.mu_up = base; base += align_up(tsz * m);
         P.nu_up = base; base += align_up(tsz * m);
+        if (separable(t)) { P.tsep = base; base += align_up(tsz * m); }
+        if (flags & QWB_FLAG_SYMMETRIC_DUAL) {   // the kept side's potentials (FP64)
+            P.f_out = (double*)base; base += align_up(sizeof(double) * m);
+            P.g_out = (double*)base; base += align_up(sizeof(double) * m);
+        }
         const void *lo, *hi;
         int st = ctx_table(ctx, N, probs[t].p, b->f64, s0, &lo, &hi);
         if (st) { batch_free(b); return st; }
@@ -411,6 +443,7 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         P.colptr = (int*)(pd + L.colptr); P.rowidx = (int*)(pd + L.rowidx); P.valc = (double*)(pd + L.valc);
         P.val_t = pd + L.val_t; P.valc_t = pd + L.valc_t;
         P.f_coarse = (double*)(pd + L.fco);
+        P.g_coarse = (double*)(pd + L.gco);
         P.sweeps = sweeps;
         P.ct_split = 2;
         P.out_index = t;
@@ -428,6 +461,7 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
     if (!st) st = up(b->prep_items_d, prep.data(), sizeof(PixItem) * prep.size());
     if (!st) st = up(b->pix_items_d, pix.data(), sizeof(PixItem) * pix.size());
     if (!st) st = up(b->cbar_items_d, cb.data(), sizeof(CbarItem) * cb.size());
+    if (!st) st = up(b->sep_items_d, sep.data(), sizeof(SepItem) * sep.size());
     if (!st) st = up(b->ct_b_items_d, ctb.data(), sizeof(CtItem) * ctb.size());
     if (!st) st = up(b->ct_p_items_d, ctp.data(), sizeof(CtItem) * ctp.size());
     if (!st) {
@@ -506,15 +540,30 @@ static int enqueue_fine(qwb_batch* b, bool batched, cudaStream_t s) {
             if ((st = mark(b, 5, s))) return st;
             if ((st = launch_upsample(b->pairs_d, b->outs_d, b->pix_items_d, b->n_pix, b->f64, s))) return st;
             if ((st = mark(b, 6, s))) return st;
-            if ((st = launch_ctransform(b->pairs_d, b->ct_b_items_d, b->n_ct_b, 0, b->ct_cfg_b, b->N_max, b->f64, cap, s))) return st;
-            if ((st = mark(b, 7, s))) return st;
-            if ((st = launch_ctransform(b->pairs_d, b->ct_b_items_d, b->n_ct_b, 1, b->ct_cfg_b, b->N_max, b->f64, cap, s))) return st;
+            for (int phase = 0; phase < 2; ++phase) {
+                if ((st = launch_sep(b->pairs_d, b->sep_items_d, b->n_sep, phase, 0, b->N_max, b->f64, cap, s))) return st;
+                if ((st = launch_sep(b->pairs_d, b->sep_items_d, b->n_sep, phase, 1, b->N_max, b->f64, cap, s))) return st;
+                if ((st = launch_ctransform(b->pairs_d, b->ct_b_items_d, b->n_ct_b, phase, b->ct_cfg_b, b->N_max, b->f64, cap, s))) return st;
+                if (phase == 0 && (st = mark(b, 7, s))) return st;
+            }
             if ((st = mark(b, 8, s))) return st;
             if ((st = launch_lbsum(b->pairs_d, b->outs_d, b->pair_ids_d, b->n, b->f64, s))) return st;
         } else {
             for (int i = 5; i <= 8; ++i) if ((st = mark(b, i, s))) return st;
         }
-        return mark(b, 9, s);
+        if ((st = mark(b, 9, s))) return st;
+        if (do_dual && (b->flags & QWB_FLAG_SYMMETRIC_DUAL)) {
+            // the same pass from g~: g-hat -> f -> g, keep the larger bound
+            if ((st = launch_centre(b->pairs_d, b->outs_d, b->pair_ids_d, b->n, s, 1))) return st;
+            if ((st = launch_upsample(b->pairs_d, b->outs_d, b->pix_items_d, b->n_pix, b->f64, s, 1))) return st;
+            for (int phase = 0; phase < 2; ++phase) {
+                if ((st = launch_sep(b->pairs_d, b->sep_items_d, b->n_sep, phase, 0, b->N_max, b->f64, cap, s))) return st;
+                if ((st = launch_sep(b->pairs_d, b->sep_items_d, b->n_sep, phase, 1, b->N_max, b->f64, cap, s))) return st;
+                if ((st = launch_ctransform(b->pairs_d, b->ct_b_items_d, b->n_ct_b, phase, b->ct_cfg_b, b->N_max, b->f64, cap, s))) return st;
+            }
+            if ((st = launch_lbsum(b->pairs_d, b->outs_d, b->pair_ids_d, b->n, b->f64, s, 1))) return st;
+        }
+        return QWB_OK;
     }
     for (int t = 0; t < b->n; ++t) {
         const int* id = b->pair_ids_d + t;
@@ -525,9 +574,20 @@ static int enqueue_fine(qwb_batch* b, bool batched, cudaStream_t s) {
         if ((st = launch_upsample(b->pairs_d, b->outs_d, b->pix_items_d + b->pix_off[t], b->pix_cnt[t], b->f64, s))) return st;
         CtConfig c = b->ct_cfg_p;
         c.p2 = (b->probs[t].p == 2.0);
-        if ((st = launch_ctransform(b->pairs_d, b->ct_p_items_d + b->ct_off[t], b->ct_cnt[t], 0, c, b->probs[t].N, b->f64, 0, s))) return st;
-        if ((st = launch_ctransform(b->pairs_d, b->ct_p_items_d + b->ct_off[t], b->ct_cnt[t], 1, c, b->probs[t].N, b->f64, 0, s))) return st;
-        if ((st = launch_lbsum(b->pairs_d, b->outs_d, id, 1, b->f64, s))) return st;
+        const int sides = (b->flags & QWB_FLAG_SYMMETRIC_DUAL) ? 2 : 1;
+        for (int side = 0; side < sides; ++side) {
+            if (side == 1) {
+                if ((st = launch_centre(b->pairs_d, b->outs_d, id, 1, s, 1))) return st;
+                if ((st = launch_upsample(b->pairs_d, b->outs_d, b->pix_items_d + b->pix_off[t], b->pix_cnt[t], b->f64, s, 1))) return st;
+            }
+            for (int phase = 0; phase < 2; ++phase) {
+                const SepItem* si = b->sep_items_d + b->sep_off[t];
+                if ((st = launch_sep(b->pairs_d, si, b->sep_cnt[t], phase, 0, b->probs[t].N, b->f64, 0, s))) return st;
+                if ((st = launch_sep(b->pairs_d, si, b->sep_cnt[t], phase, 1, b->probs[t].N, b->f64, 0, s))) return st;
+                if ((st = launch_ctransform(b->pairs_d, b->ct_p_items_d + b->ct_off[t], b->ct_cnt[t], phase, c, b->probs[t].N, b->f64, 0, s))) return st;
+            }
+            if ((st = launch_lbsum(b->pairs_d, b->outs_d, id, 1, b->f64, s, side))) return st;
+        }
     }
     return QWB_OK;
 }
@@ -719,6 +779,7 @@ static int solve_pair(qwb_batch* b, int t) {
             rowidx[pos] = k; valc[pos] = sol.val[e];
         }
     std::memcpy(ph + L.fco, sol.f.data(), sizeof(double) * M);
+    std::memcpy(ph + L.gco, sol.g.data(), sizeof(double) * M);
     stage_typed_values(ph, L, nnz, b->f64);
     b->pairs_h[t].nnz = nnz;
     // (1b) optional min-cost lower bound: a dual-feasible pair of the C^min
@@ -913,7 +974,7 @@ void qwb_ctx_destroy(qwb_ctx* ctx) {
 int qwb_batch_create(qwb_ctx* ctx, int32_t n_pairs, const qwb_problem* probs_h, int32_t ipf_sweeps,
                      int32_t flags, qwb_prec prec, qwb_batch** out) {
     if (!ctx || !out) return fail(QWB_ERR_INVALID_ARG, "qwb_batch_create: null argument");
-    if (flags & ~15) return fail(QWB_ERR_INVALID_ARG, "qwb_batch_create: unknown flags");
+    if (flags & ~63) return fail(QWB_ERR_INVALID_ARG, "qwb_batch_create: unknown flags");
     std::lock_guard<std::mutex> lk(ctx->mtx);
     QWB_CUDA(cudaSetDevice(ctx->device));
     return batch_build(ctx, n_pairs, probs_h, ipf_sweeps, flags, prec, out);
@@ -1010,8 +1071,14 @@ int qwb_batch_potentials(qwb_batch* b, int32_t pair, double* f_d, double* g_d, v
     cudaStream_t s = (cudaStream_t)stream;
     const int m = b->probs[pair].N * b->probs[pair].N;
     int st;
-    if (f_d && (st = launch_from_work(b->pairs_h[pair].f, f_d, m, b->f64, s))) return st;
-    if (g_d && (st = launch_from_work(b->pairs_h[pair].g, g_d, m, b->f64, s))) return st;
+    const PairDev& P = b->pairs_h[pair];
+    if (P.f_out) {   // both sides ran: the lower-bound kernel kept the better pair
+        if (f_d) QWB_CUDA(cudaMemcpyAsync(f_d, P.f_out, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+        if (g_d) QWB_CUDA(cudaMemcpyAsync(g_d, P.g_out, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+        return QWB_OK;
+    }
+    if (f_d && (st = launch_from_work(P.f, f_d, m, b->f64, s))) return st;
+    if (g_d && (st = launch_from_work(P.g, g_d, m, b->f64, s))) return st;
     return QWB_OK;
 }
 
@@ -1037,17 +1104,17 @@ int qwb_bounds(qwb_ctx* ctx, int32_t n_pairs, const qwb_problem* probs_h, const 
 
 // ---- standalone pass entry points ----------------------------------------
 static int single_batch(qwb_ctx* ctx, const qwb_problem* prob, int sweeps, qwb_prec prec,
-                        qwb_batch** out) {
+                        qwb_batch** out, int flags = 0) {
     for (auto* b : ctx->single_cache)
         if (b->probs[0].N == prob->N && b->probs[0].kappa == prob->kappa && b->probs[0].p == prob->p &&
-            b->f64 == (prec == QWB_PREC_F64)) {
+            b->f64 == (prec == QWB_PREC_F64) && b->flags == flags) {
             b->sweeps = sweeps;
             b->pairs_h[0].sweeps = sweeps;
             *out = b;
             return QWB_OK;
         }
     qwb_batch* b = nullptr;
-    int st = batch_build(ctx, 1, prob, sweeps, 0, prec, &b);
+    int st = batch_build(ctx, 1, prob, sweeps, flags, prec, &b);
     if (st) return st;
     if (ctx->single_cache.size() >= 8) { batch_free(ctx->single_cache.front()); ctx->single_cache.erase(ctx->single_cache.begin()); }
     ctx->single_cache.push_back(b);
@@ -1243,6 +1310,28 @@ int qwb_ctransform(qwb_ctx* ctx, int32_t N, double p, const double* h_d, double*
     CtConfig c = b->ct_cfg_p;
     c.p2 = (p == 2.0);
     if ((st = launch_ctransform(b->pairs_d, b->ct_p_items_d, b->ct_cnt[0], 0, c, N, b->f64, 0, s))) return st;
+    if ((st = launch_from_work(P.g, out_d, N * N, b->f64, s))) return st;
+    QWB_CUDA(cudaStreamSynchronize(s));
+    return QWB_OK;
+}
+
+int qwb_ctransform_separable(qwb_ctx* ctx, int32_t N, const double* h_d, double* out_d,
+                             qwb_prec prec, void* stream) {
+    if (!ctx || !h_d || !out_d) return fail(QWB_ERR_INVALID_ARG, "qwb_ctransform_separable: null argument");
+    qwb_problem prob{N, N, 2.0};
+    int st = check_problem(&prob);
+    if (st) return st;
+    std::lock_guard<std::mutex> lk(ctx->mtx);
+    QWB_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    qwb_batch* b;
+    if ((st = single_batch(ctx, &prob, 1, prec, &b, QWB_FLAG_SEPARABLE))) return st;
+    PairDev& P = b->pairs_h[0];
+    P.f_out = nullptr; P.g_out = nullptr;
+    if ((st = single_upload(b, s))) return st;
+    if ((st = launch_to_work(h_d, P.fhat, P.g, N * N, b->f64, s))) return st;
+    if ((st = launch_sep(b->pairs_d, b->sep_items_d, b->n_sep, 0, 0, N, b->f64, 0, s))) return st;
+    if ((st = launch_sep(b->pairs_d, b->sep_items_d, b->n_sep, 0, 1, N, b->f64, 0, s))) return st;
     if ((st = launch_from_work(P.g, out_d, N * N, b->f64, s))) return st;
     QWB_CUDA(cudaStreamSynchronize(s));
     return QWB_OK;

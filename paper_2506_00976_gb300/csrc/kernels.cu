@@ -554,7 +554,7 @@ __device__ T block_pair_num(const PairDev& P, int k, int l) {
 template <typename T>
 __global__ void __launch_bounds__(PRIMAL_THREADS, 2)
 primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
-              const int* __restrict__ pair_ids) {
+              const int* __restrict__ pair_ids, int csr_cap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[33];
     const PairDev& P = pairs[pair_ids[blockIdx.x]];
@@ -570,6 +570,28 @@ primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
     const T kinv4 = T(1) / (T)((double)kap * kap * kap * kap);
     const T kk = (T)(kap * kap);
 
+    // the coarse plan's CSR and CSC (indices and pass-type values), staged in
+    // shared memory when they fit: every sweep walks them twice
+    const int* rp = P.rowptr;
+    const int* ci = P.colidx;
+    const int* cp = P.colptr;
+    const int* ri = P.rowidx;
+    const T* vt = reinterpret_cast<const T*>(P.val_t);
+    const T* vct = reinterpret_cast<const T*>(P.valc_t);
+    if (P.nnz <= csr_cap) {
+        T* v_s = At + M;
+        T* vc_s = v_s + csr_cap;
+        int* rp_s = reinterpret_cast<int*>(vc_s + csr_cap);
+        int* cp_s = rp_s + (M + 1);
+        int* ci_s = cp_s + (M + 1);
+        int* ri_s = ci_s + csr_cap;
+        for (int k = threadIdx.x; k <= M; k += blockDim.x) { rp_s[k] = rp[k]; cp_s[k] = cp[k]; }
+        for (int e = threadIdx.x; e < P.nnz; e += blockDim.x) {
+            ci_s[e] = ci[e]; ri_s[e] = ri[e]; v_s[e] = vt[e]; vc_s[e] = vct[e];
+        }
+        rp = rp_s; ci = ci_s; cp = cp_s; ri = ri_s; vt = v_s; vct = vc_s;
+    }
+
     // ---- fine sweeps ------------------------------------------------------
     const T* mu_t = reinterpret_cast<const T*>(P.mu_t);    // written by the SumPool pass
     const T* nu_t = reinterpret_cast<const T*>(P.nu_t);
@@ -580,29 +602,60 @@ primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
         for (int half = 0; half < 2; ++half) {
             // half 0: a = mu / (pi-hat b), A = block sums of a
             // half 1: b = nu / (pi-hat^T a), B = block sums of b
-            const int* ptr = half == 0 ? P.rowptr : P.colptr;
-            const int* idx = half == 0 ? P.colidx : P.rowidx;
-            const T* val = reinterpret_cast<const T*>(half == 0 ? P.val_t : P.valc_t);
+            const int* ptr = half == 0 ? rp : cp;
+            const int* idx = half == 0 ? ci : ri;
+            const T* val = half == 0 ? vt : vct;
             const T* src = half == 0 ? mu_t : nu_t;
             T* dst = half == 0 ? a : b;
             const T* other = half == 0 ? Bt : At;
             T* mine = half == 0 ? At : Bt;
-            for (int k = threadIdx.x; k < M; k += blockDim.x) {
-                T r = T(0);
-                for (int e = ptr[k]; e < ptr[k + 1]; ++e) r += val[e] * other[idx[e]];
-                r *= kinv4;
-                const T inv = r > T(0) ? T(1) / r : T(0);
-                const int k1 = k / n, k2 = k % n;
-                T s = T(0);
-                if (vec4) {
-                    for (int t1 = 0; t1 < 4; ++t1) {
-                        const int base = (k1 * 4 + t1) * N + k2 * 4;
-                        float4 v = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(src) + base);
-                        v.x *= (float)inv; v.y *= (float)inv; v.z *= (float)inv; v.w *= (float)inv;
-                        *reinterpret_cast<float4*>(reinterpret_cast<float*>(dst) + base) = v;
-                        s += (T)((v.x + v.y) + (v.z + v.w));
+            if (vec4) {
+                // up to four blocks per thread at a time: all their fine rows
+                // are requested before the first coarse matvec, so a half
+                // sweep waits for one memory round trip
+                const float* srcf = reinterpret_cast<const float*>(src);
+                float* dstf = reinterpret_cast<float*>(dst);
+                for (int kb = threadIdx.x; kb < M; kb += 4 * blockDim.x) {
+                    float4 x[4][4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int k = kb + q * blockDim.x;
+                        if (k < M) {
+                            const int k1 = k / n, k2 = k - (k / n) * n;
+#pragma unroll
+                            for (int t1 = 0; t1 < 4; ++t1)
+                                x[q][t1] = *reinterpret_cast<const float4*>(srcf + (k1 * 4 + t1) * N + k2 * 4);
+                        }
                     }
-                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int k = kb + q * blockDim.x;
+                        if (k < M) {
+                            T r = T(0);
+                            for (int e = ptr[k]; e < ptr[k + 1]; ++e) r += val[e] * other[idx[e]];
+                            r *= kinv4;
+                            const float inv = r > T(0) ? (float)(T(1) / r) : 0.0f;
+                            const int k1 = k / n, k2 = k - (k / n) * n;
+                            T s = T(0);
+#pragma unroll
+                            for (int t1 = 0; t1 < 4; ++t1) {
+                                float4 v = x[q][t1];
+                                v.x *= inv; v.y *= inv; v.z *= inv; v.w *= inv;
+                                *reinterpret_cast<float4*>(dstf + (k1 * 4 + t1) * N + k2 * 4) = v;
+                                s += (T)((v.x + v.y) + (v.z + v.w));
+                            }
+                            mine[k] = s;
+                        }
+                    }
+                }
+            } else {
+                for (int k = threadIdx.x; k < M; k += blockDim.x) {
+                    T r = T(0);
+                    for (int e = ptr[k]; e < ptr[k + 1]; ++e) r += val[e] * other[idx[e]];
+                    r *= kinv4;
+                    const T inv = r > T(0) ? T(1) / r : T(0);
+                    const int k1 = k / n, k2 = k % n;
+                    T s = T(0);
                     for (int t1 = 0; t1 < kap; ++t1) {
                         const int base = (k1 * kap + t1) * N + k2 * kap;
                         for (int t2 = 0; t2 < kap; ++t2) {
@@ -611,8 +664,8 @@ primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
                             s += v;
                         }
                     }
+                    mine[k] = s;
                 }
-                mine[k] = s;
             }
             __syncthreads();
         }
@@ -633,7 +686,7 @@ primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
     for (;;) {
         for (int k = threadIdx.x; k < M; k += blockDim.x) {        // a = mu / (pi-hat b)
             double r = 0.0;
-            for (int e = P.rowptr[k]; e < P.rowptr[k + 1]; ++e) r += P.val[e] * Bd[P.colidx[e]];
+            for (int e = rp[k]; e < rp[k + 1]; ++e) r += P.val[e] * Bd[ci[e]];
             r *= kinv4_rn;
             alpha[k] = r > 0.0 ? 1.0 / r : 0.0;
             Ad[k] = alpha[k] * P.mu_c[k];
@@ -641,7 +694,7 @@ primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
         __syncthreads();
         for (int l = threadIdx.x; l < M; l += blockDim.x) {        // b = nu / (pi-hat^T a)
             double s = 0.0;
-            for (int e = P.colptr[l]; e < P.colptr[l + 1]; ++e) s += P.valc[e] * Ad[P.rowidx[e]];
+            for (int e = cp[l]; e < cp[l + 1]; ++e) s += P.valc[e] * Ad[ri[e]];
             s *= kinv4_rn;
             beta[l] = s > 0.0 ? 1.0 / s : 0.0;
         }
@@ -650,7 +703,7 @@ primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
         double res = 0.0;                                         // ||mu-hat - mu||_1
         for (int k = threadIdx.x; k < M; k += blockDim.x) {
             double s = 0.0;
-            for (int e = P.rowptr[k]; e < P.rowptr[k + 1]; ++e) s += P.val[e] * beta[P.colidx[e]] * P.nu_c[P.colidx[e]];
+            for (int e = rp[k]; e < rp[k + 1]; ++e) s += P.val[e] * beta[ci[e]] * P.nu_c[ci[e]];
             res += fabs(alpha[k] * kinv4_rn * s - 1.0) * P.mu_c[k];
         }
         res = block_reduce_rn(res, red);
@@ -686,8 +739,8 @@ primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
     for (int k = threadIdx.x; k < M; k += blockDim.x) {
         const double m_hi = P.mu_c_hi[k], w_hi = P.mu_w_hi[k];
         double s_lo = 0.0, s_hi = 0.0;
-        for (int e = P.rowptr[k]; e < P.rowptr[k + 1]; ++e) {
-            const int l = P.colidx[e];
+        for (int e = rp[k]; e < rp[k + 1]; ++e) {
+            const int l = ci[e];
             s_lo = __fma_rd(__dmul_rd(P.val[e], beta[l]), P.nu_c_lo[l], s_lo);
             s_hi = __fma_ru(__dmul_ru(P.val[e], beta[l]), P.nu_c_hi[l], s_hi);
         }
@@ -702,8 +755,8 @@ primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
     for (int l = threadIdx.x; l < M; l += blockDim.x) {
         const double m_hi = P.nu_c_hi[l], w_hi = P.nu_w_hi[l];
         double s_lo = 0.0, s_hi = 0.0;
-        for (int e = P.colptr[l]; e < P.colptr[l + 1]; ++e) {
-            const int k = P.rowidx[e];
+        for (int e = cp[l]; e < cp[l + 1]; ++e) {
+            const int k = ri[e];
             s_lo = __fma_rd(__dmul_rd(P.valc[e], alpha[k]), P.mu_c_lo[k], s_lo);
             s_hi = __fma_ru(__dmul_ru(P.valc[e], alpha[k]), P.mu_c_hi[k], s_hi);
         }
@@ -722,8 +775,8 @@ primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
     for (int e = threadIdx.x; e < P.nnz; e += blockDim.x) {
         // row of entry e: binary search in rowptr
         int lo = 0, hi = M;
-        while (hi - lo > 1) { const int mid = (lo + hi) >> 1; if (P.rowptr[mid] <= e) lo = mid; else hi = mid; }
-        const int k = lo, l = P.colidx[e];
+        while (hi - lo > 1) { const int mid = (lo + hi) >> 1; if (rp[mid] <= e) lo = mid; else hi = mid; }
+        const int k = lo, l = ci[e];
         const T num = kap == 4 ? block_pair_num<T, 4>(P, k, l) : block_pair_num<T, 0>(P, k, l);
         const double term = __dmul_ru(__dmul_ru(__dmul_ru(__dmul_ru(P.val[e], kinv4_hi), alpha[k]), beta[l]),
                                       (double)num);
@@ -752,17 +805,24 @@ primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
 }
 
 int launch_primal(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs,
-                  int M_max, int, bool f64, cudaStream_t stream) {
+                  int M_max, int nnz_max, bool f64, cudaStream_t stream) {
     if (n_pairs <= 0) return QWB_OK;
     const size_t tsz = f64 ? 8 : 4;
-    const size_t smem = 4 * sizeof(double) * (size_t)M_max + 2 * tsz * (size_t)M_max;
-    if (smem > 220 * 1024) return QWB_ERR_UNSUPPORTED;
+    const size_t base = 4 * sizeof(double) * (size_t)M_max + 2 * tsz * (size_t)M_max;
+    if (base > 220 * 1024) return QWB_ERR_UNSUPPORTED;
+    // stage the plan in shared memory when it fits next to two CTAs per SM
+    // (network simplex plans have at most 2M - 1 entries)
+    const int cap = std::max(nnz_max, 2 * M_max);
+    const size_t csr = 2 * (tsz + sizeof(int)) * (size_t)cap + 2 * sizeof(int) * (size_t)(M_max + 1);
+    const bool staged = base + csr <= 110 * 1024;
+    const size_t smem = staged ? base + csr : base;
+    const int csr_cap = staged ? cap : -1;
     if (f64) {
         QWB_CUDA(cudaFuncSetAttribute(primal_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        primal_kernel<double><<<n_pairs, PRIMAL_THREADS, smem, stream>>>(pairs_d, outs_d, pair_ids);
+        primal_kernel<double><<<n_pairs, PRIMAL_THREADS, smem, stream>>>(pairs_d, outs_d, pair_ids, csr_cap);
     } else {
         QWB_CUDA(cudaFuncSetAttribute(primal_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        primal_kernel<float><<<n_pairs, PRIMAL_THREADS, smem, stream>>>(pairs_d, outs_d, pair_ids);
+        primal_kernel<float><<<n_pairs, PRIMAL_THREADS, smem, stream>>>(pairs_d, outs_d, pair_ids, csr_cap);
     }
     QWB_LAUNCHED();
     return QWB_OK;
@@ -773,19 +833,22 @@ int launch_primal(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, 
 // bound is invariant to such shifts because both measures have mass 1).
 // --------------------------------------------------------------------------
 __global__ void centre_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
-                              const int* __restrict__ pair_ids) {
+                              const int* __restrict__ pair_ids, int side) {
     __shared__ double red[33];
     const PairDev& P = pairs[pair_ids[blockIdx.x]];
+    // side 0: <f~, mu~>; side 1 (upscaling from g~): <g~, nu~>
+    const double* pc = side ? P.g_coarse : P.f_coarse;
+    const double* wc = side ? P.nu_c : P.mu_c;
     double s = 0.0;
-    for (int k = threadIdx.x; k < P.M; k += blockDim.x) s += P.f_coarse[k] * P.mu_c[k];
+    for (int k = threadIdx.x; k < P.M; k += blockDim.x) s += pc[k] * wc[k];
     s = block_reduce_rn(s, red);
     if (threadIdx.x == 0) outs[P.out_index].centre_shift = s;
 }
 
 int launch_centre(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs,
-                  cudaStream_t stream) {
+                  cudaStream_t stream, int side) {
     if (n_pairs <= 0) return QWB_OK;
-    centre_kernel<<<n_pairs, 256, 0, stream>>>(pairs_d, outs_d, pair_ids);
+    centre_kernel<<<n_pairs, 256, 0, stream>>>(pairs_d, outs_d, pair_ids, side);
     QWB_LAUNCHED();
     return QWB_OK;
 }
@@ -798,23 +861,30 @@ int launch_centre(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, 
 // --------------------------------------------------------------------------
 template <typename T>
 __global__ void upsample_kernel(const PairDev* __restrict__ pairs, const PairOut* __restrict__ outs,
-                                const PixItem* __restrict__ items) {
+                                const PixItem* __restrict__ items, int side) {
     const PixItem I = items[blockIdx.x];
     const PairDev& P = pairs[I.pair];
     const int i = I.start + threadIdx.x;
     const int N = P.N, n = P.n, kap = P.kappa;
     if (i >= N * N) return;
     const double s = outs[P.out_index].centre_shift;
+    const double* fc = side ? P.g_coarse : P.f_coarse;   // the coarse potential upscaled
     const int r = i / N, c = i % N;
     double v;
     if (n == 1) {
-        v = P.f_coarse[0] - s;
+        v = fc[0] - s;
     } else {
-        const double tr = (r - 0.5 * (kap - 1)) / kap, tc = (c - 0.5 * (kap - 1)) / kap;
-        const int r0 = min(max((int)floor(tr), 0), n - 2), c0 = min(max((int)floor(tc), 0), n - 2);
-        const double wr = tr - r0, wc = tc - c0;
-        const double f00 = P.f_coarse[r0 * n + c0] - s, f01 = P.f_coarse[r0 * n + c0 + 1] - s;
-        const double f10 = P.f_coarse[(r0 + 1) * n + c0] - s, f11 = P.f_coarse[(r0 + 1) * n + c0 + 1] - s;
+        // t = (x - (kappa-1)/2) / kappa = (2x - kappa + 1) / (2 kappa): the cell
+        // index by integer floor division, the weight from the integer
+        // remainder (one reciprocal per thread instead of two divisions)
+        const int den = 2 * kap, nr = 2 * r - kap + 1, nc = 2 * c - kap + 1;
+        const int flr = nr >= 0 ? nr / den : -((-nr + den - 1) / den);
+        const int flc = nc >= 0 ? nc / den : -((-nc + den - 1) / den);
+        const int r0 = min(max(flr, 0), n - 2), c0 = min(max(flc, 0), n - 2);
+        const double inv = 1.0 / den;
+        const double wr = (double)(nr - den * r0) * inv, wc = (double)(nc - den * c0) * inv;
+        const double f00 = fc[r0 * n + c0] - s, f01 = fc[r0 * n + c0 + 1] - s;
+        const double f10 = fc[(r0 + 1) * n + c0] - s, f11 = fc[(r0 + 1) * n + c0 + 1] - s;
         const double top = (1.0 - wc) * f00 + wc * f01;
         const double bot = (1.0 - wc) * f10 + wc * f11;
         v = (1.0 - wr) * top + wr * bot;
@@ -825,10 +895,10 @@ __global__ void upsample_kernel(const PairDev* __restrict__ pairs, const PairOut
 }
 
 int launch_upsample(const PairDev* pairs_d, PairOut* outs_d, const PixItem* items, int n_items,
-                    bool f64, cudaStream_t stream) {
+                    bool f64, cudaStream_t stream, int side) {
     if (n_items <= 0) return QWB_OK;
-    if (f64) upsample_kernel<double><<<n_items, 256, 0, stream>>>(pairs_d, outs_d, items);
-    else upsample_kernel<float><<<n_items, 256, 0, stream>>>(pairs_d, outs_d, items);
+    if (f64) upsample_kernel<double><<<n_items, 256, 0, stream>>>(pairs_d, outs_d, items, side);
+    else upsample_kernel<float><<<n_items, 256, 0, stream>>>(pairs_d, outs_d, items, side);
     QWB_LAUNCHED();
     return QWB_OK;
 }
@@ -1025,6 +1095,115 @@ int launch_ctransform(const PairDev* pairs_d, const CtItem* items, int n_items, 
 }
 
 // --------------------------------------------------------------------------
+// Separable c-transform for p = 2 (squared Euclidean cost on the grid):
+//   min over (i1, i2) of (i1-j1)^2 + (i2-j2)^2 - h(i1,i2)
+//     = min over i1 of (i1-j1)^2 + t(i1, j2),   t(i1, j2) = min over i2 of (i2-j2)^2 - h(i1,i2),
+// two one-dimensional transforms of N^3 candidate pairs each instead of N^4.
+// One launch is one stage over lines of N values:
+//   out[j * N + r] = sign * min_i fl_down((i - j)^2 - in[r * N + i])
+// stage 1: in = h, sign = -1, out = the scratch (holds -t, transposed);
+// stage 2: in = the scratch, sign = +1, out = the result (transposed back).
+// Every candidate is rounded toward -inf and minima are exact, so t is at
+// most the exact row minimum and the result at most
+// (i1-j1)^2 + (i2-j2)^2 - h(i1,i2) for every input: the output is a
+// certified c-transform.  Thread t of a line owns SEP_R consecutive outputs
+// and walks the inputs in chunks of SEP_TC, with the SEP_R + SEP_TC - 1
+// distinct squared offsets of a chunk held in registers (the same register
+// blocking as the two-dimensional kernel).  Lines are padded to a multiple of
+// SEP_R with -inf inputs (candidates +inf); outputs are staged in shared
+// memory and written transposed in contiguous runs.
+// --------------------------------------------------------------------------
+constexpr int SEP_R = 8, SEP_TC = 8, SEP_THREADS = 256;
+
+int sep_lines_per_cta(int N) {
+    const int Lp = (N + SEP_R - 1) / SEP_R * SEP_R;
+    return std::max(1, SEP_THREADS / (Lp / SEP_R));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SEP_THREADS)
+sep_kernel(const PairDev* __restrict__ pairs, const SepItem* __restrict__ items, int n_items,
+           int phase, int stage) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int NQ = SEP_R + SEP_TC - 1;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const SepItem I = items[it];
+        const PairDev& P = pairs[I.pair];
+        const int N = P.N;
+        const int Lp = (N + SEP_R - 1) / SEP_R * SEP_R;
+        const int tpl = Lp / SEP_R;
+        const T* in;
+        T* out;
+        if (stage == 0) { in = reinterpret_cast<const T*>(phase == 0 ? P.fhat : P.g); out = reinterpret_cast<T*>(P.tsep); }
+        else { in = reinterpret_cast<const T*>(P.tsep); out = reinterpret_cast<T*>(phase == 0 ? P.g : P.f); }
+        T* hs = reinterpret_cast<T*>(smem_raw);                 // [lines][Lp]
+        T* os = hs + I.lines * Lp;                              // [lines][Lp + 1]
+        for (int k = threadIdx.x; k < I.lines * Lp; k += blockDim.x) {
+            const int r = k / Lp, i = k - r * Lp;
+            hs[k] = i < N ? in[(size_t)(I.line0 + r) * N + i] : -pos_inf<T>();
+        }
+        __syncthreads();
+        const int line = threadIdx.x / tpl;
+        if (line < I.lines) {
+            const int j0 = (threadIdx.x - line * tpl) * SEP_R;
+            T mins[SEP_R];
+#pragma unroll
+            for (int r = 0; r < SEP_R; ++r) mins[r] = pos_inf<T>();
+            const T* hrow = hs + line * Lp;
+            for (int c0 = 0; c0 < Lp; c0 += SEP_TC) {
+                T q[NQ];
+#pragma unroll
+                for (int e = 0; e < NQ; ++e) {
+                    const T d = (T)(c0 - j0 + e - (SEP_R - 1));
+                    q[e] = d * d;                                // exact integers
+                }
+                T fv[SEP_TC];
+#pragma unroll
+                for (int s = 0; s < SEP_TC; ++s) fv[s] = hrow[c0 + s];
+#pragma unroll
+                for (int s = 0; s < SEP_TC; s += 2)
+#pragma unroll
+                    for (int r = 0; r < SEP_R; ++r)
+                        mins[r] = min3(mins[r], sub_rd(q[s - r + SEP_R - 1], fv[s]),
+                                       sub_rd(q[s + 1 - r + SEP_R - 1], fv[s + 1]));
+            }
+            const T sign = stage == 0 ? T(-1) : T(1);
+#pragma unroll
+            for (int r = 0; r < SEP_R; ++r) os[line * (Lp + 1) + j0 + r] = sign * mins[r];
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < I.lines * N; k += blockDim.x) {
+            const int j = k / I.lines, r = k - j * I.lines;
+            out[(size_t)j * N + I.line0 + r] = os[r * (Lp + 1) + j];
+        }
+        __syncthreads();
+    }
+}
+
+int launch_sep(const PairDev* pairs_d, const SepItem* items, int n_items, int phase, int stage,
+               int N_max, bool f64, int grid_cap, cudaStream_t stream) {
+    if (n_items <= 0) return QWB_OK;
+    const size_t tsz = f64 ? 8 : 4;
+    (void)N_max;
+    // per item: lines * Lp <= SEP_THREADS * SEP_R inputs, as many outputs plus
+    // one pad per line (at most SEP_THREADS lines)
+    const size_t smem = tsz * ((size_t)SEP_THREADS * SEP_R * 2 + SEP_THREADS);
+    auto run = [&](auto kern) -> int {
+        QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int grid = n_items;
+        if (grid_cap > 0) {
+            int occ = 1;
+            QWB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, SEP_THREADS, smem));
+            grid = std::min(n_items, grid_cap * std::max(1, occ));
+        }
+        kern<<<grid, SEP_THREADS, smem, stream>>>(pairs_d, items, n_items, phase, stage);
+        QWB_LAUNCHED();
+        return QWB_OK;
+    };
+    return f64 ? run(sep_kernel<double>) : run(sep_kernel<float>);
+}
+
+// --------------------------------------------------------------------------
 // lbsum: lb_p = <f, mu> + <g, nu> summed with FP64 round-down fused
 // multiply-adds, so lb_p <= the real dual objective of the stored (f, g)
 // (Sec. 3.5, eq. upscaling LB); LB = max(lb_p, 0)^(1/p) rounded down.
@@ -1046,33 +1225,41 @@ __device__ __forceinline__ double block_reduce_rd(double v, double* red) {
 
 template <typename T>
 __global__ void lbsum_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
-                             const int* __restrict__ pair_ids) {
+                             const int* __restrict__ pair_ids, int side) {
     __shared__ double red[33];
     const PairDev& P = pairs[pair_ids[blockIdx.x]];
     const int m = P.N * P.N;
-    const T* f = reinterpret_cast<const T*>(P.f);
-    const T* g = reinterpret_cast<const T*>(P.g);
+    // side 0: the transforms ran f-hat -> g -> f.  Side 1 (upscaling from
+    // g~): they ran g-hat -> f -> g, so the buffer named g holds the
+    // potential on mu's side and the buffer named f the one on nu's side.
+    const T* fm = reinterpret_cast<const T*>(side ? P.g : P.f);
+    const T* gn = reinterpret_cast<const T*>(side ? P.f : P.g);
     double s = 0.0;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        const double fi = (double)f[i], gi = (double)g[i];
-        s = __fma_rd(fi, P.mu[i], s);
-        s = __fma_rd(gi, P.nu[i], s);
-        if (P.f_out) P.f_out[i] = fi;
-        if (P.g_out) P.g_out[i] = gi;
+        s = __fma_rd((double)fm[i], P.mu[i], s);
+        s = __fma_rd((double)gn[i], P.nu[i], s);
     }
     s = block_reduce_rd(s, red);
-    if (threadIdx.x == 0) {
-        PairOut& O = outs[P.out_index];
+    PairOut& O = outs[P.out_index];
+    // the larger of the two certified bounds is kept, with its potentials
+    const bool keep = side == 0 || s > O.lb_p;
+    if (keep && (P.f_out || P.g_out)) {
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            if (P.f_out) P.f_out[i] = (double)fm[i];
+            if (P.g_out) P.g_out[i] = (double)gn[i];
+        }
+    }
+    if (keep && threadIdx.x == 0) {
         O.lb_p = s;
         O.lb = root_p_rd(fmax(s, 0.0), P.p);
     }
 }
 
 int launch_lbsum(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs,
-                 bool f64, cudaStream_t stream) {
+                 bool f64, cudaStream_t stream, int side) {
     if (n_pairs <= 0) return QWB_OK;
-    if (f64) lbsum_kernel<double><<<n_pairs, 1024, 0, stream>>>(pairs_d, outs_d, pair_ids);
-    else lbsum_kernel<float><<<n_pairs, 1024, 0, stream>>>(pairs_d, outs_d, pair_ids);
+    if (f64) lbsum_kernel<double><<<n_pairs, 1024, 0, stream>>>(pairs_d, outs_d, pair_ids, side);
+    else lbsum_kernel<float><<<n_pairs, 1024, 0, stream>>>(pairs_d, outs_d, pair_ids, side);
     QWB_LAUNCHED();
     return QWB_OK;
 }

@@ -41,8 +41,10 @@ struct PairDev {
     double* a_out; double* b_out;   // optional FP64 outputs
     // dual pass
     const double* f_coarse; // M
+    const double* g_coarse; // M (the other coarse potential; upscaled when both sides are used)
     void* fhat; void* g; void* f;   // N*N (T)
     double* f_out; double* g_out;   // optional FP64 outputs
+    void* tsep;             // N*N (T) scratch of the separable p = 2 c-transform (may be null)
     int ct_split;           // > 1 when c-transform outputs are combined by atomics
     int out_index;          // index into the results array
 };
@@ -59,6 +61,7 @@ struct CbarItem { int pair, w1, seg, pad; };   // wrapped block-row diagonal w1 
 struct CtItem { int pair, out0, in_row0, in_rows; };
 constexpr int CT_TILE = 4096;   // outputs per c-transform work item (a multiple of every R)
 struct PixItem { int pair, start; };
+struct SepItem { int pair, line0, lines; };   // separable c-transform: lines [line0, line0 + lines)
 
 // Launch configuration of the c-transform (chosen by the autotuner).
 struct CtConfig {
@@ -79,15 +82,20 @@ int launch_cbar(const PairDev* pairs_d, const CbarItem* items, int n_items, int 
                 int n_max, int N_max, bool f64, cudaStream_t stream, int variant = 0);
 int launch_primal(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs,
                   int M_max, int nnz_max, bool f64, cudaStream_t stream);
+// side 0 upscales f~ (the dual pass of Alg. 5); side 1 upscales g~ (the
+// same pass started from the other coarse potential)
 int launch_upsample(const PairDev* pairs_d, PairOut* outs_d, const PixItem* items, int n_items,
-                    bool f64, cudaStream_t stream);
+                    bool f64, cudaStream_t stream, int side = 0);
 int launch_centre(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs,
-                  cudaStream_t stream);
+                  cudaStream_t stream, int side = 0);
 int launch_ctransform(const PairDev* pairs_d, const CtItem* items, int n_items, int phase,
                       const CtConfig& cfg, int N_max, bool f64, int grid_cap,
                       cudaStream_t stream);
+int sep_lines_per_cta(int N);
+int launch_sep(const PairDev* pairs_d, const SepItem* items, int n_items, int phase, int stage,
+               int N_max, bool f64, int grid_cap, cudaStream_t stream);
 int launch_lbsum(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs,
-                 bool f64, cudaStream_t stream);
+                 bool f64, cudaStream_t stream, int side = 0);
 int launch_to_work(const double* h, void* work_in, void* work_out, int m, bool f64,
                    cudaStream_t stream);
 int launch_from_work(const void* work, double* out, int m, bool f64, cudaStream_t stream);

@@ -173,3 +173,40 @@ def test_mincost_lower_bound_larger_grid():
     ref = O.lb_mincost(mu, nu, N, kappa, p)
     r = api.bounds([T(mu)], [T(nu)], [(N, kappa, p)], ipf_sweeps=2, prec="mixed", flags=8)[0]
     assert abs(r["lb_mincost"] - ref) <= 1e-9 * ref and r["lb_mincost"] <= ref * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+@pytest.mark.parametrize("batched", [True, False])
+def test_symmetric_dual(prec, batched):
+    """QWB_FLAG_SYMMETRIC_DUAL (Sec. 3.5 from both coarse potentials): the
+    bound is the larger of the two certified ones, so at least the one-sided
+    bound of the same coarse solution and at most the exact W; the kept
+    potentials are dual feasible on every pixel pair and reproduce lb_p; the
+    upper bounds do not change."""
+    N, kappa = 16, 4
+    pairs = [(synth.make_measure(N, c, 81, 2 * t), synth.make_measure(N, c, 81, 2 * t + 1))
+             for t, c in enumerate(["gauss", "cauchy", "field", "white", "blobs3", "gauss"])]
+    X = O.grid_points(N)
+    sides = 0
+    for p in (1.0, 2.0):
+        mus = [T(a) for a, _ in pairs]
+        nus = [T(b) for _, b in pairs]
+        probs = [(N, kappa, p)] * len(pairs)
+        with api.Batch(probs, ipf_sweeps=3, prec=prec) as b0, \
+                api.Batch(probs, ipf_sweeps=3, prec=prec, flags=32) as b1:
+            for b in (b0, b1):
+                b.coarse(mus, nus, batched=batched); b.solve(); b.fine(mus, nus, batched=batched)
+            r0, r1 = b0.results(), b1.results()
+            C = O.ground_cost(X, X, p)
+            for t, (mu, nu) in enumerate(pairs):
+                assert r1[t]["status"] == 0
+                assert r1[t]["lb"] >= r0[t]["lb"] and r1[t]["lb_p"] >= r0[t]["lb_p"]
+                assert r1[t]["ub_weighted"] == r0[t]["ub_weighted"]
+                W = O.wasserstein_exact(mu, nu, N, p)
+                assert r1[t]["lb"] <= W
+                f, g = (x.cpu().numpy() for x in b1.potentials(t))
+                assert (f[:, None] + g[None, :] - C).max() <= 1e-10
+                s = float(f @ mu + g @ nu)
+                assert r1[t]["lb_p"] <= s + 1e-12 and s - r1[t]["lb_p"] <= 1e-9 * (1 + abs(s))
+                sides += r1[t]["lb_p"] > r0[t]["lb_p"]
+    assert sides >= 1, "the side started from g~ never won: its path went unexercised"

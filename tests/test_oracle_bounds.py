@@ -237,3 +237,22 @@ def test_ctransform_at_closed_form_and_brute_force():
             brute = min(((xi - xj) ** 2 + (yi - yj) ** 2) ** (p / 2) - h[xi * n + yi]
                         for xi in range(n) for yi in range(n))
             assert O.c_transform_at(h, n, p, [j])[0] == pytest.approx(brute, abs=1e-12)
+
+
+def test_dual_from_g_is_the_swapped_problem():
+    """Starting from g~ is the f~ route of the swapped problem (the cost is
+    symmetric): LB_g(mu, nu; g~) = LB_f(nu, mu; f~ = g~), with f and g
+    exchanged; and both routes bound the exact W from below."""
+    N, kappa, p = 12, 3, 2.0
+    mu, nu = synth.make_measure(N, "gauss", 80, 0), synth.make_measure(N, "gauss", 80, 1)
+    mt, nt = O.sumpool(mu, N, kappa), O.sumpool(nu, N, kappa)
+    _, f_c, g_c, _ = O.exact_ot(O.coarse_cost_centre(N, kappa, p), mt, nt)
+    a = O.lb_dual_from_g(mu, nu, N, kappa, p, g_c)
+    b = O.lb_dual(nu, mu, N, kappa, p, f_c=g_c)
+    assert a["lb_p"] == pytest.approx(b["lb_p"], rel=1e-13, abs=1e-12)
+    np.testing.assert_allclose(a["f"], b["g"], atol=1e-10)
+    np.testing.assert_allclose(a["g"], b["f"], atol=1e-10)
+    W = O.wasserstein_exact(mu, nu, N, p)
+    sym = O.lb_dual_symmetric(mu, nu, N, kappa, p, f_c=f_c, g_c=g_c)
+    assert O.lb_dual(mu, nu, N, kappa, p, f_c=f_c)["lb"] <= sym["lb"] <= W + 1e-12
+    assert a["lb"] <= W + 1e-12
