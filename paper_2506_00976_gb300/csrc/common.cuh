@@ -46,6 +46,20 @@ template <typename T> __device__ __forceinline__ T from_double_rn(double x);
 template <> __device__ __forceinline__ float from_double_rn<float>(double x) { return __double2float_rn(x); }
 template <> __device__ __forceinline__ double from_double_rn<double>(double x) { return x; }
 
+// FP32 -> FP64 widening by exponent re-biasing on the integer pipes (exact
+// for every normal float; zero, subnormals, infinities and NaN take the
+// conversion instruction), which keeps bulk widening off the FP64 pipe.
+__device__ __forceinline__ double widen_f32(float v) {
+    const unsigned u = __float_as_uint(v);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)v;
+    const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) |
+                                    ((unsigned long long)(e + 896u) << 52) |
+                                    ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+__device__ __forceinline__ double widen_f32(double v) { return v; }
+
 template <typename T> __device__ __forceinline__ T pos_inf();
 template <> __device__ __forceinline__ float pos_inf<float>() { return __int_as_float(0x7f800000); }
 template <> __device__ __forceinline__ double pos_inf<double>() { return __longlong_as_double(0x7ff0000000000000LL); }

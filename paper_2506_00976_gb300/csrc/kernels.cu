@@ -397,7 +397,7 @@ cbar_kernel(const PairDev* __restrict__ pairs, const CbarItem* __restrict__ item
                 if (l1 < 0) l1 += n;
                 const T v = out_s[rowid * n + l2];
                 if (v == v)                                          // NaN marks a direct write
-                    cbar[(size_t)(k1 * n + k2) * M + l1 * n + l2] = (double)v;
+                    cbar[(size_t)(k1 * n + k2) * M + l1 * n + l2] = widen_f32(v);
             }
         }
     }

@@ -16,6 +16,15 @@ Value classes (the paper evaluates 10 images per class, all 45 pairs, Sec. 5):
 The small blob case (``blobs3``) is three Gaussian blobs of amplitude 1 with
 sigma ~ U[2, 6] px plus the 1e-3 floor.
 
+Volumes (N x N x N, flat row-major, for the 3-D experiments of the paper, whose
+cryo-EM density maps are not available here):
+  density -- a compact "molecule": K ~ U{8..24} Gaussian blobs with centres
+             drawn around the volume centre (normal, sd N/6, clipped to the
+             grid), sigma ~ U[1, 2.5] * N/16 voxels, amplitudes U[0.5, 1],
+             plus a 1e-3 floor per voxel;
+  field3  -- exp(z) for z a Gaussian-filtered (sigma = 2 voxels, reflect)
+             standard normal volume rescaled to unit variance.
+
 Seeds: numpy PCG64 over SeedSequence([250600976, workload, class, image]).
 """
 from __future__ import annotations
@@ -25,7 +34,9 @@ import itertools
 import numpy as np
 
 CLASSES = ("white", "gauss", "cauchy", "field")
-_CLASS_ID = {"white": 0, "gauss": 1, "cauchy": 2, "field": 3, "blobs3": 4}
+_CLASS_ID = {"white": 0, "gauss": 1, "cauchy": 2, "field": 3, "blobs3": 4,
+             "density": 5, "field3": 6}
+VOLUME_CLASSES = ("density", "field3")
 _ROOT_SEED = 250600976
 
 
@@ -73,6 +84,36 @@ def make_measure(N: int, cls: str, workload: int = 0, image: int = 0) -> np.ndar
         raise ValueError(f"unknown class {cls!r}")
     img = img.ravel()
     return img / img.sum()
+
+
+def make_volume(N: int, cls: str, workload: int = 0, image: int = 0) -> np.ndarray:
+    """One seeded N x N x N measure of class ``cls`` as a flat float64 array of mass 1."""
+    rng = _rng(workload, cls, image)
+    if cls == "density":
+        x = np.arange(N, dtype=np.float64)
+        a, b, c = np.meshgrid(x, x, x, indexing="ij")
+        vol = np.full((N, N, N), 1e-3)
+        for _ in range(int(rng.integers(8, 25))):
+            ctr = np.clip(rng.normal((N - 1) / 2.0, N / 6.0, size=3), 0.0, N - 1.0)
+            s = rng.uniform(1.0, 2.5) * N / 16.0
+            amp = rng.uniform(0.5, 1.0)
+            d2 = (a - ctr[0]) ** 2 + (b - ctr[1]) ** 2 + (c - ctr[2]) ** 2
+            vol += amp * np.exp(-0.5 * d2 / (s * s))
+    elif cls == "field3":
+        from scipy.ndimage import gaussian_filter
+        z = gaussian_filter(rng.standard_normal((N, N, N)), sigma=2.0, mode="reflect")
+        z = (z - z.mean()) / z.std()
+        vol = np.exp(z)
+    else:
+        raise ValueError(f"unknown volume class {cls!r}")
+    vol = vol.ravel()
+    return vol / vol.sum()
+
+
+def volume_pairs(N: int, cls: str, workload: int, count: int = 10):
+    """All 45 pairs (mu, nu) of ``count`` volumes of one class, in a fixed order."""
+    vols = [make_volume(N, cls, workload, i) for i in range(count)]
+    return [(vols[i], vols[j]) for i, j in all_pairs(count)]
 
 
 def class_images(N: int, cls: str, workload: int, count: int = 10):

@@ -60,7 +60,7 @@ def test_sign_error_in_ctransform_is_caught(monkeypatch):
     good = (C - h[:, None]).min(axis=0)
     assert np.allclose(O.c_transform(h, N, 2), good)
     orig = O.c_transform
-    monkeypatch.setattr(O, "c_transform", lambda hh, NN, p, chunk=1024: orig(-hh, NN, p, chunk))
+    monkeypatch.setattr(O, "c_transform", lambda hh, NN, p, chunk=1024, d=2: orig(-hh, NN, p, chunk, d))
     g = O.c_transform(h, N, 2)
     assert (h[:, None] + g[None, :] - C).max() > 1e-6        # feasibility pin fails
 
@@ -78,7 +78,7 @@ def test_dropped_kernel_normalisation_is_caught(monkeypatch):
     assert np.allclose(O.upscaled_plan_apply(plan, v, N, kappa), dense @ v)
     orig = O.upscaled_plan_apply
     monkeypatch.setattr(O, "upscaled_plan_apply",
-                        lambda pc, vv, NN, kk: orig(pc, vv, NN, kk) * kk ** 4)
+                        lambda pc, vv, NN, kk, d=2: orig(pc, vv, NN, kk, d) * kk ** 4)
     assert not np.allclose(O.upscaled_plan_apply(plan, v, N, kappa), dense @ v)
 
 
@@ -88,7 +88,7 @@ def test_tv_weights_without_power_is_caught(monkeypatch):
     N = 8
     rng = np.random.default_rng(2)
     orig = O.tv_weights
-    monkeypatch.setattr(O, "tv_weights", lambda NN, p: orig(NN, 1.0))
+    monkeypatch.setattr(O, "tv_weights", lambda NN, p, d=2: orig(NN, 1.0, d))
     broken = False
     for t in range(20):
         mu = np.zeros(N * N); mh = np.zeros(N * N)
