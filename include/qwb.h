@@ -76,12 +76,17 @@ enum {
 /* Precision of the device passes (see the file comment). */
 typedef enum { QWB_PREC_F64 = 0, QWB_PREC_MIXED = 1 } qwb_prec;
 
-/* One problem: grid side N, block side kappa, order p (d = 2 fixed).
- * Requirements: 1 <= kappa <= N, N % kappa == 0, p >= 1, N <= 1024. */
+/* One problem: grid [N]^d with side N, block side kappa, order p, dimension
+ * d = 2 (images; 0 also means 2) or d = 3 (volumes, flattened row-major:
+ * index (x1 * N + x2) * N + x3; coarse index (k1 * n + k2) * n + k3).
+ * Requirements: 1 <= kappa <= N, N % kappa == 0, p >= 1; d = 2: N <= 1024 and
+ * n = N / kappa <= 64; d = 3: N <= 64 and n <= 16. */
 typedef struct {
     int32_t N;
     int32_t kappa;
     double p;
+    int32_t d;
+    int32_t reserved;   /* must be 0 */
 } qwb_problem;
 
 /* Results for one pair.  Bounds are in the units of W_p (pixels); the *_p

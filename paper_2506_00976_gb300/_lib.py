@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "QWB_OK", 1: "QWB_ERR_INVALID_ARG", 2: "QWB_ERR_MASS", 3: "QW
 
 
 class QwbProblem(ctypes.Structure):
-    _fields_ = [("N", c_int32), ("kappa", c_int32), ("p", c_double)]
+    _fields_ = [("N", c_int32), ("kappa", c_int32), ("p", c_double), ("d", c_int32),
+                ("reserved", c_int32)]
 
 
 class QwbResult(ctypes.Structure):

@@ -56,18 +56,19 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
 
 
-def problem(N, kappa, p):
-    return QwbProblem(int(N), int(kappa), float(p))
+def problem(N, kappa, p, d=2):
+    """One problem on the grid [N]^d (d = 2 images, d = 3 volumes)."""
+    return QwbProblem(int(N), int(kappa), float(p), int(d), 0)
 
 
-def coarse_cost(mu, nu, N, kappa, p, prec="mixed"):
+def coarse_cost(mu, nu, N, kappa, p, prec="mixed", d=2):
     """qwb_coarse_cost: (C-bar [M, M], mu~ [M], nu~ [M]) on the device."""
     n = N // kappa
-    M = n * n
+    M = n ** d
     cbar = torch.empty((M, M), dtype=torch.float64, device=mu.device)
     mc = torch.empty(M, dtype=torch.float64, device=mu.device)
     nc = torch.empty(M, dtype=torch.float64, device=mu.device)
-    pr = problem(N, kappa, p)
+    pr = problem(N, kappa, p, d)
     check(_lib.load().qwb_coarse_cost(context(mu.device), ctypes.byref(pr), _dev64(mu, "mu"),
                                       _dev64(nu, "nu"), _ptr(cbar), _ptr(mc), _ptr(nc),
                                       _prec(prec), _stream(mu)), "qwb_coarse_cost")
@@ -98,7 +99,7 @@ def coarse_solve(C, a, b):
 
 
 def primal_upscale_ipf(mu, nu, N, kappa, p, rowptr, col, val, sweeps=50, prec="mixed",
-                       want_scalings=False):
+                       want_scalings=False, d=2):
     """qwb_primal_upscale_ipf: the primal upscaling upper bound from a coarse CSR plan."""
     dev = mu.device
     rp = torch.as_tensor(np.asarray(rowptr, dtype=np.int32), device=dev)
@@ -106,10 +107,10 @@ def primal_upscale_ipf(mu, nu, N, kappa, p, rowptr, col, val, sweeps=50, prec="m
     vl = torch.as_tensor(np.asarray(val, dtype=np.float64), device=dev)
     a = b = None
     if want_scalings:
-        a = torch.empty(N * N, dtype=torch.float64, device=dev)
-        b = torch.empty(N * N, dtype=torch.float64, device=dev)
+        a = torch.empty(N ** d, dtype=torch.float64, device=dev)
+        b = torch.empty(N ** d, dtype=torch.float64, device=dev)
     res = QwbResult()
-    pr = problem(N, kappa, p)
+    pr = problem(N, kappa, p, d)
     check(_lib.load().qwb_primal_upscale_ipf(context(dev), ctypes.byref(pr), _dev64(mu, "mu"),
                                              _dev64(nu, "nu"), _ptr(rp), _ptr(cl), _ptr(vl),
                                              int(vl.numel()), int(sweeps), _ptr(a), _ptr(b),
@@ -121,17 +122,17 @@ def primal_upscale_ipf(mu, nu, N, kappa, p, rowptr, col, val, sweeps=50, prec="m
     return out
 
 
-def dual_upscale_ctransform(mu, nu, N, kappa, p, f_coarse, prec="mixed", want_potentials=True):
+def dual_upscale_ctransform(mu, nu, N, kappa, p, f_coarse, prec="mixed", want_potentials=True, d=2):
     """qwb_dual_upscale_ctransform: the dual upscaling lower bound from a coarse potential."""
     dev = mu.device
     fc = torch.as_tensor(np.asarray(f_coarse, dtype=np.float64), device=dev) \
         if not isinstance(f_coarse, torch.Tensor) else f_coarse
     f = g = None
     if want_potentials:
-        f = torch.empty(N * N, dtype=torch.float64, device=dev)
-        g = torch.empty(N * N, dtype=torch.float64, device=dev)
+        f = torch.empty(N ** d, dtype=torch.float64, device=dev)
+        g = torch.empty(N ** d, dtype=torch.float64, device=dev)
     res = QwbResult()
-    pr = problem(N, kappa, p)
+    pr = problem(N, kappa, p, d)
     check(_lib.load().qwb_dual_upscale_ctransform(context(dev), ctypes.byref(pr), _dev64(mu, "mu"),
                                                   _dev64(nu, "nu"), _dev64(fc, "f_coarse"),
                                                   _ptr(f), _ptr(g), ctypes.byref(res),
@@ -226,9 +227,9 @@ class Batch:
         return json.loads(buf.value.decode())
 
     def potentials(self, t):
-        N = self.problems[t].N
-        f = torch.empty(N * N, dtype=torch.float64, device=self._dev)
-        g = torch.empty(N * N, dtype=torch.float64, device=self._dev)
+        N, d = self.problems[t].N, self.problems[t].d or 2
+        f = torch.empty(N ** d, dtype=torch.float64, device=self._dev)
+        g = torch.empty(N ** d, dtype=torch.float64, device=self._dev)
         check(_lib.load().qwb_batch_potentials(self._h, int(t), _ptr(f), _ptr(g), self._stream()),
               "qwb_batch_potentials")
         return f, g

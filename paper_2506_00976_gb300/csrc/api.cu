@@ -37,14 +37,25 @@ static size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
 static int check_problem(const qwb_problem* p) {
     if (!p) return fail(QWB_ERR_INVALID_ARG, "null problem");
+    if (p->d != 0 && p->d != 2 && p->d != 3) return fail(QWB_ERR_INVALID_ARG, "d must be 2 or 3");
+    if (p->reserved != 0) return fail(QWB_ERR_INVALID_ARG, "qwb_problem.reserved must be 0");
     if (p->N < 1 || p->N > 1024) return fail(QWB_ERR_INVALID_ARG, "N must be in [1, 1024]");
     if (p->kappa < 1 || p->kappa > p->N || p->N % p->kappa != 0)
         return fail(QWB_ERR_INVALID_ARG, "kappa must divide N");
     if (!(p->p >= 1.0) || !std::isfinite(p->p)) return fail(QWB_ERR_INVALID_ARG, "p must be >= 1");
     const int n = p->N / p->kappa;
+    if (p->d == 3) {
+        if (p->N > 64) return fail(QWB_ERR_UNSUPPORTED, "3-D grids are limited to N <= 64");
+        if (n > 16) return fail(QWB_ERR_UNSUPPORTED, "3-D coarse grid larger than 16^3");
+        if (p->kappa > 16) return fail(QWB_ERR_UNSUPPORTED, "3-D blocks are limited to kappa <= 16");
+        return QWB_OK;
+    }
     if (n > 64) return fail(QWB_ERR_UNSUPPORTED, "coarse grid larger than 64 x 64");
     return QWB_OK;
 }
+
+static inline int dim_of(const qwb_problem& p) { return p.d == 3 ? 3 : 2; }
+static inline int ipow(int x, int d) { int r = 1; while (d-- > 0) r *= x; return r; }
 
 }  // namespace qwb
 
@@ -59,6 +70,7 @@ struct CostTable {
     bool f64;
     void* lo;
     void* hi;
+    int d;
 };
 
 // Launch configuration chosen by the autotuner for one problem signature.
@@ -108,14 +120,14 @@ static void tune_cache_store(qwb_ctx* c) {
 }
 
 static int ctx_table(qwb_ctx* c, int N, double p, bool f64, cudaStream_t s, const void** lo,
-                     const void** hi) {
+                     const void** hi, int d = 2) {
     for (auto& t : c->tables)
-        if (t.N == N && t.p == p && t.f64 == f64) { *lo = t.lo; *hi = t.hi; return QWB_OK; }
-    CostTable t{N, p, f64, nullptr, nullptr};
-    const size_t bytes = (size_t)N * N * (f64 ? 8 : 4);
+        if (t.N == N && t.p == p && t.f64 == f64 && t.d == d) { *lo = t.lo; *hi = t.hi; return QWB_OK; }
+    CostTable t{N, p, f64, nullptr, nullptr, d};
+    const size_t bytes = (size_t)ipow(N, d) * (f64 ? 8 : 4);
     if (cudaMalloc(&t.lo, bytes) != cudaSuccess) return fail(QWB_ERR_OOM, "cost table allocation");
     if (cudaMalloc(&t.hi, bytes) != cudaSuccess) { cudaFree(t.lo); return fail(QWB_ERR_OOM, "cost table allocation"); }
-    int st = launch_cost_tables(N, p, f64, t.lo, t.hi, s);
+    int st = d == 3 ? launch_cost_tables3(N, p, f64, t.lo, t.hi, s) : launch_cost_tables(N, p, f64, t.lo, t.hi, s);
     if (st) return st;
     c->tables.push_back(t);
     *lo = t.lo; *hi = t.hi;
@@ -152,7 +164,12 @@ struct qwb_batch {
     CtItem* ct_p_items_d = nullptr;
     SepItem* sep_items_d = nullptr;          // separable p = 2 c-transform items
     std::vector<int> sep_off, sep_cnt;       // per pair (count 0: brute-force transform)
-    int n_sep = 0;
+    int n_sep = 0, sep_stages = 0;           // stages: the largest d of a separable pair
+    PixItem* cbar3_items_d = nullptr;        // 3-D C-bar items (one per source block)
+    std::vector<int> cbar3_off, cbar3_cnt;
+    int n_cbar3 = 0;
+    bool has_3d = false;
+    int n_max2 = 0, N_max2 = 0;              // largest n, N over 2-D pairs (2-D C-bar kernel)
     std::vector<int> prep_off, prep_cnt, pix_off, pix_cnt, cbar_off, cbar_cnt, ct_off, ct_cnt;
     int n_prep = 0, n_pix = 0, n_cbar = 0, n_ct_b = 0;
     CtConfig ct_cfg_b, ct_cfg_p;
@@ -262,16 +279,25 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
     // sizes
     size_t off = 0;
     std::vector<size_t> pair_off(n);
-    int kap0 = probs[0].kappa;
+    int kap0 = -1;                 // the 2-D C-bar kernel's kappa (over 2-D pairs)
     bool same_kap = true, all_p2 = true;
     int N_gcd = 0;   // the c-transform's outputs per thread must divide every N
     // p = 2 pairs take the separable c-transform when QWB_FLAG_SEPARABLE is set
     auto separable = [&](int t) { return (flags & QWB_FLAG_SEPARABLE) && probs[t].p == 2.0; };
     const bool want_cbar = !(flags & QWB_FLAG_NO_WEIGHTED);
     for (int t = 0; t < n; ++t) {
-        const int N = probs[t].N, kap = probs[t].kappa, nn = N / kap, M = nn * nn, m = N * N;
+        const int dd = dim_of(probs[t]);
+        const int N = probs[t].N, kap = probs[t].kappa, nn = N / kap, M = ipow(nn, dd), m = ipow(N, dd);
         b->Ms.push_back(M);
-        same_kap &= (kap == kap0);
+        if (dd == 3) b->has_3d = true;
+        if (dd == 2) {
+            if (kap0 < 0) kap0 = kap;
+            same_kap &= (kap == kap0);
+            b->kappa_code = std::max(b->kappa_code, kap);
+            b->n_max2 = std::max(b->n_max2, nn);
+            b->N_max2 = std::max(b->N_max2, N);
+        }
+        if (separable(t)) b->sep_stages = std::max(b->sep_stages, dd);
         if (!separable(t)) {
             all_p2 &= (probs[t].p == 2.0);
             int a = N_gcd, c = N;
@@ -281,15 +307,15 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         b->N_max = std::max(b->N_max, N);
         b->n_max = std::max(b->n_max, nn);
         b->M_max = std::max(b->M_max, M);
-        b->kappa_code = std::max(b->kappa_code, kap);
         pair_off[t] = off;
         off += align_up(12 * sizeof(double) * M);
         if (want_cbar) off += align_up(sizeof(double) * (size_t)M * M);
-        off += (separable(t) ? 10 : 9) * align_up(tsz * m);
+        off += (separable(t) ? (dd == 3 ? 11 : 10) : 9) * align_up(tsz * m);
         if (flags & QWB_FLAG_SYMMETRIC_DUAL) off += 2 * align_up(sizeof(double) * m);
     }
     if (N_gcd == 0) N_gcd = 8;   // every pair is separable: no brute-force items
-    if (!(same_kap && (kap0 == 1 || kap0 == 2 || kap0 == 4))) b->kappa_code = -b->kappa_code;
+    if (kap0 < 0) b->kappa_code = 1;          // no 2-D pair: the 2-D C-bar kernel has no items
+    else if (!(same_kap && (kap0 == 1 || kap0 == 2 || kap0 == 4))) b->kappa_code = -b->kappa_code;
     // descriptors and item lists
     const int sm = ctx->sm_count > 0 ? ctx->sm_count : 148;
     std::vector<PixItem> prep, pix;
@@ -307,6 +333,7 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         for (int t = 0; t < n; ++t) {
             std::ostringstream p1;
             p1 << probs[t].N << "/" << probs[t].kappa << "/" << probs[t].p;
+            if (dim_of(probs[t]) == 3) p1 << "/d3";
             parts.push_back(p1.str());
         }
         std::sort(parts.begin(), parts.end());
@@ -323,9 +350,12 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
     }
     const int tile_out = CT_TILE;
     long total_tiles = 0;
-    for (int t = 0; t < n; ++t) total_tiles += ((long)probs[t].N * probs[t].N + tile_out - 1) / tile_out;
+    for (int t = 0; t < n; ++t) total_tiles += ((long)ipow(probs[t].N, dim_of(probs[t])) + tile_out - 1) / tile_out;
+    std::vector<PixItem> cb3;      // 3-D C-bar: one item per source block
     for (int t = 0; t < n; ++t) {
-        const int N = probs[t].N, nn = N / probs[t].kappa, M = nn * nn, m = N * N;
+        const int dd = dim_of(probs[t]);
+        const int N = probs[t].N, nn = N / probs[t].kappa, M = ipow(nn, dd), m = ipow(N, dd);
+        const int rows_all = ipow(N, dd - 1);         // lines of N points
         b->prep_off.push_back((int)prep.size());
         for (int k = 0; k < M; k += 256) prep.push_back({t, k});
         b->prep_cnt.push_back((int)prep.size() - b->prep_off.back());
@@ -333,12 +363,17 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         for (int i = 0; i < m; i += 256) pix.push_back({t, i});
         b->pix_cnt.push_back((int)pix.size() - b->pix_off.back());
         b->cbar_off.push_back((int)cb.size());
-        for (int w1 = 0; w1 < nn; ++w1) cb.push_back({t, w1, 0, 0});
+        b->cbar3_off.push_back((int)cb3.size());
+        if (dd == 2)
+            for (int w1 = 0; w1 < nn; ++w1) cb.push_back({t, w1, 0, 0});
+        else
+            for (int k = 0; k < M; ++k) cb3.push_back({t, k});
         b->cbar_cnt.push_back((int)cb.size() - b->cbar_off.back());
+        b->cbar3_cnt.push_back((int)cb3.size() - b->cbar3_off.back());
         b->sep_off.push_back((int)sep.size());
         if (separable(t)) {
             const int lines = sep_lines_per_cta(N);
-            for (int r0 = 0; r0 < N; r0 += lines) sep.push_back({t, r0, std::min(lines, N - r0)});
+            for (int r0 = 0; r0 < rows_all; r0 += lines) sep.push_back({t, r0, std::min(lines, rows_all - r0)});
             b->sep_cnt.push_back((int)sep.size() - b->sep_off.back());
             b->ct_off.push_back((int)ctp.size());
             b->ct_cnt.push_back(0);
@@ -348,15 +383,17 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         const int tiles = (m + tile_out - 1) / tile_out;
         // batched form: about 12 items per SM over the whole batch (six waves
         // of the persistent grid), each pair split evenly
+        // (input lines staged per item: at most 32 KB of shared memory)
+        const int rows_cap = std::max(1, (int)(32768 / (tsz * (size_t)N)));
         const long splits_b = std::max<long>(1, (12L * sm + total_tiles - 1) / std::max<long>(1, total_tiles));
-        const int rows_b = pick_in_rows(N, 1, (int)std::min<long>(splits_b, N));
+        const int rows_b = std::min(rows_cap, pick_in_rows(rows_all, 1, (int)std::min<long>(splits_b, rows_all)));
         for (int o = 0; o < m; o += tile_out)
-            for (int r0 = 0; r0 < N; r0 += rows_b) ctb.push_back({t, o, r0, std::min(rows_b, N - r0)});
+            for (int r0 = 0; r0 < rows_all; r0 += rows_b) ctb.push_back({t, o, r0, std::min(rows_b, rows_all - r0)});
         // plain form: one pair fills the GPU, about 2 items per SM
-        const int rows_p = pick_in_rows(N, tiles, 2 * sm);
+        const int rows_p = std::min(rows_cap, pick_in_rows(rows_all, tiles, 2 * sm));
         b->ct_off.push_back((int)ctp.size());
         for (int o = 0; o < m; o += tile_out)
-            for (int r0 = 0; r0 < N; r0 += rows_p) ctp.push_back({t, o, r0, std::min(rows_p, N - r0)});
+            for (int r0 = 0; r0 < rows_all; r0 += rows_p) ctp.push_back({t, o, r0, std::min(rows_p, rows_all - r0)});
         b->ct_cnt.push_back((int)ctp.size() - b->ct_off.back());
         int maxrows = 0;
         for (auto& it : ctb) maxrows = std::max(maxrows, it.in_rows);
@@ -365,6 +402,7 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         b->ct_cfg_p.in_rows = b->ct_cfg_b.in_rows;
     }
     b->n_prep = (int)prep.size(); b->n_pix = (int)pix.size(); b->n_cbar = (int)cb.size();
+    b->n_cbar3 = (int)cb3.size();
     b->n_ct_b = (int)ctb.size();
     b->n_sep = (int)sep.size();
     // device allocation
@@ -377,7 +415,8 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
     const size_t o_ctb = align_up(o_cb + sizeof(CbarItem) * cb.size());
     const size_t o_ctp = align_up(o_ctb + sizeof(CtItem) * ctb.size());
     const size_t o_sep = align_up(o_ctp + sizeof(CtItem) * ctp.size());
-    const size_t total = align_up(o_sep + sizeof(SepItem) * sep.size());
+    const size_t o_cb3 = align_up(o_sep + sizeof(SepItem) * sep.size());
+    const size_t total = align_up(o_cb3 + sizeof(PixItem) * cb3.size());
     if (cudaMalloc(&b->dmem, total) != cudaSuccess) { batch_free(b); return fail(QWB_ERR_OOM, "batch workspace"); }
     b->pairs_d = (PairDev*)(b->dmem + o_pairs);
     b->outs_d = (PairOut*)(b->dmem + o_outs);
@@ -388,6 +427,7 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
     b->ct_b_items_d = (CtItem*)(b->dmem + o_ctb);
     b->ct_p_items_d = (CtItem*)(b->dmem + o_ctp);
     b->sep_items_d = (SepItem*)(b->dmem + o_sep);
+    b->cbar3_items_d = (PixItem*)(b->dmem + o_cb3);
     // coarse-plan staging
     size_t poff = 0;
     for (int t = 0; t < n; ++t) { b->plan_off.push_back(poff); poff += plan_layout(b->Ms[t]).total; }
@@ -407,11 +447,13 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
     // per-pair descriptors
     cudaStream_t s0 = 0;
     for (int t = 0; t < n; ++t) {
-        const int N = probs[t].N, kap = probs[t].kappa, nn = N / kap, M = nn * nn, m = N * N;
+        const int dd = dim_of(probs[t]);
+        const int N = probs[t].N, kap = probs[t].kappa, nn = N / kap, M = ipow(nn, dd), m = ipow(N, dd);
         char* base = b->dmem + pair_off[t];
         PairDev P;
         std::memset(&P, 0, sizeof(P));
         P.N = N; P.kappa = kap; P.n = nn; P.M = M; P.p = probs[t].p;
+        P.d = dd; P.m = m; P.rows = ipow(N, dd - 1);
         P.mu_c = (double*)base; P.nu_c = P.mu_c + M; P.mu_c_lo = P.nu_c + M; P.nu_c_lo = P.mu_c_lo + M;
         P.mu_rinv = P.nu_c_lo + M; P.nu_rinv = P.mu_rinv + M;
         P.mu_rinv32 = (float*)(P.nu_rinv + M); P.nu_rinv32 = P.mu_rinv32 + M;
@@ -429,12 +471,13 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         P.mu_up = base; base += align_up(tsz * m);
         P.nu_up = base; base += align_up(tsz * m);
         if (separable(t)) { P.tsep = base; base += align_up(tsz * m); }
+        if (separable(t) && dd == 3) { P.tsep2 = base; base += align_up(tsz * m); }
         if (flags & QWB_FLAG_SYMMETRIC_DUAL) {   // the kept side's potentials (FP64)
             P.f_out = (double*)base; base += align_up(sizeof(double) * m);
             P.g_out = (double*)base; base += align_up(sizeof(double) * m);
         }
         const void *lo, *hi;
-        int st = ctx_table(ctx, N, probs[t].p, b->f64, s0, &lo, &hi);
+        int st = ctx_table(ctx, N, probs[t].p, b->f64, s0, &lo, &hi, dd);
         if (st) { batch_free(b); return st; }
         P.ctab_lo = lo; P.ctab_hi = hi;
         const PlanLayout L = plan_layout(M);
@@ -462,6 +505,7 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
     if (!st) st = up(b->pix_items_d, pix.data(), sizeof(PixItem) * pix.size());
     if (!st) st = up(b->cbar_items_d, cb.data(), sizeof(CbarItem) * cb.size());
     if (!st) st = up(b->sep_items_d, sep.data(), sizeof(SepItem) * sep.size());
+    if (!st) st = up(b->cbar3_items_d, cb3.data(), sizeof(PixItem) * cb3.size());
     if (!st) st = up(b->ct_b_items_d, ctb.data(), sizeof(CtItem) * ctb.size());
     if (!st) st = up(b->ct_p_items_d, ctp.data(), sizeof(CtItem) * ctp.size());
     if (!st) {
@@ -507,16 +551,22 @@ static int enqueue_coarse(qwb_batch* b, bool batched, cudaStream_t s) {
         if ((st = mark(b, 0, s))) return st;
         if ((st = launch_prepare(b->pairs_d, b->outs_d, b->prep_items_d, b->n_prep, b->f64, s))) return st;
         if ((st = mark(b, 1, s))) return st;
-        if (!(b->flags & QWB_FLAG_NO_WEIGHTED) &&
-            (st = launch_cbar(b->pairs_d, b->cbar_items_d, b->n_cbar, b->kappa_code, b->n_max, b->N_max, b->f64, s,
-                              b->cbar_variant)))
-            return st;
+        if (!(b->flags & QWB_FLAG_NO_WEIGHTED)) {
+            if ((st = launch_cbar(b->pairs_d, b->cbar_items_d, b->n_cbar, b->kappa_code, b->n_max2, b->N_max2,
+                                  b->f64, s, b->cbar_variant)))
+                return st;
+            if ((st = launch_cbar3(b->pairs_d, b->cbar3_items_d, b->n_cbar3, b->f64, s))) return st;
+        }
         return mark(b, 2, s);
     }
     for (int t = 0; t < b->n; ++t) {
         QWB_CUDA(cudaMemsetAsync(b->outs_d + t, 0, sizeof(PairOut), s));
         if ((st = launch_prepare(b->pairs_d, b->outs_d, b->prep_items_d + b->prep_off[t], b->prep_cnt[t], b->f64, s))) return st;
         if (b->flags & QWB_FLAG_NO_WEIGHTED) continue;
+        if (dim_of(b->probs[t]) == 3) {
+            if ((st = launch_cbar3(b->pairs_d, b->cbar3_items_d + b->cbar3_off[t], b->cbar3_cnt[t], b->f64, s))) return st;
+            continue;
+        }
         const int nn = b->probs[t].N / b->probs[t].kappa;
         const int kc = (b->probs[t].kappa == 1 || b->probs[t].kappa == 2 || b->probs[t].kappa == 4)
                            ? b->probs[t].kappa : -b->probs[t].kappa;
@@ -541,8 +591,8 @@ static int enqueue_fine(qwb_batch* b, bool batched, cudaStream_t s) {
             if ((st = launch_upsample(b->pairs_d, b->outs_d, b->pix_items_d, b->n_pix, b->f64, s))) return st;
             if ((st = mark(b, 6, s))) return st;
             for (int phase = 0; phase < 2; ++phase) {
-                if ((st = launch_sep(b->pairs_d, b->sep_items_d, b->n_sep, phase, 0, b->N_max, b->f64, cap, s))) return st;
-                if ((st = launch_sep(b->pairs_d, b->sep_items_d, b->n_sep, phase, 1, b->N_max, b->f64, cap, s))) return st;
+                for (int stage = 0; stage < b->sep_stages; ++stage)
+                    if ((st = launch_sep(b->pairs_d, b->sep_items_d, b->n_sep, phase, stage, b->N_max, b->f64, cap, s))) return st;
                 if ((st = launch_ctransform(b->pairs_d, b->ct_b_items_d, b->n_ct_b, phase, b->ct_cfg_b, b->N_max, b->f64, cap, s))) return st;
                 if (phase == 0 && (st = mark(b, 7, s))) return st;
             }
@@ -557,8 +607,8 @@ static int enqueue_fine(qwb_batch* b, bool batched, cudaStream_t s) {
             if ((st = launch_centre(b->pairs_d, b->outs_d, b->pair_ids_d, b->n, s, 1))) return st;
             if ((st = launch_upsample(b->pairs_d, b->outs_d, b->pix_items_d, b->n_pix, b->f64, s, 1))) return st;
             for (int phase = 0; phase < 2; ++phase) {
-                if ((st = launch_sep(b->pairs_d, b->sep_items_d, b->n_sep, phase, 0, b->N_max, b->f64, cap, s))) return st;
-                if ((st = launch_sep(b->pairs_d, b->sep_items_d, b->n_sep, phase, 1, b->N_max, b->f64, cap, s))) return st;
+                for (int stage = 0; stage < b->sep_stages; ++stage)
+                    if ((st = launch_sep(b->pairs_d, b->sep_items_d, b->n_sep, phase, stage, b->N_max, b->f64, cap, s))) return st;
                 if ((st = launch_ctransform(b->pairs_d, b->ct_b_items_d, b->n_ct_b, phase, b->ct_cfg_b, b->N_max, b->f64, cap, s))) return st;
             }
             if ((st = launch_lbsum(b->pairs_d, b->outs_d, b->pair_ids_d, b->n, b->f64, s, 1))) return st;
@@ -582,8 +632,8 @@ static int enqueue_fine(qwb_batch* b, bool batched, cudaStream_t s) {
             }
             for (int phase = 0; phase < 2; ++phase) {
                 const SepItem* si = b->sep_items_d + b->sep_off[t];
-                if ((st = launch_sep(b->pairs_d, si, b->sep_cnt[t], phase, 0, b->probs[t].N, b->f64, 0, s))) return st;
-                if ((st = launch_sep(b->pairs_d, si, b->sep_cnt[t], phase, 1, b->probs[t].N, b->f64, 0, s))) return st;
+                for (int stage = 0; stage < dim_of(b->probs[t]) && b->sep_cnt[t] > 0; ++stage)
+                    if ((st = launch_sep(b->pairs_d, si, b->sep_cnt[t], phase, stage, b->probs[t].N, b->f64, 0, s))) return st;
                 if ((st = launch_ctransform(b->pairs_d, b->ct_p_items_d + b->ct_off[t], b->ct_cnt[t], phase, c, b->probs[t].N, b->f64, 0, s))) return st;
             }
             if ((st = launch_lbsum(b->pairs_d, b->outs_d, id, 1, b->f64, s, side))) return st;
@@ -626,7 +676,7 @@ static int tune_cbar(qwb_batch* b, cudaStream_t s) {
     for (int v = 0; v < 2; ++v) {
         double ms;
         st = time_variant(s, b->ev[0], b->ev[1], [&] {
-            return launch_cbar(b->pairs_d, b->cbar_items_d, b->n_cbar, b->kappa_code, b->n_max, b->N_max,
+            return launch_cbar(b->pairs_d, b->cbar_items_d, b->n_cbar, b->kappa_code, b->n_max2, b->N_max2,
                                b->f64, s, v);
         }, &ms);
         if (st) return st;
@@ -715,36 +765,68 @@ static int run_pass(qwb_batch* b, int kind, bool batched, cudaStream_t s) {
 }
 
 // ---- host exact solves ---------------------------------------------------
-// C^min on the coarse grid as a table over block offsets (Sec. 3.3): the
-// per-axis gap between two blocks is max(0, kappa |dk| - (kappa - 1)) pixels,
-// C^min = (gap1^2 + gap2^2)^(p/2), rounded down so that the LP value stays a
-// lower bound.
+// Coarse-grid costs depend only on the block offset |k - l| per axis; tables
+// hold them for every offset, tab[(|dk1| * n + |dk2|) * n + |dk3|] (2-D: no dk3).
+static int grid_offset(int d, int nn, int k, int l) {
+    if (d == 3) {
+        const int a = std::abs(k / (nn * nn) - l / (nn * nn)), b = std::abs((k / nn) % nn - (l / nn) % nn);
+        return (a * nn + b) * nn + std::abs(k % nn - l % nn);
+    }
+    return std::abs(k / nn - l / nn) * nn + std::abs(k % nn - l % nn);
+}
+
+// |delta|^p from the exact squared length s, rounded down (round_down) or to
+// nearest: the centre cost feeds an exact solve, the minimum cost a bound.
+static double cost_of_sq(double s, double p, bool round_down) {
+    if (p == 2.0) return s;
+    double c = p == 1.0 ? std::sqrt(s) : std::pow(s, 0.5 * p);
+    if (round_down) {
+        if (p == 1.0) { if (c * c > s) c = std::nextafter(c, 0.0); }
+        else c *= 1.0 - std::ldexp(1.0, -49);
+    }
+    return c;
+}
+
+// C^min on the coarse grid (Sec. 3.3): the per-axis gap between two blocks is
+// max(0, kappa |dk| - (kappa - 1)) points, C^min = (sum of gap^2)^(p/2),
+// rounded down so that the LP value stays a lower bound.
 static void mincost_table(const qwb_problem& pr, std::vector<double>& tab) {
-    const int nn = pr.N / pr.kappa;
-    tab.resize((size_t)nn * nn);
+    const int nn = pr.N / pr.kappa, d = dim_of(pr), d3 = d == 3 ? nn : 1;
+    tab.resize((size_t)ipow(nn, d));
     for (int d1 = 0; d1 < nn; ++d1)
-        for (int d2 = 0; d2 < nn; ++d2) {
-            const double g1 = std::max(0, pr.kappa * d1 - (pr.kappa - 1));
-            const double g2 = std::max(0, pr.kappa * d2 - (pr.kappa - 1));
-            const double s = g1 * g1 + g2 * g2;   // exact integer
-            double c;
-            if (pr.p == 2.0) c = s;
-            else if (pr.p == 1.0) { c = std::sqrt(s); if (c * c > s) c = std::nextafter(c, 0.0); }
-            else c = std::pow(s, 0.5 * pr.p) * (1.0 - std::ldexp(1.0, -49));
-            tab[(size_t)d1 * nn + d2] = c;
-        }
+        for (int d2 = 0; d2 < nn; ++d2)
+            for (int dz = 0; dz < d3; ++dz) {
+                const double g1 = std::max(0, pr.kappa * d1 - (pr.kappa - 1));
+                const double g2 = std::max(0, pr.kappa * d2 - (pr.kappa - 1));
+                const double g3 = d == 3 ? std::max(0, pr.kappa * dz - (pr.kappa - 1)) : 0.0;
+                tab[((size_t)d1 * nn + d2) * d3 + dz] = cost_of_sq(g1 * g1 + g2 * g2 + g3 * g3, pr.p, true);
+            }
 }
 
 // C~ on the coarse grid as a table over block offsets: (kappa |dk|)^p.
 static void centre_cost_table(const qwb_problem& pr, std::vector<double>& tab) {
-    const int nn = pr.N / pr.kappa;
-    tab.resize((size_t)nn * nn);
+    const int nn = pr.N / pr.kappa, d = dim_of(pr), d3 = d == 3 ? nn : 1;
+    tab.resize((size_t)ipow(nn, d));
     for (int d1 = 0; d1 < nn; ++d1)
-        for (int d2 = 0; d2 < nn; ++d2) {
-            const double x = (double)pr.kappa * d1, y = (double)pr.kappa * d2;
-            const double s = x * x + y * y;
-            tab[(size_t)d1 * nn + d2] = pr.p == 2.0 ? s : (pr.p == 1.0 ? std::sqrt(s) : std::pow(s, 0.5 * pr.p));
-        }
+        for (int d2 = 0; d2 < nn; ++d2)
+            for (int dz = 0; dz < d3; ++dz) {
+                const double x = (double)pr.kappa * d1, y = (double)pr.kappa * d2;
+                const double z = d == 3 ? (double)pr.kappa * dz : 0.0;
+                tab[((size_t)d1 * nn + d2) * d3 + dz] = cost_of_sq(x * x + y * y + z * z, pr.p, false);
+            }
+}
+
+// Exact solve of a coarse problem whose cost is a block-offset table: the
+// grid network simplex (no M x M matrix) in 2-D, the dense one in 3-D.
+static int solve_table(const qwb_problem& pr, const std::vector<double>& tab, const double* a,
+                       const double* b, NSSolution& out, NSBasis* basis_out, const NSBasis* warm) {
+    const int nn = pr.N / pr.kappa, d = dim_of(pr);
+    if (d == 2) return network_simplex_grid(nn, tab.data(), a, b, out, -1, basis_out, warm);
+    const int M = ipow(nn, d);
+    std::vector<double> C((size_t)M * M);
+    for (int k = 0; k < M; ++k)
+        for (int l = 0; l < M; ++l) C[(size_t)k * M + l] = tab[grid_offset(d, nn, k, l)];
+    return network_simplex(M, M, C.data(), a, b, out, -1, warm, basis_out);
 }
 
 static int solve_pair(qwb_batch* b, int t) {
@@ -757,7 +839,7 @@ static int solve_pair(qwb_batch* b, int t) {
     centre_cost_table(pr, Ct);
     NSSolution sol;
     NSBasis basis;
-    int st = network_simplex_grid(pr.N / pr.kappa, Ct.data(), mc, nc, sol, -1, &basis);
+    int st = solve_table(pr, Ct, mc, nc, sol, &basis, nullptr);
     if (st) return st;
     const PlanLayout L = plan_layout(M);
     char* ph = b->plan_h + b->plan_off[t];
@@ -789,14 +871,14 @@ static int solve_pair(qwb_batch* b, int t) {
         std::vector<double> Cm;
         mincost_table(pr, Cm);
         NSSolution sm;
-        st = network_simplex_grid(pr.N / pr.kappa, Cm.data(), mc, nc, sm, -1, nullptr, &basis);
+        st = solve_table(pr, Cm, mc, nc, sm, nullptr, &basis);
         if (st) return st;
-        const int nn = pr.N / pr.kappa;
+        const int nn = pr.N / pr.kappa, dd = dim_of(pr);
         // g_j = min_i C_ij - f_i rounded down keeps f_i + g_j <= C_ij exactly
         std::vector<double> g(M, HUGE_VAL);
         for (int i = 0; i < M; ++i)
             for (int j = 0; j < M; ++j) {
-                const double c = Cm[(size_t)std::abs(i / nn - j / nn) * nn + std::abs(i % nn - j % nn)];
+                const double c = Cm[grid_offset(dd, nn, i, j)];
                 double v = c - sm.f[i];
                 if (v + sm.f[i] > c) v = std::nextafter(v, -HUGE_VAL);
                 g[j] = std::min(g[j], v);
@@ -1069,7 +1151,7 @@ int qwb_batch_potentials(qwb_batch* b, int32_t pair, double* f_d, double* g_d, v
     if (b->flags & QWB_FLAG_NO_DUAL) return fail(QWB_ERR_INVALID_ARG, "the batch skipped the dual pass");
     QWB_CUDA(cudaSetDevice(b->ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
-    const int m = b->probs[pair].N * b->probs[pair].N;
+    const int m = ipow(b->probs[pair].N, dim_of(b->probs[pair]));
     int st;
     const PairDev& P = b->pairs_h[pair];
     if (P.f_out) {   // both sides ran: the lower-bound kernel kept the better pair
@@ -1161,8 +1243,12 @@ int qwb_coarse_cost(qwb_ctx* ctx, const qwb_problem* prob, const double* mu_d, c
     QWB_CUDA(cudaMemsetAsync(b->outs_d, 0, sizeof(PairOut), s));
     if ((st = single_validate(b, s))) return st;
     const int kc = (prob->kappa == 1 || prob->kappa == 2 || prob->kappa == 4) ? prob->kappa : -prob->kappa;
-    if ((st = launch_cbar(b->pairs_d, b->cbar_items_d, b->n_cbar, kc, prob->N / prob->kappa, prob->N,
-                          b->f64, s))) return st;
+    if (dim_of(*prob) == 3) {
+        if ((st = launch_cbar3(b->pairs_d, b->cbar3_items_d, b->n_cbar3, b->f64, s))) return st;
+    } else if ((st = launch_cbar(b->pairs_d, b->cbar_items_d, b->n_cbar, kc, prob->N / prob->kappa, prob->N,
+                                 b->f64, s))) {
+        return st;
+    }
     const size_t M = b->Ms[0];
     if (mu_coarse_d) QWB_CUDA(cudaMemcpyAsync(mu_coarse_d, P.mu_c, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
     if (nu_coarse_d) QWB_CUDA(cudaMemcpyAsync(nu_coarse_d, P.nu_c, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));

@@ -84,20 +84,25 @@ __device__ __forceinline__ void atomic_min_fp(double* addr, double v) {
 // other p use the FP64 pow (error at most 2 ulp) widened by 2^-49 relative.
 template <typename T> struct CostPair { T lo, hi; };
 
-__device__ __forceinline__ CostPair<double> ground_cost_f64(int dr, int dc, double p) {
-    const double d2 = (double)dr * dr + (double)dc * dc;   // exact integer
+// Brackets of |delta|^p from the exact squared length d2 (an integer below 2^24).
+__device__ __forceinline__ CostPair<double> ground_cost_sq_f64(double d2, double p) {
     if (p == 2.0) return {d2, d2};
     if (p == 1.0) return {__dsqrt_rd(d2), __dsqrt_ru(d2)};
     if (d2 == 0.0) return {0.0, 0.0};
     const double c = pow(d2, 0.5 * p);
     return {__dmul_rd(c, 1.0 - 0x1p-49), __dmul_ru(c, 1.0 + 0x1p-49)};
 }
-__device__ __forceinline__ CostPair<float> ground_cost_f32(int dr, int dc, double p) {
-    const double d2 = (double)dr * dr + (double)dc * dc;
+__device__ __forceinline__ CostPair<float> ground_cost_sq_f32(double d2, double p) {
     if (p == 2.0) return {(float)d2, (float)d2};            // exact below 2^24
     if (p == 1.0) return {__fsqrt_rd((float)d2), __fsqrt_ru((float)d2)};
-    const CostPair<double> c = ground_cost_f64(dr, dc, p);
+    const CostPair<double> c = ground_cost_sq_f64(d2, p);
     return {__double2float_rd(c.lo), __double2float_ru(c.hi)};
+}
+__device__ __forceinline__ CostPair<double> ground_cost_f64(int dr, int dc, double p) {
+    return ground_cost_sq_f64((double)dr * dr + (double)dc * dc, p);   // exact integer
+}
+__device__ __forceinline__ CostPair<float> ground_cost_f32(int dr, int dc, double p) {
+    return ground_cost_sq_f32((double)dr * dr + (double)dc * dc, p);
 }
 
 }  // namespace qwb

@@ -40,6 +40,30 @@ __global__ void cost_table_kernel(int N, double p, T* lo, T* hi) {
     }
 }
 
+// 3-D tables: tab[(d1 * N + d2) * N + d3] brackets rho((d1, d2, d3))^p.
+template <typename T>
+__global__ void cost_table3_kernel(int N, double p, T* lo, T* hi) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * N * N) return;
+    const int d1 = idx / (N * N), d2 = (idx / N) % N, d3 = idx % N;
+    const double s = (double)d1 * d1 + (double)d2 * d2 + (double)d3 * d3;
+    if constexpr (sizeof(T) == 4) {
+        CostPair<float> c = ground_cost_sq_f32(s, p);
+        lo[idx] = c.lo; hi[idx] = c.hi;
+    } else {
+        CostPair<double> c = ground_cost_sq_f64(s, p);
+        lo[idx] = c.lo; hi[idx] = c.hi;
+    }
+}
+
+int launch_cost_tables3(int N, double p, bool f64, void* lo, void* hi, cudaStream_t stream) {
+    const int n = N * N * N, th = 256, bl = (n + th - 1) / th;
+    if (f64) cost_table3_kernel<double><<<bl, th, 0, stream>>>(N, p, (double*)lo, (double*)hi);
+    else cost_table3_kernel<float><<<bl, th, 0, stream>>>(N, p, (float*)lo, (float*)hi);
+    QWB_LAUNCHED();
+    return QWB_OK;
+}
+
 int launch_cost_tables(int N, double p, bool f64, void* lo, void* hi, cudaStream_t stream) {
     const int n = N * N, th = 256, bl = (n + th - 1) / th;
     if (f64) cost_table_kernel<double><<<bl, th, 0, stream>>>(N, p, (double*)lo, (double*)hi);
@@ -48,10 +72,12 @@ int launch_cost_tables(int N, double p, bool f64, void* lo, void* hi, cudaStream
     return QWB_OK;
 }
 
-// rho(x-bar, x)^p bracket for the TV weights, x-bar = ((N-1)/2, (N-1)/2).
-__device__ __forceinline__ double tv_weight_hi(int r, int c, int N, double p) {
+// rho(x-bar, x)^p bracket for the TV weights, x-bar = the grid centre
+// ((N-1)/2 on every axis); z < 0 for 2-D points.
+__device__ __forceinline__ double tv_weight_hi(int r, int c, int N, double p, int z = -1) {
     const double dr = r - 0.5 * (N - 1), dc = c - 0.5 * (N - 1);
-    const double d2 = dr * dr + dc * dc;                  // exact (quarter integers)
+    const double dz = z >= 0 ? z - 0.5 * (N - 1) : 0.0;
+    const double d2 = dr * dr + dc * dc + dz * dz;        // exact (quarter integers)
     if (p == 2.0) return d2;
     if (p == 1.0) return __dsqrt_ru(d2);
     if (d2 == 0.0) return 0.0;
@@ -73,25 +99,34 @@ __global__ void prepare_kernel(const PairDev* __restrict__ pairs, PairOut* __res
     int bad_mu = 0, bad_nu = 0;
     if (k < P.M) {
         const int N = P.N, kap = P.kappa, n = P.n;
-        const int k1 = k / n, k2 = k % n;
+        // block coordinates; its kappa^d points in row-major order
+        const int k1 = P.d == 3 ? k / (n * n) : k / n;
+        const int k2 = P.d == 3 ? (k / n) % n : k % n;
+        const int k3 = P.d == 3 ? k % n : 0;
+        const int pts = P.d == 3 ? kap * kap * kap : kap * kap;
         double mu_rn = 0.0, mu_rd = 0.0, nu_rn = 0.0, nu_rd = 0.0, mu_ru = 0.0, nu_ru = 0.0;
         double mu_w = 0.0, nu_w = 0.0;
-        for (int t1 = 0; t1 < kap; ++t1) {
-            const int row = (k1 * kap + t1) * N + k2 * kap;
-            for (int t2 = 0; t2 < kap; ++t2) {
-                const double x = P.mu[row + t2], y = P.nu[row + t2];
-                reinterpret_cast<T*>(P.mu_up)[row + t2] = from_double_ru<T>(x);
-                reinterpret_cast<T*>(P.nu_up)[row + t2] = from_double_ru<T>(y);
-                reinterpret_cast<T*>(P.mu_t)[row + t2] = (T)x;
-                reinterpret_cast<T*>(P.nu_t)[row + t2] = (T)y;
-                const double w = tv_weight_hi(k1 * kap + t1, k2 * kap + t2, N, P.p);
-                mu_w = __fma_ru(w, x, mu_w);
-                nu_w = __fma_ru(w, y, nu_w);
-                bad_mu |= !(x >= 0.0) || !isfinite(x);
-                bad_nu |= !(y >= 0.0) || !isfinite(y);
-                mu_rn += x; mu_rd = __dadd_rd(mu_rd, x); mu_ru = __dadd_ru(mu_ru, x);
-                nu_rn += y; nu_rd = __dadd_rd(nu_rd, y); nu_ru = __dadd_ru(nu_ru, y);
+        for (int q = 0; q < pts; ++q) {
+            int c1, c2, c3, i;
+            if (P.d == 3) {
+                c1 = k1 * kap + q / (kap * kap); c2 = k2 * kap + (q / kap) % kap; c3 = k3 * kap + q % kap;
+                i = (c1 * N + c2) * N + c3;
+            } else {
+                c1 = k1 * kap + q / kap; c2 = k2 * kap + q % kap; c3 = -1;
+                i = c1 * N + c2;
             }
+            const double x = P.mu[i], y = P.nu[i];
+            reinterpret_cast<T*>(P.mu_up)[i] = from_double_ru<T>(x);
+            reinterpret_cast<T*>(P.nu_up)[i] = from_double_ru<T>(y);
+            reinterpret_cast<T*>(P.mu_t)[i] = (T)x;
+            reinterpret_cast<T*>(P.nu_t)[i] = (T)y;
+            const double w = tv_weight_hi(c1, c2, N, P.p, c3);
+            mu_w = __fma_ru(w, x, mu_w);
+            nu_w = __fma_ru(w, y, nu_w);
+            bad_mu |= !(x >= 0.0) || !isfinite(x);
+            bad_nu |= !(y >= 0.0) || !isfinite(y);
+            mu_rn += x; mu_rd = __dadd_rd(mu_rd, x); mu_ru = __dadd_ru(mu_ru, x);
+            nu_rn += y; nu_rd = __dadd_rd(nu_rd, y); nu_ru = __dadd_ru(nu_ru, y);
         }
         P.mu_c[k] = mu_rn; P.mu_c_lo[k] = mu_rd; P.mu_c_hi[k] = mu_ru;
         P.nu_c[k] = nu_rn; P.nu_c_lo[k] = nu_rd; P.nu_c_hi[k] = nu_ru;
@@ -403,6 +438,79 @@ cbar_kernel(const PairDev* __restrict__ pairs, const CbarItem* __restrict__ item
     }
 }
 
+// --------------------------------------------------------------------------
+// cbar3: C-bar on 3-D grids (volumes), the same definition and rounding as
+// cbar_kernel: num_kl = sum_{a in X_k} mu_a sum_{b in Y_l} nu_b rho(a, b)^p
+// with upward-rounded FMAs (inner sums over b first), then multiplied by
+// upward-rounded reciprocals of the block masses.  One CTA per source block
+// k stages mu's block; its threads walk the target blocks l.  Costs come from
+// the 3-D upper-bracket table tab[(|d1| * N + |d2|) * N + |d3|].
+// --------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+cbar3_kernel(const PairDev* __restrict__ pairs, const PixItem* __restrict__ items) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const PixItem I = items[blockIdx.x];
+    const PairDev& P = pairs[I.pair];
+    const int N = P.N, kap = P.kappa, n = P.n, M = P.M, k = I.start;
+    const int pts = kap * kap * kap;
+    T* mu_s = reinterpret_cast<T*>(smem_raw);
+    const T* mu_up = reinterpret_cast<const T*>(P.mu_up);
+    const T* nu_up = reinterpret_cast<const T*>(P.nu_up);
+    const T* tab = reinterpret_cast<const T*>(P.ctab_hi);
+    const int k1 = k / (n * n), k2 = (k / n) % n, k3 = k % n;
+    for (int q = threadIdx.x; q < pts; q += blockDim.x) {
+        const int a1 = k1 * kap + q / (kap * kap), a2 = k2 * kap + (q / kap) % kap, a3 = k3 * kap + q % kap;
+        mu_s[q] = mu_up[(a1 * N + a2) * N + a3];
+    }
+    __syncthreads();
+    const T rk = sizeof(T) == 4 ? (T)P.mu_rinv32[k] : (T)P.mu_rinv[k];
+    for (int l = threadIdx.x; l < M; l += blockDim.x) {
+        const int l1 = l / (n * n), l2 = (l / n) % n, l3 = l % n;
+        const int D1 = kap * (k1 - l1), D2 = kap * (k2 - l2), D3 = kap * (k3 - l3);
+        const int nb = (l1 * kap * N + l2 * kap) * N + l3 * kap;     // first point of Y_l
+        T acc = T(0);
+        for (int qa = 0; qa < pts; ++qa) {
+            const int a1 = qa / (kap * kap), a2 = (qa / kap) % kap, a3 = qa % kap;
+            T inner = T(0);
+            for (int qb = 0; qb < pts; ++qb) {
+                const int b1 = qb / (kap * kap), b2 = (qb / kap) % kap, b3 = qb % kap;
+                const int e1 = abs(D1 + a1 - b1), e2 = abs(D2 + a2 - b2), e3 = abs(D3 + a3 - b3);
+                inner = fma_ru(nu_up[nb + (b1 * N + b2) * N + b3], tab[(e1 * N + e2) * N + e3], inner);
+            }
+            acc = fma_ru(mu_s[qa], inner, acc);
+        }
+        const T rl = sizeof(T) == 4 ? (T)P.nu_rinv32[l] : (T)P.nu_rinv[l];
+        double out;
+        if (rk > T(0) && rl > T(0)) {
+            out = widen_f32(mul_ru(mul_ru(acc, rk), rl));
+        } else if (P.mu_c_lo[k] > 0.0 && P.nu_c_lo[l] > 0.0) {
+            out = __dmul_ru(__dmul_ru((double)acc, P.mu_rinv[k]), P.nu_rinv[l]);
+        } else {                      // a zero-mass block: the unweighted mean cost
+            double mean = 0.0;
+            for (int qa = 0; qa < pts; ++qa)
+                for (int qb = 0; qb < pts; ++qb) {
+                    const int e1 = abs(D1 + qa / (kap * kap) - qb / (kap * kap));
+                    const int e2 = abs(D2 + (qa / kap) % kap - (qb / kap) % kap);
+                    const int e3 = abs(D3 + qa % kap - qb % kap);
+                    mean = __dadd_ru(mean, (double)tab[(e1 * N + e2) * N + e3]);
+                }
+            out = __ddiv_ru(mean, (double)pts * pts);
+        }
+        P.cbar[(size_t)k * M + l] = out;
+    }
+}
+
+int launch_cbar3(const PairDev* pairs_d, const PixItem* items, int n_items, bool f64,
+                 cudaStream_t stream) {
+    if (n_items <= 0) return QWB_OK;
+    const size_t smem = (f64 ? 8 : 4) * (size_t)16 * 16 * 16;      // kappa <= 16
+    if (f64) cbar3_kernel<double><<<n_items, 256, smem, stream>>>(pairs_d, items);
+    else cbar3_kernel<float><<<n_items, 256, smem, stream>>>(pairs_d, items);
+    QWB_LAUNCHED();
+    return QWB_OK;
+}
+
 static size_t cbar_smem(size_t tsz, int kap, int n, int N, bool windows) {
     const size_t win = windows ? (size_t)2 * (2 * n - 1) * CBAR_WPAD : (size_t)2 * (2 * kap - 1) * N;
     return tsz * ((size_t)2 * CBAR_S * kap * N + win + (size_t)CBAR_S * n * n + (size_t)2 * CBAR_S * n);
@@ -551,6 +659,41 @@ __device__ T block_pair_num(const PairDev& P, int k, int l) {
     return acc;
 }
 
+// The same numerator on 3-D grids (the rounding and order of cbar3_kernel).
+template <typename T>
+__device__ T block_pair_num3(const PairDev& P, int k, int l) {
+    const int N = P.N, n = P.n, kap = P.kappa, pts = kap * kap * kap;
+    const T* tab = reinterpret_cast<const T*>(P.ctab_hi);
+    const T* mu_up = reinterpret_cast<const T*>(P.mu_up);
+    const T* nu_up = reinterpret_cast<const T*>(P.nu_up);
+    const int k1 = k / (n * n), k2 = (k / n) % n, k3 = k % n;
+    const int l1 = l / (n * n), l2 = (l / n) % n, l3 = l % n;
+    const int D1 = kap * (k1 - l1), D2 = kap * (k2 - l2), D3 = kap * (k3 - l3);
+    const int mb = (k1 * kap * N + k2 * kap) * N + k3 * kap, nb = (l1 * kap * N + l2 * kap) * N + l3 * kap;
+    T acc = T(0);
+    for (int qa = 0; qa < pts; ++qa) {
+        const int a1 = qa / (kap * kap), a2 = (qa / kap) % kap, a3 = qa % kap;
+        T inner = T(0);
+        for (int qb = 0; qb < pts; ++qb) {
+            const int b1 = qb / (kap * kap), b2 = (qb / kap) % kap, b3 = qb % kap;
+            const int e1 = abs(D1 + a1 - b1), e2 = abs(D2 + a2 - b2), e3 = abs(D3 + a3 - b3);
+            inner = fma_ru(nu_up[nb + (b1 * N + b2) * N + b3], tab[(e1 * N + e2) * N + e3], inner);
+        }
+        acc = fma_ru(mu_up[mb + (a1 * N + a2) * N + a3], inner, acc);
+    }
+    return acc;
+}
+
+// Flat index of point t (row-major inside the block) of coarse block k.
+__device__ __forceinline__ int block_point(const PairDev& P, int k, int t) {
+    const int N = P.N, n = P.n, kap = P.kappa;
+    if (P.d == 3) {
+        const int k1 = k / (n * n), k2 = (k / n) % n, k3 = k % n;
+        return ((k1 * kap + t / (kap * kap)) * N + k2 * kap + (t / kap) % kap) * N + k3 * kap + t % kap;
+    }
+    return (k / n * kap + t / kap) * N + (k % n) * kap + t % kap;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(PRIMAL_THREADS, 2)
 primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
@@ -567,8 +710,9 @@ primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
     T* At = Bt + M;
     T* a = reinterpret_cast<T*>(P.a);
     T* b = reinterpret_cast<T*>(P.b);
-    const T kinv4 = T(1) / (T)((double)kap * kap * kap * kap);
-    const T kk = (T)(kap * kap);
+    const int kpts = P.d == 3 ? kap * kap * kap : kap * kap;     // points per block, kappa^d
+    const T kinvK = T(1) / (T)((double)kpts * kpts);             // the kernel value kappa^-2d
+    const T kk = (T)kpts;
 
     // the coarse plan's CSR and CSC (indices and pass-type values), staged in
     // shared memory when they fit: every sweep walks them twice
@@ -597,7 +741,7 @@ primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
     const T* nu_t = reinterpret_cast<const T*>(P.nu_t);
     for (int l = threadIdx.x; l < M; l += blockDim.x) Bt[l] = kk;    // b = 1
     __syncthreads();
-    const bool vec4 = (sizeof(T) == 4) && (kap == 4);              // block rows are one float4
+    const bool vec4 = (sizeof(T) == 4) && (kap == 4) && P.d == 2;  // block rows are one float4
     for (int sweep = 0; sweep < P.sweeps; ++sweep) {
         for (int half = 0; half < 2; ++half) {
             // half 0: a = mu / (pi-hat b), A = block sums of a
@@ -633,7 +777,7 @@ primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
                         if (k < M) {
                             T r = T(0);
                             for (int e = ptr[k]; e < ptr[k + 1]; ++e) r += val[e] * other[idx[e]];
-                            r *= kinv4;
+                            r *= kinvK;
                             const float inv = r > T(0) ? (float)(T(1) / r) : 0.0f;
                             const int k1 = k / n, k2 = k - (k / n) * n;
                             T s = T(0);
@@ -652,17 +796,14 @@ primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
                 for (int k = threadIdx.x; k < M; k += blockDim.x) {
                     T r = T(0);
                     for (int e = ptr[k]; e < ptr[k + 1]; ++e) r += val[e] * other[idx[e]];
-                    r *= kinv4;
+                    r *= kinvK;
                     const T inv = r > T(0) ? T(1) / r : T(0);
-                    const int k1 = k / n, k2 = k % n;
                     T s = T(0);
-                    for (int t1 = 0; t1 < kap; ++t1) {
-                        const int base = (k1 * kap + t1) * N + k2 * kap;
-                        for (int t2 = 0; t2 < kap; ++t2) {
-                            const T v = src[base + t2] * inv;
-                            dst[base + t2] = v;
-                            s += v;
-                        }
+                    for (int t = 0; t < kpts; ++t) {
+                        const int i = block_point(P, k, t);
+                        const T v = src[i] * inv;
+                        dst[i] = v;
+                        s += v;
                     }
                     mine[k] = s;
                 }
@@ -678,9 +819,9 @@ primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
     // fixed point is reached after one sweep, whereas from the rounded FP32
     // state IPF on the tree-shaped support of pi~ barely contracts.  They stop
     // once the FP64 residual is at rounding level (at most four sweeps).
-    const double k4 = (double)kap * kap * kap * kap;
+    const double k4 = (double)kpts * kpts;                       // kappa^2d
     const double kinv4_rn = 1.0 / k4, kinv4_lo = __drcp_rd(k4), kinv4_hi = __drcp_ru(k4);
-    for (int l = threadIdx.x; l < M; l += blockDim.x) Bd[l] = (double)(kap * kap);
+    for (int l = threadIdx.x; l < M; l += blockDim.x) Bd[l] = (double)kpts;
     __syncthreads();
     int fp64_sweeps = 0;
     for (;;) {
@@ -712,26 +853,18 @@ primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
         __syncthreads();
     }
     // the certified plan is pi-hat_xi(i,j) = alpha_k mu_i kappa^-4 pi~_kl beta_l nu_j
-    if (P.a_out) {
-        for (int k = threadIdx.x; k < M; k += blockDim.x) {
-            const int k1 = k / n, k2 = k % n;
-            for (int t1 = 0; t1 < kap; ++t1)
-                for (int t2 = 0; t2 < kap; ++t2) {
-                    const int i = (k1 * kap + t1) * N + k2 * kap + t2;
-                    P.a_out[i] = alpha[k] * P.mu[i];
-                }
-        }
-    }
-    if (P.b_out) {
-        for (int l = threadIdx.x; l < M; l += blockDim.x) {
-            const int l1 = l / n, l2 = l % n;
-            for (int t1 = 0; t1 < kap; ++t1)
-                for (int t2 = 0; t2 < kap; ++t2) {
-                    const int j = (l1 * kap + t1) * N + l2 * kap + t2;
-                    P.b_out[j] = beta[l] * P.nu[j];
-                }
-        }
-    }
+    if (P.a_out)
+        for (int k = threadIdx.x; k < M; k += blockDim.x)
+            for (int t = 0; t < kpts; ++t) {
+                const int i = block_point(P, k, t);
+                P.a_out[i] = alpha[k] * P.mu[i];
+            }
+    if (P.b_out)
+        for (int l = threadIdx.x; l < M; l += blockDim.x)
+            for (int t = 0; t < kpts; ++t) {
+                const int j = block_point(P, l, t);
+                P.b_out[j] = beta[l] * P.nu[j];
+            }
 
     // ---- certified marginals and TV sums ---------------------------------
     // rho_k = alpha_k kappa^-4 sum_l pi~_kl beta_l nu~_l ;  mu-hat = rho_k mu
@@ -777,7 +910,8 @@ primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
         int lo = 0, hi = M;
         while (hi - lo > 1) { const int mid = (lo + hi) >> 1; if (rp[mid] <= e) lo = mid; else hi = mid; }
         const int k = lo, l = ci[e];
-        const T num = kap == 4 ? block_pair_num<T, 4>(P, k, l) : block_pair_num<T, 0>(P, k, l);
+        const T num = P.d == 3 ? block_pair_num3<T>(P, k, l)
+                               : (kap == 4 ? block_pair_num<T, 4>(P, k, l) : block_pair_num<T, 0>(P, k, l));
         const double term = __dmul_ru(__dmul_ru(__dmul_ru(__dmul_ru(P.val[e], kinv4_hi), alpha[k]), beta[l]),
                                       (double)num);
         cost = __dadd_ru(cost, term);
@@ -866,13 +1000,38 @@ __global__ void upsample_kernel(const PairDev* __restrict__ pairs, const PairOut
     const PairDev& P = pairs[I.pair];
     const int i = I.start + threadIdx.x;
     const int N = P.N, n = P.n, kap = P.kappa;
-    if (i >= N * N) return;
+    if (i >= P.m) return;
     const double s = outs[P.out_index].centre_shift;
     const double* fc = side ? P.g_coarse : P.f_coarse;   // the coarse potential upscaled
-    const int r = i / N, c = i % N;
+    const int r = P.d == 3 ? i / (N * N) : i / N, c = P.d == 3 ? (i / N) % N : i % N;
     double v;
     if (n == 1) {
         v = fc[0] - s;
+    } else if (P.d == 3) {
+        // trilinear: interpolate along the first axis, then the second, then
+        // the third (the tensor-product rule, per axis as in two dimensions)
+        const int z = i % N;
+        const int den = 2 * kap;
+        const double inv = 1.0 / den;
+        int k0[3];
+        double w[3];
+        const int x[3] = {r, c, z};
+        for (int a = 0; a < 3; ++a) {
+            const int num = 2 * x[a] - kap + 1;
+            const int fl = num >= 0 ? num / den : -((-num + den - 1) / den);
+            k0[a] = min(max(fl, 0), n - 2);
+            w[a] = (double)(num - den * k0[a]) * inv;
+        }
+        double h[2];
+        for (int e3 = 0; e3 < 2; ++e3) {
+            double g2[2];
+            for (int e2 = 0; e2 < 2; ++e2) {
+                const int b = ((k0[0]) * n + k0[1] + e2) * n + k0[2] + e3;
+                g2[e2] = (1.0 - w[0]) * (fc[b] - s) + w[0] * (fc[b + n * n] - s);
+            }
+            h[e3] = (1.0 - w[1]) * g2[0] + w[1] * g2[1];
+        }
+        v = (1.0 - w[2]) * h[0] + w[2] * h[1];
     } else {
         // t = (x - (kappa-1)/2) / kappa = (2x - kappa + 1) / (2 kappa): the cell
         // index by integer floor division, the weight from the integer
@@ -954,7 +1113,8 @@ ctransform_kernel(const PairDev* __restrict__ pairs, const CtItem* __restrict__ 
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const CtItem I = items[it];
         const PairDev& P = pairs[I.pair];
-        const int N = P.N, m = N * N;
+        const int N = P.N, m = P.m;
+        const bool d3 = P.d == 3;
         const T* h = reinterpret_cast<const T*>(phase == 0 ? P.fhat : P.g);
         T* out = reinterpret_cast<T*>(phase == 0 ? P.g : P.f);
         const int nin = I.in_rows * N;
@@ -966,7 +1126,10 @@ ctransform_kernel(const PairDev* __restrict__ pairs, const CtItem* __restrict__ 
             T mins[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) mins[r] = pos_inf<T>();
+            // a line of N points: every coordinate but the last is fixed
+            // (2-D: the row j1; 3-D: (ja, jb)), j2 is the last coordinate
             const int j1 = o / N, j2 = o % N;
+            const int ja = d3 ? j1 / N : j1, jb = d3 ? j1 % N : 0;
             const T* tab = reinterpret_cast<const T*>(P.ctab_lo);
             for (int c0 = 0; c0 < N; c0 += TC) {
                 T colq[NQ];
@@ -979,13 +1142,14 @@ ctransform_kernel(const PairDev* __restrict__ pairs, const CtItem* __restrict__ 
                 }
                 for (int r1 = 0; r1 < I.in_rows; ++r1) {
                     const int i1 = I.in_row0 + r1;
+                    const int ia = d3 ? i1 / N : i1, ib = d3 ? i1 % N : 0;
                     T q[NQ];
                     if constexpr (P2) {
-                        const T A = (T)((i1 - j1) * (i1 - j1));
+                        const T A = (T)((ia - ja) * (ia - ja) + (ib - jb) * (ib - jb));
 #pragma unroll
                         for (int e = 0; e < NQ; ++e) q[e] = A + colq[e];      // exact integers
                     } else {
-                        const T* trow = tab + (size_t)abs(i1 - j1) * N;
+                        const T* trow = tab + ((size_t)abs(ia - ja) * (d3 ? N : 1) + abs(ib - jb)) * N;
 #pragma unroll
                         for (int e = 0; e < NQ; ++e) q[e] = trow[abs(c0 - j2 + e - (R - 1))];
                     }
@@ -1031,7 +1195,7 @@ ctransform_kernel(const PairDev* __restrict__ pairs, const CtItem* __restrict__ 
                     }
                 }
             }
-            if (I.in_rows < N) {      // partial minimum: combine across items
+            if (I.in_rows < P.rows) {      // partial minimum: combine across items
 #pragma unroll
                 for (int r = 0; r < R; ++r) atomic_min_fp(&out[o + r], mins[r]);
             } else {
@@ -1129,13 +1293,15 @@ sep_kernel(const PairDev* __restrict__ pairs, const SepItem* __restrict__ items,
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const SepItem I = items[it];
         const PairDev& P = pairs[I.pair];
-        const int N = P.N;
+        if (stage >= P.d) continue;                   // fewer axes than this stage
+        const int N = P.N, L = P.rows;                // L lines of N points
         const int Lp = (N + SEP_R - 1) / SEP_R * SEP_R;
         const int tpl = Lp / SEP_R;
-        const T* in;
-        T* out;
-        if (stage == 0) { in = reinterpret_cast<const T*>(phase == 0 ? P.fhat : P.g); out = reinterpret_cast<T*>(P.tsep); }
-        else { in = reinterpret_cast<const T*>(P.tsep); out = reinterpret_cast<T*>(phase == 0 ? P.g : P.f); }
+        const int last = P.d - 1;
+        const T* in = reinterpret_cast<const T*>(stage == 0 ? (phase == 0 ? P.fhat : P.g)
+                                                             : (stage == 1 ? P.tsep : P.tsep2));
+        T* out = reinterpret_cast<T*>(stage == last ? (phase == 0 ? P.g : P.f)
+                                                    : (stage == 0 ? P.tsep : P.tsep2));
         T* hs = reinterpret_cast<T*>(smem_raw);                 // [lines][Lp]
         T* os = hs + I.lines * Lp;                              // [lines][Lp + 1]
         for (int k = threadIdx.x; k < I.lines * Lp; k += blockDim.x) {
@@ -1167,14 +1333,14 @@ sep_kernel(const PairDev* __restrict__ pairs, const SepItem* __restrict__ items,
                         mins[r] = min3(mins[r], sub_rd(q[s - r + SEP_R - 1], fv[s]),
                                        sub_rd(q[s + 1 - r + SEP_R - 1], fv[s + 1]));
             }
-            const T sign = stage == 0 ? T(-1) : T(1);
+            const T sign = stage == last ? T(1) : T(-1);
 #pragma unroll
             for (int r = 0; r < SEP_R; ++r) os[line * (Lp + 1) + j0 + r] = sign * mins[r];
         }
         __syncthreads();
         for (int k = threadIdx.x; k < I.lines * N; k += blockDim.x) {
             const int j = k / I.lines, r = k - j * I.lines;
-            out[(size_t)j * N + I.line0 + r] = os[r * (Lp + 1) + j];
+            out[(size_t)j * L + I.line0 + r] = os[r * (Lp + 1) + j];
         }
         __syncthreads();
     }
@@ -1228,7 +1394,7 @@ __global__ void lbsum_kernel(const PairDev* __restrict__ pairs, PairOut* __restr
                              const int* __restrict__ pair_ids, int side) {
     __shared__ double red[33];
     const PairDev& P = pairs[pair_ids[blockIdx.x]];
-    const int m = P.N * P.N;
+    const int m = P.m;
     // side 0: the transforms ran f-hat -> g -> f.  Side 1 (upscaling from
     // g~): they ran g-hat -> f -> g, so the buffer named g holds the
     // potential on mu's side and the buffer named f the one on nu's side.

@@ -10,7 +10,8 @@ namespace qwb {
 // (MIXED) or double (F64); typed arrays are stored as void* and cast by the
 // kernels, which are templated on that type.
 struct PairDev {
-    int N, kappa, n, M;
+    int N, kappa, n, M;     // side, block side, coarse side, coarse points n^d
+    int d, m, rows;         // dimension (2 or 3), points N^d, lines N^(d-1)
     double p;
     const double* mu;       // N*N fine measures (FP64, caller-owned)
     const double* nu;
@@ -44,7 +45,8 @@ struct PairDev {
     const double* g_coarse; // M (the other coarse potential; upscaled when both sides are used)
     void* fhat; void* g; void* f;   // N*N (T)
     double* f_out; double* g_out;   // optional FP64 outputs
-    void* tsep;             // N*N (T) scratch of the separable p = 2 c-transform (may be null)
+    void* tsep;             // N^d (T) scratches of the separable p = 2 c-transform
+    void* tsep2;            // (tsep2: second buffer, d = 3 only; may be null)
     int ct_split;           // > 1 when c-transform outputs are combined by atomics
     int out_index;          // index into the results array
 };
@@ -74,6 +76,9 @@ struct CtConfig {
 };
 
 // Launchers.  All enqueue on `stream` and return a qwb status.
+int launch_cost_tables3(int N, double p, bool f64, void* lo, void* hi, cudaStream_t stream);
+int launch_cbar3(const PairDev* pairs_d, const PixItem* items, int n_items, bool f64,
+                 cudaStream_t stream);
 int launch_cost_tables(int N, double p, bool f64, void* lo, void* hi, cudaStream_t stream);
 int launch_prepare(const PairDev* pairs_d, PairOut* outs_d, const PixItem* items, int n_items,
                    bool f64, cudaStream_t stream);

@@ -114,6 +114,7 @@ extern "C" int qwb_ctransform_noalloc(int32_t N, double p, const double* h_d, do
     PairDev P;
     std::memset(&P, 0, sizeof(P));
     P.N = N; P.kappa = N; P.n = 1; P.M = 1; P.p = p;
+    P.d = 2; P.m = N * N; P.rows = N;
     P.ctab_lo = tab_lo; P.ctab_hi = tab_hi;
     P.fhat = h32; P.g = out32;
 
