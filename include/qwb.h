@@ -206,6 +206,26 @@ int qwb_dual_upscale_ctransform(qwb_ctx* ctx, const qwb_problem* prob, const dou
 int qwb_ctransform(qwb_ctx* ctx, int32_t N, double p, const double* h_d, double* out_d,
                    qwb_prec prec, void* stream);
 
+/* qwb_ctransform on [N]^d (d = 2 or 3) with an explicit launch shape instead
+ * of the default one, for tuning and for testing every compiled variant
+ * (Sec. 4, eq. lazy c-transform; the values do not depend on the shape).
+ * The transform runs over the N^d grid points, read as N^(d-1) lines of N:
+ *   R        outputs per thread (consecutive along a grid line), must divide N;
+ *   TC       input columns per register chunk, must divide N;
+ *   packing  0 scalar subtractions; 1 (MIXED only) two columns per packed
+ *            f32x2 subtraction; 2 (MIXED only) two input lines per packed
+ *            subtraction.
+ *   in_rows  input lines per work item (0 = the default split); work items
+ *            that see part of the input lines combine by atomic min.
+ * Compiled shapes: packing 0: (R, TC) in {1,2,4,8,16} x {same} and (16,8),
+ * (8,16); packing 1: (8,8), (16,8), (16,16); packing 2: (8,8), (16,8), (8,16),
+ * (16,16).  Other shapes return QWB_ERR_UNSUPPORTED.
+ * h_d, out_d: N^d FP64 device.  Synchronises `stream` before returning.
+ * Errors: INVALID_ARG, UNSUPPORTED, CUDA, OOM. */
+int qwb_ctransform_shape(qwb_ctx* ctx, int32_t N, int32_t d, double p, const double* h_d,
+                         double* out_d, int32_t R, int32_t TC, int32_t packing, int32_t in_rows,
+                         qwb_prec prec, void* stream);
+
 /* The same lazy c-transform (MIXED precision: h rounded up to FP32, result
  * rounded down, widened to FP64) for callers that cannot allocate device
  * memory when they need it -- for instance code running under a frozen or

@@ -59,6 +59,8 @@ SIGNATURES = [
                                               ctypes.POINTER(QwbResult), c_int32, c_void_p]),
     ("qwb_ctransform", c_int32, [c_void_p, c_int32, c_double, c_void_p, c_void_p, c_int32,
                                  c_void_p]),
+    ("qwb_ctransform_shape", c_int32, [c_void_p, c_int32, c_int32, c_double, c_void_p, c_void_p,
+                                       c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p]),
     ("qwb_ctransform_noalloc", c_int32, [c_int32, c_double, c_void_p, c_void_p, c_void_p]),
     ("qwb_ctransform_separable", c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_int32, c_void_p]),
     ("qwb_lb_adjoint", c_int32, [c_void_p, c_int32, c_double, c_void_p, c_void_p, c_double,

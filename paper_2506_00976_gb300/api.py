@@ -152,6 +152,15 @@ def ctransform(h, N, p, prec="mixed"):
     return out
 
 
+def ctransform_shape(h, N, p, R, TC, packing=0, in_rows=0, prec="mixed", d=2):
+    """qwb_ctransform_shape: the lazy c-transform on [N]^d with an explicit launch shape."""
+    out = torch.empty(N ** d, dtype=torch.float64, device=h.device)
+    check(_lib.load().qwb_ctransform_shape(context(h.device), int(N), int(d), float(p), _dev64(h, "h"),
+                                           _ptr(out), int(R), int(TC), int(packing), int(in_rows),
+                                           _prec(prec), _stream(h)), "qwb_ctransform_shape")
+    return out
+
+
 def ctransform_separable(h, N, prec="mixed"):
     """qwb_ctransform_separable: the p = 2 c-transform by separation over the grid axes."""
     out = torch.empty(N * N, dtype=torch.float64, device=h.device)

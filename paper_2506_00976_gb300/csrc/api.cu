@@ -323,6 +323,7 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
     std::vector<CtItem> ctb, ctp;
     std::vector<SepItem> sep;
     b->ct_cfg_b = pick_ct_config(N_gcd, all_p2);
+    b->ct_cfg_b.has_3d = b->has_3d;
     b->ct_cfg_p = b->ct_cfg_b;
     b->N_gcd = N_gcd;
     b->all_p2 = all_p2;
@@ -344,7 +345,7 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         if (!found) { ctx->tunes.push_back(TuneEntry{}); found = &ctx->tunes.back(); found->key = key.str(); }
         b->tune = found;
         if (found->ct_done && found->R > 0 && N_gcd % found->R == 0 && N_gcd % found->TC == 0) {
-            b->ct_cfg_b.R = found->R; b->ct_cfg_b.TC = found->TC; b->ct_cfg_b.packed = found->packed != 0;
+            b->ct_cfg_b.R = found->R; b->ct_cfg_b.TC = found->TC; b->ct_cfg_b.packed = found->packed;
         }
         if (found->cbar_done) b->cbar_variant = found->cbar_variant;
     }
@@ -624,6 +625,7 @@ static int enqueue_fine(qwb_batch* b, bool batched, cudaStream_t s) {
         if ((st = launch_upsample(b->pairs_d, b->outs_d, b->pix_items_d + b->pix_off[t], b->pix_cnt[t], b->f64, s))) return st;
         CtConfig c = b->ct_cfg_p;
         c.p2 = (b->probs[t].p == 2.0);
+        c.has_3d = dim_of(b->probs[t]) == 3;
         const int sides = (b->flags & QWB_FLAG_SYMMETRIC_DUAL) ? 2 : 1;
         for (int side = 0; side < sides; ++side) {
             if (side == 1) {
@@ -698,7 +700,8 @@ static int tune_ctransform(qwb_batch* b, cudaStream_t s) {
     if (!st) st = launch_upsample(b->pairs_d, b->outs_d, b->pix_items_d, b->n_pix, b->f64, s);
     if (st) return st;
     const int cand[][3] = {{4, 4, 0}, {8, 8, 0}, {16, 8, 0}, {16, 16, 0}, {8, 16, 0},
-                           {8, 8, 1}, {16, 8, 1}, {16, 16, 1}};
+                           {8, 8, 1}, {16, 8, 1}, {16, 16, 1},
+                           {8, 8, 2}, {16, 8, 2}, {8, 16, 2}, {16, 16, 2}};
     const int sm = b->ctx->sm_count > 0 ? b->ctx->sm_count : 148;
     std::ostringstream rep;
     double best = 1e30;
@@ -707,20 +710,20 @@ static int tune_ctransform(qwb_batch* b, cudaStream_t s) {
     for (auto& c : cand) {
         if (b->N_gcd % c[0] || b->N_gcd % c[1] || (c[2] && b->f64)) continue;
         CtConfig cfg = b->ct_cfg_b;
-        cfg.R = c[0]; cfg.TC = c[1]; cfg.packed = c[2] != 0;
+        cfg.R = c[0]; cfg.TC = c[1]; cfg.packed = c[2];
         double ms;
         st = time_variant(s, b->ev[0], b->ev[1], [&] {
             return launch_ctransform(b->pairs_d, b->ct_b_items_d, b->n_ct_b, 0, cfg, b->N_max, b->f64, sm, s);
         }, &ms);
         if (st) return st;
-        rep << (first ? "" : ", ") << "\"R" << c[0] << "xT" << c[1] << (c[2] ? "_packed" : "") << "\": " << ms;
+        rep << (first ? "" : ", ") << "\"R" << c[0] << "xT" << c[1] << (c[2] == 1 ? "_packed" : c[2] == 2 ? "_linepairs" : "") << "\": " << ms;
         first = false;
         if (ms < best) { best = ms; e->R = c[0]; e->TC = c[1]; e->packed = c[2]; }
     }
     rep << "}";
     e->ct_report = rep.str();
     e->ct_done = e->R > 0;
-    if (e->ct_done) { b->ct_cfg_b.R = e->R; b->ct_cfg_b.TC = e->TC; b->ct_cfg_b.packed = e->packed != 0; }
+    if (e->ct_done) { b->ct_cfg_b.R = e->R; b->ct_cfg_b.TC = e->TC; b->ct_cfg_b.packed = e->packed; }
     tune_cache_store(b->ctx);
     return QWB_OK;
 }
@@ -1135,7 +1138,7 @@ int qwb_batch_tuning(qwb_batch* b, char* json_out, int32_t capacity) {
     if (!b || !json_out || capacity <= 0) return fail(QWB_ERR_INVALID_ARG, "qwb_batch_tuning: bad argument");
     std::ostringstream o;
     o << "{\"key\": \"" << (b->tune ? b->tune->key : "") << "\", \"ctransform\": {\"R\": " << b->ct_cfg_b.R
-      << ", \"TC\": " << b->ct_cfg_b.TC << ", \"packed\": " << (b->ct_cfg_b.packed ? "true" : "false")
+      << ", \"TC\": " << b->ct_cfg_b.TC << ", \"packed\": " << b->ct_cfg_b.packed
       << ", \"candidates_ms\": " << (b->tune && !b->tune->ct_report.empty() ? b->tune->ct_report : "{}")
       << "}, \"cbar\": {\"min_ctas_per_sm\": " << (b->cbar_variant ? 3 : 2)
       << ", \"candidates_ms\": " << (b->tune && !b->tune->cbar_report.empty() ? b->tune->cbar_report : "{}")
@@ -1189,7 +1192,7 @@ static int single_batch(qwb_ctx* ctx, const qwb_problem* prob, int sweeps, qwb_p
                         qwb_batch** out, int flags = 0) {
     for (auto* b : ctx->single_cache)
         if (b->probs[0].N == prob->N && b->probs[0].kappa == prob->kappa && b->probs[0].p == prob->p &&
-            b->f64 == (prec == QWB_PREC_F64) && b->flags == flags) {
+            dim_of(b->probs[0]) == dim_of(*prob) && b->f64 == (prec == QWB_PREC_F64) && b->flags == flags) {
             b->sweeps = sweeps;
             b->pairs_h[0].sweeps = sweeps;
             *out = b;
@@ -1378,10 +1381,17 @@ int qwb_dual_upscale_ctransform(qwb_ctx* ctx, const qwb_problem* prob, const dou
     return QWB_OK;
 }
 
-int qwb_ctransform(qwb_ctx* ctx, int32_t N, double p, const double* h_d, double* out_d, qwb_prec prec,
-                   void* stream) {
+// The standalone transform with the default launch shape (shape == nullptr)
+// or a given one; in_rows > 0 re-splits the input lines into items of that
+// many lines each.
+static int ctransform_impl(qwb_ctx* ctx, int32_t N, double p, const double* h_d, double* out_d,
+                           qwb_prec prec, void* stream, const CtConfig* shape, int in_rows, int d = 2) {
     if (!ctx || !h_d || !out_d) return fail(QWB_ERR_INVALID_ARG, "qwb_ctransform: null argument");
-    qwb_problem prob{N, N, p};
+    if (d != 2 && d != 3) return fail(QWB_ERR_INVALID_ARG, "qwb_ctransform: d must be 2 or 3");
+    qwb_problem prob{N, N, p, d, 0};
+    if (d == 3)      // the coarse grid is unused here; pick a block side check_problem accepts
+        for (int k = 1; k <= 16; ++k)
+            if (N % k == 0 && N / k <= 16) { prob.kappa = k; break; }
     int st = check_problem(&prob);
     if (st) return st;
     std::lock_guard<std::mutex> lk(ctx->mtx);
@@ -1392,13 +1402,54 @@ int qwb_ctransform(qwb_ctx* ctx, int32_t N, double p, const double* h_d, double*
     PairDev& P = b->pairs_h[0];
     P.f_out = nullptr; P.g_out = nullptr;
     if ((st = single_upload(b, s))) return st;
-    if ((st = launch_to_work(h_d, P.fhat, P.g, N * N, b->f64, s))) return st;
     CtConfig c = b->ct_cfg_p;
+    if (shape) { c.R = shape->R; c.TC = shape->TC; c.packed = shape->packed; }
     c.p2 = (p == 2.0);
-    if ((st = launch_ctransform(b->pairs_d, b->ct_p_items_d, b->ct_cnt[0], 0, c, N, b->f64, 0, s))) return st;
-    if ((st = launch_from_work(P.g, out_d, N * N, b->f64, s))) return st;
+    const CtItem* items = b->ct_p_items_d;
+    int n_items = b->ct_cnt[0];
+    CtItem* own = nullptr;
+    const int m = ipow(N, d), lines = ipow(N, d - 1);
+    if (in_rows > 0) {           // a one-off item list with the requested split
+        std::vector<CtItem> it;
+        for (int o = 0; o < m; o += CT_TILE)
+            for (int r0 = 0; r0 < lines; r0 += in_rows) it.push_back({0, o, r0, std::min(in_rows, lines - r0)});
+        if (cudaMalloc((void**)&own, sizeof(CtItem) * it.size()) != cudaSuccess)
+            return fail(QWB_ERR_OOM, "qwb_ctransform_shape: item list");
+        QWB_CUDA(cudaMemcpyAsync(own, it.data(), sizeof(CtItem) * it.size(), cudaMemcpyHostToDevice, s));
+        items = own; n_items = (int)it.size();
+        c.in_rows = in_rows;
+    }
+    // outputs start at +inf: items that see part of the lines combine by atomic min
+    st = launch_to_work(h_d, P.fhat, P.g, m, b->f64, s);
+    if (!st) st = launch_ctransform(b->pairs_d, items, n_items, 0, c, N, b->f64, 0, s);
+    if (!st) st = launch_from_work(P.g, out_d, m, b->f64, s);
+    if (own) {
+        const cudaError_t e = cudaStreamSynchronize(s);
+        cudaFree(own);
+        if (e != cudaSuccess) return cuda_fail(e, "qwb_ctransform_shape");
+    }
+    if (st) return st;
     QWB_CUDA(cudaStreamSynchronize(s));
     return QWB_OK;
+}
+
+int qwb_ctransform(qwb_ctx* ctx, int32_t N, double p, const double* h_d, double* out_d, qwb_prec prec,
+                   void* stream) {
+    return ctransform_impl(ctx, N, p, h_d, out_d, prec, stream, nullptr, 0);
+}
+
+int qwb_ctransform_shape(qwb_ctx* ctx, int32_t N, int32_t d, double p, const double* h_d,
+                         double* out_d, int32_t R, int32_t TC, int32_t packing, int32_t in_rows,
+                         qwb_prec prec, void* stream) {
+    if (R < 1 || TC < 1 || N < 1 || N % R || N % TC || packing < 0 || packing > 2 || in_rows < 0)
+        return fail(QWB_ERR_INVALID_ARG, "qwb_ctransform_shape: R and TC must divide N; packing in 0..2");
+    if (packing && prec == QWB_PREC_F64)
+        return fail(QWB_ERR_INVALID_ARG, "qwb_ctransform_shape: packing needs MIXED precision");
+    CtConfig c;
+    c.R = R; c.TC = TC; c.packed = packing;
+    const int st = ctransform_impl(ctx, N, p, h_d, out_d, prec, stream, &c, in_rows, d);
+    if (st == QWB_ERR_UNSUPPORTED) return fail(st, "qwb_ctransform_shape: shape not compiled");
+    return st;
 }
 
 int qwb_ctransform_separable(qwb_ctx* ctx, int32_t N, const double* h_d, double* out_d,

@@ -1207,6 +1207,146 @@ ctransform_kernel(const PairDev* __restrict__ pairs, const CtItem* __restrict__ 
     }
 }
 
+// --------------------------------------------------------------------------
+// Line-paired variant (FP32): the same candidates, packed two input lines at
+// a time.  For input lines i1, i1' and output j, the candidates
+// c(i1, s; j) - h(i1, s) and c(i1', s; j) - h(i1', s) share the column offset
+// s - j2, so one packed subtraction rounded toward -inf (sub.rm.f32x2) forms
+// both and one 3-input min folds both into out_j.  The staged inputs are
+// interleaved by line pairs, (h(i1, c), h(i1', c)), so one 16-byte shared
+// load brings two packed operands.  The packed costs (A + D_e, A' + D_e) are
+// one packed addition of the line parts (A, A') and the duplicated column
+// part (D_e, D_e) (exact integers for p = 2), computed when first needed: for
+// the column s the R outputs use the costs e = s .. s + R - 1, a window that
+// slides by one per column.  Per two candidates this issues one packed
+// subtraction and one 3-input min.  An odd last line is paired with
+// h = -inf, whose candidates are +inf.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long add_rn_x2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+template <int R, int TC, bool P2, bool D3>
+__global__ void __launch_bounds__(256)
+ctransform_rp_kernel(const PairDev* __restrict__ pairs, const CtItem* __restrict__ items,
+                     int n_items, int phase) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* hs2 = reinterpret_cast<float2*>(smem_raw);      // [line pair][column]
+    constexpr int NQ = R + TC - 1;
+    static_assert(TC % 2 == 0, "two columns per 16-byte shared load");
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const CtItem I = items[it];
+        const PairDev& P = pairs[I.pair];
+        const int N = P.N, m = P.m;
+        const float* h = reinterpret_cast<const float*>(phase == 0 ? P.fhat : P.g);
+        float* out = reinterpret_cast<float*>(phase == 0 ? P.g : P.f);
+        const int npairs = (I.in_rows + 1) >> 1;
+        const float* hsrc = h + (size_t)I.in_row0 * N;
+        for (int k = threadIdx.x; k < npairs * N; k += blockDim.x) {
+            const int lp = k / N, c = k - lp * N;
+            const float lo = hsrc[(size_t)(2 * lp) * N + c];
+            const float hi = 2 * lp + 1 < I.in_rows ? hsrc[(size_t)(2 * lp + 1) * N + c]
+                                                    : __int_as_float(0xff800000);   // -inf
+            hs2[k] = make_float2(lo, hi);
+        }
+        __syncthreads();
+        const float* tab = reinterpret_cast<const float*>(P.ctab_lo);
+        const int o_end = min(I.out0 + CT_TILE, m);
+        const int last = I.in_row0 + I.in_rows - 1;
+        for (int o = I.out0 + threadIdx.x * R; o < o_end; o += blockDim.x * R) {
+            float mins[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) mins[r] = pos_inf<float>();
+            const int j1 = o / N, j2 = o % N;
+            const int ja = D3 ? j1 / N : j1, jb = D3 ? j1 % N : 0;
+            for (int c0 = 0; c0 < N; c0 += TC) {
+                unsigned long long DD[NQ];              // (D_e, D_e), p = 2
+                if constexpr (P2) {
+#pragma unroll
+                    for (int e = 0; e < NQ; ++e) {
+                        const float d = (float)(c0 - j2 + e - (R - 1));
+                        DD[e] = pack2(d * d, d * d);
+                    }
+                }
+                const float4* hrow = reinterpret_cast<const float4*>(hs2 + c0);
+                int i1 = I.in_row0;
+                for (int lp = 0; lp < npairs; ++lp, hrow += N / 2, i1 += 2) {
+                    const int i1b = min(i1 + 1, last);          // odd tail: h = -inf there
+                    unsigned long long AA = 0ull;
+                    const float* t0 = nullptr;
+                    const float* t1 = nullptr;
+                    if constexpr (P2) {
+                        float A1, A2;
+                        if constexpr (D3) {
+                            const int ia = i1 / N, ib = i1 - (i1 / N) * N;
+                            const int ia2 = i1b / N, ib2 = i1b - (i1b / N) * N;
+                            A1 = (float)((ia - ja) * (ia - ja) + (ib - jb) * (ib - jb));
+                            A2 = (float)((ia2 - ja) * (ia2 - ja) + (ib2 - jb) * (ib2 - jb));
+                        } else {
+                            A1 = (float)((i1 - ja) * (i1 - ja));
+                            A2 = (float)((i1b - ja) * (i1b - ja));
+                        }
+                        AA = pack2(A1, A2);
+                    } else {
+                        if constexpr (D3) {
+                            const int ia = i1 / N, ib = i1 - (i1 / N) * N;
+                            const int ia2 = i1b / N, ib2 = i1b - (i1b / N) * N;
+                            t0 = tab + ((size_t)abs(ia - ja) * N + abs(ib - jb)) * N;
+                            t1 = tab + ((size_t)abs(ia2 - ja) * N + abs(ib2 - jb)) * N;
+                        } else {
+                            t0 = tab + (size_t)abs(i1 - ja) * N;
+                            t1 = tab + (size_t)abs(i1b - ja) * N;
+                        }
+                    }
+                    auto cost = [&](int e) -> unsigned long long {
+                        if constexpr (P2) {
+                            return add_rn_x2(AA, DD[e]);            // exact integers
+                        } else {
+                            const int a = abs(c0 - j2 + e - (R - 1));
+                            return pack2(t0[a], t1[a]);
+                        }
+                    };
+                    // window of costs for column s: e = s - r + R - 1, r = R-1 .. 0
+                    // before column 0 the window is that of column -1: win[r] = cost(R - 2 - r)
+                    unsigned long long win[R];
+#pragma unroll
+                    for (int r = 0; r < R - 1; ++r) win[r] = cost(R - 2 - r);
+#pragma unroll
+                    for (int s = 0; s < TC; s += 2) {
+                        const float4 v = hrow[s / 2];
+                        const unsigned long long hp0 = pack2(v.x, v.y), hp1 = pack2(v.z, v.w);
+#pragma unroll
+                        for (int ss = 0; ss < 2; ++ss) {
+                            const int sc = s + ss;
+                            // slide: win[r] holds cost e = sc - r + R - 1
+#pragma unroll
+                            for (int r = R - 1; r > 0; --r) win[r] = win[r - 1];
+                            win[0] = cost(sc + R - 1);
+                            const unsigned long long hp = ss ? hp1 : hp0;
+#pragma unroll
+                            for (int r = 0; r < R; ++r) {
+                                float a, b;
+                                sub_rd_x2(win[r], hp, a, b);
+                                mins[r] = min3(mins[r], a, b);
+                            }
+                        }
+                    }
+                }
+            }
+            if (I.in_rows < P.rows) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) atomic_min_fp(&out[o + r], mins[r]);
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) out[o + r] = mins[r];
+            }
+        }
+        __syncthreads();
+    }
+}
+
 int ct_pick_r(int N, int want) {
     for (int r = want; r > 1; r >>= 1)
         if (N % r == 0) return r;
@@ -1232,17 +1372,45 @@ static int ct_launch_rt(const PairDev* pairs_d, const CtItem* items, int n_items
     return QWB_OK;
 }
 
+template <int R, int TC, bool P2>
+static int ct_launch_rp(const PairDev* pairs_d, const CtItem* items, int n_items, int phase,
+                        int threads, int in_rows, int N_max, int grid_cap, bool d3,
+                        cudaStream_t stream) {
+    auto kern = d3 ? ctransform_rp_kernel<R, TC, P2, true> : ctransform_rp_kernel<R, TC, P2, false>;
+    threads = std::min(threads, CT_TILE / R);     // every thread owns R outputs of the tile
+    const size_t smem = sizeof(float2) * (size_t)((in_rows + 1) / 2) * N_max;
+    if (smem > 227 * 1024) return QWB_ERR_UNSUPPORTED;
+    QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int grid = n_items;
+    if (grid_cap > 0) {
+        int occ = 1;
+        QWB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem));
+        grid = std::min(n_items, grid_cap * std::max(1, occ));
+    }
+    kern<<<grid, threads, smem, stream>>>(pairs_d, items, n_items, phase);
+    QWB_LAUNCHED();
+    return QWB_OK;
+}
+
 template <typename T, bool P2>
 static int ct_launch_t(const PairDev* pairs_d, const CtItem* items, int n_items, int phase,
                        const CtConfig& c, int N_max, int grid_cap, cudaStream_t stream) {
 #define QWB_CT(RR, TT, PK)                                                                 \
     if (c.R == RR && c.TC == TT && c.packed == PK)                                         \
-        return ct_launch_rt<T, RR, TT, P2, PK>(pairs_d, items, n_items, phase, c.threads,  \
+        return ct_launch_rt<T, RR, TT, P2, (PK != 0)>(pairs_d, items, n_items, phase, c.threads,  \
                                                c.in_rows, N_max, grid_cap, stream);
-    QWB_CT(1, 1, false) QWB_CT(2, 2, false) QWB_CT(4, 4, false) QWB_CT(8, 8, false)
-    QWB_CT(16, 8, false) QWB_CT(16, 16, false) QWB_CT(8, 16, false)
-    QWB_CT(8, 8, true) QWB_CT(16, 8, true) QWB_CT(16, 16, true)
+    QWB_CT(1, 1, 0) QWB_CT(2, 2, 0) QWB_CT(4, 4, 0) QWB_CT(8, 8, 0)
+    QWB_CT(16, 8, 0) QWB_CT(16, 16, 0) QWB_CT(8, 16, 0)
+    QWB_CT(8, 8, 1) QWB_CT(16, 8, 1) QWB_CT(16, 16, 1)
 #undef QWB_CT
+    if constexpr (sizeof(T) == 4) {
+#define QWB_CTRP(RR, TT)                                                                   \
+        if (c.R == RR && c.TC == TT && c.packed == 2)                                      \
+            return ct_launch_rp<RR, TT, P2>(pairs_d, items, n_items, phase, c.threads,     \
+                                            c.in_rows, N_max, grid_cap, c.has_3d, stream);
+        QWB_CTRP(8, 8) QWB_CTRP(16, 8) QWB_CTRP(8, 16) QWB_CTRP(16, 16)
+#undef QWB_CTRP
+    }
     return QWB_ERR_UNSUPPORTED;
 }
 

@@ -72,7 +72,10 @@ struct CtConfig {
     int threads = 256;  // threads per CTA
     int in_rows = 4;    // input rows per work item (split of the min)
     bool p2 = false;    // every pair of the launch has p = 2 (exact integer costs)
-    bool packed = false;  // FP32: packed f32x2 subtraction of two candidates
+    // FP32 packing: 0 none; 1 two columns per packed f32x2 subtraction;
+    // 2 two input lines per packed subtraction (row-paired kernel)
+    int packed = 0;
+    bool has_3d = false;  // some pair of the launch is a volume (selects the 3-D line indexing)
 };
 
 // Launchers.  All enqueue on `stream` and return a qwb status.

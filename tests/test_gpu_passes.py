@@ -166,3 +166,61 @@ def test_invalid_inputs():
         api.coarse_cost(T(mu), T(nu), N, 3, 2.0)
     with pytest.raises(QwbError, match="INVALID_ARG"):
         api.ctransform(T(mu), N, 0.5)
+
+
+SHAPES = [(R, TC, 0) for R, TC in [(1, 1), (2, 2), (4, 4), (8, 8), (16, 8), (16, 16), (8, 16)]] + \
+         [(8, 8, 1), (16, 8, 1), (16, 16, 1)] + \
+         [(8, 8, 2), (16, 8, 2), (8, 16, 2), (16, 16, 2)]
+
+
+@pytest.mark.parametrize("R,TC,packing", SHAPES)
+@pytest.mark.parametrize("N,in_rows", [(32, 0), (32, 5), (64, 7), (64, 1)])
+def test_ctransform_every_shape_p2(R, TC, packing, N, in_rows):
+    """Every compiled launch shape gives the p = 2 transform bit for bit
+    (round-down of the exact minimum), including odd line splits whose items
+    combine by atomic min and the line-paired kernel's odd tail."""
+    h = fp32_values(np.random.default_rng(100 + N + in_rows), N * N, 3.0 * N)
+    g = api.ctransform_shape(T(h), N, 2.0, R, TC, packing, in_rows).cpu().numpy()
+    np.testing.assert_array_equal(g, rd32(O.c_transform(h, N, 2.0)))
+
+
+@pytest.mark.parametrize("R,TC,packing", [(8, 8, 0), (16, 8, 1), (16, 8, 2), (8, 16, 2), (16, 16, 2)])
+@pytest.mark.parametrize("p", [1.0, 1.5])
+def test_ctransform_every_shape_general_p(R, TC, packing, p):
+    N = 32
+    h = fp32_values(np.random.default_rng(200), N * N, 2.0 * N)
+    g = api.ctransform_shape(T(h), N, p, R, TC, packing, 3).cpu().numpy()
+    ref = api.ctransform_shape(T(h), N, p, 1, 1, 0, 0).cpu().numpy()
+    np.testing.assert_array_equal(g, ref)        # same round-down table, same minimum
+    exact = O.c_transform(h, N, p)
+    X = O.grid_points(N)
+    C = O.ground_cost(X, X, p)
+    assert np.all(g <= exact + 1e-12 * np.maximum(np.abs(exact), C.max()))
+    assert (h[:, None] + g[None, :] - C).max() <= 1e-9
+
+
+@pytest.mark.parametrize("R,TC,packing", [(8, 8, 0), (16, 8, 2), (8, 16, 2)])
+@pytest.mark.parametrize("p", [2.0, 1.0])
+def test_ctransform_every_shape_3d(R, TC, packing, p):
+    """Line-paired packing across the lines of a volume ([N]^3, lines of N)."""
+    N = 16
+    h = fp32_values(np.random.default_rng(300), N ** 3, 2.0 * N)
+    g = api.ctransform_shape(T(h), N, p, R, TC, packing, 5, d=3).cpu().numpy()
+    exact = O.c_transform(h, N, p, d=3)
+    if p == 2.0:
+        np.testing.assert_array_equal(g, rd32(exact))
+    else:
+        ref = api.ctransform_shape(T(h), N, p, 1, 1, 0, 0, d=3).cpu().numpy()
+        np.testing.assert_array_equal(g, ref)
+        assert np.all(g <= exact + 1e-9)
+
+
+def test_ctransform_shape_rejects():
+    from paper_2506_00976_gb300._lib import QwbError
+    h = T(np.zeros(64))
+    with pytest.raises(QwbError, match="INVALID_ARG"):
+        api.ctransform_shape(h, 8, 2.0, 3, 8, 0)            # R does not divide N
+    with pytest.raises(QwbError, match="INVALID_ARG"):
+        api.ctransform_shape(h, 8, 2.0, 8, 8, 2, prec="f64")  # packing is FP32 only
+    with pytest.raises(QwbError, match="UNSUPPORTED"):
+        api.ctransform_shape(h, 8, 2.0, 2, 8, 0)             # not compiled

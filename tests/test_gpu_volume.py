@@ -152,3 +152,17 @@ def test_volume_32_sampled():
     np.testing.assert_allclose(g[J], g_ref, rtol=0, atol=8 * np.spacing(np.float32(scale)))
     b = api.bounds([T(mu)], [T(nu)], [(N, kappa, p, D)], ipf_sweeps=10)[0]
     assert b["status"] == 0 and 0 <= b["lb"] <= min(b["ub_weighted"], b["ub_primal"])
+
+
+def test_plane_and_volume_of_same_side_do_not_share_state():
+    """A 2-D call and a 3-D call with equal N, kappa and p use separate
+    per-problem workspaces (the 3-D measures hold N^3 values)."""
+    N, kappa = 8, 8
+    h = np.random.default_rng(5).standard_normal(N * N).astype(np.float32).astype(np.float64)
+    api.ctransform(T(h), N, 2.0)                   # 2-D workspace for (8, 8, 2)
+    mu, nu = _pair(N, "field3", 103)
+    _, f_c, _ = _oracle_plan(mu, nu, N, kappa, 2.0)
+    r = api.dual_upscale_ctransform(T(mu), T(nu), N, kappa, 2.0, f_c, prec="mixed", d=D)
+    ref = O.lb_dual(mu, nu, N, kappa, 2.0, f_c=f_c, d=D)
+    fmax = np.abs(ref["f"]).max() + np.abs(ref["g"]).max()
+    assert abs(r["lb_p"] - ref["lb_p"]) <= 1e-4 * max(abs(ref["lb_p"]), 1e-3) + 64 * 6e-8 * fmax
