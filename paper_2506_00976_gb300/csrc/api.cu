@@ -195,6 +195,7 @@ struct qwb_batch {
     std::vector<GraphEntry> graphs;
     TuneEntry* tune = nullptr;
     int cbar_variant = 0;
+    bool cbar_pow2 = true;      // every 2-D coarse side n is a power of two (cbar4 kernel)
     int N_gcd = 1;
     bool all_p2 = false;
 };
@@ -294,6 +295,7 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
             if (kap0 < 0) kap0 = kap;
             same_kap &= (kap == kap0);
             b->kappa_code = std::max(b->kappa_code, kap);
+            if (nn & (nn - 1)) b->cbar_pow2 = false;
             b->n_max2 = std::max(b->n_max2, nn);
             b->N_max2 = std::max(b->N_max2, N);
         }
@@ -347,7 +349,10 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         if (found->ct_done && found->R > 0 && N_gcd % found->R == 0 && N_gcd % found->TC == 0) {
             b->ct_cfg_b.R = found->R; b->ct_cfg_b.TC = found->TC; b->ct_cfg_b.packed = found->packed;
         }
-        if (found->cbar_done) b->cbar_variant = found->cbar_variant;
+        // untuned default: the row-direct kappa = 4 kernel where it applies
+        b->cbar_variant = (b->cbar_pow2 && !b->f64 && b->kappa_code == 4) ? 2 : 0;
+        if (found->cbar_done && (found->cbar_variant < 2 || (b->cbar_pow2 && !b->f64)))
+            b->cbar_variant = found->cbar_variant;
     }
     const int tile_out = CT_TILE;
     long total_tiles = 0;
@@ -666,6 +671,15 @@ static int time_variant(cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1,
     return QWB_OK;
 }
 
+static const char* cbar_variant_name(int v) {
+    switch (v) {
+        case 0: return "staged_rows/2_ctas_per_sm";
+        case 1: return "staged_rows/3_ctas_per_sm";
+        case 2: return "direct_rows/3_ctas_per_sm";
+        default: return "direct_rows/2_ctas_per_sm";
+    }
+}
+
 static int tune_cbar(qwb_batch* b, cudaStream_t s) {
     TuneEntry* e = b->tune;
     if (!b->ctx->autotune || !e || e->cbar_done || !b->ev_ok) return QWB_OK;
@@ -675,14 +689,15 @@ static int tune_cbar(qwb_batch* b, cudaStream_t s) {
     std::ostringstream rep;
     double best = 1e30;
     rep << "{";
-    for (int v = 0; v < 2; ++v) {
+    const int nv = (b->cbar_pow2 && !b->f64) ? 4 : 2;
+    for (int v = 0; v < nv; ++v) {
         double ms;
         st = time_variant(s, b->ev[0], b->ev[1], [&] {
             return launch_cbar(b->pairs_d, b->cbar_items_d, b->n_cbar, b->kappa_code, b->n_max2, b->N_max2,
                                b->f64, s, v);
         }, &ms);
         if (st) return st;
-        rep << (v ? ", " : "") << "\"min_ctas_per_sm=" << (v ? 3 : 2) << "\": " << ms;
+        rep << (v ? ", " : "") << "\"" << cbar_variant_name(v) << "\": " << ms;
         if (ms < best) { best = ms; e->cbar_variant = v; }
     }
     rep << "}";
@@ -1140,7 +1155,7 @@ int qwb_batch_tuning(qwb_batch* b, char* json_out, int32_t capacity) {
     o << "{\"key\": \"" << (b->tune ? b->tune->key : "") << "\", \"ctransform\": {\"R\": " << b->ct_cfg_b.R
       << ", \"TC\": " << b->ct_cfg_b.TC << ", \"packed\": " << b->ct_cfg_b.packed
       << ", \"candidates_ms\": " << (b->tune && !b->tune->ct_report.empty() ? b->tune->ct_report : "{}")
-      << "}, \"cbar\": {\"min_ctas_per_sm\": " << (b->cbar_variant ? 3 : 2)
+      << "}, \"cbar\": {\"variant\": \"" << cbar_variant_name(b->cbar_variant) << "\""
       << ", \"candidates_ms\": " << (b->tune && !b->tune->cbar_report.empty() ? b->tune->cbar_report : "{}")
       << "}, \"enabled\": " << (b->ctx->autotune ? "true" : "false") << "}";
     const std::string str = o.str();

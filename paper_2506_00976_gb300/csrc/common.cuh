@@ -46,16 +46,27 @@ template <typename T> __device__ __forceinline__ T from_double_rn(double x);
 template <> __device__ __forceinline__ float from_double_rn<float>(double x) { return __double2float_rn(x); }
 template <> __device__ __forceinline__ double from_double_rn<double>(double x) { return x; }
 
-// FP32 -> FP64 widening by exponent re-biasing on the integer pipes (exact
-// for every normal float; zero, subnormals, infinities and NaN take the
-// conversion instruction), which keeps bulk widening off the FP64 pipe.
+// FP32 -> FP64 widening by exponent re-biasing on the integer pipes, exact
+// for every float (normal, subnormal, zero, infinity, NaN), which keeps bulk
+// widening off the FP64 pipe.
 __device__ __forceinline__ double widen_f32(float v) {
     const unsigned u = __float_as_uint(v);
     const unsigned e = (u >> 23) & 0xffu;
-    if (e == 0u || e == 0xffu) return (double)v;
-    const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) |
-                                    ((unsigned long long)(e + 896u) << 52) |
-                                    ((unsigned long long)(u & 0x7fffffu) << 29);
+    unsigned m = u & 0x7fffffu;
+    unsigned long long ebits;
+    if (e == 0xffu) {
+        ebits = 0x7ffull;                       // infinity or NaN (payload kept)
+    } else if (e != 0u) {
+        ebits = e + 896u;                       // 1023 - 127
+    } else if (m == 0u) {
+        ebits = 0ull;                           // signed zero
+    } else {                                    // subnormal m * 2^-149: normalise
+        const int sh = __clz(m) - 8;            // brings the leading one to bit 23
+        m = (m << sh) & 0x7fffffu;
+        ebits = (unsigned long long)(897 - sh);
+    }
+    const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) | (ebits << 52) |
+                                    ((unsigned long long)m << 29);
     return __longlong_as_double((long long)bits);
 }
 __device__ __forceinline__ double widen_f32(double v) { return v; }

@@ -439,6 +439,145 @@ cbar_kernel(const PairDev* __restrict__ pairs, const CbarItem* __restrict__ item
 }
 
 // --------------------------------------------------------------------------
+// cbar4: the kappa = 4 FP32 C-bar for coarse sides n that are powers of two.
+// Same item (one wrapped block-row diagonal w1 of a pair), same sums and
+// rounding as cbar_kernel, a different thread mapping: thread slot b covers
+// the block pair (k2, l2) = (b / n, b % n) of every staged block row, so the
+// threads of a warp hold consecutive target blocks l2 of one source block
+// row and write their FP64 results straight to consecutive C-bar entries
+// (no staging of outputs, shifts instead of divisions).  Each thread keeps
+// the 49 costs of its block offset in registers across the staged rows.
+// --------------------------------------------------------------------------
+static size_t cbar4_smem(int n, int N) {
+    return sizeof(float) * ((size_t)2 * CBAR_S * 4 * N + (size_t)2 * (2 * n - 1) * CBAR_WPAD +
+                            (size_t)2 * CBAR_S * n);
+}
+
+template <int MINB>
+__global__ void __launch_bounds__(CBAR_THREADS, MINB)
+cbar4_kernel(const PairDev* __restrict__ pairs, const CbarItem* __restrict__ items, int n_items) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int KAP = 4, WK = 2 * KAP - 1;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const CbarItem I = items[it];
+        const PairDev& P = pairs[I.pair];
+        const int N = P.N, n = P.n, M = P.M;
+        const int lg = 31 - __clz(n);               // n is a power of two
+        const int w1 = I.w1;
+        double* __restrict__ cbar = P.cbar;
+        float* mu_s = reinterpret_cast<float*>(smem_raw);     // [S][KAP][N]
+        float* nu_s = mu_s + CBAR_S * KAP * N;                 // [S][KAP][N]
+        float* win_s = nu_s + CBAR_S * KAP * N;                // [2][2n-1][CBAR_WPAD]
+        float* rk_s = win_s + 2 * (2 * n - 1) * CBAR_WPAD;     // [S][n]
+        float* rl_s = rk_s + CBAR_S * n;                       // [S][n]
+        const float* tab = reinterpret_cast<const float*>(P.ctab_hi);
+        const float* mu_up = reinterpret_cast<const float*>(P.mu_up);
+        const float* nu_up = reinterpret_cast<const float*>(P.nu_up);
+        __syncthreads();            // the previous item's readers are done
+        for (int vd = threadIdx.x; vd < 2 * (2 * n - 1); vd += blockDim.x) {
+            const int v = vd / (2 * n - 1), dd = vd - v * (2 * n - 1);
+            const int D1 = KAP * (v == 0 ? w1 : w1 - n), D2 = KAP * (dd - (n - 1));
+            float* dst = win_s + vd * CBAR_WPAD;
+#pragma unroll
+            for (int d1 = 0; d1 < WK; ++d1) {
+                const int row = abs(D1 + d1 - (KAP - 1));
+                const float* trow = tab + row * N;
+#pragma unroll
+                for (int d2 = 0; d2 < WK; ++d2)
+                    dst[d1 * WK + d2] = row < N ? trow[abs(D2 + d2 - (KAP - 1))] : 0.0f;
+            }
+        }
+        for (int k1_0 = 0; k1_0 < n; k1_0 += CBAR_S) {
+            const int S = min(CBAR_S, n - k1_0);
+            __syncthreads();        // windows built / the previous chunk is consumed
+            const int rowlen4 = N;  // KAP * N floats = N float4 per block row
+            for (int s = 0; s < S; ++s) {
+                const int k1 = k1_0 + s;
+                int l1 = k1 - w1;
+                if (l1 < 0) l1 += n;
+                const float4* msrc = reinterpret_cast<const float4*>(mu_up + (size_t)k1 * KAP * N);
+                const float4* nsrc = reinterpret_cast<const float4*>(nu_up + (size_t)l1 * KAP * N);
+                float4* mdst = reinterpret_cast<float4*>(mu_s + s * KAP * N);
+                float4* ndst = reinterpret_cast<float4*>(nu_s + s * KAP * N);
+                for (int c = threadIdx.x; c < rowlen4; c += blockDim.x) { mdst[c] = msrc[c]; ndst[c] = nsrc[c]; }
+                if (threadIdx.x < n) {
+                    rk_s[s * n + threadIdx.x] = P.mu_rinv32[k1 * n + threadIdx.x];
+                    rl_s[s * n + threadIdx.x] = P.nu_rinv32[l1 * n + threadIdx.x];
+                }
+            }
+            __syncthreads();
+            for (int b = threadIdx.x; b < (n << lg); b += blockDim.x) {
+                const int k2 = b >> lg, l2 = b & (n - 1);
+                const int D2 = k2 - l2;
+                float cw[WK * WK];
+                int cur_v = -1;
+                for (int s = 0; s < S; ++s) {
+                    const int k1 = k1_0 + s;
+                    const int v = k1 >= w1 ? 0 : 1;          // block-row offset w1 or w1 - n
+                    if (v != cur_v) {
+                        const float4* src = reinterpret_cast<const float4*>(
+                            win_s + (v * (2 * n - 1) + D2 + n - 1) * CBAR_WPAD);
+                        float buf[CBAR_WPAD];
+#pragma unroll
+                        for (int q = 0; q < CBAR_WPAD / 4; ++q) *reinterpret_cast<float4*>(buf + 4 * q) = src[q];
+#pragma unroll
+                        for (int q = 0; q < WK * WK; ++q) cw[q] = buf[q];
+                        cur_v = v;
+                    }
+                    // inner[a] = sum_b nu[b] c(a - b) (order b1, b2 per accumulator),
+                    // then acc = sum_a mu[a] inner[a] (order a1, a2), all rounded up
+                    float inner[KAP][KAP];
+#pragma unroll
+                    for (int a1 = 0; a1 < KAP; ++a1)
+#pragma unroll
+                        for (int a2 = 0; a2 < KAP; ++a2) inner[a1][a2] = 0.0f;
+#pragma unroll
+                    for (int b1 = 0; b1 < KAP; ++b1) {
+                        const float4 v4 = *reinterpret_cast<const float4*>(nu_s + (s * KAP + b1) * N + l2 * KAP);
+                        const float nrow[KAP] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+                        for (int b2 = 0; b2 < KAP; ++b2)
+#pragma unroll
+                            for (int a1 = 0; a1 < KAP; ++a1)
+#pragma unroll
+                                for (int a2 = 0; a2 < KAP; ++a2)
+                                    inner[a1][a2] = fma_ru(nrow[b2], cw[(a1 - b1 + KAP - 1) * WK + a2 - b2 + KAP - 1],
+                                                           inner[a1][a2]);
+                    }
+                    float acc = 0.0f;
+#pragma unroll
+                    for (int a1 = 0; a1 < KAP; ++a1) {
+                        const float4 v4 = *reinterpret_cast<const float4*>(mu_s + (s * KAP + a1) * N + k2 * KAP);
+                        const float mrow[KAP] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+                        for (int a2 = 0; a2 < KAP; ++a2) acc = fma_ru(mrow[a2], inner[a1][a2], acc);
+                    }
+                    int l1 = k1 - w1;
+                    if (l1 < 0) l1 += n;
+                    const int k = (k1 << lg) + k2, l = (l1 << lg) + l2;
+                    const float rk = rk_s[s * n + k2], rl = rl_s[s * n + l2];
+                    double outv;
+                    if (rk > 0.0f && rl > 0.0f) {
+                        outv = widen_f32(mul_ru(mul_ru(acc, rk), rl));
+                    } else {
+                        double mean = 0.0;
+#pragma unroll
+                        for (int d1 = 0; d1 < WK; ++d1)
+#pragma unroll
+                            for (int d2 = 0; d2 < WK; ++d2)
+                                mean = __fma_ru((double)((KAP - abs(d1 - (KAP - 1))) * (KAP - abs(d2 - (KAP - 1)))),
+                                                (double)cw[d1 * WK + d2], mean);
+                        mean = __ddiv_ru(mean, (double)(KAP * KAP * KAP * KAP));
+                        outv = cbar_special<float>(P, k, l, (double)acc, mean);
+                    }
+                    cbar[(size_t)k * M + l] = outv;
+                }
+            }
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
 // cbar3: C-bar on 3-D grids (volumes), the same definition and rounding as
 // cbar_kernel: num_kl = sum_{a in X_k} mu_a sum_{b in Y_l} nu_b rho(a, b)^p
 // with upward-rounded FMAs (inner sums over b first), then multiplied by
@@ -529,8 +668,21 @@ static int cbar_dispatch(const PairDev* pairs_d, const CbarItem* items, int n_it
         QWB_LAUNCHED();
         return QWB_OK;
     };
-    // variant 0: register budget for two CTAs per SM; 1: for three CTAs per SM
+    // variant 0: register budget for two CTAs per SM; 1: for three CTAs per SM;
+    // 2, 3: the kappa = 4 FP32 kernel with row-direct writes (every coarse side
+    // of the launch a power of two), three or two CTAs per SM
     constexpr int MB = sizeof(T) == 4 ? 3 : 1;
+    if constexpr (sizeof(T) == 4) {
+        if (kappa_code == 4 && (variant == 2 || variant == 3)) {
+            const size_t smem4 = cbar4_smem(n_max, N_max);
+            if (smem4 > 227 * 1024) return QWB_ERR_UNSUPPORTED;
+            auto kern = variant == 2 ? cbar4_kernel<3> : cbar4_kernel<2>;
+            QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4));
+            kern<<<n_items, CBAR_THREADS, smem4, stream>>>(pairs_d, items, n_items);
+            QWB_LAUNCHED();
+            return QWB_OK;
+        }
+    }
     switch (kappa_code) {   // positive: every pair of the launch has this kappa
         case 1: return run(cbar_kernel<T, 1, 2>);
         case 2: return run(cbar_kernel<T, 2, 2>);

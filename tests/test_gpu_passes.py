@@ -68,7 +68,8 @@ def test_ctransform_f64(N, p):
 
 
 @pytest.mark.parametrize("N,kappa,p", [(8, 2, 2.0), (12, 3, 2.0), (16, 4, 1.0), (32, 4, 2.0),
-                                        (32, 8, 2.0), (16, 1, 2.0), (24, 4, 1.5), (64, 4, 2.0)])
+                                        (32, 8, 2.0), (16, 1, 2.0), (24, 4, 1.5), (64, 4, 2.0),
+                                        (24, 4, 2.0), (64, 4, 1.0), (4, 4, 2.0)])
 @pytest.mark.parametrize("prec", ["mixed", "f64"])
 def test_coarse_cost(N, kappa, p, prec):
     mu, nu = synth.make_measure(N, "gauss", 20, 0), synth.make_measure(N, "field", 20, 1)
