@@ -309,6 +309,13 @@ int qwb_batch_fine(qwb_batch* batch, const double* const* mu_d, const double* co
                    int32_t batched, void* stream);
 int qwb_batch_results(qwb_batch* batch, qwb_result* out_h, void* stream);
 int qwb_batch_potentials(qwb_batch* batch, int32_t pair, double* f_d, double* g_d, void* stream);
+/* Pair t's scalings after the fine IPF sweeps of the last qwb_batch_fine
+ * (Sec. 3.4, IPF paragraph; Alg. 4): the pass-type a, b with
+ * a = mu / (pi-hat b), b = nu / (pi-hat^T a) after ipf_sweeps sweeps from
+ * b = 1, widened to FP64 (N^d each, device, either may be NULL).  The
+ * certified bound uses the FP64 block-scalar fit instead (qwb_result fields).
+ * Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA. */
+int qwb_batch_fine_scalings(qwb_batch* batch, int32_t pair, double* a_d, double* b_d, void* stream);
 /* Device time (ms) of each kernel of the last batched passes, in the order
  * SumPool, C-bar, primal (IPF + upper bound), centre, upsample,
  * c-transform f-hat -> g, c-transform g -> f, lower-bound sum; -1 where not

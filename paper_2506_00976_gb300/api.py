@@ -243,6 +243,15 @@ class Batch:
               "qwb_batch_potentials")
         return f, g
 
+    def fine_scalings(self, t):
+        """Pair t's fine IPF scalings a, b (pass type widened to FP64)."""
+        N, d = self.problems[t].N, self.problems[t].d or 2
+        a = torch.empty(N ** d, dtype=torch.float64, device=self._dev)
+        b = torch.empty(N ** d, dtype=torch.float64, device=self._dev)
+        check(_lib.load().qwb_batch_fine_scalings(self._h, int(t), _ptr(a), _ptr(b), self._stream()),
+              "qwb_batch_fine_scalings")
+        return a, b
+
     def close(self):
         if self._h:
             _lib.load().qwb_batch_destroy(self._h)

@@ -916,10 +916,31 @@ static int solve_pair(qwb_batch* b, int t) {
         b->ubw_p[t] = HUGE_VAL; b->ubw[t] = HUGE_VAL;
         return QWB_OK;
     }
-    // same supplies: the C~ optimum is a feasible starting basis
+    // same supplies: the C~ optimum is a feasible starting basis, and the
+    // arcs from each source to the 3 x 3 (3 x 3 x 3) neighbourhoods of its C~
+    // plan targets are priced first (the solve still ends optimal over all arcs)
     NSSolution sb;
     const double* Cb = b->cbar_h + b->cbar_h_off[t];
-    st = network_simplex(M, M, Cb, mc, nc, sb, -1, &basis);
+    std::vector<int64_t> cand;
+    {
+        const int nn = pr.N / pr.kappa, dd = dim_of(pr);
+        cand.reserve((size_t)sol.col.size() * (dd == 3 ? 27 : 9));
+        for (int k = 0; k < M; ++k)
+            for (int e = sol.rowptr[k]; e < sol.rowptr[k + 1]; ++e) {
+                const int l = sol.col[e];
+                const int l1 = dd == 3 ? l / (nn * nn) : l / nn, l2 = dd == 3 ? (l / nn) % nn : l % nn;
+                const int l3 = dd == 3 ? l % nn : 0;
+                for (int d1 = -1; d1 <= 1; ++d1)
+                    for (int d2 = -1; d2 <= 1; ++d2)
+                        for (int d3 = (dd == 3 ? -1 : 0); d3 <= (dd == 3 ? 1 : 0); ++d3) {
+                            const int r1 = l1 + d1, r2 = l2 + d2, r3 = l3 + d3;
+                            if (r1 < 0 || r2 < 0 || r3 < 0 || r1 >= nn || r2 >= nn || (dd == 3 && r3 >= nn)) continue;
+                            const int r = dd == 3 ? (r1 * nn + r2) * nn + r3 : r1 * nn + r2;
+                            cand.push_back((int64_t)k * M + r);
+                        }
+            }
+    }
+    st = network_simplex(M, M, Cb, mc, nc, sb, -1, &basis, nullptr, &cand);
     if (st) return st;
     double L_sum = 0.0;
     const int nnzb = (int)sb.col.size();
@@ -1179,6 +1200,19 @@ int qwb_batch_potentials(qwb_batch* b, int32_t pair, double* f_d, double* g_d, v
     }
     if (f_d && (st = launch_from_work(P.f, f_d, m, b->f64, s))) return st;
     if (g_d && (st = launch_from_work(P.g, g_d, m, b->f64, s))) return st;
+    return QWB_OK;
+}
+
+int qwb_batch_fine_scalings(qwb_batch* b, int32_t pair, double* a_d, double* b_d, void* stream) {
+    if (!b || pair < 0 || pair >= b->n) return fail(QWB_ERR_INVALID_ARG, "qwb_batch_fine_scalings: bad pair");
+    if (b->flags & QWB_FLAG_NO_PRIMAL) return fail(QWB_ERR_INVALID_ARG, "the batch skipped the primal pass");
+    QWB_CUDA(cudaSetDevice(b->ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int m = ipow(b->probs[pair].N, dim_of(b->probs[pair]));
+    const PairDev& P = b->pairs_h[pair];
+    int st;
+    if (a_d && (st = launch_from_work(P.a, a_d, m, b->f64, s))) return st;
+    if (b_d && (st = launch_from_work(P.b, b_d, m, b->f64, s))) return st;
     return QWB_OK;
 }
 

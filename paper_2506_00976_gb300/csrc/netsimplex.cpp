@@ -31,6 +31,13 @@
 //   * a solve can start from the final tree of another solve with the same
 //     supplies (a feasible, strongly feasible basis for any costs): the C-bar
 //     problem starts from the C~ optimum;
+//   * the grid problem is solved coarse to fine: the same problem on the
+//     (n/2) x (n/2) grid of 2 x 2 cell sums (costs at doubled offsets) is
+//     solved first, and the fine solve prices only the arcs between the
+//     children of the coarse plan's support (sparse pricing) until none of
+//     them has a negative reduced cost; then one scan of all arcs adds every
+//     arc that still has one, and pricing resumes, until a full scan finds
+//     none (so the result is optimal over all arcs);
 //   * at the end the tree flows are recomputed exactly from the supplies
 //     (leaf elimination) and the potentials are made exactly dual feasible by
 //     one coarse c-transform each way (g = f^c, f = g^c).
@@ -81,6 +88,21 @@ struct Solver {
     std::vector<signed char> old_up;
     std::vector<double> old_flow;
     int64_t price_pos = 0, block = 64;
+    // sparse pricing over a candidate arc list (coarse-to-fine solves)
+    bool sparse = false;
+    std::vector<int64_t> cand;
+    std::vector<int> cand_i, cand_j;  // endpoints and cost of each candidate
+    std::vector<double> cand_c;
+    std::vector<uint64_t> in_cand;    // bitset over the real arcs
+    int64_t cand_pos = 0;
+    void push_candidate(int64_t a) {
+        in_cand[(size_t)(a >> 6)] |= 1ull << (a & 63);
+        cand.push_back(a);
+        const int i = (int)(a / m), j = (int)(a % m);
+        cand_i.push_back(i);
+        cand_j.push_back(j);
+        cand_c.push_back(cst(i, j));
+    }
 
     int tail(int64_t a) const {
         if (a < NM) return (int)(a / m);
@@ -259,6 +281,66 @@ struct Solver {
         return -1;
     }
 
+    void set_candidates(const std::vector<int64_t>& arcs) {
+        sparse = true;
+        in_cand.assign((size_t)((NM + 63) / 64), 0ull);
+        cand.clear(); cand_i.clear(); cand_j.clear(); cand_c.clear();
+        for (int64_t a : arcs)
+            if (!((in_cand[(size_t)(a >> 6)] >> (a & 63)) & 1ull)) push_candidate(a);
+        cand_pos = 0;
+    }
+    // Block search over the candidate arcs (the most negative reduced cost in
+    // the first block of about sqrt(#candidates) arcs that has one).
+    int64_t find_entering_sparse(double* rc_out) {
+        const int64_t nc = (int64_t)cand.size();
+        if (nc == 0) return -1;
+        const int64_t blk = std::max<int64_t>(32, (int64_t)std::sqrt((double)nc));
+        int64_t scanned = 0, pos = cand_pos;
+        const double* pg = pot.data() + n;
+        while (scanned < nc) {
+            const int64_t end = std::min<int64_t>(pos + blk, nc);
+            double best = -eps;
+            int64_t best_a = -1;
+            const int* ci = cand_i.data();
+            const int* cj = cand_j.data();
+            const double* cc = cand_c.data();
+            int64_t best_t = -1;
+            for (int64_t t = pos; t < end; ++t) {
+                const double rc = cc[t] - pot[ci[t]] + pg[cj[t]];
+                if (rc < best) { best = rc; best_t = t; }
+            }
+            if (best_t >= 0) best_a = cand[(size_t)best_t];
+            scanned += end - pos;
+            pos = (end == nc) ? 0 : end;
+            if (best_a >= 0) { cand_pos = pos; *rc_out = best; return best_a; }
+        }
+        return -1;
+    }
+    // One scan of every real arc: add the arcs with a negative reduced cost to
+    // the candidates.  Returns how many were added.
+    int64_t add_violators() {
+        int64_t added = 0;
+        const double* pg = pot.data() + n;
+        for (int i = 0; i < n; ++i) {
+            double best = -eps;
+            int64_t dummy = -1;
+            scan_run(i, 0, m, best, dummy);          // row minimum below -eps?
+            if (dummy < 0) continue;
+            const double pi = pot[i];
+            for (int j = 0; j < m; ++j) {
+                const double rc = cst(i, j) - pi + pg[j];
+                if (rc < -eps) {
+                    const int64_t a = (int64_t)i * m + j;
+                    if (!((in_cand[(size_t)(a >> 6)] >> (a & 63)) & 1ull)) {
+                        push_candidate(a);
+                        ++added;
+                    }
+                }
+            }
+        }
+        return added;
+    }
+
     void pivot(int64_t e) {
         const int k = tail(e);
         const int l = n + (int)(e % m);   // entering arcs are real arcs
@@ -332,7 +414,8 @@ struct Solver {
 
 template <typename Cost>
 int solve(int32_t n_src, int32_t n_dst, Cost cst, double maxc, const double* a, const double* b,
-          NSSolution& out, int64_t max_pivots, const NSBasis* warm, NSBasis* basis_out) {
+          NSSolution& out, int64_t max_pivots, const NSBasis* warm, NSBasis* basis_out,
+          const std::vector<int64_t>* candidates = nullptr) {
     const int64_t NM = (int64_t)n_src * n_dst;
     if (max_pivots < 0) max_pivots = 20 * NM + 1000000;
     Solver<Cost> S;
@@ -340,12 +423,17 @@ int solve(int32_t n_src, int32_t n_dst, Cost cst, double maxc, const double* a, 
     S.init_common(n_src, n_dst, a, b, maxc);
     if (warm && warm->valid && (int)warm->parent.size() == n_src + n_dst) S.init_basis(*warm);
     else S.init_star(a, b);
+    if (candidates) S.set_candidates(*candidates);
     int64_t piv = 0;
     const int64_t recentre_every = std::max<int64_t>(256, S.V);
     for (;;) {
         double rc;
-        const int64_t e = S.find_entering(&rc);
-        if (e < 0) break;
+        const int64_t e = S.sparse ? S.find_entering_sparse(&rc) : S.find_entering(&rc);
+        if (e < 0) {
+            // sparse pricing: optimal over the candidates; a full scan decides
+            if (S.sparse && S.add_violators() > 0) continue;
+            break;
+        }
         if (++piv > max_pivots) return QWB_ERR_NOT_CONVERGED;
         S.pivot(e);
         if (piv % recentre_every == 0) S.recentre();
@@ -413,7 +501,7 @@ bool check_masses(int32_t n_src, int32_t n_dst, const double* a, const double* b
 
 int network_simplex(int32_t n_src, int32_t n_dst, const double* C, const double* a,
                     const double* b, NSSolution& out, int64_t max_pivots, const NSBasis* warm,
-                    NSBasis* basis_out) {
+                    NSBasis* basis_out, const std::vector<int64_t>* candidates) {
     if (n_src <= 0 || n_dst <= 0 || !C || !a || !b) return QWB_ERR_INVALID_ARG;
     const int64_t NM = (int64_t)n_src * n_dst;
     double maxc = 0.0;
@@ -422,8 +510,69 @@ int network_simplex(int32_t n_src, int32_t n_dst, const double* C, const double*
         maxc = std::max(maxc, C[k]);
     }
     if (!check_masses(n_src, n_dst, a, b)) return QWB_ERR_INVALID_ARG;
-    return solve(n_src, n_dst, DenseCost{C, n_dst}, maxc, a, b, out, max_pivots, warm, basis_out);
+    if (candidates)
+        for (int64_t a_ : *candidates)
+            if (a_ < 0 || a_ >= NM) return QWB_ERR_INVALID_ARG;
+    return solve(n_src, n_dst, DenseCost{C, n_dst}, maxc, a, b, out, max_pivots, warm, basis_out,
+                 candidates);
 }
+
+namespace {
+constexpr int kMultiscaleMin = 16;   // coarse-to-fine from this grid side up (even sides)
+
+int grid_solve(int32_t n_side, const double* tab, const double* a, const double* b, NSSolution& out,
+               int64_t max_pivots, NSBasis* basis_out, const NSBasis* warm);
+
+// Candidate arcs from the solution of the half-resolution problem: every
+// (fine source, fine sink) pair whose parents are joined by the coarse plan.
+int grid_candidates(int32_t n_side, const double* tab, const double* a, const double* b,
+                    std::vector<int64_t>& cand) {
+    const int h = n_side / 2, Mh = h * h, M = n_side * n_side;
+    std::vector<double> ah(Mh, 0.0), bh(Mh, 0.0), tabh((size_t)Mh);
+    for (int r = 0; r < n_side; ++r)
+        for (int c = 0; c < n_side; ++c) {
+            ah[(r / 2) * h + c / 2] += a[r * n_side + c];
+            bh[(r / 2) * h + c / 2] += b[r * n_side + c];
+        }
+    for (int d1 = 0; d1 < h; ++d1)
+        for (int d2 = 0; d2 < h; ++d2) tabh[(size_t)d1 * h + d2] = tab[(size_t)(2 * d1) * n_side + 2 * d2];
+    NSSolution sh;
+    const int st = grid_solve(h, tabh.data(), ah.data(), bh.data(), sh, -1, nullptr, nullptr);
+    if (st) return st;
+    cand.clear();
+    for (int K = 0; K < Mh; ++K)
+        for (int e = sh.rowptr[K]; e < sh.rowptr[K + 1]; ++e) {
+            const int L = sh.col[e];
+            const int K1 = K / h, K2 = K % h, L1 = L / h, L2 = L % h;
+            for (int u = 0; u < 4; ++u)
+                for (int v = 0; v < 4; ++v) {
+                    const int k = (2 * K1 + u / 2) * n_side + 2 * K2 + u % 2;
+                    const int l = (2 * L1 + v / 2) * n_side + 2 * L2 + v % 2;
+                    cand.push_back((int64_t)k * M + l);
+                }
+        }
+    return QWB_OK;
+}
+
+int grid_solve(int32_t n_side, const double* tab, const double* a, const double* b, NSSolution& out,
+               int64_t max_pivots, NSBasis* basis_out, const NSBasis* warm) {
+    double maxc = 0.0;
+    for (int k = 0; k < n_side * n_side; ++k) maxc = std::max(maxc, tab[k]);
+    const int32_t M = n_side * n_side;
+    std::vector<double> refl((size_t)n_side * (2 * n_side - 1));
+    for (int d1 = 0; d1 < n_side; ++d1)
+        for (int d2 = -(n_side - 1); d2 < n_side; ++d2)
+            refl[(size_t)d1 * (2 * n_side - 1) + n_side - 1 + d2] = tab[d1 * n_side + std::abs(d2)];
+    std::vector<int64_t> cand;
+    const bool ms = !(warm && warm->valid) && n_side >= kMultiscaleMin && n_side % 2 == 0;
+    if (ms) {
+        const int st = grid_candidates(n_side, tab, a, b, cand);
+        if (st) return st;
+    }
+    return solve(M, M, GridCost{tab, n_side, refl.data()}, maxc, a, b, out, max_pivots, warm, basis_out,
+                 ms ? &cand : nullptr);
+}
+}  // namespace
 
 int network_simplex_grid(int32_t n_side, const double* tab, const double* a, const double* b,
                          NSSolution& out, int64_t max_pivots, NSBasis* basis_out, const NSBasis* warm) {
@@ -435,11 +584,8 @@ int network_simplex_grid(int32_t n_side, const double* tab, const double* a, con
     }
     const int32_t M = n_side * n_side;
     if (!check_masses(M, M, a, b)) return QWB_ERR_INVALID_ARG;
-    std::vector<double> refl((size_t)n_side * (2 * n_side - 1));
-    for (int d1 = 0; d1 < n_side; ++d1)
-        for (int d2 = -(n_side - 1); d2 < n_side; ++d2)
-            refl[(size_t)d1 * (2 * n_side - 1) + n_side - 1 + d2] = tab[d1 * n_side + std::abs(d2)];
-    return solve(M, M, GridCost{tab, n_side, refl.data()}, maxc, a, b, out, max_pivots, warm, basis_out);
+    (void)maxc;
+    return grid_solve(n_side, tab, a, b, out, max_pivots, basis_out, warm);
 }
 
 }  // namespace qwb

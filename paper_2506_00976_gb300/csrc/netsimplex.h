@@ -30,10 +30,13 @@ struct NSBasis {
 // Returns a qwb status code (0 = OK, NOT_CONVERGED when max_pivots is hit).
 // C: n_src x n_dst row-major, non-negative and finite.  a, b: non-negative.
 // warm: optional starting basis from a solve with the same supplies;
-// basis_out: optional final basis.
+// basis_out: optional final basis; candidates: optional arcs (i * n_dst + j)
+// priced first -- when none of them can enter, a scan of all arcs adds those
+// that can, so the result is optimal over all arcs either way.
 int network_simplex(int32_t n_src, int32_t n_dst, const double* C, const double* a,
                     const double* b, NSSolution& out, int64_t max_pivots = -1,
-                    const NSBasis* warm = nullptr, NSBasis* basis_out = nullptr);
+                    const NSBasis* warm = nullptr, NSBasis* basis_out = nullptr,
+                    const std::vector<int64_t>* candidates = nullptr);
 
 // The same for the grid problem with C_kl = tab[|k1 - l1| * n_side + |k2 - l2|]
 // on an n_side x n_side coarse grid (k = k1 * n_side + k2): the centre cost

@@ -210,3 +210,40 @@ def test_symmetric_dual(prec, batched):
                 assert r1[t]["lb_p"] <= s + 1e-12 and s - r1[t]["lb_p"] <= 1e-9 * (1 + abs(s))
                 sides += r1[t]["lb_p"] > r0[t]["lb_p"]
     assert sides >= 1, "the side started from g~ never won: its path went unexercised"
+
+
+@pytest.mark.parametrize("sweeps", [1, 7, 50])
+@pytest.mark.parametrize("batched", [True, False])
+def test_fine_ipf_scalings(sweeps, batched):
+    """The fine FP32 IPF sweeps: from b = 1 the uniform kernel reaches its fixed point
+    a = kappa^2 mu / mu~, b = kappa^2 nu / nu~ after one sweep whatever the
+    coarse plan (Sec. 3.4, IPF paragraph), and further sweeps stay there up to
+    FP32 rounding.  The oracle's FP64 IPF on its own plan agrees."""
+    cases = [(32, 4, 2.0, "gauss"), (64, 8, 2.0, "field"), (32, 2, 1.0, "white"),
+             (48, 4, 1.0, "cauchy"), (64, 4, 2.0, "gauss")]
+    mus, nus, probs = [], [], []
+    for i, (N, kappa, p, cls) in enumerate(cases):
+        mu, nu = synth.make_measure(N, cls, 40 + i, 0), synth.make_measure(N, cls, 40 + i, 1)
+        if i == 4:   # a zero-mass block on each side
+            mu = mu.reshape(N, N).copy(); mu[8:12, 4:8] = 0.0; mu = (mu / mu.sum()).ravel()
+            nu = nu.reshape(N, N).copy(); nu[0:4, 60:64] = 0.0; nu = (nu / nu.sum()).ravel()
+        mus.append(mu); nus.append(nu); probs.append((N, kappa, p))
+    with api.Batch(probs, ipf_sweeps=sweeps, prec="mixed") as b:
+        md, nd = [T(x) for x in mus], [T(x) for x in nus]
+        b.coarse(md, nd, batched=batched)
+        b.solve()
+        b.fine(md, nd, batched=batched)
+        assert all(r["status"] == 0 for r in b.results())
+        for t, (N, kappa, p) in enumerate(probs):
+            a, bb = (x.cpu().numpy() for x in b.fine_scalings(t))
+            for got, meas in ((a, mus[t]), (bb, nus[t])):
+                coarse = O.sumpool(meas, N, kappa)
+                blk = np.repeat(np.repeat(coarse.reshape(N // kappa, N // kappa), kappa, 0), kappa, 1).ravel()
+                want = np.where(blk > 0, kappa ** 2 * meas / np.where(blk > 0, blk, 1.0), 0.0)
+                np.testing.assert_allclose(got, want, rtol=2e-5, atol=0)
+            if t == 0:
+                plan, _, _, _ = O.exact_ot(O.coarse_cost_centre(N, kappa, p),
+                                           O.sumpool(mus[t], N, kappa), O.sumpool(nus[t], N, kappa))
+                ref = O.ipf(mus[t], nus[t], plan, N, kappa, max_sweeps=sweeps)
+                np.testing.assert_allclose(a, ref["a"], rtol=2e-5, atol=0)
+                np.testing.assert_allclose(bb, ref["b"], rtol=2e-5, atol=0)
