@@ -338,6 +338,9 @@ def run_gpu(args):
                 "max_rel_lb_diff_vs_lazy": dlb,
                 "note": "QWB_FLAG_SEPARABLE: p = 2 c-transform as two 1-D transforms (2 N^3 pairs "
                         "each) instead of the N^4 lazy transform; same certified rounding"}
+        if not args.skip_workloads:
+            out["uneven_200"] = _uneven_workload(api, dev, args)
+            out["differentiable_256"] = _differentiable_workload(api, dev, args)
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args.cpu_seconds, args.cpu_workers)
     batch.close()
@@ -345,6 +348,95 @@ def run_gpu(args):
         dist.barrier()
         dist.destroy_process_group()
     return out
+
+
+# ----------------------------------------------------------------------------
+# secondary workloads (reported beside the headline, rank 0)
+# ----------------------------------------------------------------------------
+def _event_ms(fn, steps, warmup, flush):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    times = []
+    for _ in range(steps):
+        _flush_l2(flush)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return statistics.mean(times)
+
+
+def _uneven_workload(api, dev, args):
+    """200 pairs with N in {32, 64, 128, 256}, kappa in {4, 8}, p in {1, 2}, one
+    batch (autotuned persistent launches replayed from CUDA graphs)."""
+    import torch
+    from paper_2506_00976_gb300 import synth
+    W = synth.uneven_workload(200)
+    mus = [torch.tensor(w["mu"], dtype=torch.float64, device=dev) for w in W]
+    nus = [torch.tensor(w["nu"], dtype=torch.float64, device=dev) for w in W]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    with api.Batch([(w["N"], w["kappa"], w["p"]) for w in W], ipf_sweeps=SWEEPS, prec="mixed",
+                   device=dev) as bt:
+        bt.coarse(mus, nus, batched=True)
+        t0 = time.perf_counter()
+        bt.solve(threads=args.threads)
+        solve_s = time.perf_counter() - t0
+
+        def step():
+            bt.coarse(mus, nus, batched=True)
+            bt.fine(mus, nus, batched=True)
+        ms = _event_ms(step, max(3, min(args.steps, 5)), 3, flush)
+        res = bt.results()
+        assert all(r["status"] == 0 for r in res)
+        sizes = {}
+        for w in W:
+            sizes[w["N"]] = sizes.get(w["N"], 0) + 1
+        return {"value": round(len(W) / (ms * 1e-3), 3), "unit": "pairs/s", "ms_per_step": round(ms, 4),
+                "pairs_by_N": sizes, "host_solve_s": round(solve_s, 3),
+                "what": "device passes (SumPool, C-bar, IPF 50 sweeps + upper bound, c-transforms + "
+                        "lower bound) of one batch of 200 uneven pairs; host exact solves separate",
+                "autotune": bt.tuning()}
+
+
+def _differentiable_workload(api, dev, args):
+    """16 smooth-field pairs of 256 x 256, p = 2, kappa 4: the lower bound's
+    device passes and the adjoint kernel's gradient with respect to mu."""
+    import torch
+    from paper_2506_00976_gb300 import synth
+    Nd, kd, pd = 256, 4, 2.0
+    pairs = synth.class_pairs(Nd, "field", 4)[:16]
+    mus = [torch.tensor(a, dtype=torch.float64, device=dev) for a, _ in pairs]
+    nus = [torch.tensor(b, dtype=torch.float64, device=dev) for _, b in pairs]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    with api.Batch([(Nd, kd, pd)] * len(pairs), ipf_sweeps=1, prec="mixed", flags=1 | 2,
+                   device=dev) as bt:
+        bt.coarse(mus, nus, batched=True)
+        bt.solve(threads=args.threads)
+        bt.fine(mus, nus, batched=True)
+        res = bt.results()
+        fs = [bt.potentials(t)[0] for t in range(len(pairs))]
+
+        def fwd():
+            bt.coarse(mus, nus, batched=True)
+            bt.fine(mus, nus, batched=True)
+
+        def adj():
+            for t in range(len(pairs)):
+                api.lb_adjoint(fs[t], mus[t], Nd, pd, res[t]["lb_p"])
+        ms_f = _event_ms(fwd, 3, 3, flush)
+        ms_a = _event_ms(adj, 3, 3, flush)
+    return {"value": round(len(pairs) / ((ms_f + ms_a) * 1e-3), 3), "unit": "pairs/s",
+            "forward_ms": round(ms_f, 4), "adjoint_ms": round(ms_a, 4),
+            "what": "16 pairs of 256x256 smooth random fields, kappa 4 (64x64 coarse), p 2: lower-bound "
+                    "device passes (SumPool, upsample, two lazy c-transforms, sum) plus the adjoint "
+                    "kernel for every pair; host exact solves excluded"}
 
 
 # ----------------------------------------------------------------------------
@@ -443,6 +535,8 @@ def main():
                     help="pairs per value class (45 = the full workload; smaller for profiling)")
     ap.add_argument("--skip-plain", action="store_true", help="time only the batched form")
     ap.add_argument("--skip-e2e", action="store_true", help="skip the end-to-end timing")
+    ap.add_argument("--skip-workloads", action="store_true",
+                    help="skip the uneven 200-pair and differentiable 256x256 measurements")
     ap.add_argument("--skip-separable", action="store_true",
                     help="skip the separable p = 2 c-transform measurement")
     args = ap.parse_args()
