@@ -393,13 +393,14 @@ def _uneven_workload(api, dev, args):
             bt.coarse(mus, nus, batched=True)
             bt.fine(mus, nus, batched=True)
         ms = _event_ms(step, max(3, min(args.steps, 5)), 3, flush)
+        kern = {k: round(v, 4) for k, v in bt.kernel_times().items()}
         res = bt.results()
         assert all(r["status"] == 0 for r in res)
         sizes = {}
         for w in W:
             sizes[w["N"]] = sizes.get(w["N"], 0) + 1
         return {"value": round(len(W) / (ms * 1e-3), 3), "unit": "pairs/s", "ms_per_step": round(ms, 4),
-                "pairs_by_N": sizes, "host_solve_s": round(solve_s, 3),
+                "kernel_ms": kern, "pairs_by_N": sizes, "host_solve_s": round(solve_s, 3),
                 "what": "device passes (SumPool, C-bar, IPF 50 sweeps + upper bound, c-transforms + "
                         "lower bound) of one batch of 200 uneven pairs; host exact solves separate",
                 "autotune": bt.tuning()}

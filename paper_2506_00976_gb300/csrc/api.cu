@@ -76,7 +76,7 @@ struct CostTable {
 // Launch configuration chosen by the autotuner for one problem signature.
 struct TuneEntry {
     std::string key;
-    int R = 0, TC = 0, packed = 0, cbar_variant = 0;
+    int R = 0, TC = 0, packed = 0, cbar_variant = 2, cbar8_variant = 4;
     bool ct_done = false, cbar_done = false;
     std::string ct_report, cbar_report;   // JSON fragments: candidate -> ms
 };
@@ -105,6 +105,8 @@ static void tune_cache_load(qwb_ctx* c) {
             continue;
         e.R = std::atoi(r.c_str()); e.TC = std::atoi(tc.c_str());
         e.packed = std::atoi(pk.c_str()); e.cbar_variant = std::atoi(cv.c_str());
+        const size_t slash = cv.find('/');                      // "kappa4 variant/kappa8 variant"
+        if (slash != std::string::npos) e.cbar8_variant = std::atoi(cv.c_str() + slash + 1);
         e.ct_done = e.R > 0; e.cbar_done = true;
         e.ct_report = "\"cached\""; e.cbar_report = "\"cached\"";
         c->tunes.push_back(e);
@@ -116,7 +118,8 @@ static void tune_cache_store(qwb_ctx* c) {
     std::ofstream out(c->tune_cache, std::ios::trunc);
     for (auto& e : c->tunes)
         if (e.ct_done && e.cbar_done)
-            out << e.key << '|' << e.R << '|' << e.TC << '|' << e.packed << '|' << e.cbar_variant << "|\n";
+            out << e.key << '|' << e.R << '|' << e.TC << '|' << e.packed << '|' << e.cbar_variant << '/'
+                << e.cbar8_variant << "|\n";
 }
 
 static int ctx_table(qwb_ctx* c, int N, double p, bool f64, cudaStream_t s, const void** lo,
@@ -169,9 +172,17 @@ struct qwb_batch {
     std::vector<int> cbar3_off, cbar3_cnt;
     int n_cbar3 = 0;
     bool has_3d = false;
-    int n_max2 = 0, N_max2 = 0;              // largest n, N over 2-D pairs (2-D C-bar kernel)
+    int n_max2 = 0, N_max2 = 0;              // largest n, N over the other 2-D pairs (generic C-bar kernel)
+    // 2-D C-bar items in three groups: FP32 pairs with kappa = 4 and with
+    // kappa = 8 whose n is a power of two (cbar4 / cbar8 kernels), then the
+    // others (one generic launch, kappa_code)
+    int n_cb4 = 0, n_max4 = 0, N_max4 = 0;
+    int n_cb8 = 0, n_max8 = 0, N_max8 = 0;
+    int cbar8_variant = 4;
+    std::vector<char> cbar_group;       // per pair: 4, 8 or 0
     std::vector<int> prep_off, prep_cnt, pix_off, pix_cnt, cbar_off, cbar_cnt, ct_off, ct_cnt;
     int n_prep = 0, n_pix = 0, n_cbar = 0, n_ct_b = 0;
+    int n_ct_b_p2 = 0;   // batched c-transform items: the p = 2 pairs' items come first
     CtConfig ct_cfg_b, ct_cfg_p;
     int kappa_code = 0, n_max = 0, N_max = 0, M_max = 0;
     // coarse-plan staging (pinned host <-> device)
@@ -195,7 +206,6 @@ struct qwb_batch {
     std::vector<GraphEntry> graphs;
     TuneEntry* tune = nullptr;
     int cbar_variant = 0;
-    bool cbar_pow2 = true;      // every 2-D coarse side n is a power of two (cbar4 kernel)
     int N_gcd = 1;
     bool all_p2 = false;
 };
@@ -291,11 +301,19 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         const int N = probs[t].N, kap = probs[t].kappa, nn = N / kap, M = ipow(nn, dd), m = ipow(N, dd);
         b->Ms.push_back(M);
         if (dd == 3) b->has_3d = true;
-        if (dd == 2) {
+        const bool pow2 = dd == 2 && !(nn & (nn - 1)) && nn <= 64 && !b->f64;
+        const int grp = (pow2 && kap == 4) ? 4 : (pow2 && kap == 8) ? 8 : 0;
+        b->cbar_group.push_back((char)grp);
+        if (grp == 4) {
+            b->n_max4 = std::max(b->n_max4, nn);
+            b->N_max4 = std::max(b->N_max4, N);
+        } else if (grp == 8) {
+            b->n_max8 = std::max(b->n_max8, nn);
+            b->N_max8 = std::max(b->N_max8, N);
+        } else if (dd == 2) {
             if (kap0 < 0) kap0 = kap;
             same_kap &= (kap == kap0);
             b->kappa_code = std::max(b->kappa_code, kap);
-            if (nn & (nn - 1)) b->cbar_pow2 = false;
             b->n_max2 = std::max(b->n_max2, nn);
             b->N_max2 = std::max(b->N_max2, N);
         }
@@ -349,10 +367,12 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         if (found->ct_done && found->R > 0 && N_gcd % found->R == 0 && N_gcd % found->TC == 0) {
             b->ct_cfg_b.R = found->R; b->ct_cfg_b.TC = found->TC; b->ct_cfg_b.packed = found->packed;
         }
-        // untuned default: the row-direct kappa = 4 kernel where it applies
-        b->cbar_variant = (b->cbar_pow2 && !b->f64 && b->kappa_code == 4) ? 2 : 0;
-        if (found->cbar_done && (found->cbar_variant < 2 || (b->cbar_pow2 && !b->f64)))
+        // the kappa = 4 row-direct kernel: three (2) or two (3) CTAs per SM
+        b->cbar_variant = 2;
+        if (found->cbar_done && (found->cbar_variant == 2 || found->cbar_variant == 3))
             b->cbar_variant = found->cbar_variant;
+        if (found->cbar_done && (found->cbar8_variant == 4 || found->cbar8_variant == 5))
+            b->cbar8_variant = found->cbar8_variant;
     }
     const int tile_out = CT_TILE;
     long total_tiles = 0;
@@ -368,13 +388,9 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         b->pix_off.push_back((int)pix.size());
         for (int i = 0; i < m; i += 256) pix.push_back({t, i});
         b->pix_cnt.push_back((int)pix.size() - b->pix_off.back());
-        b->cbar_off.push_back((int)cb.size());
         b->cbar3_off.push_back((int)cb3.size());
-        if (dd == 2)
-            for (int w1 = 0; w1 < nn; ++w1) cb.push_back({t, w1, 0, 0});
-        else
+        if (dd == 3)
             for (int k = 0; k < M; ++k) cb3.push_back({t, k});
-        b->cbar_cnt.push_back((int)cb.size() - b->cbar_off.back());
         b->cbar3_cnt.push_back((int)cb3.size() - b->cbar3_off.back());
         b->sep_off.push_back((int)sep.size());
         if (separable(t)) {
@@ -407,8 +423,25 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         b->ct_cfg_b.in_rows = std::max(b->ct_cfg_b.in_rows, maxrows);
         b->ct_cfg_p.in_rows = b->ct_cfg_b.in_rows;
     }
+    // 2-D C-bar items: the cbar4 group, the cbar8 group, then the others
+    b->cbar_off.assign(n, 0); b->cbar_cnt.assign(n, 0);
+    for (int grp : {4, 8, 0}) {
+        const int before = (int)cb.size();
+        for (int t = 0; t < n; ++t) {
+            if (dim_of(probs[t]) != 2 || b->cbar_group[t] != grp) continue;
+            b->cbar_off[t] = (int)cb.size();
+            for (int w1 = 0; w1 < probs[t].N / probs[t].kappa; ++w1) cb.push_back({t, w1, 0, 0});
+            b->cbar_cnt[t] = (int)cb.size() - b->cbar_off[t];
+        }
+        if (grp == 4) b->n_cb4 = (int)cb.size() - before;
+        if (grp == 8) b->n_cb8 = (int)cb.size() - before;
+    }
     b->n_prep = (int)prep.size(); b->n_pix = (int)pix.size(); b->n_cbar = (int)cb.size();
     b->n_cbar3 = (int)cb3.size();
+    // p = 2 pairs first: their items take the exact integer-cost kernels
+    std::stable_partition(ctb.begin(), ctb.end(), [&](const CtItem& it) { return probs[it.pair].p == 2.0; });
+    b->n_ct_b_p2 = 0;
+    for (const auto& it : ctb) b->n_ct_b_p2 += probs[it.pair].p == 2.0 ? 1 : 0;
     b->n_ct_b = (int)ctb.size();
     b->n_sep = (int)sep.size();
     // device allocation
@@ -544,6 +577,14 @@ static int batch_set_measures(qwb_batch* b, const double* const* mu, const doubl
     return QWB_OK;
 }
 
+// the generic C-bar kernel's register budget: three CTAs per SM in FP32
+static int generic_cbar_variant(bool f64) { return f64 ? 0 : 1; }
+// the C-bar variant of pair t when it is launched on its own
+static int pair_cbar_variant(const qwb_batch* b, int t) {
+    return b->cbar_group[t] == 4 ? b->cbar_variant : b->cbar_group[t] == 8 ? b->cbar8_variant
+                                                                           : generic_cbar_variant(b->f64);
+}
+
 static int mark(qwb_batch* b, int i, cudaStream_t s) {
     // external records become event nodes of a captured graph
     if (b->ev_ok) QWB_CUDA(cudaEventRecordWithFlags(b->kev[i], s, cudaEventRecordExternal));
@@ -558,8 +599,15 @@ static int enqueue_coarse(qwb_batch* b, bool batched, cudaStream_t s) {
         if ((st = launch_prepare(b->pairs_d, b->outs_d, b->prep_items_d, b->n_prep, b->f64, s))) return st;
         if ((st = mark(b, 1, s))) return st;
         if (!(b->flags & QWB_FLAG_NO_WEIGHTED)) {
-            if ((st = launch_cbar(b->pairs_d, b->cbar_items_d, b->n_cbar, b->kappa_code, b->n_max2, b->N_max2,
+            if ((st = launch_cbar(b->pairs_d, b->cbar_items_d, b->n_cb4, 4, b->n_max4, b->N_max4,
                                   b->f64, s, b->cbar_variant)))
+                return st;
+            if ((st = launch_cbar(b->pairs_d, b->cbar_items_d + b->n_cb4, b->n_cb8, 8, b->n_max8, b->N_max8,
+                                  b->f64, s, b->cbar8_variant)))
+                return st;
+            const int off = b->n_cb4 + b->n_cb8;
+            if ((st = launch_cbar(b->pairs_d, b->cbar_items_d + off, b->n_cbar - off, b->kappa_code,
+                                  b->n_max2, b->N_max2, b->f64, s, generic_cbar_variant(b->f64))))
                 return st;
             if ((st = launch_cbar3(b->pairs_d, b->cbar3_items_d, b->n_cbar3, b->f64, s))) return st;
         }
@@ -574,12 +622,24 @@ static int enqueue_coarse(qwb_batch* b, bool batched, cudaStream_t s) {
             continue;
         }
         const int nn = b->probs[t].N / b->probs[t].kappa;
-        const int kc = (b->probs[t].kappa == 1 || b->probs[t].kappa == 2 || b->probs[t].kappa == 4)
-                           ? b->probs[t].kappa : -b->probs[t].kappa;
+        const int kc = (b->probs[t].kappa == 1 || b->probs[t].kappa == 2 || b->probs[t].kappa == 4 ||
+                        b->cbar_group[t] == 8) ? b->probs[t].kappa : -b->probs[t].kappa;
         if ((st = launch_cbar(b->pairs_d, b->cbar_items_d + b->cbar_off[t], b->cbar_cnt[t], kc, nn,
-                              b->probs[t].N, b->f64, s))) return st;
+                              b->probs[t].N, b->f64, s, pair_cbar_variant(b, t)))) return st;
     }
     return QWB_OK;
+}
+
+// The batched c-transform: one launch over the p = 2 pairs' items (exact
+// integer costs), one over the others (cost table).
+static int launch_ct_batched(qwb_batch* b, int phase, CtConfig cfg, int cap, cudaStream_t s) {
+    int st;
+    cfg.p2 = true;
+    if ((st = launch_ctransform(b->pairs_d, b->ct_b_items_d, b->n_ct_b_p2, phase, cfg, b->N_max, b->f64, cap, s)))
+        return st;
+    cfg.p2 = false;
+    return launch_ctransform(b->pairs_d, b->ct_b_items_d + b->n_ct_b_p2, b->n_ct_b - b->n_ct_b_p2, phase, cfg,
+                             b->N_max, b->f64, cap, s);
 }
 
 static int enqueue_fine(qwb_batch* b, bool batched, cudaStream_t s) {
@@ -599,7 +659,7 @@ static int enqueue_fine(qwb_batch* b, bool batched, cudaStream_t s) {
             for (int phase = 0; phase < 2; ++phase) {
                 for (int stage = 0; stage < b->sep_stages; ++stage)
                     if ((st = launch_sep(b->pairs_d, b->sep_items_d, b->n_sep, phase, stage, b->N_max, b->f64, cap, s))) return st;
-                if ((st = launch_ctransform(b->pairs_d, b->ct_b_items_d, b->n_ct_b, phase, b->ct_cfg_b, b->N_max, b->f64, cap, s))) return st;
+                if ((st = launch_ct_batched(b, phase, b->ct_cfg_b, cap, s))) return st;
                 if (phase == 0 && (st = mark(b, 7, s))) return st;
             }
             if ((st = mark(b, 8, s))) return st;
@@ -615,7 +675,7 @@ static int enqueue_fine(qwb_batch* b, bool batched, cudaStream_t s) {
             for (int phase = 0; phase < 2; ++phase) {
                 for (int stage = 0; stage < b->sep_stages; ++stage)
                     if ((st = launch_sep(b->pairs_d, b->sep_items_d, b->n_sep, phase, stage, b->N_max, b->f64, cap, s))) return st;
-                if ((st = launch_ctransform(b->pairs_d, b->ct_b_items_d, b->n_ct_b, phase, b->ct_cfg_b, b->N_max, b->f64, cap, s))) return st;
+                if ((st = launch_ct_batched(b, phase, b->ct_cfg_b, cap, s))) return st;
             }
             if ((st = launch_lbsum(b->pairs_d, b->outs_d, b->pair_ids_d, b->n, b->f64, s, 1))) return st;
         }
@@ -675,35 +735,50 @@ static const char* cbar_variant_name(int v) {
     switch (v) {
         case 0: return "staged_rows/2_ctas_per_sm";
         case 1: return "staged_rows/3_ctas_per_sm";
-        case 2: return "direct_rows/3_ctas_per_sm";
-        default: return "direct_rows/2_ctas_per_sm";
+        case 2: return "kappa4_direct_rows/3_ctas_per_sm";
+        case 3: return "kappa4_direct_rows/2_ctas_per_sm";
+        case 4: return "kappa8_direct_rows/2_ctas_per_sm";
+        default: return "kappa8_direct_rows/1_cta_per_sm";
     }
 }
 
 static int tune_cbar(qwb_batch* b, cudaStream_t s) {
     TuneEntry* e = b->tune;
     if (!b->ctx->autotune || !e || e->cbar_done || !b->ev_ok) return QWB_OK;
-    if (b->kappa_code != 4 || (b->flags & QWB_FLAG_NO_WEIGHTED)) { e->cbar_done = true; e->cbar_report = "{}"; return QWB_OK; }
+    if ((b->n_cb4 == 0 && b->n_cb8 == 0) || (b->flags & QWB_FLAG_NO_WEIGHTED)) { e->cbar_done = true; e->cbar_report = "{}"; return QWB_OK; }
     int st = launch_prepare(b->pairs_d, b->outs_d, b->prep_items_d, b->n_prep, b->f64, s);
     if (st) return st;
     std::ostringstream rep;
     double best = 1e30;
     rep << "{";
-    const int nv = (b->cbar_pow2 && !b->f64) ? 4 : 2;
-    for (int v = 0; v < nv; ++v) {
+    bool first = true;
+    for (int v = 2; v < 4 && b->n_cb4 > 0; ++v) {
         double ms;
         st = time_variant(s, b->ev[0], b->ev[1], [&] {
-            return launch_cbar(b->pairs_d, b->cbar_items_d, b->n_cbar, b->kappa_code, b->n_max2, b->N_max2,
-                               b->f64, s, v);
+            return launch_cbar(b->pairs_d, b->cbar_items_d, b->n_cb4, 4, b->n_max4, b->N_max4, b->f64, s, v);
         }, &ms);
         if (st) return st;
-        rep << (v ? ", " : "") << "\"" << cbar_variant_name(v) << "\": " << ms;
+        rep << (first ? "" : ", ") << "\"" << cbar_variant_name(v) << "\": " << ms;
+        first = false;
         if (ms < best) { best = ms; e->cbar_variant = v; }
+    }
+    double best8 = 1e30;
+    for (int v = 4; v < 6 && b->n_cb8 > 0; ++v) {
+        double ms;
+        st = time_variant(s, b->ev[0], b->ev[1], [&] {
+            return launch_cbar(b->pairs_d, b->cbar_items_d + b->n_cb4, b->n_cb8, 8, b->n_max8, b->N_max8, b->f64,
+                               s, v);
+        }, &ms);
+        if (st) return st;
+        rep << (first ? "" : ", ") << "\"" << cbar_variant_name(v) << "\": " << ms;
+        first = false;
+        if (ms < best8) { best8 = ms; e->cbar8_variant = v; }
     }
     rep << "}";
     e->cbar_report = rep.str();
     e->cbar_done = true;
     b->cbar_variant = e->cbar_variant;
+    b->cbar8_variant = e->cbar8_variant;
     tune_cache_store(b->ctx);
     return QWB_OK;
 }
@@ -728,7 +803,7 @@ static int tune_ctransform(qwb_batch* b, cudaStream_t s) {
         cfg.R = c[0]; cfg.TC = c[1]; cfg.packed = c[2];
         double ms;
         st = time_variant(s, b->ev[0], b->ev[1], [&] {
-            return launch_ctransform(b->pairs_d, b->ct_b_items_d, b->n_ct_b, 0, cfg, b->N_max, b->f64, sm, s);
+            return launch_ct_batched(b, 0, cfg, sm, s);
         }, &ms);
         if (st) return st;
         rep << (first ? "" : ", ") << "\"R" << c[0] << "xT" << c[1] << (c[2] == 1 ? "_packed" : c[2] == 2 ? "_linepairs" : "") << "\": " << ms;
@@ -1294,11 +1369,12 @@ int qwb_coarse_cost(qwb_ctx* ctx, const qwb_problem* prob, const double* mu_d, c
     P.cbar = own_cbar;
     QWB_CUDA(cudaMemsetAsync(b->outs_d, 0, sizeof(PairOut), s));
     if ((st = single_validate(b, s))) return st;
-    const int kc = (prob->kappa == 1 || prob->kappa == 2 || prob->kappa == 4) ? prob->kappa : -prob->kappa;
+    const int kc = (prob->kappa == 1 || prob->kappa == 2 || prob->kappa == 4 || b->cbar_group[0] == 8)
+                       ? prob->kappa : -prob->kappa;
     if (dim_of(*prob) == 3) {
         if ((st = launch_cbar3(b->pairs_d, b->cbar3_items_d, b->n_cbar3, b->f64, s))) return st;
     } else if ((st = launch_cbar(b->pairs_d, b->cbar_items_d, b->n_cbar, kc, prob->N / prob->kappa, prob->N,
-                                 b->f64, s))) {
+                                 b->f64, s, pair_cbar_variant(b, 0)))) {
         return st;
     }
     const size_t M = b->Ms[0];

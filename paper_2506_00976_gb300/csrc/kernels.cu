@@ -578,6 +578,143 @@ cbar4_kernel(const PairDev* __restrict__ pairs, const CbarItem* __restrict__ ite
 }
 
 // --------------------------------------------------------------------------
+// cbar8: the kappa = 8 FP32 C-bar for power-of-two coarse sides n.  Same sums
+// and rounding as cbar_kernel (inner[a] = sum_b nu_b c(a - b) over b1, b2,
+// then sum_a mu_a inner[a], every FMA rounded up), the thread mapping of
+// cbar4 (consecutive target blocks per warp, coalesced FP64 rows).  The
+// 15 x 15 cost window of a block offset does not fit in registers, so the
+// item stages the 2 x 15 cost-table rows of its two block-row offsets in
+// shared memory, reflected (row[c + N - 1] = table[|c|], c in (-N, N)), and a
+// thread reads the 15 costs of window row a1 - b1 as four aligned 16-byte
+// loads starting at 8 * (k2 - l2) + N - 8; 64 FMAs per window row, in two
+// passes of four source rows (32 accumulators).
+// --------------------------------------------------------------------------
+constexpr int CBAR8_S = 2;   // block rows staged per chunk
+
+static size_t cbar8_smem(int n, int N) {
+    return sizeof(float) * ((size_t)2 * 15 * 2 * N + (size_t)2 * CBAR8_S * 8 * N + (size_t)2 * CBAR8_S * n);
+}
+
+// A block pair with an empty block (kappa = 8): the unweighted mean of the
+// cost over the pair, rounded up, from the staged reflected rows.
+__device__ __noinline__ double cbar8_special(const PairDev& P, int k, int l, float acc,
+                                             const float* wbase, int RL) {
+    constexpr int KAP = 8, WK = 2 * KAP - 1;
+    double mean = 0.0;
+    for (int d1 = 0; d1 < WK; ++d1)
+        for (int d2 = 0; d2 < WK; ++d2)
+            mean = __fma_ru((double)((KAP - abs(d1 - (KAP - 1))) * (KAP - abs(d2 - (KAP - 1)))),
+                            (double)wbase[d1 * RL + d2], mean);
+    mean = __ddiv_ru(mean, (double)(KAP * KAP * KAP * KAP));
+    return cbar_special<float>(P, k, l, (double)acc, mean);
+}
+
+template <int MINB>
+__global__ void __launch_bounds__(CBAR_THREADS, MINB)
+cbar8_kernel(const PairDev* __restrict__ pairs, const CbarItem* __restrict__ items, int n_items) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int KAP = 8, WK = 2 * KAP - 1;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const CbarItem I = items[it];
+        const PairDev& P = pairs[I.pair];
+        const int N = P.N, n = P.n, M = P.M;
+        const int lg = 31 - __clz(n);
+        const int w1 = I.w1;
+        const int RL = 2 * N;                                   // reflected row length (padded)
+        double* __restrict__ cbar = P.cbar;
+        float* refl_s = reinterpret_cast<float*>(smem_raw);     // [2][15][RL]
+        float* mu_s = refl_s + 2 * WK * RL;                     // [S][KAP][N]
+        float* nu_s = mu_s + CBAR8_S * KAP * N;                 // [S][KAP][N]
+        float* rk_s = nu_s + CBAR8_S * KAP * N;                 // [S][n]
+        float* rl_s = rk_s + CBAR8_S * n;                       // [S][n]
+        const float* tab = reinterpret_cast<const float*>(P.ctab_hi);
+        const float* mu_up = reinterpret_cast<const float*>(P.mu_up);
+        const float* nu_up = reinterpret_cast<const float*>(P.nu_up);
+        __syncthreads();            // the previous item's readers are done
+        for (int idx = threadIdx.x; idx < 2 * WK * RL; idx += blockDim.x) {
+            const int vd = idx / RL, c = idx - vd * RL - (N - 1);
+            const int v = vd / WK, d1 = vd - v * WK;
+            const int row = abs(KAP * (v == 0 ? w1 : w1 - n) + d1 - (KAP - 1));
+            refl_s[idx] = (row < N && c < N) ? tab[row * N + abs(c)] : 0.0f;
+        }
+        for (int k1_0 = 0; k1_0 < n; k1_0 += CBAR8_S) {
+            const int S = min(CBAR8_S, n - k1_0);
+            __syncthreads();
+            for (int s = 0; s < S; ++s) {
+                const int k1 = k1_0 + s;
+                int l1 = k1 - w1;
+                if (l1 < 0) l1 += n;
+                const float4* msrc = reinterpret_cast<const float4*>(mu_up + (size_t)k1 * KAP * N);
+                const float4* nsrc = reinterpret_cast<const float4*>(nu_up + (size_t)l1 * KAP * N);
+                float4* mdst = reinterpret_cast<float4*>(mu_s + s * KAP * N);
+                float4* ndst = reinterpret_cast<float4*>(nu_s + s * KAP * N);
+                for (int c = threadIdx.x; c < 2 * N; c += blockDim.x) { mdst[c] = msrc[c]; ndst[c] = nsrc[c]; }
+                if (threadIdx.x < n) {
+                    rk_s[s * n + threadIdx.x] = P.mu_rinv32[k1 * n + threadIdx.x];
+                    rl_s[s * n + threadIdx.x] = P.nu_rinv32[l1 * n + threadIdx.x];
+                }
+            }
+            __syncthreads();
+            for (int b = threadIdx.x; b < (n << lg); b += blockDim.x) {
+                const int k2 = b >> lg, l2 = b & (n - 1);
+                const int D2 = k2 - l2;
+                for (int s = 0; s < S; ++s) {
+                    const int k1 = k1_0 + s;
+                    const int v = k1 >= w1 ? 0 : 1;
+                    const float* wbase = refl_s + v * WK * RL + KAP * D2 + N - KAP;   // row d1 = 0, col d2 = 0
+                    // two passes of four source rows a1 each (32 accumulators)
+                    float acc = 0.0f;
+#pragma unroll 1
+                    for (int ah = 0; ah < KAP; ah += 4) {
+                        float inner[4][KAP];
+#pragma unroll
+                        for (int ar = 0; ar < 4; ++ar)
+#pragma unroll
+                            for (int a2 = 0; a2 < KAP; ++a2) inner[ar][a2] = 0.0f;
+#pragma unroll 1
+                        for (int b1 = 0; b1 < KAP; ++b1) {
+                            const float4* np4 = reinterpret_cast<const float4*>(nu_s + (s * KAP + b1) * N + l2 * KAP);
+                            const float4 n0 = np4[0], n1 = np4[1];
+                            const float nrow[KAP] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
+#pragma unroll
+                            for (int ar = 0; ar < 4; ++ar) {
+                                const int a1 = ah + ar;
+                                const float4* wr = reinterpret_cast<const float4*>(wbase + (a1 - b1 + KAP - 1) * RL);
+                                float w[16];
+#pragma unroll
+                                for (int q = 0; q < 4; ++q) *reinterpret_cast<float4*>(w + 4 * q) = wr[q];
+#pragma unroll
+                                for (int b2 = 0; b2 < KAP; ++b2)
+#pragma unroll
+                                    for (int a2 = 0; a2 < KAP; ++a2) {
+                                        inner[ar][a2] = fma_ru(nrow[b2], w[a2 - b2 + KAP - 1], inner[ar][a2]);
+                                    }
+                            }
+                        }
+#pragma unroll
+                        for (int ar = 0; ar < 4; ++ar) {
+                            const int a1 = ah + ar;
+                            const float4* mp4 = reinterpret_cast<const float4*>(mu_s + (s * KAP + a1) * N + k2 * KAP);
+                            const float4 m0 = mp4[0], m1 = mp4[1];
+                            const float mrow[KAP] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+#pragma unroll
+                            for (int a2 = 0; a2 < KAP; ++a2) acc = fma_ru(mrow[a2], inner[ar][a2], acc);
+                        }
+                    }
+                    int l1 = k1 - w1;
+                    if (l1 < 0) l1 += n;
+                    const int k = (k1 << lg) + k2, l = (l1 << lg) + l2;
+                    const float rk = rk_s[s * n + k2], rl = rl_s[s * n + l2];
+                    cbar[(size_t)k * M + l] = (rk > 0.0f && rl > 0.0f)
+                                                  ? widen_f32(mul_ru(mul_ru(acc, rk), rl))
+                                                  : cbar8_special(P, k, l, acc, wbase, RL);
+                }
+            }
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
 // cbar3: C-bar on 3-D grids (volumes), the same definition and rounding as
 // cbar_kernel: num_kl = sum_{a in X_k} mu_a sum_{b in Y_l} nu_b rho(a, b)^p
 // with upward-rounded FMAs (inner sums over b first), then multiplied by
@@ -661,8 +798,8 @@ static int cbar_dispatch(const PairDev* pairs_d, const CbarItem* items, int n_it
     const int kmax = kappa_code > 0 ? kappa_code : -kappa_code;
     const bool windows = kappa_code == 1 || kappa_code == 2 || kappa_code == 4;
     const size_t smem = cbar_smem(sizeof(T), kmax, n_max, N_max, windows);
-    if (smem > 227 * 1024) return QWB_ERR_UNSUPPORTED;
     auto run = [&](auto kern) -> int {
+        if (smem > 227 * 1024) return QWB_ERR_UNSUPPORTED;
         QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<n_items, CBAR_THREADS, smem, stream>>>(pairs_d, items, n_items);
         QWB_LAUNCHED();
@@ -670,9 +807,19 @@ static int cbar_dispatch(const PairDev* pairs_d, const CbarItem* items, int n_it
     };
     // variant 0: register budget for two CTAs per SM; 1: for three CTAs per SM;
     // 2, 3: the kappa = 4 FP32 kernel with row-direct writes (every coarse side
-    // of the launch a power of two), three or two CTAs per SM
+    // of the launch a power of two), three or two CTAs per SM; 4, 5: the
+    // kappa = 8 FP32 kernel (powers of two), two or one CTA per SM
     constexpr int MB = sizeof(T) == 4 ? 3 : 1;
     if constexpr (sizeof(T) == 4) {
+        if (kappa_code == 8 && (variant == 4 || variant == 5)) {
+            const size_t smem8 = cbar8_smem(n_max, N_max);
+            if (smem8 > 227 * 1024) return QWB_ERR_UNSUPPORTED;
+            auto kern = variant == 4 ? cbar8_kernel<2> : cbar8_kernel<1>;
+            QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem8));
+            kern<<<n_items, CBAR_THREADS, smem8, stream>>>(pairs_d, items, n_items);
+            QWB_LAUNCHED();
+            return QWB_OK;
+        }
         if (kappa_code == 4 && (variant == 2 || variant == 3)) {
             const size_t smem4 = cbar4_smem(n_max, N_max);
             if (smem4 > 227 * 1024) return QWB_ERR_UNSUPPORTED;

@@ -94,6 +94,7 @@ struct Solver {
     std::vector<int> cand_i, cand_j;  // endpoints and cost of each candidate
     std::vector<double> cand_c;
     std::vector<uint64_t> in_cand;    // bitset over the real arcs
+    std::vector<double> row_buf;
     int64_t cand_pos = 0;
     void push_candidate(int64_t a) {
         in_cand[(size_t)(a >> 6)] |= 1ull << (a & 63);
@@ -321,14 +322,17 @@ struct Solver {
     int64_t add_violators() {
         int64_t added = 0;
         const double* pg = pot.data() + n;
+        std::vector<double>& rcs = row_buf;
+        rcs.resize(m);
         for (int i = 0; i < n; ++i) {
             double best = -eps;
             int64_t dummy = -1;
             scan_run(i, 0, m, best, dummy);          // row minimum below -eps?
             if (dummy < 0) continue;
+            row_costs(i, rcs.data());
             const double pi = pot[i];
             for (int j = 0; j < m; ++j) {
-                const double rc = cst(i, j) - pi + pg[j];
+                const double rc = rcs[j] - pi + pg[j];
                 if (rc < -eps) {
                     const int64_t a = (int64_t)i * m + j;
                     if (!((in_cand[(size_t)(a >> 6)] >> (a & 63)) & 1ull)) {
@@ -339,6 +343,19 @@ struct Solver {
             }
         }
         return added;
+    }
+    // the costs of row i (grid costs through the reflected table rows)
+    void row_costs(int i, double* out) const {
+        if constexpr (std::is_same<Cost, GridCost>::value) {
+            const int ns = cst.ns, i1 = i / ns, i2 = i % ns;
+            for (int jr = 0; jr < ns; ++jr) {
+                const double* refl = cst.refl + (size_t)std::abs(i1 - jr) * (2 * ns - 1) + (ns - 1 - i2);
+                for (int c = 0; c < ns; ++c) out[jr * ns + c] = refl[c];
+            }
+        } else {
+            const double* c = cst.C + (int64_t)i * m;
+            for (int j = 0; j < m; ++j) out[j] = c[j];
+        }
     }
 
     void pivot(int64_t e) {
@@ -519,6 +536,9 @@ int network_simplex(int32_t n_src, int32_t n_dst, const double* C, const double*
 
 namespace {
 constexpr int kMultiscaleMin = 16;   // coarse-to-fine from this grid side up (even sides)
+// fine cells added around the children of each coarse target (a wider set
+// lets more poor arcs enter early and costs more pivots than it saves)
+constexpr int kCandHalo = 0;
 
 int grid_solve(int32_t n_side, const double* tab, const double* a, const double* b, NSSolution& out,
                int64_t max_pivots, NSBasis* basis_out, const NSBasis* warm);
@@ -544,12 +564,13 @@ int grid_candidates(int32_t n_side, const double* tab, const double* a, const do
         for (int e = sh.rowptr[K]; e < sh.rowptr[K + 1]; ++e) {
             const int L = sh.col[e];
             const int K1 = K / h, K2 = K % h, L1 = L / h, L2 = L % h;
-            for (int u = 0; u < 4; ++u)
-                for (int v = 0; v < 4; ++v) {
-                    const int k = (2 * K1 + u / 2) * n_side + 2 * K2 + u % 2;
-                    const int l = (2 * L1 + v / 2) * n_side + 2 * L2 + v % 2;
-                    cand.push_back((int64_t)k * M + l);
-                }
+            for (int u = 0; u < 4; ++u) {
+                const int k = (2 * K1 + u / 2) * n_side + 2 * K2 + u % 2;
+                for (int r = 2 * L1 - kCandHalo; r <= 2 * L1 + 1 + kCandHalo; ++r)
+                    for (int c = 2 * L2 - kCandHalo; c <= 2 * L2 + 1 + kCandHalo; ++c)
+                        if (r >= 0 && c >= 0 && r < n_side && c < n_side)
+                            cand.push_back((int64_t)k * M + r * n_side + c);
+            }
         }
     return QWB_OK;
 }

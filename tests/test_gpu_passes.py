@@ -69,7 +69,8 @@ def test_ctransform_f64(N, p):
 
 @pytest.mark.parametrize("N,kappa,p", [(8, 2, 2.0), (12, 3, 2.0), (16, 4, 1.0), (32, 4, 2.0),
                                         (32, 8, 2.0), (16, 1, 2.0), (24, 4, 1.5), (64, 4, 2.0),
-                                        (24, 4, 2.0), (64, 4, 1.0), (4, 4, 2.0)])
+                                        (24, 4, 2.0), (64, 4, 1.0), (4, 4, 2.0), (64, 8, 1.0),
+                                        (48, 8, 2.0), (8, 8, 2.0)])
 @pytest.mark.parametrize("prec", ["mixed", "f64"])
 def test_coarse_cost(N, kappa, p, prec):
     mu, nu = synth.make_measure(N, "gauss", 20, 0), synth.make_measure(N, "field", 20, 1)
@@ -83,10 +84,10 @@ def test_coarse_cost(N, kappa, p, prec):
     assert np.all(got <= ref * (1 + rel) + 1e-300)
 
 
-def test_coarse_cost_zero_mass_block():
-    N, kappa = 16, 4
+@pytest.mark.parametrize("N,kappa", [(16, 4), (32, 8), (24, 4)])
+def test_coarse_cost_zero_mass_block(N, kappa):
     mu = synth.make_measure(N, "gauss", 21, 0).reshape(N, N).copy()
-    mu[4:8, 8:12] = 0.0
+    mu[kappa:2 * kappa, 2 * kappa:3 * kappa] = 0.0
     mu = (mu / mu.sum()).ravel()
     nu = synth.make_measure(N, "gauss", 21, 1)
     for prec in ("mixed", "f64"):

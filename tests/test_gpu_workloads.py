@@ -85,12 +85,12 @@ def _valid(r):
     assert np.isfinite([r["lb"], r["ub_weighted"], r["ub_primal"]]).all()
 
 
-@pytest.mark.parametrize("p", [1.0, 2.0])
-def test_ctransform_256_sampled(p):
-    """One lazy c-transform on a 256 x 256 grid (65536^2 pixel pairs): sampled
-    outputs against the oracle's one-at-a-time transform (bit-exact round-down
-    for p = 2, where every cost is exact in FP32)."""
-    N = 256
+@pytest.mark.parametrize("N,p", [(256, 1.0), (256, 2.0), (1024, 2.0), (1024, 1.5)])
+def test_ctransform_256_sampled(N, p):
+    """One lazy c-transform on a 256 x 256 grid (65536^2 pixel pairs) and on
+    the largest grid the library accepts, 1024 x 1024 (2^40 pixel pairs):
+    sampled outputs against the oracle's one-at-a-time transform (bit-exact
+    round-down for p = 2, where every cost is exact in FP32)."""
     rng = np.random.default_rng(40 + int(p))
     h = (rng.standard_normal(N * N) * 3.0 * N).astype(np.float32).astype(np.float64)
     g = api.ctransform(T(h), N, p, prec="mixed").cpu().numpy()
