@@ -341,6 +341,7 @@ def run_gpu(args):
         if not args.skip_workloads:
             out["uneven_200"] = _uneven_workload(api, dev, args)
             out["differentiable_256"] = _differentiable_workload(api, dev, args)
+            out["ipf_hbm"] = _ipf_hbm_workload(api, dev, args)
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args.cpu_seconds, args.cpu_workers)
     batch.close()
@@ -404,6 +405,57 @@ def _uneven_workload(api, dev, args):
                 "what": "device passes (SumPool, C-bar, IPF 50 sweeps + upper bound, c-transforms + "
                         "lower bound) of one batch of 200 uneven pairs; host exact solves separate",
                 "autotune": bt.tuning()}
+
+
+def _ipf_hbm_workload(api, dev, args):
+    """The IPF sweeps on a working set larger than L2: 45 pairs of 512 x 512
+    (kappa 8, 64 x 64 coarse), 50 sweeps, 4.2 MB per pair and sweep (189 MB
+    per sweep > the 129 MB L2).  Only the primal pass runs (C-bar and the dual
+    pass off)."""
+    import torch
+    from paper_2506_00976_gb300 import synth
+    Nh, kh, sweeps = 512, 8, SWEEPS
+    pairs = []
+    for ci, cls in enumerate(CLASSES):
+        pairs += synth.class_pairs(Nh, cls, 6, count=6)[:12]
+    pairs = pairs[:45]
+    mus = [torch.tensor(a, dtype=torch.float64, device=dev) for a, _ in pairs]
+    nus = [torch.tensor(b, dtype=torch.float64, device=dev) for _, b in pairs]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    with api.Batch([(Nh, kh, 2.0)] * len(pairs), ipf_sweeps=sweeps, prec="mixed", flags=1 | 4,
+                   device=dev) as bt:
+        bt.coarse(mus, nus, batched=True)
+        t0 = time.perf_counter()
+        bt.solve(threads=args.threads)
+        solve_s = time.perf_counter() - t0
+
+        def step():
+            bt.fine(mus, nus, batched=True)
+        ms = _event_ms(step, 3, 3, flush)
+        kern = bt.kernel_times()
+        res = bt.results()
+        assert all(r["status"] == 0 for r in res)
+        tuning = bt.tuning()
+    m = Nh * Nh
+    nbytes = 16.0 * m * sweeps * len(pairs)
+    ipf_ms = kern.get("ipf_cluster", 0.0)
+    sweep_ms = ipf_ms if ipf_ms > 0 else kern.get("primal", ms)
+    hbm = 6792.1
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            hbm = float(json.load(fh).get("hbm_gbs") or hbm)
+    except (OSError, ValueError):
+        pass
+    return {"bound": "hbm", "pairs": len(pairs), "N": Nh, "kappa": kh, "sweeps": sweeps,
+            "bytes_per_sweep": 16.0 * m * len(pairs), "algorithmic_bytes": nbytes,
+            "sweeps_ms": round(sweep_ms, 4), "primal_pass_ms": round(kern.get("primal", 0.0), 4),
+            "achieved_gbs": round(nbytes / (sweep_ms * 1e-3) / 1e9, 1) if sweep_ms > 0 else None,
+            "peak_gbs": hbm,
+            "frac_of_hbm": round(nbytes / (sweep_ms * 1e-3) / 1e9 / hbm, 4) if sweep_ms > 0 else None,
+            "ipf_cluster": tuning.get("ipf"), "host_solve_s": round(solve_s, 3),
+            "what": "fine IPF sweeps (16 B per pixel and sweep: read mu, write a, read nu, write b) on a "
+                    "working set larger than L2; sweeps_ms is the cluster sweep kernel, or the whole "
+                    "primal kernel when the sweeps run inside it"}
 
 
 def _differentiable_workload(api, dev, args):
@@ -536,6 +588,8 @@ def main():
                     help="pairs per value class (45 = the full workload; smaller for profiling)")
     ap.add_argument("--skip-plain", action="store_true", help="time only the batched form")
     ap.add_argument("--skip-e2e", action="store_true", help="skip the end-to-end timing")
+    ap.add_argument("--only", default="", choices=["", "ipf_hbm", "uneven_200", "differentiable_256"],
+                    help="run one secondary workload alone and print its JSON (profiling)")
     ap.add_argument("--skip-workloads", action="store_true",
                     help="skip the uneven 200-pair and differentiable 256x256 measurements")
     ap.add_argument("--skip-separable", action="store_true",
@@ -543,6 +597,15 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "native":
         args.warmup = 3
+    if args.only:
+        import torch
+        from paper_2506_00976_gb300 import api
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        fn = {"ipf_hbm": _ipf_hbm_workload, "uneven_200": _uneven_workload,
+              "differentiable_256": _differentiable_workload}[args.only]
+        print(json.dumps({args.only: fn(api, dev, args)}), flush=True)
+        return
     out = run_reference(args) if args.impl == "reference" else run_gpu(args)
     if out is not None:
         print(json.dumps(out), flush=True)

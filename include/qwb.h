@@ -309,6 +309,16 @@ int qwb_batch_fine(qwb_batch* batch, const double* const* mu_d, const double* co
                    int32_t batched, void* stream);
 int qwb_batch_results(qwb_batch* batch, qwb_result* out_h, void* stream);
 int qwb_batch_potentials(qwb_batch* batch, int32_t pair, double* f_d, double* g_d, void* stream);
+/* Where the fine FP32 IPF sweeps of the batch's 2-D FP32 pairs with block side
+ * 4 or 8 run (Sec. 3.4, IPF paragraph; Alg. 4; the values do not depend on
+ * it): C = 0 inside the primal-pass kernel, one CTA per pair; C = 2, 4, 8, 16
+ * on a thread-block cluster of (at most) C CTAs per pair that split the coarse
+ * blocks and exchange block sums through distributed shared memory -- the
+ * form that keeps HBM busy for large grids.  Each group of pairs with one
+ * block side takes the largest power of two <= C dividing all its coarse
+ * sides.  Overrides the autotuner's choice; synchronises the device and drops
+ * the batch's captured fine-pass graphs.  Errors: INVALID_ARG, CUDA. */
+int qwb_batch_set_ipf_cluster(qwb_batch* batch, int32_t C);
 /* Pair t's scalings after the fine IPF sweeps of the last qwb_batch_fine
  * (Sec. 3.4, IPF paragraph; Alg. 4): the pass-type a, b with
  * a = mu / (pi-hat b), b = nu / (pi-hat^T a) after ipf_sweeps sweeps from
@@ -318,8 +328,10 @@ int qwb_batch_potentials(qwb_batch* batch, int32_t pair, double* f_d, double* g_
 int qwb_batch_fine_scalings(qwb_batch* batch, int32_t pair, double* a_d, double* b_d, void* stream);
 /* Device time (ms) of each kernel of the last batched passes, in the order
  * SumPool, C-bar, primal (IPF + upper bound), centre, upsample,
- * c-transform f-hat -> g, c-transform g -> f, lower-bound sum; -1 where not
- * measured.  Fills min(n, 8) values; call after the stream has completed. */
+ * c-transform f-hat -> g, c-transform g -> f, lower-bound sum, then the two
+ * parts of the primal pass: the cluster IPF sweeps (0 when the sweeps run
+ * inside the primal kernel) and the primal kernel; -1 where not measured.
+ * Fills min(n, 10) values; call after the stream has completed. */
 int qwb_batch_kernel_times(qwb_batch* batch, double* ms_out, int32_t n);
 /* Launch configurations the autotuner chose for this batch and the device
  * time of every candidate it measured, as a NUL-terminated JSON object

@@ -220,12 +220,12 @@ class Batch:
         return [r.as_dict() for r in res]
 
     KERNELS = ("sumpool", "cbar", "primal", "centre", "upsample", "ctransform_g",
-               "ctransform_f", "lbsum")
+               "ctransform_f", "lbsum", "ipf_cluster", "primal_kernel")
 
     def kernel_times(self):
         """Device ms of each kernel of the last batched passes (after a sync)."""
-        out = (ctypes.c_double * 8)()
-        check(_lib.load().qwb_batch_kernel_times(self._h, out, 8), "qwb_batch_kernel_times")
+        out = (ctypes.c_double * 10)()
+        check(_lib.load().qwb_batch_kernel_times(self._h, out, 10), "qwb_batch_kernel_times")
         return dict(zip(self.KERNELS, list(out)))
 
     def tuning(self):
@@ -242,6 +242,10 @@ class Batch:
         check(_lib.load().qwb_batch_potentials(self._h, int(t), _ptr(f), _ptr(g), self._stream()),
               "qwb_batch_potentials")
         return f, g
+
+    def set_ipf_cluster(self, C):
+        """Run the fine IPF sweeps inside the primal kernel (0) or on clusters of C CTAs."""
+        check(_lib.load().qwb_batch_set_ipf_cluster(self._h, int(C)), "qwb_batch_set_ipf_cluster")
 
     def fine_scalings(self, t):
         """Pair t's fine IPF scalings a, b (pass type widened to FP64)."""

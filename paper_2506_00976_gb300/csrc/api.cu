@@ -76,9 +76,9 @@ struct CostTable {
 // Launch configuration chosen by the autotuner for one problem signature.
 struct TuneEntry {
     std::string key;
-    int R = 0, TC = 0, packed = 0, cbar_variant = 2, cbar8_variant = 4;
-    bool ct_done = false, cbar_done = false;
-    std::string ct_report, cbar_report;   // JSON fragments: candidate -> ms
+    int R = 0, TC = 0, packed = 0, cbar_variant = 2, cbar8_variant = 4, ipf_C = 0;
+    bool ct_done = false, cbar_done = false, ipf_done = false;
+    std::string ct_report, cbar_report, ipf_report;   // JSON fragments: candidate -> ms
 };
 
 struct qwb_ctx {
@@ -99,10 +99,15 @@ static void tune_cache_load(qwb_ctx* c) {
     while (std::getline(in, line)) {
         std::istringstream ls(line);
         TuneEntry e;
-        std::string r, tc, pk, cv;
+        std::string r, tc, pk, cv, ipf;
         if (!std::getline(ls, e.key, '|') || !std::getline(ls, r, '|') || !std::getline(ls, tc, '|') ||
             !std::getline(ls, pk, '|') || !std::getline(ls, cv, '|'))
             continue;
+        if (std::getline(ls, ipf, '|') && !ipf.empty()) {       // optional: fine-IPF cluster size
+            e.ipf_C = std::atoi(ipf.c_str());
+            e.ipf_done = true;
+            e.ipf_report = "\"cached\"";
+        }
         e.R = std::atoi(r.c_str()); e.TC = std::atoi(tc.c_str());
         e.packed = std::atoi(pk.c_str()); e.cbar_variant = std::atoi(cv.c_str());
         const size_t slash = cv.find('/');                      // "kappa4 variant/kappa8 variant"
@@ -118,8 +123,12 @@ static void tune_cache_store(qwb_ctx* c) {
     std::ofstream out(c->tune_cache, std::ios::trunc);
     for (auto& e : c->tunes)
         if (e.ct_done && e.cbar_done)
+        {
             out << e.key << '|' << e.R << '|' << e.TC << '|' << e.packed << '|' << e.cbar_variant << '/'
-                << e.cbar8_variant << "|\n";
+                << e.cbar8_variant << '|';
+            if (e.ipf_done) out << e.ipf_C;
+            out << "|\n";
+        }
 }
 
 static int ctx_table(qwb_ctx* c, int N, double p, bool f64, cudaStream_t s, const void** lo,
@@ -180,6 +189,15 @@ struct qwb_batch {
     int n_cb8 = 0, n_max8 = 0, N_max8 = 0;
     int cbar8_variant = 4;
     std::vector<char> cbar_group;       // per pair: 4, 8 or 0
+    // fine IPF sweeps on thread-block clusters (ipf_fine_kernel): 2-D FP32
+    // pairs grouped by kappa (4, 8); ipf_C is the requested cluster size
+    // (0: every pair sweeps inside primal_kernel), each group runs with the
+    // largest power of two <= ipf_C that divides all its coarse sides
+    struct IpfGroup { int kappa, off, cnt, M_max, gcd_n, C; };
+    std::vector<IpfGroup> ipf_groups;
+    std::vector<int> ipf_group_of;      // per pair: its group or -1
+    int* ipf_ids_d = nullptr;
+    int ipf_C = 0;
     std::vector<int> prep_off, prep_cnt, pix_off, pix_cnt, cbar_off, cbar_cnt, ct_off, ct_cnt;
     int n_prep = 0, n_pix = 0, n_cbar = 0, n_ct_b = 0;
     int n_ct_b_p2 = 0;   // batched c-transform items: the p = 2 pairs' items come first
@@ -200,7 +218,7 @@ struct qwb_batch {
     bool solved = false;
     double t_solve_ms = 0.0;
     cudaEvent_t ev[6] = {};
-    cudaEvent_t kev[10] = {};   // per-kernel boundaries of the batched passes
+    cudaEvent_t kev[11] = {};   // per-kernel boundaries of the batched passes
     bool ev_ok = false;
     std::vector<const double*> cur_mu, cur_nu;
     std::vector<GraphEntry> graphs;
@@ -257,6 +275,24 @@ static void stage_typed_values(char* ph, const PlanLayout& L, int nnz, bool f64)
         float* vct = (float*)(ph + L.valc_t);
         for (int e = 0; e < nnz; ++e) { vt[e] = (float)v[e]; vct[e] = (float)vc[e]; }
     }
+}
+
+// Cluster size of the fine IPF sweeps: every group takes the largest power of
+// two <= C that divides its coarse sides (below 2: sweeps inside
+// primal_kernel); the descriptors' fine_ext flags are re-uploaded.
+static int apply_ipf_choice(qwb_batch* b, int C) {
+    b->ipf_C = C;
+    for (auto& G : b->ipf_groups) {
+        int c = 1;
+        while (c * 2 <= C && c * 2 <= 16 && G.gcd_n % (c * 2) == 0) c *= 2;
+        G.C = c >= 2 ? c : 0;
+    }
+    for (int t = 0; t < b->n; ++t) {
+        const int g = b->ipf_group_of[t];
+        b->pairs_h[t].fine_ext = (g >= 0 && b->ipf_groups[g].C > 0) ? 1 : 0;
+    }
+    QWB_CUDA(cudaMemcpy(b->pairs_d, b->pairs_h.data(), sizeof(PairDev) * b->n, cudaMemcpyHostToDevice));
+    return QWB_OK;
 }
 
 static CtConfig pick_ct_config(int N_gcd, bool all_p2) {
@@ -455,7 +491,26 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
     const size_t o_ctp = align_up(o_ctb + sizeof(CtItem) * ctb.size());
     const size_t o_sep = align_up(o_ctp + sizeof(CtItem) * ctp.size());
     const size_t o_cb3 = align_up(o_sep + sizeof(SepItem) * sep.size());
-    const size_t total = align_up(o_cb3 + sizeof(PixItem) * cb3.size());
+    b->ipf_group_of.assign(n, -1);
+    std::vector<int> ipf_ids;
+    if (!b->f64)
+        for (int kap : {4, 8}) {
+            qwb_batch::IpfGroup G{kap, (int)ipf_ids.size(), 0, 0, 0, 0};
+            for (int t = 0; t < n; ++t) {
+                if (dim_of(probs[t]) != 2 || probs[t].kappa != kap) continue;
+                const int nn = probs[t].N / kap;
+                int x = G.gcd_n, y = nn;
+                while (y) { const int r = x % y; x = y; y = r; }
+                G.gcd_n = x;
+                G.M_max = std::max(G.M_max, nn * nn);
+                b->ipf_group_of[t] = (int)b->ipf_groups.size();
+                ipf_ids.push_back(t);
+                ++G.cnt;
+            }
+            if (G.cnt) b->ipf_groups.push_back(G);
+        }
+    const size_t o_ipf = align_up(o_cb3 + sizeof(PixItem) * cb3.size());
+    const size_t total = align_up(o_ipf + sizeof(int) * std::max<size_t>(1, ipf_ids.size()));
     if (cudaMalloc(&b->dmem, total) != cudaSuccess) { batch_free(b); return fail(QWB_ERR_OOM, "batch workspace"); }
     b->pairs_d = (PairDev*)(b->dmem + o_pairs);
     b->outs_d = (PairOut*)(b->dmem + o_outs);
@@ -467,6 +522,7 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
     b->ct_p_items_d = (CtItem*)(b->dmem + o_ctp);
     b->sep_items_d = (SepItem*)(b->dmem + o_sep);
     b->cbar3_items_d = (PixItem*)(b->dmem + o_cb3);
+    b->ipf_ids_d = (int*)(b->dmem + o_ipf);
     // coarse-plan staging
     size_t poff = 0;
     for (int t = 0; t < n; ++t) { b->plan_off.push_back(poff); poff += plan_layout(b->Ms[t]).total; }
@@ -547,6 +603,8 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
     if (!st) st = up(b->cbar3_items_d, cb3.data(), sizeof(PixItem) * cb3.size());
     if (!st) st = up(b->ct_b_items_d, ctb.data(), sizeof(CtItem) * ctb.size());
     if (!st) st = up(b->ct_p_items_d, ctp.data(), sizeof(CtItem) * ctp.size());
+    if (!st) st = up(b->ipf_ids_d, ipf_ids.data(), sizeof(int) * ipf_ids.size());
+    if (!st && b->tune && b->tune->ipf_done) st = apply_ipf_choice(b, b->tune->ipf_C);
     if (!st) {
         b->ev_ok = true;
         for (auto& e : b->ev)
@@ -648,6 +706,12 @@ static int enqueue_fine(qwb_batch* b, bool batched, cudaStream_t s) {
     const bool do_primal = !(b->flags & QWB_FLAG_NO_PRIMAL), do_dual = !(b->flags & QWB_FLAG_NO_DUAL);
     if (batched) {
         if ((st = mark(b, 3, s))) return st;
+        if (do_primal)
+            for (const auto& G : b->ipf_groups)
+                if (G.C > 0 && (st = launch_ipf_fine(b->pairs_d, b->ipf_ids_d + G.off, G.cnt, G.kappa, G.C,
+                                                     G.M_max, 0, s)))
+                    return st;
+        if ((st = mark(b, 10, s))) return st;
         if (do_primal && (st = launch_primal(b->pairs_d, b->outs_d, b->pair_ids_d, b->n, b->M_max, 0, b->f64, s))) return st;
         if ((st = mark(b, 4, s))) return st;
         const int cap = sm;       // persistent grid: all resident CTAs walk the item list
@@ -684,6 +748,10 @@ static int enqueue_fine(qwb_batch* b, bool batched, cudaStream_t s) {
     for (int t = 0; t < b->n; ++t) {
         const int* id = b->pair_ids_d + t;
         const int M = b->Ms[t];
+        if (do_primal && b->ipf_group_of[t] >= 0 && b->ipf_groups[b->ipf_group_of[t]].C > 0) {
+            const auto& G = b->ipf_groups[b->ipf_group_of[t]];
+            if ((st = launch_ipf_fine(b->pairs_d, id, 1, G.kappa, G.C, M, 0, s))) return st;
+        }
         if (do_primal && (st = launch_primal(b->pairs_d, b->outs_d, id, 1, M, 0, b->f64, s))) return st;
         if (!do_dual) continue;
         if ((st = launch_centre(b->pairs_d, b->outs_d, id, 1, s))) return st;
@@ -818,6 +886,48 @@ static int tune_ctransform(qwb_batch* b, cudaStream_t s) {
     return QWB_OK;
 }
 
+// Fine IPF: sweeps inside primal_kernel (C = 0) or on clusters of 2, 4, 8
+// CTAs per pair, timed as the whole primal pass.
+static int tune_ipf(qwb_batch* b, cudaStream_t s) {
+    TuneEntry* e = b->tune;
+    if (!b->ctx->autotune || !e || e->ipf_done || !b->ev_ok || (b->flags & QWB_FLAG_NO_PRIMAL) ||
+        b->ipf_groups.empty())
+        return QWB_OK;
+    std::ostringstream rep;
+    rep << "{";
+    double best = 1e30;
+    int bestC = 0;
+    for (int C : {0, 2, 4, 8, 16}) {
+        int st = apply_ipf_choice(b, C);
+        if (st) return st;
+        if (C > 0) {
+            bool any = false;
+            for (const auto& G : b->ipf_groups) any |= G.C == C;
+            if (!any) continue;                  // no group takes this size
+        }
+        double ms;
+        st = time_variant(s, b->ev[0], b->ev[1], [&] {
+            int st2;
+            for (const auto& G : b->ipf_groups)
+                if (G.C > 0 && (st2 = launch_ipf_fine(b->pairs_d, b->ipf_ids_d + G.off, G.cnt, G.kappa, G.C,
+                                                      G.M_max, 0, s)))
+                    return st2;
+            return launch_primal(b->pairs_d, b->outs_d, b->pair_ids_d, b->n, b->M_max, 0, b->f64, s);
+        }, &ms);
+        if (st) return st;
+        rep << (C ? ", " : "") << "\"cluster" << C << "\": " << ms;
+        if (ms < best) { best = ms; bestC = C; }
+    }
+    rep << "}";
+    const int st = apply_ipf_choice(b, bestC);
+    if (st) return st;
+    e->ipf_C = bestC;
+    e->ipf_report = rep.str();
+    e->ipf_done = true;
+    tune_cache_store(b->ctx);
+    return QWB_OK;
+}
+
 // Run a pass for the whole batch, through a captured CUDA graph when batched.
 static int run_pass(qwb_batch* b, int kind, bool batched, cudaStream_t s) {
     if (!batched) return kind == 0 ? enqueue_coarse(b, false, s) : enqueue_fine(b, false, s);
@@ -829,7 +939,8 @@ static int run_pass(qwb_batch* b, int kind, bool batched, cudaStream_t s) {
         }
     // tune this pass's kernels on the batch's data before the first capture
     {
-        const int st_t = kind == 0 ? tune_cbar(b, s) : tune_ctransform(b, s);
+        int st_t = kind == 0 ? tune_cbar(b, s) : tune_ctransform(b, s);
+        if (!st_t && kind == 1) st_t = tune_ipf(b, s);
         if (st_t) return st_t;
     }
     // capture on a private stream, then launch on the caller's stream
@@ -1233,8 +1344,8 @@ int qwb_batch_results(qwb_batch* b, qwb_result* out_h, void* stream) {
 int qwb_batch_kernel_times(qwb_batch* b, double* ms_out, int32_t n) {
     if (!b || !ms_out || n < 0) return fail(QWB_ERR_INVALID_ARG, "qwb_batch_kernel_times: bad argument");
     if (!b->ev_ok) return fail(QWB_ERR_CUDA, "no timing events");
-    const int pairs[8][2] = {{0, 1}, {1, 2}, {3, 4}, {4, 5}, {5, 6}, {6, 7}, {7, 8}, {8, 9}};
-    for (int i = 0; i < n && i < 8; ++i) {
+    const int pairs[10][2] = {{0, 1}, {1, 2}, {3, 4}, {4, 5}, {5, 6}, {6, 7}, {7, 8}, {8, 9}, {3, 10}, {10, 4}};
+    for (int i = 0; i < n && i < 10; ++i) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, b->kev[pairs[i][0]], b->kev[pairs[i][1]]) != cudaSuccess) {
             cudaGetLastError();
@@ -1253,6 +1364,8 @@ int qwb_batch_tuning(qwb_batch* b, char* json_out, int32_t capacity) {
       << ", \"candidates_ms\": " << (b->tune && !b->tune->ct_report.empty() ? b->tune->ct_report : "{}")
       << "}, \"cbar\": {\"variant\": \"" << cbar_variant_name(b->cbar_variant) << "\""
       << ", \"candidates_ms\": " << (b->tune && !b->tune->cbar_report.empty() ? b->tune->cbar_report : "{}")
+      << "}, \"ipf\": {\"cluster\": " << b->ipf_C
+      << ", \"candidates_ms\": " << (b->tune && !b->tune->ipf_report.empty() ? b->tune->ipf_report : "{}")
       << "}, \"enabled\": " << (b->ctx->autotune ? "true" : "false") << "}";
     const std::string str = o.str();
     if ((int)str.size() + 1 > capacity) return fail(QWB_ERR_INVALID_ARG, "qwb_batch_tuning: buffer too small");
@@ -1276,6 +1389,22 @@ int qwb_batch_potentials(qwb_batch* b, int32_t pair, double* f_d, double* g_d, v
     if (f_d && (st = launch_from_work(P.f, f_d, m, b->f64, s))) return st;
     if (g_d && (st = launch_from_work(P.g, g_d, m, b->f64, s))) return st;
     return QWB_OK;
+}
+
+int qwb_batch_set_ipf_cluster(qwb_batch* b, int32_t C) {
+    if (!b || (C != 0 && C != 2 && C != 4 && C != 8 && C != 16))
+        return fail(QWB_ERR_INVALID_ARG, "qwb_batch_set_ipf_cluster: C must be 0, 2, 4, 8 or 16");
+    QWB_CUDA(cudaSetDevice(b->ctx->device));
+    QWB_CUDA(cudaDeviceSynchronize());
+    // captured fine passes hold the previous launch configuration
+    std::vector<GraphEntry> keep;
+    for (auto& g : b->graphs) {
+        if (g.kind == 1) cudaGraphExecDestroy(g.exec);
+        else keep.push_back(g);
+    }
+    b->graphs.swap(keep);
+    if (b->tune) { b->tune->ipf_done = true; b->tune->ipf_C = C; b->tune->ipf_report = "\"set\""; }
+    return apply_ipf_choice(b, C);
 }
 
 int qwb_batch_fine_scalings(qwb_batch* b, int32_t pair, double* a_d, double* b_d, void* stream) {

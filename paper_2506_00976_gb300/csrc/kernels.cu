@@ -21,6 +21,8 @@
 #include "common.cuh"
 #include "kernels.h"
 
+#include <cooperative_groups.h>
+
 namespace qwb {
 
 // --------------------------------------------------------------------------
@@ -1041,7 +1043,8 @@ primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
     for (int l = threadIdx.x; l < M; l += blockDim.x) Bt[l] = kk;    // b = 1
     __syncthreads();
     const bool vec4 = (sizeof(T) == 4) && (kap == 4) && P.d == 2;  // block rows are one float4
-    for (int sweep = 0; sweep < P.sweeps; ++sweep) {
+    const int fine_sweeps = P.fine_ext ? 0 : P.sweeps;     // else done by ipf_fine_kernel
+    for (int sweep = 0; sweep < fine_sweeps; ++sweep) {
         for (int half = 0; half < 2; ++half) {
             // half 0: a = mu / (pi-hat b), A = block sums of a
             // half 1: b = nu / (pi-hat^T a), B = block sums of b
@@ -1257,6 +1260,197 @@ int launch_primal(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, 
         QWB_CUDA(cudaFuncSetAttribute(primal_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         primal_kernel<float><<<n_pairs, PRIMAL_THREADS, smem, stream>>>(pairs_d, outs_d, pair_ids, csr_cap);
     }
+    QWB_LAUNCHED();
+    return QWB_OK;
+}
+
+// --------------------------------------------------------------------------
+// ipf_fine: the fine FP32 IPF sweeps of the primal pass (Sec. 3.4, IPF
+// paragraph; Alg. 4), a = mu / (pi-hat b), b = nu / (pi-hat^T a), for large
+// 2-D pairs (block side kappa 4 or 8) on a thread-block cluster of C CTAs
+// per pair.  CTA `rank` owns the coarse blocks [rank M/C, (rank+1) M/C)
+// (n/C whole block rows, so its fine pixels are contiguous rows): it streams
+// their pixels, keeps their block sums in its shared memory and reads the
+// other CTAs' block sums through distributed shared memory for the coarse
+// products r = kappa^-4 pi~ B and s = kappa^-4 pi~^T A.  Each half sweep
+// publishes its block sums, arrives at the cluster barrier (release),
+// streams the scaled values to memory and prefetches the next half's first
+// source values while the barrier completes, then waits (acquire).  The same
+// arithmetic as the single-CTA sweeps of primal_kernel, which skips them for
+// these pairs (fine_ext): per block one FP32 reciprocal of r and a scaled
+// store of every fine value, block sums in FP32.  Every CTA of a cluster runs
+// the same number of half sweeps and arrives once per half sweep, so the
+// barrier cannot wait on a CTA that has left.
+// --------------------------------------------------------------------------
+constexpr int IPF_THREADS = 256;
+
+__device__ __forceinline__ void cluster_arrive_release() {
+    asm volatile("barrier.cluster.arrive.release;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire() {
+    asm volatile("barrier.cluster.wait.acquire;\n" ::: "memory");
+}
+
+template <int KAP>
+__global__ void __launch_bounds__(IPF_THREADS)
+ipf_fine_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair_ids, int C,
+                int csr_cap) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int rank = (int)cl.block_rank();
+    const PairDev& P = pairs[pair_ids[blockIdx.x / C]];
+    const int N = P.N, n = P.n, M = P.M;
+    const int Mc = M / C, k0 = rank * Mc;                    // owned blocks [k0, k0 + Mc)
+    float* Aown = reinterpret_cast<float*>(smem_raw);         // block sums of a (owned)
+    float* Bown = Aown + Mc;                                  // block sums of b (owned)
+    float* v_s = Bown + Mc;                                   // plan values: owned CSR rows
+    float* vc_s = v_s + csr_cap;                              //              owned CSC columns
+    int* ci_s = reinterpret_cast<int*>(vc_s + csr_cap);
+    int* ri_s = ci_s + csr_cap;
+    int* rp_s = ri_s + csr_cap;                               // Mc + 1, relative offsets
+    int* cp_s = rp_s + Mc + 1;
+    const int r_base = P.rowptr[k0], c_base = P.colptr[k0];
+    const int r_cnt = P.rowptr[k0 + Mc] - r_base, c_cnt = P.colptr[k0 + Mc] - c_base;
+    const bool staged = r_cnt <= csr_cap && c_cnt <= csr_cap;
+    const float* vt = reinterpret_cast<const float*>(P.val_t);
+    const float* vct = reinterpret_cast<const float*>(P.valc_t);
+    if (staged) {
+        for (int k = threadIdx.x; k <= Mc; k += blockDim.x) {
+            rp_s[k] = P.rowptr[k0 + k] - r_base;
+            cp_s[k] = P.colptr[k0 + k] - c_base;
+        }
+        for (int e = threadIdx.x; e < r_cnt; e += blockDim.x) { ci_s[e] = P.colidx[r_base + e]; v_s[e] = vt[r_base + e]; }
+        for (int e = threadIdx.x; e < c_cnt; e += blockDim.x) { ri_s[e] = P.rowidx[c_base + e]; vc_s[e] = vct[c_base + e]; }
+    }
+    constexpr int KK = KAP * KAP;
+    const float kinvK = 1.0f / (float)(KK * KK);              // kappa^-4, exact (a power of two)
+    for (int k = threadIdx.x; k < Mc; k += blockDim.x) Bown[k] = (float)KK;   // b = 1
+    const float* mu_t = reinterpret_cast<const float*>(P.mu_t);
+    const float* nu_t = reinterpret_cast<const float*>(P.nu_t);
+    float* a = reinterpret_cast<float*>(P.a);
+    float* bb = reinterpret_cast<float*>(P.b);
+    constexpr int Q = KAP / 4;                                // float4 per block row
+    constexpr int PF = KAP == 4 ? 4 : 1;                      // blocks per chunk and thread
+    const int chunk = PF * blockDim.x;
+    float4 x[PF][KAP][Q];
+    auto load_chunk = [&](const float* src, int kb) {
+#pragma unroll
+        for (int q = 0; q < PF; ++q) {
+            const int kl = kb + q * blockDim.x;
+            if (kl < Mc) {
+                const int k = k0 + kl;
+                const int k1 = k / n, k2 = k - (k / n) * n;
+#pragma unroll
+                for (int t1 = 0; t1 < KAP; ++t1)
+#pragma unroll
+                    for (int t2 = 0; t2 < Q; ++t2)
+                        x[q][t1][t2] = *reinterpret_cast<const float4*>(src + (size_t)(k1 * KAP + t1) * N +
+                                                                         k2 * KAP + 4 * t2);
+            }
+        }
+    };
+    if (P.sweeps > 0) load_chunk(mu_t, threadIdx.x);           // first half's first chunk
+    cl.sync();                                                  // staging and b = 1 visible
+    const int halves = 2 * P.sweeps;
+    for (int h = 0; h < halves; ++h) {
+        const int half = h & 1;
+        const float* src = half == 0 ? mu_t : nu_t;
+        float* dst = half == 0 ? a : bb;
+        float* mine = half == 0 ? Aown : Bown;
+        const float* other = half == 0 ? Bown : Aown;
+        bool arrived = false;
+        for (int kb = threadIdx.x; kb < Mc; kb += chunk) {
+            if (kb != (int)threadIdx.x) load_chunk(src, kb);   // later chunks (the first is prefetched)
+            float inv[PF];
+#pragma unroll
+            for (int q = 0; q < PF; ++q) {
+                const int kl = kb + q * blockDim.x;
+                inv[q] = 0.0f;
+                if (kl < Mc) {
+                    float r = 0.0f;
+                    const int* ptr = staged ? (half == 0 ? rp_s : cp_s) : (half == 0 ? P.rowptr : P.colptr);
+                    const int* idx = staged ? (half == 0 ? ci_s : ri_s) : (half == 0 ? P.colidx : P.rowidx);
+                    const float* val = staged ? (half == 0 ? v_s : vc_s) : (half == 0 ? vt : vct);
+                    const int row = staged ? kl : k0 + kl;
+                    for (int e = ptr[row]; e < ptr[row + 1]; ++e) {
+                        const int l = idx[e], owner = l / Mc;
+                        const float* peer = cl.map_shared_rank(other, owner);
+                        r += val[e] * peer[l - owner * Mc];
+                    }
+                    r *= kinvK;
+                    inv[q] = r > 0.0f ? 1.0f / r : 0.0f;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < PF; ++q) {
+                const int kl = kb + q * blockDim.x;
+                if (kl < Mc) {
+                    float s = 0.0f;
+#pragma unroll
+                    for (int t1 = 0; t1 < KAP; ++t1)
+#pragma unroll
+                        for (int t2 = 0; t2 < Q; ++t2) {
+                            float4& v = x[q][t1][t2];
+                            v.x *= inv[q]; v.y *= inv[q]; v.z *= inv[q]; v.w *= inv[q];
+                            s += (v.x + v.y) + (v.z + v.w);
+                        }
+                    mine[kl] = s;
+                }
+            }
+            if (kb + chunk >= Mc) { cluster_arrive_release(); arrived = true; }   // sums published
+#pragma unroll
+            for (int q = 0; q < PF; ++q) {
+                const int kl = kb + q * blockDim.x;
+                if (kl < Mc) {
+                    const int k = k0 + kl;
+                    const int k1 = k / n, k2 = k - (k / n) * n;
+#pragma unroll
+                    for (int t1 = 0; t1 < KAP; ++t1)
+#pragma unroll
+                        for (int t2 = 0; t2 < Q; ++t2)
+                            *reinterpret_cast<float4*>(dst + (size_t)(k1 * KAP + t1) * N + k2 * KAP + 4 * t2) =
+                                x[q][t1][t2];
+                }
+            }
+        }
+        if (!arrived) cluster_arrive_release();                 // threads without blocks
+        if (h + 1 < halves) load_chunk(half == 0 ? nu_t : mu_t, threadIdx.x);   // next half, first chunk
+        cluster_wait_acquire();
+    }
+}
+
+int launch_ipf_fine(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int kappa, int C,
+                    int M_max, int nnz_max, cudaStream_t stream) {
+    if (n_pairs <= 0) return QWB_OK;
+    if (C < 1 || C > 16 || (kappa != 4 && kappa != 8)) return QWB_ERR_UNSUPPORTED;
+    const int Mc = M_max / C;
+    // staged plan rows and columns of one CTA: a basic plan has at most 2M - 1
+    // entries, on average 2 per owned block; room for twice that (a CTA whose
+    // blocks hold more reads its part of the plan from global memory)
+    int csr_cap = std::max(nnz_max, 4 * Mc);
+    size_t smem = sizeof(float) * 2 * (size_t)Mc + 2 * (sizeof(float) + sizeof(int)) * (size_t)csr_cap +
+                  2 * sizeof(int) * (size_t)(Mc + 1);
+    if (smem > 100 * 1024) {
+        smem = sizeof(float) * 2 * (size_t)Mc + 2 * sizeof(int) * (size_t)(Mc + 1);
+        csr_cap = 0;
+    }
+    auto kern = kappa == 4 ? ipf_fine_kernel<4> : ipf_fine_kernel<8>;
+    QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (C > 8) QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(n_pairs * C));
+    cfg.blockDim = dim3(IPF_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    QWB_CUDA(cudaLaunchKernelEx(&cfg, kern, pairs_d, pair_ids, C, csr_cap));
     QWB_LAUNCHED();
     return QWB_OK;
 }

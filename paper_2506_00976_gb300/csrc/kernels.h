@@ -38,6 +38,7 @@ struct PairDev {
     const void* val_t; const void* valc_t;   // plan values in the pass type T
     int nnz;
     int sweeps;
+    int fine_ext;           // 1: the fine FP32 sweeps run in ipf_fine_kernel, not in primal_kernel
     void* a; void* b;       // N*N fine scalings work (T)
     double* a_out; double* b_out;   // optional FP64 outputs
     // dual pass
@@ -90,6 +91,10 @@ int launch_cbar(const PairDev* pairs_d, const CbarItem* items, int n_items, int 
                 int n_max, int N_max, bool f64, cudaStream_t stream, int variant = 0);
 int launch_primal(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs,
                   int M_max, int nnz_max, bool f64, cudaStream_t stream);
+// Fine FP32 IPF sweeps on clusters of C CTAs per pair (2-D, kappa 4 or 8,
+// FP32, C divides every pair's n); the pairs have fine_ext = 1.
+int launch_ipf_fine(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int kappa, int C,
+                    int M_max, int nnz_max, cudaStream_t stream);
 // side 0 upscales f~ (the dual pass of Alg. 5); side 1 upscales g~ (the
 // same pass started from the other coarse potential)
 int launch_upsample(const PairDev* pairs_d, PairOut* outs_d, const PixItem* items, int n_items,

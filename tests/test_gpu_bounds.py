@@ -214,13 +214,18 @@ def test_symmetric_dual(prec, batched):
 
 @pytest.mark.parametrize("sweeps", [1, 7, 50])
 @pytest.mark.parametrize("batched", [True, False])
-def test_fine_ipf_scalings(sweeps, batched):
-    """The fine FP32 IPF sweeps: from b = 1 the uniform kernel reaches its fixed point
+@pytest.mark.parametrize("cluster", [0, 2, 8, 16])
+def test_fine_ipf_scalings(sweeps, batched, cluster):
+    """The fine FP32 IPF sweeps (inside the primal kernel, or on clusters of up
+    to 2, 8 or 16 CTAs per pair): from b = 1 the uniform kernel reaches its fixed point
     a = kappa^2 mu / mu~, b = kappa^2 nu / nu~ after one sweep whatever the
     coarse plan (Sec. 3.4, IPF paragraph), and further sweeps stay there up to
     FP32 rounding.  The oracle's FP64 IPF on its own plan agrees."""
     cases = [(32, 4, 2.0, "gauss"), (64, 8, 2.0, "field"), (32, 2, 1.0, "white"),
              (48, 4, 1.0, "cauchy"), (64, 4, 2.0, "gauss")]
+    if cluster == 16:    # coarse sides divisible by 16, so both groups take 16 CTAs
+        cases = [(128, 8, 2.0, "gauss"), (64, 4, 1.0, "field"), (64, 2, 2.0, "white"),
+                 (128, 4, 2.0, "cauchy"), (64, 4, 2.0, "gauss")]
     mus, nus, probs = [], [], []
     for i, (N, kappa, p, cls) in enumerate(cases):
         mu, nu = synth.make_measure(N, cls, 40 + i, 0), synth.make_measure(N, cls, 40 + i, 1)
@@ -232,6 +237,7 @@ def test_fine_ipf_scalings(sweeps, batched):
         md, nd = [T(x) for x in mus], [T(x) for x in nus]
         b.coarse(md, nd, batched=batched)
         b.solve()
+        b.set_ipf_cluster(cluster)
         b.fine(md, nd, batched=batched)
         assert all(r["status"] == 0 for r in b.results())
         for t, (N, kappa, p) in enumerate(probs):
