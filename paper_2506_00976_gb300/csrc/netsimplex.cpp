@@ -497,11 +497,17 @@ int solve(int32_t n_src, int32_t n_dst, Cost cst, double maxc, const double* a, 
     for (int i = 0; i < n_src; ++i) { f_lo = std::min(f_lo, S.pot[i]); f_hi = std::max(f_hi, S.pot[i]); }
     const double shift = n_src > 0 ? 0.5 * (f_lo + f_hi) : 0.0;
     for (int i = 0; i < n_src; ++i) out.f[i] = S.pot[i] - shift;
-    for (int i = 0; i < n_src; ++i)
-        for (int j = 0; j < n_dst; ++j) out.g[j] = std::min(out.g[j], cst(i, j) - out.f[i]);
+    std::vector<double> crow(n_dst);
+    double* g = out.g.data();
     for (int i = 0; i < n_src; ++i) {
+        S.row_costs(i, crow.data());
+        const double fi = out.f[i];
+        for (int j = 0; j < n_dst; ++j) g[j] = std::min(g[j], crow[j] - fi);
+    }
+    for (int i = 0; i < n_src; ++i) {
+        S.row_costs(i, crow.data());
         double fi = std::numeric_limits<double>::infinity();
-        for (int j = 0; j < n_dst; ++j) fi = std::min(fi, cst(i, j) - out.g[j]);
+        for (int j = 0; j < n_dst; ++j) fi = std::min(fi, crow[j] - g[j]);
         out.f[i] = fi;
     }
     out.pivots = piv;
