@@ -342,6 +342,7 @@ def run_gpu(args):
             out["uneven_200"] = _uneven_workload(api, dev, args)
             out["differentiable_256"] = _differentiable_workload(api, dev, args)
             out["ipf_hbm"] = _ipf_hbm_workload(api, dev, args)
+            out["workload_64"] = _workload_64(api, dev, args)
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args.cpu_seconds, args.cpu_workers)
     batch.close()
@@ -405,6 +406,40 @@ def _uneven_workload(api, dev, args):
                 "what": "device passes (SumPool, C-bar, IPF 50 sweeps + upper bound, c-transforms + "
                         "lower bound) of one batch of 200 uneven pairs; host exact solves separate",
                 "autotune": bt.tuning()}
+
+
+def _workload_64(api, dev, args):
+    """45 pairs of each value class at 64 x 64 (kappa 4, 16 x 16 coarse) for
+    p = 1 and p = 2, one batch per p: pairs/s and per-pass device times."""
+    import torch
+    from paper_2506_00976_gb300 import synth
+    Nw, kw = 64, 4
+    raw = []
+    for cls in CLASSES:
+        raw += synth.class_pairs(Nw, cls, 1)
+    mus = [torch.tensor(a, dtype=torch.float64, device=dev) for a, _ in raw]
+    nus = [torch.tensor(b, dtype=torch.float64, device=dev) for _, b in raw]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    out = {}
+    for p in (1.0, 2.0):
+        with api.Batch([(Nw, kw, p)] * len(raw), ipf_sweeps=SWEEPS, prec="mixed", device=dev) as bt:
+            bt.coarse(mus, nus, batched=True)
+            t0 = time.perf_counter()
+            bt.solve(threads=args.threads)
+            solve_s = time.perf_counter() - t0
+
+            def step():
+                bt.coarse(mus, nus, batched=True)
+                bt.fine(mus, nus, batched=True)
+            ms = _event_ms(step, max(3, min(args.steps, 5)), 3, flush)
+            kern = {k: round(v, 4) for k, v in bt.kernel_times().items()}
+            assert all(r["status"] == 0 for r in bt.results())
+        out[f"p{int(p)}"] = {"value": round(len(raw) / (ms * 1e-3), 3), "unit": "pairs/s",
+                             "ms_per_step": round(ms, 4), "kernel_ms": kern,
+                             "host_solve_s": round(solve_s, 3)}
+    out["what"] = ("180 pairs (4 classes x 45) of 64x64, kappa 4, MIXED, 50 IPF sweeps, batched device "
+                   "passes; host exact solves separate")
+    return out
 
 
 def _ipf_hbm_workload(api, dev, args):
@@ -588,7 +623,8 @@ def main():
                     help="pairs per value class (45 = the full workload; smaller for profiling)")
     ap.add_argument("--skip-plain", action="store_true", help="time only the batched form")
     ap.add_argument("--skip-e2e", action="store_true", help="skip the end-to-end timing")
-    ap.add_argument("--only", default="", choices=["", "ipf_hbm", "uneven_200", "differentiable_256"],
+    ap.add_argument("--only", default="", choices=["", "ipf_hbm", "uneven_200", "differentiable_256",
+                                                   "workload_64"],
                     help="run one secondary workload alone and print its JSON (profiling)")
     ap.add_argument("--skip-workloads", action="store_true",
                     help="skip the uneven 200-pair and differentiable 256x256 measurements")
@@ -603,7 +639,7 @@ def main():
         dev = torch.device("cuda", 0)
         torch.cuda.set_device(dev)
         fn = {"ipf_hbm": _ipf_hbm_workload, "uneven_200": _uneven_workload,
-              "differentiable_256": _differentiable_workload}[args.only]
+              "differentiable_256": _differentiable_workload, "workload_64": _workload_64}[args.only]
         print(json.dumps({args.only: fn(api, dev, args)}), flush=True)
         return
     out = run_reference(args) if args.impl == "reference" else run_gpu(args)

@@ -56,19 +56,23 @@ def test_batched_equals_plain(p):
             assert a[k] == b[k], k
 
 
-def test_uneven_batch_matches_single_pairs():
-    """Pairs of different N, kappa and p in one batch: each result equals the
-    single-pair result, and every bound is valid against the exact LP."""
+@pytest.mark.parametrize("prec", ["mixed", "f64"])
+def test_uneven_batch_matches_single_pairs(prec):
+    """Pairs of different N, kappa and p in one batch (the C-bar kernels of
+    kappa 4, kappa 8 and other block sides in one pass; the c-transform's
+    p = 2 and table launches): each result equals the single-pair result, and
+    every bound is valid against the exact LP."""
     cases = [(16, 4, 2.0, "gauss"), (32, 8, 1.0, "cauchy"), (24, 4, 2.0, "field"),
-             (16, 2, 1.0, "white"), (32, 4, 2.0, "blobs3")]
+             (16, 2, 1.0, "white"), (32, 4, 2.0, "blobs3"), (16, 8, 2.0, "field"),
+             (48, 8, 1.5, "gauss")]
     mus, nus, probs, raw = [], [], [], []
     for t, (N, kappa, p, cls) in enumerate(cases):
         mu, nu = synth.make_measure(N, cls, 31, 2 * t), synth.make_measure(N, cls, 31, 2 * t + 1)
         raw.append((mu, nu))
         mus.append(T(mu)); nus.append(T(nu)); probs.append((N, kappa, p))
-    rb = api.bounds(mus, nus, probs, ipf_sweeps=5, prec="mixed", batched=True)
+    rb = api.bounds(mus, nus, probs, ipf_sweeps=5, prec=prec, batched=True)
     for t, (N, kappa, p, cls) in enumerate(cases):
-        rs = api.bounds([mus[t]], [nus[t]], [probs[t]], ipf_sweeps=5, prec="mixed", batched=False)[0]
+        rs = api.bounds([mus[t]], [nus[t]], [probs[t]], ipf_sweeps=5, prec=prec, batched=False)[0]
         for k in ("lb", "ub_weighted", "ub_primal"):
             assert rb[t][k] == rs[k], (t, k)
         if N <= 16:

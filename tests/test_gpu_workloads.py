@@ -229,3 +229,39 @@ def test_dual_pass_256_sampled():
     np.testing.assert_allclose(g[J], g_ref, rtol=0, atol=8 * np.spacing(np.float32(scale)))
     _row_checks(f, g, N, p, J[:6], 1e-6)
     _sum_check(f, g, mu, nu, r["lb_p"])
+
+
+@pytest.mark.parametrize("p", [1.0, 2.0])
+def test_workload_64_all_classes(p):
+    """45 pairs of each value class at 64 x 64, kappa 4 (coarse 16 x 16), MIXED:
+    every pair certified and ordered; the weighted bound (a unique LP value) of
+    one pair per class against the oracle within 1e-4; the primal and dual
+    passes of those pairs, fed the oracle's own coarse solution, within 1e-4
+    of the oracle's bounds."""
+    N, kappa = 64, 4
+    raw, probs = [], []
+    for cls in CLASSES:
+        for mu, nu in synth.class_pairs(N, cls, 1):
+            raw.append((mu, nu))
+            probs.append((N, kappa, p))
+    b, mus, nus, res = _run_batch(raw, probs)
+    for r in res:
+        _valid(r)
+    for c in range(len(CLASSES)):
+        t = 45 * c + 7 * c + 3
+        mu, nu = raw[t]
+        ref_w = O.ub_weighted(mu, nu, N, kappa, p)["ub_weighted"]
+        assert abs(res[t]["ub_weighted"] - ref_w) <= 1e-4 * ref_w, (t, res[t]["ub_weighted"], ref_w)
+        mt, nt = O.sumpool(mu, N, kappa), O.sumpool(nu, N, kappa)
+        plan, f_c, _, _ = O.exact_ot(O.coarse_cost_centre(N, kappa, p), mt, nt)
+        rows, cols = np.nonzero(plan)
+        rowptr = np.cumsum(np.bincount(rows + 1, minlength=plan.shape[0] + 1)).astype(np.int32)
+        rp = api.primal_upscale_ipf(mus[t], nus[t], N, kappa, p, rowptr, cols.astype(np.int32),
+                                    plan[rows, cols], sweeps=50, prec="mixed")
+        ref_p = O.ub_primal(mu, nu, N, kappa, p, plan_c=plan)
+        assert abs(rp["ub_primal"] - ref_p["ub_primal"]) <= 1e-4 * ref_p["ub_primal"], t
+        rd = api.dual_upscale_ctransform(mus[t], nus[t], N, kappa, p, f_c, prec="mixed")
+        ref_d = O.lb_dual(mu, nu, N, kappa, p, f_c=f_c)
+        assert abs(rd["lb"] - ref_d["lb"]) <= 1e-4 * ref_d["lb"] + 1e-6, t
+        assert rd["lb"] <= ref_w * (1 + 1e-12)
+    b.close()
