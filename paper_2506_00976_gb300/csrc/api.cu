@@ -71,6 +71,7 @@ struct CostTable {
     void* lo;
     void* hi;
     int d;
+    void* lo_refl;   // lo with reflected rows (line-paired c-transform)
 };
 
 // Launch configuration chosen by the autotuner for one problem signature.
@@ -132,17 +133,27 @@ static void tune_cache_store(qwb_ctx* c) {
 }
 
 static int ctx_table(qwb_ctx* c, int N, double p, bool f64, cudaStream_t s, const void** lo,
-                     const void** hi, int d = 2) {
+                     const void** hi, int d = 2, const void** lo_refl = nullptr) {
     for (auto& t : c->tables)
-        if (t.N == N && t.p == p && t.f64 == f64 && t.d == d) { *lo = t.lo; *hi = t.hi; return QWB_OK; }
-    CostTable t{N, p, f64, nullptr, nullptr, d};
+        if (t.N == N && t.p == p && t.f64 == f64 && t.d == d) {
+            *lo = t.lo; *hi = t.hi;
+            if (lo_refl) *lo_refl = t.lo_refl;
+            return QWB_OK;
+        }
+    CostTable t{N, p, f64, nullptr, nullptr, d, nullptr};
     const size_t bytes = (size_t)ipow(N, d) * (f64 ? 8 : 4);
     if (cudaMalloc(&t.lo, bytes) != cudaSuccess) return fail(QWB_ERR_OOM, "cost table allocation");
     if (cudaMalloc(&t.hi, bytes) != cudaSuccess) { cudaFree(t.lo); return fail(QWB_ERR_OOM, "cost table allocation"); }
+    if (cudaMalloc(&t.lo_refl, 2 * bytes) != cudaSuccess) {
+        cudaFree(t.lo); cudaFree(t.hi);
+        return fail(QWB_ERR_OOM, "cost table allocation");
+    }
     int st = d == 3 ? launch_cost_tables3(N, p, f64, t.lo, t.hi, s) : launch_cost_tables(N, p, f64, t.lo, t.hi, s);
-    if (st) return st;
+    if (!st) st = launch_reflect_table(N, d, f64, t.lo, t.lo_refl, s);
+    if (st) { cudaFree(t.lo); cudaFree(t.hi); cudaFree(t.lo_refl); return st; }
     c->tables.push_back(t);
     *lo = t.lo; *hi = t.hi;
+    if (lo_refl) *lo_refl = t.lo_refl;
     return QWB_OK;
 }
 
@@ -572,9 +583,10 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
             P.g_out = (double*)base; base += align_up(sizeof(double) * m);
         }
         const void *lo, *hi;
-        int st = ctx_table(ctx, N, probs[t].p, b->f64, s0, &lo, &hi, dd);
+        const void* lo_refl = nullptr;
+        int st = ctx_table(ctx, N, probs[t].p, b->f64, s0, &lo, &hi, dd, &lo_refl);
         if (st) { batch_free(b); return st; }
-        P.ctab_lo = lo; P.ctab_hi = hi;
+        P.ctab_lo = lo; P.ctab_hi = hi; P.ctab_lo_refl = lo_refl;
         const PlanLayout L = plan_layout(M);
         char* pd = b->plan_d + b->plan_off[t];
         P.rowptr = (int*)(pd + L.rowptr); P.colidx = (int*)(pd + L.col); P.val = (double*)(pd + L.val);
@@ -1274,7 +1286,7 @@ void qwb_ctx_destroy(qwb_ctx* ctx) {
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     for (auto* b : ctx->single_cache) batch_free(b);
-    for (auto& t : ctx->tables) { cudaFree(t.lo); cudaFree(t.hi); }
+    for (auto& t : ctx->tables) { cudaFree(t.lo); cudaFree(t.hi); cudaFree(t.lo_refl); }
     delete ctx;
 }
 

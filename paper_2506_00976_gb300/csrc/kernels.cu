@@ -66,6 +66,30 @@ int launch_cost_tables3(int N, double p, bool f64, void* lo, void* hi, cudaStrea
     return QWB_OK;
 }
 
+// Reflected rows of a lower-bracket table: refl[r * 2N + c + N - 1] = lo[r * N + |c|]
+// for |c| < N (the last entry of each row repeats the first one's neighbour
+// and is never read).  rows = N (2-D) or N^2 (3-D).
+template <typename T>
+__global__ void reflect_table_kernel(int N, long rows, const T* lo, T* refl) {
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * 2 * N) return;
+    const long r = idx / (2 * N);
+    const int cc = (int)(idx - r * 2 * N);
+    const int c = min(abs(cc - (N - 1)), N - 1);
+    refl[idx] = lo[r * N + c];
+}
+
+int launch_reflect_table(int N, int d, bool f64, const void* lo, void* refl, cudaStream_t stream) {
+    const long rows = d == 3 ? (long)N * N : N;
+    const long n = rows * 2 * N;
+    const int th = 256;
+    const unsigned bl = (unsigned)((n + th - 1) / th);
+    if (f64) reflect_table_kernel<double><<<bl, th, 0, stream>>>(N, rows, (const double*)lo, (double*)refl);
+    else reflect_table_kernel<float><<<bl, th, 0, stream>>>(N, rows, (const float*)lo, (float*)refl);
+    QWB_LAUNCHED();
+    return QWB_OK;
+}
+
 int launch_cost_tables(int N, double p, bool f64, void* lo, void* hi, cudaStream_t stream) {
     const int n = N * N, th = 256, bl = (n + th - 1) / th;
     if (f64) cost_table_kernel<double><<<bl, th, 0, stream>>>(N, p, (double*)lo, (double*)hi);
@@ -1745,7 +1769,7 @@ ctransform_rp_kernel(const PairDev* __restrict__ pairs, const CtItem* __restrict
             hs2[k] = make_float2(lo, hi);
         }
         __syncthreads();
-        const float* tab = reinterpret_cast<const float*>(P.ctab_lo);
+        const float* refl = reinterpret_cast<const float*>(P.ctab_lo_refl);
         const int o_end = min(I.out0 + CT_TILE, m);
         const int last = I.in_row0 + I.in_rows - 1;
         for (int o = I.out0 + threadIdx.x * R; o < o_end; o += blockDim.x * R) {
@@ -1770,6 +1794,7 @@ ctransform_rp_kernel(const PairDev* __restrict__ pairs, const CtItem* __restrict
                     unsigned long long AA = 0ull;
                     const float* t0 = nullptr;
                     const float* t1 = nullptr;
+                    float tq0[P2 ? 1 : ((NQ + 3) / 4) * 4], tq1[P2 ? 1 : ((NQ + 3) / 4) * 4];
                     if constexpr (P2) {
                         float A1, A2;
                         if constexpr (D3) {
@@ -1783,22 +1808,35 @@ ctransform_rp_kernel(const PairDev* __restrict__ pairs, const CtItem* __restrict
                         }
                         AA = pack2(A1, A2);
                     } else {
+                        // reflected table rows: row[c + N - 1] = table[|c|]; the
+                        // chunk's costs are NQ consecutive entries from an
+                        // offset that is a multiple of 8 floats
+                        size_t r0, r1;
                         if constexpr (D3) {
                             const int ia = i1 / N, ib = i1 - (i1 / N) * N;
                             const int ia2 = i1b / N, ib2 = i1b - (i1b / N) * N;
-                            t0 = tab + ((size_t)abs(ia - ja) * N + abs(ib - jb)) * N;
-                            t1 = tab + ((size_t)abs(ia2 - ja) * N + abs(ib2 - jb)) * N;
+                            r0 = (size_t)abs(ia - ja) * N + abs(ib - jb);
+                            r1 = (size_t)abs(ia2 - ja) * N + abs(ib2 - jb);
                         } else {
-                            t0 = tab + (size_t)abs(i1 - ja) * N;
-                            t1 = tab + (size_t)abs(i1b - ja) * N;
+                            r0 = (size_t)abs(i1 - ja);
+                            r1 = (size_t)abs(i1b - ja);
+                        }
+                        const int off = c0 - j2 - (R - 1) + N - 1;
+                        t0 = refl + r0 * (2 * N) + off;
+                        t1 = refl + r1 * (2 * N) + off;
+#pragma unroll
+                        for (int q = 0; q < (NQ + 3) / 4; ++q) {
+                            const float4 u = reinterpret_cast<const float4*>(t0)[q];
+                            const float4 w = reinterpret_cast<const float4*>(t1)[q];
+                            tq0[4 * q] = u.x; tq0[4 * q + 1] = u.y; tq0[4 * q + 2] = u.z; tq0[4 * q + 3] = u.w;
+                            tq1[4 * q] = w.x; tq1[4 * q + 1] = w.y; tq1[4 * q + 2] = w.z; tq1[4 * q + 3] = w.w;
                         }
                     }
                     auto cost = [&](int e) -> unsigned long long {
                         if constexpr (P2) {
                             return add_rn_x2(AA, DD[e]);            // exact integers
                         } else {
-                            const int a = abs(c0 - j2 + e - (R - 1));
-                            return pack2(t0[a], t1[a]);
+                            return pack2(tq0[e], tq1[e]);
                         }
                     };
                     // window of costs for column s: e = s - r + R - 1, r = R-1 .. 0

@@ -32,6 +32,7 @@ struct PairDev {
     double* cbar;           // M*M coarse cost out (may be null)
     const void* ctab_lo;    // N*N cost table, lower brackets (T)
     const void* ctab_hi;    // N*N cost table, upper brackets (T)
+    const void* ctab_lo_refl;  // lower brackets, rows reflected: [rows][2N], entry c + N - 1 = |c|
     // coarse plan (CSR and CSC) for the primal pass
     const int* rowptr; const int* colidx; const double* val;
     const int* colptr; const int* rowidx; const double* valc;
@@ -84,6 +85,7 @@ int launch_cost_tables3(int N, double p, bool f64, void* lo, void* hi, cudaStrea
 int launch_cbar3(const PairDev* pairs_d, const PixItem* items, int n_items, bool f64,
                  cudaStream_t stream);
 int launch_cost_tables(int N, double p, bool f64, void* lo, void* hi, cudaStream_t stream);
+int launch_reflect_table(int N, int d, bool f64, const void* lo, void* refl, cudaStream_t stream);
 int launch_prepare(const PairDev* pairs_d, PairOut* outs_d, const PixItem* items, int n_items,
                    bool f64, cudaStream_t stream);
 constexpr int CBAR_S = 4;   // block rows per C-bar work item
