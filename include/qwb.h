@@ -330,7 +330,8 @@ int qwb_batch_fine_scalings(qwb_batch* batch, int32_t pair, double* a_d, double*
  * SumPool, C-bar, primal (IPF + upper bound), centre, upsample,
  * c-transform f-hat -> g, c-transform g -> f, lower-bound sum, then the two
  * parts of the primal pass: the cluster IPF sweeps (0 when the sweeps run
- * inside the primal kernel) and the primal kernel; -1 where not measured.
+ * inside the primal kernel) and the rest (support numerators and the primal
+ * kernel); -1 where not measured.
  * Fills min(n, 10) values; call after the stream has completed. */
 int qwb_batch_kernel_times(qwb_batch* batch, double* ms_out, int32_t n);
 /* Launch configurations the autotuner chose for this batch and the device

@@ -254,7 +254,7 @@ static void batch_free(qwb_batch* b) {
 }
 
 struct PlanLayout {   // per-pair coarse plan region
-    size_t rowptr, col, val, colptr, rowidx, valc, val_t, valc_t, fco, gco, total;
+    size_t rowptr, col, val, colptr, rowidx, valc, val_t, valc_t, supp, fco, gco, total;
 };
 static PlanLayout plan_layout(int M, int cap_nnz = 0) {
     PlanLayout L;
@@ -268,6 +268,7 @@ static PlanLayout plan_layout(int M, int cap_nnz = 0) {
     L.valc = o; o = align_up(o + sizeof(double) * cap, 16);
     L.val_t = o; o = align_up(o + sizeof(double) * cap, 16);    // room for either type
     L.valc_t = o; o = align_up(o + sizeof(double) * cap, 16);
+    L.supp = o; o = align_up(o + sizeof(double) * cap, 16);      // support numerators (device only)
     L.fco = o; o = align_up(o + sizeof(double) * M, 256);
     L.gco = o; o = align_up(o + sizeof(double) * M, 256);
     L.total = o;
@@ -592,6 +593,7 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         P.rowptr = (int*)(pd + L.rowptr); P.colidx = (int*)(pd + L.col); P.val = (double*)(pd + L.val);
         P.colptr = (int*)(pd + L.colptr); P.rowidx = (int*)(pd + L.rowidx); P.valc = (double*)(pd + L.valc);
         P.val_t = pd + L.val_t; P.valc_t = pd + L.valc_t;
+        P.supp_num = pd + L.supp;
         P.f_coarse = (double*)(pd + L.fco);
         P.g_coarse = (double*)(pd + L.gco);
         P.sweeps = sweeps;
@@ -724,6 +726,7 @@ static int enqueue_fine(qwb_batch* b, bool batched, cudaStream_t s) {
                                                      G.M_max, 0, s)))
                     return st;
         if ((st = mark(b, 10, s))) return st;
+        if (do_primal && (st = launch_support_num(b->pairs_d, b->pair_ids_d, b->n, 2 * b->M_max, b->f64, s))) return st;
         if (do_primal && (st = launch_primal(b->pairs_d, b->outs_d, b->pair_ids_d, b->n, b->M_max, 0, b->f64, s))) return st;
         if ((st = mark(b, 4, s))) return st;
         const int cap = sm;       // persistent grid: all resident CTAs walk the item list
@@ -760,6 +763,7 @@ static int enqueue_fine(qwb_batch* b, bool batched, cudaStream_t s) {
     for (int t = 0; t < b->n; ++t) {
         const int* id = b->pair_ids_d + t;
         const int M = b->Ms[t];
+        if (do_primal && (st = launch_support_num(b->pairs_d, id, 1, 2 * M, b->f64, s))) return st;
         if (do_primal && b->ipf_group_of[t] >= 0 && b->ipf_groups[b->ipf_group_of[t]].C > 0) {
             const auto& G = b->ipf_groups[b->ipf_group_of[t]];
             if ((st = launch_ipf_fine(b->pairs_d, id, 1, G.kappa, G.C, M, 0, s))) return st;
@@ -905,6 +909,10 @@ static int tune_ipf(qwb_batch* b, cudaStream_t s) {
     if (!b->ctx->autotune || !e || e->ipf_done || !b->ev_ok || (b->flags & QWB_FLAG_NO_PRIMAL) ||
         b->ipf_groups.empty())
         return QWB_OK;
+    {   // the primal kernel reads the support numerators
+        const int st0 = launch_support_num(b->pairs_d, b->pair_ids_d, b->n, 2 * b->M_max, b->f64, s);
+        if (st0) return st0;
+    }
     std::ostringstream rep;
     rep << "{";
     double best = 1e30;
@@ -1591,7 +1599,7 @@ int qwb_primal_upscale_ipf(qwb_ctx* ctx, const qwb_problem* prob, const double* 
     P.mu = mu_d; P.nu = nu_d; P.nnz = pi_nnz; P.sweeps = sweeps; P.a_out = a_d; P.b_out = b_d;
     P.rowptr = (int*)(pd + L.rowptr); P.colidx = (int*)(pd + L.col); P.val = (double*)(pd + L.val);
     P.colptr = (int*)(pd + L.colptr); P.rowidx = (int*)(pd + L.rowidx); P.valc = (double*)(pd + L.valc);
-    P.val_t = pd + L.val_t; P.valc_t = pd + L.valc_t;
+    P.val_t = pd + L.val_t; P.valc_t = pd + L.valc_t; P.supp_num = pd + L.supp;
     st = single_upload(b, s);
     {   // the cached descriptor keeps the batch's own buffers
         const PairDev cur = P;
@@ -1601,6 +1609,7 @@ int qwb_primal_upscale_ipf(qwb_ctx* ctx, const qwb_problem* prob, const double* 
     if (st) return st;
     QWB_CUDA(cudaMemsetAsync(b->outs_d, 0, sizeof(PairOut), s));
     if ((st = single_validate(b, s))) return st;
+    if ((st = launch_support_num(b->pairs_d, b->pair_ids_d, 1, pi_nnz, b->f64, s))) return st;
     if ((st = launch_primal(b->pairs_d, b->outs_d, b->pair_ids_d, 1, M, pi_nnz, b->f64, s))) return st;
     PairOut o;
     QWB_CUDA(cudaMemcpyAsync(&o, b->outs_d, sizeof(PairOut), cudaMemcpyDeviceToHost, s));

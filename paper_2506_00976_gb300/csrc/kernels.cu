@@ -1019,6 +1019,41 @@ __device__ __forceinline__ int block_point(const PairDev& P, int k, int t) {
     return (k / n * kap + t / kap) * N + (k % n) * kap + t % kap;
 }
 
+// --------------------------------------------------------------------------
+// support_num: the numerators num_kl = sum_{i in X_k, j in Y_l} mu_i nu_j
+// rho(x_i, y_j)^p of the plan's support entries (Sec. 4, the cost over
+// supp pi-hat; Alg. 4), one thread per entry, with the summation order and
+// upward rounding of C-bar.  They depend only on the measures and the
+// support, so this pass runs before primal_kernel, which weights them by the
+// fitted scalings.  Grid: x over entries (256 per CTA), y over the pairs of
+// pair_ids; entries at or past a pair's nnz are skipped, and supp_num holds
+// room for every entry of the pair's staged plan.
+// --------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+support_num_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair_ids) {
+    const PairDev& P = pairs[pair_ids[blockIdx.y]];
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= P.nnz) return;
+    const int M = P.M;
+    int lo = 0, hi = M;                      // row of entry e: binary search in rowptr
+    while (hi - lo > 1) { const int mid = (lo + hi) >> 1; if (P.rowptr[mid] <= e) lo = mid; else hi = mid; }
+    const int k = lo, l = P.colidx[e];
+    const T num = P.d == 3 ? block_pair_num3<T>(P, k, l)
+                           : (P.kappa == 4 ? block_pair_num<T, 4>(P, k, l) : block_pair_num<T, 0>(P, k, l));
+    reinterpret_cast<T*>(P.supp_num)[e] = num;
+}
+
+int launch_support_num(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int nnz_max, bool f64,
+                       cudaStream_t stream) {
+    if (n_pairs <= 0 || nnz_max <= 0) return QWB_OK;
+    const dim3 grid((unsigned)((nnz_max + 255) / 256), (unsigned)n_pairs);
+    if (f64) support_num_kernel<double><<<grid, 256, 0, stream>>>(pairs_d, pair_ids);
+    else support_num_kernel<float><<<grid, 256, 0, stream>>>(pairs_d, pair_ids);
+    QWB_LAUNCHED();
+    return QWB_OK;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(PRIMAL_THREADS, 2)
 primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
@@ -1236,8 +1271,7 @@ primal_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
         int lo = 0, hi = M;
         while (hi - lo > 1) { const int mid = (lo + hi) >> 1; if (rp[mid] <= e) lo = mid; else hi = mid; }
         const int k = lo, l = ci[e];
-        const T num = P.d == 3 ? block_pair_num3<T>(P, k, l)
-                               : (kap == 4 ? block_pair_num<T, 4>(P, k, l) : block_pair_num<T, 0>(P, k, l));
+        const T num = reinterpret_cast<const T*>(P.supp_num)[e];    // support_num_kernel
         const double term = __dmul_ru(__dmul_ru(__dmul_ru(__dmul_ru(P.val[e], kinv4_hi), alpha[k]), beta[l]),
                                       (double)num);
         cost = __dadd_ru(cost, term);

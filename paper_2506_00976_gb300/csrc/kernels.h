@@ -39,6 +39,8 @@ struct PairDev {
     const void* val_t; const void* valc_t;   // plan values in the pass type T
     int nnz;
     int sweeps;
+    void* supp_num;         // numerators of the support entries (T), from support_num_kernel;
+                            // in the plan staging area, one slot per staged entry
     int fine_ext;           // 1: the fine FP32 sweeps run in ipf_fine_kernel, not in primal_kernel
     void* a; void* b;       // N*N fine scalings work (T)
     double* a_out; double* b_out;   // optional FP64 outputs
@@ -91,6 +93,10 @@ int launch_prepare(const PairDev* pairs_d, PairOut* outs_d, const PixItem* items
 constexpr int CBAR_S = 4;   // block rows per C-bar work item
 int launch_cbar(const PairDev* pairs_d, const CbarItem* items, int n_items, int kappa_max,
                 int n_max, int N_max, bool f64, cudaStream_t stream, int variant = 0);
+// support_num_kernel over the pairs of pair_ids, entries [0, nnz_max) of each
+// (nnz_max >= every pair's nnz; supp_num has room for the pair's staged plan)
+int launch_support_num(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int nnz_max, bool f64,
+                       cudaStream_t stream);
 int launch_primal(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs,
                   int M_max, int nnz_max, bool f64, cudaStream_t stream);
 // Fine FP32 IPF sweeps on clusters of C CTAs per pair (2-D, kappa 4 or 8,

@@ -226,3 +226,21 @@ def test_ctransform_shape_rejects():
         api.ctransform_shape(h, 8, 2.0, 8, 8, 2, prec="f64")  # packing is FP32 only
     with pytest.raises(QwbError, match="UNSUPPORTED"):
         api.ctransform_shape(h, 8, 2.0, 2, 8, 0)             # not compiled
+
+
+@pytest.mark.parametrize("prec", ["mixed", "f64"])
+def test_primal_pass_dense_coupling(prec):
+    """The primal pass accepts any coupling of the coarse marginals, here the
+    product coupling mu~ (x) nu~ with all M^2 entries (far more than the 2M - 1
+    of a basic plan): the upscaled bound equals the oracle's for that plan."""
+    N, kappa, p = 16, 4, 2.0
+    mu, nu = synth.make_measure(N, "gauss", 25, 0), synth.make_measure(N, "field", 25, 1)
+    mt, nt = O.sumpool(mu, N, kappa), O.sumpool(nu, N, kappa)
+    plan = np.outer(mt, nt)
+    ref = O.ub_primal(mu, nu, N, kappa, p, plan_c=plan)
+    rowptr, col, val = _csr(plan)
+    assert len(val) == plan.size
+    r = api.primal_upscale_ipf(T(mu), T(nu), N, kappa, p, rowptr, col, val, sweeps=10, prec=prec)
+    tol = TOL[prec]
+    assert r["w_hat_p"] >= ref["w_hat_p"] * (1 - 1e-12)
+    assert abs(r["ub_primal"] - ref["ub_primal"]) <= tol * ref["ub_primal"]
