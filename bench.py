@@ -343,6 +343,7 @@ def run_gpu(args):
             out["differentiable_256"] = _differentiable_workload(api, dev, args)
             out["ipf_hbm"] = _ipf_hbm_workload(api, dev, args)
             out["workload_64"] = _workload_64(api, dev, args)
+            out["kernel_upscale"] = _kernel_upscale_workload(api, dev, args)
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args.cpu_seconds, args.cpu_workers)
     batch.close()
@@ -493,6 +494,67 @@ def _ipf_hbm_workload(api, dev, args):
                     "primal kernel when the sweeps run inside it"}
 
 
+def _kernel_upscale_workload(api, dev, args):
+    """The primal pass with a general upscaling kernel (Gaussian over the
+    in-block offsets, sigma = 1 px) on the headline pairs: 180 pairs of
+    128 x 128, kappa 4, p 2, 50 FP32 sweeps; only the primal pass runs.  The
+    same batch with the uniform kernel is timed beside it, and the bounds of
+    the two kernels are compared."""
+    import numpy as np
+    import torch
+    from paper_2506_00976_gb300 import synth
+    mus_h, nus_h = _workload_arrays(0)
+    mus = [torch.tensor(a, dtype=torch.float64, device=dev) for a in mus_h]
+    nus = [torch.tensor(b, dtype=torch.float64, device=dev) for b in nus_h]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    K = synth.gaussian_offset_kernel(KAPPA, 1.0)
+    out = {}
+    for name, kern_K in (("gaussian", K), ("uniform", None)):
+        with api.Batch([(N, KAPPA, P)] * len(mus), ipf_sweeps=SWEEPS, prec="mixed", flags=1 | 4,
+                       device=dev) as bt:
+            if kern_K is not None:
+                bt.set_upscale_kernel(KAPPA, kern_K)
+            bt.coarse(mus, nus, batched=True)
+            bt.solve(threads=args.threads)
+
+            def step():
+                bt.fine(mus, nus, batched=True)
+            ms = _event_ms(step, max(3, min(args.steps, 5)), 3, flush)
+            kt = bt.kernel_times()
+            res = bt.results()
+            assert all(r["status"] == 0 for r in res)
+        out[name] = {"ms_per_step": round(ms, 4), "primal_pass_ms": round(kt.get("primal", 0.0), 4),
+                     "ipf_cluster_ms": round(kt.get("ipf_cluster", 0.0), 4),
+                     "ub_primal": [r["ub_primal"] for r in res]}
+    ug, uu = np.array(out["gaussian"].pop("ub_primal")), np.array(out["uniform"].pop("ub_primal"))
+    m, kk, n = N * N, KAPPA * KAPPA, len(mus)
+    flops = 4.0 * m * kk * SWEEPS * n          # the K products: 2 halves x m kk FMAs per sweep
+    kms = out["gaussian"]["primal_pass_ms"]
+    props = torch.cuda.get_device_properties(dev)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except (OSError, ValueError):
+        pass
+    fp32_peak = props.multi_processor_count * 128 * 2 * float(peaks.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
+    achieved = flops / (kms * 1e-3) / 1e12 if kms > 0 else None
+    out.update({
+        "pairs": n, "N": N, "kappa": KAPPA, "p": P, "sweeps": SWEEPS, "sigma_px": 1.0,
+        "value": round(n / (kms * 1e-3), 3) if kms > 0 else None, "unit": "pairs/s (primal pass)",
+        "roofline": {"bound": "fp32", "achieved": round(achieved, 3) if achieved else None,
+                     "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
+                     "frac": round(achieved / fp32_peak, 4) if achieved else None,
+                     "flops_per_launch": flops},
+        "ub_ratio_gaussian_over_uniform": {"mean": float(np.mean(ug / uu)), "min": float(np.min(ug / uu)),
+                                           "max": float(np.max(ug / uu))},
+        "what": "primalk_kernel: IPF of pi~ (x) K with a Gaussian K, 50 FP32 sweeps, certified FP64 "
+                "evaluation; achieved counts the K products only (4 m kappa^2 FLOP per sweep, the plan "
+                "gather's <= 4 (2M - 1) kappa^2 not counted); the uniform line is the uniform primal pass "
+                "(cluster sweeps + primal kernel) on the same batch"})
+    return out
+
+
 def _differentiable_workload(api, dev, args):
     """16 smooth-field pairs of 256 x 256, p = 2, kappa 4: the lower bound's
     device passes and the adjoint kernel's gradient with respect to mu."""
@@ -624,7 +686,7 @@ def main():
     ap.add_argument("--skip-plain", action="store_true", help="time only the batched form")
     ap.add_argument("--skip-e2e", action="store_true", help="skip the end-to-end timing")
     ap.add_argument("--only", default="", choices=["", "ipf_hbm", "uneven_200", "differentiable_256",
-                                                   "workload_64"],
+                                                   "workload_64", "kernel_upscale"],
                     help="run one secondary workload alone and print its JSON (profiling)")
     ap.add_argument("--skip-workloads", action="store_true",
                     help="skip the uneven 200-pair and differentiable 256x256 measurements")
@@ -639,7 +701,8 @@ def main():
         dev = torch.device("cuda", 0)
         torch.cuda.set_device(dev)
         fn = {"ipf_hbm": _ipf_hbm_workload, "uneven_200": _uneven_workload,
-              "differentiable_256": _differentiable_workload, "workload_64": _workload_64}[args.only]
+              "differentiable_256": _differentiable_workload, "workload_64": _workload_64,
+              "kernel_upscale": _kernel_upscale_workload}[args.only]
         print(json.dumps({args.only: fn(api, dev, args)}), flush=True)
         return
     out = run_reference(args) if args.impl == "reference" else run_gpu(args)

@@ -178,6 +178,27 @@ int qwb_primal_upscale_ipf(qwb_ctx* ctx, const qwb_problem* prob, const double* 
                            int32_t sweeps, double* a_d, double* b_d, qwb_result* out_h,
                            qwb_prec prec, void* stream);
 
+/* The same pass with a general normalized positive upscaling kernel (Sec.
+ * 3.4, eq. coupling tensor upscale: pi-hat_ij = pi~_{k(i) l(j)} K[u(i), v(j)]
+ * with u, v the row-major offsets of i, j inside their kappa x kappa blocks).
+ * K_d: kappa^2 x kappa^2 FP64 on the device, row-major K[u * kappa^2 + v],
+ * every entry positive and finite (its scale is absorbed by the scalings; the
+ * paper's kernels sum to 1); d = 2 and kappa <= 8.  No block-scalar shortcut
+ * exists for such K: MIXED and F64 run `sweeps` IPF sweeps on the fine
+ * vectors in FP32 / FP64, and the bound is certified for the plan
+ * diag(a) pi-hat diag(b) with those scalings as they are: interval bounds
+ * (directed rounding, FP64) of its marginals mu-hat, nu-hat and of its total
+ * mass s, the cost over its support rounded up and divided by s rounded down,
+ * and the weighted-TV corrections between mu-hat / s, nu-hat / s and mu, nu.
+ * Other arguments, outputs and errors as qwb_primal_upscale_ipf, plus
+ * UNSUPPORTED (d = 3 or kappa > 8) and INVALID_ARG (null or non-positive K). */
+int qwb_primal_upscale_ipf_kernel(qwb_ctx* ctx, const qwb_problem* prob, const double* mu_d,
+                                  const double* nu_d, const int32_t* pi_rowptr_d,
+                                  const int32_t* pi_col_d, const double* pi_val_d,
+                                  int32_t pi_nnz, const double* K_d, int32_t sweeps,
+                                  double* a_d, double* b_d, qwb_result* out_h, qwb_prec prec,
+                                  void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Pass (c): dual upscaling + c-transforms + lower bound.  Sec. 3.5 (the     */
 /* interpolation R, the c-transform and its double application, the          */
@@ -309,6 +330,13 @@ int qwb_batch_fine(qwb_batch* batch, const double* const* mu_d, const double* co
                    int32_t batched, void* stream);
 int qwb_batch_results(qwb_batch* batch, qwb_result* out_h, void* stream);
 int qwb_batch_potentials(qwb_batch* batch, int32_t pair, double* f_d, double* g_d, void* stream);
+/* Pair t's exact coarse plan pi~ of the C~ problem (Sec. 3.4; the plan the
+ * primal pass upscales), from the last qwb_batch_solve, as host CSR:
+ * rowptr_h (M + 1), col_h and val_h (cap >= nnz entries each), *nnz_out.  Any
+ * of the three arrays may be NULL (a call with all NULL returns the nnz).
+ * Errors: INVALID_ARG (bad pair, not solved, cap < nnz). */
+int qwb_batch_coarse_plan(qwb_batch* batch, int32_t pair, int32_t* rowptr_h, int32_t* col_h,
+                          double* val_h, int32_t cap, int32_t* nnz_out);
 /* Where the fine FP32 IPF sweeps of the batch's 2-D FP32 pairs with block side
  * 4 or 8 run (Sec. 3.4, IPF paragraph; Alg. 4; the values do not depend on
  * it): C = 0 inside the primal-pass kernel, one CTA per pair; C = 2, 4, 8, 16
@@ -319,11 +347,22 @@ int qwb_batch_potentials(qwb_batch* batch, int32_t pair, double* f_d, double* g_
  * sides.  Overrides the autotuner's choice; synchronises the device and drops
  * the batch's captured fine-pass graphs.  Errors: INVALID_ARG, CUDA. */
 int qwb_batch_set_ipf_cluster(qwb_batch* batch, int32_t C);
+/* Upscale the coarse plans of the batch's 2-D pairs with block side kappa by
+ * the general kernel K_d (Sec. 3.4, eq. coupling tensor upscale; layout,
+ * requirements and certification as qwb_primal_upscale_ipf_kernel) instead of
+ * the uniform kappa^-4; K_d NULL returns them to the uniform kernel.  K_d is
+ * copied (the caller keeps ownership).  Those pairs sweep inside the
+ * general-kernel primal kernel, one CTA per pair, and leave the cluster IPF
+ * groups.  Synchronises the device and drops the batch's captured fine-pass
+ * graphs.  Errors: INVALID_ARG (kappa < 1, a non-positive or non-finite
+ * entry), UNSUPPORTED (kappa > 8), CUDA, OOM. */
+int qwb_batch_set_upscale_kernel(qwb_batch* batch, int32_t kappa, const double* K_d);
 /* Pair t's scalings after the fine IPF sweeps of the last qwb_batch_fine
  * (Sec. 3.4, IPF paragraph; Alg. 4): the pass-type a, b with
  * a = mu / (pi-hat b), b = nu / (pi-hat^T a) after ipf_sweeps sweeps from
- * b = 1, widened to FP64 (N^d each, device, either may be NULL).  The
- * certified bound uses the FP64 block-scalar fit instead (qwb_result fields).
+ * b = 1, widened to FP64 (N^d each, device, either may be NULL).  With the
+ * uniform kernel the certified bound uses the FP64 block-scalar fit instead
+ * (qwb_result fields); with a general kernel it uses these scalings.
  * Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA. */
 int qwb_batch_fine_scalings(qwb_batch* batch, int32_t pair, double* a_d, double* b_d, void* stream);
 /* Device time (ms) of each kernel of the last batched passes, in the order

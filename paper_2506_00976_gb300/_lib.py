@@ -54,6 +54,10 @@ SIGNATURES = [
                                          c_void_p, c_void_p, c_void_p, c_int32, c_int32,
                                          c_void_p, c_void_p, ctypes.POINTER(QwbResult), c_int32,
                                          c_void_p]),
+    ("qwb_primal_upscale_ipf_kernel", c_int32, [c_void_p, ctypes.POINTER(QwbProblem), c_void_p,
+                                                c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
+                                                c_void_p, c_int32, c_void_p, c_void_p,
+                                                ctypes.POINTER(QwbResult), c_int32, c_void_p]),
     ("qwb_dual_upscale_ctransform", c_int32, [c_void_p, ctypes.POINTER(QwbProblem), c_void_p,
                                               c_void_p, c_void_p, c_void_p, c_void_p,
                                               ctypes.POINTER(QwbResult), c_int32, c_void_p]),
@@ -78,8 +82,11 @@ SIGNATURES = [
                                  c_int32, c_void_p]),
     ("qwb_batch_results", c_int32, [c_void_p, ctypes.POINTER(QwbResult), c_void_p]),
     ("qwb_batch_potentials", c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
+    ("qwb_batch_coarse_plan", c_int32, [c_void_p, c_int32, P_int32, P_int32, P_double, c_int32,
+                                        P_int32]),
     ("qwb_batch_fine_scalings", c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
     ("qwb_batch_set_ipf_cluster", c_int32, [c_void_p, c_int32]),
+    ("qwb_batch_set_upscale_kernel", c_int32, [c_void_p, c_int32, c_void_p]),
     ("qwb_batch_kernel_times", c_int32, [c_void_p, P_double, c_int32]),
     ("qwb_batch_tuning", c_int32, [c_void_p, ctypes.c_char_p, c_int32]),
     ("qwb_status_string", ctypes.c_char_p, [c_int32]),

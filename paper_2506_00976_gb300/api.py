@@ -122,6 +122,35 @@ def primal_upscale_ipf(mu, nu, N, kappa, p, rowptr, col, val, sweeps=50, prec="m
     return out
 
 
+def primal_upscale_ipf_kernel(mu, nu, N, kappa, p, rowptr, col, val, K, sweeps=50, prec="mixed",
+                              want_scalings=False):
+    """qwb_primal_upscale_ipf_kernel: the primal upscaling upper bound with a
+    general positive upscaling kernel K [kappa^2, kappa^2] (d = 2, kappa <= 8)."""
+    dev = mu.device
+    rp = torch.as_tensor(np.asarray(rowptr, dtype=np.int32), device=dev)
+    cl = torch.as_tensor(np.asarray(col, dtype=np.int32), device=dev)
+    vl = torch.as_tensor(np.asarray(val, dtype=np.float64), device=dev)
+    Kd = torch.as_tensor(np.ascontiguousarray(K, dtype=np.float64), device=dev).contiguous()
+    if Kd.shape != (kappa * kappa, kappa * kappa):
+        raise ValueError("K must be [kappa^2, kappa^2]")
+    a = b = None
+    if want_scalings:
+        a = torch.empty(N * N, dtype=torch.float64, device=dev)
+        b = torch.empty(N * N, dtype=torch.float64, device=dev)
+    res = QwbResult()
+    pr = problem(N, kappa, p, 2)
+    check(_lib.load().qwb_primal_upscale_ipf_kernel(context(dev), ctypes.byref(pr), _dev64(mu, "mu"),
+                                                    _dev64(nu, "nu"), _ptr(rp), _ptr(cl), _ptr(vl),
+                                                    int(vl.numel()), _ptr(Kd), int(sweeps), _ptr(a),
+                                                    _ptr(b), ctypes.byref(res), _prec(prec),
+                                                    _stream(mu)),
+          "qwb_primal_upscale_ipf_kernel")
+    out = res.as_dict()
+    if want_scalings:
+        out["a"], out["b"] = a, b
+    return out
+
+
 def dual_upscale_ctransform(mu, nu, N, kappa, p, f_coarse, prec="mixed", want_potentials=True, d=2):
     """qwb_dual_upscale_ctransform: the dual upscaling lower bound from a coarse potential."""
     dev = mu.device
@@ -243,9 +272,40 @@ class Batch:
               "qwb_batch_potentials")
         return f, g
 
+    def coarse_plan(self, t):
+        """Pair t's exact coarse plan of the last solve as a dense [M, M] numpy array."""
+        n = ctypes.c_int32()
+        L = _lib.load()
+        check(L.qwb_batch_coarse_plan(self._h, int(t), None, None, None, 0, ctypes.byref(n)),
+              "qwb_batch_coarse_plan")
+        pr = self.problems[t]
+        M = (pr.N // pr.kappa) ** (pr.d or 2)
+        rowptr = np.zeros(M + 1, dtype=np.int32)
+        col = np.zeros(max(1, n.value), dtype=np.int32)
+        val = np.zeros(max(1, n.value), dtype=np.float64)
+        check(L.qwb_batch_coarse_plan(self._h, int(t), rowptr.ctypes.data_as(_lib.P_int32),
+                                      col.ctypes.data_as(_lib.P_int32), val.ctypes.data_as(_lib.P_double),
+                                      int(len(col)), ctypes.byref(n)), "qwb_batch_coarse_plan")
+        plan = np.zeros((M, M))
+        for k in range(M):
+            for e in range(rowptr[k], rowptr[k + 1]):
+                plan[k, col[e]] = val[e]
+        return plan
+
     def set_ipf_cluster(self, C):
         """Run the fine IPF sweeps inside the primal kernel (0) or on clusters of C CTAs."""
         check(_lib.load().qwb_batch_set_ipf_cluster(self._h, int(C)), "qwb_batch_set_ipf_cluster")
+
+    def set_upscale_kernel(self, kappa, K):
+        """Upscale the plans of the 2-D pairs with block side kappa by the
+        general kernel K [kappa^2, kappa^2] (None: the uniform kernel)."""
+        Kd = None
+        if K is not None:
+            Kd = torch.as_tensor(np.ascontiguousarray(K, dtype=np.float64), device=self._dev).contiguous()
+            if Kd.shape != (kappa * kappa, kappa * kappa):
+                raise ValueError("K must be [kappa^2, kappa^2]")
+        check(_lib.load().qwb_batch_set_upscale_kernel(self._h, int(kappa), _ptr(Kd)),
+              "qwb_batch_set_upscale_kernel")
 
     def fine_scalings(self, t):
         """Pair t's fine IPF scalings a, b (pass type widened to FP64)."""

@@ -209,6 +209,14 @@ struct qwb_batch {
     std::vector<int> ipf_group_of;      // per pair: its group or -1
     int* ipf_ids_d = nullptr;
     int ipf_C = 0;
+    // pairs upscaled with a general kernel K (primalk_kernel, 2-D, kappa <= 8):
+    // K per kappa, and prim_ids_d = [uniform pairs..., K pairs...]
+    std::vector<std::pair<int, std::vector<double>>> upk;   // (kappa, K)
+    std::vector<char> upk_on;           // per pair
+    char* upk_mem = nullptr;
+    int* prim_ids_d = nullptr;
+    int n_uni = 0, n_upk = 0, upk_kappa_max = 0;
+    bool upk_all4 = false;
     std::vector<int> prep_off, prep_cnt, pix_off, pix_cnt, cbar_off, cbar_cnt, ct_off, ct_cnt;
     int n_prep = 0, n_pix = 0, n_cbar = 0, n_ct_b = 0;
     int n_ct_b_p2 = 0;   // batched c-transform items: the p = 2 pairs' items come first
@@ -246,6 +254,7 @@ static void batch_free(qwb_batch* b) {
     if (b->plan_d) cudaFree(b->plan_d);
     if (b->plan_h) cudaFreeHost(b->plan_h);
     if (b->cbar_h) cudaFreeHost(b->cbar_h);
+    if (b->upk_mem) cudaFree(b->upk_mem);
     if (b->ev_ok) {
         for (auto& e : b->ev) cudaEventDestroy(e);
         for (auto& e : b->kev) cudaEventDestroy(e);
@@ -292,6 +301,31 @@ static void stage_typed_values(char* ph, const PlanLayout& L, int nnz, bool f64)
 // Cluster size of the fine IPF sweeps: every group takes the largest power of
 // two <= C that divides its coarse sides (below 2: sweeps inside
 // primal_kernel); the descriptors' fine_ext flags are re-uploaded.
+// Group the 2-D FP32 pairs of kappa 4 and 8 that use the uniform kernel for
+// the cluster sweeps; returns the pair ids in group order.
+static std::vector<int> build_ipf_groups(qwb_batch* b) {
+    b->ipf_group_of.assign(b->n, -1);
+    b->ipf_groups.clear();
+    std::vector<int> ipf_ids;
+    if (b->f64) return ipf_ids;
+    for (int kap : {4, 8}) {
+        qwb_batch::IpfGroup G{kap, (int)ipf_ids.size(), 0, 0, 0, 0};
+        for (int t = 0; t < b->n; ++t) {
+            if (dim_of(b->probs[t]) != 2 || b->probs[t].kappa != kap || b->upk_on[t]) continue;
+            const int nn = b->probs[t].N / kap;
+            int x = G.gcd_n, y = nn;
+            while (y) { const int r = x % y; x = y; y = r; }
+            G.gcd_n = x;
+            G.M_max = std::max(G.M_max, nn * nn);
+            b->ipf_group_of[t] = (int)b->ipf_groups.size();
+            ipf_ids.push_back(t);
+            ++G.cnt;
+        }
+        if (G.cnt) b->ipf_groups.push_back(G);
+    }
+    return ipf_ids;
+}
+
 static int apply_ipf_choice(qwb_batch* b, int C) {
     b->ipf_C = C;
     for (auto& G : b->ipf_groups) {
@@ -503,24 +537,8 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
     const size_t o_ctp = align_up(o_ctb + sizeof(CtItem) * ctb.size());
     const size_t o_sep = align_up(o_ctp + sizeof(CtItem) * ctp.size());
     const size_t o_cb3 = align_up(o_sep + sizeof(SepItem) * sep.size());
-    b->ipf_group_of.assign(n, -1);
-    std::vector<int> ipf_ids;
-    if (!b->f64)
-        for (int kap : {4, 8}) {
-            qwb_batch::IpfGroup G{kap, (int)ipf_ids.size(), 0, 0, 0, 0};
-            for (int t = 0; t < n; ++t) {
-                if (dim_of(probs[t]) != 2 || probs[t].kappa != kap) continue;
-                const int nn = probs[t].N / kap;
-                int x = G.gcd_n, y = nn;
-                while (y) { const int r = x % y; x = y; y = r; }
-                G.gcd_n = x;
-                G.M_max = std::max(G.M_max, nn * nn);
-                b->ipf_group_of[t] = (int)b->ipf_groups.size();
-                ipf_ids.push_back(t);
-                ++G.cnt;
-            }
-            if (G.cnt) b->ipf_groups.push_back(G);
-        }
+    b->upk_on.assign(n, 0);
+    const std::vector<int> ipf_ids = build_ipf_groups(b);
     const size_t o_ipf = align_up(o_cb3 + sizeof(PixItem) * cb3.size());
     const size_t total = align_up(o_ipf + sizeof(int) * std::max<size_t>(1, ipf_ids.size()));
     if (cudaMalloc(&b->dmem, total) != cudaSuccess) { batch_free(b); return fail(QWB_ERR_OOM, "batch workspace"); }
@@ -726,8 +744,15 @@ static int enqueue_fine(qwb_batch* b, bool batched, cudaStream_t s) {
                                                      G.M_max, 0, s)))
                     return st;
         if ((st = mark(b, 10, s))) return st;
-        if (do_primal && (st = launch_support_num(b->pairs_d, b->pair_ids_d, b->n, 2 * b->M_max, b->f64, s))) return st;
-        if (do_primal && (st = launch_primal(b->pairs_d, b->outs_d, b->pair_ids_d, b->n, b->M_max, 0, b->f64, s))) return st;
+        if (do_primal) {
+            const int* uni = b->n_upk ? b->prim_ids_d : b->pair_ids_d;
+            const int n_uni = b->n_upk ? b->n_uni : b->n;
+            if ((st = launch_support_num(b->pairs_d, uni, n_uni, 2 * b->M_max, b->f64, s))) return st;
+            if ((st = launch_primal(b->pairs_d, b->outs_d, uni, n_uni, b->M_max, 0, b->f64, s))) return st;
+            if (b->n_upk && (st = launch_primalk(b->pairs_d, b->outs_d, b->prim_ids_d + b->n_uni, b->n_upk,
+                                                 b->upk_kappa_max, b->upk_all4, b->f64, s)))
+                return st;
+        }
         if ((st = mark(b, 4, s))) return st;
         const int cap = sm;       // persistent grid: all resident CTAs walk the item list
         if (do_dual) {
@@ -763,12 +788,17 @@ static int enqueue_fine(qwb_batch* b, bool batched, cudaStream_t s) {
     for (int t = 0; t < b->n; ++t) {
         const int* id = b->pair_ids_d + t;
         const int M = b->Ms[t];
-        if (do_primal && (st = launch_support_num(b->pairs_d, id, 1, 2 * M, b->f64, s))) return st;
-        if (do_primal && b->ipf_group_of[t] >= 0 && b->ipf_groups[b->ipf_group_of[t]].C > 0) {
-            const auto& G = b->ipf_groups[b->ipf_group_of[t]];
-            if ((st = launch_ipf_fine(b->pairs_d, id, 1, G.kappa, G.C, M, 0, s))) return st;
+        if (do_primal && b->upk_on[t]) {
+            const int kap = b->probs[t].kappa;
+            if ((st = launch_primalk(b->pairs_d, b->outs_d, id, 1, kap, kap == 4, b->f64, s))) return st;
+        } else if (do_primal) {
+            if ((st = launch_support_num(b->pairs_d, id, 1, 2 * M, b->f64, s))) return st;
+            if (b->ipf_group_of[t] >= 0 && b->ipf_groups[b->ipf_group_of[t]].C > 0) {
+                const auto& G = b->ipf_groups[b->ipf_group_of[t]];
+                if ((st = launch_ipf_fine(b->pairs_d, id, 1, G.kappa, G.C, M, 0, s))) return st;
+            }
+            if ((st = launch_primal(b->pairs_d, b->outs_d, id, 1, M, 0, b->f64, s))) return st;
         }
-        if (do_primal && (st = launch_primal(b->pairs_d, b->outs_d, id, 1, M, 0, b->f64, s))) return st;
         if (!do_dual) continue;
         if ((st = launch_centre(b->pairs_d, b->outs_d, id, 1, s))) return st;
         if ((st = launch_upsample(b->pairs_d, b->outs_d, b->pix_items_d + b->pix_off[t], b->pix_cnt[t], b->f64, s))) return st;
@@ -1411,6 +1441,23 @@ int qwb_batch_potentials(qwb_batch* b, int32_t pair, double* f_d, double* g_d, v
     return QWB_OK;
 }
 
+int qwb_batch_coarse_plan(qwb_batch* b, int32_t pair, int32_t* rowptr_h, int32_t* col_h, double* val_h,
+                          int32_t cap, int32_t* nnz_out) {
+    if (!b || pair < 0 || pair >= b->n || !nnz_out)
+        return fail(QWB_ERR_INVALID_ARG, "qwb_batch_coarse_plan: bad arguments");
+    if (!b->solved) return fail(QWB_ERR_INVALID_ARG, "qwb_batch_coarse_plan: the batch has not been solved");
+    const int M = b->Ms[pair];
+    const int nnz = b->pairs_h[pair].nnz;
+    *nnz_out = nnz;
+    if ((col_h || val_h) && cap < nnz) return fail(QWB_ERR_INVALID_ARG, "qwb_batch_coarse_plan: cap < nnz");
+    const PlanLayout L = plan_layout(M);
+    const char* ph = b->plan_h + b->plan_off[pair];
+    if (rowptr_h) std::memcpy(rowptr_h, ph + L.rowptr, sizeof(int) * (M + 1));
+    if (col_h) std::memcpy(col_h, ph + L.col, sizeof(int) * nnz);
+    if (val_h) std::memcpy(val_h, ph + L.val, sizeof(double) * nnz);
+    return QWB_OK;
+}
+
 int qwb_batch_set_ipf_cluster(qwb_batch* b, int32_t C) {
     if (!b || (C != 0 && C != 2 && C != 4 && C != 8 && C != 16))
         return fail(QWB_ERR_INVALID_ARG, "qwb_batch_set_ipf_cluster: C must be 0, 2, 4, 8 or 16");
@@ -1425,6 +1472,98 @@ int qwb_batch_set_ipf_cluster(qwb_batch* b, int32_t C) {
     b->graphs.swap(keep);
     if (b->tune) { b->tune->ipf_done = true; b->tune->ipf_C = C; b->tune->ipf_report = "\"set\""; }
     return apply_ipf_choice(b, C);
+}
+
+int qwb_batch_set_upscale_kernel(qwb_batch* b, int32_t kappa, const double* K_d) {
+    if (!b || kappa < 1) return fail(QWB_ERR_INVALID_ARG, "qwb_batch_set_upscale_kernel: bad arguments");
+    QWB_CUDA(cudaSetDevice(b->ctx->device));
+    QWB_CUDA(cudaDeviceSynchronize());
+    const int kk = kappa * kappa;
+    std::vector<double> Kh;
+    if (K_d) {
+        if (kappa > 8) return fail(QWB_ERR_UNSUPPORTED, "a general upscaling kernel needs kappa <= 8");
+        Kh.resize((size_t)kk * kk);
+        QWB_CUDA(cudaMemcpy(Kh.data(), K_d, sizeof(double) * kk * kk, cudaMemcpyDeviceToHost));
+        for (double v : Kh)
+            if (!(v > 0.0) || !std::isfinite(v))
+                return fail(QWB_ERR_INVALID_ARG, "upscaling kernel entries must be positive and finite");
+    }
+    // captured fine passes hold the previous pair lists
+    std::vector<GraphEntry> keep;
+    for (auto& g : b->graphs) {
+        if (g.kind == 1) cudaGraphExecDestroy(g.exec);
+        else keep.push_back(g);
+    }
+    b->graphs.swap(keep);
+    auto it = std::find_if(b->upk.begin(), b->upk.end(), [&](const auto& e) { return e.first == kappa; });
+    if (it != b->upk.end()) b->upk.erase(it);
+    if (K_d) b->upk.emplace_back(kappa, std::move(Kh));
+    // lay out: per kernel K (FP64) and K (pass type); per K pair the KB and
+    // evaluation scratches; the primal pair lists
+    const size_t tsz = b->f64 ? 8 : 4;
+    std::vector<size_t> k_off(b->upk.size());
+    size_t off = 0;
+    for (size_t q = 0; q < b->upk.size(); ++q) {
+        const size_t e = b->upk[q].second.size();
+        k_off[q] = off;
+        off = align_up(off + e * (8 + tsz));
+    }
+    std::vector<int> which(b->n, -1);
+    std::vector<size_t> s_off(b->n, 0);
+    for (int t = 0; t < b->n; ++t) {
+        if (dim_of(b->probs[t]) != 2) continue;
+        for (size_t q = 0; q < b->upk.size(); ++q)
+            if (b->upk[q].first == b->probs[t].kappa) which[t] = (int)q;
+        if (which[t] < 0) continue;
+        const size_t m = (size_t)b->probs[t].N * b->probs[t].N;
+        s_off[t] = off;
+        off = align_up(off + align_up(m * tsz) + 16 * m);
+    }
+    const size_t ids_off = off;
+    off = align_up(off + sizeof(int) * b->n);
+    if (b->upk_mem) { cudaFree(b->upk_mem); b->upk_mem = nullptr; }
+    if (cudaMalloc(&b->upk_mem, off) != cudaSuccess) return fail(QWB_ERR_OOM, "upscaling kernel scratch");
+    for (size_t q = 0; q < b->upk.size(); ++q) {
+        const auto& K = b->upk[q].second;
+        std::vector<char> host(K.size() * (8 + tsz));
+        std::memcpy(host.data(), K.data(), 8 * K.size());
+        for (size_t t = 0; t < K.size(); ++t) {
+            if (b->f64) ((double*)(host.data() + 8 * K.size()))[t] = K[t];
+            else ((float*)(host.data() + 8 * K.size()))[t] = (float)K[t];
+        }
+        QWB_CUDA(cudaMemcpy(b->upk_mem + k_off[q], host.data(), host.size(), cudaMemcpyHostToDevice));
+    }
+    std::vector<int> uni, kp;
+    b->upk_kappa_max = 0;
+    b->upk_all4 = true;
+    for (int t = 0; t < b->n; ++t) {
+        PairDev& P = b->pairs_h[t];
+        b->upk_on[t] = which[t] >= 0;
+        if (which[t] < 0) {
+            P.upK = nullptr; P.upK_t = nullptr; P.kb_t = nullptr; P.kscratch = nullptr;
+            uni.push_back(t);
+            continue;
+        }
+        const size_t kbytes = b->upk[which[t]].second.size();
+        const size_t m = (size_t)b->probs[t].N * b->probs[t].N;
+        P.upK = (const double*)(b->upk_mem + k_off[which[t]]);
+        P.upK_t = b->upk_mem + k_off[which[t]] + 8 * kbytes;
+        P.kb_t = b->upk_mem + s_off[t];
+        P.kscratch = (double*)(b->upk_mem + s_off[t] + align_up(m * tsz));
+        kp.push_back(t);
+        b->upk_kappa_max = std::max(b->upk_kappa_max, b->probs[t].kappa);
+        b->upk_all4 = b->upk_all4 && b->probs[t].kappa == 4;
+    }
+    b->n_uni = (int)uni.size();
+    b->n_upk = (int)kp.size();
+    uni.insert(uni.end(), kp.begin(), kp.end());
+    b->prim_ids_d = (int*)(b->upk_mem + ids_off);
+    QWB_CUDA(cudaMemcpy(b->prim_ids_d, uni.data(), sizeof(int) * b->n, cudaMemcpyHostToDevice));
+    // the cluster sweeps keep the uniform pairs only
+    const std::vector<int> ipf_ids = build_ipf_groups(b);
+    if (!ipf_ids.empty())
+        QWB_CUDA(cudaMemcpy(b->ipf_ids_d, ipf_ids.data(), sizeof(int) * ipf_ids.size(), cudaMemcpyHostToDevice));
+    return apply_ipf_choice(b, b->ipf_C);
 }
 
 int qwb_batch_fine_scalings(qwb_batch* b, int32_t pair, double* a_d, double* b_d, void* stream) {
@@ -1533,15 +1672,30 @@ int qwb_coarse_cost(qwb_ctx* ctx, const qwb_problem* prob, const double* mu_d, c
     return QWB_OK;
 }
 
-int qwb_primal_upscale_ipf(qwb_ctx* ctx, const qwb_problem* prob, const double* mu_d,
-                           const double* nu_d, const int32_t* pi_rowptr_d, const int32_t* pi_col_d,
-                           const double* pi_val_d, int32_t pi_nnz, int32_t sweeps, double* a_d,
-                           double* b_d, qwb_result* out_h, qwb_prec prec, void* stream) {
+}  // extern "C"
+
+// The primal pass of one pair: the uniform kernel when K_d is null, else the
+// general kernel K_d ((kappa^2)^2 FP64 on the device, d = 2, kappa <= 8).
+static int primal_single(qwb_ctx* ctx, const qwb_problem* prob, const double* mu_d, const double* nu_d,
+                         const int32_t* pi_rowptr_d, const int32_t* pi_col_d, const double* pi_val_d,
+                         int32_t pi_nnz, int32_t sweeps, const double* K_d, double* a_d, double* b_d,
+                         qwb_result* out_h, qwb_prec prec, void* stream) {
     if (!ctx || !mu_d || !nu_d || !pi_rowptr_d || !pi_col_d || !pi_val_d || !out_h)
         return fail(QWB_ERR_INVALID_ARG, "qwb_primal_upscale_ipf: null argument");
     int st = check_problem(prob);
     if (st) return st;
     if (sweeps < 1) return fail(QWB_ERR_INVALID_ARG, "sweeps must be >= 1");
+    const int kk = prob->kappa * prob->kappa;
+    std::vector<double> Kh;
+    if (K_d) {
+        if (dim_of(*prob) != 2 || prob->kappa > 8)
+            return fail(QWB_ERR_UNSUPPORTED, "a general upscaling kernel needs d = 2 and kappa <= 8");
+        Kh.resize((size_t)kk * kk);
+        QWB_CUDA(cudaMemcpy(Kh.data(), K_d, sizeof(double) * kk * kk, cudaMemcpyDeviceToHost));
+        for (double v : Kh)
+            if (!(v > 0.0) || !std::isfinite(v))
+                return fail(QWB_ERR_INVALID_ARG, "upscaling kernel entries must be positive and finite");
+    }
     std::lock_guard<std::mutex> lk(ctx->mtx);
     QWB_CUDA(cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
@@ -1594,9 +1748,34 @@ int qwb_primal_upscale_ipf(qwb_ctx* ctx, const qwb_problem* prob, const double* 
         }
     stage_typed_values(ph, L, pi_nnz, b->f64);
     QWB_CUDA(cudaMemcpyAsync(pd, ph, L.total, cudaMemcpyHostToDevice, s));
+    // general kernel: K in FP64 and in the pass type, the sweep and evaluation scratches
+    char* kbuf = nullptr;
+    const size_t m_pts = (size_t)prob->N * prob->N;
+    const size_t tsz = b->f64 ? 8 : 4;
+    const size_t k64_off = 0, kt_off = 8 * (size_t)kk * kk, kb_off = kt_off + 8 * (size_t)kk * kk,
+                 ks_off = kb_off + 8 * m_pts, k_total = ks_off + 16 * m_pts;
+    struct KRelease {
+        char* d;
+        ~KRelease() { if (d) cudaFree(d); }
+    } krelease{nullptr};
+    if (K_d) {
+        if (cudaMalloc(&kbuf, k_total) != cudaSuccess) return fail(QWB_ERR_OOM, "kernel scratch");
+        krelease.d = kbuf;
+        std::vector<char> kt(tsz * kk * kk);
+        for (int t = 0; t < kk * kk; ++t) {
+            if (b->f64) ((double*)kt.data())[t] = Kh[t];
+            else ((float*)kt.data())[t] = (float)Kh[t];
+        }
+        QWB_CUDA(cudaMemcpyAsync(kbuf + k64_off, K_d, sizeof(double) * kk * kk, cudaMemcpyDeviceToDevice, s));
+        QWB_CUDA(cudaMemcpyAsync(kbuf + kt_off, kt.data(), kt.size(), cudaMemcpyHostToDevice, s));
+    }
     PairDev& P = b->pairs_h[0];
     const PairDev saved = P;
     P.mu = mu_d; P.nu = nu_d; P.nnz = pi_nnz; P.sweeps = sweeps; P.a_out = a_d; P.b_out = b_d;
+    if (K_d) {
+        P.upK = (const double*)(kbuf + k64_off); P.upK_t = kbuf + kt_off;
+        P.kb_t = kbuf + kb_off; P.kscratch = (double*)(kbuf + ks_off);
+    }
     P.rowptr = (int*)(pd + L.rowptr); P.colidx = (int*)(pd + L.col); P.val = (double*)(pd + L.val);
     P.colptr = (int*)(pd + L.colptr); P.rowidx = (int*)(pd + L.rowidx); P.valc = (double*)(pd + L.valc);
     P.val_t = pd + L.val_t; P.valc_t = pd + L.valc_t; P.supp_num = pd + L.supp;
@@ -1609,8 +1788,12 @@ int qwb_primal_upscale_ipf(qwb_ctx* ctx, const qwb_problem* prob, const double* 
     if (st) return st;
     QWB_CUDA(cudaMemsetAsync(b->outs_d, 0, sizeof(PairOut), s));
     if ((st = single_validate(b, s))) return st;
-    if ((st = launch_support_num(b->pairs_d, b->pair_ids_d, 1, pi_nnz, b->f64, s))) return st;
-    if ((st = launch_primal(b->pairs_d, b->outs_d, b->pair_ids_d, 1, M, pi_nnz, b->f64, s))) return st;
+    if (K_d) {
+        if ((st = launch_primalk(b->pairs_d, b->outs_d, b->pair_ids_d, 1, prob->kappa, prob->kappa == 4, b->f64, s))) return st;
+    } else {
+        if ((st = launch_support_num(b->pairs_d, b->pair_ids_d, 1, pi_nnz, b->f64, s))) return st;
+        if ((st = launch_primal(b->pairs_d, b->outs_d, b->pair_ids_d, 1, M, pi_nnz, b->f64, s))) return st;
+    }
     PairOut o;
     QWB_CUDA(cudaMemcpyAsync(&o, b->outs_d, sizeof(PairOut), cudaMemcpyDeviceToHost, s));
     QWB_CUDA(cudaStreamSynchronize(s));
@@ -1618,6 +1801,25 @@ int qwb_primal_upscale_ipf(qwb_ctx* ctx, const qwb_problem* prob, const double* 
     out_h->ub_primal = o.ub_primal; out_h->w_hat_p = o.w_hat_p; out_h->delta_mu = o.delta_mu;
     out_h->delta_nu = o.delta_nu; out_h->ipf_residual = o.ipf_residual; out_h->ipf_sweeps_done = o.sweeps_done;
     return QWB_OK;
+}
+
+extern "C" {
+
+int qwb_primal_upscale_ipf(qwb_ctx* ctx, const qwb_problem* prob, const double* mu_d,
+                           const double* nu_d, const int32_t* pi_rowptr_d, const int32_t* pi_col_d,
+                           const double* pi_val_d, int32_t pi_nnz, int32_t sweeps, double* a_d,
+                           double* b_d, qwb_result* out_h, qwb_prec prec, void* stream) {
+    return primal_single(ctx, prob, mu_d, nu_d, pi_rowptr_d, pi_col_d, pi_val_d, pi_nnz, sweeps, nullptr,
+                         a_d, b_d, out_h, prec, stream);
+}
+
+int qwb_primal_upscale_ipf_kernel(qwb_ctx* ctx, const qwb_problem* prob, const double* mu_d,
+                                  const double* nu_d, const int32_t* pi_rowptr_d, const int32_t* pi_col_d,
+                                  const double* pi_val_d, int32_t pi_nnz, const double* K_d, int32_t sweeps,
+                                  double* a_d, double* b_d, qwb_result* out_h, qwb_prec prec, void* stream) {
+    if (!K_d) return fail(QWB_ERR_INVALID_ARG, "qwb_primal_upscale_ipf_kernel: null kernel");
+    return primal_single(ctx, prob, mu_d, nu_d, pi_rowptr_d, pi_col_d, pi_val_d, pi_nnz, sweeps, K_d,
+                         a_d, b_d, out_h, prec, stream);
 }
 
 int qwb_dual_upscale_ctransform(qwb_ctx* ctx, const qwb_problem* prob, const double* mu_d,

@@ -901,6 +901,20 @@ __device__ __forceinline__ double block_reduce_ru(double v, double* red) {
     __syncthreads();
     return red[32];
 }
+__device__ __forceinline__ double block_reduce_rd(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v = __dadd_rd(v, __shfl_down_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = __dadd_rd(s, red[w]);
+        red[32] = s;
+    }
+    __syncthreads();
+    return red[32];
+}
 __device__ __forceinline__ double block_reduce_rn(double v, double* red) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1320,6 +1334,269 @@ int launch_primal(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, 
     }
     QWB_LAUNCHED();
     return QWB_OK;
+}
+
+// --------------------------------------------------------------------------
+// primalk: the primal upscaling upper bound with a general normalized
+// positive kernel K (Sec. 3.4, eq. coupling tensor upscale; Alg. 4), d = 2,
+// kappa <= 8.  pi-hat_ij = pi~_{k(i) l(j)} K[u(i), v(j)], with u, v the
+// row-major offsets of i, j in their blocks.  One CTA per pair.  The
+// scalings a, b live block-major ([block][offset], position t = k kk + u with
+// kk = kappa^2), so a block's values are one contiguous row.
+//   fine sweeps (type T): a = mu / (pi-hat b), b = nu / (pi-hat^T a), each
+//     half in two steps: KB[l, u] = sum_w K[u, w] b[l, w] for every block
+//     (the b half: sum_w K[w, u] a[k, w]), then r[k, u] = sum_l pi~_kl
+//     KB[l, u] over the plan row (the b half: the plan column), dst = src / r;
+//   certified evaluation (FP64 intervals, directed rounding) of the plan
+//     diag(a) pi-hat diag(b) with the final a, b as they are: bounds of its
+//     marginals and of its total mass s, its cost over the support rounded
+//     up and divided by s rounded down (the plan over s couples the
+//     probability measures mu-hat / s and nu-hat / s), and the weighted-TV
+//     corrections between those and mu, nu.
+// KK = 16 (kappa 4) keeps the thread's two K rows in registers (its offset
+// u = thread index mod 16 is the same at every position it visits).
+// --------------------------------------------------------------------------
+constexpr int PRIMALK_THREADS = 512;
+
+__device__ __forceinline__ int blk_pixel(int k, int u, int n, int kap, int N) {
+    return ((k / n) * kap + u / kap) * N + (k % n) * kap + u % kap;
+}
+
+// sum_w kr[w] x[w] over one contiguous 16-entry block row
+__device__ __forceinline__ float row_dot16(const float* __restrict__ x, const float* kr) {
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    float s = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 v = x4[q];
+        s = fmaf(kr[4 * q], v.x, s);
+        s = fmaf(kr[4 * q + 1], v.y, s);
+        s = fmaf(kr[4 * q + 2], v.z, s);
+        s = fmaf(kr[4 * q + 3], v.w, s);
+    }
+    return s;
+}
+__device__ __forceinline__ double row_dot16(const double* __restrict__ x, const double* kr) {
+    const double2* x2 = reinterpret_cast<const double2*>(x);
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const double2 v = x2[q];
+        s = fma(kr[2 * q], v.x, s);
+        s = fma(kr[2 * q + 1], v.y, s);
+    }
+    return s;
+}
+
+template <typename T, int KK>
+__global__ void __launch_bounds__(PRIMALK_THREADS, sizeof(T) == 4 ? 2 : 1)
+primalk_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
+               const int* __restrict__ pair_ids) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[33];
+    const PairDev& P = pairs[pair_ids[blockIdx.x]];
+    const int N = P.N, kap = P.kappa, n = P.n, m = P.m;
+    const int kk = KK ? KK : kap * kap;
+    double* K64 = reinterpret_cast<double*>(smem_raw);       // K[u][w], FP64
+    T* Ks = reinterpret_cast<T*>(K64 + kk * kk);              // K[u][w], type T (read as K[w][u])
+    T* KsT = Ks + kk * kk;                                    // K[u][w] at [w][u] (read as K[u][w])
+    T* Khi = KsT + kk * kk;                                   // K[u][w] rounded up to T
+    for (int t = threadIdx.x; t < kk * kk; t += blockDim.x) {
+        const int u = t / kk, w = t - (t / kk) * kk;
+        const double kv = P.upK[t];
+        K64[t] = kv;
+        Ks[t] = reinterpret_cast<const T*>(P.upK_t)[t];
+        KsT[w * kk + u] = Ks[t];
+        Khi[t] = from_double_ru<T>(kv);
+    }
+    T* a = reinterpret_cast<T*>(P.a);
+    T* b = reinterpret_cast<T*>(P.b);
+    T* kb = reinterpret_cast<T*>(P.kb_t);
+    T* mu_b = reinterpret_cast<T*>(P.kscratch);               // block-major copies of mu, nu (sweeps only)
+    T* nu_b = mu_b + m;
+    const T* mu_t = reinterpret_cast<const T*>(P.mu_t);
+    const T* nu_t = reinterpret_cast<const T*>(P.nu_t);
+    for (int t = threadIdx.x; t < m; t += blockDim.x) {
+        const int i = blk_pixel(t / kk, t - (t / kk) * kk, n, kap, N);
+        mu_b[t] = mu_t[i];
+        nu_b[t] = nu_t[i];
+        b[t] = T(1);
+    }
+    __syncthreads();
+    T kr0[KK ? KK : 1], kr1[KK ? KK : 1];                     // K[u][.] and K[.][u]
+    if constexpr (KK > 0) {
+        const int u = threadIdx.x % KK;
+#pragma unroll
+        for (int w = 0; w < KK; ++w) { kr0[w] = KsT[w * KK + u]; kr1[w] = Ks[w * KK + u]; }
+    }
+    const T* vt = reinterpret_cast<const T*>(P.val_t);
+    const T* vct = reinterpret_cast<const T*>(P.valc_t);
+    // ---- fine sweeps ------------------------------------------------------
+    for (int sweep = 0; sweep < P.sweeps; ++sweep) {
+        for (int half = 0; half < 2; ++half) {
+            const T* x = half == 0 ? b : a;
+            for (int t = threadIdx.x; t < m; t += blockDim.x) {
+                const int l = t / kk, u = t - (t / kk) * kk;
+                T s;
+                if constexpr (KK > 0) {
+                    s = half == 0 ? row_dot16(x + l * KK, kr0) : row_dot16(x + l * KK, kr1);
+                } else {
+                    const T* kc = (half == 0 ? KsT : Ks) + u;
+                    const T* xr = x + l * kk;
+                    s = T(0);
+                    for (int w = 0; w < kk; ++w) s += kc[w * kk] * xr[w];
+                }
+                kb[t] = s;
+            }
+            __syncthreads();
+            const int* ptr = half == 0 ? P.rowptr : P.colptr;
+            const int* idx = half == 0 ? P.colidx : P.rowidx;
+            const T* val = half == 0 ? vt : vct;
+            const T* src = half == 0 ? mu_b : nu_b;
+            T* dst = half == 0 ? a : b;
+            for (int t = threadIdx.x; t < m; t += blockDim.x) {
+                const int k = t / kk, u = t - (t / kk) * kk;
+                T r = T(0);
+                for (int e = ptr[k]; e < ptr[k + 1]; ++e) r += val[e] * kb[idx[e] * kk + u];
+                dst[t] = r > T(0) ? src[t] / r : T(0);
+            }
+            __syncthreads();
+        }
+    }
+    if (P.a_out || P.b_out)
+        for (int t = threadIdx.x; t < m; t += blockDim.x) {
+            const int i = blk_pixel(t / kk, t - (t / kk) * kk, n, kap, N);
+            if (P.a_out) P.a_out[i] = widen_f32(a[t]);
+            if (P.b_out) P.b_out[i] = widen_f32(b[t]);
+        }
+    __syncthreads();   // the certified pass reuses kscratch (mu_b, nu_b)
+    // ---- certified evaluation (FP64) ---------------------------------------
+    double* klo = P.kscratch;                                 // m each, block-major (mu_b, nu_b are done)
+    double* khi = klo + m;
+    double s_lo = 0.0, s_hi = HUGE_VAL, tv_mu = 0.0, tv_nu = 0.0, res = 0.0;
+    for (int side = 0; side < 2; ++side) {
+        // side 0: mu-hat[k, u] = a[k, u] sum_l pi~_kl sum_w K[u, w] b[l, w]
+        // side 1: nu-hat[l, v] = b[l, v] sum_k pi~_kl sum_w K[w, v] a[k, w]
+        const T* oth = side == 0 ? b : a;
+        const T* own = side == 0 ? a : b;
+        for (int t = threadIdx.x; t < m; t += blockDim.x) {
+            const int l = t / kk, u = t - (t / kk) * kk;
+            double lo = 0.0, hi = 0.0;
+            for (int w = 0; w < kk; ++w) {
+                const double kv = side == 0 ? K64[u * kk + w] : K64[w * kk + u];
+                const double x = widen_f32(oth[l * kk + w]);
+                lo = __fma_rd(kv, x, lo);
+                hi = __fma_ru(kv, x, hi);
+            }
+            klo[t] = lo; khi[t] = hi;
+        }
+        __syncthreads();
+        const int* ptr = side == 0 ? P.rowptr : P.colptr;
+        const int* idx = side == 0 ? P.colidx : P.rowidx;
+        const double* val = side == 0 ? P.val : P.valc;
+        const double* meas = side == 0 ? P.mu : P.nu;
+        // pass 0: bounds of the total mass s; pass 1: the TV sum with them
+        for (int pass = 0; pass < 2; ++pass) {
+            double acc_lo = 0.0, acc_hi = 0.0, acc_tv = 0.0, acc_res = 0.0;
+            for (int t = threadIdx.x; t < m; t += blockDim.x) {
+                const int k = t / kk, u = t - (t / kk) * kk;
+                double rlo = 0.0, rhi = 0.0;
+                for (int e = ptr[k]; e < ptr[k + 1]; ++e) {
+                    rlo = __fma_rd(val[e], klo[idx[e] * kk + u], rlo);
+                    rhi = __fma_ru(val[e], khi[idx[e] * kk + u], rhi);
+                }
+                const double x = widen_f32(own[t]);
+                const double h_lo = __dmul_rd(x, rlo), h_hi = __dmul_ru(x, rhi);
+                if (pass == 0) {
+                    acc_lo = __dadd_rd(acc_lo, h_lo);
+                    acc_hi = __dadd_ru(acc_hi, h_hi);
+                } else {
+                    const int i = blk_pixel(k, u, n, kap, N);
+                    const double mi = meas[i];
+                    const double dev = fmax(0.0, fmax(__dsub_ru(__ddiv_ru(h_hi, s_lo), mi),
+                                                      __dsub_ru(mi, __ddiv_rd(h_lo, s_hi))));
+                    const int r = i / N, c = i - (i / N) * N;
+                    acc_tv = __fma_ru(tv_weight_hi(r, c, N, P.p), dev, acc_tv);
+                    acc_res += fabs(0.5 * (h_lo + h_hi) - mi);
+                }
+            }
+            if (pass == 0) {
+                // both sides enclose the same s: the nu side intersects
+                s_lo = fmax(s_lo, block_reduce_rd(acc_lo, red));
+                s_hi = fmin(s_hi, block_reduce_ru(acc_hi, red));
+            } else {
+                const double tv = block_reduce_ru(acc_tv, red);
+                if (side == 0) tv_mu = tv; else tv_nu = tv;
+                res += block_reduce_rn(acc_res, red);
+            }
+        }
+        __syncthreads();                                      // klo / khi are rewritten by the next side
+    }
+    // ---- cost of the fitted plan over its support, rounded up ---------------
+    // one (entry e = (k, l), source offset u) per thread and step:
+    //   a[k, u] sum_v K[u, v] b[l, v] rho(x_(k,u), y_(l,v))^p in T rounded up,
+    //   weighted by pi~_kl in FP64 rounded up
+    const T* tab = reinterpret_cast<const T*>(P.ctab_hi);
+    double cost = 0.0;
+    const long long q_end = (long long)P.nnz * kk;
+    for (long long q = threadIdx.x; q < q_end; q += blockDim.x) {
+        const int e = (int)(q / kk), u = (int)(q - (long long)e * kk);
+        int lo = 0, hi = P.M;                                 // row of entry e
+        while (hi - lo > 1) { const int mid = (lo + hi) >> 1; if (P.rowptr[mid] <= e) lo = mid; else hi = mid; }
+        const int k = lo, l = P.colidx[e];
+        const int r0 = kap * (k / n - l / n) + u / kap, c0 = kap * (k % n - l % n) + u % kap;
+        const T* kh = Khi + u * kk;
+        const T* br = b + l * kk;
+        T inner = T(0);
+        for (int v1 = 0; v1 < kap; ++v1) {
+            const T* trow = tab + abs(r0 - v1) * N;
+            for (int v2 = 0; v2 < kap; ++v2) {
+                const int v = v1 * kap + v2;
+                inner = fma_ru(mul_ru(kh[v], br[v]), trow[abs(c0 - v2)], inner);
+            }
+        }
+        cost = __fma_ru(P.val[e], widen_f32(mul_ru(a[k * kk + u], inner)), cost);
+    }
+    const double cost_sum = block_reduce_ru(cost, red);
+    if (threadIdx.x == 0) {
+        const double p = P.p;
+        const double scale = (p == 1.0) ? 1.0 : (p == 2.0 ? 2.0 : __dmul_ru(pow(2.0, p - 1.0), 1.0 + 0x1p-49));
+        const double dmu = root_p_ru(__dmul_ru(scale, tv_mu), p);
+        const double dnu = root_p_ru(__dmul_ru(scale, tv_nu), p);
+        const double w_hat_p = s_lo > 0.0 ? __ddiv_ru(cost_sum, s_lo) : HUGE_VAL;
+        const double w_hat = root_p_ru(w_hat_p, p);
+        PairOut& O = outs[P.out_index];
+        O.w_hat_p = w_hat_p;
+        O.delta_mu = dmu;
+        O.delta_nu = dnu;
+        O.ub_primal = __dadd_ru(__dadd_ru(w_hat, dmu), dnu);
+        O.ipf_residual = res;
+        O.sweeps_done = P.sweeps;
+    }
+    // leave a, b in the pixel layout of the other passes (through the KB scratch)
+    for (int side = 0; side < 2; ++side) {
+        T* x = side == 0 ? a : b;
+        for (int t = threadIdx.x; t < m; t += blockDim.x) kb[t] = x[t];
+        __syncthreads();
+        for (int t = threadIdx.x; t < m; t += blockDim.x) x[blk_pixel(t / kk, t - (t / kk) * kk, n, kap, N)] = kb[t];
+        __syncthreads();
+    }
+}
+
+int launch_primalk(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs, int kappa_max,
+                   bool all_kappa4, bool f64, cudaStream_t stream) {
+    if (n_pairs <= 0) return QWB_OK;
+    if (kappa_max > 8) return QWB_ERR_UNSUPPORTED;
+    const int kk = kappa_max * kappa_max;
+    const size_t smem = (size_t)kk * kk * (sizeof(double) + 3 * (f64 ? 8 : 4));
+    auto run = [&](auto kern) -> int {
+        QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<n_pairs, PRIMALK_THREADS, smem, stream>>>(pairs_d, outs_d, pair_ids);
+        QWB_LAUNCHED();
+        return QWB_OK;
+    };
+    if (f64) return all_kappa4 ? run(primalk_kernel<double, 16>) : run(primalk_kernel<double, 0>);
+    return all_kappa4 ? run(primalk_kernel<float, 16>) : run(primalk_kernel<float, 0>);
 }
 
 // --------------------------------------------------------------------------
@@ -2107,21 +2384,6 @@ int launch_sep(const PairDev* pairs_d, const SepItem* items, int n_items, int ph
 // multiply-adds, so lb_p <= the real dual objective of the stored (f, g)
 // (Sec. 3.5, eq. upscaling LB); LB = max(lb_p, 0)^(1/p) rounded down.
 // --------------------------------------------------------------------------
-__device__ __forceinline__ double block_reduce_rd(double v, double* red) {
-    for (int o = 16; o > 0; o >>= 1) v = __dadd_rd(v, __shfl_down_sync(0xffffffffu, v, o));
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = __dadd_rd(s, red[w]);
-        red[32] = s;
-    }
-    __syncthreads();
-    return red[32];
-}
-
 template <typename T>
 __global__ void lbsum_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
                              const int* __restrict__ pair_ids, int side) {

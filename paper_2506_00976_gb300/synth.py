@@ -144,3 +144,15 @@ def uneven_workload(n_pairs: int = 200, workload: int = 3):
         nu = make_measure(N, cls, workload, 2 * t + 1)
         out.append({"N": N, "kappa": kappa, "p": p, "cls": cls, "mu": mu, "nu": nu})
     return out
+
+
+def gaussian_offset_kernel(kappa: int, sigma: float) -> np.ndarray:
+    """An upscaling kernel input: K[u, v] over the in-block offsets u, v
+    (row-major in the kappa x kappa block) proportional to
+    exp(-|u - v|^2 / (2 sigma^2)), scaled to sum 1 -- an input of the
+    general-kernel primal pass, like the measures above."""
+    g = np.arange(kappa)
+    r, c = np.repeat(g, kappa), np.tile(g, kappa)
+    d2 = (r[:, None] - r[None, :]) ** 2 + (c[:, None] - c[None, :]) ** 2
+    K = np.exp(-d2 / (2.0 * sigma * sigma))
+    return K / K.sum()
