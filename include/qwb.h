@@ -186,10 +186,13 @@ int qwb_primal_upscale_ipf(qwb_ctx* ctx, const qwb_problem* prob, const double* 
  * paper's kernels sum to 1); d = 2 and kappa <= 8.  No block-scalar shortcut
  * exists for such K: MIXED and F64 run `sweeps` IPF sweeps on the fine
  * vectors in FP32 / FP64, and the bound is certified for the plan
- * diag(a) pi-hat diag(b) with those scalings as they are: interval bounds
- * (directed rounding, FP64) of its marginals mu-hat, nu-hat and of its total
- * mass s, the cost over its support rounded up and divided by s rounded down,
- * and the weighted-TV corrections between mu-hat / s, nu-hat / s and mu, nu.
+ * diag(a) pi-hat' diag(b) with those scalings as they are, pi-hat' built with
+ * the kernel the sweeps used (K rounded to FP32 for MIXED, K for F64; every
+ * positive kernel gives a valid bound): enclosures (FP64 with directed
+ * rounding and a-priori error bounds) of its marginals mu-hat, nu-hat and of
+ * its total mass s, the cost over its support rounded up and divided by s
+ * rounded down, and the weighted-TV corrections between mu-hat / s,
+ * nu-hat / s and mu, nu.
  * Other arguments, outputs and errors as qwb_primal_upscale_ipf, plus
  * UNSUPPORTED (d = 3 or kappa > 8) and INVALID_ARG (null or non-positive K). */
 int qwb_primal_upscale_ipf_kernel(qwb_ctx* ctx, const qwb_problem* prob, const double* mu_d,

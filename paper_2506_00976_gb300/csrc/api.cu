@@ -215,7 +215,7 @@ struct qwb_batch {
     std::vector<char> upk_on;           // per pair
     char* upk_mem = nullptr;
     int* prim_ids_d = nullptr;
-    int n_uni = 0, n_upk = 0, upk_kappa_max = 0;
+    int n_uni = 0, n_upk = 0, upk_kappa_max = 0, upk_M_max = 0, upk_m_max = 0;
     bool upk_all4 = false;
     std::vector<int> prep_off, prep_cnt, pix_off, pix_cnt, cbar_off, cbar_cnt, ct_off, ct_cnt;
     int n_prep = 0, n_pix = 0, n_cbar = 0, n_ct_b = 0;
@@ -750,7 +750,8 @@ static int enqueue_fine(qwb_batch* b, bool batched, cudaStream_t s) {
             if ((st = launch_support_num(b->pairs_d, uni, n_uni, 2 * b->M_max, b->f64, s))) return st;
             if ((st = launch_primal(b->pairs_d, b->outs_d, uni, n_uni, b->M_max, 0, b->f64, s))) return st;
             if (b->n_upk && (st = launch_primalk(b->pairs_d, b->outs_d, b->prim_ids_d + b->n_uni, b->n_upk,
-                                                 b->upk_kappa_max, b->upk_all4, b->f64, s)))
+                                                 b->upk_kappa_max, b->upk_M_max, 0, b->upk_m_max, b->upk_all4,
+                                                 b->f64, s)))
                 return st;
         }
         if ((st = mark(b, 4, s))) return st;
@@ -790,7 +791,9 @@ static int enqueue_fine(qwb_batch* b, bool batched, cudaStream_t s) {
         const int M = b->Ms[t];
         if (do_primal && b->upk_on[t]) {
             const int kap = b->probs[t].kappa;
-            if ((st = launch_primalk(b->pairs_d, b->outs_d, id, 1, kap, kap == 4, b->f64, s))) return st;
+            if ((st = launch_primalk(b->pairs_d, b->outs_d, id, 1, kap, M, 0, b->probs[t].N * b->probs[t].N,
+                                     kap == 4, b->f64, s)))
+                return st;
         } else if (do_primal) {
             if ((st = launch_support_num(b->pairs_d, id, 1, 2 * M, b->f64, s))) return st;
             if (b->ipf_group_of[t] >= 0 && b->ipf_groups[b->ipf_group_of[t]].C > 0) {
@@ -1517,7 +1520,7 @@ int qwb_batch_set_upscale_kernel(qwb_batch* b, int32_t kappa, const double* K_d)
         if (which[t] < 0) continue;
         const size_t m = (size_t)b->probs[t].N * b->probs[t].N;
         s_off[t] = off;
-        off = align_up(off + align_up(m * tsz) + 16 * m);
+        off = align_up(off + align_up(2 * m * tsz) + 16 * m);
     }
     const size_t ids_off = off;
     off = align_up(off + sizeof(int) * b->n);
@@ -1535,6 +1538,8 @@ int qwb_batch_set_upscale_kernel(qwb_batch* b, int32_t kappa, const double* K_d)
     }
     std::vector<int> uni, kp;
     b->upk_kappa_max = 0;
+    b->upk_M_max = 0;
+    b->upk_m_max = 0;
     b->upk_all4 = true;
     for (int t = 0; t < b->n; ++t) {
         PairDev& P = b->pairs_h[t];
@@ -1549,9 +1554,11 @@ int qwb_batch_set_upscale_kernel(qwb_batch* b, int32_t kappa, const double* K_d)
         P.upK = (const double*)(b->upk_mem + k_off[which[t]]);
         P.upK_t = b->upk_mem + k_off[which[t]] + 8 * kbytes;
         P.kb_t = b->upk_mem + s_off[t];
-        P.kscratch = (double*)(b->upk_mem + s_off[t] + align_up(m * tsz));
+        P.kscratch = (double*)(b->upk_mem + s_off[t] + align_up(2 * m * tsz));
         kp.push_back(t);
         b->upk_kappa_max = std::max(b->upk_kappa_max, b->probs[t].kappa);
+        b->upk_M_max = std::max(b->upk_M_max, b->Ms[t]);
+        b->upk_m_max = std::max(b->upk_m_max, b->probs[t].N * b->probs[t].N);
         b->upk_all4 = b->upk_all4 && b->probs[t].kappa == 4;
     }
     b->n_uni = (int)uni.size();
@@ -1752,8 +1759,9 @@ static int primal_single(qwb_ctx* ctx, const qwb_problem* prob, const double* mu
     char* kbuf = nullptr;
     const size_t m_pts = (size_t)prob->N * prob->N;
     const size_t tsz = b->f64 ? 8 : 4;
+    // [K FP64 | K pass type | KB, KA (2 m_pts, pass type) | evaluation scratch (2 m_pts FP64)]
     const size_t k64_off = 0, kt_off = 8 * (size_t)kk * kk, kb_off = kt_off + 8 * (size_t)kk * kk,
-                 ks_off = kb_off + 8 * m_pts, k_total = ks_off + 16 * m_pts;
+                 ks_off = kb_off + 2 * tsz * m_pts, k_total = ks_off + 16 * m_pts;
     struct KRelease {
         char* d;
         ~KRelease() { if (d) cudaFree(d); }
@@ -1789,7 +1797,9 @@ static int primal_single(qwb_ctx* ctx, const qwb_problem* prob, const double* mu
     QWB_CUDA(cudaMemsetAsync(b->outs_d, 0, sizeof(PairOut), s));
     if ((st = single_validate(b, s))) return st;
     if (K_d) {
-        if ((st = launch_primalk(b->pairs_d, b->outs_d, b->pair_ids_d, 1, prob->kappa, prob->kappa == 4, b->f64, s))) return st;
+        if ((st = launch_primalk(b->pairs_d, b->outs_d, b->pair_ids_d, 1, prob->kappa, M, pi_nnz,
+                                      prob->N * prob->N, prob->kappa == 4,
+                                      b->f64, s))) return st;
     } else {
         if ((st = launch_support_num(b->pairs_d, b->pair_ids_d, 1, pi_nnz, b->f64, s))) return st;
         if ((st = launch_primal(b->pairs_d, b->outs_d, b->pair_ids_d, 1, M, pi_nnz, b->f64, s))) return st;

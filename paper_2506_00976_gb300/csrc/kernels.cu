@@ -110,6 +110,18 @@ __device__ __forceinline__ double tv_weight_hi(int r, int c, int N, double p, in
     return __dmul_ru(pow(d2, 0.5 * p), 1.0 + 0x1p-49);
 }
 
+// The same bracket without FP64 arithmetic for p = 1, 2 when N <= 2896:
+// 4 |x - x-bar|^2 is an integer below 2^24, exact in FP32; p = 2 returns it
+// quartered (exact), p = 1 its square root rounded up, halved (exact).
+__device__ __forceinline__ double tv_weight_hi_fast(int r, int c, int N, double p) {
+    if ((p == 2.0 || p == 1.0) && N <= 2896) {
+        const int dr = 2 * r - (N - 1), dc = 2 * c - (N - 1);
+        const float d4 = (float)(dr * dr + dc * dc);
+        return widen_f32(p == 2.0 ? 0.25f * d4 : 0.5f * __fsqrt_ru(d4));
+    }
+    return tv_weight_hi(r, c, N, p);
+}
+
 // --------------------------------------------------------------------------
 // prepare: SumPool (Sec. 2.2) -- mu~_k = mu(X_k) in FP64, nearest and
 // round-down sums, plus validation (finite, non-negative, mass).
@@ -1343,75 +1355,106 @@ int launch_primal(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, 
 // row-major offsets of i, j in their blocks.  One CTA per pair.  The
 // scalings a, b live block-major ([block][offset], position t = k kk + u with
 // kk = kappa^2), so a block's values are one contiguous row.
-//   fine sweeps (type T): a = mu / (pi-hat b), b = nu / (pi-hat^T a), each
-//     half in two steps: KB[l, u] = sum_w K[u, w] b[l, w] for every block
-//     (the b half: sum_w K[w, u] a[k, w]), then r[k, u] = sum_l pi~_kl
-//     KB[l, u] over the plan row (the b half: the plan column), dst = src / r;
-//   certified evaluation (FP64 intervals, directed rounding) of the plan
-//     diag(a) pi-hat diag(b) with the final a, b as they are: bounds of its
-//     marginals and of its total mass s, its cost over the support rounded
-//     up and divided by s rounded down (the plan over s couples the
+//   fine sweeps (type T): a = mu / (pi-hat b), b = nu / (pi-hat^T a) from
+//     b = 1.  With KB[l, u] = sum_w K[u, w] b[l, w] (and KA[k, v] = sum_w
+//     K[w, v] a[k, w]) the a half is r[k, u] = sum_l pi~_kl KB[l, u],
+//     a = mu / r, the b half the same with KA and the plan's columns.
+//   certified evaluation (FP64 bounds, directed rounding) of the plan
+//     diag(a) pi-hat' diag(b) with the final a, b as they are, pi-hat' built
+//     with the kernel K' in the pass type (the FP32-rounded K for MIXED, K
+//     itself for F64; any positive kernel gives a valid bound): bounds of
+//     its marginals and of its total mass s, its cost over the support
+//     rounded up and divided by s rounded down (the plan over s couples the
 //     probability measures mu-hat / s and nu-hat / s), and the weighted-TV
 //     corrections between those and mu, nu.
-// KK = 16 (kappa 4) keeps the thread's two K rows in registers (its offset
-// u = thread index mod 16 is the same at every position it visits).
+// FP32 with kappa 2, 4 or 8 (kk = 4, 16, 64) runs the fused sweep: a thread
+// owns the four consecutive offsets 4g..4g+3 of one block, the q4 = kk / 4
+// lanes of a block hold its whole row, so after r and the new scaling the
+// next half's product (KA from a, KB from b) follows from warp shuffles of
+// that row -- one barrier per half, KA and KB double-buffered (shared memory
+// when they fit).  Other cases run two steps per half (product, barrier,
+// gather).
 // --------------------------------------------------------------------------
-constexpr int PRIMALK_THREADS = 512;
+constexpr int PRIMALK_THREADS_F32 = 1024;
+constexpr int PRIMALK_THREADS_F64 = 512;
+
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 __device__ __forceinline__ int blk_pixel(int k, int u, int n, int kap, int N) {
     return ((k / n) * kap + u / kap) * N + (k % n) * kap + u % kap;
 }
 
-// sum_w kr[w] x[w] over one contiguous 16-entry block row
-__device__ __forceinline__ float row_dot16(const float* __restrict__ x, const float* kr) {
-    const float4* x4 = reinterpret_cast<const float4*>(x);
-    float s = 0.0f;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const float4 v = x4[q];
-        s = fmaf(kr[4 * q], v.x, s);
-        s = fmaf(kr[4 * q + 1], v.y, s);
-        s = fmaf(kr[4 * q + 2], v.z, s);
-        s = fmaf(kr[4 * q + 3], v.w, s);
-    }
-    return s;
+// s / r for the FP32 sweeps (0 where r <= 0): the approximate reciprocal
+// refined by one Newton step, within a few ulp (the sweeps are not part of
+// the certificate, which takes the final scalings as they are); tiny r takes
+// and huge r take the IEEE division, so no denormal is flushed.
+__device__ __forceinline__ float ipf_div(float s, float r) {
+    if (!(r > 0x1p-100f && r < 0x1p100f)) return r > 0.f ? s / r : 0.f;
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r));
+    y = fmaf(y, fmaf(-r, y, 1.0f), y);
+    return s * y;
 }
-__device__ __forceinline__ double row_dot16(const double* __restrict__ x, const double* kr) {
-    const double2* x2 = reinterpret_cast<const double2*>(x);
-    double s = 0.0;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const double2 v = x2[q];
-        s = fma(kr[2 * q], v.x, s);
-        s = fma(kr[2 * q + 1], v.y, s);
-    }
-    return s;
+
+// err-free product and sum in FP32 (Dekker / Knuth via FMA)
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& t) {
+    s = a + b;
+    const float bp = s - a;
+    t = (a - (s - bp)) + (b - bp);
 }
 
 template <typename T, int KK>
-__global__ void __launch_bounds__(PRIMALK_THREADS, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(sizeof(T) == 4 ? PRIMALK_THREADS_F32 : PRIMALK_THREADS_F64, 1)
 primalk_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
-               const int* __restrict__ pair_ids) {
+               const int* __restrict__ pair_ids, int csr_cap, int kk_max, int kb_cap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[33];
     const PairDev& P = pairs[pair_ids[blockIdx.x]];
-    const int N = P.N, kap = P.kappa, n = P.n, m = P.m;
-    const int kk = KK ? KK : kap * kap;
-    double* K64 = reinterpret_cast<double*>(smem_raw);       // K[u][w], FP64
-    T* Ks = reinterpret_cast<T*>(K64 + kk * kk);              // K[u][w], type T (read as K[w][u])
-    T* KsT = Ks + kk * kk;                                    // K[u][w] at [w][u] (read as K[u][w])
-    T* Khi = KsT + kk * kk;                                   // K[u][w] rounded up to T
+    const int N = P.N, kap = P.kappa, n = P.n, m = P.m, M = P.M;
+    const int kk = KK ? KK : kap * kap;                       // kk_max: the launch's smem layout
+    const int q4 = KK ? KK / 4 : kk >> 2;                      // float4s per block row
+    const bool fused = sizeof(T) == 4 && (kk == 4 || kk == 16 || kk == 64);
+    // shared memory: [K (T) | K^T (T) | KB, KA (kb_cap each, when > 0) | staged plan]
+    const size_t kq = (size_t)kk_max * kk_max;
+    const size_t o_kst = align16(sizeof(T) * kq), o_kb = 2 * align16(sizeof(T) * kq),
+                 o_csr = o_kb + 2 * align16(sizeof(T) * (size_t)kb_cap);
+    T* Ks = reinterpret_cast<T*>(smem_raw);                   // K'[u][w] (row w: K'[w][.])
+    T* KsT = reinterpret_cast<T*>(smem_raw + o_kst);          // row w: K'[.][w]
     for (int t = threadIdx.x; t < kk * kk; t += blockDim.x) {
         const int u = t / kk, w = t - (t / kk) * kk;
-        const double kv = P.upK[t];
-        K64[t] = kv;
-        Ks[t] = reinterpret_cast<const T*>(P.upK_t)[t];
-        KsT[w * kk + u] = Ks[t];
-        Khi[t] = from_double_ru<T>(kv);
+        const T kt = reinterpret_cast<const T*>(P.upK_t)[t];
+        Ks[t] = kt;
+        KsT[w * kk + u] = kt;
+    }
+    // the coarse plan's CSR and CSC, staged in shared memory when they fit
+    const int* rp = P.rowptr;
+    const int* ci = P.colidx;
+    const int* cp = P.colptr;
+    const int* ri = P.rowidx;
+    const T* vt = reinterpret_cast<const T*>(P.val_t);
+    const T* vct = reinterpret_cast<const T*>(P.valc_t);
+    const double* v64 = P.val;
+    if (P.nnz <= csr_cap) {
+        // [v64 (8 cap) | v, vc (T, cap each) | rowptr, colptr (M_max + 1 each) | colidx, rowidx (cap each)]
+        double* v64_s = reinterpret_cast<double*>(smem_raw + o_csr);
+        T* v_s = reinterpret_cast<T*>(v64_s + csr_cap);
+        T* vc_s = v_s + csr_cap;
+        int* rp_s = reinterpret_cast<int*>(vc_s + csr_cap);
+        int* cp_s = rp_s + (M + 1);
+        int* ci_s = cp_s + (M + 1);
+        int* ri_s = ci_s + csr_cap;
+        for (int q = threadIdx.x; q <= M; q += blockDim.x) { rp_s[q] = rp[q]; cp_s[q] = cp[q]; }
+        for (int e = threadIdx.x; e < P.nnz; e += blockDim.x) {
+            ci_s[e] = ci[e]; ri_s[e] = ri[e]; v_s[e] = vt[e]; vc_s[e] = vct[e]; v64_s[e] = v64[e];
+        }
+        rp = rp_s; ci = ci_s; cp = cp_s; ri = ri_s; vt = v_s; vct = vc_s; v64 = v64_s;
     }
     T* a = reinterpret_cast<T*>(P.a);
     T* b = reinterpret_cast<T*>(P.b);
-    T* kb = reinterpret_cast<T*>(P.kb_t);
+    // KB (read by the a half) and KA (read by the b half)
+    T* kbB = m <= kb_cap ? reinterpret_cast<T*>(smem_raw + o_kb) : reinterpret_cast<T*>(P.kb_t);
+    T* kbA = m <= kb_cap ? reinterpret_cast<T*>(smem_raw + o_kb + align16(sizeof(T) * (size_t)kb_cap))
+                         : reinterpret_cast<T*>(P.kb_t) + m;
     T* mu_b = reinterpret_cast<T*>(P.kscratch);               // block-major copies of mu, nu (sweeps only)
     T* nu_b = mu_b + m;
     const T* mu_t = reinterpret_cast<const T*>(P.mu_t);
@@ -1423,44 +1466,105 @@ primalk_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
         b[t] = T(1);
     }
     __syncthreads();
-    T kr0[KK ? KK : 1], kr1[KK ? KK : 1];                     // K[u][.] and K[.][u]
-    if constexpr (KK > 0) {
-        const int u = threadIdx.x % KK;
-#pragma unroll
-        for (int w = 0; w < KK; ++w) { kr0[w] = KsT[w * KK + u]; kr1[w] = Ks[w * KK + u]; }
-    }
-    const T* vt = reinterpret_cast<const T*>(P.val_t);
-    const T* vct = reinterpret_cast<const T*>(P.valc_t);
     // ---- fine sweeps ------------------------------------------------------
-    for (int sweep = 0; sweep < P.sweeps; ++sweep) {
-        for (int half = 0; half < 2; ++half) {
-            const T* x = half == 0 ? b : a;
-            for (int t = threadIdx.x; t < m; t += blockDim.x) {
-                const int l = t / kk, u = t - (t / kk) * kk;
-                T s;
-                if constexpr (KK > 0) {
-                    s = half == 0 ? row_dot16(x + l * KK, kr0) : row_dot16(x + l * KK, kr1);
-                } else {
-                    const T* kc = (half == 0 ? KsT : Ks) + u;
-                    const T* xr = x + l * kk;
-                    s = T(0);
-                    for (int w = 0; w < kk; ++w) s += kc[w * kk] * xr[w];
+    if (fused) {
+        const float4* Ks4 = reinterpret_cast<const float4*>(Ks);
+        const float4* KsT4 = reinterpret_cast<const float4*>(KsT);
+        const int n_items = m >> 2;
+        const int n_iter = (n_items + blockDim.x - 1) / blockDim.x;   // the same for every thread
+        const int lane = threadIdx.x & 31;
+        // b = 1: KB[l, u] = sum_w K'[u][w]
+        for (int it = threadIdx.x; it < n_items; it += blockDim.x) {
+            const int g = it % q4;
+            float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int w = 0; w < kk; ++w) {
+                const float4 kv = KsT4[w * q4 + g];
+                s.x += kv.x; s.y += kv.y; s.z += kv.z; s.w += kv.w;
+            }
+            reinterpret_cast<float4*>(kbB)[it] = s;
+        }
+        __syncthreads();
+        for (int sweep = 0; sweep < P.sweeps; ++sweep) {
+            for (int half = 0; half < 2; ++half) {
+                const int* ptr = half == 0 ? rp : cp;
+                const int* idx = half == 0 ? ci : ri;
+                const float* val = reinterpret_cast<const float*>(half == 0 ? vt : vct);
+                const float4* src4 = reinterpret_cast<const float4*>(half == 0 ? mu_b : nu_b);
+                float4* dst4 = reinterpret_cast<float4*>(half == 0 ? a : b);
+                const float4* kin4 = reinterpret_cast<const float4*>(half == 0 ? kbB : kbA);
+                float4* kout4 = reinterpret_cast<float4*>(half == 0 ? kbA : kbB);
+                const float4* Kn4 = half == 0 ? Ks4 : KsT4;    // a -> KA (rows K'[w][.]); b -> KB (rows K'[.][w])
+                for (int jt = 0; jt < n_iter; ++jt) {
+                    const int it = threadIdx.x + jt * blockDim.x;
+                    const bool valid = it < n_items;
+                    const int k = it / q4, g = it - (it / q4) * q4;
+                    float4 xv = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (valid) {
+                        float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+                        for (int e = ptr[k]; e < ptr[k + 1]; ++e) {
+                            const float v = val[e];
+                            const float4 kv = kin4[idx[e] * q4 + g];
+                            r.x = fmaf(v, kv.x, r.x);
+                            r.y = fmaf(v, kv.y, r.y);
+                            r.z = fmaf(v, kv.z, r.z);
+                            r.w = fmaf(v, kv.w, r.w);
+                        }
+                        const float4 sv = src4[it];
+                        xv.x = ipf_div(sv.x, r.x);
+                        xv.y = ipf_div(sv.y, r.y);
+                        xv.z = ipf_div(sv.z, r.z);
+                        xv.w = ipf_div(sv.w, r.w);
+                        dst4[it] = xv;
+                    }
+                    // the block row sits in lanes lane - g .. lane - g + q4 - 1 (rows
+                    // never straddle the valid / invalid boundary: n_items = M q4)
+                    const int row0 = lane - g;
+                    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (int w4 = 0; w4 < q4; ++w4) {
+                        const float x0 = __shfl_sync(0xffffffffu, xv.x, row0 + w4);
+                        const float x1 = __shfl_sync(0xffffffffu, xv.y, row0 + w4);
+                        const float x2 = __shfl_sync(0xffffffffu, xv.z, row0 + w4);
+                        const float x3 = __shfl_sync(0xffffffffu, xv.w, row0 + w4);
+                        const float4 k0 = Kn4[(4 * w4) * q4 + g], k1 = Kn4[(4 * w4 + 1) * q4 + g];
+                        const float4 k2 = Kn4[(4 * w4 + 2) * q4 + g], k3 = Kn4[(4 * w4 + 3) * q4 + g];
+                        s.x = fmaf(k3.x, x3, fmaf(k2.x, x2, fmaf(k1.x, x1, fmaf(k0.x, x0, s.x))));
+                        s.y = fmaf(k3.y, x3, fmaf(k2.y, x2, fmaf(k1.y, x1, fmaf(k0.y, x0, s.y))));
+                        s.z = fmaf(k3.z, x3, fmaf(k2.z, x2, fmaf(k1.z, x1, fmaf(k0.z, x0, s.z))));
+                        s.w = fmaf(k3.w, x3, fmaf(k2.w, x2, fmaf(k1.w, x1, fmaf(k0.w, x0, s.w))));
+                    }
+                    if (valid) kout4[it] = s;
                 }
-                kb[t] = s;
+                __syncthreads();
             }
-            __syncthreads();
-            const int* ptr = half == 0 ? P.rowptr : P.colptr;
-            const int* idx = half == 0 ? P.colidx : P.rowidx;
-            const T* val = half == 0 ? vt : vct;
-            const T* src = half == 0 ? mu_b : nu_b;
-            T* dst = half == 0 ? a : b;
-            for (int t = threadIdx.x; t < m; t += blockDim.x) {
-                const int k = t / kk, u = t - (t / kk) * kk;
-                T r = T(0);
-                for (int e = ptr[k]; e < ptr[k + 1]; ++e) r += val[e] * kb[idx[e] * kk + u];
-                dst[t] = r > T(0) ? src[t] / r : T(0);
+        }
+    } else {
+        T* kb = kbB;
+        for (int sweep = 0; sweep < P.sweeps; ++sweep) {
+            for (int half = 0; half < 2; ++half) {
+                const T* x = half == 0 ? b : a;
+                const T* Kx = half == 0 ? KsT : Ks;
+                for (int t = threadIdx.x; t < m; t += blockDim.x) {
+                    const int l = t / kk, u = t - (t / kk) * kk;
+                    const T* kc = Kx + u;
+                    const T* xr = x + l * kk;
+                    T acc = T(0);
+                    for (int w = 0; w < kk; ++w) acc += kc[w * kk] * xr[w];
+                    kb[t] = acc;
+                }
+                __syncthreads();
+                const int* ptr = half == 0 ? rp : cp;
+                const int* idx = half == 0 ? ci : ri;
+                const T* val = half == 0 ? vt : vct;
+                const T* src = half == 0 ? mu_b : nu_b;
+                T* dst = half == 0 ? a : b;
+                for (int t = threadIdx.x; t < m; t += blockDim.x) {
+                    const int k = t / kk, u = t - (t / kk) * kk;
+                    T r = T(0);
+                    for (int e = ptr[k]; e < ptr[k + 1]; ++e) r += val[e] * kb[idx[e] * kk + u];
+                    dst[t] = r > T(0) ? src[t] / r : T(0);
+                }
+                __syncthreads();
             }
-            __syncthreads();
         }
     }
     if (P.a_out || P.b_out)
@@ -1469,101 +1573,179 @@ primalk_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
             if (P.a_out) P.a_out[i] = widen_f32(a[t]);
             if (P.b_out) P.b_out[i] = widen_f32(b[t]);
         }
-    __syncthreads();   // the certified pass reuses kscratch (mu_b, nu_b)
-    // ---- certified evaluation (FP64) ---------------------------------------
-    double* klo = P.kscratch;                                 // m each, block-major (mu_b, nu_b are done)
-    double* khi = klo + m;
-    double s_lo = 0.0, s_hi = HUGE_VAL, tv_mu = 0.0, tv_nu = 0.0, res = 0.0;
+    // ---- certified evaluation -----------------------------------------------
+    // Per side: each marginal entry mu-hat_i (nu-hat_i) is evaluated as
+    // h_i = x_i sum_e pi~_e kd_e, kd = sum_w K' x' (non-negative terms), with
+    // |mu-hat_i - h_i| <= rel h_i + slack.  FP64: kd by FP64 fused
+    // multiply-adds; FP32 scalings: kd by the compensated dot product Dot2 of
+    // Ogita, Rump and Oishi (Accurate sum and dot product, SIAM J. Sci.
+    // Comput. 26, 2005; error-free products and sums, kept as hi + lo), within
+    // a relative 2 gamma_(2kk)^2 (gamma_n = n u / (1 - n u), u = 2^-24) plus an
+    // absolute kk 2^-140 (FP32 underflow).  The gather and the product by x_i
+    // add deg + 2 FP64 roundings (deg: the plan's largest row or column
+    // degree), a relative (deg + 3) 2^-52 (Higham, Accuracy and Stability of
+    // Numerical Algorithms, Sec. 3.1); 2^-1000 covers FP64 underflow.
+    // From them: the total mass s within S_h (1 +- (rel + gamma_h)) +- m slack
+    // (S_h the round-to-nearest sum of the h_i, gamma_h its summation bound),
+    // the s-free sums
+    // A = sum_i w_i |mu-hat_i - mu_i| <= sum_i w_i (|h_i - mu_i| + rel h_i)
+    // + slack sum_i w_i and B = sum_i w_i mu_i (the SumPool pass's per-block
+    // bounds), and sum_i w_i |mu-hat_i / s - mu_i| <= A / s + B |1 / s - 1|.
+    int deg = 0;
+    for (int q = threadIdx.x; q < M; q += blockDim.x) deg = max(deg, max(rp[q + 1] - rp[q], cp[q + 1] - cp[q]));
+    for (int o = 16; o > 0; o >>= 1) deg = max(deg, __shfl_xor_sync(0xffffffffu, deg, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)deg;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double d = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) d = fmax(d, red[w]);
+        red[32] = d;
+    }
+    __syncthreads();
+    deg = (int)red[32];
+    __syncthreads();
+    double rel;                                               // relative enclosure of each entry
+    double kd_abs;                                            // absolute enclosure of each kd
+    if (sizeof(T) == 4) {
+        const double g2 = (2.0 * kk * 0x1p-24) / (1.0 - 2.0 * kk * 0x1p-24);
+        rel = __dadd_ru(__dmul_ru(2.0, __dmul_ru(g2, g2)), (double)(deg + 3) * 0x1p-52);
+        kd_abs = (double)kk * 0x1p-140;
+    } else {
+        rel = (double)(kk + deg + 3) * 0x1p-52;
+        kd_abs = 0.0;
+    }
+    // the round-to-nearest sum S_h: each h_i meets at most m / blockDim + 40
+    // additions (per thread, warp shuffles, warps), Higham Sec. 4.2
+    const double gam_m = (double)((m + blockDim.x - 1) / blockDim.x + 42) * 0x1p-52;
+    const double w_sum_hi = __dmul_ru((double)m, tv_weight_hi(0, 0, N, P.p));   // >= sum_i w_i (corner = max)
+    double* kd = P.kscratch;                                  // m, block-major (mu_b, nu_b are done)
+    double s_lo = 0.0, s_hi = HUGE_VAL, A_mu = 0.0, A_nu = 0.0, B_mu = 0.0, B_nu = 0.0, res = 0.0;
     for (int side = 0; side < 2; ++side) {
-        // side 0: mu-hat[k, u] = a[k, u] sum_l pi~_kl sum_w K[u, w] b[l, w]
-        // side 1: nu-hat[l, v] = b[l, v] sum_k pi~_kl sum_w K[w, v] a[k, w]
+        // side 0: mu-hat[k, u] = a[k, u] sum_l pi~_kl sum_w K'[u, w] b[l, w]
+        // side 1: nu-hat[l, v] = b[l, v] sum_k pi~_kl sum_w K'[w, v] a[k, w]
         const T* oth = side == 0 ? b : a;
         const T* own = side == 0 ? a : b;
-        for (int t = threadIdx.x; t < m; t += blockDim.x) {
-            const int l = t / kk, u = t - (t / kk) * kk;
-            double lo = 0.0, hi = 0.0;
-            for (int w = 0; w < kk; ++w) {
-                const double kv = side == 0 ? K64[u * kk + w] : K64[w * kk + u];
-                const double x = widen_f32(oth[l * kk + w]);
-                lo = __fma_rd(kv, x, lo);
-                hi = __fma_ru(kv, x, hi);
+        const T* Kx = side == 0 ? KsT : Ks;                   // row w over the output offsets
+        if (sizeof(T) == 4 && (kk & 3) == 0) {
+            const float4* K4 = reinterpret_cast<const float4*>(Kx);
+            for (int it = threadIdx.x; it < (m >> 2); it += blockDim.x) {
+                const int l = it / q4, g = it - (it / q4) * q4;
+                const float* xr = reinterpret_cast<const float*>(oth) + (size_t)l * kk;
+                float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+                for (int w = 0; w < kk; ++w) {
+                    const float x = xr[w];
+                    const float4 kv = K4[w * q4 + g];
+                    const float kc[4] = {kv.x, kv.y, kv.z, kv.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float pr = kc[j] * x;
+                        const float pe = fmaf(kc[j], x, -pr);
+                        float s, t;
+                        two_sum_f(hi[j], pr, s, t);
+                        hi[j] = s;
+                        lo[j] += t + pe;
+                    }
+                }
+                double2* o2 = reinterpret_cast<double2*>(kd) + 2 * it;
+                o2[0] = make_double2(widen_f32(hi[0]) + widen_f32(lo[0]), widen_f32(hi[1]) + widen_f32(lo[1]));
+                o2[1] = make_double2(widen_f32(hi[2]) + widen_f32(lo[2]), widen_f32(hi[3]) + widen_f32(lo[3]));
             }
-            klo[t] = lo; khi[t] = hi;
+        } else {
+            for (int t = threadIdx.x; t < m; t += blockDim.x) {
+                const int l = t / kk, u = t - (t / kk) * kk;
+                const T* xr = oth + (size_t)l * kk;
+                double s = 0.0;
+                for (int w = 0; w < kk; ++w) s = fma(widen_f32(Kx[w * kk + u]), widen_f32(xr[w]), s);
+                kd[t] = s;
+            }
         }
         __syncthreads();
-        const int* ptr = side == 0 ? P.rowptr : P.colptr;
-        const int* idx = side == 0 ? P.colidx : P.rowidx;
+        const int* ptr = side == 0 ? rp : cp;
+        const int* idx = side == 0 ? ci : ri;
         const double* val = side == 0 ? P.val : P.valc;
         const double* meas = side == 0 ? P.mu : P.nu;
-        // pass 0: bounds of the total mass s; pass 1: the TV sum with them
-        for (int pass = 0; pass < 2; ++pass) {
-            double acc_lo = 0.0, acc_hi = 0.0, acc_tv = 0.0, acc_res = 0.0;
-            for (int t = threadIdx.x; t < m; t += blockDim.x) {
-                const int k = t / kk, u = t - (t / kk) * kk;
-                double rlo = 0.0, rhi = 0.0;
-                for (int e = ptr[k]; e < ptr[k + 1]; ++e) {
-                    rlo = __fma_rd(val[e], klo[idx[e] * kk + u], rlo);
-                    rhi = __fma_ru(val[e], khi[idx[e] * kk + u], rhi);
-                }
-                const double x = widen_f32(own[t]);
-                const double h_lo = __dmul_rd(x, rlo), h_hi = __dmul_ru(x, rhi);
-                if (pass == 0) {
-                    acc_lo = __dadd_rd(acc_lo, h_lo);
-                    acc_hi = __dadd_ru(acc_hi, h_hi);
-                } else {
-                    const int i = blk_pixel(k, u, n, kap, N);
-                    const double mi = meas[i];
-                    const double dev = fmax(0.0, fmax(__dsub_ru(__ddiv_ru(h_hi, s_lo), mi),
-                                                      __dsub_ru(mi, __ddiv_rd(h_lo, s_hi))));
-                    const int r = i / N, c = i - (i / N) * N;
-                    acc_tv = __fma_ru(tv_weight_hi(r, c, N, P.p), dev, acc_tv);
-                    acc_res += fabs(0.5 * (h_lo + h_hi) - mi);
-                }
-            }
-            if (pass == 0) {
-                // both sides enclose the same s: the nu side intersects
-                s_lo = fmax(s_lo, block_reduce_rd(acc_lo, red));
-                s_hi = fmin(s_hi, block_reduce_ru(acc_hi, red));
-            } else {
-                const double tv = block_reduce_ru(acc_tv, red);
-                if (side == 0) tv_mu = tv; else tv_nu = tv;
-                res += block_reduce_rn(acc_res, red);
-            }
+        double acc_h = 0.0, acc_A = 0.0, acc_res = 0.0, x_max = 0.0;
+        for (int t = threadIdx.x; t < m; t += blockDim.x) {
+            const int k = t / kk, u = t - (t / kk) * kk;
+            double r = 0.0;
+            for (int e = ptr[k]; e < ptr[k + 1]; ++e) r = fma(val[e], kd[idx[e] * kk + u], r);
+            const double x = widen_f32(own[t]);
+            const double h = x * r;
+            acc_h += h;
+            x_max = fmax(x_max, x);
+            const int i = blk_pixel(k, u, n, kap, N);
+            const double mi = meas[i];
+            const double dmax = fmax(__dsub_ru(h, mi), __dsub_ru(mi, h));      // >= |h - mu_i|
+            acc_A = __fma_ru(tv_weight_hi_fast(i / N, i - (i / N) * N, N, P.p), __fma_ru(h, rel, dmax), acc_A);
+            acc_res += dmax;
         }
-        __syncthreads();                                      // klo / khi are rewritten by the next side
+        const double S_h = block_reduce_rn(acc_h, red);
+        double A = block_reduce_ru(acc_A, red);
+        res += block_reduce_rn(acc_res, red);
+        // x_max: block maximum (the kd slack reaches h through sum_e pi~_e <= 1)
+        for (int o = 16; o > 0; o >>= 1) x_max = fmax(x_max, __shfl_xor_sync(0xffffffffu, x_max, o));
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x_max;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double d = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) d = fmax(d, red[w]);
+            red[32] = d;
+        }
+        __syncthreads();
+        const double slack = __dadd_ru(__dmul_ru(red[32], kd_abs), 0x1p-1000);
+        __syncthreads();
+        A = __fma_ru(slack, w_sum_hi, A);
+        const double ms = __dmul_ru((double)m, slack);
+        const double rg = __dadd_ru(rel, gam_m);
+        // both sides enclose the same total mass s: intersect
+        s_lo = fmax(s_lo, __dsub_rd(__dmul_rd(S_h, __dsub_rd(1.0, rg)), ms));
+        s_hi = fmin(s_hi, __dadd_ru(__dmul_ru(S_h, __dadd_ru(1.0, rg)), ms));
+        // B from the SumPool pass's per-block bounds of sum_{i in block} w_i mu_i
+        const double* wb = side == 0 ? P.mu_w_hi : P.nu_w_hi;
+        double accB = 0.0;
+        for (int q = threadIdx.x; q < M; q += blockDim.x) accB = __dadd_ru(accB, wb[q]);
+        const double B = block_reduce_ru(accB, red);
+        if (side == 0) { A_mu = A; B_mu = B; } else { A_nu = A; B_nu = B; }
+        __syncthreads();                                      // kd is rewritten by the next side
     }
     // ---- cost of the fitted plan over its support, rounded up ---------------
-    // one (entry e = (k, l), source offset u) per thread and step:
-    //   a[k, u] sum_v K[u, v] b[l, v] rho(x_(k,u), y_(l,v))^p in T rounded up,
-    //   weighted by pi~_kl in FP64 rounded up
+    // position (k, u) of the source, then every plan entry e = (k, l) of its row:
+    //   a[k, u] sum_v K'[u, v] b[l, v] rho(x_(k,u), y_(l,v))^p in T rounded up
+    //   (K', a, b are exact in T), weighted by pi~_kl in FP64 rounded up
     const T* tab = reinterpret_cast<const T*>(P.ctab_hi);
     double cost = 0.0;
-    const long long q_end = (long long)P.nnz * kk;
-    for (long long q = threadIdx.x; q < q_end; q += blockDim.x) {
-        const int e = (int)(q / kk), u = (int)(q - (long long)e * kk);
-        int lo = 0, hi = P.M;                                 // row of entry e
-        while (hi - lo > 1) { const int mid = (lo + hi) >> 1; if (P.rowptr[mid] <= e) lo = mid; else hi = mid; }
-        const int k = lo, l = P.colidx[e];
-        const int r0 = kap * (k / n - l / n) + u / kap, c0 = kap * (k % n - l % n) + u % kap;
-        const T* kh = Khi + u * kk;
-        const T* br = b + l * kk;
-        T inner = T(0);
-        for (int v1 = 0; v1 < kap; ++v1) {
-            const T* trow = tab + abs(r0 - v1) * N;
-            for (int v2 = 0; v2 < kap; ++v2) {
-                const int v = v1 * kap + v2;
-                inner = fma_ru(mul_ru(kh[v], br[v]), trow[abs(c0 - v2)], inner);
+    for (int t = threadIdx.x; t < m; t += blockDim.x) {
+        const int k = t / kk, u = t - (t / kk) * kk;
+        const T a_ku = a[t];
+        const T* kh = Ks + u * kk;
+        for (int e = rp[k]; e < rp[k + 1]; ++e) {
+            const int l = ci[e];
+            const int r0 = kap * (k / n - l / n) + u / kap, c0 = kap * (k % n - l % n) + u % kap;
+            const T* br = b + l * kk;
+            T inner = T(0);
+            for (int v1 = 0; v1 < kap; ++v1) {
+                const T* trow = tab + abs(r0 - v1) * N;
+                for (int v2 = 0; v2 < kap; ++v2) {
+                    const int v = v1 * kap + v2;
+                    inner = fma_ru(mul_ru(kh[v], br[v]), trow[abs(c0 - v2)], inner);
+                }
             }
+            cost = __fma_ru(v64[e], widen_f32(mul_ru(a_ku, inner)), cost);
         }
-        cost = __fma_ru(P.val[e], widen_f32(mul_ru(a[k * kk + u], inner)), cost);
     }
     const double cost_sum = block_reduce_ru(cost, red);
     if (threadIdx.x == 0) {
         const double p = P.p;
+        const double inv_hi = s_lo > 0.0 ? __drcp_ru(s_lo) : HUGE_VAL;   // >= 1 / s
+        const double inv_lo = __drcp_rd(s_hi);                          // <= 1 / s
+        const double dinv = fmax(0.0, fmax(__dsub_ru(inv_hi, 1.0), __dsub_ru(1.0, inv_lo)));
+        const double tv_mu = __fma_ru(B_mu, dinv, __dmul_ru(A_mu, inv_hi));
+        const double tv_nu = __fma_ru(B_nu, dinv, __dmul_ru(A_nu, inv_hi));
         const double scale = (p == 1.0) ? 1.0 : (p == 2.0 ? 2.0 : __dmul_ru(pow(2.0, p - 1.0), 1.0 + 0x1p-49));
         const double dmu = root_p_ru(__dmul_ru(scale, tv_mu), p);
         const double dnu = root_p_ru(__dmul_ru(scale, tv_nu), p);
-        const double w_hat_p = s_lo > 0.0 ? __ddiv_ru(cost_sum, s_lo) : HUGE_VAL;
+        const double w_hat_p = __dmul_ru(cost_sum, inv_hi);
         const double w_hat = root_p_ru(w_hat_p, p);
         PairOut& O = outs[P.out_index];
         O.w_hat_p = w_hat_p;
@@ -1574,24 +1756,39 @@ primalk_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
         O.sweeps_done = P.sweeps;
     }
     // leave a, b in the pixel layout of the other passes (through the KB scratch)
+    T* tmp = reinterpret_cast<T*>(P.kb_t);
     for (int side = 0; side < 2; ++side) {
         T* x = side == 0 ? a : b;
-        for (int t = threadIdx.x; t < m; t += blockDim.x) kb[t] = x[t];
+        for (int t = threadIdx.x; t < m; t += blockDim.x) tmp[t] = x[t];
         __syncthreads();
-        for (int t = threadIdx.x; t < m; t += blockDim.x) x[blk_pixel(t / kk, t - (t / kk) * kk, n, kap, N)] = kb[t];
+        for (int t = threadIdx.x; t < m; t += blockDim.x) x[blk_pixel(t / kk, t - (t / kk) * kk, n, kap, N)] = tmp[t];
         __syncthreads();
     }
 }
 
 int launch_primalk(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs, int kappa_max,
-                   bool all_kappa4, bool f64, cudaStream_t stream) {
+                   int M_max, int nnz_max, int m_max, bool all_kappa4, bool f64, cudaStream_t stream) {
     if (n_pairs <= 0) return QWB_OK;
     if (kappa_max > 8) return QWB_ERR_UNSUPPORTED;
+    const size_t tsz = f64 ? 8 : 4;
     const int kk = kappa_max * kappa_max;
-    const size_t smem = (size_t)kk * kk * (sizeof(double) + 3 * (f64 ? 8 : 4));
+    const size_t kq = (size_t)kk * kk;
+    const size_t base = 2 * align16(tsz * kq);                // K' in two orientations
+    // KB and KA in shared memory when they fit; the plan staged as well when
+    // it fits next to them
+    const size_t kbb = 2 * align16(tsz * (size_t)m_max);
+    const bool kb_in = base + kbb <= 200 * 1024;
+    const size_t with_kb = kb_in ? base + kbb : base;
+    const int cap = std::max(nnz_max, 2 * M_max);
+    const size_t csr = (8 + 2 * tsz + 2 * sizeof(int)) * (size_t)cap + 2 * sizeof(int) * (size_t)(M_max + 1);
+    const bool staged = with_kb + csr <= 220 * 1024;
+    const size_t smem = staged ? with_kb + csr : with_kb;
+    const int csr_cap = staged ? cap : -1;
+    const int kb_cap = kb_in ? m_max : 0;
+    const int threads = f64 ? PRIMALK_THREADS_F64 : PRIMALK_THREADS_F32;
     auto run = [&](auto kern) -> int {
         QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<n_pairs, PRIMALK_THREADS, smem, stream>>>(pairs_d, outs_d, pair_ids);
+        kern<<<n_pairs, threads, smem, stream>>>(pairs_d, outs_d, pair_ids, csr_cap, kk, kb_cap);
         QWB_LAUNCHED();
         return QWB_OK;
     };

@@ -45,7 +45,7 @@ struct PairDev {
     void* a; void* b;       // N*N fine scalings work (T)
     const double* upK;      // null: the uniform kernel kappa^-2d; else a (kappa^2)^2 kernel K[u, v]
     const void* upK_t;      //   (row-major, offsets row-major in the block) and its copy in type T
-    void* kb_t;             // N*N scratch (T) of the general-kernel sweeps, [block][offset]
+    void* kb_t;             // 2 N*N scratch (T) of the general-kernel sweeps, [block][offset]
     double* kscratch;       // 2 N*N scratch (FP64) of its certified evaluation
     double* a_out; double* b_out;   // optional FP64 outputs
     // dual pass
@@ -106,7 +106,7 @@ int launch_primal(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, 
 // primal pass with a general upscaling kernel (P.upK set; d = 2, kappa <= kappa_max <= 8;
 // all_kappa4: every pair of the launch has kappa 4, which selects the register-row kernel)
 int launch_primalk(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs, int kappa_max,
-                   bool all_kappa4, bool f64, cudaStream_t stream);
+                   int M_max, int nnz_max, int m_max, bool all_kappa4, bool f64, cudaStream_t stream);
 // Fine FP32 IPF sweeps on clusters of C CTAs per pair (2-D, kappa 4 or 8,
 // FP32, C divides every pair's n); the pairs have fine_ext = 1.
 int launch_ipf_fine(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int kappa, int C,

@@ -6,8 +6,12 @@ Tolerances.  The plan's cost W-hat^p matches the oracle's to 1e-6 (F64) or
 |mu-hat - mu|: with FP32 scalings each marginal entry carries a relative
 rounding error of at most about (kappa^2 + row degree + 2) u (the FP32 sums
 of the half sweep that produced it, and its division), which the oracle's
-FP64 state does not have; the sums therefore agree to within
-    floor = 2^(p-1) c u sum_i w_i (mu_i + nu_i),  c = 4 (kappa^2 + deg + 2),
+FP64 state does not have, and the certified evaluation encloses each entry
+in an interval of relative half-width (kappa^2 + deg + 3) 2^-52 and the total
+mass in one wider by its summation bound (m / 256 + 42) 2^-52; the sums
+therefore agree to within
+    floor = 2^(p-1) (c u + (4 (kappa^2 + deg + 3) + 2 (m / 256 + 42)) 2^-52)
+            sum_i w_i (mu_i + nu_i),  c = 4 (kappa^2 + deg + 2),
 and each Delta to within (its oracle value^p + floor)^(1/p) above and the
 same with - floor below (u = 2^-24 for MIXED, 2^-53 for F64)."""
 import numpy as np
@@ -48,7 +52,14 @@ def _random_kernel(kappa, seed):
 def _check(r, ref, mu, nu, N, kappa, p, prec, plan):
     deg = int(max((plan > 0).sum(axis=1).max(), (plan > 0).sum(axis=0).max()))
     w = O.tv_weights(N, p)
-    floor = 2.0 ** (p - 1) * 4 * (kappa * kappa + deg + 2) * UNIT[prec] * float(np.dot(w, mu + nu))
+    # the scalings' rounding (above) and the certified evaluation's own
+    # enclosures: a relative (kappa^2 + deg + 3) 2^-52 either side of each
+    # marginal entry and, plus the summation bound (m / 256 + 42) 2^-52, of
+    # the mass s (which enters through |1/s - 1|)
+    m_terms = (N * N + 255) // 256 + 42
+    rel = (4 * (kappa * kappa + deg + 2) * UNIT[prec]
+           + (4 * (kappa * kappa + deg + 3) + 2 * m_terms) * 2.0 ** -52)
+    floor = 2.0 ** (p - 1) * rel * float(np.dot(w, mu + nu))
     tol = TOL[prec]
     assert abs(r["w_hat_p"] - ref["w_hat_p"]) <= tol * ref["w_hat_p"]
     for key in ("delta_mu", "delta_nu"):
