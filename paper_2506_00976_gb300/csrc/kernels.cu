@@ -1396,6 +1396,34 @@ __device__ __forceinline__ float ipf_div(float s, float r) {
     return s * y;
 }
 
+// one fused-sweep update: r = sum_e pi~_e KIN[idx_e, 4g..4g+3], x = src / r
+__device__ __forceinline__ float4 primalk_update(int k, int g, int q4, const int* ptr, const int* idx,
+                                                 const float* val, const float4* kin4, float4 sv) {
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int e = ptr[k]; e < ptr[k + 1]; ++e) {
+        const float v = val[e];
+        const float4 kv = kin4[idx[e] * q4 + g];
+        r.x = fmaf(v, kv.x, r.x);
+        r.y = fmaf(v, kv.y, r.y);
+        r.z = fmaf(v, kv.z, r.z);
+        r.w = fmaf(v, kv.w, r.w);
+    }
+    return make_float4(ipf_div(sv.x, r.x), ipf_div(sv.y, r.y), ipf_div(sv.z, r.z), ipf_div(sv.w, r.w));
+}
+
+// s += sum_j K'[4 w4 + j][4g..4g+3] x_(4 w4 + j), the four x taken from lane `src`
+__device__ __forceinline__ void primalk_row_fma(float4& s, const float4 xv, int src, const float4 k0,
+                                                const float4 k1, const float4 k2, const float4 k3) {
+    const float x0 = __shfl_sync(0xffffffffu, xv.x, src);
+    const float x1 = __shfl_sync(0xffffffffu, xv.y, src);
+    const float x2 = __shfl_sync(0xffffffffu, xv.z, src);
+    const float x3 = __shfl_sync(0xffffffffu, xv.w, src);
+    s.x = fmaf(k3.x, x3, fmaf(k2.x, x2, fmaf(k1.x, x1, fmaf(k0.x, x0, s.x))));
+    s.y = fmaf(k3.y, x3, fmaf(k2.y, x2, fmaf(k1.y, x1, fmaf(k0.y, x0, s.y))));
+    s.z = fmaf(k3.z, x3, fmaf(k2.z, x2, fmaf(k1.z, x1, fmaf(k0.z, x0, s.z))));
+    s.w = fmaf(k3.w, x3, fmaf(k2.w, x2, fmaf(k1.w, x1, fmaf(k0.w, x0, s.w))));
+}
+
 // err-free product and sum in FP32 (Dekker / Knuth via FMA)
 __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& t) {
     s = a + b;
@@ -1494,45 +1522,44 @@ primalk_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
                 const float4* kin4 = reinterpret_cast<const float4*>(half == 0 ? kbB : kbA);
                 float4* kout4 = reinterpret_cast<float4*>(half == 0 ? kbA : kbB);
                 const float4* Kn4 = half == 0 ? Ks4 : KsT4;    // a -> KA (rows K'[w][.]); b -> KB (rows K'[.][w])
-                for (int jt = 0; jt < n_iter; ++jt) {
-                    const int it = threadIdx.x + jt * blockDim.x;
-                    const bool valid = it < n_items;
-                    const int k = it / q4, g = it - (it / q4) * q4;
-                    float4 xv = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (valid) {
-                        float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-                        for (int e = ptr[k]; e < ptr[k + 1]; ++e) {
-                            const float v = val[e];
-                            const float4 kv = kin4[idx[e] * q4 + g];
-                            r.x = fmaf(v, kv.x, r.x);
-                            r.y = fmaf(v, kv.y, r.y);
-                            r.z = fmaf(v, kv.z, r.z);
-                            r.w = fmaf(v, kv.w, r.w);
+                // four items per step (the same g, so each K' load feeds all four)
+                constexpr int IPS = 4;
+                for (int jt = 0; jt < n_iter; jt += IPS) {
+                    const int g = threadIdx.x % q4;                // it % q4 for every item
+                    float4 xv[IPS], s[IPS];
+#pragma unroll
+                    for (int q = 0; q < IPS; ++q) {
+                        const int it = threadIdx.x + (jt + q) * blockDim.x;
+                        xv[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        s[q] = xv[q];
+                        if (it < n_items) {
+                            xv[q] = primalk_update(it / q4, g, q4, ptr, idx, val, kin4, src4[it]);
+                            dst4[it] = xv[q];
                         }
-                        const float4 sv = src4[it];
-                        xv.x = ipf_div(sv.x, r.x);
-                        xv.y = ipf_div(sv.y, r.y);
-                        xv.z = ipf_div(sv.z, r.z);
-                        xv.w = ipf_div(sv.w, r.w);
-                        dst4[it] = xv;
                     }
-                    // the block row sits in lanes lane - g .. lane - g + q4 - 1 (rows
+                    // the block rows sit in lanes lane - g .. lane - g + q4 - 1 (rows
                     // never straddle the valid / invalid boundary: n_items = M q4)
                     const int row0 = lane - g;
-                    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
                     for (int w4 = 0; w4 < q4; ++w4) {
-                        const float x0 = __shfl_sync(0xffffffffu, xv.x, row0 + w4);
-                        const float x1 = __shfl_sync(0xffffffffu, xv.y, row0 + w4);
-                        const float x2 = __shfl_sync(0xffffffffu, xv.z, row0 + w4);
-                        const float x3 = __shfl_sync(0xffffffffu, xv.w, row0 + w4);
-                        const float4 k0 = Kn4[(4 * w4) * q4 + g], k1 = Kn4[(4 * w4 + 1) * q4 + g];
-                        const float4 k2 = Kn4[(4 * w4 + 2) * q4 + g], k3 = Kn4[(4 * w4 + 3) * q4 + g];
-                        s.x = fmaf(k3.x, x3, fmaf(k2.x, x2, fmaf(k1.x, x1, fmaf(k0.x, x0, s.x))));
-                        s.y = fmaf(k3.y, x3, fmaf(k2.y, x2, fmaf(k1.y, x1, fmaf(k0.y, x0, s.y))));
-                        s.z = fmaf(k3.z, x3, fmaf(k2.z, x2, fmaf(k1.z, x1, fmaf(k0.z, x0, s.z))));
-                        s.w = fmaf(k3.w, x3, fmaf(k2.w, x2, fmaf(k1.w, x1, fmaf(k0.w, x0, s.w))));
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const float4 kv = Kn4[(4 * w4 + j) * q4 + g];
+#pragma unroll
+                            for (int q = 0; q < IPS; ++q) {
+                                const float xs = j == 0 ? xv[q].x : j == 1 ? xv[q].y : j == 2 ? xv[q].z : xv[q].w;
+                                const float x = __shfl_sync(0xffffffffu, xs, row0 + w4);
+                                s[q].x = fmaf(kv.x, x, s[q].x);
+                                s[q].y = fmaf(kv.y, x, s[q].y);
+                                s[q].z = fmaf(kv.z, x, s[q].z);
+                                s[q].w = fmaf(kv.w, x, s[q].w);
+                            }
+                        }
                     }
-                    if (valid) kout4[it] = s;
+#pragma unroll
+                    for (int q = 0; q < IPS; ++q) {
+                        const int it = threadIdx.x + (jt + q) * blockDim.x;
+                        if (it < n_items) kout4[it] = s[q];
+                    }
                 }
                 __syncthreads();
             }
@@ -1718,7 +1745,7 @@ primalk_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
     for (int t = threadIdx.x; t < m; t += blockDim.x) {
         const int k = t / kk, u = t - (t / kk) * kk;
         const T a_ku = a[t];
-        const T* kh = Ks + u * kk;
+        const T* kh = KsT + u;                                // K'[u][v] = KsT[v kk + u]: lanes on u, no conflicts
         for (int e = rp[k]; e < rp[k + 1]; ++e) {
             const int l = ci[e];
             const int r0 = kap * (k / n - l / n) + u / kap, c0 = kap * (k % n - l % n) + u % kap;
@@ -1728,7 +1755,7 @@ primalk_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
                 const T* trow = tab + abs(r0 - v1) * N;
                 for (int v2 = 0; v2 < kap; ++v2) {
                     const int v = v1 * kap + v2;
-                    inner = fma_ru(mul_ru(kh[v], br[v]), trow[abs(c0 - v2)], inner);
+                    inner = fma_ru(mul_ru(kh[v * kk], br[v]), trow[abs(c0 - v2)], inner);
                 }
             }
             cost = __fma_ru(v64[e], widen_f32(mul_ru(a_ku, inner)), cost);
