@@ -1179,7 +1179,7 @@ static int solve_pair(qwb_batch* b, int t) {
                         }
             }
     }
-    st = network_simplex(M, M, Cb, mc, nc, sb, -1, &basis, nullptr, &cand);
+    st = network_simplex(M, M, Cb, mc, nc, sb, -1, &basis, nullptr, &cand, false);   // the plan only
     if (st) return st;
     double L_sum = 0.0;
     const int nnzb = (int)sb.col.size();

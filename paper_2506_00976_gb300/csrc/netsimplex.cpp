@@ -432,7 +432,7 @@ struct Solver {
 template <typename Cost>
 int solve(int32_t n_src, int32_t n_dst, Cost cst, double maxc, const double* a, const double* b,
           NSSolution& out, int64_t max_pivots, const NSBasis* warm, NSBasis* basis_out,
-          const std::vector<int64_t>* candidates = nullptr) {
+          const std::vector<int64_t>* candidates = nullptr, bool exact_dual = true) {
     const int64_t NM = (int64_t)n_src * n_dst;
     if (max_pivots < 0) max_pivots = 20 * NM + 1000000;
     Solver<Cost> S;
@@ -497,18 +497,32 @@ int solve(int32_t n_src, int32_t n_dst, Cost cst, double maxc, const double* a, 
     for (int i = 0; i < n_src; ++i) { f_lo = std::min(f_lo, S.pot[i]); f_hi = std::max(f_hi, S.pot[i]); }
     const double shift = n_src > 0 ? 0.5 * (f_lo + f_hi) : 0.0;
     for (int i = 0; i < n_src; ++i) out.f[i] = S.pot[i] - shift;
-    std::vector<double> crow(n_dst);
     double* g = out.g.data();
+    if (!exact_dual) {
+        // the tree potentials as they are: f_i + g_j = C_ij on the tree arcs,
+        // <= C_ij + eps elsewhere (optimality up to the pricing tolerance)
+        for (int j = 0; j < n_dst; ++j) g[j] = -S.pot[n_src + j] + shift;
+        out.pivots = piv;
+        return QWB_OK;
+    }
+    // g = f^c, then f = g^c, row by row; each row is walked as runs of
+    // contiguous costs (one run per grid row for table costs) with four
+    // independent min chains in the reduction
+    std::vector<double> crow(n_dst);
     for (int i = 0; i < n_src; ++i) {
         S.row_costs(i, crow.data());
         const double fi = out.f[i];
-        for (int j = 0; j < n_dst; ++j) g[j] = std::min(g[j], crow[j] - fi);
+        const double* c = crow.data();
+        for (int j = 0; j < n_dst; ++j) {
+            const double v = c[j] - fi;
+            g[j] = v < g[j] ? v : g[j];
+        }
     }
+    std::vector<double> mg(n_dst);
+    for (int j = 0; j < n_dst; ++j) mg[j] = -g[j];
     for (int i = 0; i < n_src; ++i) {
         S.row_costs(i, crow.data());
-        double fi = std::numeric_limits<double>::infinity();
-        for (int j = 0; j < n_dst; ++j) fi = std::min(fi, crow[j] - g[j]);
-        out.f[i] = fi;
+        out.f[i] = S.run_min(crow.data(), mg.data(), n_dst);
     }
     out.pivots = piv;
     return QWB_OK;
@@ -524,7 +538,7 @@ bool check_masses(int32_t n_src, int32_t n_dst, const double* a, const double* b
 
 int network_simplex(int32_t n_src, int32_t n_dst, const double* C, const double* a,
                     const double* b, NSSolution& out, int64_t max_pivots, const NSBasis* warm,
-                    NSBasis* basis_out, const std::vector<int64_t>* candidates) {
+                    NSBasis* basis_out, const std::vector<int64_t>* candidates, bool exact_dual) {
     if (n_src <= 0 || n_dst <= 0 || !C || !a || !b) return QWB_ERR_INVALID_ARG;
     const int64_t NM = (int64_t)n_src * n_dst;
     double maxc = 0.0;
@@ -537,7 +551,7 @@ int network_simplex(int32_t n_src, int32_t n_dst, const double* C, const double*
         for (int64_t a_ : *candidates)
             if (a_ < 0 || a_ >= NM) return QWB_ERR_INVALID_ARG;
     return solve(n_src, n_dst, DenseCost{C, n_dst}, maxc, a, b, out, max_pivots, warm, basis_out,
-                 candidates);
+                 candidates, exact_dual);
 }
 
 namespace {

@@ -33,10 +33,14 @@ struct NSBasis {
 // basis_out: optional final basis; candidates: optional arcs (i * n_dst + j)
 // priced first -- when none of them can enter, a scan of all arcs adds those
 // that can, so the result is optimal over all arcs either way.
+// exact_dual = false skips the final c-transforms: f, g are then the
+// optimal tree potentials (f_i + g_j = C_ij on the plan's support and
+// <= C_ij up to the pricing tolerance elsewhere), for callers that use only
+// the plan.
 int network_simplex(int32_t n_src, int32_t n_dst, const double* C, const double* a,
                     const double* b, NSSolution& out, int64_t max_pivots = -1,
                     const NSBasis* warm = nullptr, NSBasis* basis_out = nullptr,
-                    const std::vector<int64_t>* candidates = nullptr);
+                    const std::vector<int64_t>* candidates = nullptr, bool exact_dual = true);
 
 // The same for the grid problem with C_kl = tab[|k1 - l1| * n_side + |k2 - l2|]
 // on an n_side x n_side coarse grid (k = k1 * n_side + k2): the centre cost
