@@ -347,8 +347,13 @@ int qwb_batch_coarse_plan(qwb_batch* batch, int32_t pair, int32_t* rowptr_h, int
  * blocks and exchange block sums through distributed shared memory -- the
  * form that keeps HBM busy for large grids.  Each group of pairs with one
  * block side takes the largest power of two <= C dividing all its coarse
- * sides.  Overrides the autotuner's choice; synchronises the device and drops
- * the batch's captured fine-pass graphs.  Errors: INVALID_ARG, CUDA. */
+ * sides.  C | QWB_IPF_BULK (C = 2..16) selects the form that stages the
+ * source values by bulk copies (cp.async.bulk into a ring of shared-memory
+ * stages, completion on mbarriers, every wait bounded) for groups whose pairs
+ * share N; a timed-out wait makes qwb_batch_results return CUDA.  Overrides
+ * the autotuner's choice, which times both forms; synchronises the device
+ * and drops the batch's captured fine-pass graphs.  Errors: INVALID_ARG, CUDA. */
+#define QWB_IPF_BULK 32
 int qwb_batch_set_ipf_cluster(qwb_batch* batch, int32_t C);
 /* Upscale the coarse plans of the batch's 2-D pairs with block side kappa by
  * the general kernel K_d (Sec. 3.4, eq. coupling tensor upscale; layout,

@@ -56,6 +56,9 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
 
 
+QWB_IPF_BULK = 32   # Batch.set_ipf_cluster(C | QWB_IPF_BULK): the bulk-copy staged sweeps
+
+
 def problem(N, kappa, p, d=2):
     """One problem on the grid [N]^d (d = 2 images, d = 3 volumes)."""
     return QwbProblem(int(N), int(kappa), float(p), int(d), 0)

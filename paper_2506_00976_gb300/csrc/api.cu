@@ -204,11 +204,14 @@ struct qwb_batch {
     // pairs grouped by kappa (4, 8); ipf_C is the requested cluster size
     // (0: every pair sweeps inside primal_kernel), each group runs with the
     // largest power of two <= ipf_C that divides all its coarse sides
-    struct IpfGroup { int kappa, off, cnt, M_max, gcd_n, C; };
+    // (stream: the bulk-copy variant ipf_stream_kernel, for groups whose pairs
+    // share N; n_same, N_same: that common coarse and fine side, else 0)
+    struct IpfGroup { int kappa, off, cnt, M_max, gcd_n, C, n_same, N_same; bool stream; };
     std::vector<IpfGroup> ipf_groups;
     std::vector<int> ipf_group_of;      // per pair: its group or -1
     int* ipf_ids_d = nullptr;
-    int ipf_C = 0;
+    int ipf_C = 0;                      // + QWB_IPF_BULK: the bulk-copy variant
+    int* dev_err = nullptr;             // device error word of bounded waits (0 = none)
     // pairs upscaled with a general kernel K (primalk_kernel, 2-D, kappa <= 8):
     // K per kappa, and prim_ids_d = [uniform pairs..., K pairs...]
     std::vector<std::pair<int, std::vector<double>>> upk;   // (kappa, K)
@@ -309,10 +312,12 @@ static std::vector<int> build_ipf_groups(qwb_batch* b) {
     std::vector<int> ipf_ids;
     if (b->f64) return ipf_ids;
     for (int kap : {4, 8}) {
-        qwb_batch::IpfGroup G{kap, (int)ipf_ids.size(), 0, 0, 0, 0};
+        qwb_batch::IpfGroup G{kap, (int)ipf_ids.size(), 0, 0, 0, 0, -1, -1, false};
         for (int t = 0; t < b->n; ++t) {
             if (dim_of(b->probs[t]) != 2 || b->probs[t].kappa != kap || b->upk_on[t]) continue;
             const int nn = b->probs[t].N / kap;
+            G.n_same = G.n_same < 0 ? nn : (G.n_same == nn ? nn : 0);
+            G.N_same = G.N_same < 0 ? b->probs[t].N : (G.N_same == b->probs[t].N ? G.N_same : 0);
             int x = G.gcd_n, y = nn;
             while (y) { const int r = x % y; x = y; y = r; }
             G.gcd_n = x;
@@ -326,12 +331,21 @@ static std::vector<int> build_ipf_groups(qwb_batch* b) {
     return ipf_ids;
 }
 
+// the fine sweeps of group G (pairs ids[0..cnt)) on clusters
+static int launch_ipf_group(qwb_batch* b, const qwb_batch::IpfGroup& G, const int* ids, int cnt, int M,
+                            cudaStream_t s) {
+    if (G.stream) return launch_ipf_stream(b->pairs_d, ids, cnt, G.kappa, G.C, G.n_same, G.N_same, b->dev_err, s);
+    return launch_ipf_fine(b->pairs_d, ids, cnt, G.kappa, G.C, M, 0, s);
+}
+
 static int apply_ipf_choice(qwb_batch* b, int C) {
     b->ipf_C = C;
+    const int Cs = C & ~QWB_IPF_BULK;
     for (auto& G : b->ipf_groups) {
         int c = 1;
-        while (c * 2 <= C && c * 2 <= 16 && G.gcd_n % (c * 2) == 0) c *= 2;
+        while (c * 2 <= Cs && c * 2 <= 16 && G.gcd_n % (c * 2) == 0) c *= 2;
         G.C = c >= 2 ? c : 0;
+        G.stream = (C & QWB_IPF_BULK) && G.C > 0 && G.n_same > 0 && G.N_same > 0;
     }
     for (int t = 0; t < b->n; ++t) {
         const int g = b->ipf_group_of[t];
@@ -540,7 +554,8 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
     b->upk_on.assign(n, 0);
     const std::vector<int> ipf_ids = build_ipf_groups(b);
     const size_t o_ipf = align_up(o_cb3 + sizeof(PixItem) * cb3.size());
-    const size_t total = align_up(o_ipf + sizeof(int) * std::max<size_t>(1, ipf_ids.size()));
+    const size_t o_err = align_up(o_ipf + sizeof(int) * std::max<size_t>(1, ipf_ids.size()));
+    const size_t total = align_up(o_err + sizeof(int));
     if (cudaMalloc(&b->dmem, total) != cudaSuccess) { batch_free(b); return fail(QWB_ERR_OOM, "batch workspace"); }
     b->pairs_d = (PairDev*)(b->dmem + o_pairs);
     b->outs_d = (PairOut*)(b->dmem + o_outs);
@@ -553,6 +568,7 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
     b->sep_items_d = (SepItem*)(b->dmem + o_sep);
     b->cbar3_items_d = (PixItem*)(b->dmem + o_cb3);
     b->ipf_ids_d = (int*)(b->dmem + o_ipf);
+    b->dev_err = (int*)(b->dmem + o_err);
     // coarse-plan staging
     size_t poff = 0;
     for (int t = 0; t < n; ++t) { b->plan_off.push_back(poff); poff += plan_layout(b->Ms[t]).total; }
@@ -636,6 +652,7 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
     if (!st) st = up(b->ct_b_items_d, ctb.data(), sizeof(CtItem) * ctb.size());
     if (!st) st = up(b->ct_p_items_d, ctp.data(), sizeof(CtItem) * ctp.size());
     if (!st) st = up(b->ipf_ids_d, ipf_ids.data(), sizeof(int) * ipf_ids.size());
+    if (!st && cudaMemset(b->dev_err, 0, sizeof(int)) != cudaSuccess) st = fail(QWB_ERR_CUDA, "batch set-up");
     if (!st && b->tune && b->tune->ipf_done) st = apply_ipf_choice(b, b->tune->ipf_C);
     if (!st) {
         b->ev_ok = true;
@@ -740,8 +757,7 @@ static int enqueue_fine(qwb_batch* b, bool batched, cudaStream_t s) {
         if ((st = mark(b, 3, s))) return st;
         if (do_primal)
             for (const auto& G : b->ipf_groups)
-                if (G.C > 0 && (st = launch_ipf_fine(b->pairs_d, b->ipf_ids_d + G.off, G.cnt, G.kappa, G.C,
-                                                     G.M_max, 0, s)))
+                if (G.C > 0 && (st = launch_ipf_group(b, G, b->ipf_ids_d + G.off, G.cnt, G.M_max, s)))
                     return st;
         if ((st = mark(b, 10, s))) return st;
         if (do_primal) {
@@ -798,7 +814,7 @@ static int enqueue_fine(qwb_batch* b, bool batched, cudaStream_t s) {
             if ((st = launch_support_num(b->pairs_d, id, 1, 2 * M, b->f64, s))) return st;
             if (b->ipf_group_of[t] >= 0 && b->ipf_groups[b->ipf_group_of[t]].C > 0) {
                 const auto& G = b->ipf_groups[b->ipf_group_of[t]];
-                if ((st = launch_ipf_fine(b->pairs_d, id, 1, G.kappa, G.C, M, 0, s))) return st;
+                if ((st = launch_ipf_group(b, G, id, 1, M, s))) return st;
             }
             if ((st = launch_primal(b->pairs_d, b->outs_d, id, 1, M, 0, b->f64, s))) return st;
         }
@@ -950,25 +966,26 @@ static int tune_ipf(qwb_batch* b, cudaStream_t s) {
     rep << "{";
     double best = 1e30;
     int bestC = 0;
-    for (int C : {0, 2, 4, 8, 16}) {
+    for (int C : {0, 2, 4, 8, 16, QWB_IPF_BULK | 2, QWB_IPF_BULK | 4, QWB_IPF_BULK | 8, QWB_IPF_BULK | 16}) {
         int st = apply_ipf_choice(b, C);
         if (st) return st;
         if (C > 0) {
             bool any = false;
-            for (const auto& G : b->ipf_groups) any |= G.C == C;
-            if (!any) continue;                  // no group takes this size
+            for (const auto& G : b->ipf_groups)
+                any |= G.C == (C & ~QWB_IPF_BULK) && G.stream == ((C & QWB_IPF_BULK) != 0);
+            if (!any) continue;                  // no group takes this size / form
         }
         double ms;
         st = time_variant(s, b->ev[0], b->ev[1], [&] {
             int st2;
             for (const auto& G : b->ipf_groups)
-                if (G.C > 0 && (st2 = launch_ipf_fine(b->pairs_d, b->ipf_ids_d + G.off, G.cnt, G.kappa, G.C,
-                                                      G.M_max, 0, s)))
+                if (G.C > 0 && (st2 = launch_ipf_group(b, G, b->ipf_ids_d + G.off, G.cnt, G.M_max, s)))
                     return st2;
             return launch_primal(b->pairs_d, b->outs_d, b->pair_ids_d, b->n, b->M_max, 0, b->f64, s);
         }, &ms);
         if (st) return st;
-        rep << (C ? ", " : "") << "\"cluster" << C << "\": " << ms;
+        rep << (C ? ", " : "") << "\"" << ((C & QWB_IPF_BULK) ? "bulk" : "cluster") << (C & ~QWB_IPF_BULK)
+            << "\": " << ms;
         if (ms < best) { best = ms; bestC = C; }
     }
     rep << "}";
@@ -1270,6 +1287,8 @@ static int batch_results(qwb_batch* b, qwb_result* out, cudaStream_t s) {
     QWB_CUDA(cudaStreamSynchronize(s));
     std::vector<PairOut> o(b->n);
     QWB_CUDA(cudaMemcpy(o.data(), b->outs_d, sizeof(PairOut) * b->n, cudaMemcpyDeviceToHost));
+    int dev_err = 0;
+    QWB_CUDA(cudaMemcpy(&dev_err, b->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
     float tc = 0.f, tp = 0.f, td = 0.f;
     if (b->ev_ok) {
         if (cudaEventElapsedTime(&tc, b->ev[0], b->ev[1]) != cudaSuccess) tc = 0.f;
@@ -1294,8 +1313,9 @@ static int batch_results(qwb_batch* b, qwb_result* out, cudaStream_t s) {
         if (b->flags & QWB_FLAG_NO_PRIMAL) { r.ub_primal = HUGE_VAL; r.w_hat_p = HUGE_VAL; }
         if (b->flags & QWB_FLAG_NO_DUAL) { r.lb = 0.0; r.lb_p = -HUGE_VAL; }
         r.t_coarse_cost_ms = tc; r.t_solve_ms = b->t_solve_ms; r.t_primal_ms = tp; r.t_dual_ms = td;
-        r.status = b->status[t];
+        r.status = dev_err ? QWB_ERR_CUDA : b->status[t];
     }
+    if (dev_err) return fail(QWB_ERR_CUDA, "a bounded device wait timed out (bulk-copy IPF sweeps)");
     return QWB_OK;
 }
 
@@ -1462,8 +1482,10 @@ int qwb_batch_coarse_plan(qwb_batch* b, int32_t pair, int32_t* rowptr_h, int32_t
 }
 
 int qwb_batch_set_ipf_cluster(qwb_batch* b, int32_t C) {
-    if (!b || (C != 0 && C != 2 && C != 4 && C != 8 && C != 16))
-        return fail(QWB_ERR_INVALID_ARG, "qwb_batch_set_ipf_cluster: C must be 0, 2, 4, 8 or 16");
+    const int Cs = C & ~QWB_IPF_BULK;
+    if (!b || (Cs != 0 && Cs != 2 && Cs != 4 && Cs != 8 && Cs != 16) || C == QWB_IPF_BULK)
+        return fail(QWB_ERR_INVALID_ARG,
+                    "qwb_batch_set_ipf_cluster: C must be 0, 2, 4, 8 or 16, the last four optionally | QWB_IPF_BULK");
     QWB_CUDA(cudaSetDevice(b->ctx->device));
     QWB_CUDA(cudaDeviceSynchronize());
     // captured fine passes hold the previous launch configuration

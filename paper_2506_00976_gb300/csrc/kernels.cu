@@ -2015,6 +2015,270 @@ int launch_ipf_fine(const PairDev* pairs_d, const int* pair_ids, int n_pairs, in
 }
 
 // --------------------------------------------------------------------------
+// ipf_stream: the same fine FP32 IPF sweeps as ipf_fine_kernel (same cluster
+// ownership, block sums through distributed shared memory, one cluster
+// barrier per half sweep), with the source values staged by bulk copies.
+// A CTA owns nbr = n / C whole block rows, i.e. a contiguous range of pixel
+// rows.  Each half sweep is cut into chunks of rps block rows (about 16 KB);
+// one thread keeps a ring of PK_STAGES chunks in flight with
+// cp.async.bulk (completion counted in bytes on one mbarrier per stage), and
+// keeps issuing across half-sweep boundaries, since the sources mu, nu do not
+// depend on the sweeps.  Per half sweep the CTA first forms
+// r = kappa^-4 pi~ B for its blocks (1 / r in shared memory), then per chunk:
+// wait for the stage, scale its values row-major (float4 from shared memory,
+// coalesced float4 stores), write per-row block partial sums, barrier,
+// re-issue the stage, and reduce the partials over the block's kappa rows in
+// a fixed order (the sums match ipf_fine_kernel's association only up to
+// rounding; both are FP32 sweeps outside the certificate).  Every wait on an
+// mbarrier is bounded: on time-out the CTA sets *err, stops issuing copies
+// and processing, and still takes part in every barrier, so no CTA of the
+// cluster is left waiting; before returning it waits, bounded again, for the
+// copies it issued.
+// --------------------------------------------------------------------------
+constexpr int PK_STAGES = 4;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t phase) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done) : "r"(bar), "r"(phase) : "memory");
+    return done != 0;
+}
+// bounded wait: false after about 2^22 polls (each poll may suspend the thread)
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase) {
+    for (int it = 0; it < (1 << 22); ++it)
+        if (mbar_try_wait(bar, phase)) return true;
+    return false;
+}
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+template <int KAP>
+__global__ void __launch_bounds__(IPF_THREADS)
+ipf_stream_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair_ids, int C, int rps,
+                  int stage_bytes, int csr_cap, int* __restrict__ err) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int rank = (int)cl.block_rank();
+    const PairDev& P = pairs[pair_ids[blockIdx.x / C]];
+    const int N = P.N, n = P.n;
+    const int nbr = n / C, kr0 = rank * nbr;                  // owned block rows
+    const int Mc = nbr * n, k0 = kr0 * n;                     // owned blocks [k0, k0 + Mc)
+    const int nch = nbr / rps;                                // chunks per half sweep
+    const int R = rps * KAP;                                  // pixel rows per chunk
+    const int F4 = R * N / 4;                                 // float4 per chunk
+    // [stages | mbarriers | Aown, Bown, inv (Mc each) | partial sums (2 x R x n) |
+    //  staged plan: owned CSR rows and CSC columns (values, indices; csr_cap each), offsets]
+    unsigned char* stages = smem_raw;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)PK_STAGES * stage_bytes);
+    float* Aown = reinterpret_cast<float*>(bars + PK_STAGES);
+    float* Bown = Aown + Mc;
+    float* inv_s = Bown + Mc;
+    float* psum = inv_s + Mc;
+    float* v_s = psum + 2 * rps * KAP * n;
+    float* vc_s = v_s + csr_cap;
+    int* ci_s = reinterpret_cast<int*>(vc_s + csr_cap);
+    int* ri_s = ci_s + csr_cap;
+    int* rp_s = ri_s + csr_cap;                               // Mc + 1, relative offsets
+    int* cp_s = rp_s + Mc + 1;
+    const int r_base = P.rowptr[k0], c_base = P.colptr[k0];
+    const int r_cnt = P.rowptr[k0 + Mc] - r_base, c_cnt = P.colptr[k0 + Mc] - c_base;
+    const bool staged = r_cnt <= csr_cap && c_cnt <= csr_cap;
+    if (staged) {
+        const float* vt = reinterpret_cast<const float*>(P.val_t);
+        const float* vct = reinterpret_cast<const float*>(P.valc_t);
+        for (int q = threadIdx.x; q <= Mc; q += blockDim.x) {
+            rp_s[q] = P.rowptr[k0 + q] - r_base;
+            cp_s[q] = P.colptr[k0 + q] - c_base;
+        }
+        for (int e = threadIdx.x; e < r_cnt; e += blockDim.x) { ci_s[e] = P.colidx[r_base + e]; v_s[e] = vt[r_base + e]; }
+        for (int e = threadIdx.x; e < c_cnt; e += blockDim.x) { ri_s[e] = P.rowidx[c_base + e]; vc_s[e] = vct[c_base + e]; }
+    }
+    constexpr int KK = KAP * KAP;
+    const float kinvK = 1.0f / (float)(KK * KK);              // kappa^-4, exact (a power of two)
+    const int halves = 2 * P.sweeps;
+    const int total = halves * nch;                           // chunks over the whole launch
+    const float* mu_t = reinterpret_cast<const float*>(P.mu_t);
+    const float* nu_t = reinterpret_cast<const float*>(P.nu_t);
+    float* a = reinterpret_cast<float*>(P.a);
+    float* bb = reinterpret_cast<float*>(P.b);
+    const size_t row0 = (size_t)kr0 * KAP * N;                // first owned pixel row, as a float offset
+    bool bad = false;                                         // a wait of this thread timed out
+    int issued = 0, waited = 0;                               // thread 0: chunks issued / waited for
+    auto issue = [&](int gi) {                                // thread 0: chunk gi into stage gi % PK_STAGES
+        if (gi >= total) return;
+        issued = gi + 1;
+        const int h = gi / nch, c = gi - (gi / nch) * nch;
+        const float* src = ((h & 1) == 0 ? mu_t : nu_t) + row0 + (size_t)c * R * N;
+        const int s = gi % PK_STAGES;
+        const uint32_t bar = smem_addr(bars + s);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        mbar_expect_tx(bar, (uint32_t)stage_bytes);
+        bulk_load(smem_addr(stages + (size_t)s * stage_bytes), src, (uint32_t)stage_bytes, bar);
+    };
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < PK_STAGES; ++s) mbar_init(smem_addr(bars + s), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    for (int k = threadIdx.x; k < Mc; k += blockDim.x) Bown[k] = (float)KK;   // b = 1
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int gi = 0; gi < PK_STAGES; ++gi) issue(gi);
+    cl.sync();                                                // b = 1 visible to the cluster
+    const int lane = threadIdx.x & 31;
+    const int n_f = (F4 + blockDim.x - 1) / blockDim.x;       // the same trip count for every thread
+    for (int h = 0; h < halves; ++h) {
+        const int half = h & 1;
+        float* dst = half == 0 ? a : bb;
+        float* mine = half == 0 ? Aown : Bown;
+        const float* other = half == 0 ? Bown : Aown;
+        // 1 / r for the owned blocks (coarse product over the plan row / column),
+        // four blocks per thread at a time so that their remote reads overlap
+        const int* ptr = staged ? (half == 0 ? rp_s : cp_s) : (half == 0 ? P.rowptr : P.colptr);
+        const int* idx = staged ? (half == 0 ? ci_s : ri_s) : (half == 0 ? P.colidx : P.rowidx);
+        const float* val = staged ? (half == 0 ? v_s : vc_s)
+                                  : reinterpret_cast<const float*>(half == 0 ? P.val_t : P.valc_t);
+        const int rbase = staged ? 0 : k0;
+        for (int kb = threadIdx.x; kb < Mc; kb += 4 * blockDim.x) {
+            float r[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            int e0[4], e1[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int kl = kb + q * blockDim.x;
+                e0[q] = kl < Mc ? ptr[rbase + kl] : 0;
+                e1[q] = kl < Mc ? ptr[rbase + kl + 1] : 0;
+            }
+            for (int d = 0;; ++d) {
+                bool any = false;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int e = e0[q] + d;
+                    if (e < e1[q]) {
+                        any = true;
+                        const int l = idx[e], owner = l / Mc;
+                        const float* peer = cl.map_shared_rank(other, owner);
+                        r[q] += val[e] * peer[l - owner * Mc];
+                    }
+                }
+                if (!any) break;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int kl = kb + q * blockDim.x;
+                if (kl < Mc) {
+                    const float rr = r[q] * kinvK;
+                    inv_s[kl] = rr > 0.0f ? 1.0f / rr : 0.0f;
+                }
+            }
+        }
+        __syncthreads();
+        for (int c = 0; c < nch; ++c) {
+            const int gi = h * nch + c, s = gi % PK_STAGES;
+            const uint32_t phase = (uint32_t)((gi / PK_STAGES) & 1);
+            if (!bad && !mbar_wait_bounded(smem_addr(bars + s), phase)) {
+                bad = true;
+                atomicOr(err, 1);
+            }
+            if (!bad) waited = gi + 1;
+            const float4* st4 = reinterpret_cast<const float4*>(stages + (size_t)s * stage_bytes);
+            float4* d4 = reinterpret_cast<float4*>(dst + row0 + (size_t)c * R * N);
+            float* ps = psum + (c & 1) * R * n;
+            for (int j = 0; j < n_f; ++j) {
+                const int f = threadIdx.x + j * blockDim.x;
+                const bool ok = f < F4 && !bad;
+                float part = 0.0f;
+                int pr = 0, kc = 0;
+                if (ok) {
+                    pr = (4 * f) / N;
+                    const int col = 4 * f - pr * N;
+                    kc = col / KAP;
+                    const float iv = inv_s[(c * rps + pr / KAP) * n + kc];
+                    float4 v = st4[f];
+                    v.x *= iv; v.y *= iv; v.z *= iv; v.w *= iv;
+                    d4[f] = v;
+                    part = (v.x + v.y) + (v.z + v.w);
+                }
+                if (KAP == 8) part += __shfl_xor_sync(0xffffffffu, part, 1);   // the row's two float4 of the block
+                if (ok && (KAP == 4 || (lane & 1) == 0)) ps[pr * n + kc] = part;
+            }
+            __syncthreads();                                  // stage read, partial sums written
+            if (threadIdx.x == 0 && !bad) issue(gi + PK_STAGES);
+            for (int q = threadIdx.x; q < rps * n; q += blockDim.x) {
+                const int lbr = q / n, kc = q - (q / n) * n;
+                float sum = 0.0f;
+#pragma unroll
+                for (int t1 = 0; t1 < KAP; ++t1) sum += ps[(lbr * KAP + t1) * n + kc];
+                mine[(c * rps + lbr) * n + kc] = sum;
+            }
+        }
+        cluster_arrive_release();                             // this half's block sums published
+        cluster_wait_acquire();
+    }
+    // copies issued but not waited for (none when every wait succeeded; at
+    // most PK_STAGES otherwise): wait, bounded, before the CTA leaves
+    if (threadIdx.x == 0)
+        for (int gi = waited; gi < issued; ++gi)
+            (void)mbar_wait_bounded(smem_addr(bars + gi % PK_STAGES), (uint32_t)((gi / PK_STAGES) & 1));
+}
+
+// chunk rows (block rows per stage) for a pair of the group: the largest
+// divisor of n / C with at most 16 KB per chunk (at least one block row)
+static int ipf_stream_rps(int n, int C, int kappa, int N) {
+    const int nbr = n / C;
+    int best = 1;
+    for (int r = 1; r <= nbr; ++r)
+        if (nbr % r == 0 && (size_t)r * kappa * N * sizeof(float) <= 16384) best = r;
+    return best;
+}
+
+int launch_ipf_stream(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int kappa, int C, int n,
+                      int N, int* err, cudaStream_t stream) {
+    if (n_pairs <= 0) return QWB_OK;
+    if (C < 1 || C > 16 || (kappa != 4 && kappa != 8) || n % C != 0 || N % 4 != 0) return QWB_ERR_UNSUPPORTED;
+    const int rps = ipf_stream_rps(n, C, kappa, N);
+    const int stage_bytes = rps * kappa * N * (int)sizeof(float);
+    const int Mc = (n / C) * n;
+    const size_t base = (size_t)PK_STAGES * stage_bytes + PK_STAGES * sizeof(uint64_t) +
+                        3 * sizeof(float) * (size_t)Mc + 2 * sizeof(float) * (size_t)rps * kappa * n;
+    // the owned plan rows and columns (a basic plan has on average 2 per block;
+    // room for 3, else the CTA reads them from global memory)
+    int csr_cap = 3 * Mc;
+    size_t smem = base + 2 * (sizeof(float) + sizeof(int)) * (size_t)csr_cap + 2 * sizeof(int) * (size_t)(Mc + 1);
+    if (smem > 110 * 1024) { smem = base + 2 * sizeof(int) * (size_t)(Mc + 1); csr_cap = 0; }
+    if (smem > 220 * 1024) return QWB_ERR_UNSUPPORTED;
+    auto kern = kappa == 4 ? ipf_stream_kernel<4> : ipf_stream_kernel<8>;
+    QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (C > 8) QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(n_pairs * C));
+    cfg.blockDim = dim3(IPF_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    QWB_CUDA(cudaLaunchKernelEx(&cfg, kern, pairs_d, pair_ids, C, rps, stage_bytes, csr_cap, err));
+    QWB_LAUNCHED();
+    return QWB_OK;
+}
+
+// --------------------------------------------------------------------------
 // centre: s = <f~, mu~> so that the upscaled potential is f~ - s (the lower
 // bound is invariant to such shifts because both measures have mass 1).
 // --------------------------------------------------------------------------

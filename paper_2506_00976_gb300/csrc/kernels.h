@@ -103,6 +103,11 @@ int launch_support_num(const PairDev* pairs_d, const int* pair_ids, int n_pairs,
                        cudaStream_t stream);
 int launch_primal(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs,
                   int M_max, int nnz_max, bool f64, cudaStream_t stream);
+// The same sweeps with bulk-copy staging (ipf_stream_kernel): every pair of
+// the launch has coarse side n and side N (C divides n, N % 4 == 0); err: a
+// device int that a timed-out wait sets to nonzero.
+int launch_ipf_stream(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int kappa, int C, int n,
+                      int N, int* err, cudaStream_t stream);
 // primal pass with a general upscaling kernel (P.upK set; d = 2, kappa <= kappa_max <= 8;
 // all_kappa4: every pair of the launch has kappa 4, which selects the register-row kernel)
 int launch_primalk(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs, int kappa_max,
