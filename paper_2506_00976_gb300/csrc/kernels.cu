@@ -2067,10 +2067,10 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
 template <int KAP>
 __global__ void __launch_bounds__(IPF_THREADS)
 ipf_stream_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair_ids, int C, int rps,
-                  int stage_bytes, int csr_cap, int* __restrict__ err) {
+                  int stage_bytes, int* __restrict__ err) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int rank = (int)cl.block_rank();
     const PairDev& P = pairs[pair_ids[blockIdx.x / C]];
     const int N = P.N, n = P.n;
@@ -2079,33 +2079,13 @@ ipf_stream_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pai
     const int nch = nbr / rps;                                // chunks per half sweep
     const int R = rps * KAP;                                  // pixel rows per chunk
     const int F4 = R * N / 4;                                 // float4 per chunk
-    // [stages | mbarriers | Aown, Bown, inv (Mc each) | partial sums (2 x R x n) |
-    //  staged plan: owned CSR rows and CSC columns (values, indices; csr_cap each), offsets]
+    // [stages | mbarriers | Aown, Bown, inv (Mc each) | partial sums (2 x R x n)]
     unsigned char* stages = smem_raw;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)PK_STAGES * stage_bytes);
     float* Aown = reinterpret_cast<float*>(bars + PK_STAGES);
     float* Bown = Aown + Mc;
     float* inv_s = Bown + Mc;
     float* psum = inv_s + Mc;
-    float* v_s = psum + 2 * rps * KAP * n;
-    float* vc_s = v_s + csr_cap;
-    int* ci_s = reinterpret_cast<int*>(vc_s + csr_cap);
-    int* ri_s = ci_s + csr_cap;
-    int* rp_s = ri_s + csr_cap;                               // Mc + 1, relative offsets
-    int* cp_s = rp_s + Mc + 1;
-    const int r_base = P.rowptr[k0], c_base = P.colptr[k0];
-    const int r_cnt = P.rowptr[k0 + Mc] - r_base, c_cnt = P.colptr[k0 + Mc] - c_base;
-    const bool staged = r_cnt <= csr_cap && c_cnt <= csr_cap;
-    if (staged) {
-        const float* vt = reinterpret_cast<const float*>(P.val_t);
-        const float* vct = reinterpret_cast<const float*>(P.valc_t);
-        for (int q = threadIdx.x; q <= Mc; q += blockDim.x) {
-            rp_s[q] = P.rowptr[k0 + q] - r_base;
-            cp_s[q] = P.colptr[k0 + q] - c_base;
-        }
-        for (int e = threadIdx.x; e < r_cnt; e += blockDim.x) { ci_s[e] = P.colidx[r_base + e]; v_s[e] = vt[r_base + e]; }
-        for (int e = threadIdx.x; e < c_cnt; e += blockDim.x) { ri_s[e] = P.rowidx[c_base + e]; vc_s[e] = vct[c_base + e]; }
-    }
     constexpr int KK = KAP * KAP;
     const float kinvK = 1.0f / (float)(KK * KK);              // kappa^-4, exact (a power of two)
     const int halves = 2 * P.sweeps;
@@ -2144,44 +2124,20 @@ ipf_stream_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pai
         float* dst = half == 0 ? a : bb;
         float* mine = half == 0 ? Aown : Bown;
         const float* other = half == 0 ? Bown : Aown;
-        // 1 / r for the owned blocks (coarse product over the plan row / column),
-        // four blocks per thread at a time so that their remote reads overlap
-        const int* ptr = staged ? (half == 0 ? rp_s : cp_s) : (half == 0 ? P.rowptr : P.colptr);
-        const int* idx = staged ? (half == 0 ? ci_s : ri_s) : (half == 0 ? P.colidx : P.rowidx);
-        const float* val = staged ? (half == 0 ? v_s : vc_s)
-                                  : reinterpret_cast<const float*>(half == 0 ? P.val_t : P.valc_t);
-        const int rbase = staged ? 0 : k0;
-        for (int kb = threadIdx.x; kb < Mc; kb += 4 * blockDim.x) {
-            float r[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-            int e0[4], e1[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int kl = kb + q * blockDim.x;
-                e0[q] = kl < Mc ? ptr[rbase + kl] : 0;
-                e1[q] = kl < Mc ? ptr[rbase + kl + 1] : 0;
+        // 1 / r for the owned blocks (coarse product over the plan row / column;
+        // staging the plan in shared memory measured slower: fewer resident CTAs)
+        const int* ptr = half == 0 ? P.rowptr : P.colptr;
+        const int* idx = half == 0 ? P.colidx : P.rowidx;
+        const float* val = reinterpret_cast<const float*>(half == 0 ? P.val_t : P.valc_t);
+        for (int kl = threadIdx.x; kl < Mc; kl += blockDim.x) {
+            float r = 0.0f;
+            for (int e = ptr[k0 + kl]; e < ptr[k0 + kl + 1]; ++e) {
+                const int l = idx[e], owner = l / Mc;
+                const float* peer = cl.map_shared_rank(other, owner);
+                r += val[e] * peer[l - owner * Mc];
             }
-            for (int d = 0;; ++d) {
-                bool any = false;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int e = e0[q] + d;
-                    if (e < e1[q]) {
-                        any = true;
-                        const int l = idx[e], owner = l / Mc;
-                        const float* peer = cl.map_shared_rank(other, owner);
-                        r[q] += val[e] * peer[l - owner * Mc];
-                    }
-                }
-                if (!any) break;
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int kl = kb + q * blockDim.x;
-                if (kl < Mc) {
-                    const float rr = r[q] * kinvK;
-                    inv_s[kl] = rr > 0.0f ? 1.0f / rr : 0.0f;
-                }
-            }
+            r *= kinvK;
+            inv_s[kl] = r > 0.0f ? 1.0f / r : 0.0f;
         }
         __syncthreads();
         for (int c = 0; c < nch; ++c) {
@@ -2250,13 +2206,8 @@ int launch_ipf_stream(const PairDev* pairs_d, const int* pair_ids, int n_pairs, 
     const int rps = ipf_stream_rps(n, C, kappa, N);
     const int stage_bytes = rps * kappa * N * (int)sizeof(float);
     const int Mc = (n / C) * n;
-    const size_t base = (size_t)PK_STAGES * stage_bytes + PK_STAGES * sizeof(uint64_t) +
+    const size_t smem = (size_t)PK_STAGES * stage_bytes + PK_STAGES * sizeof(uint64_t) +
                         3 * sizeof(float) * (size_t)Mc + 2 * sizeof(float) * (size_t)rps * kappa * n;
-    // the owned plan rows and columns (a basic plan has on average 2 per block;
-    // room for 3, else the CTA reads them from global memory)
-    int csr_cap = 3 * Mc;
-    size_t smem = base + 2 * (sizeof(float) + sizeof(int)) * (size_t)csr_cap + 2 * sizeof(int) * (size_t)(Mc + 1);
-    if (smem > 110 * 1024) { smem = base + 2 * sizeof(int) * (size_t)(Mc + 1); csr_cap = 0; }
     if (smem > 220 * 1024) return QWB_ERR_UNSUPPORTED;
     auto kern = kappa == 4 ? ipf_stream_kernel<4> : ipf_stream_kernel<8>;
     QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -2273,7 +2224,7 @@ int launch_ipf_stream(const PairDev* pairs_d, const int* pair_ids, int n_pairs, 
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    QWB_CUDA(cudaLaunchKernelEx(&cfg, kern, pairs_d, pair_ids, C, rps, stage_bytes, csr_cap, err));
+    QWB_CUDA(cudaLaunchKernelEx(&cfg, kern, pairs_d, pair_ids, C, rps, stage_bytes, err));
     QWB_LAUNCHED();
     return QWB_OK;
 }
