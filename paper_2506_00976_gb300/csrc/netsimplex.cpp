@@ -23,11 +23,13 @@
 //   * leaving arc by the strongly feasible rule (the last blocking arc met
 //     when the pivot cycle is traversed from its apex along the entering
 //     arc's direction), which prevents cycling under degeneracy;
-//   * after each pivot the re-hung subtree gets its depths from its new
-//     parent and its potentials shifted by one common amount (its internal
-//     arcs do not change); every V pivots all potentials are recomputed from
-//     the tree and re-centred, so that neither the shifts' rounding nor the
-//     artificial cost eats their precision;
+//   * the apex of a pivot cycle is found by walking up from both ends of the
+//     entering arc in turn, stamping the nodes, until one walk meets the
+//     other's trail (no depths are kept); after the pivot the re-hung subtree
+//     gets its potentials shifted by one common amount (its internal arcs do
+//     not change); every V pivots all potentials are recomputed from the tree
+//     and re-centred, so that neither the shifts' rounding nor the artificial
+//     cost eats their precision;
 //   * a solve can start from the final tree of another solve with the same
 //     supplies (a feasible, strongly feasible basis for any costs): the C-bar
 //     problem starts from the C~ optimum;
@@ -78,7 +80,9 @@ struct Solver {
     double BIG = 0.0, eps = 0.0;
     std::vector<double> supply;
     std::vector<signed char> art_up;  // artificial arc of node v: 1 = v -> root
-    std::vector<int> parent, depth, first_child, next_sib, prev_sib;
+    std::vector<int> parent, first_child, next_sib, prev_sib;
+    std::vector<int64_t> mark;        // apex search: 2 * stamp + side of the last walk through a node
+    int64_t stamp = 0;
     std::vector<int64_t> pred;        // arc joining v and parent[v]
     std::vector<signed char> up;      // 1 if pred[v] is directed v -> parent[v]
     std::vector<double> flow;         // flow on pred[v]
@@ -137,24 +141,21 @@ struct Solver {
         while (!stack.empty()) {
             int v = stack.back();
             stack.pop_back();
-            depth[v] = depth[parent[v]] + 1;
             pot_from_parent(v);
             for (int c = first_child[v]; c >= 0; c = next_sib[c]) stack.push_back(c);
         }
     }
     // the re-hung subtree keeps its internal arcs: its potentials move by one
-    // common amount, its depths follow from the new parent
+    // common amount
     void shift_subtree(int r) {
         const double old = pot[r];
         pot_from_parent(r);
         const double d = pot[r] - old;
-        depth[r] = depth[parent[r]] + 1;
         stack.clear();
         for (int c = first_child[r]; c >= 0; c = next_sib[c]) stack.push_back(c);
         while (!stack.empty()) {
             int v = stack.back();
             stack.pop_back();
-            depth[v] = depth[parent[v]] + 1;
             pot[v] += d;
             for (int c = first_child[v]; c >= 0; c = next_sib[c]) stack.push_back(c);
         }
@@ -179,7 +180,7 @@ struct Solver {
         supply[root] = sb - sa;
         art_up.assign(V, 0);
         for (int v = 0; v < n; ++v) art_up[v] = a[v] > 0.0 ? 1 : 0;
-        parent.assign(V, -1); depth.assign(V, 0);
+        parent.assign(V, -1); mark.assign(V, -1); stamp = 0;
         first_child.assign(V, -1); next_sib.assign(V, -1); prev_sib.assign(V, -1);
         pred.assign(V, -1); up.assign(V, 0); flow.assign(V, 0.0); pot.assign(V, 0.0);
         block = std::max<int64_t>(64, (int64_t)std::sqrt((double)NM));
@@ -190,7 +191,6 @@ struct Solver {
     void init_star(const double* a, const double* b) {
         for (int v = 0; v < n + m; ++v) {
             add_child(root, v);
-            depth[v] = 1;
             pred[v] = NM + v;
             up[v] = art_up[v];
             flow[v] = (v < n) ? a[v] : b[v - n];
@@ -361,13 +361,27 @@ struct Solver {
     void pivot(int64_t e) {
         const int k = tail(e);
         const int l = n + (int)(e % m);   // entering arcs are real arcs
-        int u = k, w = l;
-        while (u != w) {
-            if (depth[u] > depth[w]) u = parent[u];
-            else if (depth[w] > depth[u]) w = parent[w];
-            else { u = parent[u]; w = parent[w]; }
+        // apex: alternate single steps up from k and from l, stamping nodes,
+        // until a walk reaches a node the other walk has passed (the root
+        // ends a walk; both ends lie in the one spanning tree)
+        ++stamp;
+        const int64_t sk = 2 * stamp, sl = 2 * stamp + 1;
+        int u = k, w = l, apex = -1;
+        mark[u] = sk;
+        if (mark[w] == sk) apex = w;
+        else mark[w] = sl;
+        while (apex < 0) {
+            if (u != root) {
+                u = parent[u];
+                if (mark[u] == sl) { apex = u; break; }
+                mark[u] = sk;
+            }
+            if (w != root) {
+                w = parent[w];
+                if (mark[w] == sk) { apex = w; break; }
+                mark[w] = sl;
+            }
         }
-        const int apex = u;
         double delta = std::numeric_limits<double>::infinity();
         for (int v = l; v != apex; v = parent[v])      // traversed upward
             if (!up[v]) delta = std::min(delta, flow[v]);
