@@ -73,7 +73,9 @@ def _check(r, ref, mu, nu, N, kappa, p, prec, plan):
 
 @pytest.mark.parametrize("N,kappa,p,cls", [(16, 4, 2.0, "gauss"), (32, 4, 1.0, "field"),
                                             (32, 8, 2.0, "cauchy"), (24, 2, 2.0, "white"),
-                                            (40, 8, 1.5, "blobs3"), (36, 6, 2.0, "gauss")])
+                                            (40, 8, 1.5, "blobs3"), (36, 6, 2.0, "gauss"),
+                                            (27, 3, 2.0, "field"), (20, 5, 1.0, "gauss"),
+                                            (21, 7, 2.0, "blobs3"), (8, 1, 2.0, "cauchy")])
 @pytest.mark.parametrize("kind", ["gauss1", "random"])
 @pytest.mark.parametrize("prec", ["mixed", "f64"])
 def test_primal_kernel_pass(N, kappa, p, cls, kind, prec):
@@ -81,7 +83,8 @@ def test_primal_kernel_pass(N, kappa, p, cls, kind, prec):
     same coarse plan and the same number of sweeps (the oracle runs them all:
     xi = 0), for a Gaussian kernel over the in-block offsets and a random
     positive kernel; tails of ragged blocks per CTA (N / kappa not a multiple
-    of anything) are covered by N = 24, 36, 40."""
+    of anything) are covered by N = 24, 36, 40; odd kappa and kappa = 1 take
+    the scalar sweep and evaluation paths, kappa 2, 4, 8 the fused sweep."""
     mu, nu = synth.make_measure(N, cls, 41, 0), synth.make_measure(N, cls, 41, 1)
     plan = _plan(mu, nu, N, kappa, p)
     K = O.gaussian_kernel(kappa, 1.0) if kind == "gauss1" else _random_kernel(kappa, 7)
