@@ -66,6 +66,7 @@ struct GridCost {
     const double* tab;   // ns x ns, tab[|dk1| * ns + |dk2|]
     int ns;
     const double* refl = nullptr;   // ns x (2 ns - 1): refl[d1][ns - 1 + d2] = tab[d1][|d2|]
+    bool separable = false;         // tab[d1][d2] == tab[d1][0] + tab[0][d2] exactly (e.g. p = 2)
     double operator()(int i, int j) const {
         const int d1 = std::abs(i / ns - j / ns), d2 = std::abs(i % ns - j % ns);
         return tab[d1 * ns + d2];
@@ -324,7 +325,15 @@ struct Solver {
         const double* pg = pot.data() + n;
         std::vector<double>& rcs = row_buf;
         rcs.resize(m);
+        // separable grid costs: every row's min_j (c_ij + pot_j) by two 1-D
+        // min-plus passes (O(ns^3) for all rows instead of O(ns^4)); a row
+        // whose minimum clears -eps by more than the rounding margin has no
+        // violator, the others are scanned exactly as before
+        bool filter = false;
+        if constexpr (std::is_same<Cost, GridCost>::value) filter = cst.separable;
+        if (filter) row_minima_separable();
         for (int i = 0; i < n; ++i) {
+            if (filter && rowmin[i] - pot[i] >= -eps + rowmin_margin) continue;
             double best = -eps;
             int64_t dummy = -1;
             scan_run(i, 0, m, best, dummy);          // row minimum below -eps?
@@ -344,6 +353,43 @@ struct Solver {
         }
         return added;
     }
+    // rowmin[i] ~ min_j (c_ij + pot_j) for separable grid costs
+    // c_ij = A(|i1 - j1|) + B(|i2 - j2|): H[j1][i2] = min_j2 (B + pot), then
+    // rowmin[i1][i2] = min_j1 (A + H).  Each is within a few roundings of the
+    // exact minimum; rowmin_margin bounds that gap.
+    std::vector<double> rowmin, hbuf;
+    double rowmin_margin = 0.0;
+    void row_minima_separable() {
+        if constexpr (std::is_same<Cost, GridCost>::value) {
+            const int ns = cst.ns;
+            const double* pg = pot.data() + n;
+            rowmin.resize(n);
+            hbuf.resize((size_t)ns * ns);
+            double pmax = 0.0, cmax = 0.0;
+            for (int j = 0; j < m; ++j) pmax = std::max(pmax, std::fabs(pg[j]));
+            for (int d = 0; d < ns; ++d) cmax = std::max(cmax, cst.tab[(size_t)(ns - 1) * ns + d]);
+            for (int j1 = 0; j1 < ns; ++j1)
+                for (int i2 = 0; i2 < ns; ++i2) {
+                    double mn = HUGE_VAL;
+                    for (int j2 = 0; j2 < ns; ++j2)
+                        mn = std::min(mn, cst.tab[std::abs(i2 - j2)] + pg[j1 * ns + j2]);
+                    hbuf[(size_t)j1 * ns + i2] = mn;
+                }
+            for (int i1 = 0; i1 < ns; ++i1)
+                for (int i2 = 0; i2 < ns; ++i2) {
+                    double mn = HUGE_VAL;
+                    for (int j1 = 0; j1 < ns; ++j1)
+                        mn = std::min(mn, cst.tab[(size_t)std::abs(i1 - j1) * ns] + hbuf[(size_t)j1 * ns + i2]);
+                    rowmin[i1 * ns + i2] = mn;
+                }
+            // three roundings of terms below cmax + pmax each, on both sides of
+            // the comparison (with the potential of the row): a wide margin
+            double pimax = 0.0;
+            for (int i = 0; i < n; ++i) pimax = std::max(pimax, std::fabs(pot[i]));
+            rowmin_margin = 16.0 * 0x1p-52 * (cmax + pmax + pimax) + 1e-300;
+        }
+    }
+
     // the costs of row i (grid costs through the reflected table rows)
     void row_costs(int i, double* out) const {
         if constexpr (std::is_same<Cost, GridCost>::value) {
@@ -624,7 +670,11 @@ int grid_solve(int32_t n_side, const double* tab, const double* a, const double*
         const int st = grid_candidates(n_side, tab, a, b, cand);
         if (st) return st;
     }
-    return solve(M, M, GridCost{tab, n_side, refl.data()}, maxc, a, b, out, max_pivots, warm, basis_out,
+    bool sep = true;
+    for (int d1 = 0; d1 < n_side && sep; ++d1)
+        for (int d2 = 0; d2 < n_side; ++d2)
+            if (tab[(size_t)d1 * n_side + d2] != tab[(size_t)d1 * n_side] + tab[d2]) { sep = false; break; }
+    return solve(M, M, GridCost{tab, n_side, refl.data(), sep}, maxc, a, b, out, max_pivots, warm, basis_out,
                  ms ? &cand : nullptr);
 }
 }  // namespace
