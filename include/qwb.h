@@ -155,6 +155,17 @@ int qwb_coarse_cost(qwb_ctx* ctx, const qwb_problem* prob, const double* mu_d,
 int qwb_coarse_solve(int32_t n_src, int32_t n_dst, const double* C_h, const double* a_h,
                      const double* b_h, int32_t* rowptr_h, int32_t* col_h, double* val_h,
                      int32_t* nnz_out, double* f_h, double* g_h, double* obj_out);
+/* The same exact solve for a problem on an n_side x n_side grid whose cost
+ * depends only on the offset: C_kl = tab_h[|k1 - l1| * n_side + |k2 - l2|]
+ * (k = k1 * n_side + k2; the block-centre cost C~ of Sec. 3.4 / 3.5 with
+ * tab = rho(kappa d)^p), without an M x M matrix (M = n_side^2).  Solved
+ * coarse to fine (the problem on the grid of 2 x 2 cell sums first, its
+ * support's children priced first, full scans until no arc has a negative
+ * reduced cost).  Outputs and errors as qwb_coarse_solve with n_src = n_dst
+ * = M.  Needs no GPU. */
+int qwb_coarse_solve_grid(int32_t n_side, const double* tab_h, const double* a_h, const double* b_h,
+                          int32_t* rowptr_h, int32_t* col_h, double* val_h, int32_t* nnz_out,
+                          double* f_h, double* g_h, double* obj_out);
 
 /* ------------------------------------------------------------------------ */
 /* Pass (b): primal upscaling + IPF + upper bound.  Sec. 3.4 (eq. coupling    */

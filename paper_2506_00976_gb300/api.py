@@ -101,6 +101,31 @@ def coarse_solve(C, a, b):
             "obj": obj.value}
 
 
+def coarse_solve_grid(tab, a, b):
+    """qwb_coarse_solve_grid (host network simplex, offset-table cost on an
+    n x n grid): dict with CSR plan, f, g, obj (numpy)."""
+    tab = np.ascontiguousarray(tab, dtype=np.float64)
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    ns = tab.shape[0]
+    M = ns * ns
+    rowptr = np.zeros(M + 1, dtype=np.int32)
+    col = np.zeros(2 * M, dtype=np.int32)
+    val = np.zeros(2 * M, dtype=np.float64)
+    nnz = ctypes.c_int32()
+    f = np.zeros(M)
+    g = np.zeros(M)
+    obj = ctypes.c_double()
+    pd = lambda x: x.ctypes.data_as(_lib.P_double)  # noqa: E731
+    pi = lambda x: x.ctypes.data_as(_lib.P_int32)   # noqa: E731
+    check(_lib.load().qwb_coarse_solve_grid(ns, pd(tab), pd(a), pd(b), pi(rowptr), pi(col), pd(val),
+                                            ctypes.byref(nnz), pd(f), pd(g), ctypes.byref(obj)),
+          "qwb_coarse_solve_grid")
+    k = nnz.value
+    return {"rowptr": rowptr, "col": col[:k].copy(), "val": val[:k].copy(), "f": f, "g": g,
+            "obj": obj.value}
+
+
 def primal_upscale_ipf(mu, nu, N, kappa, p, rowptr, col, val, sweeps=50, prec="mixed",
                        want_scalings=False, d=2):
     """qwb_primal_upscale_ipf: the primal upscaling upper bound from a coarse CSR plan."""

@@ -37,6 +37,33 @@ const char* qwb_last_error(void) { return qwb::g_last_error.c_str(); }
 
 int64_t qwb_kernel_launch_count(void) { return qwb::g_launches.load(); }
 
+}  // extern "C"
+
+// Copies a solution to the caller's buffers (the plan arrays only when given).
+static int export_solution(const qwb::NSSolution& sol, int st, const char* who, int32_t n_src, int32_t n_dst,
+                           int32_t* rowptr_h, int32_t* col_h, double* val_h, int32_t* nnz_out, double* f_h,
+                           double* g_h, double* obj_out) {
+    if (st != QWB_OK) {
+        qwb::set_last_error(st == QWB_ERR_NOT_CONVERGED
+                                ? std::string(who) + ": pivot cap reached or artificial flow left"
+                                : std::string(who) + ": invalid costs or masses");
+        return st;
+    }
+    const int32_t nnz = (int32_t)sol.col.size();
+    if (nnz_out) *nnz_out = nnz;
+    if (rowptr_h) {
+        std::memcpy(rowptr_h, sol.rowptr.data(), sizeof(int32_t) * (n_src + 1));
+        std::memcpy(col_h, sol.col.data(), sizeof(int32_t) * nnz);
+        std::memcpy(val_h, sol.val.data(), sizeof(double) * nnz);
+    }
+    if (f_h) std::memcpy(f_h, sol.f.data(), sizeof(double) * n_src);
+    if (g_h) std::memcpy(g_h, sol.g.data(), sizeof(double) * n_dst);
+    if (obj_out) *obj_out = sol.obj;
+    return QWB_OK;
+}
+
+extern "C" {
+
 int qwb_coarse_solve(int32_t n_src, int32_t n_dst, const double* C_h, const double* a_h,
                      const double* b_h, int32_t* rowptr_h, int32_t* col_h, double* val_h,
                      int32_t* nnz_out, double* f_h, double* g_h, double* obj_out) {
@@ -56,23 +83,32 @@ int qwb_coarse_solve(int32_t n_src, int32_t n_dst, const double* C_h, const doub
         qwb::set_last_error("qwb_coarse_solve: host allocation failed");
         return QWB_ERR_OOM;
     }
-    if (st != QWB_OK) {
-        qwb::set_last_error(st == QWB_ERR_NOT_CONVERGED
-                                ? "qwb_coarse_solve: pivot cap reached or artificial flow left"
-                                : "qwb_coarse_solve: invalid costs or masses");
-        return st;
+    return export_solution(sol, st, "qwb_coarse_solve", n_src, n_dst, rowptr_h, col_h, val_h, nnz_out, f_h, g_h,
+                           obj_out);
+}
+
+int qwb_coarse_solve_grid(int32_t n_side, const double* tab_h, const double* a_h, const double* b_h,
+                          int32_t* rowptr_h, int32_t* col_h, double* val_h, int32_t* nnz_out, double* f_h,
+                          double* g_h, double* obj_out) {
+    if (n_side <= 0 || !tab_h || !a_h || !b_h) {
+        qwb::set_last_error("qwb_coarse_solve_grid: bad size or null input");
+        return QWB_ERR_INVALID_ARG;
     }
-    const int32_t nnz = (int32_t)sol.col.size();
-    if (nnz_out) *nnz_out = nnz;
-    if (rowptr_h) {
-        std::memcpy(rowptr_h, sol.rowptr.data(), sizeof(int32_t) * (n_src + 1));
-        std::memcpy(col_h, sol.col.data(), sizeof(int32_t) * nnz);
-        std::memcpy(val_h, sol.val.data(), sizeof(double) * nnz);
+    if ((rowptr_h || col_h || val_h) && !(rowptr_h && col_h && val_h && nnz_out)) {
+        qwb::set_last_error("qwb_coarse_solve_grid: plan outputs need rowptr, col, val and nnz_out");
+        return QWB_ERR_INVALID_ARG;
     }
-    if (f_h) std::memcpy(f_h, sol.f.data(), sizeof(double) * n_src);
-    if (g_h) std::memcpy(g_h, sol.g.data(), sizeof(double) * n_dst);
-    if (obj_out) *obj_out = sol.obj;
-    return QWB_OK;
+    const int32_t M = n_side * n_side;
+    qwb::NSSolution sol;
+    int st;
+    try {
+        st = qwb::network_simplex_grid(n_side, tab_h, a_h, b_h, sol);
+    } catch (...) {
+        qwb::set_last_error("qwb_coarse_solve_grid: host allocation failed");
+        return QWB_ERR_OOM;
+    }
+    return export_solution(sol, st, "qwb_coarse_solve_grid", M, M, rowptr_h, col_h, val_h, nnz_out, f_h, g_h,
+                           obj_out);
 }
 
 }  // extern "C"

@@ -94,3 +94,34 @@ def test_network_simplex_rejects_bad_input(lib):
         _solve(-np.ones((2, 2)), np.array([0.5, 0.5]), np.array([0.5, 0.5]))
     with pytest.raises(QwbError, match="INVALID_ARG"):
         _solve(np.ones((2, 2)), np.array([np.nan, 1.0]), np.array([0.5, 0.5]))
+
+
+@pytest.mark.parametrize("ns,kappa,p,cls", [(8, 4, 2.0, "gauss"), (16, 4, 2.0, "white"), (16, 2, 1.0, "field"),
+                                           (20, 4, 1.5, "cauchy"), (24, 4, 2.0, "field"), (24, 2, 1.0, "gauss")])
+def test_network_simplex_grid_table(lib, ns, kappa, p, cls):
+    """qwb_coarse_solve_grid (offset-table cost, coarse to fine for even sides
+    >= 16, the separable row-minimum filter for p = 2) against the oracle's
+    exact solver on the dense C~ matrix: the same optimal objective, a basic
+    plan with the given marginals, and potentials feasible up to rounding
+    (g = f^c, f = g^c in FP64) whose dual objective is the optimum."""
+    from paper_2506_00976_gb300 import api
+    N = ns * kappa
+    mu, nu = synth.make_measure(N, cls, 41, 0), synth.make_measure(N, cls, 41, 1)
+    if cls == "field":                               # zero-mass cells on both sides
+        mu = mu.reshape(N, N).copy(); mu[:kappa, :kappa] = 0.0; mu = (mu / mu.sum()).ravel()
+        nu = nu.reshape(N, N).copy(); nu[-kappa:, -2 * kappa:] = 0.0; nu = (nu / nu.sum()).ravel()
+    a, b = O.sumpool(mu, N, kappa), O.sumpool(nu, N, kappa)
+    C = O.coarse_cost_centre(N, kappa, p)
+    tab = np.array([[C[0, d1 * ns + d2] for d2 in range(ns)] for d1 in range(ns)])
+    r = api.coarse_solve_grid(tab, a, b)
+    _, _, _, obj = O.exact_ot(C, a, b)
+    assert r["obj"] == pytest.approx(obj, rel=1e-10)
+    M = ns * ns
+    assert len(r["val"]) <= 2 * M - 1
+    plan = np.zeros((M, M))
+    for i in range(M):
+        for e in range(r["rowptr"][i], r["rowptr"][i + 1]):
+            plan[i, r["col"][e]] += r["val"][e]
+    assert np.abs(plan.sum(1) - a).max() < 1e-13 and np.abs(plan.sum(0) - b).max() < 1e-13
+    assert (C - r["f"][:, None] - r["g"][None, :]).min() >= -1e-12 * C.max()
+    assert float(r["f"] @ a + r["g"] @ b) == pytest.approx(obj, rel=1e-9, abs=1e-12)
