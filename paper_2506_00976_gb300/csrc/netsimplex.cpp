@@ -565,6 +565,37 @@ int solve(int32_t n_src, int32_t n_dst, Cost cst, double maxc, const double* a, 
         out.pivots = piv;
         return QWB_OK;
     }
+    if constexpr (std::is_same<Cost, GridCost>::value) {
+        if (cst.separable) {
+            // separable grid costs c = A(|i1 - j1|) + B(|i2 - j2|): each
+            // transform by two 1-D min-plus passes, O(ns^3) (the values may
+            // differ from the direct minima by rounding only)
+            const int ns = cst.ns;
+            const double* tb = cst.tab;                   // A(d) = tb[d * ns], B(d) = tb[d]
+            std::vector<double> T((size_t)ns * ns), src(n_src);
+            auto transform = [&](const double* h, double* outv) {
+                // outv[j1, j2] = min_{i1, i2} A(|i1 - j1|) + B(|i2 - j2|) - h[i1, i2]
+                for (int i1 = 0; i1 < ns; ++i1)
+                    for (int j2 = 0; j2 < ns; ++j2) {
+                        double mn = HUGE_VAL;
+                        for (int i2 = 0; i2 < ns; ++i2) mn = std::min(mn, tb[std::abs(i2 - j2)] - h[i1 * ns + i2]);
+                        T[(size_t)i1 * ns + j2] = mn;
+                    }
+                for (int j1 = 0; j1 < ns; ++j1)
+                    for (int j2 = 0; j2 < ns; ++j2) {
+                        double mn = HUGE_VAL;
+                        for (int i1 = 0; i1 < ns; ++i1)
+                            mn = std::min(mn, tb[(size_t)std::abs(i1 - j1) * ns] + T[(size_t)i1 * ns + j2]);
+                        outv[j1 * ns + j2] = mn;
+                    }
+            };
+            transform(out.f.data(), g);
+            transform(g, src.data());
+            out.f.swap(src);
+            out.pivots = piv;
+            return QWB_OK;
+        }
+    }
     // g = f^c, then f = g^c, row by row; each row is walked as runs of
     // contiguous costs (one run per grid row for table costs) with four
     // independent min chains in the reduction
