@@ -361,7 +361,7 @@ int qwb_batch_coarse_plan(qwb_batch* batch, int32_t pair, int32_t* rowptr_h, int
  * sides.  C | QWB_IPF_BULK (C = 2..16) selects the form that stages the
  * source values by bulk copies (cp.async.bulk into a ring of shared-memory
  * stages, completion on mbarriers, every wait bounded) for groups whose pairs
- * share N; a timed-out wait makes qwb_batch_results return CUDA.  Overrides
+ * share N; a timed-out wait makes qwb_batch_results return TIMEOUT.  Overrides
  * the autotuner's choice, which times both forms; synchronises the device
  * and drops the batch's captured fine-pass graphs.  Errors: INVALID_ARG, CUDA. */
 #define QWB_IPF_BULK 32

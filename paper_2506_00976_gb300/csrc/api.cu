@@ -1313,9 +1313,9 @@ static int batch_results(qwb_batch* b, qwb_result* out, cudaStream_t s) {
         if (b->flags & QWB_FLAG_NO_PRIMAL) { r.ub_primal = HUGE_VAL; r.w_hat_p = HUGE_VAL; }
         if (b->flags & QWB_FLAG_NO_DUAL) { r.lb = 0.0; r.lb_p = -HUGE_VAL; }
         r.t_coarse_cost_ms = tc; r.t_solve_ms = b->t_solve_ms; r.t_primal_ms = tp; r.t_dual_ms = td;
-        r.status = dev_err ? QWB_ERR_CUDA : b->status[t];
+        r.status = dev_err ? QWB_ERR_TIMEOUT : b->status[t];
     }
-    if (dev_err) return fail(QWB_ERR_CUDA, "a bounded device wait timed out (bulk-copy IPF sweeps)");
+    if (dev_err) return fail(QWB_ERR_TIMEOUT, "a bounded device wait timed out (bulk-copy IPF sweeps)");
     return QWB_OK;
 }
 
