@@ -12,7 +12,7 @@ equation or algorithm.  Library primitives (reshape, sum, min, matmul, sqrt)
 serve as steps; there is no blocking or fusion beyond what the definitions
 state, apart from chunking loops over output indices to bound memory.
 
-Conventions (readings where the paper is silent; each is listed in the design doc):
+Conventions (readings where the paper is silent):
   * the grid is [N]^d with d = 2 (images, the default) or d = 3 (volumes);
     grid points are 0-based coordinates with unit spacing, flattened
     row-major (i = row * N + col in 2-D, ((x1 * N) + x2) * N + x3 in 3-D);
