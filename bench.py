@@ -147,6 +147,8 @@ def run_gpu(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus:
+        raise SystemExit(f"bench.py: --gpus {args.gpus} but {world} rank(s) were started")
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
@@ -270,7 +272,9 @@ def run_gpu(args):
         except (OSError, ValueError):
             pass
         sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
-        fp32_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12       # TFLOP/s
+        fp32_nominal = sms * 128 * 2 * sm_max * 1e6 / 1e12    # TFLOP/s from unit counts and clock
+        alu = alu_rates(api)
+        fp32_peak = alu["fp32_peak_tflops"]                    # measured FFMA rate x 2 flops
         hbm = float(peaks.get("hbm_gbs") or 6800.0)
         achieved = pair_ops_ct / (ct_ms * 1e-3) / 1e12 if ct_ms > 0 else None
         traffic = _ct_traffic(_kernel_digest())
@@ -307,9 +311,15 @@ def run_gpu(args):
                          "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
                          "frac": round(achieved / fp32_peak, 4) if achieved else None,
                          "traffic": traffic,
-                         "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 ops x "
-                                        f"{sm_max:.0f} MHz (MEASURED_PEAKS sm_max_mhz)",
+                         "peak_source": "measured: fma.rn.f32 rate on this GPU x 2 flops "
+                                        "(qwb_probe_fp32_rate, 8 chains per thread, one full wave)",
+                         "peak_nominal": round(fp32_nominal, 2),
+                         "frac_of_nominal": round(achieved / fp32_nominal, 4) if achieved else None,
+                         "nominal_source": f"{sms} SMs x 128 FP32 lanes x 2 ops x {sm_max:.0f} MHz",
+                         "frac_of_mix_ceiling": round(pair_ops_ct / 2 / (ct_ms * 1e-3) / alu["mix_ceiling_per_s"], 4)
+                         if ct_ms > 0 else None,
                          "ops_per_launch": pair_ops_ct, "avg_launch_ms": round(ct_ms, 4)},
+            "alu_rates": alu,
             "passes": passes,
             "host_solve": {"seconds": round(host_solve_s, 3),
                            "pairs_per_s": round(n / host_solve_s, 3),
@@ -351,6 +361,30 @@ def run_gpu(args):
         dist.barrier()
         dist.destroy_process_group()
     return out
+
+
+_ALU = None
+
+
+def alu_rates(api):
+    """FP32 instruction rates of this GPU (qwb_probe_fp32_rate): the measured
+    FP32 peak (fma.rn.f32 x 2 flops) and the c-transform's instruction-mix
+    ceiling (the best two-candidate mix: packed round-down subtraction or two
+    scalar ones, then a three-input min)."""
+    global _ALU
+    if _ALU is not None:
+        return _ALU
+    rows = [api.probe_fp32_rate(k) for k in range(len(api.PROBE_KINDS))]
+    mix = max(rows[6]["per_s"], rows[7]["per_s"])
+    _ALU = {"fp32_peak_tflops": round(2.0 * rows[0]["per_s"] / 1e12, 3),
+            "mix_ceiling_per_s": mix,
+            "mix_ceiling_tops": round(2.0 * mix / 1e12, 3),
+            "per_clk_per_sm": {r["kind"]: round(r["per_clk_per_sm"], 2) for r in rows},
+            "sm_mhz": round(statistics.median(r["sm_mhz"] for r in rows), 1),
+            "ctas_per_sm": {r["kind"]: r["ctas_per_sm"] for r in rows},
+            "what": "FP32 results (packed: 2 per instruction; mixes: candidates) per clock per SM from "
+                    "the SM cycle counter; 8 independent chains per thread, 256-thread CTAs, one wave"}
+    return _ALU
 
 
 # ----------------------------------------------------------------------------
@@ -539,7 +573,8 @@ def _kernel_upscale_workload(api, dev, args):
             peaks = json.load(fh)
     except (OSError, ValueError):
         pass
-    fp32_peak = props.multi_processor_count * 128 * 2 * float(peaks.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
+    fp32_nominal = props.multi_processor_count * 128 * 2 * float(peaks.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
+    fp32_peak = alu_rates(api)["fp32_peak_tflops"]
     achieved = flops / (kms * 1e-3) / 1e12 if kms > 0 else None
     g5 = ubs["gaussian_500"]
     out.update({
@@ -548,6 +583,8 @@ def _kernel_upscale_workload(api, dev, args):
         "roofline": {"bound": "fp32", "achieved": round(achieved, 3) if achieved else None,
                      "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
                      "frac": round(achieved / fp32_peak, 4) if achieved else None,
+                     "peak_source": "measured fma.rn.f32 rate (qwb_probe_fp32_rate) x 2 flops",
+                     "frac_of_nominal": round(achieved / fp32_nominal, 4) if achieved else None,
                      "flops_per_launch": flops},
         "ub_mean": {k: float(v.mean()) for k, v in ubs.items()},
         "gaussian_500_below": {"uniform": int((g5 < ubs["uniform"]).sum()),
@@ -675,6 +712,51 @@ def run_reference(args):
                     "d2h_bytes_per_step": 0}}
 
 
+def launch_ranks(n, argv):
+    """`bench.py --gpus N` outside a launcher: start N ranks on this node (one
+    process per GPU) with torch.distributed.run on 127.0.0.1 and return its
+    exit status; each rank reads RANK / LOCAL_RANK / WORLD_SIZE from the env."""
+    import socket
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        port = so.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__), *argv]
+    return subprocess.call(cmd)
+
+
+def run_dry(args):
+    """The multi-rank plumbing without a GPU (gloo): every rank builds its own
+    pair list (weak scaling), ranks meet at a barrier, and rank 0 reports the
+    per-rank pair counts and the maximum over ranks of a per-rank time."""
+    import torch.distributed as dist
+    from paper_2506_00976_gb300 import shard
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world != args.gpus:
+        raise SystemExit(f"bench.py: --gpus {args.gpus} but {world} rank(s) were started")
+    if world > 1:
+        dist.init_process_group("gloo")
+    t0 = time.perf_counter()
+    mus, _ = _workload_arrays(rank, args.pairs_per_class)
+    local_s = time.perf_counter() - t0
+    digest = hashlib.sha256(mus[0].tobytes()).hexdigest()[:12]
+    counts, digests = [len(mus)] * world, [digest] * world
+    if world > 1:
+        gathered = [None] * world
+        dist.all_gather_object(gathered, (len(mus), digest))
+        counts = [g[0] for g in gathered]
+        digests = [g[1] for g in gathered]
+        dist.barrier()
+    slowest = shard.max_over_ranks(local_s)
+    if world > 1:
+        dist.destroy_process_group()
+    if rank != 0:
+        return None
+    return {"dry_run": True, "n_gpus": world, "pairs_per_rank": counts, "first_pair_digest": digests,
+            "max_rank_seconds": round(slowest, 4), "backend": "gloo" if world > 1 else "none"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -691,13 +773,22 @@ def main():
     ap.add_argument("--skip-plain", action="store_true", help="time only the batched form")
     ap.add_argument("--skip-e2e", action="store_true", help="skip the end-to-end timing")
     ap.add_argument("--only", default="", choices=["", "ipf_hbm", "uneven_200", "differentiable_256",
-                                                   "workload_64", "kernel_upscale"],
+                                                   "workload_64", "kernel_upscale", "alu_rates"],
                     help="run one secondary workload alone and print its JSON (profiling)")
     ap.add_argument("--skip-workloads", action="store_true",
                     help="skip the uneven 200-pair and differentiable 256x256 measurements")
     ap.add_argument("--skip-separable", action="store_true",
                     help="skip the separable p = 2 c-transform measurement")
+    ap.add_argument("--dry-run", action="store_true",
+                    help="check the multi-rank launch on the CPU (gloo), no GPU work")
     args = ap.parse_args()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ and args.impl == "native":
+        sys.exit(launch_ranks(args.gpus, sys.argv[1:]))    # one process per GPU
+    if args.dry_run:
+        out = run_dry(args)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
     if args.warmup < 3 and args.impl == "native":
         args.warmup = 3
     if args.only:
@@ -707,7 +798,8 @@ def main():
         torch.cuda.set_device(dev)
         fn = {"ipf_hbm": _ipf_hbm_workload, "uneven_200": _uneven_workload,
               "differentiable_256": _differentiable_workload, "workload_64": _workload_64,
-              "kernel_upscale": _kernel_upscale_workload}[args.only]
+              "kernel_upscale": _kernel_upscale_workload,
+              "alu_rates": lambda a, d, r: alu_rates(a)}[args.only]
         print(json.dumps({args.only: fn(api, dev, args)}), flush=True)
         return
     out = run_reference(args) if args.impl == "reference" else run_gpu(args)

@@ -272,9 +272,14 @@ int qwb_ctransform_shape(qwb_ctx* ctx, int32_t N, int32_t d, double p, const dou
  *   N <= 256 (QWB_ERR_UNSUPPORTED beyond); h_d, out_d: N*N FP64 device.
  *   Every call shares the static array and rewrites what it reads, so
  *   calls whose GPU work overlaps (other streams, concurrent host threads)
- *   race and corrupt each other: serialise them.  The first call on a
- *   device looks up the array's address (cudaGetSymbolAddress); make it
- *   before any stream capture.  Asynchronous on `stream`.
+ *   race and corrupt each other: serialise them.
+ *   The first call on each device does a one-time set-up: it looks up the
+ *   array's device address (cudaGetSymbolAddress) and, under lazy module
+ *   loading (the CUDA default), loads the library's kernels, which itself
+ *   takes device memory.  Make that first call (a warm-up call will do)
+ *   before any stream capture and while device memory can still be
+ *   allocated.  The launch plan reaches the device as kernel arguments; no
+ *   call copies host memory.  Asynchronous on `stream`.
  * Errors: INVALID_ARG (null pointer, p < 1), UNSUPPORTED (N > 256), CUDA. */
 int qwb_ctransform_noalloc(int32_t N, double p, const double* h_d, double* out_d, void* stream);
 
@@ -351,6 +356,12 @@ int qwb_batch_potentials(qwb_batch* batch, int32_t pair, double* f_d, double* g_
  * Errors: INVALID_ARG (bad pair, not solved, cap < nnz). */
 int qwb_batch_coarse_plan(qwb_batch* batch, int32_t pair, int32_t* rowptr_h, int32_t* col_h,
                           double* val_h, int32_t cap, int32_t* nnz_out);
+/* Pair t's exact coarse dual potentials of the C~ problem (Sec. 2.1 dual,
+ * Sec. 3.5: f~ feeds the dual pass, g~ its symmetric form), from the last
+ * qwb_batch_solve, before the passes shift them: f_h, g_h (host, M FP64
+ * each, either may be NULL) with f~_k + g~_l <= C~_kl.
+ * Errors: INVALID_ARG (bad pair, not solved). */
+int qwb_batch_coarse_potentials(qwb_batch* batch, int32_t pair, double* f_h, double* g_h);
 /* Where the fine FP32 IPF sweeps of the batch's 2-D FP32 pairs with block side
  * 4 or 8 run (Sec. 3.4, IPF paragraph; Alg. 4; the values do not depend on
  * it): C = 0 inside the primal-pass kernel, one CTA per pair; C = 2, 4, 8, 16
@@ -410,6 +421,27 @@ int qwb_batch_tuning(qwb_batch* batch, char* json_out, int32_t capacity);
 const char* qwb_status_string(int status);
 /* Message of the last failed call on this thread ("" if none). */
 const char* qwb_last_error(void);
+/* Measured FP32 instruction rate of the current device: the denominator of
+ * the rooflines of the passes bound by FP32 arithmetic on the CUDA cores
+ * (the c-transform of Sec. 4 and the C-bar reduction of Sec. 3.2; neither is
+ * a dense contraction).  The paper has no counterpart.  Every thread runs
+ * eight independent dependency chains of one instruction stream, on
+ * SMs x ctas_per_sm CTAs of 256 threads (1 <= ctas_per_sm <= 8; one wave),
+ * `iters` loop trips of 128 chain steps each, after a shorter warm-up run:
+ *   kind 0 fma.rn.f32     1 sub.rm.f32     2 min.f32 (two inputs)
+ *        3 min.f32 (three inputs)     4 fma.rn.f32x2     5 sub.rm.f32x2
+ *        6 sub.rm.f32x2 then one three-input min.f32 (the line-paired
+ *          c-transform's two candidates)
+ *        7 two sub.rm.f32 then one three-input min.f32 (two candidates)
+ * ctas_per_sm is lowered to what can be resident at once.
+ * out_h (host, 5 doubles): [0] FP32 results (packed: two per instruction;
+ * kinds 6, 7: candidates) per clock per SM, from the SM cycle counter;
+ * [1] the same per second over the whole device, from CUDA events; [2] the
+ * SM clock (MHz) over the timed run; [3] the SM count; [4] the CTAs per SM
+ * used.  Allocates a small
+ * scratch, uses the current device and the legacy default stream, and
+ * synchronises.  Errors: INVALID_ARG, CUDA. */
+int qwb_probe_fp32_rate(int32_t kind, int32_t ctas_per_sm, int32_t iters, double* out_h);
 /* Number of device kernels this library has launched in this process. */
 int64_t qwb_kernel_launch_count(void);
 

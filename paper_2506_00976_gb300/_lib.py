@@ -86,6 +86,7 @@ SIGNATURES = [
     ("qwb_batch_potentials", c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
     ("qwb_batch_coarse_plan", c_int32, [c_void_p, c_int32, P_int32, P_int32, P_double, c_int32,
                                         P_int32]),
+    ("qwb_batch_coarse_potentials", c_int32, [c_void_p, c_int32, P_double, P_double]),
     ("qwb_batch_fine_scalings", c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
     ("qwb_batch_set_ipf_cluster", c_int32, [c_void_p, c_int32]),
     ("qwb_batch_set_upscale_kernel", c_int32, [c_void_p, c_int32, c_void_p]),
@@ -94,6 +95,7 @@ SIGNATURES = [
     ("qwb_status_string", ctypes.c_char_p, [c_int32]),
     ("qwb_last_error", ctypes.c_char_p, []),
     ("qwb_kernel_launch_count", c_int64, []),
+    ("qwb_probe_fp32_rate", c_int32, [c_int32, c_int32, c_int32, P_double]),
 ]
 
 _LIB = None

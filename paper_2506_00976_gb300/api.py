@@ -83,6 +83,8 @@ def coarse_solve(C, a, b):
     C = np.ascontiguousarray(C, dtype=np.float64)
     a = np.ascontiguousarray(a, dtype=np.float64)
     b = np.ascontiguousarray(b, dtype=np.float64)
+    if C.ndim != 2 or a.shape != (C.shape[0],) or b.shape != (C.shape[1],):
+        raise ValueError("coarse_solve: C must be (n, m) with a of n and b of m entries")
     n, m = C.shape
     rowptr = np.zeros(n + 1, dtype=np.int32)
     col = np.zeros(n + m, dtype=np.int32)
@@ -107,8 +109,12 @@ def coarse_solve_grid(tab, a, b):
     tab = np.ascontiguousarray(tab, dtype=np.float64)
     a = np.ascontiguousarray(a, dtype=np.float64)
     b = np.ascontiguousarray(b, dtype=np.float64)
+    if tab.ndim != 2 or tab.shape[0] != tab.shape[1]:
+        raise ValueError("coarse_solve_grid: tab must be a square (n_side, n_side) table")
     ns = tab.shape[0]
     M = ns * ns
+    if a.shape != (M,) or b.shape != (M,):
+        raise ValueError(f"coarse_solve_grid: a and b must have n_side^2 = {M} entries")
     rowptr = np.zeros(M + 1, dtype=np.int32)
     col = np.zeros(2 * M, dtype=np.int32)
     val = np.zeros(2 * M, dtype=np.float64)
@@ -320,6 +326,17 @@ class Batch:
                 plan[k, col[e]] = val[e]
         return plan
 
+    def coarse_potentials(self, t):
+        """Pair t's exact coarse dual potentials (f~, g~) of the last solve (numpy, M each)."""
+        pr = self.problems[t]
+        M = (pr.N // pr.kappa) ** (pr.d or 2)
+        f = np.zeros(M)
+        g = np.zeros(M)
+        check(_lib.load().qwb_batch_coarse_potentials(self._h, int(t), f.ctypes.data_as(_lib.P_double),
+                                                      g.ctypes.data_as(_lib.P_double)),
+              "qwb_batch_coarse_potentials")
+        return f, g
+
     def set_ipf_cluster(self, C):
         """Run the fine IPF sweeps inside the primal kernel (0) or on clusters of C CTAs."""
         check(_lib.load().qwb_batch_set_ipf_cluster(self._h, int(C)), "qwb_batch_set_ipf_cluster")
@@ -372,6 +389,21 @@ def bounds(mus, nus, problems, ipf_sweeps=50, prec="mixed", batched=True, thread
                                  int(flags), res, _prec(prec), int(bool(batched)), int(threads),
                                  _stream(mus[0])), "qwb_bounds")
     return [r.as_dict() for r in res]
+
+
+PROBE_KINDS = ("fma.rn.f32", "sub.rm.f32", "min.f32 (2 inputs)", "min.f32 (3 inputs)", "fma.rn.f32x2",
+               "sub.rm.f32x2", "sub.rm.f32x2 + 3-input min (2 candidates)",
+               "2 x sub.rm.f32 + 3-input min (2 candidates)")
+
+
+def probe_fp32_rate(kind, ctas_per_sm=8, iters=2048):
+    """Measured FP32 instruction rate of the current device (qwb_probe_fp32_rate):
+    results per clock per SM, results per second, the SM clock (MHz) and the SM count."""
+    out = np.zeros(5)
+    check(_lib.load().qwb_probe_fp32_rate(int(kind), int(ctas_per_sm), int(iters),
+                                          out.ctypes.data_as(_lib.P_double)), "qwb_probe_fp32_rate")
+    return {"kind": PROBE_KINDS[kind], "per_clk_per_sm": float(out[0]), "per_s": float(out[1]),
+            "sm_mhz": float(out[2]), "sms": int(out[3]), "ctas_per_sm": int(out[4])}
 
 
 def kernel_launch_count():

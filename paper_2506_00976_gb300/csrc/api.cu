@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "fault.h"
 #include "kernels.h"
 #include "netsimplex.h"
 
@@ -212,6 +213,8 @@ struct qwb_batch {
     int* ipf_ids_d = nullptr;
     int ipf_C = 0;                      // + QWB_IPF_BULK: the bulk-copy variant
     int* dev_err = nullptr;             // device error word of bounded waits (0 = none)
+    unsigned long long wait_ns = 0;     // limit of every bounded device wait (QWB_WAIT_TIMEOUT_MS)
+    int fault_skip_chunk = -1;          // QWB_FAULT ipf_bulk_skip_chunk (tests), else -1
     // pairs upscaled with a general kernel K (primalk_kernel, 2-D, kappa <= 8):
     // K per kappa, and prim_ids_d = [uniform pairs..., K pairs...]
     std::vector<std::pair<int, std::vector<double>>> upk;   // (kappa, K)
@@ -334,7 +337,9 @@ static std::vector<int> build_ipf_groups(qwb_batch* b) {
 // the fine sweeps of group G (pairs ids[0..cnt)) on clusters
 static int launch_ipf_group(qwb_batch* b, const qwb_batch::IpfGroup& G, const int* ids, int cnt, int M,
                             cudaStream_t s) {
-    if (G.stream) return launch_ipf_stream(b->pairs_d, ids, cnt, G.kappa, G.C, G.n_same, G.N_same, b->dev_err, s);
+    if (G.stream)
+        return launch_ipf_stream(b->pairs_d, ids, cnt, G.kappa, G.C, G.n_same, G.N_same, b->dev_err, b->wait_ns,
+                                 b->fault_skip_chunk, s);
     return launch_ipf_fine(b->pairs_d, ids, cnt, G.kappa, G.C, M, 0, s);
 }
 
@@ -381,6 +386,8 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
     qwb_batch* b = new qwb_batch();
     b->ctx = ctx; b->n = n; b->f64 = (prec == QWB_PREC_F64); b->sweeps = sweeps;
     b->flags = flags;
+    b->wait_ns = wait_timeout_ns();
+    b->fault_skip_chunk = (int)fault_param("ipf_bulk_skip_chunk", -1);
     b->probs.assign(probs, probs + n);
     const size_t tsz = b->f64 ? 8 : 4;
     // sizes
@@ -1478,6 +1485,18 @@ int qwb_batch_coarse_plan(qwb_batch* b, int32_t pair, int32_t* rowptr_h, int32_t
     if (rowptr_h) std::memcpy(rowptr_h, ph + L.rowptr, sizeof(int) * (M + 1));
     if (col_h) std::memcpy(col_h, ph + L.col, sizeof(int) * nnz);
     if (val_h) std::memcpy(val_h, ph + L.val, sizeof(double) * nnz);
+    return QWB_OK;
+}
+
+int qwb_batch_coarse_potentials(qwb_batch* b, int32_t pair, double* f_h, double* g_h) {
+    if (!b || pair < 0 || pair >= b->n)
+        return fail(QWB_ERR_INVALID_ARG, "qwb_batch_coarse_potentials: bad pair");
+    if (!b->solved) return fail(QWB_ERR_INVALID_ARG, "qwb_batch_coarse_potentials: the batch has not been solved");
+    const int M = b->Ms[pair];
+    const PlanLayout L = plan_layout(M);
+    const char* ph = b->plan_h + b->plan_off[pair];
+    if (f_h) std::memcpy(f_h, ph + L.fco, sizeof(double) * M);
+    if (g_h) std::memcpy(g_h, ph + L.gco, sizeof(double) * M);
     return QWB_OK;
 }
 

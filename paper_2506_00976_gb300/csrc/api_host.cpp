@@ -1,10 +1,13 @@
 // api_host.cpp -- host-only parts of the C ABI: status strings, thread-local
 // error messages, the launch counter and the exact coarse solve entry point.
+#include <algorithm>
 #include <atomic>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
 #include "../../include/qwb.h"
+#include "fault.h"
 #include "netsimplex.h"
 
 namespace qwb {
@@ -14,6 +17,26 @@ static std::atomic<int64_t> g_launches{0};
 
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 void count_launch(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+int64_t fault_param(const char* site, int64_t def) {
+    const char* env = std::getenv("QWB_FAULT");
+    if (!env || !*env) return def;
+    const std::string all(env), key = std::string(site) + "=";
+    size_t pos = 0;
+    while (pos <= all.size()) {
+        const size_t end = std::min(all.find(',', pos), all.size());
+        const std::string item = all.substr(pos, end - pos);
+        if (item.compare(0, key.size(), key) == 0) return std::strtoll(item.c_str() + key.size(), nullptr, 10);
+        pos = end + 1;
+    }
+    return def;
+}
+
+uint64_t wait_timeout_ns() {
+    const char* env = std::getenv("QWB_WAIT_TIMEOUT_MS");
+    const double ms = (env && *env) ? std::strtod(env, nullptr) : 2000.0;
+    return (uint64_t)((ms > 0.0 ? ms : 2000.0) * 1e6);
+}
 
 }  // namespace qwb
 

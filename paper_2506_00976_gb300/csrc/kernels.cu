@@ -2053,11 +2053,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t phase) {
         : "=r"(done) : "r"(bar), "r"(phase) : "memory");
     return done != 0;
 }
-// bounded wait: false after about 2^22 polls (each poll may suspend the thread)
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase) {
-    for (int it = 0; it < (1 << 22); ++it)
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// bounded wait: false once timeout_ns nanoseconds of the global timer have
+// passed without the phase completing (each poll may suspend the thread)
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase, unsigned long long timeout_ns) {
+    const unsigned long long t0 = global_ns();
+    for (;;) {
         if (mbar_try_wait(bar, phase)) return true;
-    return false;
+        if (global_ns() - t0 > timeout_ns) return false;
+    }
 }
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
@@ -2067,7 +2075,7 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
 template <int KAP>
 __global__ void __launch_bounds__(IPF_THREADS)
 ipf_stream_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair_ids, int C, int rps,
-                  int stage_bytes, int* __restrict__ err) {
+                  int stage_bytes, int* __restrict__ err, unsigned long long timeout_ns, int skip_chunk) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -2100,6 +2108,7 @@ ipf_stream_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pai
     auto issue = [&](int gi) {                                // thread 0: chunk gi into stage gi % PK_STAGES
         if (gi >= total) return;
         issued = gi + 1;
+        if (gi == skip_chunk) return;                         // host-requested fault: never issued
         const int h = gi / nch, c = gi - (gi / nch) * nch;
         const float* src = ((h & 1) == 0 ? mu_t : nu_t) + row0 + (size_t)c * R * N;
         const int s = gi % PK_STAGES;
@@ -2143,7 +2152,7 @@ ipf_stream_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pai
         for (int c = 0; c < nch; ++c) {
             const int gi = h * nch + c, s = gi % PK_STAGES;
             const uint32_t phase = (uint32_t)((gi / PK_STAGES) & 1);
-            if (!bad && !mbar_wait_bounded(smem_addr(bars + s), phase)) {
+            if (!bad && !mbar_wait_bounded(smem_addr(bars + s), phase, timeout_ns)) {
                 bad = true;
                 atomicOr(err, 1);
             }
@@ -2186,7 +2195,9 @@ ipf_stream_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pai
     // most PK_STAGES otherwise): wait, bounded, before the CTA leaves
     if (threadIdx.x == 0)
         for (int gi = waited; gi < issued; ++gi)
-            (void)mbar_wait_bounded(smem_addr(bars + gi % PK_STAGES), (uint32_t)((gi / PK_STAGES) & 1));
+            if (gi != skip_chunk)
+                (void)mbar_wait_bounded(smem_addr(bars + gi % PK_STAGES), (uint32_t)((gi / PK_STAGES) & 1),
+                                        timeout_ns);
 }
 
 // chunk rows (block rows per stage) for a pair of the group: the largest
@@ -2200,7 +2211,7 @@ static int ipf_stream_rps(int n, int C, int kappa, int N) {
 }
 
 int launch_ipf_stream(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int kappa, int C, int n,
-                      int N, int* err, cudaStream_t stream) {
+                      int N, int* err, unsigned long long timeout_ns, int skip_chunk, cudaStream_t stream) {
     if (n_pairs <= 0) return QWB_OK;
     if (C < 1 || C > 16 || (kappa != 4 && kappa != 8) || n % C != 0 || N % 4 != 0) return QWB_ERR_UNSUPPORTED;
     const int rps = ipf_stream_rps(n, C, kappa, N);
@@ -2224,7 +2235,7 @@ int launch_ipf_stream(const PairDev* pairs_d, const int* pair_ids, int n_pairs, 
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    QWB_CUDA(cudaLaunchKernelEx(&cfg, kern, pairs_d, pair_ids, C, rps, stage_bytes, err));
+    QWB_CUDA(cudaLaunchKernelEx(&cfg, kern, pairs_d, pair_ids, C, rps, stage_bytes, err, timeout_ns, skip_chunk));
     QWB_LAUNCHED();
     return QWB_OK;
 }

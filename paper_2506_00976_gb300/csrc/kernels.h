@@ -105,9 +105,11 @@ int launch_primal(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, 
                   int M_max, int nnz_max, bool f64, cudaStream_t stream);
 // The same sweeps with bulk-copy staging (ipf_stream_kernel): every pair of
 // the launch has coarse side n and side N (C divides n, N % 4 == 0); err: a
-// device int that a timed-out wait sets to nonzero.
+// device int that a timed-out wait sets to nonzero; timeout_ns: the limit of
+// every mbarrier wait (global timer); skip_chunk >= 0: every CTA leaves that
+// chunk unissued (host-side fault injection for the time-out path), else -1.
 int launch_ipf_stream(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int kappa, int C, int n,
-                      int N, int* err, cudaStream_t stream);
+                      int N, int* err, unsigned long long timeout_ns, int skip_chunk, cudaStream_t stream);
 // primal pass with a general upscaling kernel (P.upK set; d = 2, kappa <= kappa_max <= 8;
 // all_kappa4: every pair of the launch has kappa 4, which selects the register-row kernel)
 int launch_primalk(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs, int kappa_max,

@@ -44,6 +44,7 @@
 //     (leaf elimination) and the potentials are made exactly dual feasible by
 //     one coarse c-transform each way (g = f^c, f = g^c).
 #include "netsimplex.h"
+#include "fault.h"
 
 #include <algorithm>
 #include <cmath>
@@ -495,6 +496,8 @@ int solve(int32_t n_src, int32_t n_dst, Cost cst, double maxc, const double* a, 
           const std::vector<int64_t>* candidates = nullptr, bool exact_dual = true) {
     const int64_t NM = (int64_t)n_src * n_dst;
     if (max_pivots < 0) max_pivots = 20 * NM + 1000000;
+    const int64_t cap = fault_param("ns_pivot_cap", -1);     // host-side fault injection (tests)
+    if (cap >= 0) max_pivots = std::min<int64_t>(max_pivots, cap);
     Solver<Cost> S;
     S.cst = cst;
     S.init_common(n_src, n_dst, a, b, maxc);

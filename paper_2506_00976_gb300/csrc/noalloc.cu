@@ -14,8 +14,14 @@
 //     contents; each call rewrites everything it reads before reading it;
 //   * calls whose GPU work overlaps (different streams, or host threads
 //     racing) corrupt each other's results: serialise them;
-//   * the first call on a device looks up the array's device address; make
-//     that first call before any stream capture.
+//   * the first call on a device does the set-up: it looks up the array's
+//     device address and, under lazy module loading (the CUDA default), loads
+//     the kernels, which itself takes device memory.  Make that first call
+//     before any stream capture and while memory can still be allocated.
+//
+// The launch plan (pair descriptor and work items) is written into the array
+// by a set-up kernel from values passed by value, so no call copies host
+// memory to the device.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -69,6 +75,21 @@ int scratch_for_current_device(unsigned char** out) {
     return QWB_OK;
 }
 
+// Writes the pair descriptor and the work items into the static scratch:
+// tile t (CT_TILE outputs from t * CT_TILE), input-row split r (input rows
+// [r * rows, min(N, (r + 1) * rows))), item index t * splits + r -- the same
+// items the host plan of qwb_ctransform builds.
+__global__ void noalloc_plan_kernel(PairDev P, PairDev* __restrict__ desc, CtItem* __restrict__ items,
+                                    int rows, int splits, int n_items) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *desc = P;
+    if (i < n_items) {
+        const int t = i / splits, r = i - t * splits;
+        const int r0 = r * rows;
+        items[i] = CtItem{0, t * CT_TILE, r0, min(rows, P.N - r0)};
+    }
+}
+
 }  // namespace
 }  // namespace qwb
 
@@ -99,18 +120,22 @@ extern "C" int qwb_ctransform_noalloc(int32_t N, double p, const double* h_d, do
     PairDev* desc = reinterpret_cast<PairDev*>(base + kOffDesc);
     CtItem* items = reinterpret_cast<CtItem*>(base + kOffItems);
 
-    // launch plan: 4096-output tiles, each split into about two items per SM
+    // launch plan: 4096-output tiles, each split into about two items per SM;
+    // the staged input rows of an item must fit in shared memory
     int dev = 0, sm = 148;
     QWB_CUDA(cudaGetDevice(&dev));
-    cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
+    QWB_CUDA(cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev));
     const int m = N * N;
     const int tiles = (m + CT_TILE - 1) / CT_TILE;
-    const int splits = std::max(1, std::min(std::min(N, kMaxItems / tiles), (2 * sm + tiles - 1) / tiles));
-    const int rows = (N + splits - 1) / splits;
-    CtItem host_items[kMaxItems];   // on the stack: no heap allocation either
-    int n_items = 0;
-    for (int o = 0; o < m; o += CT_TILE)
-        for (int r0 = 0; r0 < N; r0 += rows) host_items[n_items++] = {0, o, r0, std::min(rows, N - r0)};
+    const int splits0 = std::max(1, std::min(std::min(N, kMaxItems / tiles), (2 * sm + tiles - 1) / tiles));
+    const int rows_smem = (227 * 1024) / (int)(sizeof(float) * N);   // >= 227 for N <= 256
+    const int rows = std::min((N + splits0 - 1) / splits0, rows_smem);
+    const int splits = (N + rows - 1) / rows;                        // every split non-empty
+    const int n_items = tiles * splits;                              // <= 512 (splits <= max(splits0, 2))
+    if (n_items > kMaxItems) {
+        set_last_error("qwb_ctransform_noalloc: launch plan exceeds the static item list");
+        return QWB_ERR_UNSUPPORTED;
+    }
     PairDev P;
     std::memset(&P, 0, sizeof(P));
     P.N = N; P.kappa = N; P.n = 1; P.M = 1; P.p = p;
@@ -119,10 +144,9 @@ extern "C" int qwb_ctransform_noalloc(int32_t N, double p, const double* h_d, do
     P.fhat = h32; P.g = out32;
 
     // everything the kernels read is rewritten here, so the previous call's
-    // contents never leak into this one (pageable host sources are consumed
-    // before each copy call returns)
-    QWB_CUDA(cudaMemcpyAsync(desc, &P, sizeof(P), cudaMemcpyHostToDevice, s));
-    QWB_CUDA(cudaMemcpyAsync(items, host_items, sizeof(CtItem) * n_items, cudaMemcpyHostToDevice, s));
+    // contents never leak into this one; the plan travels as kernel arguments
+    noalloc_plan_kernel<<<(n_items + 255) / 256, 256, 0, s>>>(P, desc, items, rows, splits, n_items);
+    QWB_LAUNCHED();
     if (p != 2.0 && (st = launch_cost_tables(N, p, false, tab_lo, tab_hi, s))) return st;
     if ((st = launch_to_work(h_d, h32, out32, m, false, s))) return st;   // h rounded up, out = +inf
     CtConfig cfg;

@@ -1,0 +1,235 @@
+// probe.cu -- measured FP32 instruction rates of the current GPU.
+//
+// The c-transform and C-bar passes are bound by FP32 arithmetic on the CUDA
+// cores (no dense contraction, no tensor cores), so their rooflines need the
+// rate at which this GPU retires the instructions they use.  Each probe runs
+// one instruction stream per thread: eight independent dependency chains,
+// unrolled sixteen times per loop trip, on SMs x ctas_per_sm CTAs of 256
+// threads (one wave: every CTA is resident from the start).  Rates are
+// counted in FP32 results (a packed f32x2 instruction counts two; the
+// c-transform mixes count candidates, i.e. (input, output) pairs) per clock
+// per SM, from the SM cycle counter, and per second over the device, from
+// CUDA events.  Not a step of the paper: a measurement of the hardware the
+// passes are judged against.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <vector>
+
+#include "common.cuh"
+
+namespace qwb {
+namespace {
+
+constexpr int PROBE_THREADS = 256;
+constexpr int PROBE_CHAINS = 8;
+constexpr int PROBE_UNROLL = 16;
+
+__device__ __forceinline__ float p_fma(float a, float b, float c) {
+    float d;
+    asm("fma.rn.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float p_sub_rm(float a, float b) {
+    float d;
+    asm("sub.rm.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+__device__ __forceinline__ float p_min2(float a, float b) {
+    float d;
+    asm("min.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+__device__ __forceinline__ float p_min3(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long p_fma2(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long p_sub2_rm(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("sub.rm.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long p_pack(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void p_unpack(unsigned long long v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+// FP32 results per chain step of each kind (0..7)
+__host__ __device__ constexpr int probe_results_per_step(int kind) {
+    return (kind == 4 || kind == 5 || kind == 6 || kind == 7) ? 2 : 1;
+}
+
+// kind: 0 fma.rn.f32, 1 sub.rm.f32, 2 min.f32 (2 inputs), 3 min.f32 (3 inputs),
+// 4 fma.rn.f32x2, 5 sub.rm.f32x2, 6 sub.rm.f32x2 + 3-input min (two candidates),
+// 7 two sub.rm.f32 + 3-input min (two candidates).  The chains stay finite:
+// the subtrahend and addend are tiny, the multiplier just below one.
+template <int KIND>
+__global__ void __launch_bounds__(PROBE_THREADS)
+probe_kernel(int iters, float seed, float* __restrict__ sink, long long* __restrict__ cycles) {
+    float x[PROBE_CHAINS], y[PROBE_CHAINS], z[PROBE_CHAINS];
+    unsigned long long xp[PROBE_CHAINS];
+#pragma unroll
+    for (int k = 0; k < PROBE_CHAINS; ++k) {
+        x[k] = seed + 0.125f * k + 1e-3f * (float)threadIdx.x;
+        y[k] = x[k] + 0.5f;
+        z[k] = x[k] + 0.25f;
+        xp[k] = p_pack(x[k], y[k]);
+    }
+    const float a = 0.99999994f, c = 1e-30f;
+    const unsigned long long a2 = p_pack(a, a), c2 = p_pack(c, c);
+    __syncthreads();
+    long long t0 = clock64();
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < PROBE_UNROLL; ++u) {
+#pragma unroll
+            for (int k = 0; k < PROBE_CHAINS; ++k) {
+                if constexpr (KIND == 0) {
+                    x[k] = p_fma(x[k], a, c);
+                } else if constexpr (KIND == 1) {
+                    x[k] = p_sub_rm(x[k], c);
+                } else if constexpr (KIND == 2) {
+                    x[k] = p_min2(x[k], x[(k + 1) % PROBE_CHAINS]);          // chains coupled cyclically
+                } else if constexpr (KIND == 3) {
+                    x[k] = p_min3(x[k], x[(k + 1) % PROBE_CHAINS], x[(k + 2) % PROBE_CHAINS]);
+                } else if constexpr (KIND == 4) {
+                    xp[k] = p_fma2(xp[k], a2, c2);
+                } else if constexpr (KIND == 5) {
+                    xp[k] = p_sub2_rm(xp[k], c2);
+                } else if constexpr (KIND == 6) {
+                    xp[k] = p_sub2_rm(xp[k], c2);
+                    float lo, hi;
+                    p_unpack(xp[k], lo, hi);
+                    y[k] = p_min3(y[k], lo, hi);
+                } else {
+                    x[k] = p_sub_rm(x[k], c);
+                    z[k] = p_sub_rm(z[k], c);
+                    y[k] = p_min3(y[k], x[k], z[k]);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    long long t1 = clock64();
+    float acc = 0.0f;                 // only the chains this kind advanced stay live
+#pragma unroll
+    for (int k = 0; k < PROBE_CHAINS; ++k) {
+        float lo, hi;
+        p_unpack(xp[k], lo, hi);
+        if constexpr (KIND <= 3) acc += x[k];
+        else if constexpr (KIND <= 5) acc += lo + hi;
+        else if constexpr (KIND == 6) acc += lo + hi + y[k];
+        else acc += x[k] + y[k] + z[k];
+    }
+    if (acc == 1234.5f) sink[blockIdx.x * blockDim.x + threadIdx.x] = acc;   // keeps the chains live
+    if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+}
+
+template <int KIND>
+int probe_launch(int grid, int iters, float* sink, long long* cycles, cudaStream_t s) {
+    probe_kernel<KIND><<<grid, PROBE_THREADS, 0, s>>>(iters, 1.0f, sink, cycles);
+    QWB_LAUNCHED();
+    return QWB_OK;
+}
+
+const void* probe_kernel_for(int kind) {
+    switch (kind) {
+        case 0: return (const void*)probe_kernel<0>;
+        case 1: return (const void*)probe_kernel<1>;
+        case 2: return (const void*)probe_kernel<2>;
+        case 3: return (const void*)probe_kernel<3>;
+        case 4: return (const void*)probe_kernel<4>;
+        case 5: return (const void*)probe_kernel<5>;
+        case 6: return (const void*)probe_kernel<6>;
+        default: return (const void*)probe_kernel<7>;
+    }
+}
+
+int probe_dispatch(int kind, int grid, int iters, float* sink, long long* cycles, cudaStream_t s) {
+    switch (kind) {
+        case 0: return probe_launch<0>(grid, iters, sink, cycles, s);
+        case 1: return probe_launch<1>(grid, iters, sink, cycles, s);
+        case 2: return probe_launch<2>(grid, iters, sink, cycles, s);
+        case 3: return probe_launch<3>(grid, iters, sink, cycles, s);
+        case 4: return probe_launch<4>(grid, iters, sink, cycles, s);
+        case 5: return probe_launch<5>(grid, iters, sink, cycles, s);
+        case 6: return probe_launch<6>(grid, iters, sink, cycles, s);
+        case 7: return probe_launch<7>(grid, iters, sink, cycles, s);
+        default: return QWB_ERR_INVALID_ARG;
+    }
+}
+
+}  // namespace
+}  // namespace qwb
+
+using namespace qwb;
+
+extern "C" int qwb_probe_fp32_rate(int32_t kind, int32_t ctas_per_sm, int32_t iters, double* out_h) {
+    if (kind < 0 || kind > 7 || ctas_per_sm < 1 || ctas_per_sm > 8 || iters < 1 || !out_h) {
+        set_last_error("qwb_probe_fp32_rate: kind in [0, 7], ctas_per_sm in [1, 8], iters >= 1, out_h non-null");
+        return QWB_ERR_INVALID_ARG;
+    }
+    int dev = 0, sms = 0;
+    QWB_CUDA(cudaGetDevice(&dev));
+    QWB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // one wave: no more CTAs per SM than can be resident at once
+    int occ = 1;
+    QWB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, probe_kernel_for(kind), PROBE_THREADS, 0));
+    ctas_per_sm = std::max(1, std::min(ctas_per_sm, occ));
+    const int grid = sms * ctas_per_sm;
+    float* sink = nullptr;
+    long long* cycles = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int st = QWB_OK;
+    std::vector<long long> cyc(grid);
+    float ms = 0.0f;
+    auto cleanup = [&]() {
+        if (sink) cudaFree(sink);
+        if (cycles) cudaFree(cycles);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+#define PROBE_TRY(call)                                   \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) { cleanup(); return cuda_fail(e_, #call); } \
+    } while (0)
+    PROBE_TRY(cudaMalloc(&sink, sizeof(float) * (size_t)grid * PROBE_THREADS));
+    PROBE_TRY(cudaMalloc(&cycles, sizeof(long long) * (size_t)grid));
+    PROBE_TRY(cudaEventCreate(&e0));
+    PROBE_TRY(cudaEventCreate(&e1));
+    cudaStream_t s = 0;
+    // warm-up (module load, clocks up), then the timed run
+    if ((st = probe_dispatch(kind, grid, std::max(1, iters / 8), sink, cycles, s))) { cleanup(); return st; }
+    PROBE_TRY(cudaEventRecord(e0, s));
+    if ((st = probe_dispatch(kind, grid, iters, sink, cycles, s))) { cleanup(); return st; }
+    PROBE_TRY(cudaEventRecord(e1, s));
+    PROBE_TRY(cudaEventSynchronize(e1));
+    PROBE_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    PROBE_TRY(cudaMemcpy(cyc.data(), cycles, sizeof(long long) * (size_t)grid, cudaMemcpyDeviceToHost));
+#undef PROBE_TRY
+    cleanup();
+    double mean_cyc = 0.0;
+    for (long long c : cyc) mean_cyc += (double)c;
+    mean_cyc /= (double)grid;
+    const double per_cta = (double)PROBE_THREADS * iters * PROBE_UNROLL * PROBE_CHAINS *
+                           probe_results_per_step(kind);
+    out_h[0] = per_cta * ctas_per_sm / mean_cyc;                 // results per clock per SM
+    out_h[1] = per_cta * grid / (ms * 1e-3);                     // results per second, whole device
+    out_h[2] = mean_cyc / (ms * 1e-3) / 1e6;                     // SM clock (MHz) over the run
+    out_h[3] = (double)sms;
+    out_h[4] = (double)ctas_per_sm;
+    return QWB_OK;
+}

@@ -125,3 +125,30 @@ def test_network_simplex_grid_table(lib, ns, kappa, p, cls):
     assert np.abs(plan.sum(1) - a).max() < 1e-13 and np.abs(plan.sum(0) - b).max() < 1e-13
     assert (C - r["f"][:, None] - r["g"][None, :]).min() >= -1e-12 * C.max()
     assert float(r["f"] @ a + r["g"] @ b) == pytest.approx(obj, rel=1e-9, abs=1e-12)
+
+
+def test_pivot_cap_reports_not_converged(lib, monkeypatch):
+    """Host-side fault injection (QWB_FAULT=ns_pivot_cap=k): a network simplex
+    stopped after a few pivots on a problem that needs many reports
+    QWB_ERR_NOT_CONVERGED with a message, and the next call without the fault
+    solves the same problem to the oracle's optimum."""
+    from paper_2506_00976_gb300 import api
+    from paper_2506_00976_gb300._lib import QwbError
+    rng = np.random.default_rng(11)
+    n = 40
+    C = rng.random((n, n)) * 100
+    a = rng.random(n); a /= a.sum()
+    b = rng.random(n); b /= b.sum()
+    monkeypatch.setenv("QWB_FAULT", "ns_pivot_cap=3")
+    with pytest.raises(QwbError, match="NOT_CONVERGED"):
+        api.coarse_solve(C, a, b)
+    assert b"pivot cap" in lib.qwb_last_error()
+    side = 8
+    tab = (np.arange(side)[:, None] ** 2 + np.arange(side)[None, :] ** 2).astype(np.float64)
+    ga = rng.random(side * side); ga /= ga.sum()
+    gb = rng.random(side * side); gb /= gb.sum()
+    with pytest.raises(QwbError, match="NOT_CONVERGED"):
+        api.coarse_solve_grid(tab, ga, gb)
+    monkeypatch.setenv("QWB_FAULT", "")
+    r = api.coarse_solve(C, a, b)
+    assert r["obj"] == pytest.approx(O.exact_ot(C, a, b)[3], rel=1e-10)

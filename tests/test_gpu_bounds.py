@@ -216,6 +216,53 @@ def test_symmetric_dual(prec, batched):
     assert sides >= 1, "the side started from g~ never won: its path went unexercised"
 
 
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+@pytest.mark.parametrize("batched", [True, False])
+def test_symmetric_dual_vs_oracle(prec, batched):
+    """The dual pass from g~ against the oracle (Sec. 3.5 started from the
+    other coarse potential).  Both sides consume the batch's own exact coarse
+    potentials (f~, g~): the batch's lb_p equals the oracle's
+    lb_dual_symmetric (the larger of lb_dual from f~ and lb_dual_from_g from
+    g~), and the kept potentials f, g equal the oracle's on the kept side,
+    element by element.  The single-pair entry point run from g~ with the
+    measures swapped computes the same g~-side pass (the cost is symmetric):
+    its potentials equal lb_dual_from_g's with f and g exchanged."""
+    N, kappa = 16, 4
+    pairs = [(synth.make_measure(N, c, 81, 2 * t), synth.make_measure(N, c, 81, 2 * t + 1))
+             for t, c in enumerate(["gauss", "cauchy", "field", "white", "blobs3", "gauss"])]
+    tol = TOL[prec]
+    g_side_kept = 0
+    for p in (1.0, 2.0):
+        mus = [T(a) for a, _ in pairs]
+        nus = [T(b) for _, b in pairs]
+        with api.Batch([(N, kappa, p)] * len(pairs), ipf_sweeps=3, prec=prec, flags=32) as b:
+            b.coarse(mus, nus, batched=batched); b.solve(); b.fine(mus, nus, batched=batched)
+            res = b.results()
+            for t, (mu, nu) in enumerate(pairs):
+                f_c, g_c = b.coarse_potentials(t)
+                A = O.lb_dual(mu, nu, N, kappa, p, f_c=f_c)
+                B = O.lb_dual_from_g(mu, nu, N, kappa, p, g_c)
+                S = O.lb_dual_symmetric(mu, nu, N, kappa, p, f_c=f_c, g_c=g_c)
+                fmax = max(np.abs(X["f"]).max() + np.abs(X["g"]).max() for X in (A, B))
+                slack = tol * max(abs(S["lb_p"]), 1e-3) + 64 * 6e-8 * fmax * (prec == "mixed")
+                assert res[t]["status"] == 0
+                assert abs(res[t]["lb_p"] - S["lb_p"]) <= slack, (p, t, res[t]["lb_p"], A["lb_p"], B["lb_p"])
+                atol = 8 * np.spacing(np.float32(fmax)) if prec == "mixed" else 1e-10 * (1 + fmax)
+                f, g = (x.cpu().numpy() for x in b.potentials(t))
+                if abs(A["lb_p"] - B["lb_p"]) > 2 * slack:     # the kept side is unambiguous
+                    np.testing.assert_allclose(f, S["f"], rtol=0, atol=atol)
+                    np.testing.assert_allclose(g, S["g"], rtol=0, atol=atol)
+                    g_side_kept += B["lb_p"] > A["lb_p"]
+                else:                                           # either side is a correct choice
+                    assert any(np.abs(f - X["f"]).max() <= atol and np.abs(g - X["g"]).max() <= atol
+                               for X in (A, B))
+                r = api.dual_upscale_ctransform(T(nu), T(mu), N, kappa, p, g_c, prec=prec)
+                np.testing.assert_allclose(r["f"].cpu().numpy(), B["g"], rtol=0, atol=atol)
+                np.testing.assert_allclose(r["g"].cpu().numpy(), B["f"], rtol=0, atol=atol)
+                assert abs(r["lb_p"] - B["lb_p"]) <= slack
+    assert g_side_kept >= 1, "no pair kept the g~ side: its potentials were never compared"
+
+
 @pytest.mark.parametrize("sweeps", [1, 7, 50])
 @pytest.mark.parametrize("batched", [True, False])
 @pytest.mark.parametrize("cluster", [2, 4, 8, 16])
