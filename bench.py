@@ -374,17 +374,32 @@ def alu_rates(api):
     global _ALU
     if _ALU is not None:
         return _ALU
+    api.probe_fp32_rate(0, iters=16384)             # clocks up before the measured runs
     rows = [api.probe_fp32_rate(k) for k in range(len(api.PROBE_KINDS))]
     mix = max(rows[6]["per_s"], rows[7]["per_s"])
     _ALU = {"fp32_peak_tflops": round(2.0 * rows[0]["per_s"] / 1e12, 3),
             "mix_ceiling_per_s": mix,
             "mix_ceiling_tops": round(2.0 * mix / 1e12, 3),
-            "per_clk_per_sm": {r["kind"]: round(r["per_clk_per_sm"], 2) for r in rows},
-            "sm_mhz": round(statistics.median(r["sm_mhz"] for r in rows), 1),
-            "ctas_per_sm": {r["kind"]: r["ctas_per_sm"] for r in rows},
-            "what": "FP32 results (packed: 2 per instruction; mixes: candidates) per clock per SM from "
-                    "the SM cycle counter; 8 independent chains per thread, 256-thread CTAs, one wave"}
+            "per_s": {r["kind"]: round(r["per_s"] / 1e12, 4) for r in rows},
+            "per_cycle_per_sm": {r["kind"]: round(r["per_clk_per_sm"], 2) for r in rows},
+            "counter_mhz": {r["kind"]: round(r["counter_mhz"], 1) for r in rows},
+            "ctas_per_sm": {r["kind"]: [r["ctas_per_sm"], r["most_ctas_on_one_sm"]] for r in rows},
+            "what": "FP32 results (packed: 2 per instruction; mixes: candidates) per second (x1e12, CUDA "
+                    "events) and per cycle of each SM's cycle counter; 8 independent chains per thread, "
+                    "256-thread CTAs; ctas_per_sm = [requested, most on one SM]"}
     return _ALU
+
+
+def alu_sweep(api):
+    """The c-transform's instructions (kinds 3, 5, 6, 7 of qwb_probe_fp32_rate)
+    at 1-8 resident 256-thread CTAs per SM: how the rates depend on the number
+    of warps an SM can interleave."""
+    api.probe_fp32_rate(0, iters=16384)
+    out = {}
+    for k in (0, 3, 5, 6, 7):
+        out[api.PROBE_KINDS[k]] = {c: round(api.probe_fp32_rate(k, ctas_per_sm=c)["per_s"] / 1e12, 3)
+                                   for c in (1, 2, 3, 4, 6, 8)}
+    return {"per_s_x1e12_by_ctas_per_sm": out}
 
 
 # ----------------------------------------------------------------------------
@@ -773,7 +788,7 @@ def main():
     ap.add_argument("--skip-plain", action="store_true", help="time only the batched form")
     ap.add_argument("--skip-e2e", action="store_true", help="skip the end-to-end timing")
     ap.add_argument("--only", default="", choices=["", "ipf_hbm", "uneven_200", "differentiable_256",
-                                                   "workload_64", "kernel_upscale", "alu_rates"],
+                                                   "workload_64", "kernel_upscale", "alu_rates", "alu_sweep"],
                     help="run one secondary workload alone and print its JSON (profiling)")
     ap.add_argument("--skip-workloads", action="store_true",
                     help="skip the uneven 200-pair and differentiable 256x256 measurements")
@@ -799,7 +814,8 @@ def main():
         fn = {"ipf_hbm": _ipf_hbm_workload, "uneven_200": _uneven_workload,
               "differentiable_256": _differentiable_workload, "workload_64": _workload_64,
               "kernel_upscale": _kernel_upscale_workload,
-              "alu_rates": lambda a, d, r: alu_rates(a)}[args.only]
+              "alu_rates": lambda a, d, r: alu_rates(a),
+              "alu_sweep": lambda a, d, r: alu_sweep(a)}[args.only]
         print(json.dumps({args.only: fn(api, dev, args)}), flush=True)
         return
     out = run_reference(args) if args.impl == "reference" else run_gpu(args)

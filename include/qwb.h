@@ -249,12 +249,17 @@ int qwb_ctransform(qwb_ctx* ctx, int32_t N, double p, const double* h_d, double*
  *   TC       input columns per register chunk, must divide N;
  *   packing  0 scalar subtractions; 1 (MIXED only) two columns per packed
  *            f32x2 subtraction; 2 (MIXED only) two input lines per packed
- *            subtraction.
+ *            subtraction; 3-6 (MIXED, d = 2 only) packing 2 with the
+ *            register budget cut for 3 (packings 3, 4) or 2 (5, 6) resident
+ *            CTAs per SM, the p = 2 window costs formed on the fly (3, 6) or
+ *            kept in registers (4, 5).
  *   in_rows  input lines per work item (0 = the default split); work items
  *            that see part of the input lines combine by atomic min.
  * Compiled shapes: packing 0: (R, TC) in {1,2,4,8,16} x {same} and (16,8),
  * (8,16); packing 1: (8,8), (16,8), (16,16); packing 2: (8,8), (16,8), (8,16),
- * (16,16).  Other shapes return QWB_ERR_UNSUPPORTED.
+ * (16,16); packing 3: (8,8); packing 4: (8,8), (8,16); packing 5: (8,16),
+ * (16,8), (16,16); packing 6: (8,16).  Other shapes return
+ * QWB_ERR_UNSUPPORTED.
  * h_d, out_d: N^d FP64 device.  Synchronises `stream` before returning.
  * Errors: INVALID_ARG, UNSUPPORTED, CUDA, OOM. */
 int qwb_ctransform_shape(qwb_ctx* ctx, int32_t N, int32_t d, double p, const double* h_d,
@@ -434,11 +439,12 @@ const char* qwb_last_error(void);
  *          c-transform's two candidates)
  *        7 two sub.rm.f32 then one three-input min.f32 (two candidates)
  * ctas_per_sm is lowered to what can be resident at once.
- * out_h (host, 5 doubles): [0] FP32 results (packed: two per instruction;
- * kinds 6, 7: candidates) per clock per SM, from the SM cycle counter;
- * [1] the same per second over the whole device, from CUDA events; [2] the
- * SM clock (MHz) over the timed run; [3] the SM count; [4] the CTAs per SM
- * used.  Allocates a small
+ * out_h (host, 6 doubles): [0] FP32 results (packed: two per instruction;
+ * kinds 6, 7: candidates) per cycle per SM, over each SM's span of its cycle
+ * counter (first CTA start to last CTA end); [1] the same per second over
+ * the whole device, from CUDA events; [2] the cycle counter's rate (MHz)
+ * over the timed run; [3] the SM count; [4] the CTAs per SM requested after
+ * the occupancy limit; [5] the most CTAs one SM ran.  Allocates a small
  * scratch, uses the current device and the legacy default stream, and
  * synchronises.  Errors: INVALID_ARG, CUDA. */
 int qwb_probe_fp32_rate(int32_t kind, int32_t ctas_per_sm, int32_t iters, double* out_h);

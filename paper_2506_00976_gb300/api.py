@@ -398,12 +398,14 @@ PROBE_KINDS = ("fma.rn.f32", "sub.rm.f32", "min.f32 (2 inputs)", "min.f32 (3 inp
 
 def probe_fp32_rate(kind, ctas_per_sm=8, iters=2048):
     """Measured FP32 instruction rate of the current device (qwb_probe_fp32_rate):
-    results per clock per SM, results per second, the SM clock (MHz) and the SM count."""
-    out = np.zeros(5)
+    results per cycle per SM, results per second, the cycle counter's rate (MHz),
+    the SM count and the CTA placement."""
+    out = np.zeros(6)
     check(_lib.load().qwb_probe_fp32_rate(int(kind), int(ctas_per_sm), int(iters),
                                           out.ctypes.data_as(_lib.P_double)), "qwb_probe_fp32_rate")
     return {"kind": PROBE_KINDS[kind], "per_clk_per_sm": float(out[0]), "per_s": float(out[1]),
-            "sm_mhz": float(out[2]), "sms": int(out[3]), "ctas_per_sm": int(out[4])}
+            "counter_mhz": float(out[2]), "sms": int(out[3]), "ctas_per_sm": int(out[4]),
+            "most_ctas_on_one_sm": int(out[5])}
 
 
 def kernel_launch_count():

@@ -931,14 +931,18 @@ static int tune_ctransform(qwb_batch* b, cudaStream_t s) {
     if (st) return st;
     const int cand[][3] = {{4, 4, 0}, {8, 8, 0}, {16, 8, 0}, {16, 16, 0}, {8, 16, 0},
                            {8, 8, 1}, {16, 8, 1}, {16, 16, 1},
-                           {8, 8, 2}, {16, 8, 2}, {8, 16, 2}, {16, 16, 2}};
+                           {8, 8, 2}, {16, 8, 2}, {8, 16, 2}, {16, 16, 2},
+                           {8, 8, 3}, {8, 8, 4}, {8, 16, 4}, {8, 16, 5}, {16, 8, 5}, {16, 16, 5},
+                           {8, 16, 6}};
+    static const char* const kPackName[] = {"", "_packed", "_linepairs", "_linepairs_3cta_fly",
+                                            "_linepairs_3cta", "_linepairs_2cta", "_linepairs_2cta_fly"};
     const int sm = b->ctx->sm_count > 0 ? b->ctx->sm_count : 148;
     std::ostringstream rep;
     double best = 1e30;
     bool first = true;
     rep << "{";
     for (auto& c : cand) {
-        if (b->N_gcd % c[0] || b->N_gcd % c[1] || (c[2] && b->f64)) continue;
+        if (b->N_gcd % c[0] || b->N_gcd % c[1] || (c[2] && b->f64) || (c[2] >= 3 && b->has_3d)) continue;
         CtConfig cfg = b->ct_cfg_b;
         cfg.R = c[0]; cfg.TC = c[1]; cfg.packed = c[2];
         double ms;
@@ -946,7 +950,7 @@ static int tune_ctransform(qwb_batch* b, cudaStream_t s) {
             return launch_ct_batched(b, 0, cfg, sm, s);
         }, &ms);
         if (st) return st;
-        rep << (first ? "" : ", ") << "\"R" << c[0] << "xT" << c[1] << (c[2] == 1 ? "_packed" : c[2] == 2 ? "_linepairs" : "") << "\": " << ms;
+        rep << (first ? "" : ", ") << "\"R" << c[0] << "xT" << c[1] << kPackName[c[2]] << "\": " << ms;
         first = false;
         if (ms < best) { best = ms; e->R = c[0]; e->TC = c[1]; e->packed = c[2]; }
     }
@@ -1969,8 +1973,8 @@ int qwb_ctransform(qwb_ctx* ctx, int32_t N, double p, const double* h_d, double*
 int qwb_ctransform_shape(qwb_ctx* ctx, int32_t N, int32_t d, double p, const double* h_d,
                          double* out_d, int32_t R, int32_t TC, int32_t packing, int32_t in_rows,
                          qwb_prec prec, void* stream) {
-    if (R < 1 || TC < 1 || N < 1 || N % R || N % TC || packing < 0 || packing > 2 || in_rows < 0)
-        return fail(QWB_ERR_INVALID_ARG, "qwb_ctransform_shape: R and TC must divide N; packing in 0..2");
+    if (R < 1 || TC < 1 || N < 1 || N % R || N % TC || packing < 0 || packing > 6 || in_rows < 0)
+        return fail(QWB_ERR_INVALID_ARG, "qwb_ctransform_shape: R and TC must divide N; packing in 0..6");
     if (packing && prec == QWB_PREC_F64)
         return fail(QWB_ERR_INVALID_ARG, "qwb_ctransform_shape: packing needs MIXED precision");
     CtConfig c;

@@ -90,6 +90,15 @@ __device__ __forceinline__ void atomic_min_fp(double* addr, double v) {
                   static_cast<unsigned long long>(__double_as_longlong(v)));
 }
 
+// 3-input minimum: one instruction for two candidates in FP32 (PTX min with
+// three operands, sm_100 and later); FP64 uses two two-input minima.
+__device__ __forceinline__ float min3(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ double min3(double a, double b, double c) { return fmin(a, fmin(b, c)); }
+
 // Ground cost rho(x,y)^p of an integer offset (dr, dc) >= 0, bracketed:
 // lo <= true value <= hi.  p = 1 and p = 2 use correctly rounded operations;
 // other p use the FP64 pow (error at most 2 ulp) widened by 2^-49 relative.

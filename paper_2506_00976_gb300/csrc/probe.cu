@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstdint>
 #include <vector>
 
@@ -134,7 +135,13 @@ probe_kernel(int iters, float seed, float* __restrict__ sink, long long* __restr
         else acc += x[k] + y[k] + z[k];
     }
     if (acc == 1234.5f) sink[blockIdx.x * blockDim.x + threadIdx.x] = acc;   // keeps the chains live
-    if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+    if (threadIdx.x == 0) {
+        unsigned smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        cycles[3 * blockIdx.x] = t0;
+        cycles[3 * blockIdx.x + 1] = t1;
+        cycles[3 * blockIdx.x + 2] = (long long)smid;
+    }
 }
 
 template <int KIND>
@@ -193,7 +200,7 @@ extern "C" int qwb_probe_fp32_rate(int32_t kind, int32_t ctas_per_sm, int32_t it
     long long* cycles = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     int st = QWB_OK;
-    std::vector<long long> cyc(grid);
+    std::vector<long long> cyc(3 * (size_t)grid);
     float ms = 0.0f;
     auto cleanup = [&]() {
         if (sink) cudaFree(sink);
@@ -207,7 +214,7 @@ extern "C" int qwb_probe_fp32_rate(int32_t kind, int32_t ctas_per_sm, int32_t it
         if (e_ != cudaSuccess) { cleanup(); return cuda_fail(e_, #call); } \
     } while (0)
     PROBE_TRY(cudaMalloc(&sink, sizeof(float) * (size_t)grid * PROBE_THREADS));
-    PROBE_TRY(cudaMalloc(&cycles, sizeof(long long) * (size_t)grid));
+    PROBE_TRY(cudaMalloc(&cycles, sizeof(long long) * 3 * (size_t)grid));
     PROBE_TRY(cudaEventCreate(&e0));
     PROBE_TRY(cudaEventCreate(&e1));
     cudaStream_t s = 0;
@@ -218,18 +225,32 @@ extern "C" int qwb_probe_fp32_rate(int32_t kind, int32_t ctas_per_sm, int32_t it
     PROBE_TRY(cudaEventRecord(e1, s));
     PROBE_TRY(cudaEventSynchronize(e1));
     PROBE_TRY(cudaEventElapsedTime(&ms, e0, e1));
-    PROBE_TRY(cudaMemcpy(cyc.data(), cycles, sizeof(long long) * (size_t)grid, cudaMemcpyDeviceToHost));
+    PROBE_TRY(cudaMemcpy(cyc.data(), cycles, sizeof(long long) * 3 * (size_t)grid, cudaMemcpyDeviceToHost));
 #undef PROBE_TRY
     cleanup();
-    double mean_cyc = 0.0;
-    for (long long c : cyc) mean_cyc += (double)c;
-    mean_cyc /= (double)grid;
+    // per SM: the span of its cycle counter from the first CTA's start to the
+    // last CTA's end, and the CTAs it ran (CTAs need not all be co-resident)
+    int max_sm = 0;
+    for (int i = 0; i < grid; ++i) max_sm = std::max(max_sm, (int)cyc[3 * (size_t)i + 2]);
+    std::vector<long long> lo(max_sm + 1, LLONG_MAX), hi(max_sm + 1, LLONG_MIN);
+    std::vector<int> cnt(max_sm + 1, 0);
+    for (int i = 0; i < grid; ++i) {
+        const int sm = (int)cyc[3 * (size_t)i + 2];
+        lo[sm] = std::min(lo[sm], cyc[3 * (size_t)i]);
+        hi[sm] = std::max(hi[sm], cyc[3 * (size_t)i + 1]);
+        cnt[sm]++;
+    }
+    double span_sum = 0.0;
+    int used = 0, most = 0;
+    for (int sm = 0; sm <= max_sm; ++sm)
+        if (cnt[sm]) { span_sum += (double)(hi[sm] - lo[sm]); ++used; most = std::max(most, cnt[sm]); }
     const double per_cta = (double)PROBE_THREADS * iters * PROBE_UNROLL * PROBE_CHAINS *
                            probe_results_per_step(kind);
-    out_h[0] = per_cta * ctas_per_sm / mean_cyc;                 // results per clock per SM
+    out_h[0] = per_cta * grid / span_sum;                        // results per cycle per SM
     out_h[1] = per_cta * grid / (ms * 1e-3);                     // results per second, whole device
-    out_h[2] = mean_cyc / (ms * 1e-3) / 1e6;                     // SM clock (MHz) over the run
+    out_h[2] = span_sum / used / (ms * 1e-3) / 1e6;              // cycle-counter MHz over the run
     out_h[3] = (double)sms;
     out_h[4] = (double)ctas_per_sm;
+    out_h[5] = (double)most;                                     // most CTAs one SM ran
     return QWB_OK;
 }

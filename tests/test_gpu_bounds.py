@@ -11,6 +11,8 @@ from oracle import qwb_oracle as O
 from paper_2506_00976_gb300 import api, synth
 
 pytestmark = pytest.mark.gpu
+
+TOL = {"mixed": 1e-4, "f64": 1e-6}   # relative, on the bounds
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 

@@ -172,7 +172,8 @@ def test_invalid_inputs():
 
 SHAPES = [(R, TC, 0) for R, TC in [(1, 1), (2, 2), (4, 4), (8, 8), (16, 8), (16, 16), (8, 16)]] + \
          [(8, 8, 1), (16, 8, 1), (16, 16, 1)] + \
-         [(8, 8, 2), (16, 8, 2), (8, 16, 2), (16, 16, 2)]
+         [(8, 8, 2), (16, 8, 2), (8, 16, 2), (16, 16, 2)] + \
+         [(8, 8, 3), (8, 8, 4), (8, 16, 4), (8, 16, 5), (16, 8, 5), (16, 16, 5), (8, 16, 6)]
 
 
 @pytest.mark.parametrize("R,TC,packing", SHAPES)
@@ -186,7 +187,8 @@ def test_ctransform_every_shape_p2(R, TC, packing, N, in_rows):
     np.testing.assert_array_equal(g, rd32(O.c_transform(h, N, 2.0)))
 
 
-@pytest.mark.parametrize("R,TC,packing", [(8, 8, 0), (16, 8, 1), (16, 8, 2), (8, 16, 2), (16, 16, 2)])
+@pytest.mark.parametrize("R,TC,packing", [(8, 8, 0), (16, 8, 1), (16, 8, 2), (8, 16, 2), (16, 16, 2),
+                                           (8, 8, 3), (8, 16, 4), (16, 16, 5), (8, 16, 6)])
 @pytest.mark.parametrize("p", [1.0, 1.5])
 def test_ctransform_every_shape_general_p(R, TC, packing, p):
     N = 32
@@ -226,6 +228,8 @@ def test_ctransform_shape_rejects():
         api.ctransform_shape(h, 8, 2.0, 8, 8, 2, prec="f64")  # packing is FP32 only
     with pytest.raises(QwbError, match="UNSUPPORTED"):
         api.ctransform_shape(h, 8, 2.0, 2, 8, 0)             # not compiled
+    with pytest.raises(QwbError, match="UNSUPPORTED"):
+        api.ctransform_shape(T(np.zeros(512)), 8, 2.0, 8, 8, 4, d=3)   # register-cut shapes are 2-D only
 
 
 @pytest.mark.parametrize("prec", ["mixed", "f64"])
