@@ -131,8 +131,10 @@ def _ct_traffic(digest):
 
 
 def _kernel_digest():
+    """SHA-256 of the c-transform's source (csrc/ctransform.cu), which the
+    traffic record names so that a changed kernel invalidates it."""
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_2506_00976_gb300", "csrc", "kernels.cu"), "rb") as fh:
+    with open(os.path.join(ROOT, "paper_2506_00976_gb300", "csrc", "ctransform.cu"), "rb") as fh:
         h.update(fh.read())
     return h.hexdigest()
 
@@ -229,16 +231,26 @@ def run_gpu(args):
     res_h = results
     torch.cuda.synchronize()
     barrier()
+    parts = {"h2d_and_coarse_enqueue": [], "solve_call": [], "host_exact_solves": [], "fine_and_results": []}
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
+        ta = time.perf_counter()
         dev_buf.copy_(host, non_blocking=True)
         batch.coarse(mus, nus, batched=True)
+        tb = time.perf_counter()
         batch.solve(threads=args.threads)
+        tc = time.perf_counter()
         batch.fine(mus, nus, batched=True)
         res_h = batch.results()
+        td = time.perf_counter()
+        parts["h2d_and_coarse_enqueue"].append(tb - ta)
+        parts["solve_call"].append(tc - tb)
+        parts["host_exact_solves"].append(res_h[0]["t_solve_ms"] * 1e-3)
+        parts["fine_and_results"].append(td - tc)
     torch.cuda.synchronize()
     barrier()
     e2e_s = (time.perf_counter() - t0) / max(1, e2e_steps) if e2e_steps else float("nan")
+    e2e_parts = {k: round(1e3 * statistics.mean(v), 3) for k, v in parts.items() if v}
     e2e_s = shard.max_over_ranks(e2e_s, dev)
     assert all(r["status"] == 0 for r in res_h)
     # the same batch with the separable p = 2 c-transform (an exact O(N^3)
@@ -256,6 +268,7 @@ def run_gpu(args):
     ms_sep_max = shard.max_over_ranks(statistics.mean(sep_times), dev) if sep_times else None
 
     h2d = int(host.numel() * host.element_size())
+    M_C = (N // KAPPA) ** 2          # coarse cells: C-bar (M^2) and mu~, nu~ (M each) come back per pair
     d2h = n * 8 * 14   # the result records read back per step
 
     out = None
@@ -327,7 +340,13 @@ def run_gpu(args):
                            "what": "network simplex on C~ and C-bar (M = 1024) per pair"},
             "e2e": {"value": round(n * world / e2e_s, 3), "unit": "pairs/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "steps": e2e_steps},
+                    "steps": e2e_steps, "ms_per_step": round(1e3 * e2e_s, 3),
+                    "internal_d2h_bytes_per_step": n * (M_C * M_C + 2 * M_C) * 8,
+                    "parts_ms": e2e_parts,
+                    "parts_note": "host wall time of each API call per step: the copy of the measures and "
+                                  "the asynchronous coarse pass; qwb_batch_solve (waits for the coarse "
+                                  "pass, reads C-bar back, runs the host exact solves, uploads the plans); "
+                                  "of which the exact solves alone; the fine passes and the results read"},
             "gpu_launches": int(launches),
             "autotune": batch.tuning(),
             "clocks": clocks,

@@ -236,8 +236,15 @@ struct qwb_batch {
     // host copies for the exact solves
     double* cbar_h = nullptr;   // pinned, sum of M^2
     std::vector<size_t> cbar_h_off;
-    std::vector<double> mu_c_h, nu_c_h;
+    double* mu_c_h = nullptr;   // pinned: coarse masses of every pair (nu_c_h follows mu_c_h)
+    double* nu_c_h = nullptr;
     std::vector<size_t> mc_off;
+    // overlap of the exact solves with the C-bar pass: the SumPool results are
+    // read on `aux` once the SumPool kernel of a batched coarse pass is done,
+    // C-bar comes back in groups of kCbarGroup pairs, each marked by an event
+    bool coarse_batched = false;
+    cudaStream_t aux = nullptr;
+    std::vector<cudaEvent_t> cb_ev;
     std::vector<double> ubw, ubw_p, lbmin;
     std::vector<int> status;
     bool solved = false;
@@ -260,6 +267,9 @@ static void batch_free(qwb_batch* b) {
     if (b->plan_d) cudaFree(b->plan_d);
     if (b->plan_h) cudaFreeHost(b->plan_h);
     if (b->cbar_h) cudaFreeHost(b->cbar_h);
+    if (b->mu_c_h) cudaFreeHost(b->mu_c_h);
+    for (auto& e : b->cb_ev) cudaEventDestroy(e);
+    if (b->aux) cudaStreamDestroy(b->aux);
     if (b->upk_mem) cudaFree(b->upk_mem);
     if (b->ev_ok) {
         for (auto& e : b->ev) cudaEventDestroy(e);
@@ -590,7 +600,10 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
     }
     size_t moff = 0;
     for (int t = 0; t < n; ++t) { b->mc_off.push_back(moff); moff += b->Ms[t]; }
-    b->mu_c_h.resize(moff); b->nu_c_h.resize(moff);
+    if (cudaMallocHost(&b->mu_c_h, sizeof(double) * 2 * std::max<size_t>(moff, 1)) != cudaSuccess) {
+        b->mu_c_h = nullptr; batch_free(b); return fail(QWB_ERR_OOM, "host coarse-mass buffer");
+    }
+    b->nu_c_h = b->mu_c_h + moff;
     b->ubw.assign(n, 0.0); b->ubw_p.assign(n, 0.0); b->lbmin.assign(n, 0.0); b->status.assign(n, QWB_OK);
     // per-pair descriptors
     cudaStream_t s0 = 0;
@@ -1114,11 +1127,12 @@ static int solve_table(const qwb_problem& pr, const std::vector<double>& tab, co
     return network_simplex(M, M, C.data(), a, b, out, -1, warm, basis_out);
 }
 
-static int solve_pair(qwb_batch* b, int t) {
+// wait_cbar (may be empty): blocks until pair t's C-bar is on the host
+static int solve_pair(qwb_batch* b, int t, const std::function<int(int)>& wait_cbar) {
     const qwb_problem& pr = b->probs[t];
     const int M = b->Ms[t];
-    const double* mc = b->mu_c_h.data() + b->mc_off[t];
-    const double* nc = b->nu_c_h.data() + b->mc_off[t];
+    const double* mc = b->mu_c_h + b->mc_off[t];
+    const double* nc = b->nu_c_h + b->mc_off[t];
     // (1) C~ problem: plan and potential for the primal and dual passes
     std::vector<double> Ct;
     centre_cost_table(pr, Ct);
@@ -1186,6 +1200,10 @@ static int solve_pair(qwb_batch* b, int t) {
     // same supplies: the C~ optimum is a feasible starting basis, and the
     // arcs from each source to the 3 x 3 (3 x 3 x 3) neighbourhoods of its C~
     // plan targets are priced first (the solve still ends optimal over all arcs)
+    if (wait_cbar) {
+        const int stw = wait_cbar(t);
+        if (stw) return stw;
+    }
     NSSolution sb;
     const double* Cb = b->cbar_h + b->cbar_h_off[t];
     std::vector<int64_t> cand;
@@ -1241,20 +1259,55 @@ static int solve_pair(qwb_batch* b, int t) {
     return QWB_OK;
 }
 
+constexpr int kCbarGroup = 8;   // pairs per C-bar copy group (one event each)
+
 static int batch_solve(qwb_batch* b, int n_threads, cudaStream_t s) {
-    QWB_CUDA(cudaStreamSynchronize(s));
-    // read the coarse pass results
+    // After a batched coarse pass the SumPool kernel's end is marked by an
+    // event inside the captured graph: the coarse masses (all the C~ solves
+    // need) are read as soon as it has passed, on a second stream, while the
+    // C-bar kernels still run; C-bar comes back on the caller's stream in
+    // groups, and a worker waits for its pair's group only before the C-bar
+    // solve.  Otherwise everything is read after the whole coarse pass.
+    const bool overlap = b->coarse_batched && b->ev_ok && !(b->flags & QWB_FLAG_NO_WEIGHTED);
+    const int n_groups = (b->n + kCbarGroup - 1) / kCbarGroup;
     std::vector<PairOut> outs(b->n);
-    QWB_CUDA(cudaMemcpy(outs.data(), b->outs_d, sizeof(PairOut) * b->n, cudaMemcpyDeviceToHost));
-    for (int t = 0; t < b->n; ++t) {
-        const int M = b->Ms[t];
-        const PairDev& P = b->pairs_h[t];
-        QWB_CUDA(cudaMemcpyAsync(b->mu_c_h.data() + b->mc_off[t], P.mu_c, sizeof(double) * M, cudaMemcpyDeviceToHost, s));
-        QWB_CUDA(cudaMemcpyAsync(b->nu_c_h.data() + b->mc_off[t], P.nu_c, sizeof(double) * M, cudaMemcpyDeviceToHost, s));
-        if (!(b->flags & QWB_FLAG_NO_WEIGHTED))
-            QWB_CUDA(cudaMemcpyAsync(b->cbar_h + b->cbar_h_off[t], P.cbar, sizeof(double) * (size_t)M * M, cudaMemcpyDeviceToHost, s));
+    if (overlap) {
+        if (!b->aux) QWB_CUDA(cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking));
+        while ((int)b->cb_ev.size() < n_groups) {
+            cudaEvent_t e;
+            QWB_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            b->cb_ev.push_back(e);
+        }
+        QWB_CUDA(cudaStreamWaitEvent(b->aux, b->kev[1], 0));
+        QWB_CUDA(cudaMemcpyAsync(outs.data(), b->outs_d, sizeof(PairOut) * b->n, cudaMemcpyDeviceToHost, b->aux));
+        for (int t = 0; t < b->n; ++t) {
+            const int M = b->Ms[t];
+            const PairDev& P = b->pairs_h[t];
+            QWB_CUDA(cudaMemcpyAsync(b->mu_c_h + b->mc_off[t], P.mu_c, sizeof(double) * M, cudaMemcpyDeviceToHost, b->aux));
+            QWB_CUDA(cudaMemcpyAsync(b->nu_c_h + b->mc_off[t], P.nu_c, sizeof(double) * M, cudaMemcpyDeviceToHost, b->aux));
+        }
+        for (int g = 0; g < n_groups; ++g) {
+            for (int t = g * kCbarGroup; t < std::min(b->n, (g + 1) * kCbarGroup); ++t) {
+                const int M = b->Ms[t];
+                QWB_CUDA(cudaMemcpyAsync(b->cbar_h + b->cbar_h_off[t], b->pairs_h[t].cbar,
+                                         sizeof(double) * (size_t)M * M, cudaMemcpyDeviceToHost, s));
+            }
+            QWB_CUDA(cudaEventRecord(b->cb_ev[g], s));
+        }
+        QWB_CUDA(cudaStreamSynchronize(b->aux));
+    } else {
+        QWB_CUDA(cudaStreamSynchronize(s));
+        QWB_CUDA(cudaMemcpy(outs.data(), b->outs_d, sizeof(PairOut) * b->n, cudaMemcpyDeviceToHost));
+        for (int t = 0; t < b->n; ++t) {
+            const int M = b->Ms[t];
+            const PairDev& P = b->pairs_h[t];
+            QWB_CUDA(cudaMemcpyAsync(b->mu_c_h + b->mc_off[t], P.mu_c, sizeof(double) * M, cudaMemcpyDeviceToHost, s));
+            QWB_CUDA(cudaMemcpyAsync(b->nu_c_h + b->mc_off[t], P.nu_c, sizeof(double) * M, cudaMemcpyDeviceToHost, s));
+            if (!(b->flags & QWB_FLAG_NO_WEIGHTED))
+                QWB_CUDA(cudaMemcpyAsync(b->cbar_h + b->cbar_h_off[t], P.cbar, sizeof(double) * (size_t)M * M, cudaMemcpyDeviceToHost, s));
+        }
+        QWB_CUDA(cudaStreamSynchronize(s));
     }
-    QWB_CUDA(cudaStreamSynchronize(s));
     int first_bad = QWB_OK;
     for (int t = 0; t < b->n; ++t) {
         const PairOut& O = outs[t];
@@ -1264,7 +1317,17 @@ static int batch_solve(qwb_batch* b, int n_threads, cudaStream_t s) {
             if (!first_bad) first_bad = QWB_ERR_MASS;
         }
     }
-    if (first_bad) { b->solved = false; return fail(first_bad, "measures must be finite, non-negative and of mass 1 (1e-12)"); }
+    if (first_bad) {
+        b->solved = false;
+        if (overlap) QWB_CUDA(cudaStreamSynchronize(s));      // no copy left in flight
+        return fail(first_bad, "measures must be finite, non-negative and of mass 1 (1e-12)");
+    }
+    std::function<int(int)> wait_cbar;
+    if (overlap)
+        wait_cbar = [b](int t) -> int {
+            const cudaError_t e = cudaEventSynchronize(b->cb_ev[t / kCbarGroup]);
+            return e == cudaSuccess ? QWB_OK : QWB_ERR_CUDA;
+        };
     const auto t0 = std::chrono::steady_clock::now();
     int nt = n_threads > 0 ? n_threads : (int)std::max(1u, std::thread::hardware_concurrency());
     nt = std::min(nt, b->n);
@@ -1274,7 +1337,7 @@ static int batch_solve(qwb_batch* b, int n_threads, cudaStream_t s) {
             const int t = next.fetch_add(1);
             if (t >= b->n) break;
             int st;
-            try { st = solve_pair(b, t); } catch (...) { st = QWB_ERR_OOM; }
+            try { st = solve_pair(b, t, wait_cbar); } catch (...) { st = QWB_ERR_OOM; }
             b->status[t] = st;
         }
     };
@@ -1283,6 +1346,7 @@ static int batch_solve(qwb_batch* b, int n_threads, cudaStream_t s) {
     worker();
     for (auto& th : pool) th.join();
     b->t_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (overlap) QWB_CUDA(cudaStreamSynchronize(s));          // every C-bar copy has landed
     for (int t = 0; t < b->n; ++t)
         if (b->status[t]) { b->solved = false; return fail(b->status[t], "exact coarse solve failed"); }
     // upload the plans (and nnz in the descriptors)
@@ -1388,6 +1452,7 @@ int qwb_batch_coarse(qwb_batch* b, const double* const* mu_d, const double* cons
     if (b->ev_ok) QWB_CUDA(cudaEventRecord(b->ev[0], s));
     st = run_pass(b, 0, batched != 0, s);
     if (st) return st;
+    b->coarse_batched = batched != 0;
     if (b->ev_ok) QWB_CUDA(cudaEventRecord(b->ev[1], s));
     return QWB_OK;
 }
