@@ -252,14 +252,16 @@ int qwb_ctransform(qwb_ctx* ctx, int32_t N, double p, const double* h_d, double*
  *            subtraction; 3-6 (MIXED, d = 2 only) packing 2 with the
  *            register budget cut for 3 (packings 3, 4) or 2 (5, 6) resident
  *            CTAs per SM, the p = 2 window costs formed on the fly (3, 6) or
- *            kept in registers (4, 5).
+ *            kept in registers (4, 5); 7, 8 (MIXED, d = 2 only) packings 5
+ *            and 2 with each candidate pair's subtraction and min fused in
+ *            one assembly block.
  *   in_rows  input lines per work item (0 = the default split); work items
  *            that see part of the input lines combine by atomic min.
  * Compiled shapes: packing 0: (R, TC) in {1,2,4,8,16} x {same} and (16,8),
  * (8,16); packing 1: (8,8), (16,8), (16,16); packing 2: (8,8), (16,8), (8,16),
  * (16,16); packing 3: (8,8); packing 4: (8,8), (8,16); packing 5: (8,16),
- * (16,8), (16,16); packing 6: (8,16).  Other shapes return
- * QWB_ERR_UNSUPPORTED.
+ * (16,8), (16,16); packing 6: (8,16); packing 7: (16,16), (16,8), (8,16);
+ * packing 8: (16,16).  Other shapes return QWB_ERR_UNSUPPORTED.
  * h_d, out_d: N^d FP64 device.  Synchronises `stream` before returning.
  * Errors: INVALID_ARG, UNSUPPORTED, CUDA, OOM. */
 int qwb_ctransform_shape(qwb_ctx* ctx, int32_t N, int32_t d, double p, const double* h_d,
@@ -377,10 +379,21 @@ int qwb_batch_coarse_potentials(qwb_batch* batch, int32_t pair, double* f_h, dou
  * sides.  C | QWB_IPF_BULK (C = 2..16) selects the form that stages the
  * source values by bulk copies (cp.async.bulk into a ring of shared-memory
  * stages, completion on mbarriers, every wait bounded) for groups whose pairs
- * share N; a timed-out wait makes qwb_batch_results return TIMEOUT.  Overrides
- * the autotuner's choice, which times both forms; synchronises the device
- * and drops the batch's captured fine-pass graphs.  Errors: INVALID_ARG, CUDA. */
+ * share N; a timed-out wait makes qwb_batch_results return TIMEOUT.
+ * C | QWB_IPF_ASYNC selects the form in which every thread brings its own
+ * blocks' source values in by 16-byte asynchronous copies (cp.async) into a
+ * private shared-memory slot, re-filled with the next chunk before the
+ * current one is stored (256 threads per CTA, one slot per thread);
+ * C | QWB_IPF_ASYNC2 the same with 128 threads per CTA and two slots per
+ * thread; C | QWB_IPF_ASYNC3 with 128 threads, three slots and the plan
+ * read from global memory.  Overrides the autotuner's choice, which times
+ * every form;
+ * synchronises the device and drops the batch's captured fine-pass graphs.
+ * Errors: INVALID_ARG, CUDA. */
 #define QWB_IPF_BULK 32
+#define QWB_IPF_ASYNC 64
+#define QWB_IPF_ASYNC2 128
+#define QWB_IPF_ASYNC3 256
 int qwb_batch_set_ipf_cluster(qwb_batch* batch, int32_t C);
 /* Upscale the coarse plans of the batch's 2-D pairs with block side kappa by
  * the general kernel K_d (Sec. 3.4, eq. coupling tensor upscale; layout,

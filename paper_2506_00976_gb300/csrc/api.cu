@@ -207,11 +207,11 @@ struct qwb_batch {
     // largest power of two <= ipf_C that divides all its coarse sides
     // (stream: the bulk-copy variant ipf_stream_kernel, for groups whose pairs
     // share N; n_same, N_same: that common coarse and fine side, else 0)
-    struct IpfGroup { int kappa, off, cnt, M_max, gcd_n, C, n_same, N_same; bool stream; };
+    struct IpfGroup { int kappa, off, cnt, M_max, gcd_n, C, n_same, N_same; bool stream; int async_v; };
     std::vector<IpfGroup> ipf_groups;
     std::vector<int> ipf_group_of;      // per pair: its group or -1
     int* ipf_ids_d = nullptr;
-    int ipf_C = 0;                      // + QWB_IPF_BULK: the bulk-copy variant
+    int ipf_C = 0;                      // | QWB_IPF_BULK / _ASYNC / _ASYNC2: the staged forms
     int* dev_err = nullptr;             // device error word of bounded waits (0 = none)
     unsigned long long wait_ns = 0;     // limit of every bounded device wait (QWB_WAIT_TIMEOUT_MS)
     int fault_skip_chunk = -1;          // QWB_FAULT ipf_bulk_skip_chunk (tests), else -1
@@ -350,17 +350,19 @@ static int launch_ipf_group(qwb_batch* b, const qwb_batch::IpfGroup& G, const in
     if (G.stream)
         return launch_ipf_stream(b->pairs_d, ids, cnt, G.kappa, G.C, G.n_same, G.N_same, b->dev_err, b->wait_ns,
                                  b->fault_skip_chunk, s);
+    if (G.async_v >= 0) return launch_ipf_async(b->pairs_d, ids, cnt, G.kappa, G.C, G.async_v, M, 0, s);
     return launch_ipf_fine(b->pairs_d, ids, cnt, G.kappa, G.C, M, 0, s);
 }
 
 static int apply_ipf_choice(qwb_batch* b, int C) {
     b->ipf_C = C;
-    const int Cs = C & ~QWB_IPF_BULK;
+    const int Cs = C & 31;
     for (auto& G : b->ipf_groups) {
         int c = 1;
         while (c * 2 <= Cs && c * 2 <= 16 && G.gcd_n % (c * 2) == 0) c *= 2;
         G.C = c >= 2 ? c : 0;
         G.stream = (C & QWB_IPF_BULK) && G.C > 0 && G.n_same > 0 && G.N_same > 0;
+        G.async_v = G.C > 0 ? ((C & QWB_IPF_ASYNC) ? 0 : (C & QWB_IPF_ASYNC2) ? 1 : (C & QWB_IPF_ASYNC3) ? 2 : -1) : -1;
     }
     for (int t = 0; t < b->n; ++t) {
         const int g = b->ipf_group_of[t];
@@ -946,9 +948,10 @@ static int tune_ctransform(qwb_batch* b, cudaStream_t s) {
                            {8, 8, 1}, {16, 8, 1}, {16, 16, 1},
                            {8, 8, 2}, {16, 8, 2}, {8, 16, 2}, {16, 16, 2},
                            {8, 8, 3}, {8, 8, 4}, {8, 16, 4}, {8, 16, 5}, {16, 8, 5}, {16, 16, 5},
-                           {8, 16, 6}};
+                           {8, 16, 6}, {16, 16, 7}, {16, 8, 7}, {8, 16, 7}, {16, 16, 8}};
     static const char* const kPackName[] = {"", "_packed", "_linepairs", "_linepairs_3cta_fly",
-                                            "_linepairs_3cta", "_linepairs_2cta", "_linepairs_2cta_fly"};
+                                            "_linepairs_3cta", "_linepairs_2cta", "_linepairs_2cta_fly",
+                                            "_linepairs_2cta_fused", "_linepairs_fused"};
     const int sm = b->ctx->sm_count > 0 ? b->ctx->sm_count : 148;
     std::ostringstream rep;
     double best = 1e30;
@@ -990,13 +993,16 @@ static int tune_ipf(qwb_batch* b, cudaStream_t s) {
     rep << "{";
     double best = 1e30;
     int bestC = 0;
-    for (int C : {0, 2, 4, 8, 16, QWB_IPF_BULK | 2, QWB_IPF_BULK | 4, QWB_IPF_BULK | 8, QWB_IPF_BULK | 16}) {
+    for (int C : {0, 2, 4, 8, 16, QWB_IPF_BULK | 2, QWB_IPF_BULK | 4, QWB_IPF_BULK | 8, QWB_IPF_BULK | 16,
+                  QWB_IPF_ASYNC | 2, QWB_IPF_ASYNC | 4, QWB_IPF_ASYNC | 8, QWB_IPF_ASYNC2 | 4,
+                  QWB_IPF_ASYNC2 | 8, QWB_IPF_ASYNC3 | 4, QWB_IPF_ASYNC3 | 8}) {
         int st = apply_ipf_choice(b, C);
         if (st) return st;
         if (C > 0) {
+            const int av = (C & QWB_IPF_ASYNC) ? 0 : (C & QWB_IPF_ASYNC2) ? 1 : (C & QWB_IPF_ASYNC3) ? 2 : -1;
             bool any = false;
             for (const auto& G : b->ipf_groups)
-                any |= G.C == (C & ~QWB_IPF_BULK) && G.stream == ((C & QWB_IPF_BULK) != 0);
+                any |= G.C == (C & 31) && G.stream == ((C & QWB_IPF_BULK) != 0) && G.async_v == av;
             if (!any) continue;                  // no group takes this size / form
         }
         double ms;
@@ -1008,8 +1014,10 @@ static int tune_ipf(qwb_batch* b, cudaStream_t s) {
             return launch_primal(b->pairs_d, b->outs_d, b->pair_ids_d, b->n, b->M_max, 0, b->f64, s);
         }, &ms);
         if (st) return st;
-        rep << (C ? ", " : "") << "\"" << ((C & QWB_IPF_BULK) ? "bulk" : "cluster") << (C & ~QWB_IPF_BULK)
-            << "\": " << ms;
+        rep << (C ? ", " : "") << "\""
+            << ((C & QWB_IPF_BULK) ? "bulk" : (C & QWB_IPF_ASYNC) ? "async" : (C & QWB_IPF_ASYNC2) ? "async2slot"
+                : (C & QWB_IPF_ASYNC3) ? "async3slot" : "cluster")
+            << (C & 31) << "\": " << ms;
         if (ms < best) { best = ms; bestC = C; }
     }
     rep << "}";
@@ -1570,10 +1578,14 @@ int qwb_batch_coarse_potentials(qwb_batch* b, int32_t pair, double* f_h, double*
 }
 
 int qwb_batch_set_ipf_cluster(qwb_batch* b, int32_t C) {
-    const int Cs = C & ~QWB_IPF_BULK;
-    if (!b || (Cs != 0 && Cs != 2 && Cs != 4 && Cs != 8 && Cs != 16) || C == QWB_IPF_BULK)
+    const int Cs = C & 31, form = C & ~31;
+    if (!b || (Cs != 0 && Cs != 2 && Cs != 4 && Cs != 8 && Cs != 16) ||
+        (form != 0 && form != QWB_IPF_BULK && form != QWB_IPF_ASYNC && form != QWB_IPF_ASYNC2 &&
+         form != QWB_IPF_ASYNC3) ||
+        (form != 0 && Cs == 0))
         return fail(QWB_ERR_INVALID_ARG,
-                    "qwb_batch_set_ipf_cluster: C must be 0, 2, 4, 8 or 16, the last four optionally | QWB_IPF_BULK");
+                    "qwb_batch_set_ipf_cluster: C must be 0, 2, 4, 8 or 16, the last four optionally with one of "
+                    "QWB_IPF_BULK, QWB_IPF_ASYNC, QWB_IPF_ASYNC2, QWB_IPF_ASYNC3");
     QWB_CUDA(cudaSetDevice(b->ctx->device));
     QWB_CUDA(cudaDeviceSynchronize());
     // captured fine passes hold the previous launch configuration
@@ -2038,8 +2050,8 @@ int qwb_ctransform(qwb_ctx* ctx, int32_t N, double p, const double* h_d, double*
 int qwb_ctransform_shape(qwb_ctx* ctx, int32_t N, int32_t d, double p, const double* h_d,
                          double* out_d, int32_t R, int32_t TC, int32_t packing, int32_t in_rows,
                          qwb_prec prec, void* stream) {
-    if (R < 1 || TC < 1 || N < 1 || N % R || N % TC || packing < 0 || packing > 6 || in_rows < 0)
-        return fail(QWB_ERR_INVALID_ARG, "qwb_ctransform_shape: R and TC must divide N; packing in 0..6");
+    if (R < 1 || TC < 1 || N < 1 || N % R || N % TC || packing < 0 || packing > 8 || in_rows < 0)
+        return fail(QWB_ERR_INVALID_ARG, "qwb_ctransform_shape: R and TC must divide N; packing in 0..8");
     if (packing && prec == QWB_PREC_F64)
         return fail(QWB_ERR_INVALID_ARG, "qwb_ctransform_shape: packing needs MIXED precision");
     CtConfig c;

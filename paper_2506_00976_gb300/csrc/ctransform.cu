@@ -171,6 +171,14 @@ __device__ __forceinline__ unsigned long long add_rn_x2(unsigned long long a, un
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
+// m' = min(m, fl_down(w.lo - h.lo), fl_down(w.hi - h.hi)) in one assembly block
+__device__ __forceinline__ float sub2_min3(unsigned long long w, unsigned long long h, float m) {
+    float d;
+    asm("{\n .reg .b64 t;\n .reg .f32 lo, hi;\n sub.rm.f32x2 t, %1, %2;\n mov.b64 {lo, hi}, t;\n"
+        " min.f32 %0, %3, lo, hi;\n}"
+        : "=f"(d) : "l"(w), "l"(h), "f"(m));
+    return d;
+}
 __device__ __forceinline__ unsigned long long fma_rn_x2(unsigned long long a, unsigned long long b,
                                                         unsigned long long c) {
     unsigned long long d;
@@ -183,7 +191,11 @@ __device__ __forceinline__ unsigned long long fma_rn_x2(unsigned long long a, un
 // fma(d, d, A), d advancing by one per column, instead of keeping the NQ
 // squared column offsets of a chunk in registers (fewer registers, one more
 // FMA-pipe instruction per new cost).
-template <int R, int TC, bool P2, bool D3, int MINB = 1, bool DDFLY = false>
+// FUSE: the staged h pairs are read as two 64-bit operands per 16-byte load,
+// and each candidate pair's packed subtraction and 3-input min are one inline
+// assembly block, so no value crosses between the packed and the scalar views
+// outside it.
+template <int R, int TC, bool P2, bool D3, int MINB = 1, bool DDFLY = false, bool FUSE = false>
 __global__ void __launch_bounds__(256, MINB)
 ctransform_rp_kernel(const PairDev* __restrict__ pairs, const CtItem* __restrict__ items,
                      int n_items, int phase) {
@@ -292,8 +304,14 @@ ctransform_rp_kernel(const PairDev* __restrict__ pairs, const CtItem* __restrict
                     for (int r = R - 2; r >= 0; --r) win[r] = cost(R - 2 - r);
 #pragma unroll
                     for (int s = 0; s < TC; s += 2) {
-                        const float4 v = hrow[s / 2];
-                        const unsigned long long hp0 = pack2(v.x, v.y), hp1 = pack2(v.z, v.w);
+                        unsigned long long hp0, hp1;
+                        if constexpr (FUSE) {
+                            const ulonglong2 v = reinterpret_cast<const ulonglong2*>(hrow)[s / 2];
+                            hp0 = v.x; hp1 = v.y;
+                        } else {
+                            const float4 v = hrow[s / 2];
+                            hp0 = pack2(v.x, v.y); hp1 = pack2(v.z, v.w);
+                        }
 #pragma unroll
                         for (int ss = 0; ss < 2; ++ss) {
                             const int sc = s + ss;
@@ -304,9 +322,13 @@ ctransform_rp_kernel(const PairDev* __restrict__ pairs, const CtItem* __restrict
                             const unsigned long long hp = ss ? hp1 : hp0;
 #pragma unroll
                             for (int r = 0; r < R; ++r) {
-                                float a, b;
-                                sub_rd_x2(win[r], hp, a, b);
-                                mins[r] = min3(mins[r], a, b);
+                                if constexpr (FUSE) {
+                                    mins[r] = sub2_min3(win[r], hp, mins[r]);
+                                } else {
+                                    float a, b;
+                                    sub_rd_x2(win[r], hp, a, b);
+                                    mins[r] = min3(mins[r], a, b);
+                                }
                             }
                         }
                     }
@@ -369,10 +391,10 @@ static int ct_launch_rp(const PairDev* pairs_d, const CtItem* items, int n_items
     return QWB_OK;
 }
 
-template <int R, int TC, bool P2, int MINB, bool DDFLY>
+template <int R, int TC, bool P2, int MINB, bool DDFLY, bool FUSE = false>
 static int ct_launch_rp2d(const PairDev* pairs_d, const CtItem* items, int n_items, int phase,
                           int threads, int in_rows, int N_max, int grid_cap, cudaStream_t stream) {
-    auto kern = ctransform_rp_kernel<R, TC, P2, false, MINB, DDFLY>;
+    auto kern = ctransform_rp_kernel<R, TC, P2, false, MINB, DDFLY, FUSE>;
     threads = std::min(threads, CT_TILE / R);
     const size_t smem = sizeof(float2) * (size_t)((in_rows + 1) / 2) * N_max;
     if (smem > 227 * 1024) return QWB_ERR_UNSUPPORTED;
@@ -418,6 +440,16 @@ static int ct_launch_t(const PairDev* pairs_d, const CtItem* items, int n_items,
         QWB_CTRPV(5, 2, false, 8, 16) QWB_CTRPV(5, 2, false, 16, 8) QWB_CTRPV(5, 2, false, 16, 16)
         QWB_CTRPV(6, 2, true, 8, 16)
 #undef QWB_CTRPV
+        // packings 7, 8 (2-D only): packings 5 and 2 with the fused
+        // subtraction-and-min blocks
+        if ((c.packed == 7 || c.packed == 8) && c.has_3d) return QWB_ERR_UNSUPPORTED;
+#define QWB_CTRPF(PK, MB, RR, TT)                                                          \
+        if (c.R == RR && c.TC == TT && c.packed == PK)                                     \
+            return ct_launch_rp2d<RR, TT, P2, MB, false, true>(pairs_d, items, n_items, phase, \
+                                                            c.threads, c.in_rows, N_max, grid_cap, stream);
+        QWB_CTRPF(7, 2, 16, 16) QWB_CTRPF(7, 2, 16, 8) QWB_CTRPF(7, 2, 8, 16)
+        QWB_CTRPF(8, 1, 16, 16)
+#undef QWB_CTRPF
     }
     return QWB_ERR_UNSUPPORTED;
 }

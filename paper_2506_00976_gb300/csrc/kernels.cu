@@ -2015,6 +2015,242 @@ int launch_ipf_fine(const PairDev* pairs_d, const int* pair_ids, int n_pairs, in
 }
 
 // --------------------------------------------------------------------------
+// ipf_async: the same fine FP32 IPF sweeps as ipf_fine_kernel (same cluster
+// ownership of the coarse blocks, plan rows / columns staged in shared memory,
+// block sums through distributed shared memory, one cluster barrier per half
+// sweep), with the source values brought in by per-thread asynchronous
+// copies (cp.async, 16 bytes each) into a ring of SLOTS private shared-memory
+// slots per thread.  A thread reads only the slot it filled itself, so a
+// chunk needs no block barrier: the thread waits for its own oldest copy
+// group, reads the chunk into registers, scales it, and re-fills that slot
+// with the chunk SLOTS ahead -- which may belong to the next half sweep, since
+// the sources mu, nu do not depend on the sweeps -- before it stores the
+// scaled values.  So the loads of the next chunks stay in flight while a
+// chunk is scaled and stored and while the cluster barrier is crossed.  The
+// slot is re-filled only after the values read from it have been consumed by
+// the scaling, so the copy cannot overtake the read.  Per thread and chunk:
+// PF blocks of kappa x kappa pixels, 16 float4 (PF = 4 for kappa = 4, 1 for
+// kappa = 8); float4 j of thread t sits at position j ^ (t & 7) of its slot,
+// so that the eight threads of a quarter warp read distinct banks.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr_u32(smem_dst)), "l"(gsrc)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory"); }
+
+constexpr int IPFA_SLOT_F4 = 16;   // float4 per thread and chunk
+
+template <int KAP, int THR, int SLOTS>
+__global__ void __launch_bounds__(THR)
+ipf_async_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair_ids, int C, int csr_cap) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int rank = (int)cl.block_rank();
+    const PairDev& P = pairs[pair_ids[blockIdx.x / C]];
+    const int N = P.N, n = P.n, M = P.M;
+    const int Mc = M / C, k0 = rank * Mc;                    // owned blocks [k0, k0 + Mc)
+    float4* ring = reinterpret_cast<float4*>(smem_raw);      // [SLOTS][THR][IPFA_SLOT_F4]
+    float* Aown = reinterpret_cast<float*>(ring + (size_t)SLOTS * THR * IPFA_SLOT_F4);
+    float* Bown = Aown + Mc;
+    float* v_s = Bown + Mc;
+    float* vc_s = v_s + csr_cap;
+    int* ci_s = reinterpret_cast<int*>(vc_s + csr_cap);
+    int* ri_s = ci_s + csr_cap;
+    int* rp_s = ri_s + csr_cap;
+    int* cp_s = rp_s + Mc + 1;
+    const int r_base = P.rowptr[k0], c_base = P.colptr[k0];
+    const int r_cnt = P.rowptr[k0 + Mc] - r_base, c_cnt = P.colptr[k0 + Mc] - c_base;
+    const bool staged = csr_cap > 0 && r_cnt <= csr_cap && c_cnt <= csr_cap;
+    const float* vt = reinterpret_cast<const float*>(P.val_t);
+    const float* vct = reinterpret_cast<const float*>(P.valc_t);
+    if (staged) {
+        for (int k = threadIdx.x; k <= Mc; k += THR) {
+            rp_s[k] = P.rowptr[k0 + k] - r_base;
+            cp_s[k] = P.colptr[k0 + k] - c_base;
+        }
+        for (int e = threadIdx.x; e < r_cnt; e += THR) { ci_s[e] = P.colidx[r_base + e]; v_s[e] = vt[r_base + e]; }
+        for (int e = threadIdx.x; e < c_cnt; e += THR) { ri_s[e] = P.rowidx[c_base + e]; vc_s[e] = vct[c_base + e]; }
+    }
+    constexpr int KK = KAP * KAP;
+    const float kinvK = 1.0f / (float)(KK * KK);              // kappa^-4, exact (a power of two)
+    for (int k = threadIdx.x; k < Mc; k += THR) Bown[k] = (float)KK;   // b = 1
+    const float* mu_t = reinterpret_cast<const float*>(P.mu_t);
+    const float* nu_t = reinterpret_cast<const float*>(P.nu_t);
+    float* a = reinterpret_cast<float*>(P.a);
+    float* bb = reinterpret_cast<float*>(P.b);
+    constexpr int Q = KAP / 4;                                // float4 per block row
+    constexpr int PF = KAP == 4 ? 4 : 1;                      // blocks per chunk and thread
+    constexpr int CH = PF * THR;                              // blocks per chunk
+    const int nch = (Mc + CH - 1) / CH;                       // chunks per half sweep
+    const int halves = 2 * P.sweeps;
+    const int total = halves * nch;
+    // chunk gi -> slot gi % SLOTS; blocks kl = c CH + q THR + tid of half gi / nch
+    auto issue = [&](int gi) {
+        if (gi < total) {
+            const int c = gi - (gi / nch) * nch;
+            const float* src = ((gi / nch) & 1) == 0 ? mu_t : nu_t;
+            float4* slot = ring + ((size_t)(gi % SLOTS) * THR + threadIdx.x) * IPFA_SLOT_F4;
+#pragma unroll
+            for (int q = 0; q < PF; ++q) {
+                const int kl = c * CH + q * THR + threadIdx.x;
+                if (kl < Mc) {
+                    const int k = k0 + kl;
+                    const int k1 = k / n, k2 = k - (k / n) * n;
+#pragma unroll
+                    for (int t1 = 0; t1 < KAP; ++t1)
+#pragma unroll
+                        for (int t2 = 0; t2 < Q; ++t2)
+                            cp_async16(slot + (((q * KAP + t1) * Q + t2) ^ (threadIdx.x & 7)),
+                                       src + (size_t)(k1 * KAP + t1) * N + k2 * KAP + 4 * t2);
+                }
+            }
+        }
+        cp_async_commit();                                    // possibly empty: uniform group count
+    };
+#pragma unroll
+    for (int gi = 0; gi < SLOTS; ++gi) issue(gi);
+    cl.sync();                                                // staging and b = 1 visible
+    int gi = 0;
+    for (int h = 0; h < halves; ++h) {
+        const int half = h & 1;
+        float* dst = half == 0 ? a : bb;
+        float* mine = half == 0 ? Aown : Bown;
+        const float* other = half == 0 ? Bown : Aown;
+        bool arrived = false;
+        for (int c = 0; c < nch; ++c, ++gi) {
+            cp_async_wait<SLOTS - 1>();                       // this thread's chunk gi has landed
+            const float4* slot = ring + ((size_t)(gi % SLOTS) * THR + threadIdx.x) * IPFA_SLOT_F4;
+            float4 x[PF][KAP][Q];
+#pragma unroll
+            for (int q = 0; q < PF; ++q)
+#pragma unroll
+                for (int t1 = 0; t1 < KAP; ++t1)
+#pragma unroll
+                    for (int t2 = 0; t2 < Q; ++t2) x[q][t1][t2] = slot[((q * KAP + t1) * Q + t2) ^ (threadIdx.x & 7)];
+            float inv[PF];
+#pragma unroll
+            for (int q = 0; q < PF; ++q) {
+                const int kl = c * CH + q * THR + threadIdx.x;
+                inv[q] = 0.0f;
+                if (kl < Mc) {
+                    float r = 0.0f;
+                    const int* ptr = staged ? (half == 0 ? rp_s : cp_s) : (half == 0 ? P.rowptr : P.colptr);
+                    const int* idx = staged ? (half == 0 ? ci_s : ri_s) : (half == 0 ? P.colidx : P.rowidx);
+                    const float* val = staged ? (half == 0 ? v_s : vc_s) : (half == 0 ? vt : vct);
+                    const int row = staged ? kl : k0 + kl;
+                    for (int e = ptr[row]; e < ptr[row + 1]; ++e) {
+                        const int l = idx[e], owner = l / Mc;
+                        const float* peer = cl.map_shared_rank(other, owner);
+                        r += val[e] * peer[l - owner * Mc];
+                    }
+                    r *= kinvK;
+                    inv[q] = r > 0.0f ? 1.0f / r : 0.0f;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < PF; ++q) {
+                const int kl = c * CH + q * THR + threadIdx.x;
+                if (kl < Mc) {
+                    float sum = 0.0f;
+#pragma unroll
+                    for (int t1 = 0; t1 < KAP; ++t1)
+#pragma unroll
+                        for (int t2 = 0; t2 < Q; ++t2) {
+                            float4& v = x[q][t1][t2];
+                            v.x *= inv[q]; v.y *= inv[q]; v.z *= inv[q]; v.w *= inv[q];
+                            sum += (v.x + v.y) + (v.z + v.w);
+                        }
+                    mine[kl] = sum;
+                }
+            }
+            issue(gi + SLOTS);                                // the slot's values are consumed
+            if (c == nch - 1) { cluster_arrive_release(); arrived = true; }   // sums published
+#pragma unroll
+            for (int q = 0; q < PF; ++q) {
+                const int kl = c * CH + q * THR + threadIdx.x;
+                if (kl < Mc) {
+                    const int k = k0 + kl;
+                    const int k1 = k / n, k2 = k - (k / n) * n;
+#pragma unroll
+                    for (int t1 = 0; t1 < KAP; ++t1)
+#pragma unroll
+                        for (int t2 = 0; t2 < Q; ++t2)
+                            *reinterpret_cast<float4*>(dst + (size_t)(k1 * KAP + t1) * N + k2 * KAP + 4 * t2) =
+                                x[q][t1][t2];
+                }
+            }
+        }
+        if (!arrived) cluster_arrive_release();
+        cluster_wait_acquire();
+    }
+    cp_async_wait<0>();                                       // nothing left in flight
+}
+
+// ring, block sums, and (csr_cap > 0) the staged plan rows and columns
+static size_t ipf_async_smem(int slots, int thr, int Mc, int csr_cap) {
+    return sizeof(float4) * (size_t)slots * thr * IPFA_SLOT_F4 + sizeof(float) * 2 * (size_t)Mc +
+           (csr_cap > 0 ? 2 * (sizeof(float) + sizeof(int)) * (size_t)csr_cap + 2 * sizeof(int) * (size_t)(Mc + 1)
+                        : 0);
+}
+
+template <int KAP, int THR, int SLOTS>
+static int ipf_async_launch(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int C, int M_max,
+                            int nnz_max, bool stage_plan, cudaStream_t stream) {
+    const int Mc = M_max / C;
+    // staged plan rows and columns (room for the 2 Mc entries a basic plan
+    // has on average per CTA; a CTA whose blocks hold more reads its part of
+    // the plan from global memory) only while two CTAs still fit on an SM
+    int csr_cap = stage_plan ? std::max(nnz_max, 2 * Mc + 64) : 0;
+    size_t smem = ipf_async_smem(SLOTS, THR, Mc, csr_cap);
+    if (smem > 112 * 1024) { csr_cap = 0; smem = ipf_async_smem(SLOTS, THR, Mc, 0); }
+    if (smem > 227 * 1024) return QWB_ERR_UNSUPPORTED;
+    auto kern = ipf_async_kernel<KAP, THR, SLOTS>;
+    QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (C > 8) QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(n_pairs * C));
+    cfg.blockDim = dim3(THR);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    QWB_CUDA(cudaLaunchKernelEx(&cfg, kern, pairs_d, pair_ids, C, csr_cap));
+    QWB_LAUNCHED();
+    return QWB_OK;
+}
+
+int launch_ipf_async(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int kappa, int C, int variant,
+                     int M_max, int nnz_max, cudaStream_t stream) {
+    if (n_pairs <= 0) return QWB_OK;
+    if (C < 1 || C > 16 || (kappa != 4 && kappa != 8)) return QWB_ERR_UNSUPPORTED;
+    // variant 0: 256 threads, one slot per thread; 1: 128 threads, two slots;
+    // 2: 128 threads, three slots, the plan read from global memory (the
+    // ring then fills the shared memory two CTAs per SM can have)
+    if (variant == 0)
+        return kappa == 4 ? ipf_async_launch<4, 256, 1>(pairs_d, pair_ids, n_pairs, C, M_max, nnz_max, true, stream)
+                          : ipf_async_launch<8, 256, 1>(pairs_d, pair_ids, n_pairs, C, M_max, nnz_max, true, stream);
+    if (variant == 1)
+        return kappa == 4 ? ipf_async_launch<4, 128, 2>(pairs_d, pair_ids, n_pairs, C, M_max, nnz_max, true, stream)
+                          : ipf_async_launch<8, 128, 2>(pairs_d, pair_ids, n_pairs, C, M_max, nnz_max, true, stream);
+    if (variant == 2)
+        return kappa == 4 ? ipf_async_launch<4, 128, 3>(pairs_d, pair_ids, n_pairs, C, M_max, nnz_max, false, stream)
+                          : ipf_async_launch<8, 128, 3>(pairs_d, pair_ids, n_pairs, C, M_max, nnz_max, false, stream);
+    return QWB_ERR_UNSUPPORTED;
+}
+
+// --------------------------------------------------------------------------
 // ipf_stream: the same fine FP32 IPF sweeps as ipf_fine_kernel (same cluster
 // ownership, block sums through distributed shared memory, one cluster
 // barrier per half sweep), with the source values staged by bulk copies.

@@ -173,7 +173,8 @@ def test_invalid_inputs():
 SHAPES = [(R, TC, 0) for R, TC in [(1, 1), (2, 2), (4, 4), (8, 8), (16, 8), (16, 16), (8, 16)]] + \
          [(8, 8, 1), (16, 8, 1), (16, 16, 1)] + \
          [(8, 8, 2), (16, 8, 2), (8, 16, 2), (16, 16, 2)] + \
-         [(8, 8, 3), (8, 8, 4), (8, 16, 4), (8, 16, 5), (16, 8, 5), (16, 16, 5), (8, 16, 6)]
+         [(8, 8, 3), (8, 8, 4), (8, 16, 4), (8, 16, 5), (16, 8, 5), (16, 16, 5), (8, 16, 6)] + \
+         [(16, 16, 7), (16, 8, 7), (8, 16, 7), (16, 16, 8)]
 
 
 @pytest.mark.parametrize("R,TC,packing", SHAPES)
@@ -188,7 +189,8 @@ def test_ctransform_every_shape_p2(R, TC, packing, N, in_rows):
 
 
 @pytest.mark.parametrize("R,TC,packing", [(8, 8, 0), (16, 8, 1), (16, 8, 2), (8, 16, 2), (16, 16, 2),
-                                           (8, 8, 3), (8, 16, 4), (16, 16, 5), (8, 16, 6)])
+                                           (8, 8, 3), (8, 16, 4), (16, 16, 5), (8, 16, 6), (16, 16, 7),
+                                           (16, 16, 8)])
 @pytest.mark.parametrize("p", [1.0, 1.5])
 def test_ctransform_every_shape_general_p(R, TC, packing, p):
     N = 32
