@@ -254,14 +254,21 @@ int qwb_ctransform(qwb_ctx* ctx, int32_t N, double p, const double* h_d, double*
  *            CTAs per SM, the p = 2 window costs formed on the fly (3, 6) or
  *            kept in registers (4, 5); 7, 8 (MIXED, d = 2 only) packings 5
  *            and 2 with each candidate pair's subtraction and min fused in
- *            one assembly block.
+ *            one assembly block; 9, 10 (MIXED, d = 2, p = 2 only) the
+ *            shifted form with 2 (9) or 1 (10) resident CTAs per SM: the
+ *            line part A of c = A + D is taken off the staged potential
+ *            (h - A rounded up) and each candidate is D - (h - A) rounded
+ *            down, so the result is still a certified transform
+ *            (h_i + out_j <= C_ij) but may lie below the once-rounded one by
+ *            the rounding of h - A.
  *   in_rows  input lines per work item (0 = the default split); work items
  *            that see part of the input lines combine by atomic min.
  * Compiled shapes: packing 0: (R, TC) in {1,2,4,8,16} x {same} and (16,8),
  * (8,16); packing 1: (8,8), (16,8), (16,16); packing 2: (8,8), (16,8), (8,16),
  * (16,16); packing 3: (8,8); packing 4: (8,8), (8,16); packing 5: (8,16),
  * (16,8), (16,16); packing 6: (8,16); packing 7: (16,16), (16,8), (8,16);
- * packing 8: (16,16).  Other shapes return QWB_ERR_UNSUPPORTED.
+ * packing 8: (16,16); packing 9: (16,16), (16,8), (8,16); packing 10:
+ * (16,16), (32,16), (32,8).  Other shapes return QWB_ERR_UNSUPPORTED.
  * h_d, out_d: N^d FP64 device.  Synchronises `stream` before returning.
  * Errors: INVALID_ARG, UNSUPPORTED, CUDA, OOM. */
 int qwb_ctransform_shape(qwb_ctx* ctx, int32_t N, int32_t d, double p, const double* h_d,
@@ -382,12 +389,12 @@ int qwb_batch_coarse_potentials(qwb_batch* batch, int32_t pair, double* f_h, dou
  * share N; a timed-out wait makes qwb_batch_results return TIMEOUT.
  * C | QWB_IPF_ASYNC selects the form in which every thread brings its own
  * blocks' source values in by 16-byte asynchronous copies (cp.async) into a
- * private shared-memory slot, re-filled with the next chunk before the
- * current one is stored (256 threads per CTA, one slot per thread);
- * C | QWB_IPF_ASYNC2 the same with 128 threads per CTA and two slots per
- * thread; C | QWB_IPF_ASYNC3 with 128 threads, three slots and the plan
- * read from global memory.  Overrides the autotuner's choice, which times
- * every form;
+ * ring of private shared-memory slots, re-filling a slot with the chunk
+ * that many chunks ahead once its values are scaled, so copies stay in
+ * flight while a chunk is stored (128 threads per CTA, two slots per
+ * thread); C | QWB_IPF_ASYNC2 the same with 64 threads and four slots;
+ * C | QWB_IPF_ASYNC3 with 256 threads and two slots.  Overrides the
+ * autotuner's choice, which times every form;
  * synchronises the device and drops the batch's captured fine-pass graphs.
  * Errors: INVALID_ARG, CUDA. */
 #define QWB_IPF_BULK 32

@@ -57,9 +57,9 @@ def _ptr(t):
 
 
 QWB_IPF_BULK = 32   # Batch.set_ipf_cluster(C | QWB_IPF_BULK): the bulk-copy staged sweeps
-QWB_IPF_ASYNC = 64    # ... | QWB_IPF_ASYNC: per-thread asynchronous copies, one slot per thread
-QWB_IPF_ASYNC2 = 128  # ... | QWB_IPF_ASYNC2: the same with 128-thread CTAs and two slots
-QWB_IPF_ASYNC3 = 256  # ... | QWB_IPF_ASYNC3: 128-thread CTAs, three slots, plan read from global memory
+QWB_IPF_ASYNC = 64    # ... | QWB_IPF_ASYNC: per-thread asynchronous copies, 128 threads x 2 slots
+QWB_IPF_ASYNC2 = 128  # ... | QWB_IPF_ASYNC2: 64 threads x 4 slots
+QWB_IPF_ASYNC3 = 256  # ... | QWB_IPF_ASYNC3: 256 threads x 2 slots
 
 
 def problem(N, kappa, p, d=2):

@@ -767,6 +767,8 @@ static int launch_ct_batched(qwb_batch* b, int phase, CtConfig cfg, int cap, cud
     if ((st = launch_ctransform(b->pairs_d, b->ct_b_items_d, b->n_ct_b_p2, phase, cfg, b->N_max, b->f64, cap, s)))
         return st;
     cfg.p2 = false;
+    if (cfg.packed == 9) cfg.packed = 5;          // the shifted kernels are p = 2 only: the same shape
+    else if (cfg.packed == 10) cfg.packed = 2;    // with the costs added per line pair
     return launch_ctransform(b->pairs_d, b->ct_b_items_d + b->n_ct_b_p2, b->n_ct_b - b->n_ct_b_p2, phase, cfg,
                              b->N_max, b->f64, cap, s);
 }
@@ -948,10 +950,12 @@ static int tune_ctransform(qwb_batch* b, cudaStream_t s) {
                            {8, 8, 1}, {16, 8, 1}, {16, 16, 1},
                            {8, 8, 2}, {16, 8, 2}, {8, 16, 2}, {16, 16, 2},
                            {8, 8, 3}, {8, 8, 4}, {8, 16, 4}, {8, 16, 5}, {16, 8, 5}, {16, 16, 5},
-                           {8, 16, 6}, {16, 16, 7}, {16, 8, 7}, {8, 16, 7}, {16, 16, 8}};
+                           {8, 16, 6}, {16, 16, 7}, {16, 8, 7}, {8, 16, 7}, {16, 16, 8},
+                           {16, 16, 9}, {16, 8, 9}, {8, 16, 9}, {16, 16, 10}, {32, 16, 10}, {32, 8, 10}};
     static const char* const kPackName[] = {"", "_packed", "_linepairs", "_linepairs_3cta_fly",
                                             "_linepairs_3cta", "_linepairs_2cta", "_linepairs_2cta_fly",
-                                            "_linepairs_2cta_fused", "_linepairs_fused"};
+                                            "_linepairs_2cta_fused", "_linepairs_fused",
+                                            "_linepairs_shifted_2cta", "_linepairs_shifted"};
     const int sm = b->ctx->sm_count > 0 ? b->ctx->sm_count : 148;
     std::ostringstream rep;
     double best = 1e30;
@@ -959,6 +963,7 @@ static int tune_ctransform(qwb_batch* b, cudaStream_t s) {
     rep << "{";
     for (auto& c : cand) {
         if (b->N_gcd % c[0] || b->N_gcd % c[1] || (c[2] && b->f64) || (c[2] >= 3 && b->has_3d)) continue;
+        if (c[2] >= 9 && b->n_ct_b_p2 == 0) continue;            // p = 2 only
         CtConfig cfg = b->ct_cfg_b;
         cfg.R = c[0]; cfg.TC = c[1]; cfg.packed = c[2];
         double ms;
@@ -994,8 +999,8 @@ static int tune_ipf(qwb_batch* b, cudaStream_t s) {
     double best = 1e30;
     int bestC = 0;
     for (int C : {0, 2, 4, 8, 16, QWB_IPF_BULK | 2, QWB_IPF_BULK | 4, QWB_IPF_BULK | 8, QWB_IPF_BULK | 16,
-                  QWB_IPF_ASYNC | 2, QWB_IPF_ASYNC | 4, QWB_IPF_ASYNC | 8, QWB_IPF_ASYNC2 | 4,
-                  QWB_IPF_ASYNC2 | 8, QWB_IPF_ASYNC3 | 4, QWB_IPF_ASYNC3 | 8}) {
+                  QWB_IPF_ASYNC | 2, QWB_IPF_ASYNC | 4, QWB_IPF_ASYNC | 8, QWB_IPF_ASYNC2 | 2,
+                  QWB_IPF_ASYNC2 | 4, QWB_IPF_ASYNC3 | 2, QWB_IPF_ASYNC3 | 4}) {
         int st = apply_ipf_choice(b, C);
         if (st) return st;
         if (C > 0) {
@@ -1015,8 +1020,8 @@ static int tune_ipf(qwb_batch* b, cudaStream_t s) {
         }, &ms);
         if (st) return st;
         rep << (C ? ", " : "") << "\""
-            << ((C & QWB_IPF_BULK) ? "bulk" : (C & QWB_IPF_ASYNC) ? "async" : (C & QWB_IPF_ASYNC2) ? "async2slot"
-                : (C & QWB_IPF_ASYNC3) ? "async3slot" : "cluster")
+            << ((C & QWB_IPF_BULK) ? "bulk" : (C & QWB_IPF_ASYNC) ? "async128x2" : (C & QWB_IPF_ASYNC2) ? "async64x4"
+                : (C & QWB_IPF_ASYNC3) ? "async256x2" : "cluster")
             << (C & 31) << "\": " << ms;
         if (ms < best) { best = ms; bestC = C; }
     }
@@ -2050,8 +2055,8 @@ int qwb_ctransform(qwb_ctx* ctx, int32_t N, double p, const double* h_d, double*
 int qwb_ctransform_shape(qwb_ctx* ctx, int32_t N, int32_t d, double p, const double* h_d,
                          double* out_d, int32_t R, int32_t TC, int32_t packing, int32_t in_rows,
                          qwb_prec prec, void* stream) {
-    if (R < 1 || TC < 1 || N < 1 || N % R || N % TC || packing < 0 || packing > 8 || in_rows < 0)
-        return fail(QWB_ERR_INVALID_ARG, "qwb_ctransform_shape: R and TC must divide N; packing in 0..8");
+    if (R < 1 || TC < 1 || N < 1 || N % R || N % TC || packing < 0 || packing > 10 || in_rows < 0)
+        return fail(QWB_ERR_INVALID_ARG, "qwb_ctransform_shape: R and TC must divide N; packing in 0..10");
     if (packing && prec == QWB_PREC_F64)
         return fail(QWB_ERR_INVALID_ARG, "qwb_ctransform_shape: packing needs MIXED precision");
     CtConfig c;

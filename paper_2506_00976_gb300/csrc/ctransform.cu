@@ -346,6 +346,117 @@ ctransform_rp_kernel(const PairDev* __restrict__ pairs, const CtItem* __restrict
     }
 }
 
+// --------------------------------------------------------------------------
+// Shifted line-paired variant (p = 2, FP32, 2-D).  With c_ij = A + D,
+// A = (i1 - j1)^2 the line part and D = (i2 - j2)^2 the column part, the
+// candidate is c_ij - h_i = D - (h_i - A).  Per input line pair the thread
+// forms hA = h - A once per staged value, rounded up (so hA >= h - A), and
+// every candidate of the pair is fl_down(D_e - hA) with the column parts D_e
+// of the chunk's window, which do not depend on the line: one packed
+// subtraction and one 3-input min per two candidates, no per-line window.
+// Since D - hA <= c - h, every candidate is at most the exact c_ij - h_i and
+// h_i + out_j <= c_ij holds exactly; against the transform rounded down once
+// per candidate, a result can be lower by the rounding of hA (an ulp of
+// |h - A|).  A odd last line is paired with h = -inf (candidates +inf).
+// --------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long sub_ru_x2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("sub.rp.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long mul_rn_x2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+template <int R, int TC, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+ctransform_rpd_kernel(const PairDev* __restrict__ pairs, const CtItem* __restrict__ items,
+                      int n_items, int phase) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* hs2 = reinterpret_cast<float2*>(smem_raw);      // [line pair][column]
+    constexpr int NQ = R + TC - 1;
+    static_assert(TC % 2 == 0, "two columns per 16-byte shared load");
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const CtItem I = items[it];
+        const PairDev& P = pairs[I.pair];
+        const int N = P.N, m = P.m;
+        const float* h = reinterpret_cast<const float*>(phase == 0 ? P.fhat : P.g);
+        float* out = reinterpret_cast<float*>(phase == 0 ? P.g : P.f);
+        const int npairs = (I.in_rows + 1) >> 1;
+        const float* hsrc = h + (size_t)I.in_row0 * N;
+        for (int k = threadIdx.x; k < npairs * N; k += blockDim.x) {
+            const int lp = k / N, c = k - lp * N;
+            const float lo = hsrc[(size_t)(2 * lp) * N + c];
+            const float hi = 2 * lp + 1 < I.in_rows ? hsrc[(size_t)(2 * lp + 1) * N + c]
+                                                    : __int_as_float(0xff800000);   // -inf
+            hs2[k] = make_float2(lo, hi);
+        }
+        __syncthreads();
+        const int o_end = min(I.out0 + CT_TILE, m);
+        for (int o = I.out0 + threadIdx.x * R; o < o_end; o += blockDim.x * R) {
+            float mins[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) mins[r] = pos_inf<float>();
+            const int j1 = o / N, j2 = o % N;
+            const float a0 = (float)(I.in_row0 - j1);                 // i1 - j1 of the first line
+            for (int c0 = 0; c0 < N; c0 += TC) {
+                unsigned long long DD[NQ];                            // (D_e, D_e), exact integers
+#pragma unroll
+                for (int e = 0; e < NQ; ++e) {
+                    const float d = (float)(c0 - j2 + e - (R - 1));
+                    DD[e] = pack2(d * d, d * d);
+                }
+                const ulonglong2* hrow = reinterpret_cast<const ulonglong2*>(hs2 + c0);
+                unsigned long long tt = pack2(a0, a0 + 1.0f);         // (i1 - j1, i1 + 1 - j1)
+                for (int lp = 0; lp < npairs; ++lp, hrow += N / 2) {
+                    const unsigned long long AA = mul_rn_x2(tt, tt);  // line parts, exact
+                    tt = add_rn_x2(tt, 0x4000000040000000ull);        // + (2, 2)
+#pragma unroll
+                    for (int s = 0; s < TC; s += 2) {
+                        const ulonglong2 v = hrow[s / 2];
+                        const unsigned long long hA0 = sub_ru_x2(v.x, AA), hA1 = sub_ru_x2(v.y, AA);
+#pragma unroll
+                        for (int ss = 0; ss < 2; ++ss) {
+                            const unsigned long long hA = ss ? hA1 : hA0;
+#pragma unroll
+                            for (int r = 0; r < R; ++r) mins[r] = sub2_min3(DD[s + ss - r + R - 1], hA, mins[r]);
+                        }
+                    }
+                }
+            }
+            if (I.in_rows < P.rows) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) atomic_min_fp(&out[o + r], mins[r]);
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) out[o + r] = mins[r];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int R, int TC, int MINB>
+static int ct_launch_rpd(const PairDev* pairs_d, const CtItem* items, int n_items, int phase,
+                         int threads, int in_rows, int N_max, int grid_cap, cudaStream_t stream) {
+    auto kern = ctransform_rpd_kernel<R, TC, MINB>;
+    threads = std::min(threads, CT_TILE / R);
+    const size_t smem = sizeof(float2) * (size_t)((in_rows + 1) / 2) * N_max;
+    if (smem > 227 * 1024) return QWB_ERR_UNSUPPORTED;
+    QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int grid = n_items;
+    if (grid_cap > 0) {
+        int occ = 1;
+        QWB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem));
+        grid = std::min(n_items, grid_cap * std::max(1, occ));
+    }
+    kern<<<grid, threads, smem, stream>>>(pairs_d, items, n_items, phase);
+    QWB_LAUNCHED();
+    return QWB_OK;
+}
+
 int ct_pick_r(int N, int want) {
     for (int r = want; r > 1; r >>= 1)
         if (N % r == 0) return r;
@@ -450,6 +561,18 @@ static int ct_launch_t(const PairDev* pairs_d, const CtItem* items, int n_items,
         QWB_CTRPF(7, 2, 16, 16) QWB_CTRPF(7, 2, 16, 8) QWB_CTRPF(7, 2, 8, 16)
         QWB_CTRPF(8, 1, 16, 16)
 #undef QWB_CTRPF
+        // packings 9, 10 (p = 2, 2-D only): the shifted line-paired kernel with
+        // the register budget of 2 (9) or 1 (10) resident CTAs per SM
+        if ((c.packed == 9 || c.packed == 10) && (c.has_3d || !P2)) return QWB_ERR_UNSUPPORTED;
+        if constexpr (P2) {
+#define QWB_CTRPD(PK, MB, RR, TT)                                                          \
+            if (c.R == RR && c.TC == TT && c.packed == PK)                                 \
+                return ct_launch_rpd<RR, TT, MB>(pairs_d, items, n_items, phase, c.threads, c.in_rows, \
+                                                 N_max, grid_cap, stream);
+            QWB_CTRPD(9, 2, 16, 16) QWB_CTRPD(9, 2, 16, 8) QWB_CTRPD(9, 2, 8, 16) QWB_CTRPD(10, 1, 16, 16)
+            QWB_CTRPD(10, 1, 32, 16) QWB_CTRPD(10, 1, 32, 8)
+#undef QWB_CTRPD
+        }
     }
     return QWB_ERR_UNSUPPORTED;
 }

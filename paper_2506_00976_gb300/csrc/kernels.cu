@@ -2056,15 +2056,17 @@ ipf_async_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair
     const PairDev& P = pairs[pair_ids[blockIdx.x / C]];
     const int N = P.N, n = P.n, M = P.M;
     const int Mc = M / C, k0 = rank * Mc;                    // owned blocks [k0, k0 + Mc)
+    // [ring | block sums | staged plan: values (float), block indices and
+    // row / column offsets (16 bits: M <= 4096 and offsets <= csr_cap < 2^16)]
     float4* ring = reinterpret_cast<float4*>(smem_raw);      // [SLOTS][THR][IPFA_SLOT_F4]
     float* Aown = reinterpret_cast<float*>(ring + (size_t)SLOTS * THR * IPFA_SLOT_F4);
     float* Bown = Aown + Mc;
     float* v_s = Bown + Mc;
     float* vc_s = v_s + csr_cap;
-    int* ci_s = reinterpret_cast<int*>(vc_s + csr_cap);
-    int* ri_s = ci_s + csr_cap;
-    int* rp_s = ri_s + csr_cap;
-    int* cp_s = rp_s + Mc + 1;
+    uint16_t* ci_s = reinterpret_cast<uint16_t*>(vc_s + csr_cap);
+    uint16_t* ri_s = ci_s + csr_cap;
+    uint16_t* rp_s = ri_s + csr_cap;
+    uint16_t* cp_s = rp_s + Mc + 1;
     const int r_base = P.rowptr[k0], c_base = P.colptr[k0];
     const int r_cnt = P.rowptr[k0 + Mc] - r_base, c_cnt = P.colptr[k0 + Mc] - c_base;
     const bool staged = csr_cap > 0 && r_cnt <= csr_cap && c_cnt <= csr_cap;
@@ -2072,11 +2074,11 @@ ipf_async_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair
     const float* vct = reinterpret_cast<const float*>(P.valc_t);
     if (staged) {
         for (int k = threadIdx.x; k <= Mc; k += THR) {
-            rp_s[k] = P.rowptr[k0 + k] - r_base;
-            cp_s[k] = P.colptr[k0 + k] - c_base;
+            rp_s[k] = (uint16_t)(P.rowptr[k0 + k] - r_base);
+            cp_s[k] = (uint16_t)(P.colptr[k0 + k] - c_base);
         }
-        for (int e = threadIdx.x; e < r_cnt; e += THR) { ci_s[e] = P.colidx[r_base + e]; v_s[e] = vt[r_base + e]; }
-        for (int e = threadIdx.x; e < c_cnt; e += THR) { ri_s[e] = P.rowidx[c_base + e]; vc_s[e] = vct[c_base + e]; }
+        for (int e = threadIdx.x; e < r_cnt; e += THR) { ci_s[e] = (uint16_t)P.colidx[r_base + e]; v_s[e] = vt[r_base + e]; }
+        for (int e = threadIdx.x; e < c_cnt; e += THR) { ri_s[e] = (uint16_t)P.rowidx[c_base + e]; vc_s[e] = vct[c_base + e]; }
     }
     constexpr int KK = KAP * KAP;
     const float kinvK = 1.0f / (float)(KK * KK);              // kappa^-4, exact (a power of two)
@@ -2141,14 +2143,24 @@ ipf_async_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair
                 inv[q] = 0.0f;
                 if (kl < Mc) {
                     float r = 0.0f;
-                    const int* ptr = staged ? (half == 0 ? rp_s : cp_s) : (half == 0 ? P.rowptr : P.colptr);
-                    const int* idx = staged ? (half == 0 ? ci_s : ri_s) : (half == 0 ? P.colidx : P.rowidx);
-                    const float* val = staged ? (half == 0 ? v_s : vc_s) : (half == 0 ? vt : vct);
-                    const int row = staged ? kl : k0 + kl;
-                    for (int e = ptr[row]; e < ptr[row + 1]; ++e) {
-                        const int l = idx[e], owner = l / Mc;
-                        const float* peer = cl.map_shared_rank(other, owner);
-                        r += val[e] * peer[l - owner * Mc];
+                    if (staged) {
+                        const uint16_t* ptr = half == 0 ? rp_s : cp_s;
+                        const uint16_t* idx = half == 0 ? ci_s : ri_s;
+                        const float* val = half == 0 ? v_s : vc_s;
+                        for (int e = ptr[kl]; e < ptr[kl + 1]; ++e) {
+                            const int l = idx[e], owner = l / Mc;
+                            const float* peer = cl.map_shared_rank(other, owner);
+                            r += val[e] * peer[l - owner * Mc];
+                        }
+                    } else {
+                        const int* ptr = half == 0 ? P.rowptr : P.colptr;
+                        const int* idx = half == 0 ? P.colidx : P.rowidx;
+                        const float* val = half == 0 ? vt : vct;
+                        for (int e = ptr[k0 + kl]; e < ptr[k0 + kl + 1]; ++e) {
+                            const int l = idx[e], owner = l / Mc;
+                            const float* peer = cl.map_shared_rank(other, owner);
+                            r += val[e] * peer[l - owner * Mc];
+                        }
                     }
                     r *= kinvK;
                     inv[q] = r > 0.0f ? 1.0f / r : 0.0f;
@@ -2196,7 +2208,8 @@ ipf_async_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair
 // ring, block sums, and (csr_cap > 0) the staged plan rows and columns
 static size_t ipf_async_smem(int slots, int thr, int Mc, int csr_cap) {
     return sizeof(float4) * (size_t)slots * thr * IPFA_SLOT_F4 + sizeof(float) * 2 * (size_t)Mc +
-           (csr_cap > 0 ? 2 * (sizeof(float) + sizeof(int)) * (size_t)csr_cap + 2 * sizeof(int) * (size_t)(Mc + 1)
+           (csr_cap > 0 ? 2 * (sizeof(float) + sizeof(uint16_t)) * (size_t)csr_cap +
+                              2 * sizeof(uint16_t) * (size_t)(Mc + 1)
                         : 0);
 }
 
@@ -2206,10 +2219,12 @@ static int ipf_async_launch(const PairDev* pairs_d, const int* pair_ids, int n_p
     const int Mc = M_max / C;
     // staged plan rows and columns (room for the 2 Mc entries a basic plan
     // has on average per CTA; a CTA whose blocks hold more reads its part of
-    // the plan from global memory) only while two CTAs still fit on an SM
+    // the plan from global memory) only while two CTAs still fit on an SM,
+    // or, for a ring too large for two, within one CTA's shared memory
     int csr_cap = stage_plan ? std::max(nnz_max, 2 * Mc + 64) : 0;
     size_t smem = ipf_async_smem(SLOTS, THR, Mc, csr_cap);
-    if (smem > 112 * 1024) { csr_cap = 0; smem = ipf_async_smem(SLOTS, THR, Mc, 0); }
+    const size_t budget = ipf_async_smem(SLOTS, THR, 0, 0) <= 96 * 1024 ? 112 * 1024 : 220 * 1024;
+    if (smem > budget) { csr_cap = 0; smem = ipf_async_smem(SLOTS, THR, Mc, 0); }
     if (smem > 227 * 1024) return QWB_ERR_UNSUPPORTED;
     auto kern = ipf_async_kernel<KAP, THR, SLOTS>;
     QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -2235,18 +2250,18 @@ int launch_ipf_async(const PairDev* pairs_d, const int* pair_ids, int n_pairs, i
                      int M_max, int nnz_max, cudaStream_t stream) {
     if (n_pairs <= 0) return QWB_OK;
     if (C < 1 || C > 16 || (kappa != 4 && kappa != 8)) return QWB_ERR_UNSUPPORTED;
-    // variant 0: 256 threads, one slot per thread; 1: 128 threads, two slots;
-    // 2: 128 threads, three slots, the plan read from global memory (the
-    // ring then fills the shared memory two CTAs per SM can have)
+    // variant 0: 128 threads, two slots per thread; 1: 64 threads, four
+    // slots; 2: 256 threads, two slots (64 KB, 64 KB and 128 KB of copies in
+    // flight per CTA; the first two leave room for two CTAs per SM)
     if (variant == 0)
-        return kappa == 4 ? ipf_async_launch<4, 256, 1>(pairs_d, pair_ids, n_pairs, C, M_max, nnz_max, true, stream)
-                          : ipf_async_launch<8, 256, 1>(pairs_d, pair_ids, n_pairs, C, M_max, nnz_max, true, stream);
-    if (variant == 1)
         return kappa == 4 ? ipf_async_launch<4, 128, 2>(pairs_d, pair_ids, n_pairs, C, M_max, nnz_max, true, stream)
                           : ipf_async_launch<8, 128, 2>(pairs_d, pair_ids, n_pairs, C, M_max, nnz_max, true, stream);
+    if (variant == 1)
+        return kappa == 4 ? ipf_async_launch<4, 64, 4>(pairs_d, pair_ids, n_pairs, C, M_max, nnz_max, true, stream)
+                          : ipf_async_launch<8, 64, 4>(pairs_d, pair_ids, n_pairs, C, M_max, nnz_max, true, stream);
     if (variant == 2)
-        return kappa == 4 ? ipf_async_launch<4, 128, 3>(pairs_d, pair_ids, n_pairs, C, M_max, nnz_max, false, stream)
-                          : ipf_async_launch<8, 128, 3>(pairs_d, pair_ids, n_pairs, C, M_max, nnz_max, false, stream);
+        return kappa == 4 ? ipf_async_launch<4, 256, 2>(pairs_d, pair_ids, n_pairs, C, M_max, nnz_max, true, stream)
+                          : ipf_async_launch<8, 256, 2>(pairs_d, pair_ids, n_pairs, C, M_max, nnz_max, true, stream);
     return QWB_ERR_UNSUPPORTED;
 }
 

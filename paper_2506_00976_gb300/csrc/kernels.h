@@ -111,9 +111,8 @@ int launch_primal(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, 
 int launch_ipf_stream(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int kappa, int C, int n,
                       int N, int* err, unsigned long long timeout_ns, int skip_chunk, cudaStream_t stream);
 // The same sweeps with per-thread asynchronous copies into private shared-
-// memory slots (ipf_async_kernel): variant 0 = 256 threads and one slot per
-// thread, 1 = 128 threads and two slots, 2 = 128 threads and three slots with
-// the plan read from global memory.
+// memory slots (ipf_async_kernel): variant 0 = 128 threads and two slots per
+// thread, 1 = 64 threads and four slots, 2 = 256 threads and two slots.
 int launch_ipf_async(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int kappa, int C, int variant,
                      int M_max, int nnz_max, cudaStream_t stream);
 // primal pass with a general upscaling kernel (P.upK set; d = 2, kappa <= kappa_max <= 8;

@@ -188,6 +188,31 @@ def test_ctransform_every_shape_p2(R, TC, packing, N, in_rows):
     np.testing.assert_array_equal(g, rd32(O.c_transform(h, N, 2.0)))
 
 
+@pytest.mark.parametrize("R,TC,packing", [(16, 16, 9), (16, 8, 9), (8, 16, 9), (16, 16, 10), (32, 16, 10),
+                                           (32, 8, 10)])
+@pytest.mark.parametrize("N,in_rows", [(32, 0), (32, 5), (64, 7), (64, 1), (128, 0)])
+def test_ctransform_shifted_p2(R, TC, packing, N, in_rows):
+    """The shifted line-paired kernels (p = 2): every candidate is
+    fl_down(D - fl_up(h - A)) <= c - h, so the result never exceeds the exact
+    transform and every pair stays feasible (checked on all pixel pairs for
+    N <= 64); it lies below the once-rounded transform by at most the rounding
+    of h - A plus that of the result: within 3 FP32 ulps of the magnitudes
+    involved, and equal to it when every h - A is exact (integer h)."""
+    h = fp32_values(np.random.default_rng(500 + N + in_rows), N * N, 3.0 * N)
+    g = api.ctransform_shape(T(h), N, 2.0, R, TC, packing, in_rows).cpu().numpy()
+    exact = O.c_transform(h, N, 2.0)
+    assert np.all(g <= exact)
+    scale = np.abs(h).max() + 2.0 * (N - 1) ** 2
+    assert np.all(g >= exact - 3 * float(np.spacing(np.float32(scale))))
+    if N <= 64:
+        X = O.grid_points(N)
+        assert (h[:, None] + g[None, :] - O.ground_cost(X, X, 2.0)).max() <= 0.0
+    # integer potentials: h - A is exact, so the result is the once-rounded one
+    hi = np.round(h)
+    gi = api.ctransform_shape(T(hi), N, 2.0, R, TC, packing, in_rows).cpu().numpy()
+    np.testing.assert_array_equal(gi, rd32(O.c_transform(hi, N, 2.0)))
+
+
 @pytest.mark.parametrize("R,TC,packing", [(8, 8, 0), (16, 8, 1), (16, 8, 2), (8, 16, 2), (16, 16, 2),
                                            (8, 8, 3), (8, 16, 4), (16, 16, 5), (8, 16, 6), (16, 16, 7),
                                            (16, 16, 8)])
@@ -232,6 +257,8 @@ def test_ctransform_shape_rejects():
         api.ctransform_shape(h, 8, 2.0, 2, 8, 0)             # not compiled
     with pytest.raises(QwbError, match="UNSUPPORTED"):
         api.ctransform_shape(T(np.zeros(512)), 8, 2.0, 8, 8, 4, d=3)   # register-cut shapes are 2-D only
+    with pytest.raises(QwbError, match="UNSUPPORTED"):
+        api.ctransform_shape(T(np.zeros(256)), 16, 1.0, 16, 16, 9)     # shifted form: p = 2 only
 
 
 @pytest.mark.parametrize("prec", ["mixed", "f64"])
