@@ -75,19 +75,23 @@ template <typename T> __device__ __forceinline__ T pos_inf();
 template <> __device__ __forceinline__ float pos_inf<float>() { return __int_as_float(0x7f800000); }
 template <> __device__ __forceinline__ double pos_inf<double>() { return __longlong_as_double(0x7ff0000000000000LL); }
 
-// Atomic minimum on a float/double stored as such.  Non-negative values
-// order like signed integers, negative values order in reverse as unsigned
-// integers; the two branches together give an exact floating-point min.
+// Atomic minimum on a float/double stored as such.  Values with a clear sign
+// bit order like signed integers, values with the sign bit set order in
+// reverse as unsigned integers; the two branches together give an exact
+// floating-point min.  The branch is taken on the sign bit, not on v >= 0:
+// -0.0 compares equal to 0 but its signed-integer image is the most negative
+// integer, which would win a signed minimum against every negative value
+// already stored.
 __device__ __forceinline__ void atomic_min_fp(float* addr, float v) {
-    if (v >= 0.0f) atomicMin(reinterpret_cast<int*>(addr), __float_as_int(v));
+    if (!(__float_as_uint(v) >> 31)) atomicMin(reinterpret_cast<int*>(addr), __float_as_int(v));
     else atomicMax(reinterpret_cast<unsigned int*>(addr), __float_as_uint(v));
 }
 __device__ __forceinline__ void atomic_min_fp(double* addr, double v) {
-    if (v >= 0.0)
+    const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(v));
+    if (!(u >> 63))
         atomicMin(reinterpret_cast<long long*>(addr), __double_as_longlong(v));
     else
-        atomicMax(reinterpret_cast<unsigned long long*>(addr),
-                  static_cast<unsigned long long>(__double_as_longlong(v)));
+        atomicMax(reinterpret_cast<unsigned long long*>(addr), u);
 }
 
 // 3-input minimum: one instruction for two candidates in FP32 (PTX min with

@@ -188,6 +188,23 @@ def test_ctransform_every_shape_p2(R, TC, packing, N, in_rows):
     np.testing.assert_array_equal(g, rd32(O.c_transform(h, N, 2.0)))
 
 
+@pytest.mark.parametrize("R,TC,packing", SHAPES + [(16, 16, 9), (32, 16, 10)])
+@pytest.mark.parametrize("N,in_rows", [(32, 5), (32, 3), (64, 7)])
+def test_ctransform_integer_potentials_split(R, TC, packing, N, in_rows):
+    """Integer potentials make many candidates exact zeros, which the
+    round-down subtraction returns as -0.0; items that see part of the input
+    lines combine their minima by atomic min, and -0.0 must not beat a
+    negative partial minimum there (its signed-integer image is the most
+    negative integer).  The transform must be the exact one, bit for bit, and
+    feasible on every pixel pair."""
+    h = np.round(fp32_values(np.random.default_rng(700 + N + in_rows), N * N, 3.0 * N))
+    g = api.ctransform_shape(T(h), N, 2.0, R, TC, packing, in_rows).cpu().numpy()
+    exact = O.c_transform(h, N, 2.0)
+    np.testing.assert_array_equal(g, exact)
+    X = O.grid_points(N)
+    assert (h[:, None] + g[None, :] - O.ground_cost(X, X, 2.0)).max() <= 0.0
+
+
 @pytest.mark.parametrize("R,TC,packing", [(16, 16, 9), (16, 8, 9), (8, 16, 9), (16, 16, 10), (32, 16, 10),
                                            (32, 8, 10)])
 @pytest.mark.parametrize("N,in_rows", [(32, 0), (32, 5), (64, 7), (64, 1), (128, 0)])
