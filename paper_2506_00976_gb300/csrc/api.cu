@@ -256,6 +256,7 @@ struct qwb_batch {
     std::vector<GraphEntry> graphs;
     TuneEntry* tune = nullptr;
     int cbar_variant = 0;
+    bool cbar_forced = false;   // QWB_CBAR_VARIANT set: the tuner leaves the kappa = 4 choice alone
     int N_gcd = 1;
     bool all_p2 = false;
 };
@@ -372,6 +373,14 @@ static int apply_ipf_choice(qwb_batch* b, int C) {
     return QWB_OK;
 }
 
+// QWB_CBAR_VARIANT (testing, tuning): force the kappa = 4 C-bar kernel variant
+static void apply_cbar_env(qwb_batch* b) {
+    if (const char* v = std::getenv("QWB_CBAR_VARIANT")) {
+        const int cv = std::atoi(v);
+        if (cv == 2 || cv == 3 || (cv >= 6 && cv <= 8)) { b->cbar_variant = cv; b->cbar_forced = true; }
+    }
+}
+
 static CtConfig pick_ct_config(int N_gcd, bool all_p2) {
     CtConfig c;
     c.R = ct_pick_r(N_gcd, 16);
@@ -482,13 +491,16 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         if (found->ct_done && found->R > 0 && N_gcd % found->R == 0 && N_gcd % found->TC == 0) {
             b->ct_cfg_b.R = found->R; b->ct_cfg_b.TC = found->TC; b->ct_cfg_b.packed = found->packed;
         }
-        // the kappa = 4 row-direct kernel: three (2) or two (3) CTAs per SM
+        // the kappa = 4 row-direct kernel: three (2) or two (3) CTAs per SM, or
+        // the variants with first terms as products (6, 7, 8)
         b->cbar_variant = 2;
-        if (found->cbar_done && (found->cbar_variant == 2 || found->cbar_variant == 3))
+        if (found->cbar_done && (found->cbar_variant == 2 || found->cbar_variant == 3 ||
+                                 (found->cbar_variant >= 6 && found->cbar_variant <= 8)))
             b->cbar_variant = found->cbar_variant;
         if (found->cbar_done && (found->cbar8_variant == 4 || found->cbar8_variant == 5))
             b->cbar8_variant = found->cbar8_variant;
     }
+    apply_cbar_env(b);
     const int tile_out = CT_TILE;
     long total_tiles = 0;
     for (int t = 0; t < n; ++t) total_tiles += ((long)ipow(probs[t].N, dim_of(probs[t])) + tile_out - 1) / tile_out;
@@ -895,7 +907,10 @@ static const char* cbar_variant_name(int v) {
         case 2: return "kappa4_direct_rows/3_ctas_per_sm";
         case 3: return "kappa4_direct_rows/2_ctas_per_sm";
         case 4: return "kappa8_direct_rows/2_ctas_per_sm";
-        default: return "kappa8_direct_rows/1_cta_per_sm";
+        case 5: return "kappa8_direct_rows/1_cta_per_sm";
+        case 6: return "kappa4_direct_rows_8staged_firstmul/3_ctas_per_sm";
+        case 7: return "kappa4_direct_rows_8staged_firstmul/2_ctas_per_sm";
+        default: return "kappa4_direct_rows_firstmul/3_ctas_per_sm";
     }
 }
 
@@ -909,7 +924,8 @@ static int tune_cbar(qwb_batch* b, cudaStream_t s) {
     double best = 1e30;
     rep << "{";
     bool first = true;
-    for (int v = 2; v < 4 && b->n_cb4 > 0; ++v) {
+    for (int v : {2, 3, 6, 7, 8}) {
+        if (b->n_cb4 == 0) break;
         double ms;
         st = time_variant(s, b->ev[0], b->ev[1], [&] {
             return launch_cbar(b->pairs_d, b->cbar_items_d, b->n_cb4, 4, b->n_max4, b->N_max4, b->f64, s, v);
@@ -934,7 +950,7 @@ static int tune_cbar(qwb_batch* b, cudaStream_t s) {
     rep << "}";
     e->cbar_report = rep.str();
     e->cbar_done = true;
-    b->cbar_variant = e->cbar_variant;
+    if (!b->cbar_forced) b->cbar_variant = e->cbar_variant;
     b->cbar8_variant = e->cbar8_variant;
     tune_cache_store(b->ctx);
     return QWB_OK;
@@ -1784,6 +1800,7 @@ int qwb_coarse_cost(qwb_ctx* ctx, const qwb_problem* prob, const double* mu_d, c
     cudaStream_t s = (cudaStream_t)stream;
     qwb_batch* b;
     if ((st = single_batch(ctx, prob, 1, prec, &b))) return st;
+    apply_cbar_env(b);
     PairDev& P = b->pairs_h[0];
     double* own_cbar = P.cbar;
     P.mu = mu_d; P.nu = nu_d; P.cbar = cbar_d;

@@ -486,12 +486,15 @@ cbar_kernel(const PairDev* __restrict__ pairs, const CbarItem* __restrict__ item
 // (no staging of outputs, shifts instead of divisions).  Each thread keeps
 // the 49 costs of its block offset in registers across the staged rows.
 // --------------------------------------------------------------------------
-static size_t cbar4_smem(int n, int N) {
-    return sizeof(float) * ((size_t)2 * CBAR_S * 4 * N + (size_t)2 * (2 * n - 1) * CBAR_WPAD +
-                            (size_t)2 * CBAR_S * n);
+static size_t cbar4_smem(int n, int N, int cs = CBAR_S) {
+    return sizeof(float) * ((size_t)2 * cs * 4 * N + (size_t)2 * (2 * n - 1) * CBAR_WPAD + (size_t)2 * cs * n);
 }
 
-template <int MINB>
+// CS: block rows staged per chunk (the cost window of a thread's block
+// offset is reloaded once per chunk); FIRSTMUL: the first term of each
+// accumulator is a round-up product instead of a round-up FMA onto zero (the
+// same value: every term is non-negative), so no accumulator is cleared.
+template <int MINB, int CS = CBAR_S, bool FIRSTMUL = false>
 __global__ void __launch_bounds__(CBAR_THREADS, MINB)
 cbar4_kernel(const PairDev* __restrict__ pairs, const CbarItem* __restrict__ items, int n_items) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -504,10 +507,10 @@ cbar4_kernel(const PairDev* __restrict__ pairs, const CbarItem* __restrict__ ite
         const int w1 = I.w1;
         double* __restrict__ cbar = P.cbar;
         float* mu_s = reinterpret_cast<float*>(smem_raw);     // [S][KAP][N]
-        float* nu_s = mu_s + CBAR_S * KAP * N;                 // [S][KAP][N]
-        float* win_s = nu_s + CBAR_S * KAP * N;                // [2][2n-1][CBAR_WPAD]
+        float* nu_s = mu_s + CS * KAP * N;                 // [S][KAP][N]
+        float* win_s = nu_s + CS * KAP * N;                // [2][2n-1][CBAR_WPAD]
         float* rk_s = win_s + 2 * (2 * n - 1) * CBAR_WPAD;     // [S][n]
-        float* rl_s = rk_s + CBAR_S * n;                       // [S][n]
+        float* rl_s = rk_s + CS * n;                       // [S][n]
         const float* tab = reinterpret_cast<const float*>(P.ctab_hi);
         const float* mu_up = reinterpret_cast<const float*>(P.mu_up);
         const float* nu_up = reinterpret_cast<const float*>(P.nu_up);
@@ -525,8 +528,8 @@ cbar4_kernel(const PairDev* __restrict__ pairs, const CbarItem* __restrict__ ite
                     dst[d1 * WK + d2] = row < N ? trow[abs(D2 + d2 - (KAP - 1))] : 0.0f;
             }
         }
-        for (int k1_0 = 0; k1_0 < n; k1_0 += CBAR_S) {
-            const int S = min(CBAR_S, n - k1_0);
+        for (int k1_0 = 0; k1_0 < n; k1_0 += CS) {
+            const int S = min(CS, n - k1_0);
             __syncthreads();        // windows built / the previous chunk is consumed
             const int rowlen4 = N;  // KAP * N floats = N float4 per block row
             for (int s = 0; s < S; ++s) {
@@ -565,10 +568,12 @@ cbar4_kernel(const PairDev* __restrict__ pairs, const CbarItem* __restrict__ ite
                     // inner[a] = sum_b nu[b] c(a - b) (order b1, b2 per accumulator),
                     // then acc = sum_a mu[a] inner[a] (order a1, a2), all rounded up
                     float inner[KAP][KAP];
+                    if constexpr (!FIRSTMUL) {
 #pragma unroll
-                    for (int a1 = 0; a1 < KAP; ++a1)
+                        for (int a1 = 0; a1 < KAP; ++a1)
 #pragma unroll
-                        for (int a2 = 0; a2 < KAP; ++a2) inner[a1][a2] = 0.0f;
+                            for (int a2 = 0; a2 < KAP; ++a2) inner[a1][a2] = 0.0f;
+                    }
 #pragma unroll
                     for (int b1 = 0; b1 < KAP; ++b1) {
                         const float4 v4 = *reinterpret_cast<const float4*>(nu_s + (s * KAP + b1) * N + l2 * KAP);
@@ -578,9 +583,11 @@ cbar4_kernel(const PairDev* __restrict__ pairs, const CbarItem* __restrict__ ite
 #pragma unroll
                             for (int a1 = 0; a1 < KAP; ++a1)
 #pragma unroll
-                                for (int a2 = 0; a2 < KAP; ++a2)
-                                    inner[a1][a2] = fma_ru(nrow[b2], cw[(a1 - b1 + KAP - 1) * WK + a2 - b2 + KAP - 1],
-                                                           inner[a1][a2]);
+                                for (int a2 = 0; a2 < KAP; ++a2) {
+                                    const float c = cw[(a1 - b1 + KAP - 1) * WK + a2 - b2 + KAP - 1];
+                                    if (FIRSTMUL && b1 == 0 && b2 == 0) inner[a1][a2] = mul_ru(nrow[b2], c);
+                                    else inner[a1][a2] = fma_ru(nrow[b2], c, inner[a1][a2]);
+                                }
                     }
                     float acc = 0.0f;
 #pragma unroll
@@ -588,7 +595,10 @@ cbar4_kernel(const PairDev* __restrict__ pairs, const CbarItem* __restrict__ ite
                         const float4 v4 = *reinterpret_cast<const float4*>(mu_s + (s * KAP + a1) * N + k2 * KAP);
                         const float mrow[KAP] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
-                        for (int a2 = 0; a2 < KAP; ++a2) acc = fma_ru(mrow[a2], inner[a1][a2], acc);
+                        for (int a2 = 0; a2 < KAP; ++a2) {
+                            if (FIRSTMUL && a1 == 0 && a2 == 0) acc = mul_ru(mrow[a2], inner[a1][a2]);
+                            else acc = fma_ru(mrow[a2], inner[a1][a2], acc);
+                        }
                     }
                     int l1 = k1 - w1;
                     if (l1 < 0) l1 += n;
@@ -846,7 +856,9 @@ static int cbar_dispatch(const PairDev* pairs_d, const CbarItem* items, int n_it
     // variant 0: register budget for two CTAs per SM; 1: for three CTAs per SM;
     // 2, 3: the kappa = 4 FP32 kernel with row-direct writes (every coarse side
     // of the launch a power of two), three or two CTAs per SM; 4, 5: the
-    // kappa = 8 FP32 kernel (powers of two), two or one CTA per SM
+    // kappa = 8 FP32 kernel (powers of two), two or one CTA per SM; 6, 7, 8:
+    // the kappa = 4 kernel with first terms as products, 8 staged rows (6: three
+    // CTAs, 7: two CTAs per SM) or 4 (8: three CTAs)
     constexpr int MB = sizeof(T) == 4 ? 3 : 1;
     if constexpr (sizeof(T) == 4) {
         if (kappa_code == 8 && (variant == 4 || variant == 5)) {
@@ -858,10 +870,14 @@ static int cbar_dispatch(const PairDev* pairs_d, const CbarItem* items, int n_it
             QWB_LAUNCHED();
             return QWB_OK;
         }
-        if (kappa_code == 4 && (variant == 2 || variant == 3)) {
-            const size_t smem4 = cbar4_smem(n_max, N_max);
+        if (kappa_code == 4 && (variant == 2 || variant == 3 || (variant >= 6 && variant <= 8))) {
+            // 6, 7, 8: first terms as products; 8 rows per chunk for 6 and 7
+            const int cs = (variant == 6 || variant == 7) ? 8 : CBAR_S;
+            const size_t smem4 = cbar4_smem(n_max, N_max, cs);
             if (smem4 > 227 * 1024) return QWB_ERR_UNSUPPORTED;
-            auto kern = variant == 2 ? cbar4_kernel<3> : cbar4_kernel<2>;
+            auto kern = variant == 2 ? cbar4_kernel<3> : variant == 3 ? cbar4_kernel<2>
+                      : variant == 6 ? cbar4_kernel<3, 8, true> : variant == 7 ? cbar4_kernel<2, 8, true>
+                                     : cbar4_kernel<3, CBAR_S, true>;
             QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4));
             kern<<<n_items, CBAR_THREADS, smem4, stream>>>(pairs_d, items, n_items);
             QWB_LAUNCHED();

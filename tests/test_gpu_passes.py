@@ -155,6 +155,27 @@ def test_dual_pass(N, kappa, p, cls, prec):
         assert (f[:, None] + g[None, :] - O.ground_cost(X, X, p)).max() <= 1e-10
 
 
+@pytest.mark.parametrize("N,p", [(64, 2.0), (128, 1.0), (32, 2.0)])
+def test_coarse_cost_kappa4_variants(N, p, monkeypatch):
+    """Every compiled variant of the kappa = 4 FP32 C-bar kernel (forced with
+    QWB_CBAR_VARIANT) gives the same rounded-up coarse cost, bit for bit, at
+    or above the oracle's and within 2e-5 of it; a zero-mass block takes the
+    unweighted mean."""
+    kappa = 4
+    mu, nu = synth.make_measure(N, "gauss", 26, 0), synth.make_measure(N, "cauchy", 26, 1)
+    mu = mu.reshape(N, N).copy(); mu[4:8, 8:12] = 0.0; mu = (mu / mu.sum()).ravel()
+    ref = O.coarse_cost_weighted(mu, nu, N, kappa, p)
+    got = {}
+    for v in (2, 3, 6, 7, 8):
+        monkeypatch.setenv("QWB_CBAR_VARIANT", str(v))
+        cbar, _, _ = api.coarse_cost(T(mu), T(nu), N, kappa, p, prec="mixed")
+        got[v] = cbar.cpu().numpy()
+        assert np.all(got[v] >= ref * (1 - 1e-15)), v
+        np.testing.assert_allclose(got[v], ref, rtol=2e-5, atol=0)
+    for v in (3, 6, 7, 8):
+        np.testing.assert_array_equal(got[v], got[2])
+
+
 def test_invalid_inputs():
     from paper_2506_00976_gb300._lib import QwbError
     N = 8
