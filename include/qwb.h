@@ -260,7 +260,8 @@ int qwb_ctransform(qwb_ctx* ctx, int32_t N, double p, const double* h_d, double*
  *            (h - A rounded up) and each candidate is D - (h - A) rounded
  *            down, so the result is still a certified transform
  *            (h_i + out_j <= C_ij) but may lie below the once-rounded one by
- *            the rounding of h - A.
+ *            the rounding of h - A; 11, 12: 9 and 10 with the chunk's
+ *            squared column offsets pinned in registers.
  *   in_rows  input lines per work item (0 = the default split); work items
  *            that see part of the input lines combine by atomic min.
  * Compiled shapes: packing 0: (R, TC) in {1,2,4,8,16} x {same} and (16,8),
@@ -268,7 +269,8 @@ int qwb_ctransform(qwb_ctx* ctx, int32_t N, double p, const double* h_d, double*
  * (16,16); packing 3: (8,8); packing 4: (8,8), (8,16); packing 5: (8,16),
  * (16,8), (16,16); packing 6: (8,16); packing 7: (16,16), (16,8), (8,16);
  * packing 8: (16,16); packing 9: (16,16), (16,8), (8,16); packing 10:
- * (16,16), (32,16), (32,8).  Other shapes return QWB_ERR_UNSUPPORTED.
+ * (16,16), (32,16), (32,8); packing 11: (16,16), (16,8), (8,16); packing 12:
+ * (16,16), (32,8).  Other shapes return QWB_ERR_UNSUPPORTED.
  * h_d, out_d: N^d FP64 device.  Synchronises `stream` before returning.
  * Errors: INVALID_ARG, UNSUPPORTED, CUDA, OOM. */
 int qwb_ctransform_shape(qwb_ctx* ctx, int32_t N, int32_t d, double p, const double* h_d,
@@ -393,14 +395,18 @@ int qwb_batch_coarse_potentials(qwb_batch* batch, int32_t pair, double* f_h, dou
  * that many chunks ahead once its values are scaled, so copies stay in
  * flight while a chunk is stored (128 threads per CTA, two slots per
  * thread); C | QWB_IPF_ASYNC2 the same with 64 threads and four slots;
- * C | QWB_IPF_ASYNC3 with 256 threads and two slots.  Overrides the
- * autotuner's choice, which times every form;
+ * C | QWB_IPF_ASYNC3 with 256 threads and two slots.  C | QWB_IPF_PAIR2
+ * runs the register form with two pairs per cluster whose half sweeps
+ * interleave, so that each cluster barrier completes behind the other
+ * pair's half sweep.  Overrides the autotuner's choice, which times every
+ * form;
  * synchronises the device and drops the batch's captured fine-pass graphs.
  * Errors: INVALID_ARG, CUDA. */
 #define QWB_IPF_BULK 32
 #define QWB_IPF_ASYNC 64
 #define QWB_IPF_ASYNC2 128
 #define QWB_IPF_ASYNC3 256
+#define QWB_IPF_PAIR2 512
 int qwb_batch_set_ipf_cluster(qwb_batch* batch, int32_t C);
 /* Upscale the coarse plans of the batch's 2-D pairs with block side kappa by
  * the general kernel K_d (Sec. 3.4, eq. coupling tensor upscale; layout,

@@ -207,7 +207,7 @@ struct qwb_batch {
     // largest power of two <= ipf_C that divides all its coarse sides
     // (stream: the bulk-copy variant ipf_stream_kernel, for groups whose pairs
     // share N; n_same, N_same: that common coarse and fine side, else 0)
-    struct IpfGroup { int kappa, off, cnt, M_max, gcd_n, C, n_same, N_same; bool stream; int async_v; };
+    struct IpfGroup { int kappa, off, cnt, M_max, gcd_n, C, n_same, N_same; bool stream; int async_v; bool pair2; };
     std::vector<IpfGroup> ipf_groups;
     std::vector<int> ipf_group_of;      // per pair: its group or -1
     int* ipf_ids_d = nullptr;
@@ -352,6 +352,7 @@ static int launch_ipf_group(qwb_batch* b, const qwb_batch::IpfGroup& G, const in
         return launch_ipf_stream(b->pairs_d, ids, cnt, G.kappa, G.C, G.n_same, G.N_same, b->dev_err, b->wait_ns,
                                  b->fault_skip_chunk, s);
     if (G.async_v >= 0) return launch_ipf_async(b->pairs_d, ids, cnt, G.kappa, G.C, G.async_v, M, 0, s);
+    if (G.pair2) return launch_ipf_fine2(b->pairs_d, ids, cnt, G.kappa, G.C, M, s);
     return launch_ipf_fine(b->pairs_d, ids, cnt, G.kappa, G.C, M, 0, s);
 }
 
@@ -364,6 +365,7 @@ static int apply_ipf_choice(qwb_batch* b, int C) {
         G.C = c >= 2 ? c : 0;
         G.stream = (C & QWB_IPF_BULK) && G.C > 0 && G.n_same > 0 && G.N_same > 0;
         G.async_v = G.C > 0 ? ((C & QWB_IPF_ASYNC) ? 0 : (C & QWB_IPF_ASYNC2) ? 1 : (C & QWB_IPF_ASYNC3) ? 2 : -1) : -1;
+        G.pair2 = G.C > 0 && (C & QWB_IPF_PAIR2) != 0;
     }
     for (int t = 0; t < b->n; ++t) {
         const int g = b->ipf_group_of[t];
@@ -779,8 +781,10 @@ static int launch_ct_batched(qwb_batch* b, int phase, CtConfig cfg, int cap, cud
     if ((st = launch_ctransform(b->pairs_d, b->ct_b_items_d, b->n_ct_b_p2, phase, cfg, b->N_max, b->f64, cap, s)))
         return st;
     cfg.p2 = false;
-    if (cfg.packed == 9) cfg.packed = 5;          // the shifted kernels are p = 2 only: the same shape
-    else if (cfg.packed == 10) cfg.packed = 2;    // with the costs added per line pair
+    // the shifted kernels are p = 2 only: the other pairs take the line-paired
+    // kernel with per-line costs and the same budget (R capped at 16)
+    if (cfg.packed == 9 || cfg.packed == 11) cfg.packed = 5;
+    else if (cfg.packed == 10 || cfg.packed == 12) { cfg.packed = 2; cfg.R = std::min(cfg.R, 16); }
     return launch_ctransform(b->pairs_d, b->ct_b_items_d + b->n_ct_b_p2, b->n_ct_b - b->n_ct_b_p2, phase, cfg,
                              b->N_max, b->f64, cap, s);
 }
@@ -967,11 +971,13 @@ static int tune_ctransform(qwb_batch* b, cudaStream_t s) {
                            {8, 8, 2}, {16, 8, 2}, {8, 16, 2}, {16, 16, 2},
                            {8, 8, 3}, {8, 8, 4}, {8, 16, 4}, {8, 16, 5}, {16, 8, 5}, {16, 16, 5},
                            {8, 16, 6}, {16, 16, 7}, {16, 8, 7}, {8, 16, 7}, {16, 16, 8},
-                           {16, 16, 9}, {16, 8, 9}, {8, 16, 9}, {16, 16, 10}, {32, 16, 10}, {32, 8, 10}};
+                           {16, 16, 9}, {16, 8, 9}, {8, 16, 9}, {16, 16, 10}, {32, 16, 10}, {32, 8, 10},
+                           {16, 16, 11}, {16, 8, 11}, {8, 16, 11}, {16, 16, 12}, {32, 8, 12}};
     static const char* const kPackName[] = {"", "_packed", "_linepairs", "_linepairs_3cta_fly",
                                             "_linepairs_3cta", "_linepairs_2cta", "_linepairs_2cta_fly",
                                             "_linepairs_2cta_fused", "_linepairs_fused",
-                                            "_linepairs_shifted_2cta", "_linepairs_shifted"};
+                                            "_linepairs_shifted_2cta", "_linepairs_shifted",
+                                            "_linepairs_shifted_pinned_2cta", "_linepairs_shifted_pinned"};
     const int sm = b->ctx->sm_count > 0 ? b->ctx->sm_count : 148;
     std::ostringstream rep;
     double best = 1e30;
@@ -1016,14 +1022,16 @@ static int tune_ipf(qwb_batch* b, cudaStream_t s) {
     int bestC = 0;
     for (int C : {0, 2, 4, 8, 16, QWB_IPF_BULK | 2, QWB_IPF_BULK | 4, QWB_IPF_BULK | 8, QWB_IPF_BULK | 16,
                   QWB_IPF_ASYNC | 2, QWB_IPF_ASYNC | 4, QWB_IPF_ASYNC | 8, QWB_IPF_ASYNC2 | 2,
-                  QWB_IPF_ASYNC2 | 4, QWB_IPF_ASYNC3 | 2, QWB_IPF_ASYNC3 | 4}) {
+                  QWB_IPF_ASYNC2 | 4, QWB_IPF_ASYNC3 | 2, QWB_IPF_ASYNC3 | 4, QWB_IPF_PAIR2 | 2,
+                  QWB_IPF_PAIR2 | 4, QWB_IPF_PAIR2 | 8, QWB_IPF_PAIR2 | 16}) {
         int st = apply_ipf_choice(b, C);
         if (st) return st;
         if (C > 0) {
             const int av = (C & QWB_IPF_ASYNC) ? 0 : (C & QWB_IPF_ASYNC2) ? 1 : (C & QWB_IPF_ASYNC3) ? 2 : -1;
             bool any = false;
             for (const auto& G : b->ipf_groups)
-                any |= G.C == (C & 31) && G.stream == ((C & QWB_IPF_BULK) != 0) && G.async_v == av;
+                any |= G.C == (C & 31) && G.stream == ((C & QWB_IPF_BULK) != 0) && G.async_v == av &&
+                       G.pair2 == ((C & QWB_IPF_PAIR2) != 0);
             if (!any) continue;                  // no group takes this size / form
         }
         double ms;
@@ -1037,7 +1045,7 @@ static int tune_ipf(qwb_batch* b, cudaStream_t s) {
         if (st) return st;
         rep << (C ? ", " : "") << "\""
             << ((C & QWB_IPF_BULK) ? "bulk" : (C & QWB_IPF_ASYNC) ? "async128x2" : (C & QWB_IPF_ASYNC2) ? "async64x4"
-                : (C & QWB_IPF_ASYNC3) ? "async256x2" : "cluster")
+                : (C & QWB_IPF_ASYNC3) ? "async256x2" : (C & QWB_IPF_PAIR2) ? "pair2_cluster" : "cluster")
             << (C & 31) << "\": " << ms;
         if (ms < best) { best = ms; bestC = C; }
     }
@@ -1602,11 +1610,11 @@ int qwb_batch_set_ipf_cluster(qwb_batch* b, int32_t C) {
     const int Cs = C & 31, form = C & ~31;
     if (!b || (Cs != 0 && Cs != 2 && Cs != 4 && Cs != 8 && Cs != 16) ||
         (form != 0 && form != QWB_IPF_BULK && form != QWB_IPF_ASYNC && form != QWB_IPF_ASYNC2 &&
-         form != QWB_IPF_ASYNC3) ||
+         form != QWB_IPF_ASYNC3 && form != QWB_IPF_PAIR2) ||
         (form != 0 && Cs == 0))
         return fail(QWB_ERR_INVALID_ARG,
                     "qwb_batch_set_ipf_cluster: C must be 0, 2, 4, 8 or 16, the last four optionally with one of "
-                    "QWB_IPF_BULK, QWB_IPF_ASYNC, QWB_IPF_ASYNC2, QWB_IPF_ASYNC3");
+                    "QWB_IPF_BULK, QWB_IPF_ASYNC, QWB_IPF_ASYNC2, QWB_IPF_ASYNC3, QWB_IPF_PAIR2");
     QWB_CUDA(cudaSetDevice(b->ctx->device));
     QWB_CUDA(cudaDeviceSynchronize());
     // captured fine passes hold the previous launch configuration
@@ -2072,8 +2080,8 @@ int qwb_ctransform(qwb_ctx* ctx, int32_t N, double p, const double* h_d, double*
 int qwb_ctransform_shape(qwb_ctx* ctx, int32_t N, int32_t d, double p, const double* h_d,
                          double* out_d, int32_t R, int32_t TC, int32_t packing, int32_t in_rows,
                          qwb_prec prec, void* stream) {
-    if (R < 1 || TC < 1 || N < 1 || N % R || N % TC || packing < 0 || packing > 10 || in_rows < 0)
-        return fail(QWB_ERR_INVALID_ARG, "qwb_ctransform_shape: R and TC must divide N; packing in 0..10");
+    if (R < 1 || TC < 1 || N < 1 || N % R || N % TC || packing < 0 || packing > 12 || in_rows < 0)
+        return fail(QWB_ERR_INVALID_ARG, "qwb_ctransform_shape: R and TC must divide N; packing in 0..12");
     if (packing && prec == QWB_PREC_F64)
         return fail(QWB_ERR_INVALID_ARG, "qwb_ctransform_shape: packing needs MIXED precision");
     CtConfig c;

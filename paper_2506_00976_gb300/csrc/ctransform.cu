@@ -370,7 +370,16 @@ __device__ __forceinline__ unsigned long long mul_rn_x2(unsigned long long a, un
     return d;
 }
 
-template <int R, int TC, int MINB>
+// PIN: the chunk's squared column offsets pass through a volatile move when
+// they are formed, so that the compiler keeps them in registers across the
+// line-pair loop instead of forming them again inside it.
+__device__ __forceinline__ unsigned long long pin64(unsigned long long v) {
+    unsigned long long r;
+    asm volatile("mov.b64 %0, %1;" : "=l"(r) : "l"(v));
+    return r;
+}
+
+template <int R, int TC, int MINB, bool PIN = false>
 __global__ void __launch_bounds__(256, MINB)
 ctransform_rpd_kernel(const PairDev* __restrict__ pairs, const CtItem* __restrict__ items,
                       int n_items, int phase) {
@@ -406,7 +415,7 @@ ctransform_rpd_kernel(const PairDev* __restrict__ pairs, const CtItem* __restric
 #pragma unroll
                 for (int e = 0; e < NQ; ++e) {
                     const float d = (float)(c0 - j2 + e - (R - 1));
-                    DD[e] = pack2(d * d, d * d);
+                    DD[e] = PIN ? pin64(pack2(d * d, d * d)) : pack2(d * d, d * d);
                 }
                 const ulonglong2* hrow = reinterpret_cast<const ulonglong2*>(hs2 + c0);
                 unsigned long long tt = pack2(a0, a0 + 1.0f);         // (i1 - j1, i1 + 1 - j1)
@@ -438,10 +447,10 @@ ctransform_rpd_kernel(const PairDev* __restrict__ pairs, const CtItem* __restric
     }
 }
 
-template <int R, int TC, int MINB>
+template <int R, int TC, int MINB, bool PIN = false>
 static int ct_launch_rpd(const PairDev* pairs_d, const CtItem* items, int n_items, int phase,
                          int threads, int in_rows, int N_max, int grid_cap, cudaStream_t stream) {
-    auto kern = ctransform_rpd_kernel<R, TC, MINB>;
+    auto kern = ctransform_rpd_kernel<R, TC, MINB, PIN>;
     threads = std::min(threads, CT_TILE / R);
     const size_t smem = sizeof(float2) * (size_t)((in_rows + 1) / 2) * N_max;
     if (smem > 227 * 1024) return QWB_ERR_UNSUPPORTED;
@@ -563,14 +572,18 @@ static int ct_launch_t(const PairDev* pairs_d, const CtItem* items, int n_items,
 #undef QWB_CTRPF
         // packings 9, 10 (p = 2, 2-D only): the shifted line-paired kernel with
         // the register budget of 2 (9) or 1 (10) resident CTAs per SM
-        if ((c.packed == 9 || c.packed == 10) && (c.has_3d || !P2)) return QWB_ERR_UNSUPPORTED;
+        // packings 11, 12 (p = 2, 2-D only): 9 and 10 with the squared column
+        // offsets pinned in registers
+        if (c.packed >= 9 && c.packed <= 12 && (c.has_3d || !P2)) return QWB_ERR_UNSUPPORTED;
         if constexpr (P2) {
-#define QWB_CTRPD(PK, MB, RR, TT)                                                          \
+#define QWB_CTRPD(PK, MB, PIN, RR, TT)                                                     \
             if (c.R == RR && c.TC == TT && c.packed == PK)                                 \
-                return ct_launch_rpd<RR, TT, MB>(pairs_d, items, n_items, phase, c.threads, c.in_rows, \
-                                                 N_max, grid_cap, stream);
-            QWB_CTRPD(9, 2, 16, 16) QWB_CTRPD(9, 2, 16, 8) QWB_CTRPD(9, 2, 8, 16) QWB_CTRPD(10, 1, 16, 16)
-            QWB_CTRPD(10, 1, 32, 16) QWB_CTRPD(10, 1, 32, 8)
+                return ct_launch_rpd<RR, TT, MB, PIN>(pairs_d, items, n_items, phase, c.threads, c.in_rows, \
+                                                      N_max, grid_cap, stream);
+            QWB_CTRPD(9, 2, false, 16, 16) QWB_CTRPD(9, 2, false, 16, 8) QWB_CTRPD(9, 2, false, 8, 16)
+            QWB_CTRPD(10, 1, false, 16, 16) QWB_CTRPD(10, 1, false, 32, 16) QWB_CTRPD(10, 1, false, 32, 8)
+            QWB_CTRPD(11, 2, true, 16, 16) QWB_CTRPD(11, 2, true, 16, 8) QWB_CTRPD(11, 2, true, 8, 16)
+            QWB_CTRPD(12, 1, true, 16, 16) QWB_CTRPD(12, 1, true, 32, 8)
 #undef QWB_CTRPD
         }
     }

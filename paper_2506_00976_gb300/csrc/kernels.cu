@@ -1995,6 +1995,227 @@ ipf_fine_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair_
     }
 }
 
+// --------------------------------------------------------------------------
+// ipf_fine2: the sweeps of ipf_fine_kernel with two pairs per cluster, their
+// half sweeps interleaved so that each cluster barrier completes behind the
+// other pair's work.  The barrier sequence stays arrive, wait, arrive, wait:
+//   A(0) arrive | B(0) wait arrive | A(1) wait arrive | B(1) wait arrive | ...
+// where X(h) is pair X's half sweep h (block sums published, then the arrive).
+// A(h+1) needs every CTA's sums of A(h): the wait before the arrive after
+// B(h) completes A(h)'s phase, and A(h+1) only starts after it; likewise for
+// B.  A sums buffer is rewritten two halves of its own pair later, after the
+// barrier that follows its readers' half.  A cluster with one pair left runs
+// the same barrier sequence with an empty B.  Per pair and CTA the arithmetic
+// is that of ipf_fine_kernel.
+// --------------------------------------------------------------------------
+template <int KAP>
+struct IpfPairState {
+    const PairDev* P;
+    int N, n, Mc, k0;
+    float* Aown; float* Bown;
+    const float* v_s; const float* vc_s; const int* ci_s; const int* ri_s; const int* rp_s; const int* cp_s;
+    bool staged;
+};
+
+template <int KAP>
+__device__ __forceinline__ void ipf2_load(const IpfPairState<KAP>& S, const float* src, int kb, float4 (&x)[KAP == 4 ? 4 : 1][KAP][KAP / 4]) {
+    constexpr int Q = KAP / 4, PF = KAP == 4 ? 4 : 1;
+#pragma unroll
+    for (int q = 0; q < PF; ++q) {
+        const int kl = kb + q * IPF_THREADS;
+        if (kl < S.Mc) {
+            const int k = S.k0 + kl;
+            const int k1 = k / S.n, k2 = k - (k / S.n) * S.n;
+#pragma unroll
+            for (int t1 = 0; t1 < KAP; ++t1)
+#pragma unroll
+                for (int t2 = 0; t2 < Q; ++t2)
+                    x[q][t1][t2] = *reinterpret_cast<const float4*>(src + (size_t)(k1 * KAP + t1) * S.N + k2 * KAP + 4 * t2);
+        }
+    }
+}
+
+// one pair's half sweep h: every owned block's r from the other side's sums
+// (distributed shared memory), scaled values streamed out, own sums written.
+// x holds the prefetched first chunk on entry.
+template <int KAP>
+__device__ __forceinline__ void ipf2_half(cooperative_groups::cluster_group& cl, const IpfPairState<KAP>& S, int h,
+                                          float4 (&x)[KAP == 4 ? 4 : 1][KAP][KAP / 4]) {
+    constexpr int Q = KAP / 4, PF = KAP == 4 ? 4 : 1;
+    constexpr int KK = KAP * KAP;
+    const float kinvK = 1.0f / (float)(KK * KK);
+    const PairDev& P = *S.P;
+    const int half = h & 1;
+    const float* src = half == 0 ? reinterpret_cast<const float*>(P.mu_t) : reinterpret_cast<const float*>(P.nu_t);
+    float* dst = half == 0 ? reinterpret_cast<float*>(P.a) : reinterpret_cast<float*>(P.b);
+    float* mine = half == 0 ? S.Aown : S.Bown;
+    const float* other = half == 0 ? S.Bown : S.Aown;
+    const int chunk = PF * IPF_THREADS;
+    const float* vt = reinterpret_cast<const float*>(P.val_t);
+    const float* vct = reinterpret_cast<const float*>(P.valc_t);
+    for (int kb = threadIdx.x; kb < S.Mc; kb += chunk) {
+        if (kb != (int)threadIdx.x) ipf2_load<KAP>(S, src, kb, x);
+        float inv[PF];
+#pragma unroll
+        for (int q = 0; q < PF; ++q) {
+            const int kl = kb + q * IPF_THREADS;
+            inv[q] = 0.0f;
+            if (kl < S.Mc) {
+                float r = 0.0f;
+                const int* ptr = S.staged ? (half == 0 ? S.rp_s : S.cp_s) : (half == 0 ? P.rowptr : P.colptr);
+                const int* idx = S.staged ? (half == 0 ? S.ci_s : S.ri_s) : (half == 0 ? P.colidx : P.rowidx);
+                const float* val = S.staged ? (half == 0 ? S.v_s : S.vc_s) : (half == 0 ? vt : vct);
+                const int row = S.staged ? kl : S.k0 + kl;
+                for (int e = ptr[row]; e < ptr[row + 1]; ++e) {
+                    const int l = idx[e], owner = l / S.Mc;
+                    const float* peer = cl.map_shared_rank(other, owner);
+                    r += val[e] * peer[l - owner * S.Mc];
+                }
+                r *= kinvK;
+                inv[q] = r > 0.0f ? 1.0f / r : 0.0f;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < PF; ++q) {
+            const int kl = kb + q * IPF_THREADS;
+            if (kl < S.Mc) {
+                float sum = 0.0f;
+#pragma unroll
+                for (int t1 = 0; t1 < KAP; ++t1)
+#pragma unroll
+                    for (int t2 = 0; t2 < Q; ++t2) {
+                        float4& v = x[q][t1][t2];
+                        v.x *= inv[q]; v.y *= inv[q]; v.z *= inv[q]; v.w *= inv[q];
+                        sum += (v.x + v.y) + (v.z + v.w);
+                    }
+                mine[kl] = sum;
+                const int k = S.k0 + kl;
+                const int k1 = k / S.n, k2 = k - (k / S.n) * S.n;
+#pragma unroll
+                for (int t1 = 0; t1 < KAP; ++t1)
+#pragma unroll
+                    for (int t2 = 0; t2 < Q; ++t2)
+                        *reinterpret_cast<float4*>(dst + (size_t)(k1 * KAP + t1) * S.N + k2 * KAP + 4 * t2) = x[q][t1][t2];
+            }
+        }
+    }
+}
+
+template <int KAP>
+__global__ void __launch_bounds__(IPF_THREADS, 2)
+ipf_fine2_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair_ids, int n_pairs, int C,
+                 int csr_cap, int sums_cap) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int rank = (int)cl.block_rank();
+    const int cid = blockIdx.x / C;
+    const int nA = 2 * cid, nB = 2 * cid + 1;
+    __shared__ IpfPairState<KAP> S[2];                        // read by every thread, kept out of registers
+    // per pair: [Aown, Bown (sums_cap each) | v, vc (csr_cap, float) | ci, ri (csr_cap, int) | rp, cp (sums_cap + 1)]
+    const size_t per_pair = sizeof(float) * 2 * (size_t)sums_cap + 2 * (sizeof(float) + sizeof(int)) * (size_t)csr_cap +
+                            2 * sizeof(int) * (size_t)(sums_cap + 1);
+    bool have[2] = {nA < n_pairs, nB < n_pairs};
+    for (int w = 0; w < 2; ++w) {
+        if (!have[w]) continue;
+        const PairDev& P = pairs[pair_ids[w == 0 ? nA : nB]];
+        unsigned char* base = smem_raw + w * ((per_pair + 15) & ~(size_t)15);
+        const int Mc = P.M / C, k0 = rank * Mc;
+        float* Aown = reinterpret_cast<float*>(base);
+        float* Bown = Aown + sums_cap;
+        float* v_s = Bown + sums_cap;
+        float* vc_s = v_s + csr_cap;
+        int* ci_s = reinterpret_cast<int*>(vc_s + csr_cap);
+        int* ri_s = ci_s + csr_cap;
+        int* rp_s = ri_s + csr_cap;
+        int* cp_s = rp_s + sums_cap + 1;
+        const int r_base = P.rowptr[k0], c_base = P.colptr[k0];
+        const int r_cnt = P.rowptr[k0 + Mc] - r_base, c_cnt = P.colptr[k0 + Mc] - c_base;
+        const bool staged = r_cnt <= csr_cap && c_cnt <= csr_cap;
+        const float* vt = reinterpret_cast<const float*>(P.val_t);
+        const float* vct = reinterpret_cast<const float*>(P.valc_t);
+        if (staged) {
+            for (int k = threadIdx.x; k <= Mc; k += IPF_THREADS) {
+                rp_s[k] = P.rowptr[k0 + k] - r_base;
+                cp_s[k] = P.colptr[k0 + k] - c_base;
+            }
+            for (int e = threadIdx.x; e < r_cnt; e += IPF_THREADS) { ci_s[e] = P.colidx[r_base + e]; v_s[e] = vt[r_base + e]; }
+            for (int e = threadIdx.x; e < c_cnt; e += IPF_THREADS) { ri_s[e] = P.rowidx[c_base + e]; vc_s[e] = vct[c_base + e]; }
+        }
+        for (int k = threadIdx.x; k < Mc; k += IPF_THREADS) Bown[k] = (float)(KAP * KAP);   // b = 1
+        if (threadIdx.x == 0) {
+            IpfPairState<KAP>& X = S[w];
+            X.P = &P; X.N = P.N; X.n = P.n; X.Mc = Mc; X.k0 = k0;
+            X.Aown = Aown; X.Bown = Bown;
+            X.v_s = v_s; X.vc_s = vc_s; X.ci_s = ci_s; X.ri_s = ri_s; X.rp_s = rp_s; X.cp_s = cp_s;
+            X.staged = staged;
+        }
+    }
+    __syncthreads();                                          // the pair states are visible
+    const int halves = have[0] ? 2 * S[0].P->sweeps : 0;     // both pairs of a group run the same sweeps
+    float4 x[KAP == 4 ? 4 : 1][KAP][KAP / 4];
+    if (halves > 0) ipf2_load<KAP>(S[0], reinterpret_cast<const float*>(S[0].P->mu_t), threadIdx.x, x);
+    cl.sync();                                                // staging and b = 1 visible
+    if (halves == 0) return;
+    ipf2_half<KAP>(cl, S[0], 0, x);
+    cluster_arrive_release();                                 // A(0) published
+    for (int h = 0; h < halves; ++h) {
+        if (have[1]) {
+            const float* srcB = (h & 1) == 0 ? reinterpret_cast<const float*>(S[1].P->mu_t)
+                                             : reinterpret_cast<const float*>(S[1].P->nu_t);
+            ipf2_load<KAP>(S[1], srcB, threadIdx.x, x);
+            ipf2_half<KAP>(cl, S[1], h, x);
+        }
+        cluster_wait_acquire();                               // A(h) complete
+        cluster_arrive_release();                             // B(h) published
+        if (h + 1 < halves) {
+            const float* srcA = ((h + 1) & 1) == 0 ? reinterpret_cast<const float*>(S[0].P->mu_t)
+                                                   : reinterpret_cast<const float*>(S[0].P->nu_t);
+            ipf2_load<KAP>(S[0], srcA, threadIdx.x, x);
+            ipf2_half<KAP>(cl, S[0], h + 1, x);
+            cluster_wait_acquire();                           // B(h) complete
+            cluster_arrive_release();                         // A(h + 1) published
+        } else {
+            cluster_wait_acquire();                           // B(last) complete
+        }
+    }
+}
+
+int launch_ipf_fine2(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int kappa, int C,
+                     int M_max, cudaStream_t stream) {
+    if (n_pairs <= 0) return QWB_OK;
+    if (C < 1 || C > 16 || (kappa != 4 && kappa != 8)) return QWB_ERR_UNSUPPORTED;
+    const int Mc = M_max / C;
+    int csr_cap = 2 * Mc + 64;
+    auto smem_of = [&](int cap) {
+        const size_t per_pair = sizeof(float) * 2 * (size_t)Mc + 2 * (sizeof(float) + sizeof(int)) * (size_t)cap +
+                                2 * sizeof(int) * (size_t)(Mc + 1);
+        return 2 * ((per_pair + 15) & ~(size_t)15);
+    };
+    size_t smem = smem_of(csr_cap);
+    if (smem > 110 * 1024) { csr_cap = 0; smem = smem_of(0); }
+    if (smem > 227 * 1024) return QWB_ERR_UNSUPPORTED;
+    auto kern = kappa == 4 ? ipf_fine2_kernel<4> : ipf_fine2_kernel<8>;
+    QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (C > 8) QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    const int clusters = (n_pairs + 1) / 2;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(clusters * C));
+    cfg.blockDim = dim3(IPF_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    QWB_CUDA(cudaLaunchKernelEx(&cfg, kern, pairs_d, pair_ids, n_pairs, C, csr_cap, Mc));
+    QWB_LAUNCHED();
+    return QWB_OK;
+}
+
 int launch_ipf_fine(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int kappa, int C,
                     int M_max, int nnz_max, cudaStream_t stream) {
     if (n_pairs <= 0) return QWB_OK;

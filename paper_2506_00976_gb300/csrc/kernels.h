@@ -115,6 +115,11 @@ int launch_ipf_stream(const PairDev* pairs_d, const int* pair_ids, int n_pairs, 
 // thread, 1 = 64 threads and four slots, 2 = 256 threads and two slots.
 int launch_ipf_async(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int kappa, int C, int variant,
                      int M_max, int nnz_max, cudaStream_t stream);
+// The register-streaming sweeps with two pairs per cluster whose half sweeps
+// interleave, so that each cluster barrier completes behind the other pair's
+// work (ipf_fine2_kernel); n_pairs pairs in (n_pairs + 1) / 2 clusters.
+int launch_ipf_fine2(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int kappa, int C,
+                     int M_max, cudaStream_t stream);
 // primal pass with a general upscaling kernel (P.upK set; d = 2, kappa <= kappa_max <= 8;
 // all_kappa4: every pair of the launch has kappa 4, which selects the register-row kernel)
 int launch_primalk(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs, int kappa_max,

@@ -311,10 +311,12 @@ def test_fine_ipf_scalings_bulk(sweeps, batched, cluster):
 @pytest.mark.parametrize("sweeps", [1, 7])
 @pytest.mark.parametrize("batched", [True, False])
 @pytest.mark.parametrize("cluster", [2, 4, 8])
-@pytest.mark.parametrize("form", ["ASYNC", "ASYNC2", "ASYNC3"])
+@pytest.mark.parametrize("form", ["ASYNC", "ASYNC2", "ASYNC3", "PAIR2"])
 def test_fine_ipf_scalings_async(sweeps, batched, cluster, form):
     """The sweeps with per-thread asynchronous copies into private slots
-    (cluster | QWB_IPF_ASYNC, _ASYNC2, _ASYNC3): several chunks per half sweep
+    (cluster | QWB_IPF_ASYNC, _ASYNC2, _ASYNC3) and the register form with two
+    pairs per cluster (QWB_IPF_PAIR2: 3 pairs at kappa 4, so one cluster has a
+    single pair): several chunks per half sweep
     and copies issued across half-sweep boundaries (256^2 at kappa 8, 128^2 at
     kappa 4, a 64^2 pair whose blocks do not fill a chunk, a zero-mass block).
     The scalings reach the uniform kernel's fixed point and equal the

@@ -209,7 +209,7 @@ def test_ctransform_every_shape_p2(R, TC, packing, N, in_rows):
     np.testing.assert_array_equal(g, rd32(O.c_transform(h, N, 2.0)))
 
 
-@pytest.mark.parametrize("R,TC,packing", SHAPES + [(16, 16, 9), (32, 16, 10)])
+@pytest.mark.parametrize("R,TC,packing", SHAPES + [(16, 16, 9), (32, 16, 10), (16, 8, 11), (32, 8, 12)])
 @pytest.mark.parametrize("N,in_rows", [(32, 5), (32, 3), (64, 7)])
 def test_ctransform_integer_potentials_split(R, TC, packing, N, in_rows):
     """Integer potentials make many candidates exact zeros, which the
@@ -227,7 +227,8 @@ def test_ctransform_integer_potentials_split(R, TC, packing, N, in_rows):
 
 
 @pytest.mark.parametrize("R,TC,packing", [(16, 16, 9), (16, 8, 9), (8, 16, 9), (16, 16, 10), (32, 16, 10),
-                                           (32, 8, 10)])
+                                           (32, 8, 10), (16, 16, 11), (16, 8, 11), (8, 16, 11), (16, 16, 12),
+                                           (32, 8, 12)])
 @pytest.mark.parametrize("N,in_rows", [(32, 0), (32, 5), (64, 7), (64, 1), (128, 0)])
 def test_ctransform_shifted_p2(R, TC, packing, N, in_rows):
     """The shifted line-paired kernels (p = 2): every candidate is
