@@ -389,24 +389,14 @@ int qwb_batch_coarse_potentials(qwb_batch* batch, int32_t pair, double* f_h, dou
  * source values by bulk copies (cp.async.bulk into a ring of shared-memory
  * stages, completion on mbarriers, every wait bounded) for groups whose pairs
  * share N; a timed-out wait makes qwb_batch_results return TIMEOUT.
- * C | QWB_IPF_ASYNC selects the form in which every thread brings its own
- * blocks' source values in by 16-byte asynchronous copies (cp.async) into a
- * ring of private shared-memory slots, re-filling a slot with the chunk
- * that many chunks ahead once its values are scaled, so copies stay in
- * flight while a chunk is stored (128 threads per CTA, two slots per
- * thread); C | QWB_IPF_ASYNC2 the same with 64 threads and four slots;
- * C | QWB_IPF_ASYNC3 with 256 threads and two slots.  C | QWB_IPF_PAIR2
- * runs the register form with two pairs per cluster whose half sweeps
- * interleave, so that each cluster barrier completes behind the other
- * pair's half sweep.  Overrides the autotuner's choice, which times every
- * form;
+ * C | QWB_IPF_HINTS runs the register form with cache-policy hints: the
+ * source values read through the read-only path with a 256-byte L2 prefetch
+ * per request, the scaled values stored with the evict-first policy.
+ * Overrides the autotuner's choice, which times every form;
  * synchronises the device and drops the batch's captured fine-pass graphs.
  * Errors: INVALID_ARG, CUDA. */
 #define QWB_IPF_BULK 32
-#define QWB_IPF_ASYNC 64
-#define QWB_IPF_ASYNC2 128
-#define QWB_IPF_ASYNC3 256
-#define QWB_IPF_PAIR2 512
+#define QWB_IPF_HINTS 64
 int qwb_batch_set_ipf_cluster(qwb_batch* batch, int32_t C);
 /* Upscale the coarse plans of the batch's 2-D pairs with block side kappa by
  * the general kernel K_d (Sec. 3.4, eq. coupling tensor upscale; layout,

@@ -57,10 +57,7 @@ def _ptr(t):
 
 
 QWB_IPF_BULK = 32   # Batch.set_ipf_cluster(C | QWB_IPF_BULK): the bulk-copy staged sweeps
-QWB_IPF_ASYNC = 64    # ... | QWB_IPF_ASYNC: per-thread asynchronous copies, 128 threads x 2 slots
-QWB_IPF_ASYNC2 = 128  # ... | QWB_IPF_ASYNC2: 64 threads x 4 slots
-QWB_IPF_ASYNC3 = 256  # ... | QWB_IPF_ASYNC3: 256 threads x 2 slots
-QWB_IPF_PAIR2 = 512   # ... | QWB_IPF_PAIR2: register form, two pairs per cluster, interleaved half sweeps
+QWB_IPF_HINTS = 64    # ... | QWB_IPF_HINTS: register form with read-only / L2-prefetch loads, streaming stores
 
 
 def problem(N, kappa, p, d=2):

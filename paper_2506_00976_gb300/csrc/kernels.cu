@@ -1866,7 +1866,21 @@ __device__ __forceinline__ void cluster_wait_acquire() {
     asm volatile("barrier.cluster.wait.acquire;\n" ::: "memory");
 }
 
-template <int KAP>
+// HINTS: the source values are read through the read-only path with a 256-byte
+// L2 prefetch per request and the scaled values are stored with the streaming
+// (evict-first) policy, since this kernel never reads them back.
+__device__ __forceinline__ float4 ld_nc_l2pf(const float* p) {
+    float4 v;
+    asm("ld.global.nc.L2::256B.v4.f32 {%0, %1, %2, %3}, [%4];"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ void st_cs(float* p, const float4 v) {
+    asm volatile("st.global.cs.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
+template <int KAP, bool HINTS = false>
 __global__ void __launch_bounds__(IPF_THREADS)
 ipf_fine_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair_ids, int C,
                 int csr_cap) {
@@ -1919,9 +1933,10 @@ ipf_fine_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair_
 #pragma unroll
                 for (int t1 = 0; t1 < KAP; ++t1)
 #pragma unroll
-                    for (int t2 = 0; t2 < Q; ++t2)
-                        x[q][t1][t2] = *reinterpret_cast<const float4*>(src + (size_t)(k1 * KAP + t1) * N +
-                                                                         k2 * KAP + 4 * t2);
+                    for (int t2 = 0; t2 < Q; ++t2) {
+                        const float* ps = src + (size_t)(k1 * KAP + t1) * N + k2 * KAP + 4 * t2;
+                        x[q][t1][t2] = HINTS ? ld_nc_l2pf(ps) : *reinterpret_cast<const float4*>(ps);
+                    }
             }
         }
     };
@@ -1983,9 +1998,11 @@ ipf_fine_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair_
 #pragma unroll
                     for (int t1 = 0; t1 < KAP; ++t1)
 #pragma unroll
-                        for (int t2 = 0; t2 < Q; ++t2)
-                            *reinterpret_cast<float4*>(dst + (size_t)(k1 * KAP + t1) * N + k2 * KAP + 4 * t2) =
-                                x[q][t1][t2];
+                        for (int t2 = 0; t2 < Q; ++t2) {
+                            float* pd = dst + (size_t)(k1 * KAP + t1) * N + k2 * KAP + 4 * t2;
+                            if (HINTS) st_cs(pd, x[q][t1][t2]);
+                            else *reinterpret_cast<float4*>(pd) = x[q][t1][t2];
+                        }
                 }
             }
         }
@@ -1995,229 +2012,8 @@ ipf_fine_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair_
     }
 }
 
-// --------------------------------------------------------------------------
-// ipf_fine2: the sweeps of ipf_fine_kernel with two pairs per cluster, their
-// half sweeps interleaved so that each cluster barrier completes behind the
-// other pair's work.  The barrier sequence stays arrive, wait, arrive, wait:
-//   A(0) arrive | B(0) wait arrive | A(1) wait arrive | B(1) wait arrive | ...
-// where X(h) is pair X's half sweep h (block sums published, then the arrive).
-// A(h+1) needs every CTA's sums of A(h): the wait before the arrive after
-// B(h) completes A(h)'s phase, and A(h+1) only starts after it; likewise for
-// B.  A sums buffer is rewritten two halves of its own pair later, after the
-// barrier that follows its readers' half.  A cluster with one pair left runs
-// the same barrier sequence with an empty B.  Per pair and CTA the arithmetic
-// is that of ipf_fine_kernel.
-// --------------------------------------------------------------------------
-template <int KAP>
-struct IpfPairState {
-    const PairDev* P;
-    int N, n, Mc, k0;
-    float* Aown; float* Bown;
-    const float* v_s; const float* vc_s; const int* ci_s; const int* ri_s; const int* rp_s; const int* cp_s;
-    bool staged;
-};
-
-template <int KAP>
-__device__ __forceinline__ void ipf2_load(const IpfPairState<KAP>& S, const float* src, int kb, float4 (&x)[KAP == 4 ? 4 : 1][KAP][KAP / 4]) {
-    constexpr int Q = KAP / 4, PF = KAP == 4 ? 4 : 1;
-#pragma unroll
-    for (int q = 0; q < PF; ++q) {
-        const int kl = kb + q * IPF_THREADS;
-        if (kl < S.Mc) {
-            const int k = S.k0 + kl;
-            const int k1 = k / S.n, k2 = k - (k / S.n) * S.n;
-#pragma unroll
-            for (int t1 = 0; t1 < KAP; ++t1)
-#pragma unroll
-                for (int t2 = 0; t2 < Q; ++t2)
-                    x[q][t1][t2] = *reinterpret_cast<const float4*>(src + (size_t)(k1 * KAP + t1) * S.N + k2 * KAP + 4 * t2);
-        }
-    }
-}
-
-// one pair's half sweep h: every owned block's r from the other side's sums
-// (distributed shared memory), scaled values streamed out, own sums written.
-// x holds the prefetched first chunk on entry.
-template <int KAP>
-__device__ __forceinline__ void ipf2_half(cooperative_groups::cluster_group& cl, const IpfPairState<KAP>& S, int h,
-                                          float4 (&x)[KAP == 4 ? 4 : 1][KAP][KAP / 4]) {
-    constexpr int Q = KAP / 4, PF = KAP == 4 ? 4 : 1;
-    constexpr int KK = KAP * KAP;
-    const float kinvK = 1.0f / (float)(KK * KK);
-    const PairDev& P = *S.P;
-    const int half = h & 1;
-    const float* src = half == 0 ? reinterpret_cast<const float*>(P.mu_t) : reinterpret_cast<const float*>(P.nu_t);
-    float* dst = half == 0 ? reinterpret_cast<float*>(P.a) : reinterpret_cast<float*>(P.b);
-    float* mine = half == 0 ? S.Aown : S.Bown;
-    const float* other = half == 0 ? S.Bown : S.Aown;
-    const int chunk = PF * IPF_THREADS;
-    const float* vt = reinterpret_cast<const float*>(P.val_t);
-    const float* vct = reinterpret_cast<const float*>(P.valc_t);
-    for (int kb = threadIdx.x; kb < S.Mc; kb += chunk) {
-        if (kb != (int)threadIdx.x) ipf2_load<KAP>(S, src, kb, x);
-        float inv[PF];
-#pragma unroll
-        for (int q = 0; q < PF; ++q) {
-            const int kl = kb + q * IPF_THREADS;
-            inv[q] = 0.0f;
-            if (kl < S.Mc) {
-                float r = 0.0f;
-                const int* ptr = S.staged ? (half == 0 ? S.rp_s : S.cp_s) : (half == 0 ? P.rowptr : P.colptr);
-                const int* idx = S.staged ? (half == 0 ? S.ci_s : S.ri_s) : (half == 0 ? P.colidx : P.rowidx);
-                const float* val = S.staged ? (half == 0 ? S.v_s : S.vc_s) : (half == 0 ? vt : vct);
-                const int row = S.staged ? kl : S.k0 + kl;
-                for (int e = ptr[row]; e < ptr[row + 1]; ++e) {
-                    const int l = idx[e], owner = l / S.Mc;
-                    const float* peer = cl.map_shared_rank(other, owner);
-                    r += val[e] * peer[l - owner * S.Mc];
-                }
-                r *= kinvK;
-                inv[q] = r > 0.0f ? 1.0f / r : 0.0f;
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < PF; ++q) {
-            const int kl = kb + q * IPF_THREADS;
-            if (kl < S.Mc) {
-                float sum = 0.0f;
-#pragma unroll
-                for (int t1 = 0; t1 < KAP; ++t1)
-#pragma unroll
-                    for (int t2 = 0; t2 < Q; ++t2) {
-                        float4& v = x[q][t1][t2];
-                        v.x *= inv[q]; v.y *= inv[q]; v.z *= inv[q]; v.w *= inv[q];
-                        sum += (v.x + v.y) + (v.z + v.w);
-                    }
-                mine[kl] = sum;
-                const int k = S.k0 + kl;
-                const int k1 = k / S.n, k2 = k - (k / S.n) * S.n;
-#pragma unroll
-                for (int t1 = 0; t1 < KAP; ++t1)
-#pragma unroll
-                    for (int t2 = 0; t2 < Q; ++t2)
-                        *reinterpret_cast<float4*>(dst + (size_t)(k1 * KAP + t1) * S.N + k2 * KAP + 4 * t2) = x[q][t1][t2];
-            }
-        }
-    }
-}
-
-template <int KAP>
-__global__ void __launch_bounds__(IPF_THREADS, 2)
-ipf_fine2_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair_ids, int n_pairs, int C,
-                 int csr_cap, int sums_cap) {
-    namespace cg = cooperative_groups;
-    cg::cluster_group cl = cg::this_cluster();
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int rank = (int)cl.block_rank();
-    const int cid = blockIdx.x / C;
-    const int nA = 2 * cid, nB = 2 * cid + 1;
-    __shared__ IpfPairState<KAP> S[2];                        // read by every thread, kept out of registers
-    // per pair: [Aown, Bown (sums_cap each) | v, vc (csr_cap, float) | ci, ri (csr_cap, int) | rp, cp (sums_cap + 1)]
-    const size_t per_pair = sizeof(float) * 2 * (size_t)sums_cap + 2 * (sizeof(float) + sizeof(int)) * (size_t)csr_cap +
-                            2 * sizeof(int) * (size_t)(sums_cap + 1);
-    bool have[2] = {nA < n_pairs, nB < n_pairs};
-    for (int w = 0; w < 2; ++w) {
-        if (!have[w]) continue;
-        const PairDev& P = pairs[pair_ids[w == 0 ? nA : nB]];
-        unsigned char* base = smem_raw + w * ((per_pair + 15) & ~(size_t)15);
-        const int Mc = P.M / C, k0 = rank * Mc;
-        float* Aown = reinterpret_cast<float*>(base);
-        float* Bown = Aown + sums_cap;
-        float* v_s = Bown + sums_cap;
-        float* vc_s = v_s + csr_cap;
-        int* ci_s = reinterpret_cast<int*>(vc_s + csr_cap);
-        int* ri_s = ci_s + csr_cap;
-        int* rp_s = ri_s + csr_cap;
-        int* cp_s = rp_s + sums_cap + 1;
-        const int r_base = P.rowptr[k0], c_base = P.colptr[k0];
-        const int r_cnt = P.rowptr[k0 + Mc] - r_base, c_cnt = P.colptr[k0 + Mc] - c_base;
-        const bool staged = r_cnt <= csr_cap && c_cnt <= csr_cap;
-        const float* vt = reinterpret_cast<const float*>(P.val_t);
-        const float* vct = reinterpret_cast<const float*>(P.valc_t);
-        if (staged) {
-            for (int k = threadIdx.x; k <= Mc; k += IPF_THREADS) {
-                rp_s[k] = P.rowptr[k0 + k] - r_base;
-                cp_s[k] = P.colptr[k0 + k] - c_base;
-            }
-            for (int e = threadIdx.x; e < r_cnt; e += IPF_THREADS) { ci_s[e] = P.colidx[r_base + e]; v_s[e] = vt[r_base + e]; }
-            for (int e = threadIdx.x; e < c_cnt; e += IPF_THREADS) { ri_s[e] = P.rowidx[c_base + e]; vc_s[e] = vct[c_base + e]; }
-        }
-        for (int k = threadIdx.x; k < Mc; k += IPF_THREADS) Bown[k] = (float)(KAP * KAP);   // b = 1
-        if (threadIdx.x == 0) {
-            IpfPairState<KAP>& X = S[w];
-            X.P = &P; X.N = P.N; X.n = P.n; X.Mc = Mc; X.k0 = k0;
-            X.Aown = Aown; X.Bown = Bown;
-            X.v_s = v_s; X.vc_s = vc_s; X.ci_s = ci_s; X.ri_s = ri_s; X.rp_s = rp_s; X.cp_s = cp_s;
-            X.staged = staged;
-        }
-    }
-    __syncthreads();                                          // the pair states are visible
-    const int halves = have[0] ? 2 * S[0].P->sweeps : 0;     // both pairs of a group run the same sweeps
-    float4 x[KAP == 4 ? 4 : 1][KAP][KAP / 4];
-    if (halves > 0) ipf2_load<KAP>(S[0], reinterpret_cast<const float*>(S[0].P->mu_t), threadIdx.x, x);
-    cl.sync();                                                // staging and b = 1 visible
-    if (halves == 0) return;
-    ipf2_half<KAP>(cl, S[0], 0, x);
-    cluster_arrive_release();                                 // A(0) published
-    for (int h = 0; h < halves; ++h) {
-        if (have[1]) {
-            const float* srcB = (h & 1) == 0 ? reinterpret_cast<const float*>(S[1].P->mu_t)
-                                             : reinterpret_cast<const float*>(S[1].P->nu_t);
-            ipf2_load<KAP>(S[1], srcB, threadIdx.x, x);
-            ipf2_half<KAP>(cl, S[1], h, x);
-        }
-        cluster_wait_acquire();                               // A(h) complete
-        cluster_arrive_release();                             // B(h) published
-        if (h + 1 < halves) {
-            const float* srcA = ((h + 1) & 1) == 0 ? reinterpret_cast<const float*>(S[0].P->mu_t)
-                                                   : reinterpret_cast<const float*>(S[0].P->nu_t);
-            ipf2_load<KAP>(S[0], srcA, threadIdx.x, x);
-            ipf2_half<KAP>(cl, S[0], h + 1, x);
-            cluster_wait_acquire();                           // B(h) complete
-            cluster_arrive_release();                         // A(h + 1) published
-        } else {
-            cluster_wait_acquire();                           // B(last) complete
-        }
-    }
-}
-
-int launch_ipf_fine2(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int kappa, int C,
-                     int M_max, cudaStream_t stream) {
-    if (n_pairs <= 0) return QWB_OK;
-    if (C < 1 || C > 16 || (kappa != 4 && kappa != 8)) return QWB_ERR_UNSUPPORTED;
-    const int Mc = M_max / C;
-    int csr_cap = 2 * Mc + 64;
-    auto smem_of = [&](int cap) {
-        const size_t per_pair = sizeof(float) * 2 * (size_t)Mc + 2 * (sizeof(float) + sizeof(int)) * (size_t)cap +
-                                2 * sizeof(int) * (size_t)(Mc + 1);
-        return 2 * ((per_pair + 15) & ~(size_t)15);
-    };
-    size_t smem = smem_of(csr_cap);
-    if (smem > 110 * 1024) { csr_cap = 0; smem = smem_of(0); }
-    if (smem > 227 * 1024) return QWB_ERR_UNSUPPORTED;
-    auto kern = kappa == 4 ? ipf_fine2_kernel<4> : ipf_fine2_kernel<8>;
-    QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    if (C > 8) QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    const int clusters = (n_pairs + 1) / 2;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(clusters * C));
-    cfg.blockDim = dim3(IPF_THREADS);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)C;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    QWB_CUDA(cudaLaunchKernelEx(&cfg, kern, pairs_d, pair_ids, n_pairs, C, csr_cap, Mc));
-    QWB_LAUNCHED();
-    return QWB_OK;
-}
-
 int launch_ipf_fine(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int kappa, int C,
-                    int M_max, int nnz_max, cudaStream_t stream) {
+                    int M_max, int nnz_max, bool hints, cudaStream_t stream) {
     if (n_pairs <= 0) return QWB_OK;
     if (C < 1 || C > 16 || (kappa != 4 && kappa != 8)) return QWB_ERR_UNSUPPORTED;
     const int Mc = M_max / C;
@@ -2231,7 +2027,8 @@ int launch_ipf_fine(const PairDev* pairs_d, const int* pair_ids, int n_pairs, in
         smem = sizeof(float) * 2 * (size_t)Mc + 2 * sizeof(int) * (size_t)(Mc + 1);
         csr_cap = 0;
     }
-    auto kern = kappa == 4 ? ipf_fine_kernel<4> : ipf_fine_kernel<8>;
+    auto kern = kappa == 4 ? (hints ? ipf_fine_kernel<4, true> : ipf_fine_kernel<4, false>)
+                           : (hints ? ipf_fine_kernel<8, true> : ipf_fine_kernel<8, false>);
     QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (C > 8) QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     cudaLaunchConfig_t cfg = {};
@@ -2249,257 +2046,6 @@ int launch_ipf_fine(const PairDev* pairs_d, const int* pair_ids, int n_pairs, in
     QWB_CUDA(cudaLaunchKernelEx(&cfg, kern, pairs_d, pair_ids, C, csr_cap));
     QWB_LAUNCHED();
     return QWB_OK;
-}
-
-// --------------------------------------------------------------------------
-// ipf_async: the same fine FP32 IPF sweeps as ipf_fine_kernel (same cluster
-// ownership of the coarse blocks, plan rows / columns staged in shared memory,
-// block sums through distributed shared memory, one cluster barrier per half
-// sweep), with the source values brought in by per-thread asynchronous
-// copies (cp.async, 16 bytes each) into a ring of SLOTS private shared-memory
-// slots per thread.  A thread reads only the slot it filled itself, so a
-// chunk needs no block barrier: the thread waits for its own oldest copy
-// group, reads the chunk into registers, scales it, and re-fills that slot
-// with the chunk SLOTS ahead -- which may belong to the next half sweep, since
-// the sources mu, nu do not depend on the sweeps -- before it stores the
-// scaled values.  So the loads of the next chunks stay in flight while a
-// chunk is scaled and stored and while the cluster barrier is crossed.  The
-// slot is re-filled only after the values read from it have been consumed by
-// the scaling, so the copy cannot overtake the read.  Per thread and chunk:
-// PF blocks of kappa x kappa pixels, 16 float4 (PF = 4 for kappa = 4, 1 for
-// kappa = 8); float4 j of thread t sits at position j ^ (t & 7) of its slot,
-// so that the eight threads of a quarter warp read distinct banks.
-// --------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_addr_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr_u32(smem_dst)), "l"(gsrc)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int NPEND>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory"); }
-
-constexpr int IPFA_SLOT_F4 = 16;   // float4 per thread and chunk
-
-template <int KAP, int THR, int SLOTS>
-__global__ void __launch_bounds__(THR)
-ipf_async_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair_ids, int C, int csr_cap) {
-    namespace cg = cooperative_groups;
-    cg::cluster_group cl = cg::this_cluster();
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int rank = (int)cl.block_rank();
-    const PairDev& P = pairs[pair_ids[blockIdx.x / C]];
-    const int N = P.N, n = P.n, M = P.M;
-    const int Mc = M / C, k0 = rank * Mc;                    // owned blocks [k0, k0 + Mc)
-    // [ring | block sums | staged plan: values (float), block indices and
-    // row / column offsets (16 bits: M <= 4096 and offsets <= csr_cap < 2^16)]
-    float4* ring = reinterpret_cast<float4*>(smem_raw);      // [SLOTS][THR][IPFA_SLOT_F4]
-    float* Aown = reinterpret_cast<float*>(ring + (size_t)SLOTS * THR * IPFA_SLOT_F4);
-    float* Bown = Aown + Mc;
-    float* v_s = Bown + Mc;
-    float* vc_s = v_s + csr_cap;
-    uint16_t* ci_s = reinterpret_cast<uint16_t*>(vc_s + csr_cap);
-    uint16_t* ri_s = ci_s + csr_cap;
-    uint16_t* rp_s = ri_s + csr_cap;
-    uint16_t* cp_s = rp_s + Mc + 1;
-    const int r_base = P.rowptr[k0], c_base = P.colptr[k0];
-    const int r_cnt = P.rowptr[k0 + Mc] - r_base, c_cnt = P.colptr[k0 + Mc] - c_base;
-    const bool staged = csr_cap > 0 && r_cnt <= csr_cap && c_cnt <= csr_cap;
-    const float* vt = reinterpret_cast<const float*>(P.val_t);
-    const float* vct = reinterpret_cast<const float*>(P.valc_t);
-    if (staged) {
-        for (int k = threadIdx.x; k <= Mc; k += THR) {
-            rp_s[k] = (uint16_t)(P.rowptr[k0 + k] - r_base);
-            cp_s[k] = (uint16_t)(P.colptr[k0 + k] - c_base);
-        }
-        for (int e = threadIdx.x; e < r_cnt; e += THR) { ci_s[e] = (uint16_t)P.colidx[r_base + e]; v_s[e] = vt[r_base + e]; }
-        for (int e = threadIdx.x; e < c_cnt; e += THR) { ri_s[e] = (uint16_t)P.rowidx[c_base + e]; vc_s[e] = vct[c_base + e]; }
-    }
-    constexpr int KK = KAP * KAP;
-    const float kinvK = 1.0f / (float)(KK * KK);              // kappa^-4, exact (a power of two)
-    for (int k = threadIdx.x; k < Mc; k += THR) Bown[k] = (float)KK;   // b = 1
-    const float* mu_t = reinterpret_cast<const float*>(P.mu_t);
-    const float* nu_t = reinterpret_cast<const float*>(P.nu_t);
-    float* a = reinterpret_cast<float*>(P.a);
-    float* bb = reinterpret_cast<float*>(P.b);
-    constexpr int Q = KAP / 4;                                // float4 per block row
-    constexpr int PF = KAP == 4 ? 4 : 1;                      // blocks per chunk and thread
-    constexpr int CH = PF * THR;                              // blocks per chunk
-    const int nch = (Mc + CH - 1) / CH;                       // chunks per half sweep
-    const int halves = 2 * P.sweeps;
-    const int total = halves * nch;
-    // chunk gi -> slot gi % SLOTS; blocks kl = c CH + q THR + tid of half gi / nch
-    auto issue = [&](int gi) {
-        if (gi < total) {
-            const int c = gi - (gi / nch) * nch;
-            const float* src = ((gi / nch) & 1) == 0 ? mu_t : nu_t;
-            float4* slot = ring + ((size_t)(gi % SLOTS) * THR + threadIdx.x) * IPFA_SLOT_F4;
-#pragma unroll
-            for (int q = 0; q < PF; ++q) {
-                const int kl = c * CH + q * THR + threadIdx.x;
-                if (kl < Mc) {
-                    const int k = k0 + kl;
-                    const int k1 = k / n, k2 = k - (k / n) * n;
-#pragma unroll
-                    for (int t1 = 0; t1 < KAP; ++t1)
-#pragma unroll
-                        for (int t2 = 0; t2 < Q; ++t2)
-                            cp_async16(slot + (((q * KAP + t1) * Q + t2) ^ (threadIdx.x & 7)),
-                                       src + (size_t)(k1 * KAP + t1) * N + k2 * KAP + 4 * t2);
-                }
-            }
-        }
-        cp_async_commit();                                    // possibly empty: uniform group count
-    };
-#pragma unroll
-    for (int gi = 0; gi < SLOTS; ++gi) issue(gi);
-    cl.sync();                                                // staging and b = 1 visible
-    int gi = 0;
-    for (int h = 0; h < halves; ++h) {
-        const int half = h & 1;
-        float* dst = half == 0 ? a : bb;
-        float* mine = half == 0 ? Aown : Bown;
-        const float* other = half == 0 ? Bown : Aown;
-        bool arrived = false;
-        for (int c = 0; c < nch; ++c, ++gi) {
-            cp_async_wait<SLOTS - 1>();                       // this thread's chunk gi has landed
-            const float4* slot = ring + ((size_t)(gi % SLOTS) * THR + threadIdx.x) * IPFA_SLOT_F4;
-            float4 x[PF][KAP][Q];
-#pragma unroll
-            for (int q = 0; q < PF; ++q)
-#pragma unroll
-                for (int t1 = 0; t1 < KAP; ++t1)
-#pragma unroll
-                    for (int t2 = 0; t2 < Q; ++t2) x[q][t1][t2] = slot[((q * KAP + t1) * Q + t2) ^ (threadIdx.x & 7)];
-            float inv[PF];
-#pragma unroll
-            for (int q = 0; q < PF; ++q) {
-                const int kl = c * CH + q * THR + threadIdx.x;
-                inv[q] = 0.0f;
-                if (kl < Mc) {
-                    float r = 0.0f;
-                    if (staged) {
-                        const uint16_t* ptr = half == 0 ? rp_s : cp_s;
-                        const uint16_t* idx = half == 0 ? ci_s : ri_s;
-                        const float* val = half == 0 ? v_s : vc_s;
-                        for (int e = ptr[kl]; e < ptr[kl + 1]; ++e) {
-                            const int l = idx[e], owner = l / Mc;
-                            const float* peer = cl.map_shared_rank(other, owner);
-                            r += val[e] * peer[l - owner * Mc];
-                        }
-                    } else {
-                        const int* ptr = half == 0 ? P.rowptr : P.colptr;
-                        const int* idx = half == 0 ? P.colidx : P.rowidx;
-                        const float* val = half == 0 ? vt : vct;
-                        for (int e = ptr[k0 + kl]; e < ptr[k0 + kl + 1]; ++e) {
-                            const int l = idx[e], owner = l / Mc;
-                            const float* peer = cl.map_shared_rank(other, owner);
-                            r += val[e] * peer[l - owner * Mc];
-                        }
-                    }
-                    r *= kinvK;
-                    inv[q] = r > 0.0f ? 1.0f / r : 0.0f;
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < PF; ++q) {
-                const int kl = c * CH + q * THR + threadIdx.x;
-                if (kl < Mc) {
-                    float sum = 0.0f;
-#pragma unroll
-                    for (int t1 = 0; t1 < KAP; ++t1)
-#pragma unroll
-                        for (int t2 = 0; t2 < Q; ++t2) {
-                            float4& v = x[q][t1][t2];
-                            v.x *= inv[q]; v.y *= inv[q]; v.z *= inv[q]; v.w *= inv[q];
-                            sum += (v.x + v.y) + (v.z + v.w);
-                        }
-                    mine[kl] = sum;
-                }
-            }
-            issue(gi + SLOTS);                                // the slot's values are consumed
-            if (c == nch - 1) { cluster_arrive_release(); arrived = true; }   // sums published
-#pragma unroll
-            for (int q = 0; q < PF; ++q) {
-                const int kl = c * CH + q * THR + threadIdx.x;
-                if (kl < Mc) {
-                    const int k = k0 + kl;
-                    const int k1 = k / n, k2 = k - (k / n) * n;
-#pragma unroll
-                    for (int t1 = 0; t1 < KAP; ++t1)
-#pragma unroll
-                        for (int t2 = 0; t2 < Q; ++t2)
-                            *reinterpret_cast<float4*>(dst + (size_t)(k1 * KAP + t1) * N + k2 * KAP + 4 * t2) =
-                                x[q][t1][t2];
-                }
-            }
-        }
-        if (!arrived) cluster_arrive_release();
-        cluster_wait_acquire();
-    }
-    cp_async_wait<0>();                                       // nothing left in flight
-}
-
-// ring, block sums, and (csr_cap > 0) the staged plan rows and columns
-static size_t ipf_async_smem(int slots, int thr, int Mc, int csr_cap) {
-    return sizeof(float4) * (size_t)slots * thr * IPFA_SLOT_F4 + sizeof(float) * 2 * (size_t)Mc +
-           (csr_cap > 0 ? 2 * (sizeof(float) + sizeof(uint16_t)) * (size_t)csr_cap +
-                              2 * sizeof(uint16_t) * (size_t)(Mc + 1)
-                        : 0);
-}
-
-template <int KAP, int THR, int SLOTS>
-static int ipf_async_launch(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int C, int M_max,
-                            int nnz_max, bool stage_plan, cudaStream_t stream) {
-    const int Mc = M_max / C;
-    // staged plan rows and columns (room for the 2 Mc entries a basic plan
-    // has on average per CTA; a CTA whose blocks hold more reads its part of
-    // the plan from global memory) only while two CTAs still fit on an SM,
-    // or, for a ring too large for two, within one CTA's shared memory
-    int csr_cap = stage_plan ? std::max(nnz_max, 2 * Mc + 64) : 0;
-    size_t smem = ipf_async_smem(SLOTS, THR, Mc, csr_cap);
-    const size_t budget = ipf_async_smem(SLOTS, THR, 0, 0) <= 96 * 1024 ? 112 * 1024 : 220 * 1024;
-    if (smem > budget) { csr_cap = 0; smem = ipf_async_smem(SLOTS, THR, Mc, 0); }
-    if (smem > 227 * 1024) return QWB_ERR_UNSUPPORTED;
-    auto kern = ipf_async_kernel<KAP, THR, SLOTS>;
-    QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    if (C > 8) QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(n_pairs * C));
-    cfg.blockDim = dim3(THR);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)C;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    QWB_CUDA(cudaLaunchKernelEx(&cfg, kern, pairs_d, pair_ids, C, csr_cap));
-    QWB_LAUNCHED();
-    return QWB_OK;
-}
-
-int launch_ipf_async(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int kappa, int C, int variant,
-                     int M_max, int nnz_max, cudaStream_t stream) {
-    if (n_pairs <= 0) return QWB_OK;
-    if (C < 1 || C > 16 || (kappa != 4 && kappa != 8)) return QWB_ERR_UNSUPPORTED;
-    // variant 0: 128 threads, two slots per thread; 1: 64 threads, four
-    // slots; 2: 256 threads, two slots (64 KB, 64 KB and 128 KB of copies in
-    // flight per CTA; the first two leave room for two CTAs per SM)
-    if (variant == 0)
-        return kappa == 4 ? ipf_async_launch<4, 128, 2>(pairs_d, pair_ids, n_pairs, C, M_max, nnz_max, true, stream)
-                          : ipf_async_launch<8, 128, 2>(pairs_d, pair_ids, n_pairs, C, M_max, nnz_max, true, stream);
-    if (variant == 1)
-        return kappa == 4 ? ipf_async_launch<4, 64, 4>(pairs_d, pair_ids, n_pairs, C, M_max, nnz_max, true, stream)
-                          : ipf_async_launch<8, 64, 4>(pairs_d, pair_ids, n_pairs, C, M_max, nnz_max, true, stream);
-    if (variant == 2)
-        return kappa == 4 ? ipf_async_launch<4, 256, 2>(pairs_d, pair_ids, n_pairs, C, M_max, nnz_max, true, stream)
-                          : ipf_async_launch<8, 256, 2>(pairs_d, pair_ids, n_pairs, C, M_max, nnz_max, true, stream);
-    return QWB_ERR_UNSUPPORTED;
 }
 
 // --------------------------------------------------------------------------

@@ -110,24 +110,15 @@ int launch_primal(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, 
 // chunk unissued (host-side fault injection for the time-out path), else -1.
 int launch_ipf_stream(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int kappa, int C, int n,
                       int N, int* err, unsigned long long timeout_ns, int skip_chunk, cudaStream_t stream);
-// The same sweeps with per-thread asynchronous copies into private shared-
-// memory slots (ipf_async_kernel): variant 0 = 128 threads and two slots per
-// thread, 1 = 64 threads and four slots, 2 = 256 threads and two slots.
-int launch_ipf_async(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int kappa, int C, int variant,
-                     int M_max, int nnz_max, cudaStream_t stream);
-// The register-streaming sweeps with two pairs per cluster whose half sweeps
-// interleave, so that each cluster barrier completes behind the other pair's
-// work (ipf_fine2_kernel); n_pairs pairs in (n_pairs + 1) / 2 clusters.
-int launch_ipf_fine2(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int kappa, int C,
-                     int M_max, cudaStream_t stream);
 // primal pass with a general upscaling kernel (P.upK set; d = 2, kappa <= kappa_max <= 8;
 // all_kappa4: every pair of the launch has kappa 4, which selects the register-row kernel)
 int launch_primalk(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs, int kappa_max,
                    int M_max, int nnz_max, int m_max, bool all_kappa4, bool f64, cudaStream_t stream);
 // Fine FP32 IPF sweeps on clusters of C CTAs per pair (2-D, kappa 4 or 8,
 // FP32, C divides every pair's n); the pairs have fine_ext = 1.
+// hints: read-only loads with a 256-byte L2 prefetch and evict-first stores.
 int launch_ipf_fine(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int kappa, int C,
-                    int M_max, int nnz_max, cudaStream_t stream);
+                    int M_max, int nnz_max, bool hints, cudaStream_t stream);
 // side 0 upscales f~ (the dual pass of Alg. 5); side 1 upscales g~ (the
 // same pass started from the other coarse potential)
 int launch_upsample(const PairDev* pairs_d, PairOut* outs_d, const PixItem* items, int n_items,

@@ -311,16 +311,13 @@ def test_fine_ipf_scalings_bulk(sweeps, batched, cluster):
 @pytest.mark.parametrize("sweeps", [1, 7])
 @pytest.mark.parametrize("batched", [True, False])
 @pytest.mark.parametrize("cluster", [2, 4, 8])
-@pytest.mark.parametrize("form", ["ASYNC", "ASYNC2", "ASYNC3", "PAIR2"])
-def test_fine_ipf_scalings_async(sweeps, batched, cluster, form):
-    """The sweeps with per-thread asynchronous copies into private slots
-    (cluster | QWB_IPF_ASYNC, _ASYNC2, _ASYNC3) and the register form with two
-    pairs per cluster (QWB_IPF_PAIR2: 3 pairs at kappa 4, so one cluster has a
-    single pair): several chunks per half sweep
-    and copies issued across half-sweep boundaries (256^2 at kappa 8, 128^2 at
-    kappa 4, a 64^2 pair whose blocks do not fill a chunk, a zero-mass block).
-    The scalings reach the uniform kernel's fixed point and equal the
-    register-streaming cluster sweeps up to FP32 rounding; the certified bound,
+@pytest.mark.parametrize("form", ["HINTS"])
+def test_fine_ipf_scalings_hints(sweeps, batched, cluster, form):
+    """The register-streaming cluster sweeps with cache-policy hints
+    (cluster | QWB_IPF_HINTS): several chunks per half sweep (256^2 at kappa
+    8, 128^2 at kappa 4, a 64^2 pair whose blocks do not fill a chunk, a
+    zero-mass block).  The scalings reach the uniform kernel's fixed point and
+    equal the sweeps without hints up to FP32 rounding; the certified bound,
     which the FP64 block-scalar sweeps define, is bit-identical."""
     cases = [(256, 8, 2.0, "gauss"), (128, 4, 1.0, "field"), (64, 4, 2.0, "white"),
              (128, 4, 2.0, "cauchy")]
@@ -333,7 +330,7 @@ def test_fine_ipf_scalings_async(sweeps, batched, cluster, form):
         mus.append(mu); nus.append(nu); probs.append((N, kappa, p))
     md, nd = [T(x) for x in mus], [T(x) for x in nus]
     out = {}
-    for name, flag in (("async", getattr(api, "QWB_IPF_" + form)), ("registers", 0)):
+    for name, flag in (("hinted", getattr(api, "QWB_IPF_" + form)), ("registers", 0)):
         with api.Batch(probs, ipf_sweeps=sweeps, prec="mixed", flags=1 | 4) as b:
             b.coarse(md, nd, batched=batched)
             b.solve()
@@ -344,9 +341,9 @@ def test_fine_ipf_scalings_async(sweeps, batched, cluster, form):
             out[name] = ([r["ub_primal"] for r in res], [[x.cpu().numpy() for x in b.fine_scalings(t)]
                                                           for t in range(len(probs))])
     for t, (N, kappa, p) in enumerate(probs):
-        assert out["async"][0][t] == out["registers"][0][t], t
+        assert out["hinted"][0][t] == out["registers"][0][t], t
         for side, meas in enumerate((mus[t], nus[t])):
-            got = out["async"][1][t][side]
+            got = out["hinted"][1][t][side]
             coarse = O.sumpool(meas, N, kappa)
             blk = np.repeat(np.repeat(coarse.reshape(N // kappa, N // kappa), kappa, 0), kappa, 1).ravel()
             want = np.where(blk > 0, kappa ** 2 * meas / np.where(blk > 0, blk, 1.0), 0.0)
