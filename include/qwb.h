@@ -389,14 +389,10 @@ int qwb_batch_coarse_potentials(qwb_batch* batch, int32_t pair, double* f_h, dou
  * source values by bulk copies (cp.async.bulk into a ring of shared-memory
  * stages, completion on mbarriers, every wait bounded) for groups whose pairs
  * share N; a timed-out wait makes qwb_batch_results return TIMEOUT.
- * C | QWB_IPF_HINTS runs the register form with cache-policy hints: the
- * source values read through the read-only path with a 256-byte L2 prefetch
- * per request, the scaled values stored with the evict-first policy.
- * Overrides the autotuner's choice, which times every form;
+ * Overrides the autotuner's choice, which times both forms;
  * synchronises the device and drops the batch's captured fine-pass graphs.
  * Errors: INVALID_ARG, CUDA. */
 #define QWB_IPF_BULK 32
-#define QWB_IPF_HINTS 64
 int qwb_batch_set_ipf_cluster(qwb_batch* batch, int32_t C);
 /* Upscale the coarse plans of the batch's 2-D pairs with block side kappa by
  * the general kernel K_d (Sec. 3.4, eq. coupling tensor upscale; layout,

@@ -57,7 +57,6 @@ def _ptr(t):
 
 
 QWB_IPF_BULK = 32   # Batch.set_ipf_cluster(C | QWB_IPF_BULK): the bulk-copy staged sweeps
-QWB_IPF_HINTS = 64    # ... | QWB_IPF_HINTS: register form with read-only / L2-prefetch loads, streaming stores
 
 
 def problem(N, kappa, p, d=2):

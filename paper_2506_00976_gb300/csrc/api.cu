@@ -207,11 +207,11 @@ struct qwb_batch {
     // largest power of two <= ipf_C that divides all its coarse sides
     // (stream: the bulk-copy variant ipf_stream_kernel, for groups whose pairs
     // share N; n_same, N_same: that common coarse and fine side, else 0)
-    struct IpfGroup { int kappa, off, cnt, M_max, gcd_n, C, n_same, N_same; bool stream; bool hints; };
+    struct IpfGroup { int kappa, off, cnt, M_max, gcd_n, C, n_same, N_same; bool stream; };
     std::vector<IpfGroup> ipf_groups;
     std::vector<int> ipf_group_of;      // per pair: its group or -1
     int* ipf_ids_d = nullptr;
-    int ipf_C = 0;                      // | QWB_IPF_BULK: bulk-copy form; | QWB_IPF_HINTS: cache hints
+    int ipf_C = 0;                      // | QWB_IPF_BULK: the bulk-copy form
     int* dev_err = nullptr;             // device error word of bounded waits (0 = none)
     unsigned long long wait_ns = 0;     // limit of every bounded device wait (QWB_WAIT_TIMEOUT_MS)
     int fault_skip_chunk = -1;          // QWB_FAULT ipf_bulk_skip_chunk (tests), else -1
@@ -351,7 +351,7 @@ static int launch_ipf_group(qwb_batch* b, const qwb_batch::IpfGroup& G, const in
     if (G.stream)
         return launch_ipf_stream(b->pairs_d, ids, cnt, G.kappa, G.C, G.n_same, G.N_same, b->dev_err, b->wait_ns,
                                  b->fault_skip_chunk, s);
-    return launch_ipf_fine(b->pairs_d, ids, cnt, G.kappa, G.C, M, 0, G.hints, s);
+    return launch_ipf_fine(b->pairs_d, ids, cnt, G.kappa, G.C, M, 0, s);
 }
 
 static int apply_ipf_choice(qwb_batch* b, int C) {
@@ -362,7 +362,6 @@ static int apply_ipf_choice(qwb_batch* b, int C) {
         while (c * 2 <= Cs && c * 2 <= 16 && G.gcd_n % (c * 2) == 0) c *= 2;
         G.C = c >= 2 ? c : 0;
         G.stream = (C & QWB_IPF_BULK) && G.C > 0 && G.n_same > 0 && G.N_same > 0;
-        G.hints = G.C > 0 && !G.stream && (C & QWB_IPF_HINTS) != 0;
     }
     for (int t = 0; t < b->n; ++t) {
         const int g = b->ipf_group_of[t];
@@ -1017,15 +1016,13 @@ static int tune_ipf(qwb_batch* b, cudaStream_t s) {
     rep << "{";
     double best = 1e30;
     int bestC = 0;
-    for (int C : {0, 2, 4, 8, 16, QWB_IPF_BULK | 2, QWB_IPF_BULK | 4, QWB_IPF_BULK | 8, QWB_IPF_BULK | 16,
-                  QWB_IPF_HINTS | 2, QWB_IPF_HINTS | 4, QWB_IPF_HINTS | 8, QWB_IPF_HINTS | 16}) {
+    for (int C : {0, 2, 4, 8, 16, QWB_IPF_BULK | 2, QWB_IPF_BULK | 4, QWB_IPF_BULK | 8, QWB_IPF_BULK | 16}) {
         int st = apply_ipf_choice(b, C);
         if (st) return st;
         if (C > 0) {
             bool any = false;
             for (const auto& G : b->ipf_groups)
-                any |= G.C == (C & 31) && G.stream == ((C & QWB_IPF_BULK) != 0) &&
-                       G.hints == ((C & QWB_IPF_HINTS) != 0);
+                any |= G.C == (C & 31) && G.stream == ((C & QWB_IPF_BULK) != 0);
             if (!any) continue;                  // no group takes this size / form
         }
         double ms;
@@ -1038,7 +1035,7 @@ static int tune_ipf(qwb_batch* b, cudaStream_t s) {
         }, &ms);
         if (st) return st;
         rep << (C ? ", " : "") << "\""
-            << ((C & QWB_IPF_BULK) ? "bulk" : (C & QWB_IPF_HINTS) ? "cluster_hints" : "cluster")
+            << ((C & QWB_IPF_BULK) ? "bulk" : "cluster")
             << (C & 31) << "\": " << ms;
         if (ms < best) { best = ms; bestC = C; }
     }
@@ -1602,11 +1599,11 @@ int qwb_batch_coarse_potentials(qwb_batch* b, int32_t pair, double* f_h, double*
 int qwb_batch_set_ipf_cluster(qwb_batch* b, int32_t C) {
     const int Cs = C & 31, form = C & ~31;
     if (!b || (Cs != 0 && Cs != 2 && Cs != 4 && Cs != 8 && Cs != 16) ||
-        (form != 0 && form != QWB_IPF_BULK && form != QWB_IPF_HINTS) ||
+        (form != 0 && form != QWB_IPF_BULK) ||
         (form != 0 && Cs == 0))
         return fail(QWB_ERR_INVALID_ARG,
                     "qwb_batch_set_ipf_cluster: C must be 0, 2, 4, 8 or 16, the last four optionally with one of "
-                    "QWB_IPF_BULK or QWB_IPF_HINTS");
+                    "QWB_IPF_BULK");
     QWB_CUDA(cudaSetDevice(b->ctx->device));
     QWB_CUDA(cudaDeviceSynchronize());
     // captured fine passes hold the previous launch configuration

@@ -1866,21 +1866,7 @@ __device__ __forceinline__ void cluster_wait_acquire() {
     asm volatile("barrier.cluster.wait.acquire;\n" ::: "memory");
 }
 
-// HINTS: the source values are read through the read-only path with a 256-byte
-// L2 prefetch per request and the scaled values are stored with the streaming
-// (evict-first) policy, since this kernel never reads them back.
-__device__ __forceinline__ float4 ld_nc_l2pf(const float* p) {
-    float4 v;
-    asm("ld.global.nc.L2::256B.v4.f32 {%0, %1, %2, %3}, [%4];"
-        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
-    return v;
-}
-__device__ __forceinline__ void st_cs(float* p, const float4 v) {
-    asm volatile("st.global.cs.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
-                 : "memory");
-}
-
-template <int KAP, bool HINTS = false>
+template <int KAP>
 __global__ void __launch_bounds__(IPF_THREADS)
 ipf_fine_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair_ids, int C,
                 int csr_cap) {
@@ -1933,10 +1919,9 @@ ipf_fine_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair_
 #pragma unroll
                 for (int t1 = 0; t1 < KAP; ++t1)
 #pragma unroll
-                    for (int t2 = 0; t2 < Q; ++t2) {
-                        const float* ps = src + (size_t)(k1 * KAP + t1) * N + k2 * KAP + 4 * t2;
-                        x[q][t1][t2] = HINTS ? ld_nc_l2pf(ps) : *reinterpret_cast<const float4*>(ps);
-                    }
+                    for (int t2 = 0; t2 < Q; ++t2)
+                        x[q][t1][t2] = *reinterpret_cast<const float4*>(src + (size_t)(k1 * KAP + t1) * N +
+                                                                         k2 * KAP + 4 * t2);
             }
         }
     };
@@ -1998,11 +1983,9 @@ ipf_fine_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair_
 #pragma unroll
                     for (int t1 = 0; t1 < KAP; ++t1)
 #pragma unroll
-                        for (int t2 = 0; t2 < Q; ++t2) {
-                            float* pd = dst + (size_t)(k1 * KAP + t1) * N + k2 * KAP + 4 * t2;
-                            if (HINTS) st_cs(pd, x[q][t1][t2]);
-                            else *reinterpret_cast<float4*>(pd) = x[q][t1][t2];
-                        }
+                        for (int t2 = 0; t2 < Q; ++t2)
+                            *reinterpret_cast<float4*>(dst + (size_t)(k1 * KAP + t1) * N + k2 * KAP + 4 * t2) =
+                                x[q][t1][t2];
                 }
             }
         }
@@ -2013,7 +1996,7 @@ ipf_fine_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair_
 }
 
 int launch_ipf_fine(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int kappa, int C,
-                    int M_max, int nnz_max, bool hints, cudaStream_t stream) {
+                    int M_max, int nnz_max, cudaStream_t stream) {
     if (n_pairs <= 0) return QWB_OK;
     if (C < 1 || C > 16 || (kappa != 4 && kappa != 8)) return QWB_ERR_UNSUPPORTED;
     const int Mc = M_max / C;
@@ -2027,8 +2010,7 @@ int launch_ipf_fine(const PairDev* pairs_d, const int* pair_ids, int n_pairs, in
         smem = sizeof(float) * 2 * (size_t)Mc + 2 * sizeof(int) * (size_t)(Mc + 1);
         csr_cap = 0;
     }
-    auto kern = kappa == 4 ? (hints ? ipf_fine_kernel<4, true> : ipf_fine_kernel<4, false>)
-                           : (hints ? ipf_fine_kernel<8, true> : ipf_fine_kernel<8, false>);
+    auto kern = kappa == 4 ? ipf_fine_kernel<4> : ipf_fine_kernel<8>;
     QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (C > 8) QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     cudaLaunchConfig_t cfg = {};

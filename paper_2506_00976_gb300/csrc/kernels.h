@@ -116,9 +116,8 @@ int launch_primalk(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids,
                    int M_max, int nnz_max, int m_max, bool all_kappa4, bool f64, cudaStream_t stream);
 // Fine FP32 IPF sweeps on clusters of C CTAs per pair (2-D, kappa 4 or 8,
 // FP32, C divides every pair's n); the pairs have fine_ext = 1.
-// hints: read-only loads with a 256-byte L2 prefetch and evict-first stores.
 int launch_ipf_fine(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int kappa, int C,
-                    int M_max, int nnz_max, bool hints, cudaStream_t stream);
+                    int M_max, int nnz_max, cudaStream_t stream);
 // side 0 upscales f~ (the dual pass of Alg. 5); side 1 upscales g~ (the
 // same pass started from the other coarse potential)
 int launch_upsample(const PairDev* pairs_d, PairOut* outs_d, const PixItem* items, int n_items,

@@ -308,49 +308,6 @@ def test_fine_ipf_scalings_bulk(sweeps, batched, cluster):
             np.testing.assert_allclose(got, out["registers"][1][t][side], rtol=2e-5, atol=0)
 
 
-@pytest.mark.parametrize("sweeps", [1, 7])
-@pytest.mark.parametrize("batched", [True, False])
-@pytest.mark.parametrize("cluster", [2, 4, 8])
-@pytest.mark.parametrize("form", ["HINTS"])
-def test_fine_ipf_scalings_hints(sweeps, batched, cluster, form):
-    """The register-streaming cluster sweeps with cache-policy hints
-    (cluster | QWB_IPF_HINTS): several chunks per half sweep (256^2 at kappa
-    8, 128^2 at kappa 4, a 64^2 pair whose blocks do not fill a chunk, a
-    zero-mass block).  The scalings reach the uniform kernel's fixed point and
-    equal the sweeps without hints up to FP32 rounding; the certified bound,
-    which the FP64 block-scalar sweeps define, is bit-identical."""
-    cases = [(256, 8, 2.0, "gauss"), (128, 4, 1.0, "field"), (64, 4, 2.0, "white"),
-             (128, 4, 2.0, "cauchy")]
-    mus, nus, probs = [], [], []
-    for i, (N, kappa, p, cls) in enumerate(cases):
-        mu, nu = synth.make_measure(N, cls, 70 + i, 0), synth.make_measure(N, cls, 70 + i, 1)
-        if i == 3:   # a zero-mass block on each side
-            mu = mu.reshape(N, N).copy(); mu[8:12, 4:8] = 0.0; mu = (mu / mu.sum()).ravel()
-            nu = nu.reshape(N, N).copy(); nu[0:4, 60:64] = 0.0; nu = (nu / nu.sum()).ravel()
-        mus.append(mu); nus.append(nu); probs.append((N, kappa, p))
-    md, nd = [T(x) for x in mus], [T(x) for x in nus]
-    out = {}
-    for name, flag in (("hinted", getattr(api, "QWB_IPF_" + form)), ("registers", 0)):
-        with api.Batch(probs, ipf_sweeps=sweeps, prec="mixed", flags=1 | 4) as b:
-            b.coarse(md, nd, batched=batched)
-            b.solve()
-            b.set_ipf_cluster(cluster | flag)
-            b.fine(md, nd, batched=batched)
-            res = b.results()
-            assert all(r["status"] == 0 for r in res)
-            out[name] = ([r["ub_primal"] for r in res], [[x.cpu().numpy() for x in b.fine_scalings(t)]
-                                                          for t in range(len(probs))])
-    for t, (N, kappa, p) in enumerate(probs):
-        assert out["hinted"][0][t] == out["registers"][0][t], t
-        for side, meas in enumerate((mus[t], nus[t])):
-            got = out["hinted"][1][t][side]
-            coarse = O.sumpool(meas, N, kappa)
-            blk = np.repeat(np.repeat(coarse.reshape(N // kappa, N // kappa), kappa, 0), kappa, 1).ravel()
-            want = np.where(blk > 0, kappa ** 2 * meas / np.where(blk > 0, blk, 1.0), 0.0)
-            np.testing.assert_allclose(got, want, rtol=2e-5, atol=0)
-            np.testing.assert_allclose(got, out["registers"][1][t][side], rtol=2e-5, atol=0)
-
-
 @pytest.mark.parametrize("sweeps", [1, 7, 50])
 @pytest.mark.parametrize("batched", [True, False])
 @pytest.mark.parametrize("cluster", [0, 2, 8, 16])
