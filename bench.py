@@ -402,7 +402,7 @@ def alu_rates(api):
     if _ALU is not None:
         return _ALU
     api.probe_fp32_rate(0, iters=16384)             # clocks up before the measured runs
-    rows = [api.probe_fp32_rate(k) for k in range(len(api.PROBE_KINDS))]
+    rows = [api.probe_fp32_rate(k) for k in range(8)]
     mix = max(rows[6]["per_s"], rows[7]["per_s"])
     _ALU = {"fp32_peak_tflops": round(2.0 * rows[0]["per_s"] / 1e12, 3),
             "mix_ceiling_per_s": mix,

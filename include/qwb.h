@@ -450,6 +450,11 @@ const char* qwb_last_error(void);
  *        6 sub.rm.f32x2 then one three-input min.f32 (the line-paired
  *          c-transform's two candidates)
  *        7 two sub.rm.f32 then one three-input min.f32 (two candidates)
+ *        8, 9 the shifted c-transform's inner block alone (16 outputs per
+ *          thread, 8 columns per chunk, squared offsets in registers, one
+ *          rounded-up packed subtraction per column; per candidate pair one
+ *          packed round-down subtraction and one three-input min, in one
+ *          assembly block (8) or two (9)); 2 CTAs per SM at most
  * ctas_per_sm is lowered to what can be resident at once.
  * out_h (host, 6 doubles): [0] FP32 results (packed: two per instruction;
  * kinds 6, 7: candidates) per cycle per SM, over each SM's span of its cycle

@@ -393,7 +393,9 @@ def bounds(mus, nus, problems, ipf_sweeps=50, prec="mixed", batched=True, thread
 
 PROBE_KINDS = ("fma.rn.f32", "sub.rm.f32", "min.f32 (2 inputs)", "min.f32 (3 inputs)", "fma.rn.f32x2",
                "sub.rm.f32x2", "sub.rm.f32x2 + 3-input min (2 candidates)",
-               "2 x sub.rm.f32 + 3-input min (2 candidates)")
+               "2 x sub.rm.f32 + 3-input min (2 candidates)",
+               "c-transform inner block, fused subtraction-and-min (2 candidates)",
+               "c-transform inner block, separate subtraction and min (2 candidates)")
 
 
 def probe_fp32_rate(kind, ctas_per_sm=8, iters=2048):

@@ -502,6 +502,28 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
     const int tile_out = CT_TILE;
     long total_tiles = 0;
     for (int t = 0; t < n; ++t) total_tiles += ((long)ipow(probs[t].N, dim_of(probs[t])) + tile_out - 1) / tile_out;
+    // Input-line splits of the batched c-transform items.  The persistent
+    // grid (SMs x resident CTAs, 1 to 3 per SM depending on the kernel the
+    // autotuner picks) walks the items round-robin, so the last round runs
+    // partly empty unless the item count nearly fills a whole number of
+    // rounds: take the split, between the one giving about 4 items per SM
+    // and 16, whose worst round fill over 1, 2 and 3 CTAs per SM is best
+    // (ties to fewer splits, i.e. more input lines per item).
+    long splits_fill = 1;
+    {
+        double best = -1.0;
+        const long s_lo = std::max<long>(1, (4L * sm + total_tiles - 1) / std::max<long>(1, total_tiles));
+        for (long sp = s_lo; sp <= std::max<long>(s_lo, 16); ++sp) {
+            const long items = total_tiles * sp;
+            double worst = 1.0;
+            for (int occ = 1; occ <= 3; ++occ) {
+                const long g = (long)sm * occ;
+                const long rounds = (items + g - 1) / g;
+                worst = std::min(worst, (double)items / (double)(rounds * g));
+            }
+            if (worst > best + 1e-3) { best = worst; splits_fill = sp; }
+        }
+    }
     std::vector<PixItem> cb3;      // 3-D C-bar: one item per source block
     for (int t = 0; t < n; ++t) {
         const int dd = dim_of(probs[t]);
@@ -528,11 +550,10 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         }
         b->sep_cnt.push_back(0);
         const int tiles = (m + tile_out - 1) / tile_out;
-        // batched form: about 12 items per SM over the whole batch (six waves
-        // of the persistent grid), each pair split evenly
-        // (input lines staged per item: at most 32 KB of shared memory)
+        // batched form: each pair's input lines split splits_fill ways (see
+        // above; input lines staged per item: at most 32 KB of shared memory)
         const int rows_cap = std::max(1, (int)(32768 / (tsz * (size_t)N)));
-        const long splits_b = std::max<long>(1, (12L * sm + total_tiles - 1) / std::max<long>(1, total_tiles));
+        const long splits_b = splits_fill;
         const int rows_b = std::min(rows_cap, pick_in_rows(rows_all, 1, (int)std::min<long>(splits_b, rows_all)));
         for (int o = 0; o < m; o += tile_out)
             for (int r0 = 0; r0 < rows_all; r0 += rows_b) ctb.push_back({t, o, r0, std::min(rows_b, rows_all - r0)});

@@ -67,15 +67,91 @@ __device__ __forceinline__ void p_unpack(unsigned long long v, float& lo, float&
     asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
 }
 
-// FP32 results per chain step of each kind (0..7)
+// FP32 results per chain step of each kind (0..9)
 __host__ __device__ constexpr int probe_results_per_step(int kind) {
-    return (kind == 4 || kind == 5 || kind == 6 || kind == 7) ? 2 : 1;
+    return (kind >= 4) ? 2 : 1;
+}
+
+// kinds 8, 9: the shifted line-paired c-transform's inner block in isolation
+// (16 outputs per thread, chunks of 8 columns, the 23 squared column offsets
+// in registers, two packed potentials per 16-byte shared load, one rounded-up
+// packed subtraction per column, then per output one packed round-down
+// subtraction and one 3-input min); 8 with each subtraction-and-min pair in
+// one assembly block, 9 with separate blocks.  A chain step is one
+// (column, output) candidate pair.
+template <bool FUSED>
+__device__ __forceinline__ void probe_ct_block(int iters, const ulonglong2* hs, float (&mins)[16]) {
+    unsigned long long DD[23];
+#pragma unroll
+    for (int e = 0; e < 23; ++e) {
+        const float d = (float)(e - 15 + (int)(threadIdx.x & 7));
+        DD[e] = p_pack(d * d, d * d);
+    }
+    unsigned long long AA = p_pack(1.0f, 4.0f);
+    for (int it = 0; it < iters; ++it) {
+        const ulonglong2* hrow = hs + (it & 7) * 4;
+#pragma unroll
+        for (int s = 0; s < 8; s += 2) {
+            const ulonglong2 v = hrow[s / 2];
+            unsigned long long hA0, hA1;
+            asm("sub.rp.f32x2 %0, %1, %2;" : "=l"(hA0) : "l"(v.x), "l"(AA));
+            asm("sub.rp.f32x2 %0, %1, %2;" : "=l"(hA1) : "l"(v.y), "l"(AA));
+#pragma unroll
+            for (int ss = 0; ss < 2; ++ss) {
+                const unsigned long long hA = ss ? hA1 : hA0;
+#pragma unroll
+                for (int r = 0; r < 16; ++r) {
+                    if (FUSED) {
+                        float d;
+                        asm("{\n .reg .b64 t;\n .reg .f32 lo, hi;\n sub.rm.f32x2 t, %1, %2;\n mov.b64 {lo, hi}, t;\n"
+                            " min.f32 %0, %3, lo, hi;\n}" : "=f"(d) : "l"(DD[s + ss - r + 15]), "l"(hA), "f"(mins[r]));
+                        mins[r] = d;
+                    } else {
+                        const unsigned long long t = p_sub2_rm(DD[s + ss - r + 15], hA);
+                        float lo, hi;
+                        p_unpack(t, lo, hi);
+                        mins[r] = p_min3(mins[r], lo, hi);
+                    }
+                }
+            }
+        }
+        AA = p_pack(1.0f + (float)(it & 1), 4.0f);
+    }
 }
 
 // kind: 0 fma.rn.f32, 1 sub.rm.f32, 2 min.f32 (2 inputs), 3 min.f32 (3 inputs),
 // 4 fma.rn.f32x2, 5 sub.rm.f32x2, 6 sub.rm.f32x2 + 3-input min (two candidates),
 // 7 two sub.rm.f32 + 3-input min (two candidates).  The chains stay finite:
 // the subtrahend and addend are tiny, the multiplier just below one.
+template <int KIND>
+__global__ void __launch_bounds__(PROBE_THREADS, 2)
+probe_ct_kernel(int iters, float seed, float* __restrict__ sink, long long* __restrict__ cycles) {
+    __shared__ ulonglong2 hs[64];
+    if (threadIdx.x < 64) {
+        const float a = seed + (float)threadIdx.x, b = seed - (float)threadIdx.x;
+        hs[threadIdx.x] = make_ulonglong2(p_pack(a, b), p_pack(b, a));
+    }
+    float mins[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) mins[r] = 1e30f;
+    __syncthreads();
+    long long t0 = clock64();
+    probe_ct_block<KIND == 8>(iters, hs, mins);
+    __syncthreads();
+    long long t1 = clock64();
+    float acc = 0.0f;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) acc += mins[r];
+    if (acc == 1234.5f) sink[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+    if (threadIdx.x == 0) {
+        unsigned smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        cycles[3 * blockIdx.x] = t0;
+        cycles[3 * blockIdx.x + 1] = t1;
+        cycles[3 * blockIdx.x + 2] = (long long)smid;
+    }
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(PROBE_THREADS)
 probe_kernel(int iters, float seed, float* __restrict__ sink, long long* __restrict__ cycles) {
@@ -146,7 +222,8 @@ probe_kernel(int iters, float seed, float* __restrict__ sink, long long* __restr
 
 template <int KIND>
 int probe_launch(int grid, int iters, float* sink, long long* cycles, cudaStream_t s) {
-    probe_kernel<KIND><<<grid, PROBE_THREADS, 0, s>>>(iters, 1.0f, sink, cycles);
+    if constexpr (KIND >= 8) probe_ct_kernel<KIND><<<grid, PROBE_THREADS, 0, s>>>(iters, 1.0f, sink, cycles);
+    else probe_kernel<KIND><<<grid, PROBE_THREADS, 0, s>>>(iters, 1.0f, sink, cycles);
     QWB_LAUNCHED();
     return QWB_OK;
 }
@@ -160,7 +237,9 @@ const void* probe_kernel_for(int kind) {
         case 4: return (const void*)probe_kernel<4>;
         case 5: return (const void*)probe_kernel<5>;
         case 6: return (const void*)probe_kernel<6>;
-        default: return (const void*)probe_kernel<7>;
+        case 7: return (const void*)probe_kernel<7>;
+        case 8: return (const void*)probe_ct_kernel<8>;
+        default: return (const void*)probe_ct_kernel<9>;
     }
 }
 
@@ -174,6 +253,8 @@ int probe_dispatch(int kind, int grid, int iters, float* sink, long long* cycles
         case 5: return probe_launch<5>(grid, iters, sink, cycles, s);
         case 6: return probe_launch<6>(grid, iters, sink, cycles, s);
         case 7: return probe_launch<7>(grid, iters, sink, cycles, s);
+        case 8: return probe_launch<8>(grid, iters, sink, cycles, s);
+        case 9: return probe_launch<9>(grid, iters, sink, cycles, s);
         default: return QWB_ERR_INVALID_ARG;
     }
 }
@@ -184,8 +265,8 @@ int probe_dispatch(int kind, int grid, int iters, float* sink, long long* cycles
 using namespace qwb;
 
 extern "C" int qwb_probe_fp32_rate(int32_t kind, int32_t ctas_per_sm, int32_t iters, double* out_h) {
-    if (kind < 0 || kind > 7 || ctas_per_sm < 1 || ctas_per_sm > 8 || iters < 1 || !out_h) {
-        set_last_error("qwb_probe_fp32_rate: kind in [0, 7], ctas_per_sm in [1, 8], iters >= 1, out_h non-null");
+    if (kind < 0 || kind > 9 || ctas_per_sm < 1 || ctas_per_sm > 8 || iters < 1 || !out_h) {
+        set_last_error("qwb_probe_fp32_rate: kind in [0, 9], ctas_per_sm in [1, 8], iters >= 1, out_h non-null");
         return QWB_ERR_INVALID_ARG;
     }
     int dev = 0, sms = 0;
