@@ -379,6 +379,7 @@ def run_gpu(args):
             out["uneven_200"] = _uneven_workload(api, dev, args)
             out["differentiable_256"] = _differentiable_workload(api, dev, args)
             out["ipf_hbm"] = _ipf_hbm_workload(api, dev, args)
+            out["ipf_hbm_76"] = _ipf_hbm_workload(api, dev, args, n_pairs=76)
             out["workload_64"] = _workload_64(api, dev, args)
             out["kernel_upscale"] = _kernel_upscale_workload(api, dev, args)
         if not args.no_cpu_baseline:
@@ -519,18 +520,18 @@ def _workload_64(api, dev, args):
     return out
 
 
-def _ipf_hbm_workload(api, dev, args):
-    """The IPF sweeps on a working set larger than L2: 45 pairs of 512 x 512
-    (kappa 8, 64 x 64 coarse), 50 sweeps, 4.2 MB per pair and sweep (189 MB
-    per sweep > the 129 MB L2).  Only the primal pass runs (C-bar and the dual
-    pass off)."""
+def _ipf_hbm_workload(api, dev, args, n_pairs=45):
+    """The IPF sweeps on a working set larger than L2: n_pairs pairs of
+    512 x 512 (kappa 8, 64 x 64 coarse), 50 sweeps, 4.2 MB per pair and sweep
+    (45 pairs: 189 MB per sweep > the 129 MB L2).  Only the primal pass runs
+    (C-bar and the dual pass off)."""
     import torch
     from paper_2506_00976_gb300 import synth
     Nh, kh, sweeps = 512, 8, SWEEPS
     pairs = []
     for ci, cls in enumerate(CLASSES):
-        pairs += synth.class_pairs(Nh, cls, 6, count=6)[:12]
-    pairs = pairs[:45]
+        pairs += synth.class_pairs(Nh, cls, 6, count=6 if n_pairs <= 60 else 8)[:(n_pairs + 3) // 4]
+    pairs = pairs[:n_pairs]
     mus = [torch.tensor(a, dtype=torch.float64, device=dev) for a, _ in pairs]
     nus = [torch.tensor(b, dtype=torch.float64, device=dev) for _, b in pairs]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
@@ -814,7 +815,7 @@ def main():
                     help="pairs per value class (45 = the full workload; smaller for profiling)")
     ap.add_argument("--skip-plain", action="store_true", help="time only the batched form")
     ap.add_argument("--skip-e2e", action="store_true", help="skip the end-to-end timing")
-    ap.add_argument("--only", default="", choices=["", "ipf_hbm", "uneven_200", "differentiable_256",
+    ap.add_argument("--only", default="", choices=["", "ipf_hbm", "ipf_hbm_76", "uneven_200", "differentiable_256",
                                                    "workload_64", "kernel_upscale", "alu_rates", "alu_sweep"],
                     help="run one secondary workload alone and print its JSON (profiling)")
     ap.add_argument("--skip-workloads", action="store_true",
@@ -839,6 +840,7 @@ def main():
         dev = torch.device("cuda", 0)
         torch.cuda.set_device(dev)
         fn = {"ipf_hbm": _ipf_hbm_workload, "uneven_200": _uneven_workload,
+              "ipf_hbm_76": lambda a, d, r: _ipf_hbm_workload(a, d, r, n_pairs=76),
               "differentiable_256": _differentiable_workload, "workload_64": _workload_64,
               "kernel_upscale": _kernel_upscale_workload,
               "alu_rates": lambda a, d, r: alu_rates(a),
