@@ -586,12 +586,14 @@ def _kernel_upscale_workload(api, dev, args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     K = synth.gaussian_offset_kernel(KAPPA, 1.0)
     out, ubs = {}, {}
-    for name, kern_K, sweeps, flags in (("gaussian", K, SWEEPS, 1 | 4), ("gaussian_500", K, 500, 1 | 4),
-                                        ("uniform", None, SWEEPS, 4)):
+    for name, kern_K, sweeps, flags in (("gaussian", K, SWEEPS, 1 | 4), ("gaussian_single_cta", K, SWEEPS, 1 | 4),
+                                        ("gaussian_500", K, 500, 1 | 4), ("uniform", None, SWEEPS, 4)):
         with api.Batch([(N, KAPPA, P)] * len(mus), ipf_sweeps=sweeps, prec="mixed", flags=flags,
                        device=dev) as bt:
             if kern_K is not None:
                 bt.set_upscale_kernel(KAPPA, kern_K)
+            if name == "gaussian_single_cta":
+                bt.set_upscale_cluster(0)          # the one-CTA-per-pair kernel, for comparison
             bt.coarse(mus, nus, batched=True)
             bt.solve(threads=args.threads)
 
@@ -601,11 +603,33 @@ def _kernel_upscale_workload(api, dev, args):
             kt = bt.kernel_times()
             res = bt.results()
             assert all(r["status"] == 0 for r in res)
+            form = bt.tuning().get("upscale_kernel") if kern_K is not None else None
         out[name] = {"sweeps": sweeps, "ms_per_step": round(ms, 4), "primal_pass_ms": round(kt.get("primal", 0.0), 4),
                      "ipf_cluster_ms": round(kt.get("ipf_cluster", 0.0), 4)}
+        if form is not None:
+            out[name]["form"] = form
         ubs[name] = np.array([r["ub_primal"] for r in res])
         if name == "uniform":
             ubs["weighted"] = np.array([r["ub_weighted"] for r in res])
+    # a smaller batch, 40 pairs (at most one per SM): the cluster form spreads
+    # each pair over several SMs; the tuned pass beside the one-CTA kernel
+    small = {}
+    for name, single in (("tuned", False), ("single_cta", True)):
+        with api.Batch([(N, KAPPA, P)] * 40, ipf_sweeps=SWEEPS, prec="mixed", flags=1 | 4, device=dev) as bt:
+            bt.set_upscale_kernel(KAPPA, K)
+            if single:
+                bt.set_upscale_cluster(0)
+            bt.coarse(mus[:40], nus[:40], batched=True)
+            bt.solve(threads=args.threads)
+
+            def step():
+                bt.fine(mus[:40], nus[:40], batched=True)
+            ms = _event_ms(step, max(3, min(args.steps, 5)), 3, flush)
+            kt = bt.kernel_times()
+            assert all(r["status"] == 0 for r in bt.results())
+            small[name] = {"ms_per_step": round(ms, 4), "primal_pass_ms": round(kt.get("primal", 0.0), 4),
+                           "form": bt.tuning().get("upscale_kernel")}
+    out["gaussian_40_pairs"] = small
     m, kk, n = N * N, KAPPA * KAPPA, len(mus)
     flops = 4.0 * m * kk * SWEEPS * n          # the K products: 2 halves x m kk FMAs per sweep
     kms = out["gaussian"]["primal_pass_ms"]
@@ -632,7 +656,9 @@ def _kernel_upscale_workload(api, dev, args):
         "ub_mean": {k: float(v.mean()) for k, v in ubs.items()},
         "gaussian_500_below": {"uniform": int((g5 < ubs["uniform"]).sum()),
                                "weighted": int((g5 < ubs["weighted"]).sum())},
-        "what": "primalk_kernel: IPF of pi~ (x) K with a Gaussian K, FP32 sweeps, certified FP64 evaluation; "
+        "what": "general-kernel primal pass (primalk_cl_kernel on clusters, or primalk_kernel one CTA per pair, as "
+                "tuned; gaussian_single_cta forces the latter): IPF of pi~ (x) K with a Gaussian K, FP32 sweeps, "
+                "certified FP64 evaluation; "
                 "achieved counts the K products only (4 m kappa^2 FLOP per sweep, the plan gather's "
                 "<= 4 (2M - 1) kappa^2 not counted); 'uniform' is the uniform primal pass (cluster sweeps + "
                 "primal kernel) of a batch that also computes the weighted-cost bound; gaussian_500_below "

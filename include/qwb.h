@@ -398,12 +398,28 @@ int qwb_batch_set_ipf_cluster(qwb_batch* batch, int32_t C);
  * the general kernel K_d (Sec. 3.4, eq. coupling tensor upscale; layout,
  * requirements and certification as qwb_primal_upscale_ipf_kernel) instead of
  * the uniform kappa^-4; K_d NULL returns them to the uniform kernel.  K_d is
- * copied (the caller keeps ownership).  Those pairs sweep inside the
- * general-kernel primal kernel, one CTA per pair, and leave the cluster IPF
- * groups.  Synchronises the device and drops the batch's captured fine-pass
+ * copied (the caller keeps ownership).  Those pairs run the general-kernel
+ * primal pass (one CTA or one cluster per pair, qwb_batch_set_upscale_cluster)
+ * and leave the cluster IPF groups.  Synchronises the device and drops the batch's captured fine-pass
  * graphs.  Errors: INVALID_ARG (kappa < 1, a non-positive or non-finite
  * entry), UNSUPPORTED (kappa > 8), CUDA, OOM. */
 int qwb_batch_set_upscale_kernel(qwb_batch* batch, int32_t kappa, const double* K_d);
+/* Where the general-kernel primal pass (the pairs given a kernel K by
+ * qwb_batch_set_upscale_kernel) runs: C = 0 one CTA per pair; C = 1, 2, 4, 8
+ * the cluster form, one pair on a thread-block cluster of C CTAs of
+ * `threads` (256, 128 or 64) threads that split the coarse block rows and
+ * read each other's K-product rows through distributed shared memory, which
+ * lets a batch of pairs fill every SM at once (Sec. 3.4, eq. coupling tensor
+ * upscale; Alg. 4).  The fine sweeps give the same scalings in every form;
+ * the certified sums run in another order, so the bounds can differ in
+ * their last bits (each is certified).  The cluster form needs FP32 and one
+ * block side 2, 4 or 8 for every K pair; otherwise C = 0 runs.  Overrides,
+ * for this batch only, the autotuner's choice, which times the forms on the
+ * batch's own data; batched and per-pair passes use the same form.  Synchronises the device
+ * and drops the batch's captured fine-pass graphs.  Errors: INVALID_ARG (C
+ * or threads not listed), UNSUPPORTED (C > 0 while the batch's K pairs
+ * cannot take the cluster form), CUDA. */
+int qwb_batch_set_upscale_cluster(qwb_batch* batch, int32_t C, int32_t threads);
 /* Pair t's scalings after the fine IPF sweeps of the last qwb_batch_fine
  * (Sec. 3.4, IPF paragraph; Alg. 4): the pass-type a, b with
  * a = mu / (pi-hat b), b = nu / (pi-hat^T a) after ipf_sweeps sweeps from

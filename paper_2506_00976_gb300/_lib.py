@@ -90,6 +90,7 @@ SIGNATURES = [
     ("qwb_batch_fine_scalings", c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
     ("qwb_batch_set_ipf_cluster", c_int32, [c_void_p, c_int32]),
     ("qwb_batch_set_upscale_kernel", c_int32, [c_void_p, c_int32, c_void_p]),
+    ("qwb_batch_set_upscale_cluster", c_int32, [c_void_p, c_int32, c_int32]),
     ("qwb_batch_kernel_times", c_int32, [c_void_p, P_double, c_int32]),
     ("qwb_batch_tuning", c_int32, [c_void_p, ctypes.c_char_p, c_int32]),
     ("qwb_status_string", ctypes.c_char_p, [c_int32]),

@@ -294,7 +294,7 @@ class Batch:
     def tuning(self):
         """The autotuner's choices and candidate timings for this batch (dict)."""
         import json
-        buf = ctypes.create_string_buffer(8192)
+        buf = ctypes.create_string_buffer(65536)
         check(_lib.load().qwb_batch_tuning(self._h, buf, len(buf)), "qwb_batch_tuning")
         return json.loads(buf.value.decode())
 
@@ -351,6 +351,12 @@ class Batch:
                 raise ValueError("K must be [kappa^2, kappa^2]")
         check(_lib.load().qwb_batch_set_upscale_kernel(self._h, int(kappa), _ptr(Kd)),
               "qwb_batch_set_upscale_kernel")
+
+    def set_upscale_cluster(self, C, threads=128):
+        """Run the general-kernel primal pass one CTA per pair (C = 0) or on
+        clusters of C in {1, 2, 4, 8} CTAs of `threads` threads per pair."""
+        check(_lib.load().qwb_batch_set_upscale_cluster(self._h, int(C), int(threads)),
+              "qwb_batch_set_upscale_cluster")
 
     def fine_scalings(self, t):
         """Pair t's fine IPF scalings a, b (pass type widened to FP64)."""

@@ -79,8 +79,9 @@ struct CostTable {
 struct TuneEntry {
     std::string key;
     int R = 0, TC = 0, packed = 0, cbar_variant = 2, cbar8_variant = 4, ipf_C = 0;
-    bool ct_done = false, cbar_done = false, ipf_done = false;
-    std::string ct_report, cbar_report, ipf_report;   // JSON fragments: candidate -> ms
+    int upk_C = 0, upk_var = 0;                       // general-kernel primal pass (cluster form)
+    bool ct_done = false, cbar_done = false, ipf_done = false, upk_done = false;
+    std::string ct_report, cbar_report, ipf_report, upk_report;   // JSON fragments: candidate -> ms
 };
 
 struct qwb_ctx {
@@ -101,7 +102,7 @@ static void tune_cache_load(qwb_ctx* c) {
     while (std::getline(in, line)) {
         std::istringstream ls(line);
         TuneEntry e;
-        std::string r, tc, pk, cv, ipf;
+        std::string r, tc, pk, cv, ipf, upk;
         if (!std::getline(ls, e.key, '|') || !std::getline(ls, r, '|') || !std::getline(ls, tc, '|') ||
             !std::getline(ls, pk, '|') || !std::getline(ls, cv, '|'))
             continue;
@@ -109,6 +110,13 @@ static void tune_cache_load(qwb_ctx* c) {
             e.ipf_C = std::atoi(ipf.c_str());
             e.ipf_done = true;
             e.ipf_report = "\"cached\"";
+        }
+        if (std::getline(ls, upk, '|') && !upk.empty()) {       // optional: "C/variant" of the K pass
+            e.upk_C = std::atoi(upk.c_str());
+            const size_t sl = upk.find('/');
+            if (sl != std::string::npos) e.upk_var = std::atoi(upk.c_str() + sl + 1);
+            e.upk_done = true;
+            e.upk_report = "\"cached\"";
         }
         e.R = std::atoi(r.c_str()); e.TC = std::atoi(tc.c_str());
         e.packed = std::atoi(pk.c_str()); e.cbar_variant = std::atoi(cv.c_str());
@@ -129,6 +137,8 @@ static void tune_cache_store(qwb_ctx* c) {
             out << e.key << '|' << e.R << '|' << e.TC << '|' << e.packed << '|' << e.cbar_variant << '/'
                 << e.cbar8_variant << '|';
             if (e.ipf_done) out << e.ipf_C;
+            out << '|';
+            if (e.upk_done) out << e.upk_C << '/' << e.upk_var;
             out << "|\n";
         }
 }
@@ -223,6 +233,12 @@ struct qwb_batch {
     int* prim_ids_d = nullptr;
     int n_uni = 0, n_upk = 0, upk_kappa_max = 0, upk_M_max = 0, upk_m_max = 0;
     bool upk_all4 = false;
+    // the cluster form of that pass (primalk_cl_kernel): upk_kappa = the
+    // common kappa of the K pairs when it is 2, 4 or 8 and the batch is FP32
+    // (else 0: the cluster form is not available); upk_C = 0 runs
+    // primalk_kernel, else clusters of upk_C CTAs of the thread variant upk_var
+    int upk_kappa = 0, upk_n_max = 0, upk_C = 0, upk_var = 0;
+    int upk_req_C = -1, upk_req_var = 0;    // qwb_batch_set_upscale_cluster's choice (-1: none)
     std::vector<int> prep_off, prep_cnt, pix_off, pix_cnt, cbar_off, cbar_cnt, ct_off, ct_cnt;
     int n_prep = 0, n_pix = 0, n_cbar = 0, n_ct_b = 0;
     int n_ct_b_p2 = 0;   // batched c-transform items: the p = 2 pairs' items come first
@@ -806,6 +822,16 @@ static int launch_ct_batched(qwb_batch* b, int phase, CtConfig cfg, int cap, cud
                              b->N_max, b->f64, cap, s);
 }
 
+// The general-kernel primal pass over n pairs of ids: primalk_kernel, or the
+// cluster form when one was chosen.
+static int launch_upk(qwb_batch* b, const int* ids, int n, cudaStream_t s) {
+    if (b->upk_C > 0 && b->upk_kappa)
+        return launch_primalk_cl(b->pairs_d, b->outs_d, ids, n, b->upk_kappa, b->upk_C, b->upk_var,
+                                 b->upk_n_max, s);
+    return launch_primalk(b->pairs_d, b->outs_d, ids, n, b->upk_kappa_max, b->upk_M_max, 0, b->upk_m_max,
+                          b->upk_all4, b->f64, s);
+}
+
 static int enqueue_fine(qwb_batch* b, bool batched, cudaStream_t s) {
     int st;
     const int sm = b->ctx->sm_count > 0 ? b->ctx->sm_count : 148;
@@ -822,10 +848,7 @@ static int enqueue_fine(qwb_batch* b, bool batched, cudaStream_t s) {
             const int n_uni = b->n_upk ? b->n_uni : b->n;
             if ((st = launch_support_num(b->pairs_d, uni, n_uni, 2 * b->M_max, b->f64, s))) return st;
             if ((st = launch_primal(b->pairs_d, b->outs_d, uni, n_uni, b->M_max, 0, b->f64, s))) return st;
-            if (b->n_upk && (st = launch_primalk(b->pairs_d, b->outs_d, b->prim_ids_d + b->n_uni, b->n_upk,
-                                                 b->upk_kappa_max, b->upk_M_max, 0, b->upk_m_max, b->upk_all4,
-                                                 b->f64, s)))
-                return st;
+            if (b->n_upk && (st = launch_upk(b, b->prim_ids_d + b->n_uni, b->n_upk, s))) return st;
         }
         if ((st = mark(b, 4, s))) return st;
         const int cap = sm;       // persistent grid: all resident CTAs walk the item list
@@ -863,10 +886,16 @@ static int enqueue_fine(qwb_batch* b, bool batched, cudaStream_t s) {
         const int* id = b->pair_ids_d + t;
         const int M = b->Ms[t];
         if (do_primal && b->upk_on[t]) {
-            const int kap = b->probs[t].kappa;
-            if ((st = launch_primalk(b->pairs_d, b->outs_d, id, 1, kap, M, 0, b->probs[t].N * b->probs[t].N,
-                                     kap == 4, b->f64, s)))
-                return st;
+            if (b->upk_C > 0) {     // the same form and shape as the batched pass
+                if ((st = launch_primalk_cl(b->pairs_d, b->outs_d, id, 1, b->upk_kappa, b->upk_C, b->upk_var,
+                                            b->probs[t].N / b->upk_kappa, s)))
+                    return st;
+            } else {
+                const int kap = b->probs[t].kappa;
+                if ((st = launch_primalk(b->pairs_d, b->outs_d, id, 1, kap, M, 0, b->probs[t].N * b->probs[t].N,
+                                         kap == 4, b->f64, s)))
+                    return st;
+            }
         } else if (do_primal) {
             if ((st = launch_support_num(b->pairs_d, id, 1, 2 * M, b->f64, s))) return st;
             if (b->ipf_group_of[t] >= 0 && b->ipf_groups[b->ipf_group_of[t]].C > 0) {
@@ -1070,6 +1099,54 @@ static int tune_ipf(qwb_batch* b, cudaStream_t s) {
     return QWB_OK;
 }
 
+// General-kernel primal pass: primalk_kernel (one CTA per pair, "single")
+// or the cluster form with C CTAs per pair and 256, 128 or 64 threads per
+// CTA, timed as the launch over the batch's K pairs.
+static int tune_upk(qwb_batch* b, cudaStream_t s) {
+    TuneEntry* e = b->tune;
+    if (!b->n_upk || !b->upk_kappa || b->upk_req_C >= 0) return QWB_OK;
+    if (e && e->upk_done) {                              // timed by another batch of this signature
+        b->upk_C = e->upk_C;
+        b->upk_var = e->upk_var;
+        return QWB_OK;
+    }
+    if (!b->ctx->autotune || !e || !b->ev_ok || (b->flags & QWB_FLAG_NO_PRIMAL)) return QWB_OK;
+    static const int threads_of[3] = {256, 128, 64};
+    struct Cand { int C, var; };
+    const Cand cands[] = {{0, 0}, {1, 0}, {2, 0}, {2, 1}, {4, 1}, {4, 2}, {8, 1}, {8, 2}};
+    std::ostringstream rep;
+    rep << "{";
+    double best = 1e30;
+    Cand pick{0, 0};
+    bool first = true;
+    for (const Cand& c : cands) {
+        if (c.C > b->upk_n_max) continue;                    // every CTA owns at least one block row
+        b->upk_C = c.C;
+        b->upk_var = c.var;
+        double ms;
+        const int st = time_variant(s, b->ev[0], b->ev[1], [&] {
+            return launch_upk(b, b->prim_ids_d + b->n_uni, b->n_upk, s);
+        }, &ms);
+        if (st == QWB_ERR_UNSUPPORTED) continue;             // shared memory does not fit this size
+        if (st) { b->upk_C = 0; return st; }
+        rep << (first ? "" : ", ") << "\"";
+        if (c.C) rep << "cluster" << c.C << "x" << threads_of[c.var];
+        else rep << "single";
+        rep << "\": " << ms;
+        first = false;
+        if (ms < best) { best = ms; pick = c; }
+    }
+    rep << "}";
+    b->upk_C = pick.C;
+    b->upk_var = pick.var;
+    e->upk_C = pick.C;
+    e->upk_var = pick.var;
+    e->upk_report = rep.str();
+    e->upk_done = true;
+    tune_cache_store(b->ctx);
+    return QWB_OK;
+}
+
 // Run a pass for the whole batch, through a captured CUDA graph when batched.
 static int run_pass(qwb_batch* b, int kind, bool batched, cudaStream_t s) {
     if (!batched) return kind == 0 ? enqueue_coarse(b, false, s) : enqueue_fine(b, false, s);
@@ -1083,6 +1160,7 @@ static int run_pass(qwb_batch* b, int kind, bool batched, cudaStream_t s) {
     {
         int st_t = kind == 0 ? tune_cbar(b, s) : tune_ctransform(b, s);
         if (!st_t && kind == 1) st_t = tune_ipf(b, s);
+        if (!st_t && kind == 1) st_t = tune_upk(b, s);
         if (st_t) return st_t;
     }
     // capture on a private stream, then launch on the caller's stream
@@ -1563,6 +1641,11 @@ int qwb_batch_tuning(qwb_batch* b, char* json_out, int32_t capacity) {
       << ", \"candidates_ms\": " << (b->tune && !b->tune->cbar_report.empty() ? b->tune->cbar_report : "{}")
       << "}, \"ipf\": {\"cluster\": " << b->ipf_C
       << ", \"candidates_ms\": " << (b->tune && !b->tune->ipf_report.empty() ? b->tune->ipf_report : "{}")
+      << "}, \"upscale_kernel\": {\"cluster\": " << b->upk_C << ", \"threads\": "
+      << (b->upk_C ? (b->upk_var == 0 ? 256 : b->upk_var == 1 ? 128 : 64) : (b->f64 ? 512 : 1024))
+      << ", \"candidates_ms\": "
+      << (b->upk_req_C >= 0 ? std::string("\"set\"")
+                            : b->tune && !b->tune->upk_report.empty() ? b->tune->upk_report : std::string("{}"))
       << "}, \"enabled\": " << (b->ctx->autotune ? "true" : "false") << "}";
     const std::string str = o.str();
     if ((int)str.size() + 1 > capacity) return fail(QWB_ERR_INVALID_ARG, "qwb_batch_tuning: buffer too small");
@@ -1636,6 +1719,30 @@ int qwb_batch_set_ipf_cluster(qwb_batch* b, int32_t C) {
     b->graphs.swap(keep);
     if (b->tune) { b->tune->ipf_done = true; b->tune->ipf_C = C; b->tune->ipf_report = "\"set\""; }
     return apply_ipf_choice(b, C);
+}
+
+int qwb_batch_set_upscale_cluster(qwb_batch* b, int32_t C, int32_t threads) {
+    if (!b || (C != 0 && C != 1 && C != 2 && C != 4 && C != 8) ||
+        (C != 0 && threads != 256 && threads != 128 && threads != 64))
+        return fail(QWB_ERR_INVALID_ARG,
+                    "qwb_batch_set_upscale_cluster: C must be 0, 1, 2, 4 or 8 and threads 256, 128 or 64");
+    if (C != 0 && b->n_upk && !b->upk_kappa)
+        return fail(QWB_ERR_UNSUPPORTED,
+                    "the cluster form needs FP32 and one block side (2, 4 or 8) for every pair with a kernel K");
+    QWB_CUDA(cudaSetDevice(b->ctx->device));
+    QWB_CUDA(cudaDeviceSynchronize());
+    std::vector<GraphEntry> keep;                // captured fine passes hold the previous form
+    for (auto& g : b->graphs) {
+        if (g.kind == 1) cudaGraphExecDestroy(g.exec);
+        else keep.push_back(g);
+    }
+    b->graphs.swap(keep);
+    const int var = C == 0 ? 0 : threads == 256 ? 0 : threads == 128 ? 1 : 2;
+    b->upk_req_C = C;
+    b->upk_req_var = var;
+    b->upk_C = b->upk_kappa ? C : 0;
+    b->upk_var = var;
+    return QWB_OK;
 }
 
 int qwb_batch_set_upscale_kernel(qwb_batch* b, int32_t kappa, const double* K_d) {
@@ -1724,6 +1831,21 @@ int qwb_batch_set_upscale_kernel(qwb_batch* b, int32_t kappa, const double* K_d)
     }
     b->n_uni = (int)uni.size();
     b->n_upk = (int)kp.size();
+    // the cluster form needs FP32 and one kappa in {2, 4, 8} for every K pair
+    b->upk_kappa = 0;
+    b->upk_n_max = 0;
+    if (!b->f64 && !kp.empty()) {
+        const int k0 = b->probs[kp[0]].kappa;
+        bool same = k0 == 2 || k0 == 4 || k0 == 8;
+        for (int t : kp) {
+            same = same && b->probs[t].kappa == k0;
+            b->upk_n_max = std::max(b->upk_n_max, b->probs[t].N / k0);
+        }
+        if (same) b->upk_kappa = k0;
+    }
+    if (b->upk_req_C >= 0) { b->upk_C = b->upk_req_C; b->upk_var = b->upk_req_var; }
+    else if (b->tune && b->tune->upk_done) { b->upk_C = b->tune->upk_C; b->upk_var = b->tune->upk_var; }
+    if (!b->upk_kappa) b->upk_C = 0;
     uni.insert(uni.end(), kp.begin(), kp.end());
     b->prim_ids_d = (int*)(b->upk_mem + ids_off);
     QWB_CUDA(cudaMemcpy(b->prim_ids_d, uni.data(), sizeof(int) * b->n, cudaMemcpyHostToDevice));

@@ -1840,6 +1840,458 @@ int launch_primalk(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids,
 }
 
 // --------------------------------------------------------------------------
+// primalk_cl: the primal pass of primalk_kernel (the same definition, the
+// same fine sweeps item for item, the same certified evaluation) for FP32
+// pairs with kappa 2, 4 or 8, one pair on a thread-block cluster of C CTAs.
+// CTA `rank` owns the block rows [rank R, (rank + 1) R), R = ceil(n / C):
+// blocks [k0, k0 + nb) and, because whole block rows are owned, the same
+// range of positions in the block-major and in the pixel layout.  It keeps
+// the KB rows of its own target blocks and the KA rows of its own source
+// blocks in shared memory; a half sweep reads the other CTAs' rows through
+// distributed shared memory and ends at a cluster barrier (KB and KA are
+// separate buffers, so one barrier per half suffices).  The evaluation runs
+// on the owned blocks as well: the kd rows of both sides go to global memory
+// (cluster barrier), each CTA gathers the marginal entries of its rows and
+// columns and its part of the support cost, and rank 0 combines the CTAs'
+// partial sums, read from their shared memory, into the bounds.  With
+// several CTAs per pair, a batch of pairs spreads over all SMs in one wave
+// instead of one CTA per SM in two.
+//   Enclosures: as in primalk_kernel, with two changes that only tighten
+// them.  The total mass is enclosed by a round-down and a round-up sum of
+// the h_i (no summation bound needed), and |h_i - mu_i| is taken from the
+// nearest-rounded difference d_i, |h_i - mu_i| <= |d_i| + 2^-53 (h_i + mu_i),
+// so sum_i w_i |mu-hat_i - mu_i| <= sum w |d| + (rel + 2^-53) sum w h
+// + 2^-53 B + slack sum w, every sum rounded up.
+// --------------------------------------------------------------------------
+constexpr int PKC_PARTS = 16;
+
+__device__ __forceinline__ double block_reduce_max(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = red[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) s = fmax(s, red[w]);
+        red[32] = s;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+template <int KK, int TH, int MINB>
+__global__ void __launch_bounds__(TH, MINB)
+primalk_cl_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
+                  const int* __restrict__ pair_ids, int C, int kb_cap, int csr_cap) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[33];
+    __shared__ double part[PKC_PARTS];
+    constexpr int q4 = KK / 4;                                // float4s per block row
+    constexpr int IPS = 4;                                    // items per step (one K' load feeds four)
+    static_assert(TH % q4 == 0 && 32 % q4 == 0, "a block row lies in one warp");
+    const int rank = (int)cl.block_rank();
+    const PairDev& P = pairs[pair_ids[blockIdx.x / C]];
+    const int N = P.N, kap = P.kappa, n = P.n, m = P.m;
+    const int R = (n + C - 1) / C, Rn = R * n;                // block rows and blocks per CTA
+    const int r0 = min(n, rank * R), r1 = min(n, r0 + R);
+    const int k0 = r0 * n, nb = (r1 - r0) * n;                // owned blocks [k0, k0 + nb)
+    const int t0 = k0 * KK, tn = nb * KK;                     // owned positions
+    float* Ks = reinterpret_cast<float*>(smem_raw);           // row w: K'[w][.]
+    float* KsT = Ks + KK * KK;                                // row w: K'[.][w]
+    float* kbB = KsT + KK * KK;                               // KB rows of the owned blocks
+    float* kbA = kbB + kb_cap;                                // KA rows of the owned blocks
+    // the plan's rows of the owned source blocks and columns of the owned
+    // target blocks, staged with offsets relative to the first owned entry
+    // (when they fit csr_cap; else read from global memory)
+    float* v_s = kbA + kb_cap;
+    float* vc_s = v_s + csr_cap;
+    int* ci_s = reinterpret_cast<int*>(vc_s + csr_cap);
+    int* ri_s = ci_s + csr_cap;
+    int* rp_s = ri_s + csr_cap;                               // Rn + 1 entries each
+    int* cp_s = rp_s + Rn + 1;
+    for (int t = threadIdx.x; t < KK * KK; t += TH) {
+        const int u = t / KK, w = t - u * KK;
+        const float kt = reinterpret_cast<const float*>(P.upK_t)[t];
+        Ks[t] = kt;
+        KsT[w * KK + u] = kt;
+    }
+    const int r_base = P.rowptr[k0], c_base = P.colptr[k0];
+    const int r_cnt = P.rowptr[k0 + nb] - r_base, c_cnt = P.colptr[k0 + nb] - c_base;
+    const bool staged = r_cnt <= csr_cap && c_cnt <= csr_cap;
+    if (staged) {
+        for (int q = threadIdx.x; q <= nb; q += TH) {
+            rp_s[q] = P.rowptr[k0 + q] - r_base;
+            cp_s[q] = P.colptr[k0 + q] - c_base;
+        }
+        const float* vt = reinterpret_cast<const float*>(P.val_t);
+        const float* vct = reinterpret_cast<const float*>(P.valc_t);
+        for (int e = threadIdx.x; e < r_cnt; e += TH) { ci_s[e] = P.colidx[r_base + e]; v_s[e] = vt[r_base + e]; }
+        for (int e = threadIdx.x; e < c_cnt; e += TH) { ri_s[e] = P.rowidx[c_base + e]; vc_s[e] = vct[c_base + e]; }
+    }
+    float* a = reinterpret_cast<float*>(P.a);
+    float* b = reinterpret_cast<float*>(P.b);
+    float* mu_b = reinterpret_cast<float*>(P.kscratch);       // block-major mu, nu (sweeps only)
+    float* nu_b = mu_b + m;
+    const float* mu_t = reinterpret_cast<const float*>(P.mu_t);
+    const float* nu_t = reinterpret_cast<const float*>(P.nu_t);
+    for (int t = threadIdx.x; t < tn; t += TH) {
+        const int tt = t0 + t;
+        const int i = blk_pixel(tt / KK, tt - (tt / KK) * KK, n, kap, N);
+        mu_b[tt] = mu_t[i];
+        nu_b[tt] = nu_t[i];
+        b[tt] = 1.0f;
+    }
+    __syncthreads();
+    const float4* Ks4 = reinterpret_cast<const float4*>(Ks);
+    const float4* KsT4 = reinterpret_cast<const float4*>(KsT);
+    const int n_own = nb * q4;                                // float4 items of the owned blocks
+    const int n_iter = (n_own + TH - 1) / TH;                 // the same for every thread of the CTA
+    const int g = threadIdx.x % q4;                           // item % q4 for every item of the thread
+    const int row0 = (threadIdx.x & 31) - g;                  // first lane of the item's block row
+    // b = 1: KB[l, u] = sum_w K'[u][w]
+    for (int it = threadIdx.x; it < n_own; it += TH) {
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int w = 0; w < KK; ++w) {
+            const float4 kv = KsT4[w * q4 + g];
+            s.x += kv.x; s.y += kv.y; s.z += kv.z; s.w += kv.w;
+        }
+        reinterpret_cast<float4*>(kbB)[it] = s;
+    }
+    cl.sync();                                                // KB rows visible to the cluster
+    for (int sweep = 0; sweep < P.sweeps; ++sweep) {
+        for (int half = 0; half < 2; ++half) {
+            // owned row (column) kl: entries [ptr[kl], ptr[kl + 1]) of idx / val
+            const int* ptr = staged ? (half == 0 ? rp_s : cp_s) : (half == 0 ? P.rowptr + k0 : P.colptr + k0);
+            const int* idx = staged ? (half == 0 ? ci_s : ri_s) : (half == 0 ? P.colidx : P.rowidx);
+            const float* val = staged ? (half == 0 ? v_s : vc_s)
+                                      : reinterpret_cast<const float*>(half == 0 ? P.val_t : P.valc_t);
+            const float4* src4 = reinterpret_cast<const float4*>(half == 0 ? mu_b : nu_b) + k0 * q4;
+            float4* dst4 = reinterpret_cast<float4*>(half == 0 ? a : b) + k0 * q4;
+            float* kin = half == 0 ? kbB : kbA;               // this CTA's rows; the others' by rank
+            float4* kout4 = reinterpret_cast<float4*>(half == 0 ? kbA : kbB);
+            const float4* Kn4 = half == 0 ? Ks4 : KsT4;       // a -> KA (rows K'[w][.]); b -> KB
+            for (int jt = 0; jt < n_iter; jt += IPS) {
+                float4 xv[IPS], s[IPS], sv[IPS], r[IPS];
+                int e0[IPS], e1[IPS];
+                int dmax = 0;
+                // the items' measure values and plan ranges first, then their
+                // gathers side by side (each item's terms in entry order)
+#pragma unroll
+                for (int q = 0; q < IPS; ++q) {
+                    const int it = threadIdx.x + (jt + q) * TH;
+                    s[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    r[q] = s[q];
+                    sv[q] = s[q];
+                    e0[q] = e1[q] = 0;
+                    if (it < n_own) {
+                        sv[q] = src4[it];
+                        e0[q] = ptr[it / q4];
+                        e1[q] = ptr[it / q4 + 1];
+                        dmax = max(dmax, e1[q] - e0[q]);
+                    }
+                }
+                for (int d = 0; d < dmax; ++d) {
+#pragma unroll
+                    for (int q = 0; q < IPS; ++q) {
+                        const int e = e0[q] + d;
+                        if (e < e1[q]) {
+                            const int l = idx[e], owner = l / Rn;
+                            const float4* peer = reinterpret_cast<const float4*>(cl.map_shared_rank(kin, owner));
+                            const float4 kv = peer[(l - owner * Rn) * q4 + g];
+                            const float v = val[e];
+                            r[q].x = fmaf(v, kv.x, r[q].x);
+                            r[q].y = fmaf(v, kv.y, r[q].y);
+                            r[q].z = fmaf(v, kv.z, r[q].z);
+                            r[q].w = fmaf(v, kv.w, r[q].w);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < IPS; ++q) {
+                    const int it = threadIdx.x + (jt + q) * TH;
+                    xv[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (it < n_own) {
+                        xv[q] = make_float4(ipf_div(sv[q].x, r[q].x), ipf_div(sv[q].y, r[q].y),
+                                            ipf_div(sv[q].z, r[q].z), ipf_div(sv[q].w, r[q].w));
+                        dst4[it] = xv[q];
+                    }
+                }
+                for (int w4 = 0; w4 < q4; ++w4) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float4 kv = Kn4[(4 * w4 + j) * q4 + g];
+#pragma unroll
+                        for (int q = 0; q < IPS; ++q) {
+                            const float xs = j == 0 ? xv[q].x : j == 1 ? xv[q].y : j == 2 ? xv[q].z : xv[q].w;
+                            const float x = __shfl_sync(0xffffffffu, xs, row0 + w4);
+                            s[q].x = fmaf(kv.x, x, s[q].x);
+                            s[q].y = fmaf(kv.y, x, s[q].y);
+                            s[q].z = fmaf(kv.z, x, s[q].z);
+                            s[q].w = fmaf(kv.w, x, s[q].w);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < IPS; ++q) {
+                    const int it = threadIdx.x + (jt + q) * TH;
+                    if (it < n_own) kout4[it] = s[q];
+                }
+            }
+            cl.sync();                                        // the next half reads the new rows
+        }
+    }
+    if (P.a_out || P.b_out)
+        for (int t = threadIdx.x; t < tn; t += TH) {
+            const int tt = t0 + t;
+            const int i = blk_pixel(tt / KK, tt - (tt / KK) * KK, n, kap, N);
+            if (P.a_out) P.a_out[i] = widen_f32(a[tt]);
+            if (P.b_out) P.b_out[i] = widen_f32(b[tt]);
+        }
+    // ---- certified evaluation on the owned blocks ---------------------------
+    // kd rows of both sides: side 0 (mu-hat) kd[l, u] = sum_w K'[u, w] b[l, w]
+    // for the owned l, side 1 (nu-hat) kd[k, v] = sum_w K'[w, v] a[k, w] for
+    // the owned k, by the compensated dot product Dot2 in FP32 (hi + lo)
+    double* kd0 = P.kscratch;                                 // mu_b, nu_b are done (last barrier)
+    double* kd1 = P.kscratch + m;
+    for (int side = 0; side < 2; ++side) {
+        const float* oth = side == 0 ? b : a;
+        const float4* K4 = side == 0 ? KsT4 : Ks4;            // row w over the output offsets
+        double2* kd2 = reinterpret_cast<double2*>(side == 0 ? kd0 : kd1);
+        for (int it = threadIdx.x; it < n_own; it += TH) {
+            const int git = k0 * q4 + it;
+            const float* xr = oth + (size_t)(git / q4) * KK;
+            float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int w = 0; w < KK; ++w) {
+                const float x = xr[w];
+                const float4 kv = K4[w * q4 + g];
+                const float kc[4] = {kv.x, kv.y, kv.z, kv.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float pr = kc[j] * x;
+                    const float pe = fmaf(kc[j], x, -pr);
+                    float s, t;
+                    two_sum_f(hi[j], pr, s, t);
+                    hi[j] = s;
+                    lo[j] += t + pe;
+                }
+            }
+            kd2[2 * git] = make_double2(widen_f32(hi[0]) + widen_f32(lo[0]), widen_f32(hi[1]) + widen_f32(lo[1]));
+            kd2[2 * git + 1] = make_double2(widen_f32(hi[2]) + widen_f32(lo[2]), widen_f32(hi[3]) + widen_f32(lo[3]));
+        }
+    }
+    // the owned rows (side 0) and columns (side 1) of the plan: local index
+    // kl = k - k0, entries [ptr[kl], ptr[kl + 1]) of idx and of the FP64 values
+    const int* ptr_s[2] = {staged ? rp_s : P.rowptr + k0, staged ? cp_s : P.colptr + k0};
+    const int* idx_s[2] = {staged ? ci_s : P.colidx, staged ? ri_s : P.rowidx};
+    const double* v64_s[2] = {staged ? P.val + r_base : P.val, staged ? P.valc + c_base : P.valc};
+    int deg = 0;                                              // largest row / column degree (owned)
+    for (int q = threadIdx.x; q < nb; q += TH)
+        deg = max(deg, max(ptr_s[0][q + 1] - ptr_s[0][q], ptr_s[1][q + 1] - ptr_s[1][q]));
+    const double deg_cta = block_reduce_max((double)deg, red);
+    cl.sync();                                                // every CTA's kd rows visible
+    // marginal entries of the owned rows (side 0) and columns (side 1):
+    // h = x r with r = sum_e pi~_e kd[idx_e, u] (FP64 FMAs), x the own scaling
+    double sums[12];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const int* ptr = ptr_s[side];
+        const int* idx = idx_s[side];
+        const double* val = v64_s[side];
+        const double* meas = side == 0 ? P.mu : P.nu;
+        const float* own = side == 0 ? a : b;
+        const double* kd = side == 0 ? kd0 : kd1;
+        double s_lo = 0.0, s_hi = 0.0, dsum = 0.0, whsum = 0.0, rsum = 0.0;
+        float xm = 0.0f;
+        for (int t = threadIdx.x; t < tn; t += TH) {
+            const int tt = t0 + t;
+            const int k = tt / KK, u = tt - (tt / KK) * KK;
+            double r = 0.0;
+            for (int e = ptr[k - k0]; e < ptr[k - k0 + 1]; ++e) r = fma(val[e], kd[idx[e] * KK + u], r);
+            const float xf = own[tt];
+            const double h = widen_f32(xf) * r;
+            s_lo = __dadd_rd(s_lo, h);
+            s_hi = __dadd_ru(s_hi, h);
+            const int i = blk_pixel(k, u, n, kap, N);
+            const double ad = fabs(h - meas[i]);              // nearest-rounded |h - mu_i|
+            const double w = tv_weight_hi_fast(i / N, i - (i / N) * N, N, P.p);
+            dsum = __fma_ru(w, ad, dsum);
+            whsum = __fma_ru(w, h, whsum);
+            rsum += ad;
+            xm = fmaxf(xm, xf);
+        }
+        sums[6 * side + 0] = block_reduce_rd(s_lo, red);
+        sums[6 * side + 1] = block_reduce_ru(s_hi, red);
+        sums[6 * side + 2] = block_reduce_ru(dsum, red);
+        sums[6 * side + 3] = block_reduce_ru(whsum, red);
+        sums[6 * side + 4] = block_reduce_rn(rsum, red);
+        sums[6 * side + 5] = block_reduce_max(widen_f32(xm), red);
+    }
+    // B: the SumPool pass's per-block bounds of sum_{i in block} w_i mu_i (owned blocks)
+    double bmu = 0.0, bnu = 0.0;
+    for (int q = threadIdx.x; q < nb; q += TH) {
+        bmu = __dadd_ru(bmu, P.mu_w_hi[k0 + q]);
+        bnu = __dadd_ru(bnu, P.nu_w_hi[k0 + q]);
+    }
+    const double B_mu_cta = block_reduce_ru(bmu, red);
+    const double B_nu_cta = block_reduce_ru(bnu, red);
+    // cost of the fitted plan over its support (owned source positions), as primalk_kernel
+    const float* tab = reinterpret_cast<const float*>(P.ctab_hi);
+    double cost = 0.0;
+    for (int t = threadIdx.x; t < tn; t += TH) {
+        const int tt = t0 + t;
+        const int k = tt / KK, u = tt - (tt / KK) * KK;
+        const float a_ku = a[tt];
+        const float* kh = KsT + u;                            // K'[u][v] = KsT[v KK + u]
+        for (int e = ptr_s[0][k - k0]; e < ptr_s[0][k - k0 + 1]; ++e) {
+            const int l = idx_s[0][e];
+            const int rr = kap * (k / n - l / n) + u / kap, c0 = kap * (k % n - l % n) + u % kap;
+            const float* br = b + l * KK;
+            float inner = 0.0f;
+            for (int v1 = 0; v1 < kap; ++v1) {
+                const float* trow = tab + abs(rr - v1) * N;
+                for (int v2 = 0; v2 < kap; ++v2) {
+                    const int v = v1 * kap + v2;
+                    inner = fma_ru(mul_ru(kh[v * KK], br[v]), trow[abs(c0 - v2)], inner);
+                }
+            }
+            cost = __fma_ru(v64_s[0][e], widen_f32(mul_ru(a_ku, inner)), cost);
+        }
+    }
+    const double cost_cta = block_reduce_ru(cost, red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < 12; ++q) part[q] = sums[q];
+        part[12] = B_mu_cta;
+        part[13] = B_nu_cta;
+        part[14] = cost_cta;
+        part[15] = deg_cta;
+    }
+    cl.sync();                                                // partials published; b no longer read
+    if (rank == 0 && threadIdx.x == 0) {
+        double tot[PKC_PARTS];
+#pragma unroll
+        for (int q = 0; q < PKC_PARTS; ++q) tot[q] = 0.0;
+        for (int r = 0; r < C; ++r) {
+            const double* pr = cl.map_shared_rank(part, r);
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const int o = 6 * side;
+                tot[o + 0] = __dadd_rd(tot[o + 0], pr[o + 0]);
+                tot[o + 1] = __dadd_ru(tot[o + 1], pr[o + 1]);
+                tot[o + 2] = __dadd_ru(tot[o + 2], pr[o + 2]);
+                tot[o + 3] = __dadd_ru(tot[o + 3], pr[o + 3]);
+                tot[o + 4] += pr[o + 4];
+                tot[o + 5] = fmax(tot[o + 5], pr[o + 5]);
+            }
+            tot[12] = __dadd_ru(tot[12], pr[12]);
+            tot[13] = __dadd_ru(tot[13], pr[13]);
+            tot[14] = __dadd_ru(tot[14], pr[14]);
+            tot[15] = fmax(tot[15], pr[15]);
+        }
+        // relative enclosure of each entry (Dot2 in FP32, the gather and the
+        // product in FP64) and the absolute one of each kd, as primalk_kernel
+        const double g2 = (2.0 * KK * 0x1p-24) / (1.0 - 2.0 * KK * 0x1p-24);
+        const double rel = __dadd_ru(__dmul_ru(2.0, __dmul_ru(g2, g2)), (tot[15] + 3.0) * 0x1p-52);
+        const double kd_abs = (double)KK * 0x1p-140;
+        const double w_sum_hi = __dmul_ru((double)m, tv_weight_hi(0, 0, N, P.p));   // >= sum_i w_i
+        const double rel_d = __dadd_ru(rel, 0x1p-53);
+        double s_lo = 0.0, s_hi = HUGE_VAL, A[2];
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const int o = 6 * side;
+            const double B = tot[12 + side];
+            const double slack = __dadd_ru(__dmul_ru(tot[o + 5], kd_abs), 0x1p-1000);
+            double As = __fma_ru(rel_d, tot[o + 3], tot[o + 2]);
+            As = __fma_ru(0x1p-53, B, As);
+            A[side] = __fma_ru(slack, w_sum_hi, As);
+            const double ms = __dmul_ru((double)m, slack);
+            s_lo = fmax(s_lo, __dsub_rd(__dmul_rd(tot[o + 0], __dsub_rd(1.0, rel)), ms));
+            s_hi = fmin(s_hi, __dadd_ru(__dmul_ru(tot[o + 1], __dadd_ru(1.0, rel)), ms));
+        }
+        const double p = P.p;
+        const double inv_hi = s_lo > 0.0 ? __drcp_ru(s_lo) : HUGE_VAL;   // >= 1 / s
+        const double inv_lo = __drcp_rd(s_hi);                          // <= 1 / s
+        const double dinv = fmax(0.0, fmax(__dsub_ru(inv_hi, 1.0), __dsub_ru(1.0, inv_lo)));
+        const double tv_mu = __fma_ru(tot[12], dinv, __dmul_ru(A[0], inv_hi));
+        const double tv_nu = __fma_ru(tot[13], dinv, __dmul_ru(A[1], inv_hi));
+        const double scale = (p == 1.0) ? 1.0 : (p == 2.0 ? 2.0 : __dmul_ru(pow(2.0, p - 1.0), 1.0 + 0x1p-49));
+        const double dmu = root_p_ru(__dmul_ru(scale, tv_mu), p);
+        const double dnu = root_p_ru(__dmul_ru(scale, tv_nu), p);
+        const double w_hat_p = __dmul_ru(tot[14], inv_hi);
+        PairOut& O = outs[P.out_index];
+        O.w_hat_p = w_hat_p;
+        O.delta_mu = dmu;
+        O.delta_nu = dnu;
+        O.ub_primal = __dadd_ru(__dadd_ru(root_p_ru(w_hat_p, p), dmu), dnu);
+        O.ipf_residual = tot[4] + tot[10];
+        O.sweeps_done = P.sweeps;
+    }
+    // leave a, b in the pixel layout of the other passes: the owned range maps
+    // onto itself, staged through this CTA's KB / KA rows
+    for (int side = 0; side < 2; ++side) {
+        float* x = side == 0 ? a : b;
+        float* tmp = side == 0 ? kbB : kbA;
+        for (int t = threadIdx.x; t < tn; t += TH) tmp[t] = x[t0 + t];
+        __syncthreads();
+        for (int t = threadIdx.x; t < tn; t += TH) {
+            const int tt = t0 + t;
+            x[blk_pixel(tt / KK, tt - (tt / KK) * KK, n, kap, N)] = tmp[t];
+        }
+    }
+    cl.sync();                                                // rank 0 has read every partial
+}
+
+int launch_primalk_cl(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs, int kappa,
+                      int C, int variant, int n_max, cudaStream_t stream) {
+    if (n_pairs <= 0) return QWB_OK;
+    if ((kappa != 2 && kappa != 4 && kappa != 8) || C < 1 || C > 8 || variant < 0 || variant > 2)
+        return QWB_ERR_UNSUPPORTED;
+    const int kk = kappa * kappa;
+    const int R = (n_max + C - 1) / C;
+    const int kb_cap = R * n_max * kk;                        // floats per KB / KA array
+    // staged plan: a basic plan has at most 2M - 1 entries, about 2 per
+    // block; room for twice that per CTA (a CTA whose rows hold more reads
+    // its part of the plan from global memory)
+    const int csr_cap = 4 * R * n_max;
+    const size_t smem = sizeof(float) * (2 * (size_t)kk * kk + 2 * (size_t)kb_cap) +
+                        (size_t)csr_cap * 2 * (sizeof(float) + sizeof(int)) + 2 * sizeof(int) * (size_t)(R * n_max + 1);
+    if (smem + 1024 > 227 * 1024) return QWB_ERR_UNSUPPORTED;   // 1 KB: the kernel's static shared memory
+    // variants: threads per CTA and the CTAs per SM the register budget allows
+    static const int threads_of[3] = {256, 128, 64};
+    auto run = [&](auto kern) -> int {
+        QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(n_pairs * C));
+        cfg.blockDim = dim3((unsigned)threads_of[variant]);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        QWB_CUDA(cudaLaunchKernelEx(&cfg, kern, pairs_d, outs_d, pair_ids, C, kb_cap, csr_cap));
+        QWB_LAUNCHED();
+        return QWB_OK;
+    };
+    switch (kk * 4 + variant) {
+        case 4 * 4 + 0: return run(primalk_cl_kernel<4, 256, 2>);
+        case 4 * 4 + 1: return run(primalk_cl_kernel<4, 128, 5>);
+        case 4 * 4 + 2: return run(primalk_cl_kernel<4, 64, 10>);
+        case 16 * 4 + 0: return run(primalk_cl_kernel<16, 256, 2>);
+        case 16 * 4 + 1: return run(primalk_cl_kernel<16, 128, 5>);
+        case 16 * 4 + 2: return run(primalk_cl_kernel<16, 64, 10>);
+        case 64 * 4 + 0: return run(primalk_cl_kernel<64, 256, 2>);
+        case 64 * 4 + 1: return run(primalk_cl_kernel<64, 128, 5>);
+        default: return run(primalk_cl_kernel<64, 64, 10>);
+    }
+}
+
+// --------------------------------------------------------------------------
 // ipf_fine: the fine FP32 IPF sweeps of the primal pass (Sec. 3.4, IPF
 // paragraph; Alg. 4), a = mu / (pi-hat b), b = nu / (pi-hat^T a), for large
 // 2-D pairs (block side kappa 4 or 8) on a thread-block cluster of C CTAs

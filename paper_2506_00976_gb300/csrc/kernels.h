@@ -114,6 +114,11 @@ int launch_ipf_stream(const PairDev* pairs_d, const int* pair_ids, int n_pairs, 
 // all_kappa4: every pair of the launch has kappa 4, which selects the register-row kernel)
 int launch_primalk(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs, int kappa_max,
                    int M_max, int nnz_max, int m_max, bool all_kappa4, bool f64, cudaStream_t stream);
+// The same pass for FP32 pairs that all have block side kappa (2, 4 or 8),
+// one pair on a cluster of C (1..8) CTAs; variant 0, 1, 2: 256, 128, 64
+// threads per CTA; n_max >= every pair's coarse side n.
+int launch_primalk_cl(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs, int kappa,
+                      int C, int variant, int n_max, cudaStream_t stream);
 // Fine FP32 IPF sweeps on clusters of C CTAs per pair (2-D, kappa 4 or 8,
 // FP32, C divides every pair's n); the pairs have fine_ext = 1.
 int launch_ipf_fine(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int kappa, int C,

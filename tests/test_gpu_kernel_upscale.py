@@ -221,3 +221,88 @@ def test_batch_kernel_scalings_layout():
     ratio = (a.cpu().numpy() / mu).reshape(N // kappa, kappa, N // kappa, kappa)
     spread = ratio.max(axis=(1, 3)) - ratio.min(axis=(1, 3))
     assert np.all(spread <= 1e-9 * ratio.max(axis=(1, 3)))
+
+
+def _kernel_batch(cases, K, kappa, sweeps, batched, form, seed=47):
+    """Run the primal pass of a batch whose pairs all take the kernel K;
+    form: None (the autotuner's choice) or (C, threads)."""
+    mus, nus, probs = [], [], []
+    for t, (N, p, cls) in enumerate(cases):
+        mus.append(T(synth.make_measure(N, cls, seed, 2 * t)))
+        nus.append(T(synth.make_measure(N, cls, seed, 2 * t + 1)))
+        probs.append((N, kappa, p))
+    with api.Batch(probs, ipf_sweeps=sweeps, prec="mixed", flags=api.QWB_FLAG_NO_DUAL) as bt:
+        bt.set_upscale_kernel(kappa, K)
+        if form is not None:
+            bt.set_upscale_cluster(*form)
+        bt.coarse(mus, nus, batched=batched)
+        bt.solve()
+        bt.fine(mus, nus, batched=batched)
+        res = bt.results()
+        scal = [bt.fine_scalings(t) for t in range(len(cases))]
+        plans = [bt.coarse_plan(t) for t in range(len(cases))]
+        tuning = bt.tuning()
+    return res, scal, plans, tuning
+
+
+@pytest.mark.parametrize("kappa,cases,forms", [
+    (4, [(16, 2.0, "gauss"), (32, 2.0, "blobs3"), (24, 1.0, "field"), (40, 2.0, "cauchy")],
+     [(1, 256), (2, 128), (4, 128), (4, 64), (8, 64)]),
+    (8, [(32, 2.0, "field"), (16, 1.0, "gauss"), (48, 2.0, "white")], [(1, 128), (2, 64), (4, 128), (8, 64)]),
+    (2, [(16, 2.0, "blobs3"), (10, 2.0, "gauss")], [(2, 256), (4, 64), (8, 128)]),
+])
+def test_batch_kernel_cluster_form(kappa, cases, forms):
+    """The cluster form of the general-kernel primal pass (one pair on a
+    cluster of C CTAs that split its block rows).  Its fine sweeps are those
+    of the one-CTA kernel item for item, so the scalings agree bit for bit;
+    its certified sums run in another order with tighter enclosures, so its
+    bounds are no larger than the one-CTA kernel's and agree with the
+    oracle's on the same coarse plan within the usual floors; batched equals
+    one pair per launch bit for bit.  Covers CTAs that own no block row (C > n) and
+    uneven row splits (n = 6, 10, 5)."""
+    K = O.gaussian_kernel(kappa, 1.0) if kappa != 8 else _random_kernel(8, 5)
+    sweeps = 20
+    r0, s0, plans, _ = _kernel_batch(cases, K, kappa, sweeps, True, (0, 128))
+    for form in forms:
+        rb, sb, _, _ = _kernel_batch(cases, K, kappa, sweeps, True, form)
+        rp, sp, _, _ = _kernel_batch(cases, K, kappa, sweeps, False, form)
+        for t, (N, p, cls) in enumerate(cases):
+            for side in range(2):
+                assert torch.equal(sb[t][side], s0[t][side]), (form, t, side)
+                assert torch.equal(sp[t][side], s0[t][side]), (form, t, side)
+            for key in ("ub_primal", "w_hat_p", "delta_mu", "delta_nu"):
+                assert rb[t][key] == rp[t][key], (form, t, key)
+            # the plan cost differs by its summation order only; the TV terms
+            # drop the one-CTA kernel's summation bound on the total mass
+            # (about 43 2^-52 of the weighted mass B) and add 2^-53 of the
+            # weighted sums, so they come out no larger
+            assert abs(rb[t]["w_hat_p"] - r0[t]["w_hat_p"]) <= 1e-12 * r0[t]["w_hat_p"], (form, t)
+            for key in ("ub_primal", "delta_mu", "delta_nu"):
+                assert rb[t][key] <= r0[t][key] * (1 + 1e-12), (form, t, key)
+            mu = synth.make_measure(N, cls, 47, 2 * t)
+            nu = synth.make_measure(N, cls, 47, 2 * t + 1)
+            ref = O.ub_primal_K(mu, nu, N, kappa, p, K, xi=0.0, max_sweeps=sweeps, plan_c=plans[t])
+            _check(rb[t], ref, mu, nu, N, kappa, p, "mixed", plans[t])
+            if N <= 16:
+                W = O.wasserstein_exact(mu, nu, N, p)
+                assert W <= rb[t]["ub_primal"] * (1 + 1e-12), (form, t)
+
+
+def test_batch_kernel_cluster_tuned_and_refused():
+    """The autotuner times the one-CTA and the cluster forms and reports
+    them; the cluster form is refused for FP64 batches and unknown shapes."""
+    cases = [(32, 2.0, "gauss"), (32, 2.0, "field")]
+    K = O.gaussian_kernel(4, 1.0)
+    _, _, _, tuning = _kernel_batch(cases, K, 4, 5, True, None)
+    uk = tuning["upscale_kernel"]
+    assert "single" in uk["candidates_ms"] and any(k.startswith("cluster") for k in uk["candidates_ms"])
+    N = 16
+    mu, nu = T(synth.make_measure(N, "gauss", 48, 0)), T(synth.make_measure(N, "gauss", 48, 1))
+    with api.Batch([(N, 4, 2.0)], ipf_sweeps=3, prec="f64") as bt:
+        bt.set_upscale_kernel(4, K)
+        with pytest.raises(RuntimeError):
+            bt.set_upscale_cluster(4, 128)
+        with pytest.raises(RuntimeError):
+            bt.set_upscale_cluster(3, 128)
+        with pytest.raises(RuntimeError):
+            bt.set_upscale_cluster(4, 96)
