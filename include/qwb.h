@@ -293,9 +293,9 @@ int qwb_ctransform_shape(qwb_ctx* ctx, int32_t N, int32_t d, double p, const dou
  *   array's device address (cudaGetSymbolAddress) and, under lazy module
  *   loading (the CUDA default), loads the library's kernels, which itself
  *   takes device memory.  Make that first call (a warm-up call will do)
- *   before any stream capture and while device memory can still be
- *   allocated.  The launch plan reaches the device as kernel arguments; no
- *   call copies host memory.  Asynchronous on `stream`.
+ *   while device memory can still be allocated.  The launch plan reaches
+ *   the device as kernel arguments; no call copies host memory.
+ *   Asynchronous on `stream`.
  * Errors: INVALID_ARG (null pointer, p < 1), UNSUPPORTED (N > 256), CUDA. */
 int qwb_ctransform_noalloc(int32_t N, double p, const double* h_d, double* out_d, void* stream);
 

@@ -17,7 +17,7 @@
 //   * the first call on a device does the set-up: it looks up the array's
 //     device address and, under lazy module loading (the CUDA default), loads
 //     the kernels, which itself takes device memory.  Make that first call
-//     before any stream capture and while memory can still be allocated.
+//     while memory can still be allocated.
 //
 // The launch plan (pair descriptor and work items) is written into the array
 // by a set-up kernel from values passed by value, so no call copies host
