@@ -380,12 +380,16 @@ int qwb_batch_coarse_plan(qwb_batch* batch, int32_t pair, int32_t* rowptr_h, int
 int qwb_batch_coarse_potentials(qwb_batch* batch, int32_t pair, double* f_h, double* g_h);
 /* Where the fine FP32 IPF sweeps of the batch's 2-D FP32 pairs with block side
  * 4 or 8 run (Sec. 3.4, IPF paragraph; Alg. 4; the values do not depend on
- * it): C = 0 inside the primal-pass kernel, one CTA per pair; C = 2, 4, 8, 16
- * on a thread-block cluster of (at most) C CTAs per pair that split the coarse
- * blocks and exchange block sums through distributed shared memory -- the
- * form that keeps HBM busy for large grids.  Each group of pairs with one
- * block side takes the largest power of two <= C dividing all its coarse
- * sides.  C | QWB_IPF_BULK (C = 2..16) selects the form that stages the
+ * it): C = 0 inside the primal-pass kernel, one CTA per pair; C = 2, 3, 4, 8,
+ * 16 on a thread-block cluster of (at most) C CTAs per pair that split the
+ * coarse block rows and exchange block sums through distributed shared
+ * memory -- the form that keeps HBM busy for large grids.  Each group of
+ * pairs with one block side takes, for C = 3, three CTAs if every coarse side
+ * is at least 3 (the rows split as ceil(n / 3), the last CTA takes the rest),
+ * else the largest power of two <= C dividing all its coarse sides.
+ * C | QWB_IPF_WIDE runs that form with CTAs of 512 threads instead of 256
+ * (twice the loads in flight per CTA, one CTA per SM).
+ * C | QWB_IPF_BULK (C = 2, 4, 8, 16) selects the form that stages the
  * source values by bulk copies (cp.async.bulk into a ring of shared-memory
  * stages, completion on mbarriers, every wait bounded) for groups whose pairs
  * share N; a timed-out wait makes qwb_batch_results return TIMEOUT.
@@ -393,6 +397,7 @@ int qwb_batch_coarse_potentials(qwb_batch* batch, int32_t pair, double* f_h, dou
  * synchronises the device and drops the batch's captured fine-pass graphs.
  * Errors: INVALID_ARG, CUDA. */
 #define QWB_IPF_BULK 32
+#define QWB_IPF_WIDE 64
 int qwb_batch_set_ipf_cluster(qwb_batch* batch, int32_t C);
 /* Upscale the coarse plans of the batch's 2-D pairs with block side kappa by
  * the general kernel K_d (Sec. 3.4, eq. coupling tensor upscale; layout,

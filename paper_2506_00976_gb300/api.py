@@ -57,6 +57,7 @@ def _ptr(t):
 
 
 QWB_IPF_BULK = 32   # Batch.set_ipf_cluster(C | QWB_IPF_BULK): the bulk-copy staged sweeps
+QWB_IPF_WIDE = 64   # Batch.set_ipf_cluster(C | QWB_IPF_WIDE): the register form with 512-thread CTAs
 
 
 def problem(N, kappa, p, d=2):

@@ -217,11 +217,14 @@ struct qwb_batch {
     // largest power of two <= ipf_C that divides all its coarse sides
     // (stream: the bulk-copy variant ipf_stream_kernel, for groups whose pairs
     // share N; n_same, N_same: that common coarse and fine side, else 0)
-    struct IpfGroup { int kappa, off, cnt, M_max, gcd_n, C, n_same, N_same; bool stream; };
+    // (wide: CTAs of 512 threads instead of 256, register form only; n_min:
+    // the smallest coarse side, which bounds a cluster size that need not
+    // divide the sides)
+    struct IpfGroup { int kappa, off, cnt, M_max, gcd_n, C, n_same, N_same; bool stream; int n_min; bool wide; };
     std::vector<IpfGroup> ipf_groups;
     std::vector<int> ipf_group_of;      // per pair: its group or -1
     int* ipf_ids_d = nullptr;
-    int ipf_C = 0;                      // | QWB_IPF_BULK: the bulk-copy form
+    int ipf_C = 0;                      // | QWB_IPF_BULK: the bulk-copy form; | QWB_IPF_WIDE: 512 threads
     int* dev_err = nullptr;             // device error word of bounded waits (0 = none)
     unsigned long long wait_ns = 0;     // limit of every bounded device wait (QWB_WAIT_TIMEOUT_MS)
     int fault_skip_chunk = -1;          // QWB_FAULT ipf_bulk_skip_chunk (tests), else -1
@@ -342,7 +345,7 @@ static std::vector<int> build_ipf_groups(qwb_batch* b) {
     std::vector<int> ipf_ids;
     if (b->f64) return ipf_ids;
     for (int kap : {4, 8}) {
-        qwb_batch::IpfGroup G{kap, (int)ipf_ids.size(), 0, 0, 0, 0, -1, -1, false};
+        qwb_batch::IpfGroup G{kap, (int)ipf_ids.size(), 0, 0, 0, 0, -1, -1, false, 1 << 30, false};
         for (int t = 0; t < b->n; ++t) {
             if (dim_of(b->probs[t]) != 2 || b->probs[t].kappa != kap || b->upk_on[t]) continue;
             const int nn = b->probs[t].N / kap;
@@ -352,6 +355,7 @@ static std::vector<int> build_ipf_groups(qwb_batch* b) {
             while (y) { const int r = x % y; x = y; y = r; }
             G.gcd_n = x;
             G.M_max = std::max(G.M_max, nn * nn);
+            G.n_min = std::min(G.n_min, nn);
             b->ipf_group_of[t] = (int)b->ipf_groups.size();
             ipf_ids.push_back(t);
             ++G.cnt;
@@ -367,7 +371,7 @@ static int launch_ipf_group(qwb_batch* b, const qwb_batch::IpfGroup& G, const in
     if (G.stream)
         return launch_ipf_stream(b->pairs_d, ids, cnt, G.kappa, G.C, G.n_same, G.N_same, b->dev_err, b->wait_ns,
                                  b->fault_skip_chunk, s);
-    return launch_ipf_fine(b->pairs_d, ids, cnt, G.kappa, G.C, M, 0, s);
+    return launch_ipf_fine(b->pairs_d, ids, cnt, G.kappa, G.C, M, 0, s, G.wide ? 512 : 256);
 }
 
 static int apply_ipf_choice(qwb_batch* b, int C) {
@@ -375,9 +379,14 @@ static int apply_ipf_choice(qwb_batch* b, int C) {
     const int Cs = C & 31;
     for (auto& G : b->ipf_groups) {
         int c = 1;
-        while (c * 2 <= Cs && c * 2 <= 16 && G.gcd_n % (c * 2) == 0) c *= 2;
+        if (Cs == 3) {
+            c = G.n_min >= 3 ? 3 : 1;        // block rows split unevenly: no divisibility needed
+        } else {
+            while (c * 2 <= Cs && c * 2 <= 16 && G.gcd_n % (c * 2) == 0) c *= 2;
+        }
         G.C = c >= 2 ? c : 0;
         G.stream = (C & QWB_IPF_BULK) && G.C > 0 && G.n_same > 0 && G.N_same > 0;
+        G.wide = (C & QWB_IPF_WIDE) && G.C > 0 && !G.stream;
     }
     for (int t = 0; t < b->n; ++t) {
         const int g = b->ipf_group_of[t];
@@ -1051,8 +1060,9 @@ static int tune_ctransform(qwb_batch* b, cudaStream_t s) {
     return QWB_OK;
 }
 
-// Fine IPF: sweeps inside primal_kernel (C = 0) or on clusters of 2, 4, 8
-// CTAs per pair, timed as the whole primal pass.
+// Fine IPF: sweeps inside primal_kernel (C = 0) or on clusters of 2, 4, 8, 16
+// CTAs per pair (256 threads, or 512 for C = 2, 4; or the bulk-copy form),
+// timed as the whole primal pass.
 static int tune_ipf(qwb_batch* b, cudaStream_t s) {
     TuneEntry* e = b->tune;
     if (!b->ctx->autotune || !e || e->ipf_done || !b->ev_ok || (b->flags & QWB_FLAG_NO_PRIMAL) ||
@@ -1066,13 +1076,17 @@ static int tune_ipf(qwb_batch* b, cudaStream_t s) {
     rep << "{";
     double best = 1e30;
     int bestC = 0;
-    for (int C : {0, 2, 4, 8, 16, QWB_IPF_BULK | 2, QWB_IPF_BULK | 4, QWB_IPF_BULK | 8, QWB_IPF_BULK | 16}) {
+    // (three CTAs per pair measured slower than four on every workload tried:
+    // settable, not timed)
+    for (int C : {0, 2, 4, 8, 16, QWB_IPF_WIDE | 2, QWB_IPF_WIDE | 4, QWB_IPF_BULK | 2, QWB_IPF_BULK | 4,
+                  QWB_IPF_BULK | 8, QWB_IPF_BULK | 16}) {
         int st = apply_ipf_choice(b, C);
         if (st) return st;
         if (C > 0) {
             bool any = false;
             for (const auto& G : b->ipf_groups)
-                any |= G.C == (C & 31) && G.stream == ((C & QWB_IPF_BULK) != 0);
+                any |= G.C == (C & 31) && G.stream == ((C & QWB_IPF_BULK) != 0) &&
+                       G.wide == ((C & QWB_IPF_WIDE) != 0);
             if (!any) continue;                  // no group takes this size / form
         }
         double ms;
@@ -1085,7 +1099,7 @@ static int tune_ipf(qwb_batch* b, cudaStream_t s) {
         }, &ms);
         if (st) return st;
         rep << (C ? ", " : "") << "\""
-            << ((C & QWB_IPF_BULK) ? "bulk" : "cluster")
+            << ((C & QWB_IPF_BULK) ? "bulk" : (C & QWB_IPF_WIDE) ? "wide" : "cluster")
             << (C & 31) << "\": " << ms;
         if (ms < best) { best = ms; bestC = C; }
     }
@@ -1702,12 +1716,12 @@ int qwb_batch_coarse_potentials(qwb_batch* b, int32_t pair, double* f_h, double*
 
 int qwb_batch_set_ipf_cluster(qwb_batch* b, int32_t C) {
     const int Cs = C & 31, form = C & ~31;
-    if (!b || (Cs != 0 && Cs != 2 && Cs != 4 && Cs != 8 && Cs != 16) ||
-        (form != 0 && form != QWB_IPF_BULK) ||
-        (form != 0 && Cs == 0))
+    if (!b || (Cs != 0 && Cs != 2 && Cs != 3 && Cs != 4 && Cs != 8 && Cs != 16) ||
+        (form != 0 && form != QWB_IPF_BULK && form != QWB_IPF_WIDE) ||
+        (form != 0 && Cs == 0) || (form == QWB_IPF_BULK && Cs == 3))
         return fail(QWB_ERR_INVALID_ARG,
-                    "qwb_batch_set_ipf_cluster: C must be 0, 2, 4, 8 or 16, the last four optionally with one of "
-                    "QWB_IPF_BULK");
+                    "qwb_batch_set_ipf_cluster: C must be 0, 2, 3, 4, 8 or 16, the others than 0 optionally with "
+                    "QWB_IPF_WIDE, and 2, 4, 8, 16 with QWB_IPF_BULK");
     QWB_CUDA(cudaSetDevice(b->ctx->device));
     QWB_CUDA(cudaDeviceSynchronize());
     // captured fine passes hold the previous launch configuration

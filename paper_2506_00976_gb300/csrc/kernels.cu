@@ -2295,8 +2295,10 @@ int launch_primalk_cl(const PairDev* pairs_d, PairOut* outs_d, const int* pair_i
 // ipf_fine: the fine FP32 IPF sweeps of the primal pass (Sec. 3.4, IPF
 // paragraph; Alg. 4), a = mu / (pi-hat b), b = nu / (pi-hat^T a), for large
 // 2-D pairs (block side kappa 4 or 8) on a thread-block cluster of C CTAs
-// per pair.  CTA `rank` owns the coarse blocks [rank M/C, (rank+1) M/C)
-// (n/C whole block rows, so its fine pixels are contiguous rows): it streams
+// per pair.  CTA `rank` owns the coarse block rows [rank R, (rank+1) R),
+// R = ceil(n / C), i.e. the blocks [rank R n, (rank+1) R n) clipped to M
+// (whole block rows, so its fine pixels are contiguous rows; the last CTAs
+// may own fewer rows or none): it streams
 // their pixels, keeps their block sums in its shared memory and reads the
 // other CTAs' block sums through distributed shared memory for the coarse
 // products r = kappa^-4 pi~ B and s = kappa^-4 pi~^T A.  Each half sweep
@@ -2309,7 +2311,7 @@ int launch_primalk_cl(const PairDev* pairs_d, PairOut* outs_d, const int* pair_i
 // the same number of half sweeps and arrives once per half sweep, so the
 // barrier cannot wait on a CTA that has left.
 // --------------------------------------------------------------------------
-constexpr int IPF_THREADS = 256;
+constexpr int IPF_THREADS = 256;                         // the bulk-copy form; the register form: TH
 
 __device__ __forceinline__ void cluster_arrive_release() {
     asm volatile("barrier.cluster.arrive.release;\n" ::: "memory");
@@ -2318,8 +2320,8 @@ __device__ __forceinline__ void cluster_wait_acquire() {
     asm volatile("barrier.cluster.wait.acquire;\n" ::: "memory");
 }
 
-template <int KAP>
-__global__ void __launch_bounds__(IPF_THREADS)
+template <int KAP, int TH>
+__global__ void __launch_bounds__(TH)
 ipf_fine_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair_ids, int C,
                 int csr_cap) {
     namespace cg = cooperative_groups;
@@ -2328,15 +2330,17 @@ ipf_fine_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair_
     const int rank = (int)cl.block_rank();
     const PairDev& P = pairs[pair_ids[blockIdx.x / C]];
     const int N = P.N, n = P.n, M = P.M;
-    const int Mc = M / C, k0 = rank * Mc;                    // owned blocks [k0, k0 + Mc)
+    const int Rn = ((n + C - 1) / C) * n;                     // blocks per CTA (the same stride in all)
+    const int k0 = min(M, rank * Rn);
+    const int Mc = min(M, k0 + Rn) - k0;                      // owned blocks [k0, k0 + Mc)
     float* Aown = reinterpret_cast<float*>(smem_raw);         // block sums of a (owned)
-    float* Bown = Aown + Mc;                                  // block sums of b (owned)
-    float* v_s = Bown + Mc;                                   // plan values: owned CSR rows
+    float* Bown = Aown + Rn;                                  // block sums of b (owned)
+    float* v_s = Bown + Rn;                                   // plan values: owned CSR rows
     float* vc_s = v_s + csr_cap;                              //              owned CSC columns
     int* ci_s = reinterpret_cast<int*>(vc_s + csr_cap);
     int* ri_s = ci_s + csr_cap;
     int* rp_s = ri_s + csr_cap;                               // Mc + 1, relative offsets
-    int* cp_s = rp_s + Mc + 1;
+    int* cp_s = rp_s + Rn + 1;
     const int r_base = P.rowptr[k0], c_base = P.colptr[k0];
     const int r_cnt = P.rowptr[k0 + Mc] - r_base, c_cnt = P.colptr[k0 + Mc] - c_base;
     const bool staged = r_cnt <= csr_cap && c_cnt <= csr_cap;
@@ -2401,9 +2405,9 @@ ipf_fine_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair_
                     const float* val = staged ? (half == 0 ? v_s : vc_s) : (half == 0 ? vt : vct);
                     const int row = staged ? kl : k0 + kl;
                     for (int e = ptr[row]; e < ptr[row + 1]; ++e) {
-                        const int l = idx[e], owner = l / Mc;
+                        const int l = idx[e], owner = l / Rn;
                         const float* peer = cl.map_shared_rank(other, owner);
-                        r += val[e] * peer[l - owner * Mc];
+                        r += val[e] * peer[l - owner * Rn];
                     }
                     r *= kinvK;
                     inv[q] = r > 0.0f ? 1.0f / r : 0.0f;
@@ -2448,10 +2452,13 @@ ipf_fine_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair_
 }
 
 int launch_ipf_fine(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int kappa, int C,
-                    int M_max, int nnz_max, cudaStream_t stream) {
+                    int M_max, int nnz_max, cudaStream_t stream, int threads) {
     if (n_pairs <= 0) return QWB_OK;
-    if (C < 1 || C > 16 || (kappa != 4 && kappa != 8)) return QWB_ERR_UNSUPPORTED;
-    const int Mc = M_max / C;
+    if (C < 1 || C > 16 || (kappa != 4 && kappa != 8) || (threads != 256 && threads != 512))
+        return QWB_ERR_UNSUPPORTED;
+    int n_max = 1;                                            // square grids: M = n^2
+    while ((n_max + 1) * (n_max + 1) <= M_max) ++n_max;
+    const int Mc = ((n_max + C - 1) / C) * n_max;             // blocks per CTA at most
     // staged plan rows and columns of one CTA: a basic plan has at most 2M - 1
     // entries, on average 2 per owned block; room for twice that (a CTA whose
     // blocks hold more reads its part of the plan from global memory)
@@ -2462,12 +2469,13 @@ int launch_ipf_fine(const PairDev* pairs_d, const int* pair_ids, int n_pairs, in
         smem = sizeof(float) * 2 * (size_t)Mc + 2 * sizeof(int) * (size_t)(Mc + 1);
         csr_cap = 0;
     }
-    auto kern = kappa == 4 ? ipf_fine_kernel<4> : ipf_fine_kernel<8>;
+    auto kern = threads == 512 ? (kappa == 4 ? ipf_fine_kernel<4, 512> : ipf_fine_kernel<8, 512>)
+                               : (kappa == 4 ? ipf_fine_kernel<4, 256> : ipf_fine_kernel<8, 256>);
     QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (C > 8) QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(n_pairs * C));
-    cfg.blockDim = dim3(IPF_THREADS);
+    cfg.blockDim = dim3((unsigned)threads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];

@@ -119,10 +119,11 @@ int launch_primalk(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids,
 // threads per CTA; n_max >= every pair's coarse side n.
 int launch_primalk_cl(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs, int kappa,
                       int C, int variant, int n_max, cudaStream_t stream);
-// Fine FP32 IPF sweeps on clusters of C CTAs per pair (2-D, kappa 4 or 8,
-// FP32, C divides every pair's n); the pairs have fine_ext = 1.
+// Fine FP32 IPF sweeps on clusters of C (1..16) CTAs of `threads` (256 or
+// 512) threads per pair (2-D, kappa 4 or 8, FP32; CTA r owns the block rows
+// [r R, (r+1) R), R = ceil(n / C)); the pairs have fine_ext = 1.
 int launch_ipf_fine(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int kappa, int C,
-                    int M_max, int nnz_max, cudaStream_t stream);
+                    int M_max, int nnz_max, cudaStream_t stream, int threads = 256);
 // side 0 upscales f~ (the dual pass of Alg. 5); side 1 upscales g~ (the
 // same pass started from the other coarse potential)
 int launch_upsample(const PairDev* pairs_d, PairOut* outs_d, const PixItem* items, int n_items,

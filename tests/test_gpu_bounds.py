@@ -310,10 +310,12 @@ def test_fine_ipf_scalings_bulk(sweeps, batched, cluster):
 
 @pytest.mark.parametrize("sweeps", [1, 7, 50])
 @pytest.mark.parametrize("batched", [True, False])
-@pytest.mark.parametrize("cluster", [0, 2, 8, 16])
+@pytest.mark.parametrize("cluster", [0, 2, 8, 16, 3, 3 | 64, 4 | 64])
 def test_fine_ipf_scalings(sweeps, batched, cluster):
     """The fine FP32 IPF sweeps (inside the primal kernel, or on clusters of up
-    to 2, 8 or 16 CTAs per pair): from b = 1 the uniform kernel reaches its fixed point
+    to 2, 8 or 16 CTAs per pair, of 3 CTAs that split the block rows unevenly
+    (coarse sides 8, 12, 16: rows 3 + 3 + 2, 4 + 4 + 4, 6 + 6 + 4), and with
+    512-thread CTAs (| QWB_IPF_WIDE = 64)): from b = 1 the uniform kernel reaches its fixed point
     a = kappa^2 mu / mu~, b = kappa^2 nu / nu~ after one sweep whatever the
     coarse plan (Sec. 3.4, IPF paragraph), and further sweeps stay there up to
     FP32 rounding.  The oracle's FP64 IPF on its own plan agrees."""
