@@ -363,6 +363,13 @@ def run_gpu(args):
             skm = {k: statistics.mean(v) for k, v in sep_kern.items() if all(x >= 0 for x in v)}
             sct_ms = 0.5 * (skm.get("ctransform_g", 0.0) + skm.get("ctransform_f", 0.0))
             sep_ops = 2.0 * 2.0 * float(N) ** 3 * n          # 2 stages x N^3 pairs x 2 ops
+            cbar_bytes = 8.0 * M_C * M_C * n                  # the FP64 C-bar written
+            hbm_peak = 6700.8
+            try:
+                with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+                    hbm_peak = float(json.load(fh).get("hbm_gbs") or hbm_peak)
+            except (OSError, ValueError):
+                pass
             dlb = max(abs(a["lb"] - b["lb"]) / max(b["lb"], 1e-300) for a, b in zip(sep_res, lazy_res))
             out["separable_p2"] = {
                 "value": round(n * world / (ms_sep_max * 1e-3), 3), "unit": "pairs/s",
@@ -372,9 +379,18 @@ def run_gpu(args):
                                "achieved_tflops": round(sep_ops / (sct_ms * 1e-3) / 1e12, 3) if sct_ms else None,
                                "frac_of_fp32": round(sep_ops / (sct_ms * 1e-3) / 1e12 / fp32_peak, 4)
                                if sct_ms else None},
+                "cbar": {"bound": "hbm", "bytes_per_launch": cbar_bytes,
+                         "avg_launch_ms": round(skm.get("cbar", 0.0), 4),
+                         "achieved_gbs": round(cbar_bytes / (skm["cbar"] * 1e-3) / 1e9, 1)
+                         if skm.get("cbar") else None,
+                         "frac_of_hbm": round(cbar_bytes / (skm["cbar"] * 1e-3) / 1e9 / hbm_peak, 4)
+                         if skm.get("cbar") else None,
+                         "note": "separable C-bar: 2 kappa^2 + 2 kappa multiply-adds per block pair; bound "
+                                 "by writing the FP64 M x M matrix (bytes = 8 M^2 per pair)"},
                 "max_rel_lb_diff_vs_lazy": dlb,
                 "note": "QWB_FLAG_SEPARABLE: p = 2 c-transform as two 1-D transforms (2 N^3 pairs "
-                        "each) instead of the N^4 lazy transform; same certified rounding"}
+                        "each) instead of the N^4 lazy transform, and the C-bar sum regrouped over "
+                        "the two axes (row and column sums of each block); same certified rounding"}
         if not args.skip_workloads:
             out["uneven_200"] = _uneven_workload(api, dev, args)
             out["differentiable_256"] = _differentiable_workload(api, dev, args)

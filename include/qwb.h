@@ -67,7 +67,10 @@ enum {
     QWB_FLAG_MINCOST = 8,      /* also compute the min-cost lower bound (Sec. 3.3) */
     QWB_FLAG_SEPARABLE = 16,   /* p = 2 pairs: separable c-transform (see
                                   qwb_ctransform_separable) instead of the
-                                  N^4 lazy transform of Sec. 4 */
+                                  N^4 lazy transform of Sec. 4, and, for
+                                  2-D FP32 pairs with kappa 4 or 8, the
+                                  separable C-bar (see
+                                  qwb_coarse_cost_separable) */
     QWB_FLAG_SYMMETRIC_DUAL = 32 /* also run the dual pass from the coarse
                                   potential g~ (Sec. 3.5 from nu's side) and
                                   report the larger of the two lower bounds */
@@ -137,6 +140,24 @@ void qwb_ctx_destroy(qwb_ctx* ctx);
 int qwb_coarse_cost(qwb_ctx* ctx, const qwb_problem* prob, const double* mu_d,
                     const double* nu_d, double* cbar_d, double* mu_coarse_d,
                     double* nu_coarse_d, qwb_prec prec, void* stream);
+/* The same C-bar for p = 2 (d = 2, kappa 4 or 8, FP32 reductions) by
+ * separating the squared distance over the two axes (not a step of the
+ * paper; an exact regrouping of the sum that defines C-bar in Sec. 3.2):
+ * with R, C the row and column sums of a block's masses and
+ * D = kappa (k - l) per axis,
+ *   sum_{x in X_k, y in Y_l} mu(x) nu(y) rho(x,y)^2
+ *     = sum_{a1, b1} R_mu,k[a1] R_nu,l[b1] (D1 + a1 - b1)^2
+ *     + sum_{a2, b2} C_mu,k[a2] C_nu,l[b2] (D2 + a2 - b2)^2,
+ * 2 kappa^2 + 2 kappa multiply-adds per block pair instead of
+ * kappa^4 + kappa^2.  Every operation rounds upward from the rounded-up
+ * masses, so each entry is >= the real C-bar, as qwb_coarse_cost's; the two
+ * differ by rounding only.  Zero-mass blocks as qwb_coarse_cost.
+ * mu_d, nu_d: N*N FP64; cbar_d: M*M FP64 out.  Coarse side n <= 1365
+ * (kappa 4) or 722 (kappa 8).  Synchronous with `stream` on return.
+ * Errors: INVALID_ARG, UNSUPPORTED (p != 2, d = 3, kappa not 4 or 8, n too
+ * large), MASS, CUDA, OOM. */
+int qwb_coarse_cost_separable(qwb_ctx* ctx, const qwb_problem* prob, const double* mu_d,
+                              const double* nu_d, double* cbar_d, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Host exact coarse solve.  Sec. 2.1 (Kantorovich problem and its dual),     */

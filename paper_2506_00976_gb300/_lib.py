@@ -48,6 +48,8 @@ SIGNATURES = [
     ("qwb_ctx_destroy", None, [c_void_p]),
     ("qwb_coarse_cost", c_int32, [c_void_p, ctypes.POINTER(QwbProblem), c_void_p, c_void_p,
                                   c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
+    ("qwb_coarse_cost_separable", c_int32, [c_void_p, ctypes.POINTER(QwbProblem), c_void_p, c_void_p,
+                                            c_void_p, c_void_p]),
     ("qwb_coarse_solve", c_int32, [c_int32, c_int32, P_double, P_double, P_double, P_int32,
                                    P_int32, P_double, P_int32, P_double, P_double, P_double]),
     ("qwb_coarse_solve_grid", c_int32, [c_int32, P_double, P_double, P_double, P_int32, P_int32,

@@ -79,6 +79,18 @@ def coarse_cost(mu, nu, N, kappa, p, prec="mixed", d=2):
     return cbar, mc, nc
 
 
+def coarse_cost_separable(mu, nu, N, kappa):
+    """qwb_coarse_cost_separable: C-bar [M, M] for p = 2 (d = 2, kappa 4 or 8)
+    by separating the squared distance over the axes (FP32 reductions)."""
+    M = (N // kappa) ** 2
+    cbar = torch.empty((M, M), dtype=torch.float64, device=mu.device)
+    pr = problem(N, kappa, 2.0, 2)
+    check(_lib.load().qwb_coarse_cost_separable(context(mu.device), ctypes.byref(pr), _dev64(mu, "mu"),
+                                                _dev64(nu, "nu"), _ptr(cbar), _stream(mu)),
+          "qwb_coarse_cost_separable")
+    return cbar
+
+
 def coarse_solve(C, a, b):
     """qwb_coarse_solve (host network simplex): dict with CSR plan, f, g, obj (numpy)."""
     C = np.ascontiguousarray(C, dtype=np.float64)

@@ -210,7 +210,9 @@ struct qwb_batch {
     int n_cb4 = 0, n_max4 = 0, N_max4 = 0;
     int n_cb8 = 0, n_max8 = 0, N_max8 = 0;
     int cbar8_variant = 4;
-    std::vector<char> cbar_group;       // per pair: 4, 8 or 0
+    // separable p = 2 C-bar (QWB_FLAG_SEPARABLE, FP32, kappa 4 or 8): groups 12, 16
+    int n_cbs4 = 0, n_cbs8 = 0, n_maxs = 0;
+    std::vector<char> cbar_group;       // per pair: 4, 8, 12 (separable, kappa 4), 16 (kappa 8) or 0
     // fine IPF sweeps on thread-block clusters (ipf_fine_kernel): 2-D FP32
     // pairs grouped by kappa (4, 8); ipf_C is the requested cluster size
     // (0: every pair sweeps inside primal_kernel), each group runs with the
@@ -449,9 +451,13 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         b->Ms.push_back(M);
         if (dd == 3) b->has_3d = true;
         const bool pow2 = dd == 2 && !(nn & (nn - 1)) && nn <= 64 && !b->f64;
-        const int grp = (pow2 && kap == 4) ? 4 : (pow2 && kap == 8) ? 8 : 0;
+        const bool sepcb = want_cbar && separable(t) && dd == 2 && !b->f64 && (kap == 4 || kap == 8) &&
+                           sizeof(float) * (size_t)nn * (2 * kap + 1) <= 48 * 1024;
+        const int grp = sepcb ? (kap == 4 ? 12 : 16) : (pow2 && kap == 4) ? 4 : (pow2 && kap == 8) ? 8 : 0;
         b->cbar_group.push_back((char)grp);
-        if (grp == 4) {
+        if (grp >= 12) {
+            b->n_maxs = std::max(b->n_maxs, nn);
+        } else if (grp == 4) {
             b->n_max4 = std::max(b->n_max4, nn);
             b->N_max4 = std::max(b->N_max4, N);
         } else if (grp == 8) {
@@ -477,6 +483,7 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         pair_off[t] = off;
         off += align_up(12 * sizeof(double) * M);
         if (want_cbar) off += align_up(sizeof(double) * (size_t)M * M);
+        if (grp >= 12) off += align_up(sizeof(float) * 4 * (size_t)kap * M);
         off += (separable(t) ? (dd == 3 ? 11 : 10) : 9) * align_up(tsz * m);
         if (flags & QWB_FLAG_SYMMETRIC_DUAL) off += 2 * align_up(sizeof(double) * m);
     }
@@ -594,9 +601,10 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         b->ct_cfg_b.in_rows = std::max(b->ct_cfg_b.in_rows, maxrows);
         b->ct_cfg_p.in_rows = b->ct_cfg_b.in_rows;
     }
-    // 2-D C-bar items: the cbar4 group, the cbar8 group, then the others
+    // 2-D C-bar items: the cbar4 group, the cbar8 group, the separable groups,
+    // then the others
     b->cbar_off.assign(n, 0); b->cbar_cnt.assign(n, 0);
-    for (int grp : {4, 8, 0}) {
+    for (int grp : {4, 8, 12, 16, 0}) {
         const int before = (int)cb.size();
         for (int t = 0; t < n; ++t) {
             if (dim_of(probs[t]) != 2 || b->cbar_group[t] != grp) continue;
@@ -606,6 +614,8 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         }
         if (grp == 4) b->n_cb4 = (int)cb.size() - before;
         if (grp == 8) b->n_cb8 = (int)cb.size() - before;
+        if (grp == 12) b->n_cbs4 = (int)cb.size() - before;
+        if (grp == 16) b->n_cbs8 = (int)cb.size() - before;
     }
     b->n_prep = (int)prep.size(); b->n_pix = (int)pix.size(); b->n_cbar = (int)cb.size();
     b->n_cbar3 = (int)cb3.size();
@@ -680,6 +690,7 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         P.mu_w_hi = P.nu_c_hi + M; P.nu_w_hi = P.mu_w_hi + M;
         base += align_up(12 * sizeof(double) * M);
         if (want_cbar) { P.cbar = (double*)base; base += align_up(sizeof(double) * (size_t)M * M); }
+        if (b->cbar_group[t] >= 12) { P.bsum = (float*)base; base += align_up(sizeof(float) * 4 * (size_t)kap * M); }
         P.fhat = base; base += align_up(tsz * m);
         P.g = base; base += align_up(tsz * m);
         P.f = base; base += align_up(tsz * m);
@@ -790,7 +801,11 @@ static int enqueue_coarse(qwb_batch* b, bool batched, cudaStream_t s) {
             if ((st = launch_cbar(b->pairs_d, b->cbar_items_d + b->n_cb4, b->n_cb8, 8, b->n_max8, b->N_max8,
                                   b->f64, s, b->cbar8_variant)))
                 return st;
-            const int off = b->n_cb4 + b->n_cb8;
+            const int soff = b->n_cb4 + b->n_cb8;
+            if ((st = launch_cbar_sep(b->pairs_d, b->cbar_items_d + soff, b->n_cbs4, 4, b->n_maxs, s))) return st;
+            if ((st = launch_cbar_sep(b->pairs_d, b->cbar_items_d + soff + b->n_cbs4, b->n_cbs8, 8, b->n_maxs, s)))
+                return st;
+            const int off = soff + b->n_cbs4 + b->n_cbs8;
             if ((st = launch_cbar(b->pairs_d, b->cbar_items_d + off, b->n_cbar - off, b->kappa_code,
                                   b->n_max2, b->N_max2, b->f64, s, generic_cbar_variant(b->f64))))
                 return st;
@@ -807,6 +822,11 @@ static int enqueue_coarse(qwb_batch* b, bool batched, cudaStream_t s) {
             continue;
         }
         const int nn = b->probs[t].N / b->probs[t].kappa;
+        if (b->cbar_group[t] >= 12) {
+            if ((st = launch_cbar_sep(b->pairs_d, b->cbar_items_d + b->cbar_off[t], b->cbar_cnt[t],
+                                      b->probs[t].kappa, nn, s))) return st;
+            continue;
+        }
         const int kc = (b->probs[t].kappa == 1 || b->probs[t].kappa == 2 || b->probs[t].kappa == 4 ||
                         b->cbar_group[t] == 8) ? b->probs[t].kappa : -b->probs[t].kappa;
         if ((st = launch_cbar(b->pairs_d, b->cbar_items_d + b->cbar_off[t], b->cbar_cnt[t], kc, nn,
@@ -1973,6 +1993,34 @@ int qwb_coarse_cost(qwb_ctx* ctx, const qwb_problem* prob, const double* mu_d, c
     const size_t M = b->Ms[0];
     if (mu_coarse_d) QWB_CUDA(cudaMemcpyAsync(mu_coarse_d, P.mu_c, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
     if (nu_coarse_d) QWB_CUDA(cudaMemcpyAsync(nu_coarse_d, P.nu_c, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
+    QWB_CUDA(cudaStreamSynchronize(s));   // the cached descriptor is reused by the next call
+    return QWB_OK;
+}
+
+int qwb_coarse_cost_separable(qwb_ctx* ctx, const qwb_problem* prob, const double* mu_d, const double* nu_d,
+                              double* cbar_d, void* stream) {
+    if (!ctx || !mu_d || !nu_d || !cbar_d)
+        return fail(QWB_ERR_INVALID_ARG, "qwb_coarse_cost_separable: null argument");
+    int st = check_problem(prob);
+    if (st) return st;
+    if (prob->p != 2.0 || dim_of(*prob) != 2 || (prob->kappa != 4 && prob->kappa != 8))
+        return fail(QWB_ERR_UNSUPPORTED, "qwb_coarse_cost_separable: needs p = 2, d = 2 and kappa 4 or 8");
+    std::lock_guard<std::mutex> lk(ctx->mtx);
+    QWB_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    qwb_batch* b;
+    if ((st = single_batch(ctx, prob, 1, QWB_PREC_MIXED, &b, QWB_FLAG_SEPARABLE))) return st;
+    if (b->cbar_group[0] < 12)
+        return fail(QWB_ERR_UNSUPPORTED, "qwb_coarse_cost_separable: the coarse side is too large");
+    PairDev& P = b->pairs_h[0];
+    double* own_cbar = P.cbar;
+    P.mu = mu_d; P.nu = nu_d; P.cbar = cbar_d;
+    if ((st = single_upload(b, s))) { P.cbar = own_cbar; return st; }
+    P.cbar = own_cbar;
+    QWB_CUDA(cudaMemsetAsync(b->outs_d, 0, sizeof(PairOut), s));
+    if ((st = single_validate(b, s))) return st;
+    if ((st = launch_cbar_sep(b->pairs_d, b->cbar_items_d, b->n_cbar, prob->kappa, prob->N / prob->kappa, s)))
+        return st;
     QWB_CUDA(cudaStreamSynchronize(s));   // the cached descriptor is reused by the next call
     return QWB_OK;
 }

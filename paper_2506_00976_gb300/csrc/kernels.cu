@@ -174,6 +174,24 @@ __global__ void prepare_kernel(const PairDev* __restrict__ pairs, PairOut* __res
         P.nu_rinv[k] = nu_rd > 0.0 ? __drcp_ru(nu_rd) : 0.0;
         P.mu_rinv32[k] = mu_rd >= 1e-30 ? __frcp_ru(__double2float_rd(mu_rd)) : 0.0f;
         P.nu_rinv32[k] = nu_rd >= 1e-30 ? __frcp_ru(__double2float_rd(nu_rd)) : 0.0f;
+        if (sizeof(T) == 4 && P.bsum && P.d == 2) {
+            // the block's row and column sums of the rounded-up FP32 masses,
+            // rounded up (read back from what this thread wrote above)
+            for (int side = 0; side < 2; ++side) {
+                const float* up = reinterpret_cast<const float*>(side == 0 ? P.mu_up : P.nu_up) +
+                                  (size_t)(k1 * kap) * N + k2 * kap;
+                float* dst = P.bsum + ((size_t)side * P.M + k) * 2 * kap;
+                for (int a = 0; a < kap; ++a) {
+                    float r = 0.0f, c = 0.0f;
+                    for (int e = 0; e < kap; ++e) {
+                        r = __fadd_ru(r, up[a * N + e]);
+                        c = __fadd_ru(c, up[e * N + a]);
+                    }
+                    dst[a] = r;
+                    dst[kap + a] = c;
+                }
+            }
+        }
         smu = mu_rn; snu = nu_rn;
     }
     // block reduction of the masses, one atomic per block
@@ -890,6 +908,114 @@ static int cbar_dispatch(const PairDev* pairs_d, const CbarItem* items, int n_it
         case 4: return variant == 1 ? run(cbar_kernel<T, 4, MB>) : run(cbar_kernel<T, 4, 2>);
         default: return run(cbar_kernel<T, 0, 2>);
     }
+}
+
+// --------------------------------------------------------------------------
+// cbar_sep: C-bar for p = 2 by the separation of the squared distance over
+// the two axes.  With x = kappa k + a, y = kappa l + b per axis and
+// rho^2 = (x1 - y1)^2 + (x2 - y2)^2, the sum over every fine pixel pair of a
+// block pair (Sec. 3.2, the equation that defines C-bar) regroups exactly as
+//   sum_{a, b} mu_a nu_b rho^2
+//     = sum_{a1} Rmu[a1] sum_{b1} Rnu[b1] (D1 + a1 - b1)^2
+//     + sum_{a2} Cmu[a2] sum_{b2} Cnu[b2] (D2 + a2 - b2)^2,
+// D = kappa (k - l) per axis, R / C the block's row / column sums.  Every
+// term is non-negative and every operation rounds up (from the rounded-up
+// FP32 masses and their rounded-up sums), so the entry is an upper bound of
+// the real C-bar, as the direct kernels' are; the squares are exact FP32
+// integers.  2 kappa^2 + 2 kappa multiply-adds per block pair instead of
+// kappa^4 + kappa^2; the first axis's inner sums depend on the target block
+// only (the CTA's source block row k1 is fixed), so they are formed once per
+// target and reused over the row's n source blocks.  One item per (pair,
+// source block row): threads walk the targets l, so every output row is
+// written coalesced.
+// --------------------------------------------------------------------------
+template <int KAP>
+__global__ void __launch_bounds__(256)
+cbar_sep_kernel(const PairDev* __restrict__ pairs, const CbarItem* __restrict__ items, int n_items) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int W = 2 * KAP;                               // row sums, then column sums
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const CbarItem I = items[it];
+        const PairDev& P = pairs[I.pair];
+        const int n = P.n, M = P.M, k1 = I.w1;
+        float* ms = reinterpret_cast<float*>(smem_raw);      // [n][W] sums of the row's source blocks
+        float* rk_s = ms + n * W;                            // [n] upper bounds of 1 / mu~_k
+        __syncthreads();                                     // the previous item's readers are done
+        for (int q = threadIdx.x; q < n * W; q += blockDim.x) ms[q] = P.bsum[(size_t)k1 * n * W + q];
+        for (int q = threadIdx.x; q < n; q += blockDim.x) rk_s[q] = P.mu_rinv32[k1 * n + q];
+        __syncthreads();
+        const float* nsum = P.bsum + (size_t)M * W;
+        for (int l = threadIdx.x; l < M; l += blockDim.x) {
+            const int l1 = l / n, l2 = l - l1 * n;
+            float Rn[KAP], Cn[KAP];
+#pragma unroll
+            for (int q = 0; q < KAP; q += 4) {
+                const float4 r4 = *reinterpret_cast<const float4*>(nsum + (size_t)l * W + q);
+                const float4 c4 = *reinterpret_cast<const float4*>(nsum + (size_t)l * W + KAP + q);
+                Rn[q] = r4.x; Rn[q + 1] = r4.y; Rn[q + 2] = r4.z; Rn[q + 3] = r4.w;
+                Cn[q] = c4.x; Cn[q + 1] = c4.y; Cn[q + 2] = c4.z; Cn[q + 3] = c4.w;
+            }
+            const float rl = P.nu_rinv32[l];
+            // first axis: V1[a1] = sum_b1 Rnu[b1] (D1 + a1 - b1)^2
+            const int D1 = KAP * (k1 - l1);
+            float V1[KAP];
+#pragma unroll
+            for (int a1 = 0; a1 < KAP; ++a1) {
+                float v = 0.0f;
+#pragma unroll
+                for (int b1 = 0; b1 < KAP; ++b1) {
+                    const float d = (float)(D1 + a1 - b1);
+                    v = fma_ru(Rn[b1], d * d, v);
+                }
+                V1[a1] = v;
+            }
+            for (int k2 = 0; k2 < n; ++k2) {
+                const float* mk = ms + k2 * W;
+                const int D2 = KAP * (k2 - l2);
+                float sq[2 * KAP - 1];                       // (D2 + e - (KAP - 1))^2, exact
+#pragma unroll
+                for (int e = 0; e < 2 * KAP - 1; ++e) {
+                    const float d = (float)(D2 + e - (KAP - 1));
+                    sq[e] = d * d;
+                }
+                float t1 = 0.0f, t2 = 0.0f;
+#pragma unroll
+                for (int a = 0; a < KAP; ++a) {
+                    float v = 0.0f;
+#pragma unroll
+                    for (int b2 = 0; b2 < KAP; ++b2) v = fma_ru(Cn[b2], sq[a - b2 + KAP - 1], v);
+                    t2 = fma_ru(mk[KAP + a], v, t2);
+                    t1 = fma_ru(mk[a], V1[a], t1);
+                }
+                const float acc = __fadd_ru(t1, t2);
+                const int k = k1 * n + k2;
+                const float rk = rk_s[k2];
+                double outv;
+                if (rk > 0.0f && rl > 0.0f) {
+                    outv = widen_f32(mul_ru(mul_ru(acc, rk), rl));
+                } else {
+                    // unweighted mean over the block pair: per axis E (D + a - b)^2
+                    // = D^2 + (kappa^2 - 1) / 6 for independent uniform a, b
+                    const double var = __ddiv_ru((double)(KAP * KAP - 1), 3.0);
+                    const double mean = __dadd_ru((double)D1 * D1 + (double)D2 * D2, var);
+                    outv = cbar_special<float>(P, k, l, (double)acc, mean);
+                }
+                P.cbar[(size_t)k * M + l] = outv;
+            }
+        }
+    }
+}
+
+int launch_cbar_sep(const PairDev* pairs_d, const CbarItem* items, int n_items, int kappa, int n_max,
+                    cudaStream_t stream) {
+    if (n_items <= 0) return QWB_OK;
+    if (kappa != 4 && kappa != 8) return QWB_ERR_UNSUPPORTED;
+    const size_t smem = sizeof(float) * (size_t)n_max * (2 * kappa + 1);
+    if (smem > 48 * 1024) return QWB_ERR_UNSUPPORTED;
+    if (kappa == 4) cbar_sep_kernel<4><<<n_items, 256, smem, stream>>>(pairs_d, items, n_items);
+    else cbar_sep_kernel<8><<<n_items, 256, smem, stream>>>(pairs_d, items, n_items);
+    QWB_LAUNCHED();
+    return QWB_OK;
 }
 
 int launch_cbar(const PairDev* pairs_d, const CbarItem* items, int n_items, int kappa_code,

@@ -29,6 +29,8 @@ struct PairDev {
     void* mu_up; void* nu_up; // N*N copies of mu, nu in type T rounded upward (C-bar)
     double* mu_w_hi;        // M upper bounds of sum_{x in X_k} rho(x-bar, x)^p mu(x) (TV weights)
     double* nu_w_hi;
+    float* bsum;            // separable p = 2 C-bar (else null): [side][M][2 kappa] FP32 upper
+                            // bounds of each block's row sums, then column sums, of mu_up / nu_up
     double* cbar;           // M*M coarse cost out (may be null)
     const void* ctab_lo;    // N*N cost table, lower brackets (T)
     const void* ctab_hi;    // N*N cost table, upper brackets (T)
@@ -97,6 +99,11 @@ int launch_prepare(const PairDev* pairs_d, PairOut* outs_d, const PixItem* items
 constexpr int CBAR_S = 4;   // block rows per C-bar work item
 int launch_cbar(const PairDev* pairs_d, const CbarItem* items, int n_items, int kappa_max,
                 int n_max, int N_max, bool f64, cudaStream_t stream, int variant = 0);
+// C-bar of FP32 2-D p = 2 pairs with kappa (4 or 8) through the separation of
+// the squared cost over the two axes (P.bsum set); items (pair, w1 = source
+// block row k1); n_max >= every pair's coarse side.
+int launch_cbar_sep(const PairDev* pairs_d, const CbarItem* items, int n_items, int kappa, int n_max,
+                    cudaStream_t stream);
 // support_num_kernel over the pairs of pair_ids, entries [0, nnz_max) of each
 // (nnz_max >= every pair's nnz; supp_num has room for the pair's staged plan)
 int launch_support_num(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int nnz_max, bool f64,

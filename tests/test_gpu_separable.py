@@ -1,12 +1,16 @@
 """GPU tests of the separable p = 2 c-transform (exact reformulation of the
-lazy c-transform of Sec. 4 over the two grid axes) against the oracle's
-brute-force definition, and of batches that use it (QWB_FLAG_SEPARABLE)."""
+lazy c-transform of Sec. 4 over the two grid axes) and of the separable p = 2
+C-bar (the same separation of the sum that defines C-bar in Sec. 3.2)
+against the oracle's brute-force definitions, and of batches that use them
+(QWB_FLAG_SEPARABLE)."""
+import ctypes
+
 import numpy as np
 import pytest
 import torch
 
 from oracle import qwb_oracle as O
-from paper_2506_00976_gb300 import api, synth
+from paper_2506_00976_gb300 import _lib, api, synth
 
 pytestmark = pytest.mark.gpu
 SEPARABLE = 16
@@ -79,7 +83,9 @@ def test_256_sampled():
 def test_batch_with_separable_flag(batched):
     """A batch of p = 1 and p = 2 pairs with QWB_FLAG_SEPARABLE: p = 1 pairs
     are unchanged, p = 2 lower bounds stay valid and within FP32 rounding of
-    the brute-force ones; the upper bounds do not depend on the flag."""
+    the brute-force ones; the primal upper bounds do not depend on the flag,
+    and the weighted-cost bounds (the separable C-bar for kappa 4 and 8)
+    agree to FP32 rounding and stay above W."""
     cases = [(16, 4, 2.0, "gauss"), (32, 4, 1.0, "cauchy"), (32, 8, 2.0, "field"), (24, 4, 2.0, "white")]
     mus, nus, probs, raw = [], [], [], []
     for t, (N, kappa, p, cls) in enumerate(cases):
@@ -89,11 +95,52 @@ def test_batch_with_separable_flag(batched):
     r1 = api.bounds(mus, nus, probs, ipf_sweeps=5, batched=batched, flags=SEPARABLE)
     for t, (N, kappa, p, cls) in enumerate(cases):
         assert r1[t]["status"] == 0
-        assert r1[t]["ub_weighted"] == r0[t]["ub_weighted"] and r1[t]["ub_primal"] == r0[t]["ub_primal"]
+        assert r1[t]["ub_primal"] == r0[t]["ub_primal"]
         if p != 2.0:
-            assert r1[t]["lb"] == r0[t]["lb"]
+            assert r1[t]["lb"] == r0[t]["lb"] and r1[t]["ub_weighted"] == r0[t]["ub_weighted"]
         else:
             assert abs(r1[t]["lb_p"] - r0[t]["lb_p"]) <= 1e-4 * max(1.0, abs(r0[t]["lb_p"]))
+            assert abs(r1[t]["ub_weighted"] - r0[t]["ub_weighted"]) <= 1e-5 * r0[t]["ub_weighted"]
         if N <= 16:
             W = O.wasserstein_exact(raw[t][0], raw[t][1], N, p)
-            assert r1[t]["lb"] <= W
+            assert r1[t]["lb"] <= W <= r1[t]["ub_weighted"] * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("N,kappa", [(16, 4), (32, 4), (24, 4), (64, 4), (128, 4), (36, 4),
+                                     (32, 8), (48, 8), (8, 8), (64, 8)])
+def test_coarse_cost_separable(N, kappa):
+    """The separable p = 2 C-bar (row and column sums of each block, then the
+    two axes' squared offsets) against the oracle's direct FP64 reduction
+    over every fine pixel pair: every entry an upper bound, within FP32
+    rounding (2e-5 relative) of it and of the direct FP32 kernel; power-of-two
+    and other coarse sides (6, 9)."""
+    mu, nu = synth.make_measure(N, "gauss", 76, 0), synth.make_measure(N, "field", 76, 1)
+    got = api.coarse_cost_separable(T(mu), T(nu), N, kappa).cpu().numpy()
+    ref = O.coarse_cost_weighted(mu, nu, N, kappa, 2.0)
+    assert np.all(got >= ref * (1 - 1e-13))
+    assert np.all(got <= ref * (1 + 2e-5) + 1e-300)
+    direct = api.coarse_cost(T(mu), T(nu), N, kappa, 2.0, prec="mixed")[0].cpu().numpy()
+    np.testing.assert_allclose(got, direct, rtol=2e-5)
+    again = api.coarse_cost_separable(T(mu), T(nu), N, kappa).cpu().numpy()
+    assert np.array_equal(got, again)
+
+
+def test_coarse_cost_separable_zero_mass_and_refusals():
+    """A zero-mass block takes the unweighted mean of rho^2 over the block
+    pair, as the direct kernels do; p != 2, kappa 2 and volumes are refused."""
+    N, kappa = 32, 4
+    mu = synth.make_measure(N, "gauss", 77, 0).reshape(N, N).copy()
+    mu[kappa:2 * kappa, 2 * kappa:3 * kappa] = 0.0
+    mu = (mu / mu.sum()).ravel()
+    nu = synth.make_measure(N, "gauss", 77, 1)
+    got = api.coarse_cost_separable(T(mu), T(nu), N, kappa).cpu().numpy()
+    ref = O.coarse_cost_weighted(mu, nu, N, kappa, 2.0)
+    np.testing.assert_allclose(got, ref, rtol=2e-5)
+    assert np.all(got >= ref * (1 - 1e-13))
+    lib = _lib.load()
+    for (n2, k2, p2, d2) in ((32, 4, 1.0, 2), (32, 2, 2.0, 2), (16, 4, 2.0, 3)):
+        pr = api.problem(n2, k2, p2, d2)
+        cb = torch.empty(1, dtype=torch.float64, device="cuda")
+        assert lib.qwb_coarse_cost_separable(api.context(torch.device("cuda")), ctypes.byref(pr),
+                                             ctypes.c_void_p(T(mu).data_ptr()), ctypes.c_void_p(T(nu).data_ptr()),
+                                             ctypes.c_void_p(cb.data_ptr()), None) == 7
