@@ -2491,7 +2491,36 @@ ipf_fine_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair_
     constexpr int PF = KAP == 4 ? 4 : 1;                      // blocks per chunk and thread
     const int chunk = PF * blockDim.x;
     float4 x[PF][KAP][Q];
+    // kappa = 8: when a warp's 32 blocks are all owned and lie in one block
+    // row, the warp moves each fine row of them as 64 consecutive float4
+    // (lane L holds float4 L and L + 32: half a row of block L / 2 and of
+    // block L / 2 + 16), so every load and store instruction covers 512
+    // contiguous bytes; each block's scale comes from its owner lane and its
+    // sum from the lane pair that holds it.  Other warps keep one block per
+    // thread.  The choice depends on the warp's first block only, so the
+    // loads, the scaling and the stores of a chunk agree.
+    const int lane = threadIdx.x & 31;
+    auto row_mode = [&](int kb) {
+        if constexpr (KAP != 8) return false;
+        const int kw = kb - lane;                              // the warp's first owned block
+        if (kw + 31 >= Mc) return false;
+        const int kf = k0 + kw;
+        return (kf % n) + 31 < n;
+    };
     auto load_chunk = [&](const float* src, int kb) {
+        if constexpr (KAP == 8) {
+            if (row_mode(kb)) {
+                const int kf = k0 + kb - lane;
+                const int k1 = kf / n, k2 = kf - (kf / n) * n;
+#pragma unroll
+                for (int t1 = 0; t1 < KAP; ++t1) {
+                    const float4* span = reinterpret_cast<const float4*>(src + (size_t)(k1 * KAP + t1) * N + k2 * KAP);
+                    x[0][t1][0] = span[lane];
+                    x[0][t1][1] = span[lane + 32];
+                }
+                return;
+            }
+        }
 #pragma unroll
         for (int q = 0; q < PF; ++q) {
             const int kl = kb + q * blockDim.x;
@@ -2539,23 +2568,56 @@ ipf_fine_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair_
                     inv[q] = r > 0.0f ? 1.0f / r : 0.0f;
                 }
             }
+            const bool rows = row_mode(kb);
+            if (rows) {
+                if constexpr (KAP == 8) {
+                    const int kw = kb - lane;
 #pragma unroll
-            for (int q = 0; q < PF; ++q) {
-                const int kl = kb + q * blockDim.x;
-                if (kl < Mc) {
-                    float s = 0.0f;
+                    for (int hq = 0; hq < 2; ++hq) {             // half rows of block lane / 2 + 16 hq
+                        const float sc = __shfl_sync(0xffffffffu, inv[0], lane / 2 + 16 * hq);
+                        float s = 0.0f;
 #pragma unroll
-                    for (int t1 = 0; t1 < KAP; ++t1)
-#pragma unroll
-                        for (int t2 = 0; t2 < Q; ++t2) {
-                            float4& v = x[q][t1][t2];
-                            v.x *= inv[q]; v.y *= inv[q]; v.z *= inv[q]; v.w *= inv[q];
+                        for (int t1 = 0; t1 < KAP; ++t1) {
+                            float4& v = x[0][t1][hq];
+                            v.x *= sc; v.y *= sc; v.z *= sc; v.w *= sc;
                             s += (v.x + v.y) + (v.z + v.w);
                         }
-                    mine[kl] = s;
+                        s += __shfl_xor_sync(0xffffffffu, s, 1);
+                        if (!(lane & 1)) mine[kw + lane / 2 + 16 * hq] = s;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < PF; ++q) {
+                    const int kl = kb + q * blockDim.x;
+                    if (kl < Mc) {
+                        float s = 0.0f;
+#pragma unroll
+                        for (int t1 = 0; t1 < KAP; ++t1)
+#pragma unroll
+                            for (int t2 = 0; t2 < Q; ++t2) {
+                                float4& v = x[q][t1][t2];
+                                v.x *= inv[q]; v.y *= inv[q]; v.z *= inv[q]; v.w *= inv[q];
+                                s += (v.x + v.y) + (v.z + v.w);
+                            }
+                        mine[kl] = s;
+                    }
                 }
             }
             if (kb + chunk >= Mc) { cluster_arrive_release(); arrived = true; }   // sums published
+            if (rows) {
+                if constexpr (KAP == 8) {
+                    const int kf = k0 + kb - lane;
+                    const int k1 = kf / n, k2 = kf - (kf / n) * n;
+#pragma unroll
+                    for (int t1 = 0; t1 < KAP; ++t1) {
+                        float4* span = reinterpret_cast<float4*>(dst + (size_t)(k1 * KAP + t1) * N + k2 * KAP);
+                        span[lane] = x[0][t1][0];
+                        span[lane + 32] = x[0][t1][1];
+                    }
+                }
+                continue;
+            }
 #pragma unroll
             for (int q = 0; q < PF; ++q) {
                 const int kl = kb + q * blockDim.x;
