@@ -158,7 +158,9 @@ __global__ void prepare_kernel(const PairDev* __restrict__ pairs, PairOut* __res
             reinterpret_cast<T*>(P.nu_up)[i] = from_double_ru<T>(y);
             reinterpret_cast<T*>(P.mu_t)[i] = (T)x;
             reinterpret_cast<T*>(P.nu_t)[i] = (T)y;
-            const double w = tv_weight_hi(c1, c2, N, P.p, c3);
+            // p = 2 in 2-D: the same (exact) weight without FP64 arithmetic
+            const double w = (P.p == 2.0 && P.d == 2 && N <= 2896) ? tv_weight_hi_fast(c1, c2, N, 2.0)
+                                                                   : tv_weight_hi(c1, c2, N, P.p, c3);
             mu_w = __fma_ru(w, x, mu_w);
             nu_w = __fma_ru(w, y, nu_w);
             bad_mu |= !(x >= 0.0) || !isfinite(x);
@@ -2982,13 +2984,25 @@ __global__ void upsample_kernel(const PairDev* __restrict__ pairs, const PairOut
         const int flr = nr >= 0 ? nr / den : -((-nr + den - 1) / den);
         const int flc = nc >= 0 ? nc / den : -((-nc + den - 1) / den);
         const int r0 = min(max(flr, 0), n - 2), c0 = min(max(flc, 0), n - 2);
-        const double inv = 1.0 / den;
-        const double wr = (double)(nr - den * r0) * inv, wc = (double)(nc - den * c0) * inv;
+        const int qr = nr - den * r0, qc = nc - den * c0;          // weights qr / den, qc / den
+        double wr, wc, wr1, wc1;                                   // and 1 - each
+        if (!(kap & (kap - 1))) {
+            // den a power of two: q / den and (den - q) / den are exact in
+            // FP32 (|q| < 2^24) and widen exactly, the same values as the
+            // FP64 expressions below, without the FP64 pipe
+            const float id = __frcp_rn((float)den);
+            wr = widen_f32((float)qr * id); wc = widen_f32((float)qc * id);
+            wr1 = widen_f32((float)(den - qr) * id); wc1 = widen_f32((float)(den - qc) * id);
+        } else {
+            const double inv = 1.0 / den;
+            wr = (double)qr * inv; wc = (double)qc * inv;
+            wr1 = 1.0 - wr; wc1 = 1.0 - wc;
+        }
         const double f00 = fc[r0 * n + c0] - s, f01 = fc[r0 * n + c0 + 1] - s;
         const double f10 = fc[(r0 + 1) * n + c0] - s, f11 = fc[(r0 + 1) * n + c0 + 1] - s;
-        const double top = (1.0 - wc) * f00 + wc * f01;
-        const double bot = (1.0 - wc) * f10 + wc * f11;
-        v = (1.0 - wr) * top + wr * bot;
+        const double top = wc1 * f00 + wc * f01;
+        const double bot = wc1 * f10 + wc * f11;
+        v = wr1 * top + wr * bot;
     }
     reinterpret_cast<T*>(P.fhat)[i] = from_double_rn<T>(v);
     reinterpret_cast<T*>(P.g)[i] = pos_inf<T>();     // c-transform outputs start at +inf
