@@ -54,7 +54,8 @@ enum {
     QWB_ERR_NOT_CONVERGED = 4, /* the exact coarse solver hit its pivot cap */
     QWB_ERR_TIMEOUT = 5,       /* a bounded device-side wait expired */
     QWB_ERR_OOM = 6,           /* device or host allocation failed */
-    QWB_ERR_UNSUPPORTED = 7    /* valid problem outside this build's limits */
+    QWB_ERR_UNSUPPORTED = 7,   /* valid problem outside this build's limits */
+    QWB_ERR_VERIFY = 8         /* QWB_FLAG_VERIFY found f_i + g_j > c_ij */
 };
 
 /* Flags for qwb_batch_create / qwb_bounds: passes a caller does not need.
@@ -71,6 +72,14 @@ enum {
                                   2-D FP32 pairs with kappa 4 or 8, the
                                   separable C-bar (see
                                   qwb_coarse_cost_separable) */
+    QWB_FLAG_VERIFY = 64,      /* after each dual pass, check f_i + g_j <= c_ij
+                                  on every pair of fine points (2-D; each
+                                  sum rounded upward, compared with a lower
+                                  bracket of the cost); a failure gives the
+                                  pair the status QWB_ERR_VERIFY.  N^4 checks
+                                  per pair (FP64 ones for F64 batches: slow);
+                                  the environment variable QWB_VERIFY=1
+                                  sets it for every batch */
     QWB_FLAG_SYMMETRIC_DUAL = 32 /* also run the dual pass from the coarse
                                   potential g~ (Sec. 3.5 from nu's side) and
                                   report the larger of the two lower bounds */

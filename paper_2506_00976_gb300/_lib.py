@@ -18,10 +18,10 @@ QWB_OK = 0
 QWB_PREC_F64 = 0
 QWB_PREC_MIXED = 1
 QWB_FLAG_NO_WEIGHTED, QWB_FLAG_NO_PRIMAL, QWB_FLAG_NO_DUAL, QWB_FLAG_MINCOST = 1, 2, 4, 8
-QWB_FLAG_SEPARABLE, QWB_FLAG_SYMMETRIC_DUAL = 16, 32
+QWB_FLAG_SEPARABLE, QWB_FLAG_SYMMETRIC_DUAL, QWB_FLAG_VERIFY = 16, 32, 64
 STATUS_NAMES = {0: "QWB_OK", 1: "QWB_ERR_INVALID_ARG", 2: "QWB_ERR_MASS", 3: "QWB_ERR_CUDA",
                 4: "QWB_ERR_NOT_CONVERGED", 5: "QWB_ERR_TIMEOUT", 6: "QWB_ERR_OOM",
-                7: "QWB_ERR_UNSUPPORTED"}
+                7: "QWB_ERR_UNSUPPORTED", 8: "QWB_ERR_VERIFY"}
 
 
 class QwbProblem(ctypes.Structure):

@@ -15,7 +15,7 @@ import torch
 from . import _lib
 from ._lib import QwbProblem, QwbResult, check
 from ._lib import (QWB_FLAG_MINCOST, QWB_FLAG_NO_DUAL, QWB_FLAG_NO_PRIMAL,  # noqa: F401
-                   QWB_FLAG_NO_WEIGHTED, QWB_FLAG_SEPARABLE, QWB_FLAG_SYMMETRIC_DUAL)
+                   QWB_FLAG_NO_WEIGHTED, QWB_FLAG_SEPARABLE, QWB_FLAG_SYMMETRIC_DUAL, QWB_FLAG_VERIFY)
 
 _CTX = {}
 _CTX_LOCK = threading.Lock()

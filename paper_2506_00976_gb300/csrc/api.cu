@@ -17,6 +17,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "fault.h"
 #include "kernels.h"
@@ -230,6 +232,7 @@ struct qwb_batch {
     int* dev_err = nullptr;             // device error word of bounded waits (0 = none)
     unsigned long long wait_ns = 0;     // limit of every bounded device wait (QWB_WAIT_TIMEOUT_MS)
     int fault_skip_chunk = -1;          // QWB_FAULT ipf_bulk_skip_chunk (tests), else -1
+    double verify_shift = 0.0;          // QWB_FAULT verify_shift (tests): tightens the verify check
     // pairs upscaled with a general kernel K (primalk_kernel, 2-D, kappa <= 8):
     // K per kappa, and prim_ids_d = [uniform pairs..., K pairs...]
     std::vector<std::pair<int, std::vector<double>>> upk;   // (kappa, K)
@@ -434,6 +437,7 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
     b->flags = flags;
     b->wait_ns = wait_timeout_ns();
     b->fault_skip_chunk = (int)fault_param("ipf_bulk_skip_chunk", -1);
+    b->verify_shift = (double)fault_param("verify_shift", 0);
     b->probs.assign(probs, probs + n);
     const size_t tsz = b->f64 ? 8 : 4;
     // sizes
@@ -781,6 +785,14 @@ static int pair_cbar_variant(const qwb_batch* b, int t) {
                                                                            : generic_cbar_variant(b->f64);
 }
 
+// An NVTX range over a host call (shown by profilers that record NVTX).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 static int mark(qwb_batch* b, int i, cudaStream_t s) {
     // external records become event nodes of a captured graph
     if (b->ev_ok) QWB_CUDA(cudaEventRecordWithFlags(b->kev[i], s, cudaEventRecordExternal));
@@ -898,6 +910,9 @@ static int enqueue_fine(qwb_batch* b, bool batched, cudaStream_t s) {
             for (int i = 5; i <= 8; ++i) if ((st = mark(b, i, s))) return st;
         }
         if ((st = mark(b, 9, s))) return st;
+        if (do_dual && (b->flags & QWB_FLAG_VERIFY) &&
+            (st = launch_verify(b->pairs_d, b->outs_d, b->pix_items_d, b->n_pix, b->f64, b->verify_shift, s)))
+            return st;
         if (do_dual && (b->flags & QWB_FLAG_SYMMETRIC_DUAL)) {
             // the same pass from g~: g-hat -> f -> g, keep the larger bound
             if ((st = launch_centre(b->pairs_d, b->outs_d, b->pair_ids_d, b->n, s, 1))) return st;
@@ -908,6 +923,9 @@ static int enqueue_fine(qwb_batch* b, bool batched, cudaStream_t s) {
                 if ((st = launch_ct_batched(b, phase, b->ct_cfg_b, cap, s))) return st;
             }
             if ((st = launch_lbsum(b->pairs_d, b->outs_d, b->pair_ids_d, b->n, b->f64, s, 1))) return st;
+            if ((b->flags & QWB_FLAG_VERIFY) &&
+                (st = launch_verify(b->pairs_d, b->outs_d, b->pix_items_d, b->n_pix, b->f64, b->verify_shift, s)))
+                return st;
         }
         return QWB_OK;
     }
@@ -952,6 +970,10 @@ static int enqueue_fine(qwb_batch* b, bool batched, cudaStream_t s) {
                 if ((st = launch_ctransform(b->pairs_d, b->ct_p_items_d + b->ct_off[t], b->ct_cnt[t], phase, c, b->probs[t].N, b->f64, 0, s))) return st;
             }
             if ((st = launch_lbsum(b->pairs_d, b->outs_d, id, 1, b->f64, s, side))) return st;
+            if ((b->flags & QWB_FLAG_VERIFY) &&
+                (st = launch_verify(b->pairs_d, b->outs_d, b->pix_items_d + b->pix_off[t], b->pix_cnt[t], b->f64,
+                                    b->verify_shift, s)))
+                return st;
         }
     }
     return QWB_OK;
@@ -1549,6 +1571,8 @@ static int batch_results(qwb_batch* b, qwb_result* out, cudaStream_t s) {
         if (b->flags & QWB_FLAG_NO_DUAL) { r.lb = 0.0; r.lb_p = -HUGE_VAL; }
         r.t_coarse_cost_ms = tc; r.t_solve_ms = b->t_solve_ms; r.t_primal_ms = tp; r.t_dual_ms = td;
         r.status = dev_err ? QWB_ERR_TIMEOUT : b->status[t];
+        if (r.status == QWB_OK && (b->flags & QWB_FLAG_VERIFY) && !(b->flags & QWB_FLAG_NO_DUAL) && o[t].verify_bad)
+            r.status = QWB_ERR_VERIFY;
     }
     if (dev_err) return fail(QWB_ERR_TIMEOUT, "a bounded device wait timed out (bulk-copy IPF sweeps)");
     return QWB_OK;
@@ -1589,7 +1613,9 @@ void qwb_ctx_destroy(qwb_ctx* ctx) {
 int qwb_batch_create(qwb_ctx* ctx, int32_t n_pairs, const qwb_problem* probs_h, int32_t ipf_sweeps,
                      int32_t flags, qwb_prec prec, qwb_batch** out) {
     if (!ctx || !out) return fail(QWB_ERR_INVALID_ARG, "qwb_batch_create: null argument");
-    if (flags & ~63) return fail(QWB_ERR_INVALID_ARG, "qwb_batch_create: unknown flags");
+    if (flags & ~127) return fail(QWB_ERR_INVALID_ARG, "qwb_batch_create: unknown flags");
+    if (const char* v = std::getenv("QWB_VERIFY"))          // the verify mode for every batch
+        if (std::strcmp(v, "0") != 0) flags |= QWB_FLAG_VERIFY;
     std::lock_guard<std::mutex> lk(ctx->mtx);
     QWB_CUDA(cudaSetDevice(ctx->device));
     return batch_build(ctx, n_pairs, probs_h, ipf_sweeps, flags, prec, out);
@@ -1605,6 +1631,7 @@ void qwb_batch_destroy(qwb_batch* batch) {
 int qwb_batch_coarse(qwb_batch* b, const double* const* mu_d, const double* const* nu_d,
                      int32_t batched, void* stream) {
     if (!b) return fail(QWB_ERR_INVALID_ARG, "null batch");
+    const NvtxRange range("qwb coarse pass (SumPool, C-bar)");
     QWB_CUDA(cudaSetDevice(b->ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
     int st = batch_set_measures(b, mu_d, nu_d);
@@ -1618,6 +1645,7 @@ int qwb_batch_coarse(qwb_batch* b, const double* const* mu_d, const double* cons
 }
 
 int qwb_batch_solve(qwb_batch* b, int32_t n_threads, void* stream) {
+    const NvtxRange range("qwb exact coarse solves");
     if (!b) return fail(QWB_ERR_INVALID_ARG, "null batch");
     QWB_CUDA(cudaSetDevice(b->ctx->device));
     return batch_solve(b, n_threads, (cudaStream_t)stream);
@@ -1625,6 +1653,7 @@ int qwb_batch_solve(qwb_batch* b, int32_t n_threads, void* stream) {
 
 int qwb_batch_fine(qwb_batch* b, const double* const* mu_d, const double* const* nu_d,
                    int32_t batched, void* stream) {
+    const NvtxRange range("qwb fine passes (IPF and upper bound, c-transforms and lower bound)");
     if (!b) return fail(QWB_ERR_INVALID_ARG, "null batch");
     if (!b->solved) return fail(QWB_ERR_INVALID_ARG, "qwb_batch_fine needs a completed qwb_batch_solve");
     QWB_CUDA(cudaSetDevice(b->ctx->device));

@@ -52,6 +52,7 @@ const char* qwb_status_string(int status) {
         case QWB_ERR_TIMEOUT: return "QWB_ERR_TIMEOUT";
         case QWB_ERR_OOM: return "QWB_ERR_OOM";
         case QWB_ERR_UNSUPPORTED: return "QWB_ERR_UNSUPPORTED";
+        case QWB_ERR_VERIFY: return "QWB_ERR_VERIFY";
         default: return "QWB_ERR_UNKNOWN";
     }
 }

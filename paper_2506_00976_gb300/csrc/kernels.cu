@@ -3009,6 +3009,63 @@ __global__ void upsample_kernel(const PairDev* __restrict__ pairs, const PairOut
     reinterpret_cast<T*>(P.f)[i] = pos_inf<T>();
 }
 
+// --------------------------------------------------------------------------
+// verify: the certificate check of a dual pass.  The lower bound rests on the
+// admissibility of the pair (f, g): f_i + g_j <= c_ij for every pair of fine
+// points (the dual constraint of Sec. 2.1, which the c-transforms of Sec. 3.5
+// restore).  One thread per output point j; the input rows of f are staged
+// through shared memory.  Each sum is rounded upward and compared with a
+// lower bracket of the cost (the exact integer for p = 2, the cost table's
+// lower bracket otherwise), so a pass proves admissibility; a failure sets
+// the pair's flag.  2-D pairs only (volumes are skipped).
+// --------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+verify_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs, const PixItem* __restrict__ items,
+              T shift) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* frow = reinterpret_cast<T*>(smem_raw);                 // one row of f (N values)
+    const PixItem I = items[blockIdx.x];
+    const PairDev& P = pairs[I.pair];
+    const int N = P.N, m = P.m;
+    if (P.d != 2 || (size_t)N * sizeof(T) > 48 * 1024) return;   // the whole CTA leaves
+    const int j = I.start + threadIdx.x;
+    const bool valid = j < m;
+    const T* f = reinterpret_cast<const T*>(P.f);
+    const T gj = valid ? reinterpret_cast<const T*>(P.g)[j] : T(0);
+    const int j1 = valid ? j / N : 0, j2 = valid ? j - j1 * N : 0;
+    const bool p2 = P.p == 2.0 && N <= 2896;                  // squared offsets exact in FP32
+    const T* tab = reinterpret_cast<const T*>(P.ctab_lo);
+    int bad = 0;
+    for (int i1 = 0; i1 < N; ++i1) {
+        __syncthreads();
+        for (int q = threadIdx.x; q < N; q += blockDim.x) frow[q] = f[(size_t)i1 * N + q];
+        __syncthreads();
+        if (!valid) continue;
+        const int di1 = abs(i1 - j1);
+        const T a = (T)(di1 * di1);
+        const T* trow = tab + (size_t)di1 * N;
+        for (int i2 = 0; i2 < N; ++i2) {
+            const int d2 = i2 - j2;
+            const T c = p2 ? a + (T)(d2 * d2) : trow[abs(d2)];
+            bad |= add_ru(frow[i2], gj) > c - shift;
+        }
+    }
+    if (bad) atomicOr(&outs[P.out_index].verify_bad, 1);
+}
+
+int launch_verify(const PairDev* pairs_d, PairOut* outs_d, const PixItem* items, int n_items, bool f64,
+                  double shift, cudaStream_t stream) {
+    if (n_items <= 0) return QWB_OK;
+    // shared memory: one row of f for the largest side the items can have
+    // (at most the 48 KB default: N <= 6144 in FP64)
+    const size_t smem = 48 * 1024;
+    if (f64) verify_kernel<double><<<n_items, 256, smem, stream>>>(pairs_d, outs_d, items, shift);
+    else verify_kernel<float><<<n_items, 256, smem, stream>>>(pairs_d, outs_d, items, (float)shift);
+    QWB_LAUNCHED();
+    return QWB_OK;
+}
+
 int launch_upsample(const PairDev* pairs_d, PairOut* outs_d, const PixItem* items, int n_items,
                     bool f64, cudaStream_t stream, int side) {
     if (n_items <= 0) return QWB_OK;

@@ -66,7 +66,8 @@ struct PairOut {
     double lb, lb_p, w_hat_p, ub_primal, delta_mu, delta_nu, ipf_residual;
     double mass_mu, mass_nu, centre_shift;
     int bad_mu, bad_nu;
-    int sweeps_done, pad;
+    int sweeps_done;
+    int verify_bad;         // QWB_FLAG_VERIFY: 1 when some f_i + g_j > c_ij was found
 };
 
 struct CbarItem { int pair, w1, seg, pad; };   // wrapped block-row diagonal w1 (seg unused)
@@ -117,6 +118,13 @@ int launch_primal(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, 
 // chunk unissued (host-side fault injection for the time-out path), else -1.
 int launch_ipf_stream(const PairDev* pairs_d, const int* pair_ids, int n_pairs, int kappa, int C, int n,
                       int N, int* err, unsigned long long timeout_ns, int skip_chunk, cudaStream_t stream);
+// The certificate check of the dual potentials (QWB_FLAG_VERIFY): every pair
+// (i, j) of fine points of a 2-D pair, f_i + g_j rounded up against a lower
+// bracket of c_ij minus `shift` (0; a positive shift is host-side fault
+// injection that makes tight pairs fail); sets outs[..].verify_bad.  Items:
+// the upsample items (256 output points each).
+int launch_verify(const PairDev* pairs_d, PairOut* outs_d, const PixItem* items, int n_items, bool f64,
+                  double shift, cudaStream_t stream);
 // primal pass with a general upscaling kernel (P.upK set; d = 2, kappa <= kappa_max <= 8;
 // all_kappa4: every pair of the launch has kappa 4, which selects the register-row kernel)
 int launch_primalk(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs, int kappa_max,
