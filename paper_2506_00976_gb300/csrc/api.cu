@@ -456,7 +456,7 @@ static int batch_build(qwb_ctx* ctx, int n, const qwb_problem* probs, int sweeps
         if (dd == 3) b->has_3d = true;
         const bool pow2 = dd == 2 && !(nn & (nn - 1)) && nn <= 64 && !b->f64;
         const bool sepcb = want_cbar && separable(t) && dd == 2 && !b->f64 && (kap == 4 || kap == 8) &&
-                           sizeof(float) * (size_t)nn * (2 * kap + 1) <= 48 * 1024;
+                           sizeof(float) * ((size_t)nn * 2 * kap + ((nn + 3) & ~3)) <= 48 * 1024;
         const int grp = sepcb ? (kap == 4 ? 12 : 16) : (pow2 && kap == 4) ? 4 : (pow2 && kap == 8) ? 8 : 0;
         b->cbar_group.push_back((char)grp);
         if (grp >= 12) {

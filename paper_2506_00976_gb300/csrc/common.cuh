@@ -70,6 +70,15 @@ __device__ __forceinline__ double widen_f32(float v) {
     return __longlong_as_double((long long)bits);
 }
 __device__ __forceinline__ double widen_f32(double v) { return v; }
+// The same for a value that is usually a positive normal float (a C-bar
+// entry): then the FP64 bits are the FP32 bits shifted by 29 with the
+// exponent re-biased by 1023 - 127; anything else takes widen_f32.
+__device__ __forceinline__ double widen_pos_f32(float v) {
+    const unsigned u = __float_as_uint(v);
+    if (u - 0x00800000u < 0x7f000000u)                  // sign 0, exponent field 1..254
+        return __longlong_as_double((long long)(((unsigned long long)u << 29) + (896ull << 52)));
+    return widen_f32(v);
+}
 
 template <typename T> __device__ __forceinline__ T pos_inf();
 template <> __device__ __forceinline__ float pos_inf<float>() { return __int_as_float(0x7f800000); }

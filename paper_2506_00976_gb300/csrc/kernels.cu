@@ -626,7 +626,7 @@ cbar4_kernel(const PairDev* __restrict__ pairs, const CbarItem* __restrict__ ite
                     const float rk = rk_s[s * n + k2], rl = rl_s[s * n + l2];
                     double outv;
                     if (rk > 0.0f && rl > 0.0f) {
-                        outv = widen_f32(mul_ru(mul_ru(acc, rk), rl));
+                        outv = widen_pos_f32(mul_ru(mul_ru(acc, rk), rl));
                     } else {
                         double mean = 0.0;
 #pragma unroll
@@ -774,7 +774,7 @@ cbar8_kernel(const PairDev* __restrict__ pairs, const CbarItem* __restrict__ ite
                     const int k = (k1 << lg) + k2, l = (l1 << lg) + l2;
                     const float rk = rk_s[s * n + k2], rl = rl_s[s * n + l2];
                     cbar[(size_t)k * M + l] = (rk > 0.0f && rl > 0.0f)
-                                                  ? widen_f32(mul_ru(mul_ru(acc, rk), rl))
+                                                  ? widen_pos_f32(mul_ru(mul_ru(acc, rk), rl))
                                                   : cbar8_special(P, k, l, acc, wbase, RL);
                 }
             }
@@ -929,9 +929,13 @@ static int cbar_dispatch(const PairDev* pairs_d, const CbarItem* items, int n_it
 // only (the CTA's source block row k1 is fixed), so they are formed once per
 // target and reused over the row's n source blocks.  One item per (pair,
 // source block row): threads walk the targets l, so every output row is
-// written coalesced.
+// written coalesced.  WPRE (coarse sides with n^2 kappa floats in shared
+// memory): the second axis's weights Wt[k2][l2][b2] = sum_a2 Cmu[a2]
+// (D2 + a2 - b2)^2 depend on the source block and the target's block column
+// only, so they are formed once per item and each entry then takes kappa
+// multiply-adds per axis (the same rounded-up terms, grouped the other way).
 // --------------------------------------------------------------------------
-template <int KAP>
+template <int KAP, bool WPRE>
 __global__ void __launch_bounds__(256)
 cbar_sep_kernel(const PairDev* __restrict__ pairs, const CbarItem* __restrict__ items, int n_items) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -945,7 +949,26 @@ cbar_sep_kernel(const PairDev* __restrict__ pairs, const CbarItem* __restrict__ 
         __syncthreads();                                     // the previous item's readers are done
         for (int q = threadIdx.x; q < n * W; q += blockDim.x) ms[q] = P.bsum[(size_t)k1 * n * W + q];
         for (int q = threadIdx.x; q < n; q += blockDim.x) rk_s[q] = P.mu_rinv32[k1 * n + q];
+        float* wt = rk_s + ((n + 3) & ~3);                   // WPRE: [n][n][KAP], 16-byte aligned
         __syncthreads();
+        if constexpr (WPRE) {
+            for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
+                const int k2 = q / n, l2 = q - k2 * n;
+                const float* mk = ms + k2 * W + KAP;           // column sums of source block k2
+                const int D2 = KAP * (k2 - l2);
+#pragma unroll
+                for (int b2 = 0; b2 < KAP; ++b2) {
+                    float v = 0.0f;
+#pragma unroll
+                    for (int a2 = 0; a2 < KAP; ++a2) {
+                        const float d = (float)(D2 + a2 - b2);
+                        v = fma_ru(mk[a2], d * d, v);
+                    }
+                    wt[q * KAP + b2] = v;
+                }
+            }
+            __syncthreads();
+        }
         const float* nsum = P.bsum + (size_t)M * W;
         for (int l = threadIdx.x; l < M; l += blockDim.x) {
             const int l1 = l / n, l2 = l - l1 * n;
@@ -974,27 +997,36 @@ cbar_sep_kernel(const PairDev* __restrict__ pairs, const CbarItem* __restrict__ 
             for (int k2 = 0; k2 < n; ++k2) {
                 const float* mk = ms + k2 * W;
                 const int D2 = KAP * (k2 - l2);
-                float sq[2 * KAP - 1];                       // (D2 + e - (KAP - 1))^2, exact
-#pragma unroll
-                for (int e = 0; e < 2 * KAP - 1; ++e) {
-                    const float d = (float)(D2 + e - (KAP - 1));
-                    sq[e] = d * d;
-                }
                 float t1 = 0.0f, t2 = 0.0f;
+                if constexpr (WPRE) {
+                    const float* w = wt + (k2 * n + l2) * KAP;
 #pragma unroll
-                for (int a = 0; a < KAP; ++a) {
-                    float v = 0.0f;
+                    for (int a = 0; a < KAP; ++a) {
+                        t2 = fma_ru(Cn[a], w[a], t2);
+                        t1 = fma_ru(mk[a], V1[a], t1);
+                    }
+                } else {
+                    float sq[2 * KAP - 1];                   // (D2 + e - (KAP - 1))^2, exact
 #pragma unroll
-                    for (int b2 = 0; b2 < KAP; ++b2) v = fma_ru(Cn[b2], sq[a - b2 + KAP - 1], v);
-                    t2 = fma_ru(mk[KAP + a], v, t2);
-                    t1 = fma_ru(mk[a], V1[a], t1);
+                    for (int e = 0; e < 2 * KAP - 1; ++e) {
+                        const float d = (float)(D2 + e - (KAP - 1));
+                        sq[e] = d * d;
+                    }
+#pragma unroll
+                    for (int a = 0; a < KAP; ++a) {
+                        float v = 0.0f;
+#pragma unroll
+                        for (int b2 = 0; b2 < KAP; ++b2) v = fma_ru(Cn[b2], sq[a - b2 + KAP - 1], v);
+                        t2 = fma_ru(mk[KAP + a], v, t2);
+                        t1 = fma_ru(mk[a], V1[a], t1);
+                    }
                 }
                 const float acc = __fadd_ru(t1, t2);
                 const int k = k1 * n + k2;
                 const float rk = rk_s[k2];
                 double outv;
                 if (rk > 0.0f && rl > 0.0f) {
-                    outv = widen_f32(mul_ru(mul_ru(acc, rk), rl));
+                    outv = widen_pos_f32(mul_ru(mul_ru(acc, rk), rl));
                 } else {
                     // unweighted mean over the block pair: per axis E (D + a - b)^2
                     // = D^2 + (kappa^2 - 1) / 6 for independent uniform a, b
@@ -1012,10 +1044,16 @@ int launch_cbar_sep(const PairDev* pairs_d, const CbarItem* items, int n_items, 
                     cudaStream_t stream) {
     if (n_items <= 0) return QWB_OK;
     if (kappa != 4 && kappa != 8) return QWB_ERR_UNSUPPORTED;
-    const size_t smem = sizeof(float) * (size_t)n_max * (2 * kappa + 1);
-    if (smem > 48 * 1024) return QWB_ERR_UNSUPPORTED;
-    if (kappa == 4) cbar_sep_kernel<4><<<n_items, 256, smem, stream>>>(pairs_d, items, n_items);
-    else cbar_sep_kernel<8><<<n_items, 256, smem, stream>>>(pairs_d, items, n_items);
+    const size_t base = sizeof(float) * ((size_t)n_max * 2 * kappa + ((n_max + 3) & ~3));
+    if (base > 48 * 1024) return QWB_ERR_UNSUPPORTED;
+    const size_t wpre = base + sizeof(float) * (size_t)n_max * n_max * kappa;
+    if (wpre <= 48 * 1024) {
+        if (kappa == 4) cbar_sep_kernel<4, true><<<n_items, 256, wpre, stream>>>(pairs_d, items, n_items);
+        else cbar_sep_kernel<8, true><<<n_items, 256, wpre, stream>>>(pairs_d, items, n_items);
+    } else {
+        if (kappa == 4) cbar_sep_kernel<4, false><<<n_items, 256, base, stream>>>(pairs_d, items, n_items);
+        else cbar_sep_kernel<8, false><<<n_items, 256, base, stream>>>(pairs_d, items, n_items);
+    }
     QWB_LAUNCHED();
     return QWB_OK;
 }

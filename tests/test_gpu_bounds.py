@@ -351,3 +351,37 @@ def test_fine_ipf_scalings(sweeps, batched, cluster):
                 ref = O.ipf(mus[t], nus[t], plan, N, kappa, max_sweeps=sweeps)
                 np.testing.assert_allclose(a, ref["a"], rtol=2e-5, atol=0)
                 np.testing.assert_allclose(bb, ref["b"], rtol=2e-5, atol=0)
+
+
+@pytest.mark.parametrize("cluster", [2, 4 | 64, 8, 16])
+def test_fine_ipf_warp_rows_kappa8(cluster):
+    """Cluster sweeps at kappa 8 where whole warps own 32 blocks of one block
+    row (coarse sides 32 and 64), which move the fine rows as 64 consecutive
+    float4 per warp: the scalings reach the fixed point a = kappa^2 mu / mu~
+    (and b likewise) and the certified bound equals the in-kernel sweeps' bit
+    for bit (the FP64 block-scalar sweeps define it)."""
+    cases = [(256, 8, 2.0, "field"), (512, 8, 2.0, "gauss")]
+    mus, nus, probs = [], [], []
+    for i, (N, kappa, p, cls) in enumerate(cases):
+        mus.append(synth.make_measure(N, cls, 90 + i, 0)); nus.append(synth.make_measure(N, cls, 90 + i, 1))
+        probs.append((N, kappa, p))
+    md, nd = [T(x) for x in mus], [T(x) for x in nus]
+    ub = {}
+    for form in (0, cluster):
+        with api.Batch(probs, ipf_sweeps=7, prec="mixed", flags=1 | 4) as b:
+            b.coarse(md, nd)
+            b.solve()
+            b.set_ipf_cluster(form)
+            b.fine(md, nd)
+            res = b.results()
+            assert all(r["status"] == 0 for r in res)
+            ub[form] = [r["ub_primal"] for r in res]
+            if form:
+                for t, (N, kappa, p) in enumerate(probs):
+                    a, bb = (x.cpu().numpy() for x in b.fine_scalings(t))
+                    for got, meas in ((a, mus[t]), (bb, nus[t])):
+                        coarse = O.sumpool(meas, N, kappa)
+                        blk = np.repeat(np.repeat(coarse.reshape(N // kappa, N // kappa), kappa, 0), kappa, 1).ravel()
+                        want = np.where(blk > 0, kappa ** 2 * meas / np.where(blk > 0, blk, 1.0), 0.0)
+                        np.testing.assert_allclose(got, want, rtol=2e-5, atol=0)
+    assert ub[0] == ub[cluster]
