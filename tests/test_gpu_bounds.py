@@ -126,6 +126,25 @@ def test_adjoint_kernel_fd(p, prec):
         assert grad[i] == pytest.approx(fd, rel=1e-3 if prec == "mixed" else 1e-5, abs=1e-6)
 
 
+@pytest.mark.parametrize("p", [1.0, 2.0])
+@pytest.mark.parametrize("prec", ["mixed", "f64"])
+def test_adjoint_vs_oracle_64(p, prec):
+    """At 64 x 64 the adjoint kernel's gradient, from the GPU dual pass on the
+    oracle's coarse potential, against the oracle's gradient formula on the
+    oracle's own potentials (lb_grad_mu, pinned to finite differences on the
+    CPU), element by element."""
+    N, kappa = 64, 4
+    mu, nu = synth.make_measure(N, "field", 36, 0), synth.make_measure(N, "cauchy", 36, 1)
+    mt, nt = O.sumpool(mu, N, kappa), O.sumpool(nu, N, kappa)
+    _, f_c, _, _ = O.exact_ot(O.coarse_cost_centre(N, kappa, p), mt, nt)
+    r = api.dual_upscale_ctransform(T(mu), T(nu), N, kappa, p, f_c, prec=prec)
+    grad = api.lb_adjoint(r["f"], T(mu), N, p, r["lb_p"]).cpu().numpy()
+    ref = O.lb_dual(mu, nu, N, kappa, p, f_c=f_c)
+    want = O.lb_grad_mu(mu, ref["f"], ref["lb_p"], p)
+    scale = np.abs(want).max()
+    np.testing.assert_allclose(grad, want, rtol=0, atol=(1e-4 if prec == "mixed" else 1e-9) * scale)
+
+
 def test_lower_bound_autograd():
     """LowerBound.apply: forward equals the batch LB; backward is the adjoint of
     its own potential; finite differences through the whole method (coarse
