@@ -440,8 +440,10 @@ int qwb_batch_set_ipf_cluster(qwb_batch* batch, int32_t C);
  * entry), UNSUPPORTED (kappa > 8), CUDA, OOM. */
 int qwb_batch_set_upscale_kernel(qwb_batch* batch, int32_t kappa, const double* K_d);
 /* Where the general-kernel primal pass (the pairs given a kernel K by
- * qwb_batch_set_upscale_kernel) runs: C = 0 one CTA per pair; C = 1, 2, 4, 8
- * the cluster form, one pair on a thread-block cluster of C CTAs of
+ * qwb_batch_set_upscale_kernel) runs: C = 0 one CTA per pair; C = -1 one CTA
+ * per pair for the sweeps, then the certified evaluation spread over one CTA
+ * per (pair, coarse block row) in four launches; C = 1, 2, 4, 8 the cluster
+ * form, one pair on a thread-block cluster of C CTAs of
  * `threads` (256, 128 or 64) threads that split the coarse block rows and
  * read each other's K-product rows through distributed shared memory, which
  * lets a batch of pairs fill every SM at once (Sec. 3.4, eq. coupling tensor
@@ -452,8 +454,8 @@ int qwb_batch_set_upscale_kernel(qwb_batch* batch, int32_t kappa, const double* 
  * for this batch only, the autotuner's choice, which times the forms on the
  * batch's own data; batched and per-pair passes use the same form.  Synchronises the device
  * and drops the batch's captured fine-pass graphs.  Errors: INVALID_ARG (C
- * or threads not listed), UNSUPPORTED (C > 0 while the batch's K pairs
- * cannot take the cluster form), CUDA. */
+ * or threads not listed), UNSUPPORTED (C != 0 while the batch's K pairs
+ * cannot take the cluster or spread form), CUDA. */
 int qwb_batch_set_upscale_cluster(qwb_batch* batch, int32_t C, int32_t threads);
 /* Pair t's scalings after the fine IPF sweeps of the last qwb_batch_fine
  * (Sec. 3.4, IPF paragraph; Alg. 4): the pass-type a, b with

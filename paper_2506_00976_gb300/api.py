@@ -366,8 +366,10 @@ class Batch:
               "qwb_batch_set_upscale_kernel")
 
     def set_upscale_cluster(self, C, threads=128):
-        """Run the general-kernel primal pass one CTA per pair (C = 0) or on
-        clusters of C in {1, 2, 4, 8} CTAs of `threads` threads per pair."""
+        """Run the general-kernel primal pass one CTA per pair (C = 0), one CTA
+        per pair for the sweeps with the evaluation spread over many CTAs
+        (C = -1), or on clusters of C in {1, 2, 4, 8} CTAs of `threads`
+        threads per pair."""
         check(_lib.load().qwb_batch_set_upscale_cluster(self._h, int(C), int(threads)),
               "qwb_batch_set_upscale_cluster")
 

@@ -246,7 +246,8 @@ struct qwb_batch {
     // (else 0: the cluster form is not available); upk_C = 0 runs
     // primalk_kernel, else clusters of upk_C CTAs of the thread variant upk_var
     int upk_kappa = 0, upk_n_max = 0, upk_C = 0, upk_var = 0;
-    int upk_req_C = -1, upk_req_var = 0;    // qwb_batch_set_upscale_cluster's choice (-1: none)
+    bool upk_req = false;               // qwb_batch_set_upscale_cluster was called:
+    int upk_req_C = 0, upk_req_var = 0;     //   its choice
     std::vector<int> prep_off, prep_cnt, pix_off, pix_cnt, cbar_off, cbar_cnt, ct_off, ct_cnt;
     int n_prep = 0, n_pix = 0, n_cbar = 0, n_ct_b = 0;
     int n_ct_b_p2 = 0;   // batched c-transform items: the p = 2 pairs' items come first
@@ -869,6 +870,12 @@ static int launch_upk(qwb_batch* b, const int* ids, int n, cudaStream_t s) {
     if (b->upk_C > 0 && b->upk_kappa)
         return launch_primalk_cl(b->pairs_d, b->outs_d, ids, n, b->upk_kappa, b->upk_C, b->upk_var,
                                  b->upk_n_max, s);
+    if (b->upk_C < 0 && b->upk_kappa) {        // one-CTA sweeps, evaluation spread over the GPU
+        const int st = launch_primalk(b->pairs_d, b->outs_d, ids, n, b->upk_kappa_max, b->upk_M_max, 0,
+                                      b->upk_m_max, b->upk_all4, b->f64, s, 1);
+        if (st) return st;
+        return launch_primalk_eval(b->pairs_d, b->outs_d, ids, n, b->upk_kappa, b->upk_n_max, s);
+    }
     return launch_primalk(b->pairs_d, b->outs_d, ids, n, b->upk_kappa_max, b->upk_M_max, 0, b->upk_m_max,
                           b->upk_all4, b->f64, s);
 }
@@ -937,6 +944,12 @@ static int enqueue_fine(qwb_batch* b, bool batched, cudaStream_t s) {
                 if ((st = launch_primalk_cl(b->pairs_d, b->outs_d, id, 1, b->upk_kappa, b->upk_C, b->upk_var,
                                             b->probs[t].N / b->upk_kappa, s)))
                     return st;
+            } else if (b->upk_C < 0) {
+                const int kap = b->probs[t].kappa;
+                if ((st = launch_primalk(b->pairs_d, b->outs_d, id, 1, kap, M, 0, b->probs[t].N * b->probs[t].N,
+                                         kap == 4, b->f64, s, 1)))
+                    return st;
+                if ((st = launch_primalk_eval(b->pairs_d, b->outs_d, id, 1, kap, b->probs[t].N / kap, s))) return st;
             } else {
                 const int kap = b->probs[t].kappa;
                 if ((st = launch_primalk(b->pairs_d, b->outs_d, id, 1, kap, M, 0, b->probs[t].N * b->probs[t].N,
@@ -1160,7 +1173,7 @@ static int tune_ipf(qwb_batch* b, cudaStream_t s) {
 // CTA, timed as the launch over the batch's K pairs.
 static int tune_upk(qwb_batch* b, cudaStream_t s) {
     TuneEntry* e = b->tune;
-    if (!b->n_upk || !b->upk_kappa || b->upk_req_C >= 0) return QWB_OK;
+    if (!b->n_upk || !b->upk_kappa || b->upk_req) return QWB_OK;
     if (e && e->upk_done) {                              // timed by another batch of this signature
         b->upk_C = e->upk_C;
         b->upk_var = e->upk_var;
@@ -1169,7 +1182,7 @@ static int tune_upk(qwb_batch* b, cudaStream_t s) {
     if (!b->ctx->autotune || !e || !b->ev_ok || (b->flags & QWB_FLAG_NO_PRIMAL)) return QWB_OK;
     static const int threads_of[3] = {256, 128, 64};
     struct Cand { int C, var; };
-    const Cand cands[] = {{0, 0}, {1, 0}, {2, 0}, {2, 1}, {4, 1}, {4, 2}, {8, 1}, {8, 2}};
+    const Cand cands[] = {{0, 0}, {-1, 0}, {1, 0}, {2, 0}, {2, 1}, {4, 1}, {4, 2}, {8, 1}, {8, 2}};
     std::ostringstream rep;
     rep << "{";
     double best = 1e30;
@@ -1186,8 +1199,8 @@ static int tune_upk(qwb_batch* b, cudaStream_t s) {
         if (st == QWB_ERR_UNSUPPORTED) continue;             // shared memory does not fit this size
         if (st) { b->upk_C = 0; return st; }
         rep << (first ? "" : ", ") << "\"";
-        if (c.C) rep << "cluster" << c.C << "x" << threads_of[c.var];
-        else rep << "single";
+        if (c.C > 0) rep << "cluster" << c.C << "x" << threads_of[c.var];
+        else rep << (c.C < 0 ? "single_sweeps_spread_eval" : "single");
         rep << "\": " << ms;
         first = false;
         if (ms < best) { best = ms; pick = c; }
@@ -1705,9 +1718,9 @@ int qwb_batch_tuning(qwb_batch* b, char* json_out, int32_t capacity) {
       << "}, \"ipf\": {\"cluster\": " << b->ipf_C
       << ", \"candidates_ms\": " << (b->tune && !b->tune->ipf_report.empty() ? b->tune->ipf_report : "{}")
       << "}, \"upscale_kernel\": {\"cluster\": " << b->upk_C << ", \"threads\": "
-      << (b->upk_C ? (b->upk_var == 0 ? 256 : b->upk_var == 1 ? 128 : 64) : (b->f64 ? 512 : 1024))
+      << (b->upk_C > 0 ? (b->upk_var == 0 ? 256 : b->upk_var == 1 ? 128 : 64) : (b->f64 ? 512 : 1024))
       << ", \"candidates_ms\": "
-      << (b->upk_req_C >= 0 ? std::string("\"set\"")
+      << (b->upk_req ? std::string("\"set\"")
                             : b->tune && !b->tune->upk_report.empty() ? b->tune->upk_report : std::string("{}"))
       << "}, \"enabled\": " << (b->ctx->autotune ? "true" : "false") << "}";
     const std::string str = o.str();
@@ -1785,10 +1798,10 @@ int qwb_batch_set_ipf_cluster(qwb_batch* b, int32_t C) {
 }
 
 int qwb_batch_set_upscale_cluster(qwb_batch* b, int32_t C, int32_t threads) {
-    if (!b || (C != 0 && C != 1 && C != 2 && C != 4 && C != 8) ||
-        (C != 0 && threads != 256 && threads != 128 && threads != 64))
+    if (!b || (C != -1 && C != 0 && C != 1 && C != 2 && C != 4 && C != 8) ||
+        (C > 0 && threads != 256 && threads != 128 && threads != 64))
         return fail(QWB_ERR_INVALID_ARG,
-                    "qwb_batch_set_upscale_cluster: C must be 0, 1, 2, 4 or 8 and threads 256, 128 or 64");
+                    "qwb_batch_set_upscale_cluster: C must be -1, 0, 1, 2, 4 or 8 and threads 256, 128 or 64");
     if (C != 0 && b->n_upk && !b->upk_kappa)
         return fail(QWB_ERR_UNSUPPORTED,
                     "the cluster form needs FP32 and one block side (2, 4 or 8) for every pair with a kernel K");
@@ -1800,7 +1813,8 @@ int qwb_batch_set_upscale_cluster(qwb_batch* b, int32_t C, int32_t threads) {
         else keep.push_back(g);
     }
     b->graphs.swap(keep);
-    const int var = C == 0 ? 0 : threads == 256 ? 0 : threads == 128 ? 1 : 2;
+    const int var = C <= 0 ? 0 : threads == 256 ? 0 : threads == 128 ? 1 : 2;
+    b->upk_req = true;
     b->upk_req_C = C;
     b->upk_req_var = var;
     b->upk_C = b->upk_kappa ? C : 0;
@@ -1906,7 +1920,7 @@ int qwb_batch_set_upscale_kernel(qwb_batch* b, int32_t kappa, const double* K_d)
         }
         if (same) b->upk_kappa = k0;
     }
-    if (b->upk_req_C >= 0) { b->upk_C = b->upk_req_C; b->upk_var = b->upk_req_var; }
+    if (b->upk_req) { b->upk_C = b->upk_req_C; b->upk_var = b->upk_req_var; }
     else if (b->tune && b->tune->upk_done) { b->upk_C = b->tune->upk_C; b->upk_var = b->tune->upk_var; }
     if (!b->upk_kappa) b->upk_C = 0;
     uni.insert(uni.end(), kp.begin(), kp.end());

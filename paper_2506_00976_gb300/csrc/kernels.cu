@@ -1616,7 +1616,7 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& t) 
 template <typename T, int KK>
 __global__ void __launch_bounds__(sizeof(T) == 4 ? PRIMALK_THREADS_F32 : PRIMALK_THREADS_F64, 1)
 primalk_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
-               const int* __restrict__ pair_ids, int csr_cap, int kk_max, int kb_cap) {
+               const int* __restrict__ pair_ids, int csr_cap, int kk_max, int kb_cap, int sweeps_only) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[33];
     const PairDev& P = pairs[pair_ids[blockIdx.x]];
@@ -1782,6 +1782,9 @@ primalk_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
             if (P.a_out) P.a_out[i] = widen_f32(a[t]);
             if (P.b_out) P.b_out[i] = widen_f32(b[t]);
         }
+    // sweeps_only: the evaluation runs spread over many CTAs (primalk_eval_*
+    // kernels); a, b stay block-major for them
+    if (sweeps_only) return;
     // ---- certified evaluation -----------------------------------------------
     // Per side: each marginal entry mu-hat_i (nu-hat_i) is evaluated as
     // h_i = x_i sum_e pi~_e kd_e, kd = sum_w K' x' (non-negative terms), with
@@ -1976,7 +1979,8 @@ primalk_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
 }
 
 int launch_primalk(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs, int kappa_max,
-                   int M_max, int nnz_max, int m_max, bool all_kappa4, bool f64, cudaStream_t stream) {
+                   int M_max, int nnz_max, int m_max, bool all_kappa4, bool f64, cudaStream_t stream,
+                   int sweeps_only) {
     if (n_pairs <= 0) return QWB_OK;
     if (kappa_max > 8) return QWB_ERR_UNSUPPORTED;
     const size_t tsz = f64 ? 8 : 4;
@@ -1997,7 +2001,7 @@ int launch_primalk(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids,
     const int threads = f64 ? PRIMALK_THREADS_F64 : PRIMALK_THREADS_F32;
     auto run = [&](auto kern) -> int {
         QWB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<n_pairs, threads, smem, stream>>>(pairs_d, outs_d, pair_ids, csr_cap, kk, kb_cap);
+        kern<<<n_pairs, threads, smem, stream>>>(pairs_d, outs_d, pair_ids, csr_cap, kk, kb_cap, sweeps_only);
         QWB_LAUNCHED();
         return QWB_OK;
     };
@@ -2455,6 +2459,292 @@ int launch_primalk_cl(const PairDev* pairs_d, PairOut* outs_d, const int* pair_i
         case 64 * 4 + 1: return run(primalk_cl_kernel<64, 128, 5>);
         default: return run(primalk_cl_kernel<64, 64, 10>);
     }
+}
+
+// --------------------------------------------------------------------------
+// primalk_eval: the certified evaluation of the general-kernel primal pass
+// (the enclosures of primalk_cl_kernel) spread over one CTA per (pair,
+// coarse block row), after the one-CTA sweeps (primalk_kernel with
+// sweeps_only) left a, b block-major.  Four launches: the K products of both
+// sides per row (kd, FP64, into the pair's kscratch), the marginal entries,
+// the support cost and the TV terms per row (partial sums into the pair's
+// kb_t scratch), one combination per pair, then the pixel layout of a, b per
+// row (a row's positions map onto themselves).  With many small CTAs the
+// FP64 work reaches every SM instead of one SM per pair.
+// --------------------------------------------------------------------------
+constexpr int PKE_THREADS = 128;
+
+template <int KK>
+__global__ void __launch_bounds__(PKE_THREADS)
+primalk_eval_kd_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair_ids, int n_max) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int q4 = KK / 4;
+    const PairDev& P = pairs[pair_ids[blockIdx.x / n_max]];
+    const int k1 = blockIdx.x % n_max, n = P.n, m = P.m;
+    if (k1 >= n) return;
+    float* Ks = reinterpret_cast<float*>(smem_raw);           // row w: K'[w][.]
+    float* KsT = Ks + KK * KK;                                // row w: K'[.][w]
+    for (int t = threadIdx.x; t < KK * KK; t += blockDim.x) {
+        const int u = t / KK, w = t - u * KK;
+        const float kt = reinterpret_cast<const float*>(P.upK_t)[t];
+        Ks[t] = kt;
+        KsT[w * KK + u] = kt;
+    }
+    __syncthreads();
+    const float* a = reinterpret_cast<const float*>(P.a);
+    const float* b = reinterpret_cast<const float*>(P.b);
+    const int it0 = k1 * n * q4, n_it = n * q4;                // the row's float4 items
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const float* oth = side == 0 ? b : a;
+        const float4* K4 = reinterpret_cast<const float4*>(side == 0 ? KsT : Ks);
+        double2* kd2 = reinterpret_cast<double2*>(P.kscratch + (side == 0 ? 0 : m));
+        for (int il = threadIdx.x; il < n_it; il += blockDim.x) {
+            const int git = it0 + il, g = git % q4;
+            const float* xr = oth + (size_t)(git / q4) * KK;
+            float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int w = 0; w < KK; ++w) {
+                const float x = xr[w];
+                const float4 kv = K4[w * q4 + g];
+                const float kc[4] = {kv.x, kv.y, kv.z, kv.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float pr = kc[j] * x;
+                    const float pe = fmaf(kc[j], x, -pr);
+                    float s, t;
+                    two_sum_f(hi[j], pr, s, t);
+                    hi[j] = s;
+                    lo[j] += t + pe;
+                }
+            }
+            kd2[2 * git] = make_double2(widen_f32(hi[0]) + widen_f32(lo[0]), widen_f32(hi[1]) + widen_f32(lo[1]));
+            kd2[2 * git + 1] = make_double2(widen_f32(hi[2]) + widen_f32(lo[2]), widen_f32(hi[3]) + widen_f32(lo[3]));
+        }
+    }
+}
+
+// partial sums per row: [0..5] side 0, [6..11] side 1 (round-down mass, round-up
+// mass, sum w |d|, sum w h, residual, largest scaling), B_mu, B_nu, cost, degree
+constexpr int PKE_PARTS = 16;
+
+template <int KK>
+__global__ void __launch_bounds__(PKE_THREADS)
+primalk_eval_sum_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair_ids, int n_max) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[33];
+    const PairDev& P = pairs[pair_ids[blockIdx.x / n_max]];
+    const int k1 = blockIdx.x % n_max, n = P.n, m = P.m, N = P.N, kap = P.kappa;
+    if (k1 >= n) return;
+    float* KsT = reinterpret_cast<float*>(smem_raw);          // K'[u][v] = KsT[v KK + u]
+    for (int t = threadIdx.x; t < KK * KK; t += blockDim.x) {
+        const int u = t / KK, w = t - u * KK;
+        KsT[w * KK + u] = reinterpret_cast<const float*>(P.upK_t)[t];
+    }
+    __syncthreads();
+    const float* a = reinterpret_cast<const float*>(P.a);
+    const float* b = reinterpret_cast<const float*>(P.b);
+    const int k0 = k1 * n, t0 = k0 * KK, tn = n * KK;          // the row's blocks and positions
+    int deg = 0;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        const int k = k0 + q;
+        deg = max(deg, max(P.rowptr[k + 1] - P.rowptr[k], P.colptr[k + 1] - P.colptr[k]));
+    }
+    const double deg_row = block_reduce_max((double)deg, red);
+    double sums[12];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const int* ptr = side == 0 ? P.rowptr : P.colptr;
+        const int* idx = side == 0 ? P.colidx : P.rowidx;
+        const double* val = side == 0 ? P.val : P.valc;
+        const double* meas = side == 0 ? P.mu : P.nu;
+        const float* own = side == 0 ? a : b;
+        const double* kd = P.kscratch + (side == 0 ? 0 : m);
+        double s_lo = 0.0, s_hi = 0.0, dsum = 0.0, whsum = 0.0, rsum = 0.0;
+        float xm = 0.0f;
+        for (int t = threadIdx.x; t < tn; t += blockDim.x) {
+            const int tt = t0 + t;
+            const int k = tt / KK, u = tt - (tt / KK) * KK;
+            double r = 0.0;
+            for (int e = ptr[k]; e < ptr[k + 1]; ++e) r = fma(val[e], kd[idx[e] * KK + u], r);
+            const float xf = own[tt];
+            const double h = widen_f32(xf) * r;
+            s_lo = __dadd_rd(s_lo, h);
+            s_hi = __dadd_ru(s_hi, h);
+            const int i = blk_pixel(k, u, n, kap, N);
+            const double ad = fabs(h - meas[i]);              // nearest-rounded |h - mu_i|
+            const double w = tv_weight_hi_fast(i / N, i - (i / N) * N, N, P.p);
+            dsum = __fma_ru(w, ad, dsum);
+            whsum = __fma_ru(w, h, whsum);
+            rsum += ad;
+            xm = fmaxf(xm, xf);
+        }
+        sums[6 * side + 0] = block_reduce_rd(s_lo, red);
+        sums[6 * side + 1] = block_reduce_ru(s_hi, red);
+        sums[6 * side + 2] = block_reduce_ru(dsum, red);
+        sums[6 * side + 3] = block_reduce_ru(whsum, red);
+        sums[6 * side + 4] = block_reduce_rn(rsum, red);
+        sums[6 * side + 5] = block_reduce_max(widen_f32(xm), red);
+    }
+    double bmu = 0.0, bnu = 0.0;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        bmu = __dadd_ru(bmu, P.mu_w_hi[k0 + q]);
+        bnu = __dadd_ru(bnu, P.nu_w_hi[k0 + q]);
+    }
+    const double B_mu_row = block_reduce_ru(bmu, red);
+    const double B_nu_row = block_reduce_ru(bnu, red);
+    const float* tab = reinterpret_cast<const float*>(P.ctab_hi);
+    double cost = 0.0;
+    for (int t = threadIdx.x; t < tn; t += blockDim.x) {
+        const int tt = t0 + t;
+        const int k = tt / KK, u = tt - (tt / KK) * KK;
+        const float a_ku = a[tt];
+        const float* kh = KsT + u;
+        for (int e = P.rowptr[k]; e < P.rowptr[k + 1]; ++e) {
+            const int l = P.colidx[e];
+            const int rr = kap * (k / n - l / n) + u / kap, c0 = kap * (k % n - l % n) + u % kap;
+            const float* br = b + l * KK;
+            float inner = 0.0f;
+            for (int v1 = 0; v1 < kap; ++v1) {
+                const float* trow = tab + abs(rr - v1) * N;
+                for (int v2 = 0; v2 < kap; ++v2) {
+                    const int v = v1 * kap + v2;
+                    inner = fma_ru(mul_ru(kh[v * KK], br[v]), trow[abs(c0 - v2)], inner);
+                }
+            }
+            cost = __fma_ru(P.val[e], widen_f32(mul_ru(a_ku, inner)), cost);
+        }
+    }
+    const double cost_row = block_reduce_ru(cost, red);
+    if (threadIdx.x == 0) {
+        double* part = reinterpret_cast<double*>(P.kb_t) + (size_t)k1 * PKE_PARTS;
+#pragma unroll
+        for (int q = 0; q < 12; ++q) part[q] = sums[q];
+        part[12] = B_mu_row;
+        part[13] = B_nu_row;
+        part[14] = cost_row;
+        part[15] = deg_row;
+    }
+}
+
+template <int KK>
+__global__ void primalk_eval_final_kernel(const PairDev* __restrict__ pairs, PairOut* __restrict__ outs,
+                                          const int* __restrict__ pair_ids) {
+    const PairDev& P = pairs[pair_ids[blockIdx.x]];
+    if (threadIdx.x != 0) return;
+    const int n = P.n, m = P.m, N = P.N;
+    double tot[PKE_PARTS];
+#pragma unroll
+    for (int q = 0; q < PKE_PARTS; ++q) tot[q] = 0.0;
+    const double* part = reinterpret_cast<const double*>(P.kb_t);
+    for (int r = 0; r < n; ++r) {
+        const double* pr = part + (size_t)r * PKE_PARTS;
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const int o = 6 * side;
+            tot[o + 0] = __dadd_rd(tot[o + 0], pr[o + 0]);
+            tot[o + 1] = __dadd_ru(tot[o + 1], pr[o + 1]);
+            tot[o + 2] = __dadd_ru(tot[o + 2], pr[o + 2]);
+            tot[o + 3] = __dadd_ru(tot[o + 3], pr[o + 3]);
+            tot[o + 4] += pr[o + 4];
+            tot[o + 5] = fmax(tot[o + 5], pr[o + 5]);
+        }
+        tot[12] = __dadd_ru(tot[12], pr[12]);
+        tot[13] = __dadd_ru(tot[13], pr[13]);
+        tot[14] = __dadd_ru(tot[14], pr[14]);
+        tot[15] = fmax(tot[15], pr[15]);
+    }
+    // the enclosures of primalk_cl_kernel's combination
+    const double g2 = (2.0 * KK * 0x1p-24) / (1.0 - 2.0 * KK * 0x1p-24);
+    const double rel = __dadd_ru(__dmul_ru(2.0, __dmul_ru(g2, g2)), (tot[15] + 3.0) * 0x1p-52);
+    const double kd_abs = (double)KK * 0x1p-140;
+    const double w_sum_hi = __dmul_ru((double)m, tv_weight_hi(0, 0, N, P.p));
+    const double rel_d = __dadd_ru(rel, 0x1p-53);
+    double s_lo = 0.0, s_hi = HUGE_VAL, A[2];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const int o = 6 * side;
+        const double B = tot[12 + side];
+        const double slack = __dadd_ru(__dmul_ru(tot[o + 5], kd_abs), 0x1p-1000);
+        double As = __fma_ru(rel_d, tot[o + 3], tot[o + 2]);
+        As = __fma_ru(0x1p-53, B, As);
+        A[side] = __fma_ru(slack, w_sum_hi, As);
+        const double ms = __dmul_ru((double)m, slack);
+        s_lo = fmax(s_lo, __dsub_rd(__dmul_rd(tot[o + 0], __dsub_rd(1.0, rel)), ms));
+        s_hi = fmin(s_hi, __dadd_ru(__dmul_ru(tot[o + 1], __dadd_ru(1.0, rel)), ms));
+    }
+    const double p = P.p;
+    const double inv_hi = s_lo > 0.0 ? __drcp_ru(s_lo) : HUGE_VAL;
+    const double inv_lo = __drcp_rd(s_hi);
+    const double dinv = fmax(0.0, fmax(__dsub_ru(inv_hi, 1.0), __dsub_ru(1.0, inv_lo)));
+    const double tv_mu = __fma_ru(tot[12], dinv, __dmul_ru(A[0], inv_hi));
+    const double tv_nu = __fma_ru(tot[13], dinv, __dmul_ru(A[1], inv_hi));
+    const double scale = (p == 1.0) ? 1.0 : (p == 2.0 ? 2.0 : __dmul_ru(pow(2.0, p - 1.0), 1.0 + 0x1p-49));
+    const double dmu = root_p_ru(__dmul_ru(scale, tv_mu), p);
+    const double dnu = root_p_ru(__dmul_ru(scale, tv_nu), p);
+    const double w_hat_p = __dmul_ru(tot[14], inv_hi);
+    PairOut& O = outs[P.out_index];
+    O.w_hat_p = w_hat_p;
+    O.delta_mu = dmu;
+    O.delta_nu = dnu;
+    O.ub_primal = __dadd_ru(__dadd_ru(root_p_ru(w_hat_p, p), dmu), dnu);
+    O.ipf_residual = tot[4] + tot[10];
+    O.sweeps_done = P.sweeps;
+}
+
+template <int KK>
+__global__ void __launch_bounds__(PKE_THREADS)
+primalk_eval_layout_kernel(const PairDev* __restrict__ pairs, const int* __restrict__ pair_ids, int n_max) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const PairDev& P = pairs[pair_ids[blockIdx.x / n_max]];
+    const int k1 = blockIdx.x % n_max, n = P.n, N = P.N, kap = P.kappa;
+    if (k1 >= n) return;
+    float* tmp = reinterpret_cast<float*>(smem_raw);          // [2][n KK]
+    const int t0 = k1 * n * KK, tn = n * KK;
+    float* a = reinterpret_cast<float*>(P.a);
+    float* b = reinterpret_cast<float*>(P.b);
+    for (int t = threadIdx.x; t < tn; t += blockDim.x) {
+        tmp[t] = a[t0 + t];
+        tmp[tn + t] = b[t0 + t];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < tn; t += blockDim.x) {
+        const int tt = t0 + t;
+        const int i = blk_pixel(tt / KK, tt - (tt / KK) * KK, n, kap, N);   // in the same rows
+        a[i] = tmp[t];
+        b[i] = tmp[tn + t];
+    }
+}
+
+int launch_primalk_eval(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs, int kappa,
+                        int n_max, cudaStream_t stream) {
+    if (n_pairs <= 0) return QWB_OK;
+    if (kappa != 2 && kappa != 4 && kappa != 8) return QWB_ERR_UNSUPPORTED;
+    const int kk = kappa * kappa;
+    const size_t s_kd = sizeof(float) * 2 * (size_t)kk * kk, s_sum = sizeof(float) * (size_t)kk * kk;
+    const size_t s_lay = sizeof(float) * 2 * (size_t)n_max * kk;
+    if (s_lay > 227 * 1024) return QWB_ERR_UNSUPPORTED;
+    const unsigned grid = (unsigned)(n_pairs * n_max);
+    auto run = [&](auto kd, auto sum, auto fin, auto lay) -> int {
+        QWB_CUDA(cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_kd));
+        QWB_CUDA(cudaFuncSetAttribute(lay, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_lay));
+        kd<<<grid, PKE_THREADS, s_kd, stream>>>(pairs_d, pair_ids, n_max);
+        QWB_LAUNCHED();
+        sum<<<grid, PKE_THREADS, s_sum, stream>>>(pairs_d, pair_ids, n_max);
+        QWB_LAUNCHED();
+        fin<<<n_pairs, 32, 0, stream>>>(pairs_d, outs_d, pair_ids);
+        QWB_LAUNCHED();
+        lay<<<grid, PKE_THREADS, s_lay, stream>>>(pairs_d, pair_ids, n_max);
+        QWB_LAUNCHED();
+        return QWB_OK;
+    };
+    if (kk == 4)
+        return run(primalk_eval_kd_kernel<4>, primalk_eval_sum_kernel<4>, primalk_eval_final_kernel<4>,
+                   primalk_eval_layout_kernel<4>);
+    if (kk == 16)
+        return run(primalk_eval_kd_kernel<16>, primalk_eval_sum_kernel<16>, primalk_eval_final_kernel<16>,
+                   primalk_eval_layout_kernel<16>);
+    return run(primalk_eval_kd_kernel<64>, primalk_eval_sum_kernel<64>, primalk_eval_final_kernel<64>,
+               primalk_eval_layout_kernel<64>);
 }
 
 // --------------------------------------------------------------------------

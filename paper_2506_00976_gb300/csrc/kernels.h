@@ -128,7 +128,15 @@ int launch_verify(const PairDev* pairs_d, PairOut* outs_d, const PixItem* items,
 // primal pass with a general upscaling kernel (P.upK set; d = 2, kappa <= kappa_max <= 8;
 // all_kappa4: every pair of the launch has kappa 4, which selects the register-row kernel)
 int launch_primalk(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs, int kappa_max,
-                   int M_max, int nnz_max, int m_max, bool all_kappa4, bool f64, cudaStream_t stream);
+                   int M_max, int nnz_max, int m_max, bool all_kappa4, bool f64, cudaStream_t stream,
+                   int sweeps_only = 0);
+// The certified evaluation of that pass spread over many CTAs, after
+// launch_primalk(..., sweeps_only = 1) (FP32 pairs that all have block side
+// kappa 2, 4 or 8; n_max >= every pair's coarse side): the K products of
+// both sides, the marginal entries, the support cost and the TV terms per
+// block row, then one combination per pair and the pixel layout of a, b.
+int launch_primalk_eval(const PairDev* pairs_d, PairOut* outs_d, const int* pair_ids, int n_pairs, int kappa,
+                        int n_max, cudaStream_t stream);
 // The same pass for FP32 pairs that all have block side kappa (2, 4 or 8),
 // one pair on a cluster of C (1..8) CTAs; variant 0, 1, 2: 256, 128, 64
 // threads per CTA; n_max >= every pair's coarse side n.

@@ -247,13 +247,15 @@ def _kernel_batch(cases, K, kappa, sweeps, batched, form, seed=47):
 
 @pytest.mark.parametrize("kappa,cases,forms", [
     (4, [(16, 2.0, "gauss"), (32, 2.0, "blobs3"), (24, 1.0, "field"), (40, 2.0, "cauchy")],
-     [(1, 256), (2, 128), (4, 128), (4, 64), (8, 64)]),
-    (8, [(32, 2.0, "field"), (16, 1.0, "gauss"), (48, 2.0, "white")], [(1, 128), (2, 64), (4, 128), (8, 64)]),
-    (2, [(16, 2.0, "blobs3"), (10, 2.0, "gauss")], [(2, 256), (4, 64), (8, 128)]),
+     [(-1, 128), (1, 256), (2, 128), (4, 128), (4, 64), (8, 64)]),
+    (8, [(32, 2.0, "field"), (16, 1.0, "gauss"), (48, 2.0, "white")],
+     [(-1, 128), (1, 128), (2, 64), (4, 128), (8, 64)]),
+    (2, [(16, 2.0, "blobs3"), (10, 2.0, "gauss")], [(-1, 128), (2, 256), (4, 64), (8, 128)]),
 ])
 def test_batch_kernel_cluster_form(kappa, cases, forms):
     """The cluster form of the general-kernel primal pass (one pair on a
-    cluster of C CTAs that split its block rows).  Its fine sweeps are those
+    cluster of C CTAs that split its block rows), and the form that keeps the
+    one-CTA sweeps and spreads the evaluation over many CTAs (C = -1).  Its fine sweeps are those
     of the one-CTA kernel item for item, so the scalings agree bit for bit;
     its certified sums run in another order with tighter enclosures, so its
     bounds are no larger than the one-CTA kernel's and agree with the
@@ -295,7 +297,8 @@ def test_batch_kernel_cluster_tuned_and_refused():
     K = O.gaussian_kernel(4, 1.0)
     _, _, _, tuning = _kernel_batch(cases, K, 4, 5, True, None)
     uk = tuning["upscale_kernel"]
-    assert "single" in uk["candidates_ms"] and any(k.startswith("cluster") for k in uk["candidates_ms"])
+    assert "single" in uk["candidates_ms"] and "single_sweeps_spread_eval" in uk["candidates_ms"]
+    assert any(k.startswith("cluster") for k in uk["candidates_ms"])
     N = 16
     mu, nu = T(synth.make_measure(N, "gauss", 48, 0)), T(synth.make_measure(N, "gauss", 48, 1))
     with api.Batch([(N, 4, 2.0)], ipf_sweeps=3, prec="f64") as bt:
