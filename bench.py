@@ -672,8 +672,9 @@ def _kernel_upscale_workload(api, dev, args):
         "ub_mean": {k: float(v.mean()) for k, v in ubs.items()},
         "gaussian_500_below": {"uniform": int((g5 < ubs["uniform"]).sum()),
                                "weighted": int((g5 < ubs["weighted"]).sum())},
-        "what": "general-kernel primal pass (primalk_cl_kernel on clusters, or primalk_kernel one CTA per pair, as "
-                "tuned; gaussian_single_cta forces the latter): IPF of pi~ (x) K with a Gaussian K, FP32 sweeps, "
+        "what": "general-kernel primal pass (primalk_cl_kernel on clusters, primalk_kernel one CTA per pair, or "
+                "its sweeps with the evaluation spread over one CTA per block row, as tuned; "
+                "gaussian_single_cta forces the one-CTA kernel): IPF of pi~ (x) K with a Gaussian K, FP32 sweeps, "
                 "certified FP64 evaluation; "
                 "achieved counts the K products only (4 m kappa^2 FLOP per sweep, the plan gather's "
                 "<= 4 (2M - 1) kappa^2 not counted); 'uniform' is the uniform primal pass (cluster sweeps + "
