@@ -10,7 +10,7 @@
 // c-transform mixes count candidates, i.e. (input, output) pairs) per clock
 // per SM, from the SM cycle counter, and per second over the device, from
 // CUDA events.  Not a step of the paper: a measurement of the hardware the
-// passes are judged against.
+// passes are measured against.
 #include <cuda_runtime.h>
 
 #include <algorithm>
