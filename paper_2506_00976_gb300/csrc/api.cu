@@ -1420,7 +1420,12 @@ static int solve_pair(qwb_batch* b, int t, const std::function<int(int)>& wait_c
                         }
             }
     }
-    st = network_simplex(M, M, Cb, mc, nc, sb, -1, &basis, nullptr, &cand, false);   // the plan only
+    // every C-bar entry is a weighted mean of fine costs, all at most the cost
+    // of the grid's diagonal; twice that covers the upward rounding, and the
+    // solve checks each entry against it in its full scans (no pass of its own)
+    const double diag_sq = (double)dim_of(pr) * (double)(pr.N - 1) * (double)(pr.N - 1);
+    const double cb_bound = 2.0 * cost_of_sq(diag_sq, pr.p, false) + 1.0;
+    st = network_simplex(M, M, Cb, mc, nc, sb, -1, &basis, nullptr, &cand, false, cb_bound);   // the plan only
     if (st) return st;
     double L_sum = 0.0;
     const int nnzb = (int)sb.col.size();

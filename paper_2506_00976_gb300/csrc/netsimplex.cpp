@@ -27,9 +27,10 @@
 //     entering arc in turn, stamping the nodes, until one walk meets the
 //     other's trail (no depths are kept); after the pivot the re-hung subtree
 //     gets its potentials shifted by one common amount (its internal arcs do
-//     not change); every V pivots all potentials are recomputed from the tree
-//     and re-centred, so that neither the shifts' rounding nor the artificial
-//     cost eats their precision;
+//     not change); every V pivots, and before every full scan of the sparse
+//     pricing, all potentials are recomputed from the tree and re-centred, so
+//     that neither the shifts' rounding nor the artificial cost eats their
+//     precision;
 //   * a solve can start from the final tree of another solve with the same
 //     supplies (a feasible, strongly feasible basis for any costs): the C-bar
 //     problem starts from the C~ optimum;
@@ -212,18 +213,50 @@ struct Solver {
     }
 
     // minimum of c[t] + pg[t] over a contiguous run: four independent chains
+    // of two-lane vectors (GCC vector extensions: SSE2 or NEON registers; the
+    // compiler keeps a scalar min reduction serial); the minimum of a set
+    // does not depend on the order in which it is taken
+    typedef double v2d __attribute__((vector_size(16)));
+    static v2d load2(const double* p) { v2d v; std::memcpy(&v, p, sizeof v); return v; }
+    static v2d vmin(v2d a, v2d b) { return a < b ? a : b; }
     static double run_min(const double* c, const double* pg, int len) {
-        double m0 = HUGE_VAL, m1 = HUGE_VAL, m2 = HUGE_VAL, m3 = HUGE_VAL;
+        const v2d inf = {HUGE_VAL, HUGE_VAL};
+        v2d m0 = inf, m1 = inf, m2 = inf, m3 = inf;
+        int t = 0;
+        for (; t + 8 <= len; t += 8) {
+            m0 = vmin(load2(c + t) + load2(pg + t), m0);
+            m1 = vmin(load2(c + t + 2) + load2(pg + t + 2), m1);
+            m2 = vmin(load2(c + t + 4) + load2(pg + t + 4), m2);
+            m3 = vmin(load2(c + t + 6) + load2(pg + t + 6), m3);
+        }
+        m0 = vmin(vmin(m0, m1), vmin(m2, m3));
+        double mn = m0[0] < m0[1] ? m0[0] : m0[1];
+        for (; t < len; ++t) { const double r = c[t] + pg[t]; mn = r < mn ? r : mn; }
+        return mn;
+    }
+    // the same minimum, and whether every c[t] lies in [0, hi] (false for NaN)
+    static double run_min_checked(const double* c, const double* pg, int len, double hi, bool& ok) {
+        typedef long long v2l __attribute__((vector_size(16)));
+        const v2d inf = {HUGE_VAL, HUGE_VAL}, zero = {0.0, 0.0}, top = {hi, hi};
+        v2d m0 = inf, m1 = inf;
+        v2l good = {-1, -1};
         int t = 0;
         for (; t + 4 <= len; t += 4) {
-            const double r0 = c[t] + pg[t], r1 = c[t + 1] + pg[t + 1];
-            const double r2 = c[t + 2] + pg[t + 2], r3 = c[t + 3] + pg[t + 3];
-            m0 = r0 < m0 ? r0 : m0; m1 = r1 < m1 ? r1 : m1;
-            m2 = r2 < m2 ? r2 : m2; m3 = r3 < m3 ? r3 : m3;
+            const v2d c0 = load2(c + t), c1 = load2(c + t + 2);
+            good &= (c0 >= zero) & (c0 <= top) & (c1 >= zero) & (c1 <= top);
+            m0 = vmin(c0 + load2(pg + t), m0);
+            m1 = vmin(c1 + load2(pg + t + 2), m1);
         }
-        for (; t < len; ++t) { const double r = c[t] + pg[t]; m0 = r < m0 ? r : m0; }
-        m0 = m1 < m0 ? m1 : m0; m2 = m3 < m2 ? m3 : m2;
-        return m2 < m0 ? m2 : m0;
+        m0 = vmin(m0, m1);
+        double mn = m0[0] < m0[1] ? m0[0] : m0[1];
+        bool g = good[0] == -1 && good[1] == -1;
+        for (; t < len; ++t) {
+            g = g && c[t] >= 0.0 && c[t] <= hi;
+            const double r = c[t] + pg[t];
+            mn = r < mn ? r : mn;
+        }
+        ok = g;
+        return mn;
     }
     // scan row i, columns [j0, j1): cost run against sink potentials
     void scan_run(int i, int j0, int j1, double& best, int64_t& best_a) {
@@ -319,6 +352,11 @@ struct Solver {
         }
         return -1;
     }
+    // check_bound >= 0: the costs were not checked before the solve; every
+    // full scan checks the entries it reads (0 <= c <= check_bound, which also
+    // excludes NaN and infinity) and sets bad_cost when one fails
+    double check_bound = -1.0;
+    bool bad_cost = false;
     // One scan of every real arc: add the arcs with a negative reduced cost to
     // the candidates.  Returns how many were added.
     int64_t add_violators() {
@@ -335,10 +373,24 @@ struct Solver {
         if (filter) row_minima_separable();
         for (int i = 0; i < n; ++i) {
             if (filter && rowmin[i] - pot[i] >= -eps + rowmin_margin) continue;
-            double best = -eps;
-            int64_t dummy = -1;
-            scan_run(i, 0, m, best, dummy);          // row minimum below -eps?
-            if (dummy < 0) continue;
+            if constexpr (std::is_same<Cost, DenseCost>::value) {
+                if (check_bound >= 0.0) {           // row minimum and the entries' check in one pass
+                    bool ok = true;
+                    const double mn = run_min_checked(cst.C + (int64_t)i * m, pg, m, check_bound, ok);
+                    if (!ok) { bad_cost = true; return 0; }
+                    if (!(mn - pot[i] < -eps)) continue;
+                } else {
+                    double best = -eps;
+                    int64_t dummy = -1;
+                    scan_run(i, 0, m, best, dummy);   // row minimum below -eps?
+                    if (dummy < 0) continue;
+                }
+            } else {
+                double best = -eps;
+                int64_t dummy = -1;
+                scan_run(i, 0, m, best, dummy);       // row minimum below -eps?
+                if (dummy < 0) continue;
+            }
             row_costs(i, rcs.data());
             const double pi = pot[i];
             for (int j = 0; j < m; ++j) {
@@ -493,13 +545,15 @@ struct Solver {
 template <typename Cost>
 int solve(int32_t n_src, int32_t n_dst, Cost cst, double maxc, const double* a, const double* b,
           NSSolution& out, int64_t max_pivots, const NSBasis* warm, NSBasis* basis_out,
-          const std::vector<int64_t>* candidates = nullptr, bool exact_dual = true) {
+          const std::vector<int64_t>* candidates = nullptr, bool exact_dual = true,
+          double check_bound = -1.0) {
     const int64_t NM = (int64_t)n_src * n_dst;
     if (max_pivots < 0) max_pivots = 20 * NM + 1000000;
     const int64_t cap = fault_param("ns_pivot_cap", -1);     // host-side fault injection (tests)
     if (cap >= 0) max_pivots = std::min<int64_t>(max_pivots, cap);
     Solver<Cost> S;
     S.cst = cst;
+    S.check_bound = check_bound;
     S.init_common(n_src, n_dst, a, b, maxc);
     if (warm && warm->valid && (int)warm->parent.size() == n_src + n_dst) S.init_basis(*warm);
     else S.init_star(a, b);
@@ -511,7 +565,15 @@ int solve(int32_t n_src, int32_t n_dst, Cost cst, double maxc, const double* a, 
         const int64_t e = S.sparse ? S.find_entering_sparse(&rc) : S.find_entering(&rc);
         if (e < 0) {
             // sparse pricing: optimal over the candidates; a full scan decides
-            if (S.sparse && S.add_violators() > 0) continue;
+            // (on re-centred potentials: the potentials of a tree that still
+            // holds artificial arcs sit near the artificial cost, and their
+            // rounding would hide every row from the separable row filter)
+            if (S.sparse) {
+                S.recentre();
+                const int64_t added = S.add_violators();
+                if (S.bad_cost) return QWB_ERR_INVALID_ARG;
+                if (added > 0) continue;
+            }
             break;
         }
         if (++piv > max_pivots) return QWB_ERR_NOT_CONVERGED;
@@ -632,18 +694,34 @@ bool check_masses(int32_t n_src, int32_t n_dst, const double* a, const double* b
 
 int network_simplex(int32_t n_src, int32_t n_dst, const double* C, const double* a,
                     const double* b, NSSolution& out, int64_t max_pivots, const NSBasis* warm,
-                    NSBasis* basis_out, const std::vector<int64_t>* candidates, bool exact_dual) {
+                    NSBasis* basis_out, const std::vector<int64_t>* candidates, bool exact_dual,
+                    double cost_bound) {
     if (n_src <= 0 || n_dst <= 0 || !C || !a || !b) return QWB_ERR_INVALID_ARG;
     const int64_t NM = (int64_t)n_src * n_dst;
-    double maxc = 0.0;
-    for (int64_t k = 0; k < NM; ++k) {
-        if (!(C[k] >= 0.0) || !std::isfinite(C[k])) return QWB_ERR_INVALID_ARG;
-        maxc = std::max(maxc, C[k]);
-    }
     if (!check_masses(n_src, n_dst, a, b)) return QWB_ERR_INVALID_ARG;
     if (candidates)
         for (int64_t a_ : *candidates)
             if (a_ < 0 || a_ >= NM) return QWB_ERR_INVALID_ARG;
+    if (candidates && cost_bound >= 0.0 && std::isfinite(cost_bound)) {
+        // the entries are checked by the full scans of the sparse pricing
+        // (every one is read at least once, by the last scan)
+        for (int64_t a_ : *candidates)
+            if (!(C[a_] >= 0.0) || !(C[a_] <= cost_bound)) return QWB_ERR_INVALID_ARG;
+        if (warm && warm->valid && (int64_t)warm->pred.size() == (int64_t)n_src + n_dst)
+            for (int64_t a_ : warm->pred)          // the starting tree's real arcs
+                if (a_ >= 0 && a_ < NM && (!(C[a_] >= 0.0) || !(C[a_] <= cost_bound)))
+                    return QWB_ERR_INVALID_ARG;
+        return solve(n_src, n_dst, DenseCost{C, n_dst}, cost_bound, a, b, out, max_pivots, warm, basis_out,
+                     candidates, exact_dual, cost_bound);
+    }
+    // one pass: the maximum, and whether every entry is finite and non-negative
+    double maxc = 0.0;
+    bool ok = true;
+    for (int64_t k = 0; k < NM; ++k) {
+        ok &= (C[k] >= 0.0) & (C[k] <= std::numeric_limits<double>::max());
+        maxc = C[k] > maxc ? C[k] : maxc;
+    }
+    if (!ok) return QWB_ERR_INVALID_ARG;
     return solve(n_src, n_dst, DenseCost{C, n_dst}, maxc, a, b, out, max_pivots, warm, basis_out,
                  candidates, exact_dual);
 }

@@ -37,10 +37,16 @@ struct NSBasis {
 // optimal tree potentials (f_i + g_j = C_ij on the plan's support and
 // <= C_ij up to the pricing tolerance elsewhere), for callers that use only
 // the plan.
+// cost_bound >= 0 (with candidates): an upper bound on every C_ij known to
+// the caller.  It sets the artificial arc cost in place of the maximum, and
+// the entries (0 <= C_ij <= cost_bound) are checked by the solve's full scans
+// instead of by a pass of their own before it; a failing entry still returns
+// QWB_ERR_INVALID_ARG.
 int network_simplex(int32_t n_src, int32_t n_dst, const double* C, const double* a,
                     const double* b, NSSolution& out, int64_t max_pivots = -1,
                     const NSBasis* warm = nullptr, NSBasis* basis_out = nullptr,
-                    const std::vector<int64_t>* candidates = nullptr, bool exact_dual = true);
+                    const std::vector<int64_t>* candidates = nullptr, bool exact_dual = true,
+                    double cost_bound = -1.0);
 
 // The same for the grid problem with C_kl = tab[|k1 - l1| * n_side + |k2 - l2|]
 // on an n_side x n_side coarse grid (k = k1 * n_side + k2): the centre cost

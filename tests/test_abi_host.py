@@ -152,3 +152,75 @@ def test_pivot_cap_reports_not_converged(lib, monkeypatch):
     monkeypatch.setenv("QWB_FAULT", "")
     r = api.coarse_solve(C, a, b)
     assert r["obj"] == pytest.approx(O.exact_ot(C, a, b)[3], rel=1e-10)
+
+
+@pytest.fixture(scope="module")
+def warm_driver(tmp_path_factory):
+    """The host solver's warm C-bar solve as a small program (g++, no GPU)."""
+    import shutil
+    import subprocess
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not found")
+    exe = str(tmp_path_factory.mktemp("nsdrv") / "ns_warm_driver")
+    src = [os.path.join(ROOT, "tests", "ns_warm_driver.cpp"),
+           os.path.join(ROOT, "paper_2506_00976_gb300", "csrc", "netsimplex.cpp")]
+    subprocess.run([gxx, "-O2", "-std=c++17", "-o", exe, *src], check=True, capture_output=True)
+    return exe
+
+
+def _run_warm(exe, tmp_path, tab, a, b, C, bound):
+    import subprocess
+    path = str(tmp_path / "prob.bin")
+    with open(path, "wb") as fh:
+        np.array([tab.shape[0]], dtype=np.int32).tofile(fh)
+        for arr in (tab, a, b, C, np.array([bound])):
+            np.ascontiguousarray(arr, dtype=np.float64).tofile(fh)
+    out = subprocess.run([exe, path], check=True, capture_output=True, text=True).stdout.split()
+    return int(out[0]), float(out[1]), int(out[2]), float(out[3]), float(out[4])
+
+
+@pytest.mark.parametrize("N,kappa,p,cls", [(32, 2, 2.0, "gauss"), (40, 4, 1.5, "cauchy"), (32, 2, 1.0, "white")])
+def test_warm_cbar_solve_with_cost_bound(warm_driver, tmp_path, N, kappa, p, cls):
+    """The C-bar solve of a batch pair (Sec. 3.2): started from the C~
+    optimum's basis, the C~ plan's neighbourhoods priced first, with the
+    entries checked against a caller's bound inside the full scans (and,
+    bound < 0, by a pass of their own): the oracle's optimal objective and a
+    basic plan with the given marginals either way."""
+    ns = N // kappa
+    M = ns * ns
+    mu, nu = synth.make_measure(N, cls, 43, 0), synth.make_measure(N, cls, 43, 1)
+    a, b = O.sumpool(mu, N, kappa), O.sumpool(nu, N, kappa)
+    Ct = O.coarse_cost_centre(N, kappa, p)
+    tab = np.array([[Ct[0, d1 * ns + d2] for d2 in range(ns)] for d1 in range(ns)])
+    Cb = O.coarse_cost_weighted(mu, nu, N, kappa, p)
+    obj = O.exact_ot(Cb, a, b)[3]
+    bound = 2.0 * (2.0 * (N - 1) ** 2) ** (p / 2) + 1.0
+    for bd in (bound, -1.0):
+        st, val, nnz, re, ce = _run_warm(warm_driver, tmp_path, tab, a, b, Cb, bd)
+        assert st == 0
+        assert val == pytest.approx(obj, rel=1e-10)
+        assert nnz <= 2 * M - 1 and re < 1e-13 and ce < 1e-13
+
+
+@pytest.mark.parametrize("bad", [np.nan, -1.0, np.inf, "over"])
+@pytest.mark.parametrize("where", ["far", "near"])
+def test_warm_cbar_solve_rejects_bad_entries(warm_driver, tmp_path, bad, where):
+    """A NaN, negative, infinite or above-bound C-bar entry makes the warm
+    solve return INVALID_ARG, whether it lies among the arcs priced first
+    (checked before the solve) or only in the full scans ("far": the corner
+    arc from block 0 to block M - 1)."""
+    N, kappa, p = 32, 2, 2.0
+    ns = N // kappa
+    M = ns * ns
+    mu, nu = synth.make_measure(N, "gauss", 44, 0), synth.make_measure(N, "gauss", 44, 1)
+    a, b = O.sumpool(mu, N, kappa), O.sumpool(nu, N, kappa)
+    Ct = O.coarse_cost_centre(N, kappa, p)
+    tab = np.array([[Ct[0, d1 * ns + d2] for d2 in range(ns)] for d1 in range(ns)])
+    Cb = O.coarse_cost_weighted(mu, nu, N, kappa, p).copy()
+    bound = 2.0 * (2.0 * (N - 1) ** 2) + 1.0
+    k, l = (0, M - 1) if where == "far" else (0, 0)
+    Cb[k, l] = 3.0 * bound if bad == "over" else bad
+    for bd in ((bound, -1.0) if bad != "over" else (bound,)):
+        st = _run_warm(warm_driver, tmp_path, tab, a, b, Cb, bd)[0]
+        assert st == 1
