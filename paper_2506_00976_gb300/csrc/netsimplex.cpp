@@ -234,6 +234,13 @@ struct Solver {
         for (; t < len; ++t) { const double r = c[t] + pg[t]; mn = r < mn ? r : mn; }
         return mn;
     }
+    // out[t] = min(out[t], row[t] + s), element-wise
+    static void min_plus_row(double* out, const double* row, double s, int len) {
+        for (int t = 0; t < len; ++t) {
+            const double v = row[t] + s;
+            out[t] = v < out[t] ? v : out[t];
+        }
+    }
     // the same minimum, and whether every c[t] lies in [0, hi] (false for NaN)
     static double run_min_checked(const double* c, const double* pg, int len, double hi, bool& ok) {
         typedef long long v2l __attribute__((vector_size(16)));
@@ -421,20 +428,22 @@ struct Solver {
             double pmax = 0.0, cmax = 0.0;
             for (int j = 0; j < m; ++j) pmax = std::max(pmax, std::fabs(pg[j]));
             for (int d = 0; d < ns; ++d) cmax = std::max(cmax, cst.tab[(size_t)(ns - 1) * ns + d]);
-            for (int j1 = 0; j1 < ns; ++j1)
-                for (int i2 = 0; i2 < ns; ++i2) {
-                    double mn = HUGE_VAL;
-                    for (int j2 = 0; j2 < ns; ++j2)
-                        mn = std::min(mn, cst.tab[std::abs(i2 - j2)] + pg[j1 * ns + j2]);
-                    hbuf[(size_t)j1 * ns + i2] = mn;
-                }
-            for (int i1 = 0; i1 < ns; ++i1)
-                for (int i2 = 0; i2 < ns; ++i2) {
-                    double mn = HUGE_VAL;
-                    for (int j1 = 0; j1 < ns; ++j1)
-                        mn = std::min(mn, cst.tab[(size_t)std::abs(i1 - j1) * ns] + hbuf[(size_t)j1 * ns + i2]);
-                    rowmin[i1 * ns + i2] = mn;
-                }
+            // both passes as element-wise minima over contiguous rows (the
+            // reflected table row refl[ns - 1 + x] = B(|x|)); the same sums
+            // as the direct loops, and a minimum does not depend on the order
+            const double* refl0 = cst.refl + (ns - 1);
+            for (int j1 = 0; j1 < ns; ++j1) {
+                double* h = hbuf.data() + (size_t)j1 * ns;
+                std::fill(h, h + ns, HUGE_VAL);
+                for (int j2 = 0; j2 < ns; ++j2)
+                    min_plus_row(h, refl0 - j2, pg[j1 * ns + j2], ns);   // B(|i2 - j2|) + pg
+            }
+            for (int i1 = 0; i1 < ns; ++i1) {
+                double* r = rowmin.data() + (size_t)i1 * ns;
+                std::fill(r, r + ns, HUGE_VAL);
+                for (int j1 = 0; j1 < ns; ++j1)
+                    min_plus_row(r, hbuf.data() + (size_t)j1 * ns, cst.tab[(size_t)std::abs(i1 - j1) * ns], ns);
+            }
             // three roundings of terms below cmax + pmax each, on both sides of
             // the comparison (with the potential of the row): a wide margin
             double pimax = 0.0;
@@ -637,22 +646,23 @@ int solve(int32_t n_src, int32_t n_dst, Cost cst, double maxc, const double* a, 
             // differ from the direct minima by rounding only)
             const int ns = cst.ns;
             const double* tb = cst.tab;                   // A(d) = tb[d * ns], B(d) = tb[d]
+            const double* refl0 = cst.refl + (ns - 1);   // refl0[x] = B(|x|), |x| < ns
             std::vector<double> T((size_t)ns * ns), src(n_src);
             auto transform = [&](const double* h, double* outv) {
-                // outv[j1, j2] = min_{i1, i2} A(|i1 - j1|) + B(|i2 - j2|) - h[i1, i2]
-                for (int i1 = 0; i1 < ns; ++i1)
-                    for (int j2 = 0; j2 < ns; ++j2) {
-                        double mn = HUGE_VAL;
-                        for (int i2 = 0; i2 < ns; ++i2) mn = std::min(mn, tb[std::abs(i2 - j2)] - h[i1 * ns + i2]);
-                        T[(size_t)i1 * ns + j2] = mn;
-                    }
-                for (int j1 = 0; j1 < ns; ++j1)
-                    for (int j2 = 0; j2 < ns; ++j2) {
-                        double mn = HUGE_VAL;
-                        for (int i1 = 0; i1 < ns; ++i1)
-                            mn = std::min(mn, tb[(size_t)std::abs(i1 - j1) * ns] + T[(size_t)i1 * ns + j2]);
-                        outv[j1 * ns + j2] = mn;
-                    }
+                // outv[j1, j2] = min_{i1, i2} A(|i1 - j1|) + B(|i2 - j2|) - h[i1, i2],
+                // each pass as element-wise minima over contiguous rows
+                for (int i1 = 0; i1 < ns; ++i1) {
+                    double* Ti = T.data() + (size_t)i1 * ns;
+                    std::fill(Ti, Ti + ns, HUGE_VAL);
+                    for (int i2 = 0; i2 < ns; ++i2)
+                        S.min_plus_row(Ti, refl0 - i2, -h[i1 * ns + i2], ns);   // B(|j2 - i2|) - h
+                }
+                for (int j1 = 0; j1 < ns; ++j1) {
+                    double* o = outv + (size_t)j1 * ns;
+                    std::fill(o, o + ns, HUGE_VAL);
+                    for (int i1 = 0; i1 < ns; ++i1)
+                        S.min_plus_row(o, T.data() + (size_t)i1 * ns, tb[(size_t)std::abs(i1 - j1) * ns], ns);
+                }
             };
             transform(out.f.data(), g);
             transform(g, src.data());
