@@ -36,11 +36,13 @@
 //     problem starts from the C~ optimum;
 //   * the grid problem is solved coarse to fine: the same problem on the
 //     (n/2) x (n/2) grid of 2 x 2 cell sums (costs at doubled offsets) is
-//     solved first, and the fine solve prices only the arcs between the
-//     children of the coarse plan's support (sparse pricing) until none of
-//     them has a negative reduced cost; then one scan of all arcs adds every
-//     arc that still has one, and pricing resumes, until a full scan finds
-//     none (so the result is optimal over all arcs);
+//     solved first; the fine solve starts from a feasible tree built from
+//     the coarse plan (its flows split over the children by north-west
+//     corner passes) and prices only the arcs between the children of the
+//     coarse plan's support (sparse pricing) until none of them has a
+//     negative reduced cost; then one scan of all arcs adds every arc that
+//     still has one, and pricing resumes, until a full scan finds none (so
+//     the result is optimal over all arcs);
 //   * at the end the tree flows are recomputed exactly from the supplies
 //     (leaf elimination) and the potentials are made exactly dual feasible by
 //     one coarse c-transform each way (g = f^c, f = g^c).
@@ -139,13 +141,14 @@ struct Solver {
         pot[v] = up[v] ? c + pot[p] : pot[p] - c;   // rc of the tree arc is zero
     }
     void refresh_subtree(int r) {
-        stack.clear();
-        stack.push_back(r);
-        while (!stack.empty()) {
-            int v = stack.back();
-            stack.pop_back();
+        if ((int)stack.size() < V) stack.resize(V);
+        int* st = stack.data();
+        int top = 0;
+        st[top++] = r;
+        while (top > 0) {
+            const int v = st[--top];
             pot_from_parent(v);
-            for (int c = first_child[v]; c >= 0; c = next_sib[c]) stack.push_back(c);
+            for (int c = first_child[v]; c >= 0; c = next_sib[c]) st[top++] = c;
         }
     }
     // the re-hung subtree keeps its internal arcs: its potentials move by one
@@ -154,13 +157,18 @@ struct Solver {
         const double old = pot[r];
         pot_from_parent(r);
         const double d = pot[r] - old;
-        stack.clear();
-        for (int c = first_child[r]; c >= 0; c = next_sib[c]) stack.push_back(c);
-        while (!stack.empty()) {
-            int v = stack.back();
-            stack.pop_back();
-            pot[v] += d;
-            for (int c = first_child[v]; c >= 0; c = next_sib[c]) stack.push_back(c);
+        // explicit stack in a plain array (a subtree holds fewer than V nodes)
+        if ((int)stack.size() < V) stack.resize(V);
+        int* st = stack.data();
+        int top = 0;
+        for (int c = first_child[r]; c >= 0; c = next_sib[c]) st[top++] = c;
+        double* pt = pot.data();
+        const int* fc = first_child.data();
+        const int* nx = next_sib.data();
+        while (top > 0) {
+            const int v = st[--top];
+            pt[v] += d;
+            for (int c = fc[v]; c >= 0; c = nx[c]) st[top++] = c;
         }
     }
     void recentre() {
@@ -210,6 +218,29 @@ struct Solver {
         for (int v = 0; v < n + m; ++v) add_child(B.parent[v], v);
         for (int c = first_child[root]; c >= 0; c = next_sib[c]) refresh_subtree(c);
         recompute_flows();
+    }
+
+    // A starting tree built by the caller (not a previous final tree): after
+    // the flows are recomputed from the supplies, rounding-level negative
+    // flows (>= -tol) become zero; the tree is kept only when every flow is
+    // then non-negative and every zero-flow arc points away from the root
+    // (strongly feasible), else the caller starts from the star.
+    bool init_basis_checked(const NSBasis& B, double tol) {
+        init_basis(B);
+        for (int v = 0; v < n + m; ++v) {
+            if (flow[v] < 0.0) {
+                if (flow[v] < -tol) return false;
+                flow[v] = 0.0;
+            }
+            if (flow[v] == 0.0 && up[v]) return false;
+        }
+        return true;
+    }
+    void reset_tree() {
+        std::fill(parent.begin(), parent.end(), -1);
+        std::fill(first_child.begin(), first_child.end(), -1);
+        std::fill(next_sib.begin(), next_sib.end(), -1);
+        std::fill(prev_sib.begin(), prev_sib.end(), -1);
     }
 
     // minimum of c[t] + pg[t] over a contiguous run: four independent chains
@@ -534,13 +565,14 @@ struct Solver {
     void recompute_flows() {
         std::vector<int> order;
         order.reserve(V);
-        stack.clear();
-        stack.push_back(root);
-        while (!stack.empty()) {
-            int v = stack.back();
-            stack.pop_back();
+        if ((int)stack.size() < V) stack.resize(V);
+        int* st = stack.data();
+        int top = 0;
+        st[top++] = root;
+        while (top > 0) {
+            const int v = st[--top];
             order.push_back(v);
-            for (int c = first_child[v]; c >= 0; c = next_sib[c]) stack.push_back(c);
+            for (int c = first_child[v]; c >= 0; c = next_sib[c]) st[top++] = c;
         }
         std::vector<double> S(supply);
         for (int idx = (int)order.size() - 1; idx >= 1; --idx) {
@@ -555,7 +587,7 @@ template <typename Cost>
 int solve(int32_t n_src, int32_t n_dst, Cost cst, double maxc, const double* a, const double* b,
           NSSolution& out, int64_t max_pivots, const NSBasis* warm, NSBasis* basis_out,
           const std::vector<int64_t>* candidates = nullptr, bool exact_dual = true,
-          double check_bound = -1.0) {
+          double check_bound = -1.0, bool warm_built = false) {
     const int64_t NM = (int64_t)n_src * n_dst;
     if (max_pivots < 0) max_pivots = 20 * NM + 1000000;
     const int64_t cap = fault_param("ns_pivot_cap", -1);     // host-side fault injection (tests)
@@ -564,8 +596,19 @@ int solve(int32_t n_src, int32_t n_dst, Cost cst, double maxc, const double* a, 
     S.cst = cst;
     S.check_bound = check_bound;
     S.init_common(n_src, n_dst, a, b, maxc);
-    if (warm && warm->valid && (int)warm->parent.size() == n_src + n_dst) S.init_basis(*warm);
-    else S.init_star(a, b);
+    bool started = false;
+    if (warm && warm->valid && (int)warm->parent.size() == n_src + n_dst) {
+        if (!warm_built) {
+            S.init_basis(*warm);
+            started = true;
+        } else {
+            double mass = 0.0;
+            for (int i = 0; i < n_src; ++i) mass += a[i];
+            started = S.init_basis_checked(*warm, 1e-13 * (mass + 1.0));
+            if (!started) S.reset_tree();
+        }
+    }
+    if (!started) S.init_star(a, b);
     if (candidates) S.set_candidates(*candidates);
     int64_t piv = 0;
     const int64_t recentre_every = std::max<int64_t>(256, S.V);
@@ -747,8 +790,163 @@ int grid_solve(int32_t n_side, const double* tab, const double* a, const double*
 
 // Candidate arcs from the solution of the half-resolution problem: every
 // (fine source, fine sink) pair whose parents are joined by the coarse plan.
+// A feasible starting tree for the fine problem from the half-resolution
+// plan sh: each coarse arc's flow F_KL is split over the children of L by a
+// north-west corner pass per coarse sink (the arcs into L against the
+// children's masses), then each coarse source K splits those pieces over its
+// own children by a second pass.  Both passes conserve mass, so the fine
+// flow has the fine marginals up to rounding; its positive arcs form a
+// forest, and each component hangs from the root by the artificial arc of
+// one of its sinks (zero flow, pointing away from the root).  start.valid
+// stays false when an arc would close a cycle.
+void expand_plan(int32_t n_side, const double* a, const double* b, const NSSolution& sh, NSBasis& start) {
+    const int h = n_side / 2, Mh = h * h, M = n_side * n_side;
+    start.valid = false;
+    auto child = [&](int K, int c) { return (2 * (K / h) + c / 2) * n_side + 2 * (K % h) + c % 2; };
+    const int nnz = (int)sh.col.size();
+    // arcs into each coarse sink (CSC order: sources in increasing order)
+    std::vector<int> cptr(Mh + 1, 0), cidx(nnz);
+    for (int e = 0; e < nnz; ++e) cptr[sh.col[e] + 1]++;
+    for (int L = 0; L < Mh; ++L) cptr[L + 1] += cptr[L];
+    {
+        std::vector<int> cur(cptr.begin(), cptr.end() - 1);
+        for (int K = 0; K < Mh; ++K)
+            for (int e = sh.rowptr[K]; e < sh.rowptr[K + 1]; ++e) cidx[cur[sh.col[e]]++] = e;
+    }
+    // pass 1: piece (fine sink w, amount) lists per coarse arc, at most 4 each
+    std::vector<int> pw((size_t)nnz * 4, -1);
+    std::vector<double> px((size_t)nnz * 4, 0.0);
+    std::vector<int> pn(nnz, 0);
+    for (int L = 0; L < Mh; ++L) {
+        double rb[4];
+        for (int c = 0; c < 4; ++c) rb[c] = b[child(L, c)];
+        int c = 0;
+        for (int t = cptr[L]; t < cptr[L + 1]; ++t) {
+            const int e = cidx[t];
+            double rem = sh.val[e];
+            while (rem > 0.0 && c < 4) {
+                if (rb[c] <= 0.0) { ++c; continue; }
+                const double x = rem < rb[c] ? rem : rb[c];
+                pw[(size_t)e * 4 + pn[e]] = child(L, c);
+                px[(size_t)e * 4 + pn[e]] = x;
+                ++pn[e];
+                rem -= x;
+                rb[c] -= x;
+                if (rb[c] <= 0.0) ++c;
+            }
+        }
+    }
+    // pass 2: fine arcs (u, w, amount) per coarse source
+    std::vector<int> au, aw;
+    for (int K = 0; K < Mh; ++K) {
+        double ra[4];
+        for (int c = 0; c < 4; ++c) ra[c] = a[child(K, c)];
+        int c = 0;
+        for (int e = sh.rowptr[K]; e < sh.rowptr[K + 1]; ++e)
+            for (int q = 0; q < pn[e]; ++q) {
+                double rem = px[(size_t)e * 4 + q];
+                const int w = pw[(size_t)e * 4 + q];
+                while (rem > 0.0 && c < 4) {
+                    if (ra[c] <= 0.0) { ++c; continue; }
+                    const double x = rem < ra[c] ? rem : ra[c];
+                    au.push_back(child(K, c));
+                    aw.push_back(w);
+                    rem -= x;
+                    ra[c] -= x;
+                    if (ra[c] <= 0.0) ++c;
+                }
+            }
+    }
+    // spanning forest of those arcs (sources 0..M-1, sinks M..2M-1)
+    const int Vn = 2 * M;
+    std::vector<int> uf(Vn);
+    for (int v = 0; v < Vn; ++v) uf[v] = v;
+    auto find = [&](int v) { while (uf[v] != v) { uf[v] = uf[uf[v]]; v = uf[v]; } return v; };
+    std::vector<int> adj_ptr(Vn + 1, 0), adj((size_t)au.size() * 2);
+    for (size_t t = 0; t < au.size(); ++t) {
+        const int x = find(au[t]), y = find(M + aw[t]);
+        if (x == y) return;                          // a cycle: no starting tree
+        uf[x] = y;
+        adj_ptr[au[t] + 1]++;
+        adj_ptr[M + aw[t] + 1]++;
+    }
+    for (int v = 0; v < Vn; ++v) adj_ptr[v + 1] += adj_ptr[v];
+    {
+        std::vector<int> cur(adj_ptr.begin(), adj_ptr.end() - 1);
+        for (size_t t = 0; t < au.size(); ++t) {
+            adj[cur[au[t]]++] = M + aw[t];
+            adj[cur[M + aw[t]]++] = au[t];
+        }
+    }
+    start.parent.assign(Vn, -1);
+    start.pred.assign(Vn, -1);
+    start.up.assign(Vn, 0);
+    const int root = Vn;
+    const int64_t NM = (int64_t)M * M;
+    std::vector<int> queue;
+    queue.reserve(Vn);
+    std::vector<char> seen(Vn, 0);
+    // components hang from a sink (or, alone, from themselves): sinks first;
+    // a component's sink is the one nearest the middle of a longest path
+    // (two breadth-first walks), which keeps the tree shallow
+    std::vector<int> dist(Vn, -1), from(Vn, -1), comp;
+    auto bfs_far = [&](int s0) {
+        comp.clear();
+        comp.push_back(s0);
+        dist[s0] = 0; from[s0] = -1;
+        int far = s0;
+        for (size_t qi = 0; qi < comp.size(); ++qi) {
+            const int v = comp[qi];
+            if (dist[v] > dist[far]) far = v;
+            for (int t = adj_ptr[v]; t < adj_ptr[v + 1]; ++t)
+                if (dist[adj[t]] < 0) { dist[adj[t]] = dist[v] + 1; from[adj[t]] = v; comp.push_back(adj[t]); }
+        }
+        for (int v : comp) dist[v] = -1;
+        return far;
+    };
+    for (int pass = 0; pass < 2; ++pass)
+        for (int r0 = 0; r0 < M; ++r0) {
+            int r = pass == 0 ? M + r0 : r0;
+            if (seen[r]) continue;
+            if (pass == 0 && adj_ptr[r + 1] > adj_ptr[r]) {
+                const int f = bfs_far(r);
+                const int g = bfs_far(f);               // from[] now leads from g back to f
+                int len = 0;
+                for (int v = g; v >= 0; v = from[v]) ++len;
+                int c = g;
+                for (int k = 0; k < len / 2; ++k) c = from[c];
+                if (c < M) c = adj[adj_ptr[c]];         // a source: one of its sinks
+                r = c;
+            }
+            seen[r] = 1;
+            start.parent[r] = root;
+            start.pred[r] = NM + r;
+            start.up[r] = (r < M && a[r] > 0.0) ? 1 : 0;   // the artificial arc's direction
+            queue.clear();
+            queue.push_back(r);
+            for (size_t qi = 0; qi < queue.size(); ++qi) {
+                const int v = queue[qi];
+                for (int t = adj_ptr[v]; t < adj_ptr[v + 1]; ++t) {
+                    const int w = adj[t];
+                    if (seen[w]) continue;
+                    seen[w] = 1;
+                    start.parent[w] = v;
+                    if (w < M) {                      // source child, sink parent: arc w -> v
+                        start.pred[w] = (int64_t)w * M + (v - M);
+                        start.up[w] = 1;
+                    } else {                          // sink child, source parent: arc v -> w
+                        start.pred[w] = (int64_t)v * M + (w - M);
+                        start.up[w] = 0;
+                    }
+                    queue.push_back(w);
+                }
+            }
+        }
+    start.valid = true;
+}
+
 int grid_candidates(int32_t n_side, const double* tab, const double* a, const double* b,
-                    std::vector<int64_t>& cand) {
+                    std::vector<int64_t>& cand, NSBasis* start) {
     const int h = n_side / 2, Mh = h * h, M = n_side * n_side;
     std::vector<double> ah(Mh, 0.0), bh(Mh, 0.0), tabh((size_t)Mh);
     for (int r = 0; r < n_side; ++r)
@@ -761,6 +959,7 @@ int grid_candidates(int32_t n_side, const double* tab, const double* a, const do
     NSSolution sh;
     const int st = grid_solve(h, tabh.data(), ah.data(), bh.data(), sh, -1, nullptr, nullptr);
     if (st) return st;
+    if (start) expand_plan(n_side, a, b, sh, *start);
     cand.clear();
     for (int K = 0; K < Mh; ++K)
         for (int e = sh.rowptr[K]; e < sh.rowptr[K + 1]; ++e) {
@@ -787,15 +986,19 @@ int grid_solve(int32_t n_side, const double* tab, const double* a, const double*
         for (int d2 = -(n_side - 1); d2 < n_side; ++d2)
             refl[(size_t)d1 * (2 * n_side - 1) + n_side - 1 + d2] = tab[d1 * n_side + std::abs(d2)];
     std::vector<int64_t> cand;
+    NSBasis start;
     const bool ms = !(warm && warm->valid) && n_side >= kMultiscaleMin && n_side % 2 == 0;
     if (ms) {
-        const int st = grid_candidates(n_side, tab, a, b, cand);
+        const int st = grid_candidates(n_side, tab, a, b, cand, &start);
         if (st) return st;
     }
     bool sep = true;
     for (int d1 = 0; d1 < n_side && sep; ++d1)
         for (int d2 = 0; d2 < n_side; ++d2)
             if (tab[(size_t)d1 * n_side + d2] != tab[(size_t)d1 * n_side] + tab[d2]) { sep = false; break; }
+    if (ms && start.valid)
+        return solve(M, M, GridCost{tab, n_side, refl.data(), sep}, maxc, a, b, out, max_pivots, &start,
+                     basis_out, &cand, true, -1.0, true);
     return solve(M, M, GridCost{tab, n_side, refl.data(), sep}, maxc, a, b, out, max_pivots, warm, basis_out,
                  ms ? &cand : nullptr);
 }

@@ -127,6 +127,35 @@ def test_network_simplex_grid_table(lib, ns, kappa, p, cls):
     assert float(r["f"] @ a + r["g"] @ b) == pytest.approx(obj, rel=1e-9, abs=1e-12)
 
 
+@pytest.mark.parametrize("p", [1.0, 2.0])
+def test_network_simplex_grid_empty_parent_cells(lib, p):
+    """Coarse to fine with whole 2 x 2 parent cells of zero mass: their
+    children have no arc in the half-resolution plan, so the fine starting
+    tree built from that plan hangs them from the root alone.  Objective,
+    marginals and basis size against the oracle's exact solver."""
+    from paper_2506_00976_gb300 import api
+    ns, kappa = 16, 2
+    N = ns * kappa
+    mu = synth.make_measure(N, "gauss", 45, 0).reshape(N, N).copy()
+    nu = synth.make_measure(N, "white", 45, 1).reshape(N, N).copy()
+    mu[:2 * kappa, :2 * kappa] = 0.0
+    mu[6 * kappa:8 * kappa, 4 * kappa:6 * kappa] = 0.0
+    nu[-2 * kappa:, -4 * kappa:] = 0.0
+    mu = (mu / mu.sum()).ravel(); nu = (nu / nu.sum()).ravel()
+    a, b = O.sumpool(mu, N, kappa), O.sumpool(nu, N, kappa)
+    C = O.coarse_cost_centre(N, kappa, p)
+    tab = np.array([[C[0, d1 * ns + d2] for d2 in range(ns)] for d1 in range(ns)])
+    r = api.coarse_solve_grid(tab, a, b)
+    assert r["obj"] == pytest.approx(O.exact_ot(C, a, b)[3], rel=1e-10)
+    M = ns * ns
+    assert len(r["val"]) <= 2 * M - 1
+    plan = np.zeros((M, M))
+    for i in range(M):
+        for e in range(r["rowptr"][i], r["rowptr"][i + 1]):
+            plan[i, r["col"][e]] += r["val"][e]
+    assert np.abs(plan.sum(1) - a).max() < 1e-13 and np.abs(plan.sum(0) - b).max() < 1e-13
+
+
 def test_pivot_cap_reports_not_converged(lib, monkeypatch):
     """Host-side fault injection (QWB_FAULT=ns_pivot_cap=k): a network simplex
     stopped after a few pivots on a problem that needs many reports
