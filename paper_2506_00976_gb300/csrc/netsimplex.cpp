@@ -92,7 +92,7 @@ struct Solver {
     std::vector<signed char> up;      // 1 if pred[v] is directed v -> parent[v]
     std::vector<double> flow;         // flow on pred[v]
     std::vector<double> pot;
-    std::vector<int> stack, path;
+    std::vector<int> stack, path, walk_k, walk_l;
     std::vector<int64_t> old_pred;
     std::vector<signed char> old_up;
     std::vector<double> old_flow;
@@ -160,15 +160,19 @@ struct Solver {
         // explicit stack in a plain array (a subtree holds fewer than V nodes)
         if ((int)stack.size() < V) stack.resize(V);
         int* st = stack.data();
+        // pre-order: descend through first children, keeping each visited
+        // node's next sibling on the stack for later
         int top = 0;
-        for (int c = first_child[r]; c >= 0; c = next_sib[c]) st[top++] = c;
         double* pt = pot.data();
         const int* fc = first_child.data();
         const int* nx = next_sib.data();
-        while (top > 0) {
-            const int v = st[--top];
+        int v = fc[r];
+        while (v >= 0) {
             pt[v] += d;
-            for (int c = fc[v]; c >= 0; c = nx[c]) st[top++] = c;
+            const int sib = nx[v];
+            if (sib >= 0) st[top++] = sib;
+            v = fc[v];
+            if (v < 0 && top > 0) v = st[--top];
         }
     }
     void recentre() {
@@ -502,45 +506,61 @@ struct Solver {
         const int l = n + (int)(e % m);   // entering arcs are real arcs
         // apex: alternate single steps up from k and from l, stamping nodes,
         // until a walk reaches a node the other walk has passed (the root
-        // ends a walk; both ends lie in the one spanning tree)
+        // ends a walk; both ends lie in the one spanning tree).  The walks
+        // are recorded, so the cycle's two sides are arrays afterwards.
+        if ((int)walk_k.size() < V + 1) { walk_k.resize(V + 1); walk_l.resize(V + 1); }
+        int* wk = walk_k.data();
+        int* wl = walk_l.data();
+        int nk = 0, nl = 0;
         ++stamp;
         const int64_t sk = 2 * stamp, sl = 2 * stamp + 1;
         int u = k, w = l, apex = -1;
         mark[u] = sk;
+        wk[nk++] = u;
         if (mark[w] == sk) apex = w;
-        else mark[w] = sl;
+        else { mark[w] = sl; wl[nl++] = w; }
         while (apex < 0) {
             if (u != root) {
                 u = parent[u];
                 if (mark[u] == sl) { apex = u; break; }
                 mark[u] = sk;
+                wk[nk++] = u;
             }
             if (w != root) {
                 w = parent[w];
                 if (mark[w] == sk) { apex = w; break; }
                 mark[w] = sl;
+                wl[nl++] = w;
             }
         }
-        double delta = std::numeric_limits<double>::infinity();
-        for (int v = l; v != apex; v = parent[v])      // traversed upward
-            if (!up[v]) delta = std::min(delta, flow[v]);
-        for (int v = k; v != apex; v = parent[v])      // traversed downward
-            if (up[v]) delta = std::min(delta, flow[v]);
-        int q = -1;
-        bool on_l_side = false;
-        for (int v = l; v != apex; v = parent[v])
-            if (!up[v] && flow[v] <= delta) { q = v; on_l_side = true; }
-        if (q < 0) {
-            for (int v = k; v != apex; v = parent[v])
-                if (up[v] && flow[v] <= delta) { q = v; break; }
+        // the walk that passed the apex first went on above it: cut it there
+        for (int i = 0; i < nk; ++i) if (wk[i] == apex) { nk = i; break; }
+        for (int i = 0; i < nl; ++i) if (wl[i] == apex) { nl = i; break; }
+        // l side (traversed upward): the last arc of least flow against the
+        // cycle's direction; k side (traversed downward): the first one.
+        // Their minimum is the step delta, and the leaving arc is the l
+        // side's candidate when it attains delta (the strongly feasible rule)
+        double min_l = std::numeric_limits<double>::infinity(), min_k = min_l;
+        int ql = -1, qk = -1;
+        for (int i = 0; i < nl; ++i) {
+            const int v = wl[i];
+            if (!up[v] && flow[v] <= min_l) { min_l = flow[v]; ql = i; }
         }
-        for (int v = l; v != apex; v = parent[v]) flow[v] += up[v] ? delta : -delta;
-        for (int v = k; v != apex; v = parent[v]) flow[v] += up[v] ? -delta : delta;
+        for (int i = 0; i < nk; ++i) {
+            const int v = wk[i];
+            if (up[v] && flow[v] < min_k) { min_k = flow[v]; qk = i; }
+        }
+        const bool on_l_side = ql >= 0 && min_l <= min_k;
+        const double delta = on_l_side ? min_l : min_k;
+        const int q = on_l_side ? wl[ql] : wk[qk];
+        for (int i = 0; i < nl; ++i) { const int v = wl[i]; flow[v] += up[v] ? delta : -delta; }
+        for (int i = 0; i < nk; ++i) { const int v = wk[i]; flow[v] += up[v] ? -delta : delta; }
         const int e1 = on_l_side ? l : k;
         const int e2 = on_l_side ? k : l;
-        path.clear();
-        for (int v = e1;; v = parent[v]) { path.push_back(v); if (v == q) break; }
-        const int t = (int)path.size() - 1;
+        const int* side = on_l_side ? wl : wk;       // e1 up to q: a prefix of its walk
+        const int qi = on_l_side ? ql : qk;
+        path.assign(side, side + qi + 1);
+        const int t = qi;
         old_pred.resize(t); old_up.resize(t); old_flow.resize(t);
         for (int s = 0; s < t; ++s) {
             old_pred[s] = pred[path[s]]; old_up[s] = up[path[s]]; old_flow[s] = flow[path[s]];
