@@ -307,9 +307,8 @@ struct Solver {
         if constexpr (std::is_same<Cost, GridCost>::value) {
             const int ns = cst.ns;
             const int i1 = i / ns, i2 = i % ns;
-            int j = j0;
+            int j = j0, jr = j0 / ns, jc0 = j0 % ns;   // grid row and column of j (no division per run)
             while (j < j1) {
-                const int jr = j / ns, jc0 = j % ns;
                 const int len = std::min(ns - jc0, j1 - j);
                 // reflected table row: refl[ns - 1 + d] = tab[|i1 - jr|][|d|]
                 const double* refl = cst.refl + (size_t)std::abs(i1 - jr) * (2 * ns - 1) + (ns - 1 - i2);
@@ -321,6 +320,8 @@ struct Solver {
                     }
                 }
                 j += len;
+                ++jr;
+                jc0 = 0;
             }
         } else {
             const double* c = cst.C + (int64_t)i * m;
@@ -427,7 +428,7 @@ struct Solver {
                     scan_run(i, 0, m, best, dummy);   // row minimum below -eps?
                     if (dummy < 0) continue;
                 }
-            } else {
+            } else if (!filter) {                    // (a row the filter kept is scanned directly)
                 double best = -eps;
                 int64_t dummy = -1;
                 scan_run(i, 0, m, best, dummy);       // row minimum below -eps?
