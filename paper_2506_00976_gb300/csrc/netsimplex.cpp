@@ -664,24 +664,35 @@ int solve(int32_t n_src, int32_t n_dst, Cost cst, double maxc, const double* a, 
         basis_out->up.assign(S.up.begin(), S.up.end() - 1);
         basis_out->valid = true;
     }
-    // plan (CSR) from the real tree arcs with positive flow
-    std::vector<std::vector<std::pair<int, double>>> rows(n_src);
-    for (int v = 0; v < S.n + S.m; ++v) {
-        const int64_t arc = S.pred[v];
-        if (arc < NM && S.flow[v] > 0.0)
-            rows[arc / n_dst].push_back({(int)(arc % n_dst), S.flow[v]});
-    }
+    // plan (CSR) from the real tree arcs with positive flow: counted per row,
+    // placed, then each row's few entries put in column order
     out.rowptr.assign(n_src + 1, 0);
-    out.col.clear(); out.val.clear();
+    for (int v = 0; v < S.n + S.m; ++v)
+        if (S.pred[v] < NM && S.flow[v] > 0.0) out.rowptr[S.pred[v] / n_dst + 1]++;
+    for (int i = 0; i < n_src; ++i) out.rowptr[i + 1] += out.rowptr[i];
+    const int nnz = out.rowptr[n_src];
+    out.col.resize(nnz);
+    out.val.resize(nnz);
+    {
+        std::vector<int32_t> cur(out.rowptr.begin(), out.rowptr.end() - 1);
+        for (int v = 0; v < S.n + S.m; ++v) {
+            const int64_t arc = S.pred[v];
+            if (arc < NM && S.flow[v] > 0.0) {
+                const int pos = cur[arc / n_dst]++;
+                out.col[pos] = (int32_t)(arc % n_dst);
+                out.val[pos] = S.flow[v];
+            }
+        }
+    }
     double obj = 0.0;
     for (int i = 0; i < n_src; ++i) {
-        std::sort(rows[i].begin(), rows[i].end());
-        for (auto& cv : rows[i]) {
-            out.col.push_back(cv.first);
-            out.val.push_back(cv.second);
-            obj += cv.second * cst(i, cv.first);
-        }
-        out.rowptr[i + 1] = (int32_t)out.col.size();
+        const int e0 = out.rowptr[i], e1 = out.rowptr[i + 1];
+        for (int e = e0 + 1; e < e1; ++e)             // insertion sort by column (distinct)
+            for (int f = e; f > e0 && out.col[f - 1] > out.col[f]; --f) {
+                std::swap(out.col[f - 1], out.col[f]);
+                std::swap(out.val[f - 1], out.val[f]);
+            }
+        for (int e = e0; e < e1; ++e) obj += out.val[e] * cst(i, out.col[e]);
     }
     out.obj = obj;
     // potentials: f_i = pot[i] shifted to a zero midrange (a warm start can
