@@ -14,8 +14,10 @@
 //   * costs come either from a dense matrix (C-bar) or, for the grid centre
 //     cost C~, from a table over block offsets (|dk1|, |dk2|), so that pricing
 //     does not stream an M x M matrix;
-//   * spanning tree stored as parent pointers with doubly linked child
-//     lists; the flow of each tree arc is kept on its child node;
+//   * spanning tree stored as parent pointers plus its pre-order as a
+//     circular doubly linked thread with the last node of every subtree, so
+//     a subtree is one thread segment (the textbook threaded-index form);
+//     the flow of each tree arc is kept on its child node;
 //   * block-search pricing over the real arcs (block ~ sqrt(#arcs)), each
 //     block walked as contiguous runs of one source row (grid costs through
 //     a reflected table row, so a run is two unit-stride streams),
@@ -85,14 +87,17 @@ struct Solver {
     double BIG = 0.0, eps = 0.0;
     std::vector<double> supply;
     std::vector<signed char> art_up;  // artificial arc of node v: 1 = v -> root
-    std::vector<int> parent, first_child, next_sib, prev_sib;
+    // the tree: parent pointers, and its pre-order as a circular doubly
+    // linked thread through the root with the last node of every subtree
+    // (a subtree is the thread segment [v, last[v]])
+    std::vector<int> parent, thread, rev, last;
     std::vector<int64_t> mark;        // apex search: 2 * stamp + side of the last walk through a node
     int64_t stamp = 0;
     std::vector<int64_t> pred;        // arc joining v and parent[v]
     std::vector<signed char> up;      // 1 if pred[v] is directed v -> parent[v]
     std::vector<double> flow;         // flow on pred[v]
     std::vector<double> pot;
-    std::vector<int> stack, path, walk_k, walk_l;
+    std::vector<int> stack, path, walk_k, walk_l, lold, rold, aold;
     std::vector<int64_t> old_pred;
     std::vector<signed char> old_up;
     std::vector<double> old_flow;
@@ -121,58 +126,23 @@ struct Solver {
     }
     double cost(int64_t a) const { return a < NM ? cst((int)(a / m), (int)(a % m)) : BIG; }
 
-    void add_child(int p, int c) {
-        parent[c] = p;
-        prev_sib[c] = -1;
-        next_sib[c] = first_child[p];
-        if (first_child[p] >= 0) prev_sib[first_child[p]] = c;
-        first_child[p] = c;
-    }
-    void remove_child(int c) {
-        int p = parent[c];
-        if (prev_sib[c] >= 0) next_sib[prev_sib[c]] = next_sib[c];
-        else first_child[p] = next_sib[c];
-        if (next_sib[c] >= 0) prev_sib[next_sib[c]] = prev_sib[c];
-        prev_sib[c] = next_sib[c] = -1;
-    }
     void pot_from_parent(int v) {
         const int p = parent[v];
         const double c = cost(pred[v]);
         pot[v] = up[v] ? c + pot[p] : pot[p] - c;   // rc of the tree arc is zero
     }
-    void refresh_subtree(int r) {
-        if ((int)stack.size() < V) stack.resize(V);
-        int* st = stack.data();
-        int top = 0;
-        st[top++] = r;
-        while (top > 0) {
-            const int v = st[--top];
-            pot_from_parent(v);
-            for (int c = first_child[v]; c >= 0; c = next_sib[c]) st[top++] = c;
-        }
-    }
     // the re-hung subtree keeps its internal arcs: its potentials move by one
-    // common amount
+    // common amount (one pass along its thread segment)
     void shift_subtree(int r) {
         const double old = pot[r];
         pot_from_parent(r);
         const double d = pot[r] - old;
-        // explicit stack in a plain array (a subtree holds fewer than V nodes)
-        if ((int)stack.size() < V) stack.resize(V);
-        int* st = stack.data();
-        // pre-order: descend through first children, keeping each visited
-        // node's next sibling on the stack for later
-        int top = 0;
+        const int end = last[r];
+        const int* th = thread.data();
         double* pt = pot.data();
-        const int* fc = first_child.data();
-        const int* nx = next_sib.data();
-        int v = fc[r];
-        while (v >= 0) {
+        for (int v = r; v != end;) {
+            v = th[v];
             pt[v] += d;
-            const int sib = nx[v];
-            if (sib >= 0) st[top++] = sib;
-            v = fc[v];
-            if (v < 0 && top > 0) v = st[--top];
         }
     }
     void recentre() {
@@ -181,7 +151,53 @@ struct Solver {
         for (int v = 0; v < n + m; ++v) s += pot[v];
         s /= (double)(n + m);
         for (int v = 0; v < V; ++v) pot[v] -= s;
-        for (int c = first_child[root]; c >= 0; c = next_sib[c]) refresh_subtree(c);
+        refresh_below_root();
+    }
+    // every potential from its parent's, in pre-order from the root
+    void refresh_below_root() {
+        for (int v = root; v != last[root];) {
+            v = thread[v];
+            pot_from_parent(v);
+        }
+    }
+    // thread, rev and last from the parent pointers (children in increasing
+    // node order); false when the parent pointers do not form one tree
+    bool build_thread() {
+        std::vector<int> cnt(V + 1, 0), kids(V);
+        for (int v = 0; v < V; ++v)
+            if (v != root) {
+                if (parent[v] < 0 || parent[v] >= V) return false;
+                cnt[parent[v] + 1]++;
+            }
+        for (int v = 0; v < V; ++v) cnt[v + 1] += cnt[v];
+        {
+            std::vector<int> cur(cnt.begin(), cnt.end() - 1);
+            for (int v = 0; v < V; ++v)
+                if (v != root) kids[cur[parent[v]]++] = v;
+        }
+        std::vector<int> order;
+        order.reserve(V);
+        if ((int)stack.size() < V) stack.resize(V);
+        int* st = stack.data();
+        int top = 0;
+        st[top++] = root;
+        while (top > 0) {
+            const int v = st[--top];
+            order.push_back(v);
+            if ((int)order.size() > V) return false;
+            for (int e = cnt[v + 1] - 1; e >= cnt[v]; --e) st[top++] = kids[e];
+        }
+        if ((int)order.size() != V) return false;
+        std::vector<int> size(V, 1), pos(V);
+        for (int i = 0; i < V; ++i) {
+            const int a = order[i], b = order[(i + 1) % V];
+            thread[a] = b;
+            rev[b] = a;
+            pos[a] = i;
+        }
+        for (int i = V - 1; i >= 1; --i) size[parent[order[i]]] += size[order[i]];
+        for (int v = 0; v < V; ++v) last[v] = order[pos[v] + size[v] - 1];
+        return true;
     }
 
     void init_common(int n_, int m_, const double* a, const double* b, double maxc) {
@@ -196,7 +212,7 @@ struct Solver {
         art_up.assign(V, 0);
         for (int v = 0; v < n; ++v) art_up[v] = a[v] > 0.0 ? 1 : 0;
         parent.assign(V, -1); mark.assign(V, -1); stamp = 0;
-        first_child.assign(V, -1); next_sib.assign(V, -1); prev_sib.assign(V, -1);
+        thread.assign(V, root); rev.assign(V, root); last.assign(V, root);
         pred.assign(V, -1); up.assign(V, 0); flow.assign(V, 0.0); pot.assign(V, 0.0);
         block = std::max<int64_t>(64, (int64_t)std::sqrt((double)NM));
         price_pos = 0;
@@ -205,23 +221,27 @@ struct Solver {
     // the all-artificial star
     void init_star(const double* a, const double* b) {
         for (int v = 0; v < n + m; ++v) {
-            add_child(root, v);
+            parent[v] = root;
             pred[v] = NM + v;
             up[v] = art_up[v];
             flow[v] = (v < n) ? a[v] : b[v - n];
             pot[v] = art_up[v] ? BIG : -BIG;
         }
+        build_thread();
     }
 
-    // a previous final tree (same supplies, any costs)
-    void init_basis(const NSBasis& B) {
+    // a previous final tree (same supplies, any costs); false when its
+    // parent pointers do not form one tree
+    bool init_basis(const NSBasis& B) {
         for (int v = 0; v < n + m; ++v) {
+            parent[v] = B.parent[v];
             pred[v] = B.pred[v];
             up[v] = B.up[v];
         }
-        for (int v = 0; v < n + m; ++v) add_child(B.parent[v], v);
-        for (int c = first_child[root]; c >= 0; c = next_sib[c]) refresh_subtree(c);
+        if (!build_thread()) return false;
+        refresh_below_root();
         recompute_flows();
+        return true;
     }
 
     // A starting tree built by the caller (not a previous final tree): after
@@ -230,7 +250,7 @@ struct Solver {
     // then non-negative and every zero-flow arc points away from the root
     // (strongly feasible), else the caller starts from the star.
     bool init_basis_checked(const NSBasis& B, double tol) {
-        init_basis(B);
+        if (!init_basis(B)) return false;
         for (int v = 0; v < n + m; ++v) {
             if (flow[v] < 0.0) {
                 if (flow[v] < -tol) return false;
@@ -242,9 +262,6 @@ struct Solver {
     }
     void reset_tree() {
         std::fill(parent.begin(), parent.end(), -1);
-        std::fill(first_child.begin(), first_child.end(), -1);
-        std::fill(next_sib.begin(), next_sib.end(), -1);
-        std::fill(prev_sib.begin(), prev_sib.end(), -1);
     }
 
     // minimum of c[t] + pg[t] over a contiguous run: four independent chains
@@ -562,42 +579,62 @@ struct Solver {
         const int qi = on_l_side ? ql : qk;
         path.assign(side, side + qi + 1);
         const int t = qi;
+        // thread update.  T, the subtree of q, is the segment [q, last[q]];
+        // re-rooted at e1 its pre-order is e1's old segment, then for each
+        // s = 1..t the segment of path[s] without that of path[s - 1] (two
+        // runs around the hole), and it goes in right after e2.
+        lold.resize(t + 1); rold.resize(t + 1); aold.resize(t + 1);
+        for (int s2 = 0; s2 <= t; ++s2) {
+            const int v = path[s2];
+            lold[s2] = last[v]; rold[s2] = rev[v]; aold[s2] = thread[last[v]];
+        }
+        const int q_parent = parent[q];
+        thread[rold[t]] = aold[t];                   // cut T out
+        rev[aold[t]] = rold[t];
+        for (int u = q_parent; u >= 0 && last[u] == lold[t]; u = parent[u]) last[u] = rold[t];
+        int tl = lold[0];                            // end of the new order so far
+        for (int s2 = 1; s2 <= t; ++s2) {
+            const int v = path[s2];
+            thread[tl] = v; rev[v] = tl;             // path[s2] .. the node before the hole
+            tl = rold[s2 - 1];
+            if (lold[s2 - 1] != lold[s2]) {          // the run after the hole
+                thread[tl] = aold[s2 - 1]; rev[aold[s2 - 1]] = tl;
+                tl = lold[s2];
+            }
+        }
+        for (int s2 = 0; s2 <= t; ++s2) last[path[s2]] = tl;
+        {
+            const int nx = thread[e2];               // splice in after e2
+            const bool leaf = last[e2] == e2;
+            thread[e2] = e1; rev[e1] = e2;
+            thread[tl] = nx; rev[nx] = tl;
+            if (leaf)
+                for (int u = e2; u >= 0 && last[u] == e2; u = parent[u]) last[u] = tl;
+        }
+        // parent pointers, arcs and flows along the reversed path
         old_pred.resize(t); old_up.resize(t); old_flow.resize(t);
         for (int s = 0; s < t; ++s) {
             old_pred[s] = pred[path[s]]; old_up[s] = up[path[s]]; old_flow[s] = flow[path[s]];
         }
-        remove_child(q);
-        for (int s = 0; s < t; ++s) remove_child(path[s]);
         for (int s = 0; s < t; ++s) {
             const int child = path[s + 1];
-            add_child(path[s], child);
+            parent[child] = path[s];
             pred[child] = old_pred[s];
             up[child] = old_up[s] ? 0 : 1;
             flow[child] = old_flow[s];
         }
-        add_child(e2, e1);
+        parent[e1] = e2;
         pred[e1] = e;
         up[e1] = (tail(e) == e1) ? 1 : 0;
         flow[e1] = delta;
         shift_subtree(e1);
     }
 
-    // Exact tree flows from the supplies (post-order leaf elimination).
+    // Exact tree flows from the supplies (leaf elimination in reverse
+    // pre-order: every node after all of its descendants).
     void recompute_flows() {
-        std::vector<int> order;
-        order.reserve(V);
-        if ((int)stack.size() < V) stack.resize(V);
-        int* st = stack.data();
-        int top = 0;
-        st[top++] = root;
-        while (top > 0) {
-            const int v = st[--top];
-            order.push_back(v);
-            for (int c = first_child[v]; c >= 0; c = next_sib[c]) st[top++] = c;
-        }
         std::vector<double> S(supply);
-        for (int idx = (int)order.size() - 1; idx >= 1; --idx) {
-            const int v = order[idx];
+        for (int v = rev[root]; v != root; v = rev[v]) {
             flow[v] = up[v] ? S[v] : -S[v];
             S[parent[v]] += S[v];
         }
