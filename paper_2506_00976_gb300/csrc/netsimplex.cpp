@@ -384,31 +384,73 @@ struct Solver {
         for (int64_t a : arcs)
             if (!((in_cand[(size_t)(a >> 6)] >> (a & 63)) & 1ull)) push_candidate(a);
         cand_pos = 0;
+        qn = 0;
     }
-    // Block search over the candidate arcs (the most negative reduced cost in
-    // the first block of about sqrt(#candidates) arcs that has one).
+    // Block search over the candidate arcs: the most negative reduced cost in
+    // the first block of about sqrt(#candidates) arcs that has one.  The
+    // block's next few most negative arcs are queued; the following calls
+    // take the best queued arc that is still negative at the current
+    // potentials before scanning again (partial pricing with a short
+    // candidate list: fewer scans for about as many pivots).
+    static constexpr int kQueue = 6;  // arcs kept from a block scan (the best included)
+    int qn = 0;                       // queued candidates from the last block scan
+    int64_t qt[kQueue];
     int64_t find_entering_sparse(double* rc_out) {
         const int64_t nc = (int64_t)cand.size();
         if (nc == 0) return -1;
+        const int* ci = cand_i.data();
+        const int* cj = cand_j.data();
+        const double* cc = cand_c.data();
+        const double* pg = pot.data() + n;
+        // first the arcs queued by the last scan, at today's potentials
+        if (qn > 0) {
+            double best = -eps;
+            int bi = -1, keep = 0;
+            for (int u = 0; u < qn; ++u) {
+                const int64_t t = qt[u];
+                const double rc = cc[t] - pot[ci[t]] + pg[cj[t]];
+                if (rc < -eps) {
+                    qt[keep] = t;
+                    if (rc < best) { best = rc; bi = keep; }
+                    ++keep;
+                }
+            }
+            qn = keep;
+            if (bi >= 0) {
+                const int64_t t = qt[bi];
+                qt[bi] = qt[--qn];
+                *rc_out = best;
+                return cand[(size_t)t];
+            }
+        }
+        constexpr int K = kQueue;
         const int64_t blk = std::max<int64_t>(32, (int64_t)std::sqrt((double)nc));
         int64_t scanned = 0, pos = cand_pos;
-        const double* pg = pot.data() + n;
         while (scanned < nc) {
             const int64_t end = std::min<int64_t>(pos + blk, nc);
-            double best = -eps;
-            int64_t best_a = -1;
-            const int* ci = cand_i.data();
-            const int* cj = cand_j.data();
-            const double* cc = cand_c.data();
-            int64_t best_t = -1;
+            // the K most negative reduced costs of the block, sorted
+            double brc[K];
+            int64_t bt[K];
+            int nb = 0;
+            double worst = -eps;
             for (int64_t t = pos; t < end; ++t) {
                 const double rc = cc[t] - pot[ci[t]] + pg[cj[t]];
-                if (rc < best) { best = rc; best_t = t; }
+                if (rc < worst) {
+                    int u = nb < K ? nb++ : K - 1;
+                    while (u > 0 && brc[u - 1] > rc) { brc[u] = brc[u - 1]; bt[u] = bt[u - 1]; --u; }
+                    brc[u] = rc; bt[u] = t;
+                    if (nb == K) worst = brc[K - 1];
+                }
             }
-            if (best_t >= 0) best_a = cand[(size_t)best_t];
             scanned += end - pos;
             pos = (end == nc) ? 0 : end;
-            if (best_a >= 0) { cand_pos = pos; *rc_out = best; return best_a; }
+            if (nb > 0) {
+                cand_pos = pos;
+                qn = 0;
+                for (int u = 1; u < nb; ++u) qt[qn++] = bt[u];
+                *rc_out = brc[0];
+                return cand[(size_t)bt[0]];
+            }
         }
         return -1;
     }
