@@ -140,10 +140,12 @@ struct Solver {
         const int end = last[r];
         const int* th = thread.data();
         double* pt = pot.data();
-        for (int v = r; v != end;) {
+        int steps = 0;
+        for (int v = r; v != end && ++steps < V;) {
             v = th[v];
             pt[v] += d;
         }
+        if (steps >= V) broken = true;
     }
     void recentre() {
         // subtract a common constant (rc is invariant); keep real nodes small
@@ -155,11 +157,17 @@ struct Solver {
     }
     // every potential from its parent's, in pre-order from the root
     void refresh_below_root() {
-        for (int v = root; v != last[root];) {
+        int steps = 0;
+        for (int v = root; v != last[root] && ++steps < V;) {
             v = thread[v];
             pot_from_parent(v);
         }
+        if (steps >= V) broken = true;
     }
+    // set when a walk over the tree runs past V nodes (a corrupted tree, an
+    // internal error): the solve then stops with QWB_ERR_NOT_CONVERGED
+    // instead of looping
+    bool broken = false;
     // thread, rev and last from the parent pointers (children in increasing
     // node order); false when the parent pointers do not form one tree
     bool build_thread() {
@@ -241,7 +249,7 @@ struct Solver {
         if (!build_thread()) return false;
         refresh_below_root();
         recompute_flows();
-        return true;
+        return !broken;
     }
 
     // A starting tree built by the caller (not a previous final tree): after
@@ -262,6 +270,7 @@ struct Solver {
     }
     void reset_tree() {
         std::fill(parent.begin(), parent.end(), -1);
+        broken = false;
     }
 
     // minimum of c[t] + pg[t] over a contiguous run: four independent chains
@@ -579,7 +588,9 @@ struct Solver {
         wk[nk++] = u;
         if (mark[w] == sk) apex = w;
         else { mark[w] = sl; wl[nl++] = w; }
+        int guard = 0;
         while (apex < 0) {
+            if (++guard > 2 * V) { broken = true; return; }
             if (u != root) {
                 u = parent[u];
                 if (mark[u] == sl) { apex = u; break; }
@@ -633,7 +644,7 @@ struct Solver {
         const int q_parent = parent[q];
         thread[rold[t]] = aold[t];                   // cut T out
         rev[aold[t]] = rold[t];
-        for (int u = q_parent; u >= 0 && last[u] == lold[t]; u = parent[u]) last[u] = rold[t];
+        for (int u = q_parent, k2 = 0; u >= 0 && last[u] == lold[t] && k2 < V; u = parent[u], ++k2) last[u] = rold[t];
         int tl = lold[0];                            // end of the new order so far
         for (int s2 = 1; s2 <= t; ++s2) {
             const int v = path[s2];
@@ -651,7 +662,7 @@ struct Solver {
             thread[e2] = e1; rev[e1] = e2;
             thread[tl] = nx; rev[nx] = tl;
             if (leaf)
-                for (int u = e2; u >= 0 && last[u] == e2; u = parent[u]) last[u] = tl;
+                for (int u = e2, k2 = 0; u >= 0 && last[u] == e2 && k2 < V; u = parent[u], ++k2) last[u] = tl;
         }
         // parent pointers, arcs and flows along the reversed path
         old_pred.resize(t); old_up.resize(t); old_flow.resize(t);
@@ -676,10 +687,12 @@ struct Solver {
     // pre-order: every node after all of its descendants).
     void recompute_flows() {
         std::vector<double> S(supply);
-        for (int v = rev[root]; v != root; v = rev[v]) {
+        int steps = 0;
+        for (int v = rev[root]; v != root && steps++ < V; v = rev[v]) {
             flow[v] = up[v] ? S[v] : -S[v];
             S[parent[v]] += S[v];
         }
+        if (steps >= V) broken = true;
     }
 };
 
@@ -699,8 +712,8 @@ int solve(int32_t n_src, int32_t n_dst, Cost cst, double maxc, const double* a, 
     bool started = false;
     if (warm && warm->valid && (int)warm->parent.size() == n_src + n_dst) {
         if (!warm_built) {
-            S.init_basis(*warm);
-            started = true;
+            started = S.init_basis(*warm);
+            if (!started) S.reset_tree();
         } else {
             double mass = 0.0;
             for (int i = 0; i < n_src; ++i) mass += a[i];
@@ -722,6 +735,7 @@ int solve(int32_t n_src, int32_t n_dst, Cost cst, double maxc, const double* a, 
             // rounding would hide every row from the separable row filter)
             if (S.sparse) {
                 S.recentre();
+                if (S.broken) return QWB_ERR_NOT_CONVERGED;
                 const int64_t added = S.add_violators();
                 if (S.bad_cost) return QWB_ERR_INVALID_ARG;
                 if (added > 0) continue;
@@ -730,9 +744,12 @@ int solve(int32_t n_src, int32_t n_dst, Cost cst, double maxc, const double* a, 
         }
         if (++piv > max_pivots) return QWB_ERR_NOT_CONVERGED;
         S.pivot(e);
+        if (S.broken) return QWB_ERR_NOT_CONVERGED;
         if (piv % recentre_every == 0) S.recentre();
+        if (S.broken) return QWB_ERR_NOT_CONVERGED;
     }
     S.recompute_flows();
+    if (S.broken) return QWB_ERR_NOT_CONVERGED;
     double mass = 0.0;
     for (int i = 0; i < n_src; ++i) mass += a[i];
     for (int v = 0; v < S.n + S.m; ++v)

@@ -64,6 +64,32 @@ def test_network_simplex_random_dense(lib, seed):
     assert float(r["f"] @ a + r["g"] @ b) == pytest.approx(obj, rel=1e-9, abs=1e-12)
 
 
+@pytest.mark.parametrize("seed", range(12))
+def test_network_simplex_degenerate_dense(lib, seed):
+    """Integer costs from a few values (many ties, degenerate pivots) and
+    zero masses on both sides, rectangular shapes: the oracle's optimum,
+    exact marginals, a basic plan and feasible potentials.  Exercises the
+    tree updates of long pivot sequences (re-rooted subtrees, empty and
+    re-filled subtrees, zero-flow arcs)."""
+    rng = np.random.default_rng(100 + seed)
+    n, m = rng.integers(2, 70, size=2)
+    C = rng.integers(0, 4 if seed % 2 else 40, size=(n, m)).astype(np.float64)
+    a = rng.random(n) * (rng.random(n) > 0.25)
+    b = rng.random(m) * (rng.random(m) > 0.2)
+    a[0] += 0.1; b[-1] += 0.1
+    a /= a.sum(); b /= b.sum()
+    r = _solve(C, a, b)
+    obj = O.exact_ot(C, a, b)[3]
+    assert r["obj"] == pytest.approx(obj, rel=1e-10, abs=1e-13)
+    assert len(r["val"]) <= n + m - 1
+    plan = np.zeros((n, m))
+    for i in range(n):
+        for e in range(r["rowptr"][i], r["rowptr"][i + 1]):
+            plan[i, r["col"][e]] += r["val"][e]
+    assert np.abs(plan.sum(1) - a).max() < 1e-13 and np.abs(plan.sum(0) - b).max() < 1e-13
+    assert (C - r["f"][:, None] - r["g"][None, :]).min() >= -1e-12 * max(C.max(), 1.0)
+
+
 @pytest.mark.parametrize("p", [1.0, 2.0])
 @pytest.mark.parametrize("cls", ["white", "gauss", "field"])
 def test_network_simplex_grid_costs(lib, p, cls):
