@@ -502,10 +502,16 @@ struct Solver {
                 scan_run(i, 0, m, best, dummy);       // row minimum below -eps?
                 if (dummy < 0) continue;
             }
-            row_costs(i, rcs.data());
+            const double* crow;
+            if constexpr (std::is_same<Cost, DenseCost>::value) {
+                crow = cst.C + (int64_t)i * m;
+            } else {
+                row_costs(i, rcs.data());
+                crow = rcs.data();
+            }
             const double pi = pot[i];
-            for (int j = 0; j < m; ++j) {
-                const double rc = rcs[j] - pi + pg[j];
+            auto take = [&](int j) {
+                const double rc = crow[j] - pi + pg[j];
                 if (rc < -eps) {
                     const int64_t a = (int64_t)i * m + j;
                     if (!((in_cand[(size_t)(a >> 6)] >> (a & 63)) & 1ull)) {
@@ -513,7 +519,20 @@ struct Solver {
                         ++added;
                     }
                 }
+            };
+            // four reduced costs per step on two-lane vectors (the same sums
+            // as the scalar test), which looks at a group only when it holds
+            // a violator
+            const v2d vpi = {pi, pi}, vlim = {-eps, -eps};
+            int j = 0;
+            for (; j + 4 <= m; j += 4) {
+                const v2d r0 = load2(crow + j) - vpi + load2(pg + j);
+                const v2d r1 = load2(crow + j + 2) - vpi + load2(pg + j + 2);
+                const auto hit = (r0 < vlim) | (r1 < vlim);
+                if (hit[0] | hit[1])
+                    for (int t = j; t < j + 4; ++t) take(t);
             }
+            for (; j < m; ++j) take(j);
         }
         return added;
     }
