@@ -51,7 +51,7 @@ enum {
     QWB_ERR_INVALID_ARG = 1,   /* null pointer, N % kappa != 0, p < 1, sizes */
     QWB_ERR_MASS = 2,          /* negative / non-finite entry or |mass - 1| > 1e-12 */
     QWB_ERR_CUDA = 3,          /* a CUDA runtime call failed (message has details) */
-    QWB_ERR_NOT_CONVERGED = 4, /* the exact coarse solver hit its pivot cap */
+    QWB_ERR_NOT_CONVERGED = 4, /* the exact coarse solver hit its pivot cap (or found its tree corrupted) */
     QWB_ERR_TIMEOUT = 5,       /* a bounded device-side wait expired */
     QWB_ERR_OOM = 6,           /* device or host allocation failed */
     QWB_ERR_UNSUPPORTED = 7,   /* valid problem outside this build's limits */
@@ -181,7 +181,8 @@ int qwb_coarse_cost_separable(qwb_ctx* ctx, const qwb_problem* prob, const doubl
  * n_src + n_dst), *nnz_out, potentials f_h (n_src) and g_h (n_dst) with
  * f_i + g_j <= C_ij, and *obj_out = <pi, C>.  Any output may be NULL except
  * nnz_out when the plan is requested.  Needs no GPU.
- * Errors: INVALID_ARG, NOT_CONVERGED (pivot cap), OOM. */
+ * Errors: INVALID_ARG, NOT_CONVERGED (pivot cap, or an internal check of the
+ * spanning tree failed), OOM. */
 int qwb_coarse_solve(int32_t n_src, int32_t n_dst, const double* C_h, const double* a_h,
                      const double* b_h, int32_t* rowptr_h, int32_t* col_h, double* val_h,
                      int32_t* nnz_out, double* f_h, double* g_h, double* obj_out);
